@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark of the free-flight expansion on GB300: realizations per second.
+
+One step = the whole hot path on one batch of the workload: the per-axis
+passes of eq. FF (pre-chirp, FFT, k-space phase, fold or inverse FFT with the
+post-chirp and term sum) along every axis, then |Psibar|^2 -- every kernel of
+``ffx_expand``.  Inputs are seeded synthetic fields (see
+paper_1602_03395_gb300/inputs.py) resident in HBM when the timed region
+starts; successive steps read distinct realizations from a pool larger than
+L2.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ffx|reference]
+                  [--workload two_cloud|1d|quasicondensate|large_two_cloud|
+                   large_quasicondensate] [--form auto|paper|fold]
+
+Multi-GPU (torchrun, one rank per GPU): realizations are independent, so each
+rank expands its own share with no collective on the data path (weak
+scaling); only the timing is reduced (max over ranks).
+
+``--impl reference`` times the FP64 CPU oracle (oracle/) on the host cores on
+the same workload and prints the same line with "impl": "reference".
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1602_03395_gb300 import inputs  # noqa: E402
+
+METRIC = "realizations/s and HBM GB/s vs peak at rel-L2 density err <=2e-5 vs FP64"
+UNIT = "realizations/s"
+L2_BYTES = 129 * 1024 * 1024
+SMS, FP32_LANES = 152, 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ffx", choices=["ffx", "reference"])
+    ap.add_argument("--workload", default="two_cloud",
+                    choices=["two_cloud", "1d", "quasicondensate", "large_two_cloud",
+                             "large_quasicondensate"])
+    ap.add_argument("--form", default="auto", choices=["auto", "paper", "fold"])
+    ap.add_argument("--batch", type=int, default=None, help="realizations per step (default: workload's)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name, batch):
+    w = inputs.WORKLOADS[name]()
+    if batch is not None:
+        w.batch = batch
+    return w
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return p, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def pass_flops(N: int, lam: int, lines: int, form: str) -> float:
+    """Algorithmic FP32 flops of one axis pass (5 N log2 N per complex FFT of
+    length N; 6 per complex multiply, 2 per complex add).
+    paper form, per term: FFT + IFFT + pre-chirp, k-phase, post-chirp
+    multiplies + accumulate = 10 N log2 N + 20 N.
+    fold form, per term: FFT + pre-chirp and k-phase multiplies + fold add
+    = 5 N log2 N + 14 N; plus one inverse FFT per line."""
+    lg = math.log2(N)
+    if form == "paper":
+        return lines * lam * (10 * N * lg + 20 * N)
+    return lines * (lam * (5 * N * lg + 14 * N) + 5 * N * lg)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def cpu_oracle_rate(w, budget_s=12.0):
+    """The FP64 oracle on the host cores: realizations/s over a bounded sample."""
+    import oracle as O
+    psi = [w.realization(r) for r in range(4)]
+    O.expand_density(psi[0], w.dx, w.t, w.lam)  # warm
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s or n == 0:
+        O.expand_density(psi[n % len(psi)], w.dx, w.t, w.lam)
+        n += 1
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt
+
+
+def run_reference(args):
+    """FP64 CPU oracle, as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = workload(args.workload, args.batch)
+    import oracle as O
+    pool = [w.batch_array(w.batch, start=i * w.batch) for i in range(4)]
+    for i in range(args.warmup):
+        O.expand_density(pool[i % 4], w.dx, w.t, w.lam)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        O.expand_density(pool[i % 4], w.dx, w.t, w.lam)
+    dt = time.perf_counter() - t0
+    value = args.steps * w.batch / dt
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "dims": list(w.dims), "dx": list(w.dx), "lam": list(w.lam),
+                   "t": w.t, "batch": w.batch},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} steps x {w.batch} realization(s) of {w.name}, "
+                                   "FP64 per-axis dense maps via BLAS on all host cores"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def load_traffic(kernel_key: str):
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu
+    summary, if it was taken on the current sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    from paper_1602_03395_gb300 import build as B
+    entry = rec.get(kernel_key)
+    if not entry or entry.get("sources_digest") != B._deps_digest():
+        return None
+    return entry.get("bytes_per_launch")
+
+
+def run_ffx(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1602_03395_gb300 import build as B
+    B.build()
+    from paper_1602_03395_gb300 import ffx
+
+    w = workload(args.workload, args.batch)
+    B_ = w.batch
+    M = int(np.prod(w.dims))
+    plan = ffx.Plan(w.dims, w.dx, w.t, w.lam, form=args.form)
+    form = plan.form
+    order = plan.pass_order()
+    launches = plan.launches_per_call()
+
+    # input pool larger than L2: distinct buffers, each step reads the next one
+    step_in_bytes = B_ * M * 8
+    pool_n = max(2, math.ceil(2 * L2_BYTES / step_in_bytes))
+    pool_n = min(pool_n, 256)
+    distinct = [torch.from_numpy(w.batch_array(B_, start=(rank * 1000 + i) * B_)) for i in range(4)]
+    pool_in = [distinct[i % 4].to(dev) for i in range(pool_n)]
+    pool_out = [torch.empty((B_,) + tuple(w.dims), dtype=torch.float32, device=dev)
+                for _ in range(min(pool_n, 64))]
+    stream = torch.cuda.current_stream(dev)
+
+    # parity of this very configuration against the FP64 oracle (rank 0, first realization)
+    err = None
+    if rank == 0 and M <= 1 << 20:
+        import oracle as O
+        ref = O.expand_density(distinct[0].numpy()[:1], w.dx, w.t, w.lam)
+        got = ffx.ffx_expand(plan, pool_in[0][:1].contiguous()).cpu().numpy()
+        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+    for i in range(args.warmup):
+        ffx.ffx_expand(plan, pool_in[i % pool_n], pool_out[i % len(pool_out)])
+    torch.cuda.synchronize()
+
+    # per-launch events inside the timed region (recorded by the library between launches)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * launches * args.steps)]
+    plan.trace(ev)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        ffx.ffx_expand(plan, pool_in[i % pool_n], pool_out[i % len(pool_out)])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    plan.trace(None)
+    ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+
+    # per-pass durations from the traced events
+    per_pass = [[] for _ in range(launches)]
+    for s in range(args.steps):
+        for k in range(launches):
+            i0 = 2 * (s * launches + k)
+            per_pass[k].append(ev[i0].elapsed_time(ev[i0 + 1]))
+    mean_ms = [statistics.mean(v) for v in per_pass]
+    dom = max(range(launches), key=lambda k: mean_ms[k])
+    axis = order[dom]
+    N, lam = w.dims[axis], w.lam[axis]
+    lines = B_ * M // N
+    flops = pass_flops(N, lam, lines, form)
+    pk, pk_src = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    alu_peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    achieved = flops / (mean_ms[dom] * 1e-3) / 1e12
+    kernel_key = f"pass_{form}_N{N}_lam{lam}_{args.workload}"
+    traffic = load_traffic(kernel_key)
+    # HBM view of the same launch: it reads and writes the batch once (complex64,
+    # the last pass writes float32 densities)
+    last = dom == launches - 1
+    bytes_launch = B_ * M * (8 + (4 if last else 8))
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+
+    value = args.steps * B_ * world / (ms * 1e-3)
+
+    # end to end through the C ABI with host buffers: pinned H2D, expand, D2H
+    h_in = [distinct[i % 4].pin_memory() for i in range(4)]
+    h_out = torch.empty((B_,) + tuple(w.dims), dtype=torch.float32).pin_memory()
+    d_in = torch.empty_like(pool_in[0])
+    d_out = torch.empty((B_,) + tuple(w.dims), dtype=torch.float32, device=dev)
+    for i in range(3):
+        d_in.copy_(h_in[i % 4], non_blocking=True)
+        ffx.ffx_expand(plan, d_in, d_out)
+        h_out.copy_(d_out, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_steps = args.steps
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(e2e_steps):
+        d_in.copy_(h_in[i % 4], non_blocking=True)
+        ffx.ffx_expand(plan, d_in, d_out)
+        h_out.copy_(d_out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e_value = e2e_steps * B_ * world / (e2e_ms * 1e-3)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, n, dt = cpu_oracle_rate(w)
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{n} realizations of {w.name} in {dt:.1f} s, FP64 per-axis dense "
+                         "maps via BLAS on all host cores"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "dims": list(w.dims), "dx": list(w.dx),
+                       "lam": list(w.lam), "t": w.t, "batch_per_gpu": B_, "form": form,
+                       "parallelism": f"replicas x{world} (realizations sharded, no collective)",
+                       "l2": f"rotating pool of {pool_n} input buffers "
+                             f"({pool_n * step_in_bytes / 2**20:.0f} MiB > 129 MB L2)"},
+            "rel_l2_density_err_vs_fp64": err,
+            "gpu_launches": launches * args.steps,
+            "clocks": clocks,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak,
+                         "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": traffic,
+                         "kernel": kernel_key, "launch_ms": mean_ms[dom],
+                         "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
+                                        f"(sm_max_mhz from MEASURED_PEAKS.json, {pk_src})"},
+            "roofline_hbm": {"bound": "hbm", "achieved": bytes_launch / (mean_ms[dom] * 1e-3) / 1e9,
+                             "peak": hbm_peak, "unit": "GB/s",
+                             "frac": bytes_launch / (mean_ms[dom] * 1e-3) / 1e9 / hbm_peak,
+                             "note": f"of {pk_src} hbm_gbs; one read + one write of the batch"},
+            "pass_ms": {f"axis{order[k]}_N{w.dims[order[k]]}_lam{w.lam[order[k]]}": mean_ms[k]
+                        for k in range(launches)},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B_ * M * 8,
+                    "d2h_bytes_per_step": B_ * M * 4},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ffx(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

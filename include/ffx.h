@@ -1,0 +1,190 @@
+/*
+ * ffx -- free-flight expansion of a compact wavefunction onto a magnified
+ * lattice, on one NVIDIA GB300 (sm_103a).
+ *
+ * The operation (Deuar, arXiv:1602.03395, Sec. 5.2, eq. FF with eqs. FFpsi,
+ * presf, presB, presA, FFaux):  an initial field psi_n on the lattice
+ * x_n = a + n dx (eq. xj), n = 0..M-1 per axis, surrounded by vacuum
+ * (eq. vacuum), flies freely for a time t.  The result is produced on the
+ * magnified lattice xbar_nbar = abar + nbar * lam * dx (eq. wbx) with the same
+ * number of points, lam a positive integer per axis (Sec. 5.1).  The map is the
+ * exact free flight of the vacuum-padded field on the periodic lattice of
+ * lam*M points per axis, sampled every lam points (Sec. 5.1 derivation).
+ * Units: hbar = m = 1; a physical hbar*t/m is passed as t.
+ *
+ * The library evaluates eq. FF axis by axis (every phase in it is a product
+ * over axes, so the d-dimensional map is the tensor product of 1-D maps) with
+ * CUDA kernels.  It then forms the density |Psibar|^2 (Sec. 2) and, on
+ * request, sums it over an ensemble of realizations (Sec. 1).
+ *
+ * Conventions shared by every entry point
+ *  - Arrays are row-major (C order); the last axis is contiguous.  A batch of
+ *    B realizations is laid out [B][M_0]...[M_{d-1}].
+ *  - Complex data is interleaved complex64 (float re, float im), 8-byte
+ *    aligned.  Densities are float32.
+ *  - Every data pointer is a DEVICE pointer owned by the caller; the library
+ *    neither frees nor retains it.  The plan owns its phase tables and its
+ *    workspace (device memory).
+ *  - Calls are asynchronous on the given stream (a cudaStream_t passed as
+ *    void*; NULL means the legacy default stream).  No entry point except
+ *    ffx_plan / ffx_plan_destroy synchronizes with the host.
+ *  - Errors are returned as codes, never as exceptions.  ffx_last_error()
+ *    gives a message for the most recent failure in the calling thread.
+ *  - A plan may be used from one host thread at a time.
+ */
+#ifndef FFX_H
+#define FFX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define FFX_OK           0
+#define FFX_EINVAL       1  /* bad argument: dims, lam, spacing, pointer, size */
+#define FFX_ENOMEM       2  /* device allocation failed */
+#define FFX_ECUDA        3  /* a CUDA call failed; see ffx_last_error() */
+#define FFX_EUNSUPPORTED 4  /* valid request this build has no kernel for */
+
+/* ---- plan flags -------------------------------------------------------- */
+/* Form of the per-axis sum over the fine momentum index q (eq. FFpsi).
+ * FFX_FORM_PAPER: every term runs presA (pre-chirp + FFT), presB (k-space
+ *   phase + inverse FFT), then presf with the n'' gather of eq. FFaux, and
+ *   the terms are summed (Sec. 5.2 as printed; 2*lam line FFTs per axis).
+ * FFX_FORM_FOLD: the same sum re-associated: f^(q) times the inverse-FFT
+ *   kernel at n'' equals a plain inverse-DFT kernel at the fine index
+ *   (lam*m + q) mod M, so every term's k-space line is folded into one
+ *   spectrum and a single inverse FFT follows (lam + 1 line FFTs per axis).
+ *   Same map, same rounding class.
+ * 0 (FFX_FORM_AUTO) lets the plan choose (currently FOLD). */
+#define FFX_FORM_AUTO   0x0u
+#define FFX_FORM_PAPER  0x1u
+#define FFX_FORM_FOLD   0x2u
+#define FFX_FORM_MASK   0xFu
+/* ffx_expand writes the SUM over the batch of |Psibar|^2, added to what
+ * out_density holds ([M_0..M_{d-1}], out += sum_b rho_b), instead of one
+ * density per realization.  The sum runs over b in order (deterministic). */
+#define FFX_ACCUMULATE  0x10u
+
+typedef struct ffx_plan_s* ffx_plan_t;
+
+/*
+ * ffx_plan -- build a plan for one lattice geometry and flight time.
+ *
+ *  out           receives the plan handle (set to NULL on failure).
+ *  ndim          number of lattice axes, 1..3.
+ *  dims[ndim]    M_j >= 1, points per axis (row-major order).  Each M_j must
+ *                be a line length this build has a kernel for (see
+ *                ffx_supported_length); others return FFX_EUNSUPPORTED.
+ *  spacing[ndim] dx_j > 0 (Sec. 2.1: dx_j = L_j / M_j).
+ *  t             flight time t_flight (eq. free0), any finite real.
+ *  magnification[ndim]  lam_j >= 1, integers (Sec. 5.1 requires integer
+ *                lam_j); values above 65536 return FFX_EINVAL.
+ *  a[ndim]       input lattice offsets a_j (eq. xj), or NULL for -L_j/2.
+ *  abar[ndim]    output lattice offsets abar_j (eq. wbx), or NULL for
+ *                a_j + s_j dx_j with s_j = -floor((lam_j - 1) M_j / 2), which
+ *                centres the magnified box on the input box.  Any real
+ *                offset is accepted.
+ *  flags         FFX_FORM_* | FFX_ACCUMULATE.
+ *
+ * Runs on the current CUDA device, allocates the plan's phase tables there
+ * and fills them (exact integer / 64-bit fixed-point phase reduction, then
+ * double-precision sincospi), and synchronizes before returning.
+ */
+int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spacing,
+             double t, const int32_t* magnification, const double* a,
+             const double* abar, uint32_t flags);
+
+/* Release the plan's device memory.  NULL is accepted.  Synchronizes the
+ * device first, so work still queued on the plan finishes. */
+int ffx_plan_destroy(ffx_plan_t plan);
+
+/*
+ * ffx_expand -- densities after free flight (eq. FF, then |Psibar|^2).
+ *
+ *  psi0         device complex64 [batch][M...], read only.
+ *  batch        number of realizations B >= 0.  B = 0 does nothing.
+ *  out_density  device float32: [batch][M...] (one density per realization),
+ *               or [M...] with FFX_ACCUMULATE (out += sum_b |Psibar_b|^2).
+ *               Must not overlap psi0.
+ *  stream       cudaStream_t or NULL.
+ *
+ * Uses the plan's workspace (batch * M complex64 for d >= 2), grown on demand:
+ * the first call with a larger batch allocates (cudaMalloc, host-synchronous).
+ */
+int ffx_expand(ffx_plan_t plan, const void* psi0, int64_t batch, float* out_density,
+               void* stream);
+
+/*
+ * ffx_expand_field -- the complex field Psibar itself, [batch][M...] complex64.
+ * out_field may equal psi0 (in place); otherwise the two must not overlap.
+ * Needs no workspace.  The phase of Psibar is that of the magnified lattice,
+ * which Sec. 5.4 warns is not fit for further evolution; its density is exact.
+ */
+int ffx_expand_field(ffx_plan_t plan, const void* psi0, int64_t batch, void* out_field,
+                     void* stream);
+
+/*
+ * ffx_expand_backward -- gradient of a real loss L(rho) with respect to psi0.
+ *
+ *  grad_density  device float32 dL/drho: [batch][M...], or [M...] with
+ *                FFX_ACCUMULATE (the same gradient reaches every realization).
+ *  grad_psi0     device complex64 [batch][M...], overwritten with
+ *                T^H (2 * grad_density * T psi0), i.e. dL/dRe(psi0) +
+ *                i dL/dIm(psi0) (PyTorch's convention for complex inputs).
+ *                T^H is the adjoint of the per-axis maps, applied in reverse
+ *                axis order; T psi0 is recomputed, not stored.
+ *  Uses the plan's workspace (batch * M complex64).
+ */
+int ffx_expand_backward(ffx_plan_t plan, const void* psi0, const float* grad_density,
+                        int64_t batch, void* grad_psi0, void* stream);
+
+/* Apply only the adjoint map: grad_psi0 = T^H g for a complex64 field g
+ * ([batch][M...]).  g_in and g_out may be equal (in place). */
+int ffx_expand_adjoint(ffx_plan_t plan, const void* g_in, int64_t batch, void* g_out,
+                       void* stream);
+
+/* ---- introspection ------------------------------------------------------ */
+
+/* 1 if this build has a line kernel for length n, else 0. */
+int ffx_supported_length(int64_t n);
+
+/* Bytes of plan-owned workspace a call with this batch uses. */
+int64_t ffx_workspace_bytes(ffx_plan_t plan, int64_t batch);
+
+/* The form (FFX_FORM_PAPER or FFX_FORM_FOLD) the plan runs. */
+int ffx_plan_form(ffx_plan_t plan);
+
+/* Number of kernel launches one ffx_expand / ffx_expand_backward call makes
+ * with a non-empty batch. */
+int ffx_launches_per_call(ffx_plan_t plan, int backward);
+
+/* Forward pass order: writes the lattice axis of pass k to order[k],
+ * k = 0..ndim-1.  The adjoint runs the same axes in reverse. */
+int ffx_plan_pass_order(ffx_plan_t plan, int32_t* order);
+
+/* Profiling hook.  events: n_events cudaEvent_t handles (created by the
+ * caller with timing enabled, passed as void*).  Every later kernel launch of
+ * the plan records events[2i] just before and events[2i+1] just after itself
+ * on the call's stream, i counting launches, until the array is full.
+ * NULL (or n_events = 0) switches tracing off.  The library keeps the
+ * pointer, not a copy: the array must outlive the traced calls. */
+int ffx_plan_trace(ffx_plan_t plan, void* const* events, int64_t n_events);
+
+/* Number of events recorded since the last ffx_plan_trace call. */
+int64_t ffx_plan_trace_count(ffx_plan_t plan);
+
+/* Static strings for return codes; never NULL. */
+const char* ffx_error_string(int code);
+
+/* Message for the most recent failure in the calling thread ("" if none). */
+const char* ffx_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFX_H */

@@ -1,0 +1,72 @@
+// Internal types shared by the plan code and the line-pass kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ffx {
+
+// Per-axis phase tables (device memory, filled once per plan).
+//   P [q][n]  = exp(-2 pi i q n / (lam N))                       (eq. presA pre-chirp)
+//   K [q][m]  = exp(2 pi i [l s/N - tau l^2 - (2 tau/lam) l q])  (eq. presB k-space phase)
+//   Kf[q][m]  = K[q][m] * exp(2 pi i [q s/(lam N) - tau q^2/lam^2]) / (lam N)
+//               (the q-only part of eq. presf, and the final scale, moved
+//                before the fold of the fine spectrum)
+//   F [q][nb] = exp(2 pi i [q s/(lam N) + q nb/N - tau q^2/lam^2]) / (lam N)
+//               (eq. presf with the 1/N of the inverse FFT)
+//   tw[k]     = exp(-2 pi i k / N)                               (FFT twiddles)
+//   fold[r]   = m0 with lam*m0 = r (mod N) when gcd(lam,N) | r, else -1
+// with s = (abar - a)/dx, tau = pi t / L^2, l the symmetric index of eq. kj
+// (odd-N umklapp of Sec. 5.2 applied for q >= lam/2).
+struct AxisTables {
+  const float2* P;
+  const float2* K;
+  const float2* Kf;
+  const float2* F;
+  const float2* tw;
+  const int* fold;
+};
+
+enum PassKind : int { KIND_FWD_PAPER = 0, KIND_FWD_FOLD = 1, KIND_ADJ_FOLD = 2 };
+
+// One pass of the 1-D map (or its adjoint) along one lattice axis, over every
+// line of a [B][outer][N][inner] complex64 array.
+struct PassArgs {
+  const float2* in;      // input lines (complex64)
+  const float* grad;     // non-null: input element is 2 * grad * in (adjoint's first pass)
+  float2* out_c;         // complex output (may equal in), or null
+  float* out_d;          // density output, or null
+  int64_t outer;         // product of the axes before this one (per realization)
+  int64_t inner;         // product of the axes after this one (the axis stride)
+  int64_t M;             // points per realization
+  int64_t batch;         // realizations
+  int64_t nlines;        // lines covered by the tile grid
+  int acc;               // 1: out_d[M] += sum over the batch (tiles loop over b)
+  int grad_shared;       // 1: grad is [M], shared by every realization
+  int lam;               // magnification lam
+  int g;                 // gcd(lam, N)
+  int Np;                // N / g
+  AxisTables tab;
+};
+
+// Launch one pass.  Returns a cudaError_t.
+typedef cudaError_t (*PassLauncher)(const PassArgs& a, int grid, cudaStream_t stream);
+
+struct PassKernelInfo {
+  PassLauncher launch;
+  const void* func;   // kernel symbol (for occupancy queries)
+  int threads;        // threads per block
+  int lines;          // lines per tile
+  size_t smem;        // dynamic shared memory bytes
+};
+
+// Kernel registry: returns false if no kernel exists for (N, kind).
+bool find_pass_kernel(int N, int kind, PassKernelInfo* out);
+bool supported_length(int64_t N);
+
+// Plan-time table fill (one launch per axis).
+cudaError_t launch_fill_tables(int N, int lam, uint64_t c_sN, uint64_t c_tau, uint64_t c_2tl,
+                               uint64_t c_slN, uint64_t c_tl2, float2* P, float2* K, float2* Kf,
+                               float2* F, float2* tw, cudaStream_t stream);
+
+}  // namespace ffx

@@ -1,0 +1,273 @@
+"""Thin Python binding of libffx (include/ffx.h): argument marshalling only.
+
+Every step of the expansion runs in the library's CUDA kernels; this module
+passes device pointers of PyTorch tensors and the current CUDA stream through
+ctypes.  It fails loudly if the library is missing: there is no fallback.
+
+The names follow the C ABI (``ffx_plan``, ``ffx_expand``, ``ffx_expand_field``,
+``ffx_expand_backward``, ``ffx_expand_adjoint``, ``ffx_plan_destroy``).
+``Plan`` wraps a plan handle; ``expand_density`` is a differentiable
+``torch.autograd.Function`` front end whose backward is the library's
+hand-written adjoint.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libffx.so")
+
+FFX_OK, FFX_EINVAL, FFX_ENOMEM, FFX_ECUDA, FFX_EUNSUPPORTED = 0, 1, 2, 3, 4
+FFX_FORM_AUTO, FFX_FORM_PAPER, FFX_FORM_FOLD = 0x0, 0x1, 0x2
+FFX_ACCUMULATE = 0x10
+
+_FORMS = {"auto": FFX_FORM_AUTO, "paper": FFX_FORM_PAPER, "fold": FFX_FORM_FOLD}
+
+_lib = None
+
+
+class FfxError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {msg} (code {code})")
+        self.code = code
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libffx.so (built by ``paper_1602_03395_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing; build it with "
+                           "`python -m paper_1602_03395_gb300.build`")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32, u32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint32, ctypes.c_double
+    lib.ffx_plan.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(i64), ctypes.POINTER(dbl), dbl,
+                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(dbl), ctypes.POINTER(dbl), u32]
+    lib.ffx_plan.restype = i32
+    lib.ffx_plan_destroy.argtypes = [vp]
+    lib.ffx_plan_destroy.restype = i32
+    lib.ffx_expand.argtypes = [vp, vp, i64, vp, vp]
+    lib.ffx_expand.restype = i32
+    lib.ffx_expand_field.argtypes = [vp, vp, i64, vp, vp]
+    lib.ffx_expand_field.restype = i32
+    lib.ffx_expand_backward.argtypes = [vp, vp, vp, i64, vp, vp]
+    lib.ffx_expand_backward.restype = i32
+    lib.ffx_expand_adjoint.argtypes = [vp, vp, i64, vp, vp]
+    lib.ffx_expand_adjoint.restype = i32
+    lib.ffx_supported_length.argtypes = [i64]
+    lib.ffx_supported_length.restype = i32
+    lib.ffx_workspace_bytes.argtypes = [vp, i64]
+    lib.ffx_workspace_bytes.restype = i64
+    lib.ffx_plan_form.argtypes = [vp]
+    lib.ffx_plan_form.restype = i32
+    lib.ffx_launches_per_call.argtypes = [vp, i32]
+    lib.ffx_launches_per_call.restype = i32
+    lib.ffx_plan_pass_order.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
+    lib.ffx_plan_pass_order.restype = i32
+    lib.ffx_plan_trace.argtypes = [vp, ctypes.POINTER(vp), i64]
+    lib.ffx_plan_trace.restype = i32
+    lib.ffx_plan_trace_count.argtypes = [vp]
+    lib.ffx_plan_trace_count.restype = i64
+    lib.ffx_error_string.argtypes = [i32]
+    lib.ffx_error_string.restype = ctypes.c_char_p
+    lib.ffx_last_error.argtypes = []
+    lib.ffx_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(code: int, where: str):
+    if code != FFX_OK:
+        lib = load_library()
+        raise FfxError(code, where, lib.ffx_last_error().decode() or lib.ffx_error_string(code).decode())
+
+
+def _ptr(x: torch.Tensor | None):
+    return None if x is None else ctypes.c_void_p(x.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _need(x: torch.Tensor, dtype, name: str):
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if x.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {x.dtype}")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def ffx_supported_length(n: int) -> bool:
+    return bool(load_library().ffx_supported_length(int(n)))
+
+
+class Plan:
+    """A plan for one geometry (dims, spacing, t, magnification, offsets)."""
+
+    def __init__(self, dims, spacing, t, magnification, a=None, abar=None,
+                 form: str = "auto", accumulate: bool = False):
+        lib = load_library()
+        d = len(dims)
+        self.dims = tuple(int(v) for v in dims)
+        self.spacing = tuple(float(v) for v in spacing)
+        self.t = float(t)
+        self.magnification = tuple(int(v) for v in magnification)
+        self.accumulate = bool(accumulate)
+        flags = _FORMS[form] | (FFX_ACCUMULATE if accumulate else 0)
+        arr = lambda ct, v: (ct * d)(*v) if v is not None else None  # noqa: E731
+        h = ctypes.c_void_p()
+        _check(lib.ffx_plan(ctypes.byref(h), d, arr(ctypes.c_int64, self.dims),
+                            arr(ctypes.c_double, self.spacing), self.t,
+                            arr(ctypes.c_int32, self.magnification),
+                            arr(ctypes.c_double, a), arr(ctypes.c_double, abar), flags), "ffx_plan")
+        self._h = h
+        self.form = {FFX_FORM_PAPER: "paper", FFX_FORM_FOLD: "fold"}[lib.ffx_plan_form(h)]
+        self.M = 1
+        for v in self.dims:
+            self.M *= v
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("plan destroyed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load_library().ffx_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _batch(self, x: torch.Tensor) -> int:
+        if tuple(x.shape[x.dim() - len(self.dims):]) != self.dims:
+            raise ValueError(f"trailing shape {tuple(x.shape)} does not match dims {self.dims}")
+        return int(x.numel() // self.M)
+
+    def workspace_bytes(self, batch: int) -> int:
+        return int(load_library().ffx_workspace_bytes(self.handle, batch))
+
+    def launches_per_call(self, backward: bool = False) -> int:
+        return int(load_library().ffx_launches_per_call(self.handle, int(backward)))
+
+    def pass_order(self):
+        order = (ctypes.c_int32 * len(self.dims))()
+        _check(load_library().ffx_plan_pass_order(self.handle, order), "ffx_plan_pass_order")
+        return tuple(order)
+
+    def trace(self, events):
+        """Record each kernel launch between a pair of the given
+        torch.cuda.Event objects (enable_timing=True); None switches off."""
+        lib = load_library()
+        if not events:
+            self._trace_arr = None
+            _check(lib.ffx_plan_trace(self.handle, None, 0), "ffx_plan_trace")
+            return
+        for ev in events:  # make sure the CUDA events exist
+            if ev.cuda_event == 0:
+                ev.record()
+        arr = (ctypes.c_void_p * len(events))(*[ev.cuda_event for ev in events])
+        self._trace_arr = arr  # the library keeps the pointer
+        _check(lib.ffx_plan_trace(self.handle, arr, len(events)), "ffx_plan_trace")
+
+    def trace_count(self) -> int:
+        return int(load_library().ffx_plan_trace_count(self.handle))
+
+
+def ffx_plan(dims, spacing, t, magnification, a=None, abar=None, form="auto", accumulate=False) -> Plan:
+    return Plan(dims, spacing, t, magnification, a, abar, form, accumulate)
+
+
+def ffx_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def ffx_expand(plan: Plan, psi0: torch.Tensor, out_density: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+    """Densities |Psibar|^2 ([B, *dims] float32), or their batch sum added to
+    ``out_density`` ([*dims]) for an accumulating plan."""
+    _need(psi0, torch.complex64, "psi0")
+    B = plan._batch(psi0)
+    if out_density is None:
+        shape = plan.dims if plan.accumulate else psi0.shape
+        out_density = torch.zeros(shape, dtype=torch.float32, device=psi0.device)
+    _need(out_density, torch.float32, "out_density")
+    _check(load_library().ffx_expand(plan.handle, _ptr(psi0), B, _ptr(out_density), _stream(stream)),
+           "ffx_expand")
+    return out_density
+
+
+def ffx_expand_field(plan: Plan, psi0: torch.Tensor, out_field: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+    _need(psi0, torch.complex64, "psi0")
+    B = plan._batch(psi0)
+    if out_field is None:
+        out_field = torch.empty_like(psi0)
+    _need(out_field, torch.complex64, "out_field")
+    _check(load_library().ffx_expand_field(plan.handle, _ptr(psi0), B, _ptr(out_field), _stream(stream)),
+           "ffx_expand_field")
+    return out_field
+
+
+def ffx_expand_adjoint(plan: Plan, g: torch.Tensor, out: torch.Tensor | None = None,
+                       stream=None) -> torch.Tensor:
+    _need(g, torch.complex64, "g")
+    B = plan._batch(g)
+    if out is None:
+        out = torch.empty_like(g)
+    _need(out, torch.complex64, "out")
+    _check(load_library().ffx_expand_adjoint(plan.handle, _ptr(g), B, _ptr(out), _stream(stream)),
+           "ffx_expand_adjoint")
+    return out
+
+
+def ffx_expand_backward(plan: Plan, psi0: torch.Tensor, grad_density: torch.Tensor,
+                        grad_psi0: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    _need(psi0, torch.complex64, "psi0")
+    _need(grad_density, torch.float32, "grad_density")
+    B = plan._batch(psi0)
+    if grad_psi0 is None:
+        grad_psi0 = torch.empty_like(psi0)
+    _need(grad_psi0, torch.complex64, "grad_psi0")
+    _check(load_library().ffx_expand_backward(plan.handle, _ptr(psi0), _ptr(grad_density), B,
+                                              _ptr(grad_psi0), _stream(stream)), "ffx_expand_backward")
+    return grad_psi0
+
+
+class _ExpandDensity(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, psi0, plan):
+        psi0 = psi0.contiguous()
+        ctx.plan = plan
+        ctx.save_for_backward(psi0)
+        return ffx_expand(plan, psi0)
+
+    @staticmethod
+    def backward(ctx, grad):
+        (psi0,) = ctx.saved_tensors
+        g = ffx_expand_backward(ctx.plan, psi0, grad.contiguous().to(torch.float32))
+        return g, None
+
+
+def expand_density(psi0: torch.Tensor, plan: Plan) -> torch.Tensor:
+    """Differentiable densities after free flight (gradient via the adjoint kernels)."""
+    return _ExpandDensity.apply(psi0, plan)
