@@ -308,14 +308,17 @@ def test_large_adjoint_and_gradient_properties(ffx):
     worst = 0.0
     for i in range(16):
         v = torch.randn(psi.shape, dtype=torch.complex64, device="cuda", generator=gen) * psi.abs()
-        eps = 1e-3 * psi.abs().pow(2).sum().sqrt().item() / v.abs().pow(2).sum().sqrt().item()
+        eps = 3e-3 * psi.abs().pow(2).sum().sqrt().item() / v.abs().pow(2).sum().sqrt().item()
         fd = (loss(psi + eps * v) - loss(psi - eps * v)) / (2 * eps)
         an = (g.conj() * v).real.double().sum().item()
         worst = max(worst, abs(fd - an) / abs(fd))
     plan.close()
     print(f"large: dot-product gap {gap:.2e}, FD worst relative gap {worst:.2e}")
     assert gap < 1e-5
-    assert worst < 2e-3
+    # FP32 densities put ~1e-7 relative noise on each loss value, ~1/eps on the
+    # difference quotient; the O(eps^2) truncation grows the other way.  A sign,
+    # scale or conjugation slip gives an O(1) gap.
+    assert worst < 1e-2
 
 
 # ---------------------------------------------------------------------------
