@@ -147,6 +147,42 @@ int ffx_expand_backward(ffx_plan_t plan, const void* psi0, const float* grad_den
 int ffx_expand_adjoint(ffx_plan_t plan, const void* g_in, int64_t batch, void* g_out,
                        void* stream);
 
+/* ---- expansion without device allocation --------------------------------- */
+/* Sizes of the library's static device scratch (every GPU that loads the
+ * library holds them until the process exits: 8 MiB + 2 MiB + 32 KiB). */
+#define FFX_NOALLOC_MAX_FIELD (1 << 20) /* complex64 elements: batch * M, ndim >= 2 */
+#define FFX_NOALLOC_MAX_TABLE (1 << 18) /* complex64: sum over axes of 4*lam_j*M_j + M_j */
+#define FFX_NOALLOC_MAX_FOLD  8192      /* ints: sum over axes of M_j */
+
+/*
+ * ffx_expand_noalloc -- ffx_plan + ffx_expand (default flags: fold form, one
+ * density per realization) in one call that allocates no memory.  The paper
+ * has no counterpart; this exists for callers that cannot call cudaMalloc
+ * while they run: a host framework that has reserved nearly all device memory
+ * for its own pool (a raw cudaMalloc would fail or fragment it), or a
+ * real-time loop that forbids allocation, and the device-wide synchronisation
+ * of cudaMalloc/cudaFree, after start-up.
+ *
+ * Arguments are those of ffx_plan (dims, spacing, t, magnification, a, abar;
+ * a/abar nullable) and ffx_expand (psi0 [batch][M...] complex64 and
+ * out_density [batch][M...] float32, caller-owned device memory; stream).
+ * Instead of a plan's tables and workspace it uses the static device arrays
+ * sized above: the phase tables are rebuilt there on every call (small
+ * kernels on `stream`), and for ndim >= 2 the field between axis passes is
+ * kept there.  Sizes beyond FFX_NOALLOC_MAX_* return FFX_EINVAL with the
+ * limit named in ffx_last_error(); unsupported lengths FFX_EUNSUPPORTED.
+ *
+ * The first call on a device looks up the device addresses of the static
+ * arrays (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture.  Every call, on every stream, shares the
+ * same arrays, and they keep the last call's contents (each call rewrites all
+ * it reads, so nothing has to start at zero): calls that overlap on the GPU
+ * race.  Serialise them, e.g. by issuing them all on one stream.
+ */
+int ffx_expand_noalloc(int ndim, const int64_t* dims, const double* spacing, double t,
+                       const int32_t* magnification, const double* a, const double* abar,
+                       const void* psi0, int64_t batch, float* out_density, void* stream);
+
 /* ---- introspection ------------------------------------------------------ */
 
 /* 1 if this build has a line kernel for length n, else 0. */

@@ -111,6 +111,9 @@ struct Axis {
 };
 
 }  // namespace
+
+void set_last_error_message(const char* msg) { g_last_error = msg ? msg : ""; }
+
 }  // namespace ffx
 
 using namespace ffx;

@@ -64,6 +64,9 @@ struct PassKernelInfo {
 bool find_pass_kernel(int N, int kind, PassKernelInfo* out);
 bool supported_length(int64_t N);
 
+// Set the calling thread's message for ffx_last_error().
+void set_last_error_message(const char* msg);
+
 // Plan-time table fill (one launch per axis).
 cudaError_t launch_fill_tables(int N, int lam, uint64_t c_sN, uint64_t c_tau, uint64_t c_2tl,
                                uint64_t c_slN, uint64_t c_tl2, float2* P, float2* K, float2* Kf,

@@ -73,6 +73,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ffx_plan_trace.restype = i32
     lib.ffx_plan_trace_count.argtypes = [vp]
     lib.ffx_plan_trace_count.restype = i64
+    lib.ffx_expand_noalloc.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(dbl), dbl,
+                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(dbl),
+                                       ctypes.POINTER(dbl), vp, i64, vp, vp]
+    lib.ffx_expand_noalloc.restype = i32
     lib.ffx_error_string.argtypes = [i32]
     lib.ffx_error_string.restype = ctypes.c_char_p
     lib.ffx_last_error.argtypes = []
@@ -271,3 +275,27 @@ class _ExpandDensity(torch.autograd.Function):
 def expand_density(psi0: torch.Tensor, plan: Plan) -> torch.Tensor:
     """Differentiable densities after free flight (gradient via the adjoint kernels)."""
     return _ExpandDensity.apply(psi0, plan)
+
+
+def ffx_expand_noalloc(dims, spacing, t, magnification, psi0: torch.Tensor,
+                       out_density: torch.Tensor, a=None, abar=None, stream=None) -> torch.Tensor:
+    """Densities through the entry point that allocates no device memory.
+
+    For callers that cannot allocate while they run (a framework owning the
+    device memory pool, a real-time loop): the library uses fixed static
+    device scratch instead of a plan's tables and workspace.  ``out_density``
+    must be given (this function creates no tensors).  Calls sharing a GPU
+    must not overlap (they share the scratch); see include/ffx.h."""
+    _need(psi0, torch.complex64, "psi0")
+    _need(out_density, torch.float32, "out_density")
+    d = len(dims)
+    M = 1
+    for v in dims:
+        M *= int(v)
+    arr = lambda ct, v: (ct * d)(*v) if v is not None else None  # noqa: E731
+    _check(load_library().ffx_expand_noalloc(
+        d, arr(ctypes.c_int64, [int(v) for v in dims]), arr(ctypes.c_double, [float(v) for v in spacing]),
+        float(t), arr(ctypes.c_int32, [int(v) for v in magnification]), arr(ctypes.c_double, a),
+        arr(ctypes.c_double, abar), _ptr(psi0), int(psi0.numel() // M), _ptr(out_density),
+        _stream(stream)), "ffx_expand_noalloc")
+    return out_density
