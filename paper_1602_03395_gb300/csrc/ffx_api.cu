@@ -157,6 +157,27 @@ int grid_for(const PassKernelInfo& info, int sms) {
   return per_sm * sms;
 }
 
+// Thread groups per line (qg): split a line's q-sum over qg groups when the
+// lines alone cannot fill the GPU.  Cost model: waves of resident blocks times
+// the q-terms each group runs (plus one for the epilogue); ties keep fewer groups.
+int choose_qg(const PassKernelInfo& k, int64_t nlines, int lam, int capacity) {
+  int best = 1;
+  double best_cost = 1e300;
+  const int qmax = k.max_qg < lam ? k.max_qg : lam;
+  for (int qg = 1; qg <= qmax; ++qg) {
+    const int lines = pass_lines_per_tile(k, qg);
+    if (lines < 1) break;
+    const int64_t tiles = (nlines + lines - 1) / lines;
+    const int64_t waves = (tiles + capacity - 1) / capacity;
+    const double cost = (double)waves * ((lam + qg - 1) / qg + 1);
+    if (cost < best_cost * (1.0 - 1e-9)) {
+      best_cost = cost;
+      best = qg;
+    }
+  }
+  return best;
+}
+
 int prepare_kernel(PassKernelInfo& info) {
   cudaError_t e = cudaFuncSetAttribute(info.func, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)info.smem);
@@ -218,8 +239,13 @@ int run_pass(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* 
   a.tab.tw = ax.tw;
   a.tab.fold = ax.fold;
   const PassKernelInfo& info = adjoint ? ax.adj : ax.fwd;
-  const int64_t ntiles = (a.nlines + info.lines - 1) / info.lines;
-  int64_t grid = adjoint ? ax.grid_adj : ax.grid_fwd;
+  const int capacity = adjoint ? ax.grid_adj : ax.grid_fwd;
+  // The split depends on one realization's lines only, so a realization's
+  // result does not depend on the batch it came in (bitwise).
+  a.qg = choose_qg(info, outer * inner, ax.lam, capacity);
+  const int lines = pass_lines_per_tile(info, a.qg);
+  const int64_t ntiles = (a.nlines + lines - 1) / lines;
+  int64_t grid = capacity;
   if (grid > ntiles) grid = ntiles;
   if (grid < 1) grid = 1;
   const bool traced = p->trace && p->trace_i + 2 <= p->trace_n;

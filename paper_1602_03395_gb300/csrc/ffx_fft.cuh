@@ -178,15 +178,27 @@ struct Padded {
   static constexpr int value = N + N / 16 + 1;
 };
 
-// Synchronise the T threads of one line.  Lines of <= 32 threads sit inside a
-// warp (the block is laid out line-major with T | 32); longer lines use a named
-// barrier per line (ids 1..15; id 0 is __syncthreads).
+// Synchronise the T threads of one line-group.  Groups of <= 32 threads sit
+// inside a warp on consecutive lanes (T is a power of two dividing 32, blocks
+// are laid out group-major) and synchronise with their own lane mask, so other
+// groups of the warp may be elsewhere; longer groups use a named barrier per
+// group (ids 1..15; id 0 is __syncthreads).  `key` comes from line_sync_key.
 template <int T>
-__device__ __forceinline__ void line_sync(int line_in_block) {
-  if constexpr (T <= 32) {
-    __syncwarp();
+__device__ __forceinline__ unsigned line_sync_key(int group_in_block, int tid) {
+  static_assert((T & (T - 1)) == 0, "threads per line must be a power of two");
+  if constexpr (T >= 32) {
+    return T == 32 ? 0xffffffffu : 1u + (unsigned)group_in_block;
   } else {
-    asm volatile("bar.sync %0, %1;" ::"r"(1 + line_in_block), "r"(T) : "memory");
+    return ((1u << T) - 1u) << ((tid & 31) & ~(T - 1));
+  }
+}
+
+template <int T>
+__device__ __forceinline__ void line_sync(unsigned key) {
+  if constexpr (T <= 32) {
+    __syncwarp(key);
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(key), "r"(T) : "memory");
   }
 }
 
@@ -247,14 +259,14 @@ __device__ __forceinline__ void store_owned(const float2 (&v)[P::E], float2* __r
 
 template <class P, int STAGE, bool INV>
 __device__ __forceinline__ void fft_from(float2 (&v)[P::E], float2* line, const float2* tw, int t,
-                                         int lib) {
+                                         unsigned key) {
   stage_compute<P, STAGE, INV>(v, tw, t);
   if constexpr (STAGE + 1 < P::S) {
-    line_sync<P::T>(lib);  // earlier readers of `line` are done
+    line_sync<P::T>(key);  // earlier readers of `line` are done
     stage_store<P, STAGE>(v, line, t);
-    line_sync<P::T>(lib);
+    line_sync<P::T>(key);
     load_owned<P>(v, line, t);
-    fft_from<P, STAGE + 1, INV>(v, line, tw, t, lib);
+    fft_from<P, STAGE + 1, INV>(v, line, tw, t, key);
   }
 }
 
@@ -265,8 +277,8 @@ __device__ __forceinline__ void fft_from(float2 (&v)[P::E], float2* line, const 
 // it again.
 template <class P, bool INV>
 __device__ __forceinline__ void fft_line(float2 (&v)[P::E], float2* line, const float2* tw, int t,
-                                         int lib) {
-  fft_from<P, 0, INV>(v, line, tw, t, lib);
+                                         unsigned key) {
+  fft_from<P, 0, INV>(v, line, tw, t, key);
 }
 
 }  // namespace ffx

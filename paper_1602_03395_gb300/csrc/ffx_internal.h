@@ -46,19 +46,26 @@ struct PassArgs {
   int lam;               // magnification lam
   int g;                 // gcd(lam, N)
   int Np;                // N / g
+  int qg;                // thread groups sharing one line's q-sum (0 or 1: none)
   AxisTables tab;
 };
 
 // Launch one pass.  Returns a cudaError_t.
 typedef cudaError_t (*PassLauncher)(const PassArgs& a, int grid, cudaStream_t stream);
 
+// A block holds `groups` line-groups of T threads (threads = groups * T).  With
+// qg groups per line, a tile is groups / qg lines.
 struct PassKernelInfo {
   PassLauncher launch;
   const void* func;   // kernel symbol (for occupancy queries)
-  int threads;        // threads per block
-  int lines;          // lines per tile
+  int threads;        // threads per block at most (groups * T)
+  int lines;          // lines per tile with qg = 1 (= groups)
+  int T;              // threads per line-group
+  int max_qg;         // largest qg the kernel accepts (1 when lines need named barriers)
   size_t smem;        // dynamic shared memory bytes
 };
+
+inline int pass_lines_per_tile(const PassKernelInfo& k, int qg) { return k.lines / (qg > 1 ? qg : 1); }
 
 // Kernel registry: returns false if no kernel exists for (N, kind).
 bool find_pass_kernel(int N, int kind, PassKernelInfo* out);

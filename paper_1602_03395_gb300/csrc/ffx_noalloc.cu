@@ -249,7 +249,8 @@ extern "C" int ffx_expand_noalloc(int ndim, const int64_t* dims, const double* s
     pa.g = A.g;
     pa.Np = A.Np;
     pa.tab = A.tab;
-    const int64_t ntiles = (pa.nlines + A.info.lines - 1) / A.info.lines;
+    const int64_t ntiles = (pa.nlines + pass_lines_per_tile(A.info, pa.qg) - 1) /
+                           pass_lines_per_tile(A.info, pa.qg);
     int64_t grid = A.grid < ntiles ? A.grid : ntiles;
     if (grid < 1) grid = 1;
     e = A.info.launch(pa, (int)grid, s);

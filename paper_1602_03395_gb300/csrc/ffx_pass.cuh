@@ -1,15 +1,18 @@
 // One pass of the per-axis free-flight map (eq. FF restricted to one axis),
 // or of its adjoint, over every line of a [B][outer][N][inner] complex64 array.
 //
-// A block handles LINES lines at a time (a tile), LINES * T threads, T = N/E
-// threads per line.  The tile is loaded into shared memory with coalesced
-// accesses, each line is transformed by its T threads in registers (see
-// ffx_fft.cuh), and the result is staged back through shared memory and
+// A block holds G line-groups of T = N/E threads.  qg groups share one line
+// and split its sum over the fine momentum index q (group r takes
+// q = r, r + qg, ...; the paper notes the terms are independent, Sec. 7.1),
+// so a tile is G/qg lines.  The tile is loaded into shared memory with
+// coalesced accesses; each group transforms its line in registers (see
+// ffx_fft.cuh); the groups' partial sums are added in shared memory in group
+// order (deterministic); the result is staged back through shared memory and
 // stored coalesced: complex64, or |.|^2 as float32, or |.|^2 summed over the
 // realizations of the batch (tiles then loop over b in order, so the sum is
 // deterministic and needs no atomics).
 //
-// Kinds (q runs over the fine momentum index 0..lam-1 of eq. FF):
+// Kinds:
 //  FWD_PAPER: acc += F_q * IFFT(K_q * FFT(P_q * psi))[(lam nb) mod N]
 //             -- eqs. presA, presB, presf, FFaux and the term sum FFpsi.
 //  FWD_FOLD : D[(lam m + q) mod N] += Kf_q[m] * FFT(P_q * psi)[m]; out = IFFT(D)
@@ -24,23 +27,36 @@
 
 namespace ffx {
 
-template <class P, int LINES>
+template <class P, int G>
 struct PassSmem {
   static constexpr int NP = Padded<P::N>::value;
   static constexpr size_t tw_off = 0;
   static constexpr size_t fold_off = tw_off + sizeof(float2) * P::N;
   static constexpr size_t base_off = (fold_off + sizeof(int) * P::N + 15) & ~size_t(15);
-  static constexpr size_t b_off = base_off + sizeof(long long) * LINES;
-  static constexpr size_t psi_off = (b_off + sizeof(int) * LINES + 15) & ~size_t(15);
-  static constexpr size_t work_off = psi_off + sizeof(float2) * LINES * NP;
-  static constexpr size_t bytes = work_off + sizeof(float2) * LINES * NP;
+  static constexpr size_t b_off = base_off + sizeof(long long) * G;
+  static constexpr size_t psi_off = (b_off + sizeof(int) * G + 15) & ~size_t(15);
+  static constexpr size_t work_off = psi_off + sizeof(float2) * G * NP;
+  static constexpr size_t bytes = work_off + sizeof(float2) * G * NP;
 };
 
-template <class P, int KIND, int LINES>
-__global__ void __launch_bounds__(P::T * LINES)
+// Element idx of a tile copy -> (line l, point n): along n for contiguous
+// lines, along the line index for strided ones (neighbouring lines are
+// neighbours in memory), so either way the copy is coalesced.
+__device__ __forceinline__ void tile_coords(int idx, int N, int lines, bool contiguous, int& l, int& n) {
+  if (contiguous) {
+    l = idx / N;
+    n = idx - l * N;
+  } else {
+    n = idx / lines;
+    l = idx - n * lines;
+  }
+}
+
+template <class P, int KIND, int G>
+__global__ void __launch_bounds__(P::T * G)
     pass_kernel(const PassArgs a) {
   constexpr int N = P::N, E = P::E, T = P::T;
-  using SM = PassSmem<P, LINES>;
+  using SM = PassSmem<P, G>;
   constexpr int NP = SM::NP;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tw_s = reinterpret_cast<float2*>(smem + SM::tw_off);
@@ -51,10 +67,15 @@ __global__ void __launch_bounds__(P::T * LINES)
   float2* work_s = reinterpret_cast<float2*>(smem + SM::work_off);
 
   if (a.acc && a.batch <= 0) return;  // nothing to sum (the host never launches this)
+  const int QG = a.qg > 1 ? a.qg : 1;
+  const int LINES = G / QG;
+  const int NT = LINES * QG * T;  // == blockDim.x
   const int tid = threadIdx.x;
-  const int lib = tid / T;  // line in block
-  const int t = tid - lib * T;
-  constexpr int NT = T * LINES;
+  const int lg = tid / T;  // line-group in block: line-major, group-minor
+  const int t = tid - lg * T;
+  const int line = lg / QG;
+  const int grp = lg - line * QG;
+  const unsigned key = line_sync_key<T>(lg, tid);
 
   for (int i = tid; i < N; i += NT) {
     tw_s[i] = a.tab.tw[i];
@@ -63,15 +84,16 @@ __global__ void __launch_bounds__(P::T * LINES)
 
   const int lam = a.lam;
   const int64_t inner = a.inner;
+  const bool contiguous = (inner == 1);
   const int64_t per_real_lines = a.outer * inner;
   const int64_t ntiles = (a.nlines + LINES - 1) / LINES;
   const int nb_loop = a.acc ? (int)a.batch : 1;
 
-  float2* psi_line = psi_s + lib * NP;
-  float2* wl = work_s + lib * NP;
+  float2* psi_line = psi_s + line * NP;
+  float2* wl = work_s + lg * NP;
 
-  // per-thread index helpers (q-independent)
-  int nii[E];  // (lam * (t + e T)) mod N
+  // per-thread index helper (q-independent): (lam * (t + e T)) mod N
+  int nii[E];
   {
     const int lmod = lam % N;
     const int step = (lmod * T) % N;
@@ -90,7 +112,7 @@ __global__ void __launch_bounds__(P::T * LINES)
     for (int e = 0; e < E; ++e) racc[e] = 0.f;
 
     for (int bl = 0; bl < nb_loop; ++bl) {
-      __syncthreads();  // previous tile's users of base_s / psi_s / work_s are done
+      __syncthreads();  // previous users of base_s / psi_s / work_s are done
       if (tid < LINES) {
         const int64_t gline = tile * LINES + tid;
         long long base = -1;
@@ -110,16 +132,9 @@ __global__ void __launch_bounds__(P::T * LINES)
         b_s[tid] = b;
       }
       __syncthreads();
-      // coalesced load of the tile: contiguous lines along n, strided lines along the line index
       for (int idx = tid; idx < LINES * N; idx += NT) {
         int l, n;
-        if (inner == 1) {
-          l = idx / N;
-          n = idx - l * N;
-        } else {
-          n = idx / LINES;
-          l = idx - n * LINES;
-        }
+        tile_coords(idx, N, LINES, contiguous, l, n);
         const long long base = base_s[l];
         float2 v = make_float2(0.f, 0.f);
         if (base >= 0) {
@@ -138,106 +153,130 @@ __global__ void __launch_bounds__(P::T * LINES)
       __syncthreads();
 
       float2 res[E];
-      if constexpr (KIND == KIND_FWD_PAPER) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) res[e] = make_float2(0.f, 0.f);
-        for (int q = 0; q < lam; ++q) {
+      for (int e = 0; e < E; ++e) res[e] = make_float2(0.f, 0.f);
+
+      if constexpr (KIND == KIND_FWD_PAPER) {
+        for (int q = grp; q < lam; q += QG) {
           const float2* Pq = a.tab.P + (size_t)q * N;
           const float2* Kq = a.tab.K + (size_t)q * N;
           const float2* Fq = a.tab.F + (size_t)q * N;
           float2 v[E];
 #pragma unroll
           for (int e = 0; e < E; ++e) v[e] = cmul(psi_line[pad(t + e * T)], __ldg(Pq + t + e * T));
-          fft_line<P, false>(v, wl, tw_s, t, lib);
+          fft_line<P, false>(v, wl, tw_s, t, key);
 #pragma unroll
           for (int e = 0; e < E; ++e) v[e] = cmul(v[e], __ldg(Kq + t + e * T));
-          fft_line<P, true>(v, wl, tw_s, t, lib);
-          line_sync<T>(lib);
+          fft_line<P, true>(v, wl, tw_s, t, key);
+          line_sync<T>(key);
           store_owned<P>(v, wl, t);
-          line_sync<T>(lib);
+          line_sync<T>(key);
 #pragma unroll
           for (int e = 0; e < E; ++e) res[e] = cfma(__ldg(Fq + t + e * T), wl[pad(nii[e])], res[e]);
         }
       } else if constexpr (KIND == KIND_FWD_FOLD) {
-        float2 D[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) D[e] = make_float2(0.f, 0.f);
         const int g = a.g, Np = a.Np;
-        int qN = 0;  // q mod N
-        for (int q = 0; q < lam; ++q) {
+        int qN = grp % N;  // q mod N
+        const int qstep = QG % N;
+        for (int q = grp; q < lam; q += QG) {
           const float2* Pq = a.tab.P + (size_t)q * N;
           const float2* Kq = a.tab.Kf + (size_t)q * N;
           float2 v[E];
 #pragma unroll
           for (int e = 0; e < E; ++e) v[e] = cmul(psi_line[pad(t + e * T)], __ldg(Pq + t + e * T));
-          fft_line<P, false>(v, wl, tw_s, t, lib);
+          fft_line<P, false>(v, wl, tw_s, t, key);
 #pragma unroll
           for (int e = 0; e < E; ++e) v[e] = cmul(v[e], __ldg(Kq + t + e * T));
-          line_sync<T>(lib);
+          line_sync<T>(key);
           store_owned<P>(v, wl, t);
-          line_sync<T>(lib);
+          line_sync<T>(key);
+          if (g == 1) {
 #pragma unroll
-          for (int e = 0; e < E; ++e) {
-            int jq = t + e * T - qN;
-            if (jq < 0) jq += N;
-            const int m0 = fold_s[jq];
-            if (m0 >= 0) {
-              for (int r = 0; r < g; ++r) D[e] = cadd(D[e], wl[pad(m0 + r * Np)]);
+            for (int e = 0; e < E; ++e) {
+              int jq = t + e * T - qN;
+              if (jq < 0) jq += N;
+              res[e] = cadd(res[e], wl[pad(fold_s[jq])]);
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              int jq = t + e * T - qN;
+              if (jq < 0) jq += N;
+              const int m0 = fold_s[jq];
+              if (m0 >= 0) {
+                for (int r = 0; r < g; ++r) res[e] = cadd(res[e], wl[pad(m0 + r * Np)]);
+              }
             }
           }
-          if (++qN == N) qN = 0;
+          qN += qstep;
+          if (qN >= N) qN -= N;
         }
-        fft_line<P, true>(D, wl, tw_s, t, lib);
-#pragma unroll
-        for (int e = 0; e < E; ++e) res[e] = D[e];
       } else {  // KIND_ADJ_FOLD
-        float2 v[E];
+        // D = FFT(g) once per line (group 0), kept in the line's input buffer
+        if (grp == 0) {
+          float2 v[E];
 #pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = psi_line[pad(t + e * T)];
-        fft_line<P, false>(v, wl, tw_s, t, lib);
-        line_sync<T>(lib);
-        store_owned<P>(v, psi_line, t);  // D = FFT(g) replaces g in the line buffer
-        line_sync<T>(lib);
-#pragma unroll
-        for (int e = 0; e < E; ++e) res[e] = make_float2(0.f, 0.f);
-        int qN = 0;
-        for (int q = 0; q < lam; ++q) {
+          for (int e = 0; e < E; ++e) v[e] = psi_line[pad(t + e * T)];
+          fft_line<P, false>(v, wl, tw_s, t, key);
+          line_sync<T>(key);
+          store_owned<P>(v, psi_line, t);
+        }
+        __syncthreads();
+        int qN = grp % N;
+        const int qstep = QG % N;
+        for (int q = grp; q < lam; q += QG) {
           const float2* Pq = a.tab.P + (size_t)q * N;
           const float2* Kq = a.tab.Kf + (size_t)q * N;
+          float2 v[E];
 #pragma unroll
           for (int e = 0; e < E; ++e) {
             int idx = nii[e] + qN;
             if (idx >= N) idx -= N;
             v[e] = cmulc(psi_line[pad(idx)], __ldg(Kq + t + e * T));
           }
-          fft_line<P, true>(v, wl, tw_s, t, lib);
+          fft_line<P, true>(v, wl, tw_s, t, key);
 #pragma unroll
           for (int e = 0; e < E; ++e) res[e] = cadd(res[e], cmulc(v[e], __ldg(Pq + t + e * T)));
-          if (++qN == N) qN = 0;
+          qN += qstep;
+          if (qN >= N) qN -= N;
         }
       }
 
-      if (a.acc) {
-#pragma unroll
-        for (int e = 0; e < E; ++e) racc[e] += res[e].x * res[e].x + res[e].y * res[e].y;
-      } else {
-        // stage the line in shared memory, then store the tile coalesced
-        line_sync<T>(lib);
+      // add the groups' partial sums in group order (group 0 ends with the line's sum)
+      if (QG > 1) {
+        __syncthreads();  // every group is done with its exchange buffer
         store_owned<P>(res, wl, t);
+        __syncthreads();
+        if (grp == 0) {
+          for (int r = 1; r < QG; ++r) {
+            const float2* other = work_s + (lg + r) * NP;
+#pragma unroll
+            for (int e = 0; e < E; ++e) res[e] = cadd(res[e], other[pad(t + e * T)]);
+          }
+        }
+      }
+      if constexpr (KIND == KIND_FWD_FOLD) {
+        if (QG > 1) __syncthreads();  // the other groups' buffers are read; wl is free again
+        if (grp == 0) fft_line<P, true>(res, wl, tw_s, t, key);
+      }
+
+      if (a.acc) {
+        if (grp == 0) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) racc[e] += res[e].x * res[e].x + res[e].y * res[e].y;
+        }
+      } else {
+        // stage each line (group 0's buffer) in shared memory, then store the tile coalesced
+        __syncthreads();
+        if (grp == 0) store_owned<P>(res, wl, t);
         __syncthreads();
         for (int idx = tid; idx < LINES * N; idx += NT) {
           int l, n;
-          if (inner == 1) {
-            l = idx / N;
-            n = idx - l * N;
-          } else {
-            n = idx / LINES;
-            l = idx - n * LINES;
-          }
+          tile_coords(idx, N, LINES, contiguous, l, n);
           const long long base = base_s[l];
           if (base < 0) continue;
           const int64_t addr = base + (int64_t)n * inner;
-          const float2 v = work_s[l * NP + pad(n)];
+          const float2 v = work_s[(l * QG) * NP + pad(n)];
           if (a.out_c) {
             a.out_c[addr] = v;
           } else {
@@ -248,46 +287,46 @@ __global__ void __launch_bounds__(P::T * LINES)
     }  // batch loop
 
     if (a.acc) {
-      line_sync<T>(lib);
-      float2 tmp[E];
+      __syncthreads();
+      if (grp == 0) {
+        float2 tmp[E];
 #pragma unroll
-      for (int e = 0; e < E; ++e) tmp[e] = make_float2(racc[e], 0.f);
-      store_owned<P>(tmp, wl, t);
+        for (int e = 0; e < E; ++e) tmp[e] = make_float2(racc[e], 0.f);
+        store_owned<P>(tmp, wl, t);
+      }
       __syncthreads();
       for (int idx = tid; idx < LINES * N; idx += NT) {
         int l, n;
-        if (inner == 1) {
-          l = idx / N;
-          n = idx - l * N;
-        } else {
-          n = idx / LINES;
-          l = idx - n * LINES;
-        }
+        tile_coords(idx, N, LINES, contiguous, l, n);
         const long long base = base_s[l];
         if (base < 0) continue;
         // base_s holds the last realization's line; remove its batch offset
         const int64_t addr = base - (int64_t)(nb_loop - 1) * a.M + (int64_t)n * inner;
-        a.out_d[addr] += work_s[l * NP + pad(n)].x;
+        a.out_d[addr] += work_s[(l * QG) * NP + pad(n)].x;
       }
     }
   }
 }
 
-template <class P, int KIND, int LINES>
+template <class P, int KIND, int G>
 cudaError_t launch_pass(const PassArgs& a, int grid, cudaStream_t stream) {
-  using SM = PassSmem<P, LINES>;
-  pass_kernel<P, KIND, LINES><<<grid, P::T * LINES, SM::bytes, stream>>>(a);
+  using SM = PassSmem<P, G>;
+  const int qg = a.qg > 1 ? a.qg : 1;
+  const int threads = (G / qg) * qg * P::T;
+  pass_kernel<P, KIND, G><<<grid, threads, SM::bytes, stream>>>(a);
   return cudaGetLastError();
 }
 
-template <class P, int KIND, int LINES>
+template <class P, int KIND, int G>
 PassKernelInfo pass_info() {
-  using SM = PassSmem<P, LINES>;
+  using SM = PassSmem<P, G>;
   PassKernelInfo info;
-  info.launch = &launch_pass<P, KIND, LINES>;
-  info.func = reinterpret_cast<const void*>(&pass_kernel<P, KIND, LINES>);
-  info.threads = P::T * LINES;
-  info.lines = LINES;
+  info.launch = &launch_pass<P, KIND, G>;
+  info.func = reinterpret_cast<const void*>(&pass_kernel<P, KIND, G>);
+  info.threads = P::T * G;
+  info.lines = G;
+  info.T = P::T;
+  info.max_qg = (P::T <= 32) ? (G < 8 ? G : 8) : 1;
   info.smem = SM::bytes;
   return info;
 }
