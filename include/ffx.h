@@ -103,6 +103,49 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
 int ffx_plan_destroy(ffx_plan_t plan);
 
 /*
+ * ffx_plan_many -- one plan over many instances of possibly different
+ * lattices, magnifications and flight times (an ensemble of realizations,
+ * Sec. 1), run as one persistent kernel per axis pass over a work list of all
+ * instances' tiles, the passes captured in one CUDA graph that is replayed on
+ * every call.
+ *
+ *  descs[n_instances]  one geometry per instance (ndim 1..3, dims, spacing,
+ *                      t, magnification; offsets a/abar if has_offsets, else
+ *                      the defaults of ffx_plan).  Line lengths must be one of
+ *                      16, 32, 48, 64, 96, 128, 192, 256 (FFX_EUNSUPPORTED
+ *                      otherwise).
+ *  flags               FFX_FORM_*; FFX_ACCUMULATE is rejected (instances on
+ *                      different lattices have no common density grid).
+ *
+ * Data are packed: instance i occupies points [off_i, off_i + M_i) of the
+ * input, of the density or field output, and of the gradient buffers, with
+ * off_i from ffx_plan_many_offset (instances in order, no padding).  Calls
+ * take batch = 1 (the whole set).  ffx_expand, ffx_expand_field and
+ * ffx_expand_backward accept such a plan; ffx_expand_adjoint does not
+ * (FFX_EUNSUPPORTED).  The plan allocates its tables and a packed workspace
+ * at creation; the first call of each kind builds its graph (host work and a
+ * small device allocation for the work list).
+ */
+typedef struct ffx_instance_desc {
+  int32_t ndim;
+  int64_t dims[3];
+  double spacing[3];
+  double t;
+  int32_t magnification[3];
+  int32_t has_offsets;
+  double a[3];
+  double abar[3];
+} ffx_instance_desc;
+
+int ffx_plan_many(ffx_plan_t* out, int n_instances, const ffx_instance_desc* descs, uint32_t flags);
+
+/* Packed offset (in points) of instance i, or -1 (not a many-plan, bad i). */
+int64_t ffx_plan_many_offset(ffx_plan_t plan, int i);
+
+/* Points per call: M for a single-lattice plan, sum of M_i for a many-plan. */
+int64_t ffx_plan_points(ffx_plan_t plan);
+
+/*
  * ffx_expand -- densities after free flight (eq. FF, then |Psibar|^2).
  *
  *  psi0         device complex64 [batch][M...], read only.

@@ -132,6 +132,7 @@ struct ffx_plan_s {
   void* tables = nullptr;
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  ManyPlan* many = nullptr;        // set for plans over many instances
   void* const* trace = nullptr;  // caller's cudaEvent_t array (profiling)
   int64_t trace_n = 0;
   int64_t trace_i = 0;
@@ -450,9 +451,42 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
   return FFX_OK;
 }
 
+int ffx_plan_many(ffx_plan_t* out, int n_instances, const ffx_instance_desc* descs, uint32_t flags) {
+  g_last_error.clear();
+  if (!out) return fail(FFX_EINVAL, "out is NULL");
+  *out = nullptr;
+  std::string err;
+  ManyPlan* mp = nullptr;
+  int rc = many_create(&mp, n_instances, descs, flags, &err);
+  if (rc) return fail(rc, "%s", err.c_str());
+  ffx_plan_s* p = new (std::nothrow) ffx_plan_s();
+  if (!p) {
+    many_destroy(mp);
+    return fail(FFX_ENOMEM, "host allocation failed");
+  }
+  p->many = mp;
+  p->ndim = many_max_dim(mp);
+  p->form = many_form(mp);
+  p->M = many_total(mp);
+  *out = p;
+  return FFX_OK;
+}
+
+int64_t ffx_plan_many_offset(ffx_plan_t p, int i) {
+  if (!p || !p->many) return -1;
+  return many_offset(p->many, i);
+}
+
+int64_t ffx_plan_points(ffx_plan_t p) { return p ? p->M : -1; }
+
 int ffx_plan_destroy(ffx_plan_t p) {
   if (!p) return FFX_OK;
   cudaDeviceSynchronize();
+  if (p->many) {
+    many_destroy(p->many);
+    delete p;
+    return FFX_OK;
+  }
   if (p->ws) cudaFree(p->ws);
   if (p->tables) cudaFree(p->tables);
   delete p;
@@ -485,6 +519,7 @@ int64_t ffx_workspace_bytes(ffx_plan_t p, int64_t batch) {
 
 int ffx_launches_per_call(ffx_plan_t p, int backward) {
   if (!p) return -1;
+  if (p->many) return backward ? 2 * p->ndim : p->ndim;  // one persistent kernel per phase
   return backward ? 2 * p->ndim : p->ndim;
 }
 
@@ -495,6 +530,12 @@ int ffx_expand(ffx_plan_t p, const void* psi0, int64_t batch, float* out_density
   int rc;
   if ((rc = check_ptr(psi0, "psi0")) || (rc = check_ptr(out_density, "out_density"))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
+  if (p->many) {
+    if (batch != 1) return fail(FFX_EINVAL, "a many-instance plan takes batch = 1");
+    std::string err;
+    rc = many_expand(p->many, psi0, out_density, nullptr, s, &err);
+    return rc ? fail(rc, "%s", err.c_str()) : FFX_OK;
+  }
   const float2* in = (const float2*)psi0;
   const int d = p->ndim;
   if (d > 1 && (rc = ensure_ws(p, batch))) return rc;
@@ -515,6 +556,12 @@ int ffx_expand_field(ffx_plan_t p, const void* psi0, int64_t batch, void* out_fi
   if (batch == 0) return FFX_OK;
   int rc;
   if ((rc = check_ptr(psi0, "psi0")) || (rc = check_ptr(out_field, "out_field"))) return rc;
+  if (p->many) {
+    if (batch != 1) return fail(FFX_EINVAL, "a many-instance plan takes batch = 1");
+    std::string err;
+    rc = many_expand(p->many, psi0, nullptr, out_field, (cudaStream_t)stream, &err);
+    return rc ? fail(rc, "%s", err.c_str()) : FFX_OK;
+  }
   return forward_field(p, (const float2*)psi0, batch, (float2*)out_field, (cudaStream_t)stream);
 }
 
@@ -524,6 +571,7 @@ int ffx_expand_adjoint(ffx_plan_t p, const void* g_in, int64_t batch, void* g_ou
   if (batch == 0) return FFX_OK;
   int rc;
   if ((rc = check_ptr(g_in, "g_in")) || (rc = check_ptr(g_out, "g_out"))) return rc;
+  if (p->many) return fail(FFX_EUNSUPPORTED, "ffx_expand_adjoint does not take a many-instance plan");
   const float2* cur = (const float2*)g_in;
   for (int k = p->ndim - 1; k >= 0; --k) {
     rc = run_pass(p, p->order[k], true, cur, nullptr, 0, (float2*)g_out, nullptr, 0, batch,
@@ -543,6 +591,12 @@ int ffx_expand_backward(ffx_plan_t p, const void* psi0, const float* grad_densit
   if ((rc = check_ptr(psi0, "psi0")) || (rc = check_ptr(grad_density, "grad_density")) ||
       (rc = check_ptr(grad_psi0, "grad_psi0")))
     return rc;
+  if (p->many) {
+    if (batch != 1) return fail(FFX_EINVAL, "a many-instance plan takes batch = 1");
+    std::string err;
+    rc = many_backward(p->many, psi0, grad_density, grad_psi0, (cudaStream_t)stream, &err);
+    return rc ? fail(rc, "%s", err.c_str()) : FFX_OK;
+  }
   if ((rc = ensure_ws(p, batch))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   float2* ws = (float2*)p->ws;

@@ -4,6 +4,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
+#include "../../include/ffx.h"
+
 namespace ffx {
 
 // Per-axis phase tables (device memory, filled once per plan).
@@ -73,6 +77,18 @@ bool supported_length(int64_t N);
 
 // Set the calling thread's message for ffx_last_error().
 void set_last_error_message(const char* msg);
+
+// Plans over many instances (ffx_many.cu).
+struct ManyPlan;
+int many_create(ManyPlan** out, int n, const ffx_instance_desc* d, uint32_t flags, std::string* err);
+void many_destroy(ManyPlan* mp);
+int64_t many_total(const ManyPlan* mp);
+int64_t many_offset(const ManyPlan* mp, int i);
+int many_form(const ManyPlan* mp);
+int many_max_dim(const ManyPlan* mp);
+int many_expand(ManyPlan* mp, const void* psi0, float* out_d, void* out_c, cudaStream_t s, std::string* err);
+int many_backward(ManyPlan* mp, const void* psi0, const float* grad, void* grad_psi0, cudaStream_t s,
+                  std::string* err);
 
 // Plan-time table fill (one launch per axis).
 cudaError_t launch_fill_tables(int N, int lam, uint64_t c_sN, uint64_t c_tau, uint64_t c_2tl,

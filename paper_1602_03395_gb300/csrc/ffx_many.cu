@@ -1,0 +1,630 @@
+// Plans over many instances of uneven lattices (ffx_plan_many).
+//
+// Realizations of an ensemble are independent (Sec. 1: hundreds or thousands
+// of classical-field realizations), but their lattices and magnifications may
+// differ.  Pass k of every instance (its k-th axis, longest lines first) forms
+// one phase.  A phase is ONE persistent kernel over a work list of (instance,
+// tile range) items, taken from a device counter, biggest first; each item
+// runs the same line-pass tile code as the uniform kernels, picked by the
+// instance's line length.  The phases are separated by kernel boundaries, not
+// device-side waits, and the whole sequence (counter resets + phase kernels)
+// is one CUDA graph, built once per plan and mode and replayed on the caller's
+// stream.  Buffers are packed: instance i occupies points [off_i, off_i + M_i)
+// of the input, the workspace and the output.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "../../include/ffx.h"
+#include "ffx_internal.h"
+#include "ffx_pass.cuh"
+#include "ffx_plans.h"
+
+namespace ffx {
+
+// Pointers of one call; pass arguments hold byte offsets into these.
+enum ManyBase : int { BASE_NONE = -1, BASE_PSI0 = 0, BASE_WS = 1, BASE_OUTC = 2, BASE_OUTD = 3,
+                      BASE_GRAD = 4, NBASE = 5 };
+struct ManyCall {
+  const void* base[NBASE];
+};
+
+struct ManyItem {
+  int arg;         // index into the phase's PassArgs
+  int N;           // line length (selects the tile code)
+  int in_base, outc_base, outd_base, grad_base;
+  long long t0, t1;  // tiles [t0, t1)
+};
+
+namespace {
+
+__device__ __forceinline__ const void* rebase(const ManyCall& c, int base, const void* off) {
+  return base < 0 ? nullptr : (const void*)((const char*)c.base[base] + (uintptr_t)off);
+}
+
+template <int KIND>
+__device__ __forceinline__ void run_item(const PassArgs& a, int N, long long t0, long long t1,
+                                         unsigned char* smem) {
+  switch (N) {
+    case 16: pass_tiles<Plan16, KIND, kGroups16>(a, t0, t1, 1, smem); break;
+    case 32: pass_tiles<Plan32, KIND, kGroups32>(a, t0, t1, 1, smem); break;
+    case 48: pass_tiles<Plan48, KIND, kGroups48>(a, t0, t1, 1, smem); break;
+    case 64: pass_tiles<Plan64, KIND, kGroups64>(a, t0, t1, 1, smem); break;
+    case 96: pass_tiles<Plan96, KIND, kGroups96>(a, t0, t1, 1, smem); break;
+    case 128: pass_tiles<Plan128, KIND, kGroups128>(a, t0, t1, 1, smem); break;
+    case 192: pass_tiles<Plan192, KIND, kGroups192>(a, t0, t1, 1, smem); break;
+    case 256: pass_tiles<Plan256, KIND, kGroups256>(a, t0, t1, 1, smem); break;
+    default: break;  // the host admits only the lengths above
+  }
+}
+
+constexpr int kManyLengths[] = {16, 32, 48, 64, 96, 128, 192, 256};
+
+constexpr size_t many_smem_bytes() {
+  size_t m = 0;
+  m = std::max(m, PassSmem<Plan16, kGroups16>::bytes);
+  m = std::max(m, PassSmem<Plan32, kGroups32>::bytes);
+  m = std::max(m, PassSmem<Plan48, kGroups48>::bytes);
+  m = std::max(m, PassSmem<Plan64, kGroups64>::bytes);
+  m = std::max(m, PassSmem<Plan96, kGroups96>::bytes);
+  m = std::max(m, PassSmem<Plan128, kGroups128>::bytes);
+  m = std::max(m, PassSmem<Plan192, kGroups192>::bytes);
+  m = std::max(m, PassSmem<Plan256, kGroups256>::bytes);
+  return m;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256, 2) many_kernel(const PassArgs* __restrict__ args,
+                                                   const ManyItem* __restrict__ items, int n_items,
+                                                   int* counter, const ManyCall call) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_item;
+  for (;;) {
+    __syncthreads();  // everyone has read s_item
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= n_items) break;
+    const ManyItem w = items[it];
+    PassArgs a = args[w.arg];
+    a.in = (const float2*)rebase(call, w.in_base, a.in);
+    a.out_c = (float2*)rebase(call, w.outc_base, a.out_c);
+    a.out_d = (float*)rebase(call, w.outd_base, a.out_d);
+    a.grad = (const float*)rebase(call, w.grad_base, a.grad);
+    run_item<KIND>(a, w.N, w.t0, w.t1, smem);
+  }
+}
+
+bool many_length(int64_t N) {
+  for (int n : kManyLengths)
+    if (n == N) return true;
+  return false;
+}
+
+uint64_t frac_fx64(double x) {
+  double f = x - std::floor(x);
+  if (!(f >= 0.0) || f >= 1.0) f = 0.0;
+  return (uint64_t)std::ldexp(f, 64);
+}
+
+int64_t gcd_64(int64_t a, int64_t b) {
+  while (b) {
+    int64_t t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+int64_t invmod_64(int64_t a, int64_t m) {
+  if (m == 1) return 0;
+  int64_t t = 0, nt = 1, r = m, nr = a % m;
+  while (nr) {
+    int64_t qq = r / nr, tmp = t - qq * nt;
+    t = nt;
+    nt = tmp;
+    tmp = r - qq * nr;
+    r = nr;
+    nr = tmp;
+  }
+  return t < 0 ? t + m : t;
+}
+
+struct AxisTab {
+  int N, lam, g, Np;
+  AxisTables tab;
+};
+
+struct Instance {
+  int ndim;
+  int64_t dims[3];
+  int64_t M, off;
+  int order[3];
+  int axis_tab[3];  // index into ManyPlan::tabs
+};
+
+struct Phase {
+  int kind;
+  PassArgs* d_args = nullptr;
+  ManyItem* d_items = nullptr;
+  int n_items = 0;
+};
+
+}  // namespace
+
+struct ManyPlan {
+  int n = 0;
+  int form = FFX_FORM_FOLD;
+  int64_t total = 0;
+  int max_dim = 0;
+  std::vector<Instance> inst;
+  std::vector<AxisTab> tabs;
+  void* mem = nullptr;      // tables, fold indices, args, items, counters (one allocation)
+  float2* ws = nullptr;     // packed workspace (total points)
+  int* counters = nullptr;  // one per phase
+  int grid_fwd = 0, grid_adj = 0;
+  size_t smem = 0;
+  // graphs per mode: 0 density, 1 field, 2 backward
+  std::vector<Phase> phases[3];
+  cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
+  cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
+  std::vector<cudaGraphNode_t> knodes[3];
+  ManyCall last_call[3];
+};
+
+namespace {
+
+// Items of one phase: each instance's pass cut into chunks of tiles, sorted
+// by estimated cost, biggest first.
+void build_items(const ManyPlan& mp, int step_of_instance /* -1: none */, const PassKernelInfo& k,
+                 int arg, const Instance& in, int axis_tab, int in_base, int outc_base, int outd_base,
+                 int grad_base, std::vector<std::pair<double, ManyItem>>& out) {
+  (void)step_of_instance;
+  (void)mp;
+  const AxisTab& at = mp.tabs[axis_tab];
+  const int64_t lines = in.M / at.N;
+  const int lpt = k.lines;
+  const int64_t ntiles = (lines + lpt - 1) / lpt;
+  const int64_t chunk = 4;
+  const double per_tile = (double)at.lam * at.N * std::log2((double)at.N + 1.0) * lpt;
+  for (int64_t t0 = 0; t0 < ntiles; t0 += chunk) {
+    ManyItem w;
+    w.arg = arg;
+    w.N = at.N;
+    w.in_base = in_base;
+    w.outc_base = outc_base;
+    w.outd_base = outd_base;
+    w.grad_base = grad_base;
+    w.t0 = t0;
+    w.t1 = std::min(ntiles, t0 + chunk);
+    out.push_back({per_tile * (double)(w.t1 - w.t0), w});
+  }
+}
+
+PassArgs pass_args_for(const Instance& in, int axis, const AxisTab& at, size_t in_off, size_t outc_off,
+                       size_t outd_off, size_t grad_off, bool use_outc, bool use_outd, bool use_grad) {
+  PassArgs a;
+  std::memset(&a, 0, sizeof(a));
+  int64_t outer = 1, inner = 1;
+  for (int i = 0; i < axis; ++i) outer *= in.dims[i];
+  for (int i = axis + 1; i < in.ndim; ++i) inner *= in.dims[i];
+  a.in = (const float2*)(uintptr_t)in_off;
+  a.out_c = use_outc ? (float2*)(uintptr_t)outc_off : nullptr;
+  a.out_d = use_outd ? (float*)(uintptr_t)outd_off : nullptr;
+  a.grad = use_grad ? (const float*)(uintptr_t)grad_off : nullptr;
+  a.outer = outer;
+  a.inner = inner;
+  a.M = in.M;
+  a.batch = 1;
+  a.nlines = outer * inner;
+  a.acc = 0;
+  a.grad_shared = 0;
+  a.lam = at.lam;
+  a.g = at.g;
+  a.Np = at.Np;
+  a.qg = 1;
+  a.tab = at.tab;
+  return a;
+}
+
+}  // namespace
+
+int many_create(ManyPlan** out, int n, const ffx_instance_desc* d, uint32_t flags, std::string* err) {
+  *out = nullptr;
+  if (n < 1 || !d) {
+    *err = "n_instances must be >= 1 and descs non-NULL";
+    return FFX_EINVAL;
+  }
+  if (flags & FFX_ACCUMULATE) {
+    *err = "FFX_ACCUMULATE is not defined for instances of different lattices";
+    return FFX_EINVAL;
+  }
+  const uint32_t form = flags & FFX_FORM_MASK;
+  if (flags & ~(FFX_FORM_MASK)) {
+    *err = "unknown flag bits";
+    return FFX_EINVAL;
+  }
+  if (form != FFX_FORM_AUTO && form != FFX_FORM_PAPER && form != FFX_FORM_FOLD) {
+    *err = "unknown form";
+    return FFX_EINVAL;
+  }
+  ManyPlan* mp = new ManyPlan();
+  mp->n = n;
+  mp->form = (form == FFX_FORM_PAPER) ? FFX_FORM_PAPER : FFX_FORM_FOLD;
+  // geometry checks and table keys
+  typedef std::tuple<int64_t, int, double, double, double, double> Key;  // N, lam, dx, t, a, abar
+  std::map<Key, int> keymap;
+  std::vector<Key> keys;
+  for (int i = 0; i < n; ++i) {
+    const ffx_instance_desc& e = d[i];
+    Instance in;
+    if (e.ndim < 1 || e.ndim > 3) {
+      *err = "instance " + std::to_string(i) + ": ndim must be 1..3";
+      delete mp;
+      return FFX_EINVAL;
+    }
+    if (!std::isfinite(e.t)) {
+      *err = "instance " + std::to_string(i) + ": t must be finite";
+      delete mp;
+      return FFX_EINVAL;
+    }
+    in.ndim = e.ndim;
+    in.M = 1;
+    for (int j = 0; j < e.ndim; ++j) {
+      if (e.dims[j] < 1 || !(e.spacing[j] > 0) || !std::isfinite(e.spacing[j]) || e.magnification[j] < 1 ||
+          e.magnification[j] > 65536 || (int64_t)e.magnification[j] * e.dims[j] > (int64_t(1) << 24) ||
+          (e.has_offsets && (!std::isfinite(e.a[j]) || !std::isfinite(e.abar[j])))) {
+        *err = "instance " + std::to_string(i) + ": bad dims, spacing, magnification or offsets";
+        delete mp;
+        return FFX_EINVAL;
+      }
+      if (!many_length(e.dims[j])) {
+        *err = "instance " + std::to_string(i) + ": line length " + std::to_string(e.dims[j]) +
+               " has no batched kernel (16, 32, 48, 64, 96, 128, 192, 256)";
+        delete mp;
+        return FFX_EUNSUPPORTED;
+      }
+      in.dims[j] = e.dims[j];
+      in.M *= e.dims[j];
+      const double L = e.dims[j] * e.spacing[j];
+      const double a = e.has_offsets ? e.a[j] : -0.5 * L;
+      const double ab = e.has_offsets ? e.abar[j]
+                                      : a + (double)(-(((int64_t)(e.magnification[j] - 1) * e.dims[j]) / 2)) *
+                                                e.spacing[j];
+      Key k(e.dims[j], e.magnification[j], e.spacing[j], e.t, a, ab);
+      auto itk = keymap.find(k);
+      if (itk == keymap.end()) {
+        itk = keymap.emplace(k, (int)keys.size()).first;
+        keys.push_back(k);
+      }
+      in.axis_tab[j] = itk->second;
+    }
+    in.off = mp->total;
+    mp->total += in.M;
+    for (int j = 0; j < in.ndim; ++j) in.order[j] = j;
+    for (int a = 0; a < in.ndim; ++a)
+      for (int b = a + 1; b < in.ndim; ++b)
+        if (in.dims[in.order[b]] > in.dims[in.order[a]]) std::swap(in.order[a], in.order[b]);
+    mp->max_dim = std::max(mp->max_dim, in.ndim);
+    mp->inst.push_back(in);
+  }
+  // one device allocation: tables | fold | workspace | counters (args/items are added per mode)
+  size_t tab_bytes = 0;
+  for (const Key& k : keys) {
+    const size_t N = (size_t)std::get<0>(k), lam = (size_t)std::get<1>(k);
+    tab_bytes += (4 * lam * N + N) * sizeof(float2) + ((N * sizeof(int) + 255) & ~size_t(255));
+  }
+  const size_t ws_bytes = (size_t)mp->total * sizeof(float2);
+  const size_t cnt_bytes = 256;
+  cudaError_t e = cudaMalloc(&mp->mem, tab_bytes + ws_bytes + cnt_bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *err = std::string("device allocation: ") + cudaGetErrorString(e);
+    delete mp;
+    return FFX_ENOMEM;
+  }
+  char* cur = (char*)mp->mem;
+  mp->ws = (float2*)cur;
+  cur += ws_bytes;
+  mp->counters = (int*)cur;
+  cur += cnt_bytes;
+  cudaStream_t s;
+  cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  std::vector<int> fold_h;
+  int rc = FFX_OK;
+  for (const Key& k : keys) {
+    AxisTab at;
+    at.N = (int)std::get<0>(k);
+    at.lam = std::get<1>(k);
+    const double dx = std::get<2>(k), t = std::get<3>(k), a = std::get<4>(k), ab = std::get<5>(k);
+    at.g = (int)gcd_64(at.lam, at.N);
+    at.Np = at.N / at.g;
+    const size_t lN = (size_t)at.lam * at.N;
+    float2* P = (float2*)cur;
+    float2* K = P + lN;
+    float2* Kf = K + lN;
+    float2* F = Kf + lN;
+    float2* tw = F + lN;
+    cur += (4 * lN + at.N) * sizeof(float2);
+    int* fold = (int*)cur;
+    cur += ((size_t)at.N * sizeof(int) + 255) & ~size_t(255);
+    const double L = at.N * dx, sv = (ab - a) / dx, tau = M_PI * t / (L * L);
+    e = launch_fill_tables(at.N, at.lam, frac_fx64(sv / at.N), frac_fx64(tau), frac_fx64(2.0 * tau / at.lam),
+                           frac_fx64(sv / ((double)at.lam * at.N)), frac_fx64(tau / ((double)at.lam * at.lam)),
+                           P, K, Kf, F, tw, s);
+    if (e != cudaSuccess) {
+      rc = FFX_ECUDA;
+      *err = std::string("table fill: ") + cudaGetErrorString(e);
+      break;
+    }
+    const int64_t inv = invmod_64((at.lam / at.g) % at.Np, at.Np);
+    fold_h.assign(at.N, -1);
+    for (int r = 0; r < at.N; ++r)
+      if (r % at.g == 0) fold_h[r] = (int)(((int64_t)(r / at.g) * inv) % at.Np);
+    e = cudaMemcpyAsync(fold, fold_h.data(), sizeof(int) * at.N, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // fold_h is reused
+    if (e != cudaSuccess) {
+      rc = FFX_ECUDA;
+      *err = std::string("fold upload: ") + cudaGetErrorString(e);
+      break;
+    }
+    at.tab.P = P;
+    at.tab.K = K;
+    at.tab.Kf = Kf;
+    at.tab.F = F;
+    at.tab.tw = tw;
+    at.tab.fold = fold;
+    mp->tabs.push_back(at);
+  }
+  if (rc == FFX_OK) {
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      rc = FFX_ECUDA;
+      *err = std::string("table fill: ") + cudaGetErrorString(e);
+    }
+  }
+  cudaStreamDestroy(s);
+  if (rc != FFX_OK) {
+    cudaFree(mp->mem);
+    delete mp;
+    return rc;
+  }
+  // persistent grid: resident blocks of the phase kernels
+  mp->smem = many_smem_bytes();
+  const void* kf = (mp->form == FFX_FORM_PAPER) ? (const void*)many_kernel<KIND_FWD_PAPER>
+                                                : (const void*)many_kernel<KIND_FWD_FOLD>;
+  const void* ka = (const void*)many_kernel<KIND_ADJ_FOLD>;
+  int dev = 0, sms = 1, per = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mp->smem);
+  cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mp->smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kf, 256, mp->smem) != cudaSuccess || per < 1) per = 1;
+  mp->grid_fwd = per * sms;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ka, 256, mp->smem) != cudaSuccess || per < 1) per = 1;
+  mp->grid_adj = per * sms;
+  cudaGetLastError();
+  *out = mp;
+  return FFX_OK;
+}
+
+namespace {
+
+// Phases of one mode.  mode 0: density, 1: field, 2: backward.
+int build_phases(ManyPlan* mp, int mode, std::string* err) {
+  std::vector<Phase>& phases = mp->phases[mode];
+  const int D = mp->max_dim;
+  const int fwd_kind = (mp->form == FFX_FORM_PAPER) ? KIND_FWD_PAPER : KIND_FWD_FOLD;
+  const int nsteps = (mode == 2) ? 2 * D : D;
+  for (int step = 0; step < nsteps; ++step) {
+    const bool adj = (mode == 2 && step >= D);
+    const int r = adj ? step - D : step;  // forward step r, or adjoint step r
+    Phase ph;
+    ph.kind = adj ? KIND_ADJ_FOLD : fwd_kind;
+    std::vector<PassArgs> args;
+    std::vector<std::pair<double, ManyItem>> items;
+    for (const Instance& in : mp->inst) {
+      if (r >= in.ndim) continue;
+      const int k = adj ? in.ndim - 1 - r : r;  // pass index in the instance's forward order
+      const int axis = in.order[k];
+      const AxisTab& at = mp->tabs[in.axis_tab[axis]];
+      const size_t off_c = (size_t)in.off * sizeof(float2), off_d = (size_t)in.off * sizeof(float);
+      int in_base, outc_base = BASE_NONE, outd_base = BASE_NONE, grad_base = BASE_NONE;
+      if (!adj) {
+        const bool last = (k == in.ndim - 1);
+        if (mode == 1) {
+          in_base = (k == 0) ? BASE_PSI0 : BASE_OUTC;
+          outc_base = BASE_OUTC;
+        } else {
+          in_base = (k == 0) ? BASE_PSI0 : BASE_WS;
+          if (last && mode == 0)
+            outd_base = BASE_OUTD;
+          else
+            outc_base = BASE_WS;
+        }
+      } else {
+        const bool first = (r == 0);
+        in_base = first ? BASE_WS : BASE_OUTC;  // the gradient buffer is passed as out_field
+        outc_base = BASE_OUTC;
+        if (first) grad_base = BASE_GRAD;
+      }
+      PassArgs a = pass_args_for(in, axis, at, off_c, off_c, off_d, off_d, outc_base >= 0, outd_base >= 0,
+                                 grad_base >= 0);
+      const int arg = (int)args.size();
+      args.push_back(a);
+      PassKernelInfo info;
+      find_pass_kernel(at.N, ph.kind, &info);
+      build_items(*mp, -1, info, arg, in, in.axis_tab[axis], in_base, outc_base, outd_base, grad_base, items);
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::pair<double, ManyItem>& x, const std::pair<double, ManyItem>& y) {
+                       return x.first > y.first;
+                     });
+    std::vector<ManyItem> flat;
+    flat.reserve(items.size());
+    for (auto& pi : items) flat.push_back(pi.second);
+    const size_t bytes = args.size() * sizeof(PassArgs) + flat.size() * sizeof(ManyItem);
+    void* m = nullptr;
+    cudaError_t e = cudaMalloc(&m, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *err = std::string("work list: ") + cudaGetErrorString(e);
+      return FFX_ENOMEM;
+    }
+    ph.d_args = (PassArgs*)m;
+    ph.d_items = (ManyItem*)((char*)m + args.size() * sizeof(PassArgs));
+    ph.n_items = (int)flat.size();
+    e = cudaMemcpy(ph.d_args, args.data(), args.size() * sizeof(PassArgs), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(ph.d_items, flat.data(), flat.size() * sizeof(ManyItem), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(m);
+      *err = std::string("work list upload: ") + cudaGetErrorString(e);
+      return FFX_ECUDA;
+    }
+    phases.push_back(ph);
+  }
+  return FFX_OK;
+}
+
+const void* phase_func(int kind) {
+  switch (kind) {
+    case KIND_FWD_PAPER: return (const void*)many_kernel<KIND_FWD_PAPER>;
+    case KIND_FWD_FOLD: return (const void*)many_kernel<KIND_FWD_FOLD>;
+    default: return (const void*)many_kernel<KIND_ADJ_FOLD>;
+  }
+}
+
+// The graph of one mode: memset(counter_k) -> phase kernel k -> memset(counter_k+1) -> ...
+int build_graph(ManyPlan* mp, int mode, const ManyCall& call, std::string* err) {
+  if (mp->phases[mode].empty()) {
+    int rc = build_phases(mp, mode, err);
+    if (rc) return rc;
+  }
+  cudaGraph_t g;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) {
+    *err = std::string("cudaGraphCreate: ") + cudaGetErrorString(e);
+    return FFX_ECUDA;
+  }
+  cudaGraphNode_t prev = nullptr;
+  std::vector<cudaGraphNode_t>& kn = mp->knodes[mode];
+  kn.clear();
+  std::vector<Phase>& phases = mp->phases[mode];
+  for (size_t k = 0; k < phases.size(); ++k) {
+    Phase& ph = phases[k];
+    cudaMemsetParams ms;
+    std::memset(&ms, 0, sizeof(ms));
+    ms.dst = mp->counters + k;
+    ms.value = 0;
+    ms.elementSize = sizeof(int);
+    ms.width = 1;
+    ms.height = 1;
+    cudaGraphNode_t mnode, knode;
+    e = cudaGraphAddMemsetNode(&mnode, g, prev ? &prev : nullptr, prev ? 1 : 0, &ms);
+    if (e != cudaSuccess) break;
+    int* counter = mp->counters + k;
+    void* params[] = {(void*)&ph.d_args, (void*)&ph.d_items, (void*)&ph.n_items, (void*)&counter,
+                      (void*)&call};
+    cudaKernelNodeParams kp;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.func = (void*)phase_func(ph.kind);
+    kp.gridDim = dim3(ph.kind == KIND_ADJ_FOLD ? mp->grid_adj : mp->grid_fwd);
+    kp.blockDim = dim3(256);
+    kp.sharedMemBytes = (unsigned)mp->smem;
+    kp.kernelParams = params;
+    e = cudaGraphAddKernelNode(&knode, g, &mnode, 1, &kp);
+    if (e != cudaSuccess) break;
+    kn.push_back(knode);
+    prev = knode;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&mp->exec[mode], g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    *err = std::string("graph build: ") + cudaGetErrorString(e);
+    return FFX_ECUDA;
+  }
+  mp->graph[mode] = g;
+  mp->last_call[mode] = call;
+  return FFX_OK;
+}
+
+int launch_mode(ManyPlan* mp, int mode, const ManyCall& call, cudaStream_t s, std::string* err) {
+  int rc;
+  if (!mp->exec[mode]) {
+    if ((rc = build_graph(mp, mode, call, err))) return rc;
+  } else if (std::memcmp(&call, &mp->last_call[mode], sizeof(call)) != 0) {
+    // new buffers: rewrite the phase kernels' call pointers in the executable graph
+    std::vector<Phase>& phases = mp->phases[mode];
+    for (size_t k = 0; k < phases.size(); ++k) {
+      Phase& ph = phases[k];
+      int* counter = mp->counters + k;
+      void* params[] = {(void*)&ph.d_args, (void*)&ph.d_items, (void*)&ph.n_items, (void*)&counter,
+                        (void*)&call};
+      cudaKernelNodeParams kp;
+      std::memset(&kp, 0, sizeof(kp));
+      kp.func = (void*)phase_func(ph.kind);
+      kp.gridDim = dim3(ph.kind == KIND_ADJ_FOLD ? mp->grid_adj : mp->grid_fwd);
+      kp.blockDim = dim3(256);
+      kp.sharedMemBytes = (unsigned)mp->smem;
+      kp.kernelParams = params;
+      cudaError_t e = cudaGraphExecKernelNodeSetParams(mp->exec[mode], mp->knodes[mode][k], &kp);
+      if (e != cudaSuccess) {
+        *err = std::string("graph update: ") + cudaGetErrorString(e);
+        return FFX_ECUDA;
+      }
+    }
+    mp->last_call[mode] = call;
+  }
+  cudaError_t e = cudaGraphLaunch(mp->exec[mode], s);
+  if (e != cudaSuccess) {
+    *err = std::string("cudaGraphLaunch: ") + cudaGetErrorString(e);
+    return FFX_ECUDA;
+  }
+  return FFX_OK;
+}
+
+}  // namespace
+
+void many_destroy(ManyPlan* mp) {
+  if (!mp) return;
+  for (int m = 0; m < 3; ++m) {
+    if (mp->exec[m]) cudaGraphExecDestroy(mp->exec[m]);
+    if (mp->graph[m]) cudaGraphDestroy(mp->graph[m]);
+    for (Phase& ph : mp->phases[m]) cudaFree(ph.d_args);
+  }
+  cudaFree(mp->mem);
+  delete mp;
+}
+
+int64_t many_total(const ManyPlan* mp) { return mp->total; }
+int64_t many_offset(const ManyPlan* mp, int i) { return (i < 0 || i >= mp->n) ? -1 : mp->inst[i].off; }
+int many_form(const ManyPlan* mp) { return mp->form; }
+int many_max_dim(const ManyPlan* mp) { return mp->max_dim; }
+
+int many_expand(ManyPlan* mp, const void* psi0, float* out_d, void* out_c, cudaStream_t s, std::string* err) {
+  ManyCall c;
+  std::memset(&c, 0, sizeof(c));
+  c.base[BASE_PSI0] = psi0;
+  c.base[BASE_WS] = mp->ws;
+  c.base[BASE_OUTC] = out_c;
+  c.base[BASE_OUTD] = out_d;
+  return launch_mode(mp, out_d ? 0 : 1, c, s, err);
+}
+
+int many_backward(ManyPlan* mp, const void* psi0, const float* grad, void* grad_psi0, cudaStream_t s,
+                  std::string* err) {
+  ManyCall c;
+  std::memset(&c, 0, sizeof(c));
+  c.base[BASE_PSI0] = psi0;
+  c.base[BASE_WS] = mp->ws;
+  c.base[BASE_OUTC] = grad_psi0;
+  c.base[BASE_GRAD] = grad;
+  return launch_mode(mp, 2, c, s, err);
+}
+
+}  // namespace ffx

@@ -22,6 +22,8 @@
 //             IFFT(conj(Kf_q[m]) * D[(lam m + q) mod N]).
 #pragma once
 
+#include <stdint.h>
+
 #include "ffx_fft.cuh"
 #include "ffx_internal.h"
 
@@ -52,13 +54,14 @@ __device__ __forceinline__ void tile_coords(int idx, int N, int lines, bool cont
   }
 }
 
+// Tiles first, first + step, ... (below min(last, number of tiles)) of one
+// pass.  Called by a whole block; uses `smem` (PassSmem<P, G>::bytes).
 template <class P, int KIND, int G>
-__global__ void __launch_bounds__(P::T * G)
-    pass_kernel(const PassArgs a) {
+__device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int64_t last, int64_t step,
+                                           unsigned char* smem) {
   constexpr int N = P::N, E = P::E, T = P::T;
   using SM = PassSmem<P, G>;
   constexpr int NP = SM::NP;
-  extern __shared__ __align__(16) unsigned char smem[];
   float2* tw_s = reinterpret_cast<float2*>(smem + SM::tw_off);
   int* fold_s = reinterpret_cast<int*>(smem + SM::fold_off);
   long long* base_s = reinterpret_cast<long long*>(smem + SM::base_off);
@@ -77,6 +80,7 @@ __global__ void __launch_bounds__(P::T * G)
   const int grp = lg - line * QG;
   const unsigned key = line_sync_key<T>(lg, tid);
 
+  __syncthreads();  // an earlier call on this block may still read shared memory
   for (int i = tid; i < N; i += NT) {
     tw_s[i] = a.tab.tw[i];
     if constexpr (KIND == KIND_FWD_FOLD) fold_s[i] = a.tab.fold[i];
@@ -86,7 +90,8 @@ __global__ void __launch_bounds__(P::T * G)
   const int64_t inner = a.inner;
   const bool contiguous = (inner == 1);
   const int64_t per_real_lines = a.outer * inner;
-  const int64_t ntiles = (a.nlines + LINES - 1) / LINES;
+  int64_t ntiles = (a.nlines + LINES - 1) / LINES;
+  if (last < ntiles) ntiles = last;
   const int nb_loop = a.acc ? (int)a.batch : 1;
 
   float2* psi_line = psi_s + line * NP;
@@ -106,7 +111,7 @@ __global__ void __launch_bounds__(P::T * G)
     }
   }
 
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int64_t tile = first; tile < ntiles; tile += step) {
     float racc[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) racc[e] = 0.f;
@@ -306,6 +311,12 @@ __global__ void __launch_bounds__(P::T * G)
       }
     }
   }
+}
+
+template <class P, int KIND, int G>
+__global__ void __launch_bounds__(P::T * G) pass_kernel(const PassArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  pass_tiles<P, KIND, G>(a, blockIdx.x, INT64_MAX, gridDim.x, smem);
 }
 
 template <class P, int KIND, int G>

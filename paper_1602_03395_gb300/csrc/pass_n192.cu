@@ -1,16 +1,14 @@
-// Line-pass kernels for lines of 192 points (generated list of instantiations;
-// the line plan: 192 = 4x4x4x3, 12 points per thread, 16 lines per block).
+// Line-pass kernels for lines of 192 points (see ffx_plans.h for the line plan).
 #include "ffx_pass.cuh"
+#include "ffx_plans.h"
 
 namespace ffx {
 
-using Plan192 = LinePlan<192, 12, 4,4,4,3>;
-
 bool pass_kernel_192(int kind, PassKernelInfo* out) {
   switch (kind) {
-    case KIND_FWD_PAPER: *out = pass_info<Plan192, KIND_FWD_PAPER, 16>(); return true;
-    case KIND_FWD_FOLD: *out = pass_info<Plan192, KIND_FWD_FOLD, 16>(); return true;
-    case KIND_ADJ_FOLD: *out = pass_info<Plan192, KIND_ADJ_FOLD, 16>(); return true;
+    case KIND_FWD_PAPER: *out = pass_info<Plan192, KIND_FWD_PAPER, kGroups192>(); return true;
+    case KIND_FWD_FOLD: *out = pass_info<Plan192, KIND_FWD_FOLD, kGroups192>(); return true;
+    case KIND_ADJ_FOLD: *out = pass_info<Plan192, KIND_ADJ_FOLD, kGroups192>(); return true;
     default: return false;
   }
 }

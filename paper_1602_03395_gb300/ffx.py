@@ -30,6 +30,13 @@ _FORMS = {"auto": FFX_FORM_AUTO, "paper": FFX_FORM_PAPER, "fold": FFX_FORM_FOLD}
 _lib = None
 
 
+class InstanceDesc(ctypes.Structure):
+    """ffx_instance_desc of include/ffx.h."""
+    _fields_ = [("ndim", ctypes.c_int32), ("dims", ctypes.c_int64 * 3), ("spacing", ctypes.c_double * 3),
+                ("t", ctypes.c_double), ("magnification", ctypes.c_int32 * 3),
+                ("has_offsets", ctypes.c_int32), ("a", ctypes.c_double * 3), ("abar", ctypes.c_double * 3)]
+
+
 class FfxError(RuntimeError):
     def __init__(self, code: int, where: str, msg: str):
         super().__init__(f"{where}: {msg} (code {code})")
@@ -77,6 +84,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(dbl),
                                        ctypes.POINTER(dbl), vp, i64, vp, vp]
     lib.ffx_expand_noalloc.restype = i32
+    lib.ffx_plan_many.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(InstanceDesc), u32]
+    lib.ffx_plan_many.restype = i32
+    lib.ffx_plan_many_offset.argtypes = [vp, i32]
+    lib.ffx_plan_many_offset.restype = i64
+    lib.ffx_plan_points.argtypes = [vp]
+    lib.ffx_plan_points.restype = i64
     lib.ffx_error_string.argtypes = [i32]
     lib.ffx_error_string.restype = ctypes.c_char_p
     lib.ffx_last_error.argtypes = []
@@ -195,6 +208,59 @@ class Plan:
 
     def trace_count(self) -> int:
         return int(load_library().ffx_plan_trace_count(self.handle))
+
+
+class PlanMany(Plan):
+    """A plan over many instances of (possibly) different lattices.
+
+    ``instances``: sequence of (dims, spacing, t, magnification) or
+    (dims, spacing, t, magnification, a, abar).  Inputs and outputs are packed
+    1-D tensors of ``points`` elements; instance i starts at ``offsets[i]``."""
+
+    def __init__(self, instances, form: str = "auto"):
+        lib = load_library()
+        n = len(instances)
+        descs = (InstanceDesc * n)()
+        for i, spec in enumerate(instances):
+            dims, spacing, t, lam = spec[:4]
+            d = descs[i]
+            d.ndim = len(dims)
+            for j in range(len(dims)):
+                d.dims[j] = int(dims[j])
+                d.spacing[j] = float(spacing[j])
+                d.magnification[j] = int(lam[j])
+            d.t = float(t)
+            if len(spec) > 4 and spec[4] is not None:
+                d.has_offsets = 1
+                for j in range(len(dims)):
+                    d.a[j] = float(spec[4][j])
+                    d.abar[j] = float(spec[5][j])
+        h = ctypes.c_void_p()
+        _check(lib.ffx_plan_many(ctypes.byref(h), n, descs, _FORMS[form]), "ffx_plan_many")
+        self._h = h
+        self.accumulate = False
+        self.form = {FFX_FORM_PAPER: "paper", FFX_FORM_FOLD: "fold"}[lib.ffx_plan_form(h)]
+        self.instances = [tuple(tuple(x) if hasattr(x, "__len__") else x for x in spec[:4]) for spec in instances]
+        self.points = int(lib.ffx_plan_points(h))
+        self.offsets = [int(lib.ffx_plan_many_offset(h, i)) for i in range(n)]
+        self.dims = (self.points,)
+        self.M = self.points
+
+    def _batch(self, x: torch.Tensor) -> int:
+        if x.numel() != self.points:
+            raise ValueError(f"packed tensor must have {self.points} elements, got {x.numel()}")
+        return 1
+
+    def unpack(self, x: torch.Tensor):
+        """Views of a packed tensor, one per instance, shaped like its lattice."""
+        out = []
+        for i, spec in enumerate(self.instances):
+            dims = spec[0]
+            m = 1
+            for v in dims:
+                m *= int(v)
+            out.append(x.reshape(-1)[self.offsets[i]:self.offsets[i] + m].view(*dims))
+        return out
 
 
 def ffx_plan(dims, spacing, t, magnification, a=None, abar=None, form="auto", accumulate=False) -> Plan:

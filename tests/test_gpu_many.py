@@ -1,0 +1,102 @@
+"""Many-instance plans: uneven lattices, magnifications and flight times in
+one persistent launch per axis pass, replayed as a CUDA graph.  Every
+instance against the FP64 oracle and against its own single-lattice plan."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from gpu_common import DENSITY_TOL, FIELD_TOL, random_field, rel_l2, require_gpu, to_dev
+from paper_1602_03395_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def mixed_specs(count, seed=4, lam_max=12, dims_override=None):
+    ws = inputs.config_mixed_batch(seed=seed, count=count)
+    specs, psis = [], []
+    rng = np.random.default_rng(seed)
+    for i, w in enumerate(ws):
+        dims = dims_override[i % len(dims_override)] if dims_override else w.dims
+        lam = int(rng.integers(2, lam_max + 1))
+        specs.append((dims, w.dx[:len(dims)], 4.0 * lam, (lam,) * len(dims)))
+        psis.append(random_field(rng, dims) if dims_override else w.realization(0))
+    return specs, psis
+
+
+def pack(plan, psis):
+    x = np.zeros(plan.points, np.complex64)
+    for off, p in zip(plan.offsets, psis):
+        x[off:off + p.size] = p.ravel()
+    return x
+
+
+@pytest.mark.parametrize("form", ["fold", "paper"])
+def test_many_mixed_shapes_against_oracle(form):
+    ffx = require_gpu()
+    dims_set = [(48, 16, 32), (32, 32), (96,), (16, 128, 16), (64, 48, 16), (192, 16)]
+    specs, psis = mixed_specs(9, dims_override=dims_set)
+    plan = ffx.PlanMany(specs, form=form)
+    x = to_dev(pack(plan, psis))
+    rho = ffx.ffx_expand(plan, x).cpu().numpy()
+    field = ffx.ffx_expand_field(plan, x).cpu().numpy()
+    worst_d = worst_f = 0.0
+    for (dims, dx, t, lam), p, off in zip(specs, psis, plan.offsets):
+        ref = O.expand_field(p, dx, t, lam)
+        m = p.size
+        worst_d = max(worst_d, rel_l2(rho[off:off + m].reshape(dims), np.abs(ref) ** 2))
+        worst_f = max(worst_f, rel_l2(field[off:off + m].reshape(dims), ref))
+    plan.close()
+    print(f"many ({form}): worst density {worst_d:.2e}, worst field {worst_f:.2e}")
+    assert worst_d < DENSITY_TOL and worst_f < FIELD_TOL
+
+
+def test_many_workload_shapes_match_single_plans_and_replay():
+    """Instances of the mixed-batch workload (48^3, 64^3, 96^3, 128x32x32) with
+    moderate lam: each equals its own single-lattice plan; a second call with
+    new buffers (graph parameter update) gives the same result."""
+    ffx = require_gpu()
+    specs, psis = mixed_specs(8, lam_max=10)
+    plan = ffx.PlanMany(specs)
+    x = to_dev(pack(plan, psis))
+    r1 = ffx.ffx_expand(plan, x).clone()
+    x2 = x.clone()
+    r2 = ffx.ffx_expand(plan, x2)
+    assert torch.equal(r1, r2)
+    r1 = r1.cpu().numpy()
+    worst = 0.0
+    for (dims, dx, t, lam), p, off in zip(specs, psis, plan.offsets):
+        with ffx.Plan(dims, dx, t, lam) as single:
+            ref = ffx.ffx_expand(single, to_dev(p[None])).cpu().numpy()[0]
+        worst = max(worst, rel_l2(r1[off:off + p.size].reshape(dims), ref))
+    plan.close()
+    print(f"many vs single plans: worst {worst:.2e}")
+    assert worst < 1e-5
+
+
+def test_many_backward_against_oracle():
+    ffx = require_gpu()
+    dims_set = [(32, 48), (16, 32, 16), (64,)]
+    specs, psis = mixed_specs(3, dims_override=dims_set)
+    plan = ffx.PlanMany(specs)
+    rng = np.random.default_rng(3)
+    grads = [rng.normal(size=p.shape).astype(np.float32) for p in psis]
+    g = np.zeros(plan.points, np.float32)
+    for off, gr in zip(plan.offsets, grads):
+        g[off:off + gr.size] = gr.ravel()
+    got = ffx.ffx_expand_backward(plan, to_dev(pack(plan, psis)), to_dev(g)).cpu().numpy()
+    worst = 0.0
+    for (dims, dx, t, lam), p, gr, off in zip(specs, psis, grads, plan.offsets):
+        ref = O.density_loss_gradient(p, gr, dx, t, lam)
+        worst = max(worst, rel_l2(got[off:off + p.size].reshape(dims), ref))
+    plan.close()
+    print(f"many backward: worst {worst:.2e}")
+    assert worst < FIELD_TOL
+
+
+def test_many_rejects_unsupported():
+    ffx = require_gpu()
+    with pytest.raises(ffx.FfxError) as ei:
+        ffx.PlanMany([((512,), (0.1,), 1.0, (3,))])
+    assert ei.value.code == ffx.FFX_EUNSUPPORTED
