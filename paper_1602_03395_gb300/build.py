@@ -22,6 +22,8 @@ LIB = os.path.join(PKG, "libffx.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-I", os.path.join(ROOT, "include"), "--expt-relaxed-constexpr"]
+# extra nvcc flags for experiments (e.g. -DFFX_PASS_MIN_BLOCKS=3); part of the build digest
+NVCC_FLAGS += os.environ.get("FFX_NVCC_EXTRA", "").split()
 
 
 def _nvcc():

@@ -202,12 +202,38 @@ __device__ __forceinline__ void line_sync(unsigned key) {
   }
 }
 
+// Twiddles of the last stage, which depend only on the thread: kept in
+// registers when there are few of them (forward and inverse share them).
+template <class P>
+struct LastStageTw {
+  static constexpr int STAGE = P::S - 1;
+  static constexpr int R = P::radix(STAGE);
+  static constexpr int NB = P::E / R;
+  static constexpr int COUNT = NB * (R - 1);
+  static constexpr bool enabled = (P::S > 1) && COUNT <= 8;
+  float2 w[enabled ? COUNT : 1];
+  __device__ __forceinline__ void load(const float2* __restrict__ tw, int t) {
+    if constexpr (enabled) {
+      constexpr int Ns = P::span(STAGE);
+      constexpr int step = P::N / (Ns * R);
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const int k = (t + b * P::T) % Ns;
+#pragma unroll
+        for (int r = 1; r < R; ++r) w[b * (R - 1) + r - 1] = tw[r * k * step];
+      }
+    }
+  }
+};
+
 // One butterfly stage on the registers (inputs at owned positions).
 template <class P, int STAGE, bool INV>
-__device__ __forceinline__ void stage_compute(float2 (&v)[P::E], const float2* __restrict__ tw, int t) {
+__device__ __forceinline__ void stage_compute(float2 (&v)[P::E], const float2* __restrict__ tw, int t,
+                                              const LastStageTw<P>& twc) {
   constexpr int R = P::radix(STAGE);
   constexpr int Ns = P::span(STAGE);
   constexpr int NB = P::E / R;
+  constexpr bool cached = (STAGE == P::S - 1) && LastStageTw<P>::enabled;
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     float2 x[R];
@@ -219,7 +245,12 @@ __device__ __forceinline__ void stage_compute(float2 (&v)[P::E], const float2* _
       constexpr int step = P::N / (Ns * R);
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        float2 w = tw[r * k * step];
+        float2 w;
+        if constexpr (cached) {
+          w = twc.w[b * (R - 1) + r - 1];
+        } else {
+          w = tw[r * k * step];
+        }
         if (INV) w.y = -w.y;
         x[r] = cmul(x[r], w);
       }
@@ -259,14 +290,14 @@ __device__ __forceinline__ void store_owned(const float2 (&v)[P::E], float2* __r
 
 template <class P, int STAGE, bool INV>
 __device__ __forceinline__ void fft_from(float2 (&v)[P::E], float2* line, const float2* tw, int t,
-                                         unsigned key) {
-  stage_compute<P, STAGE, INV>(v, tw, t);
+                                         unsigned key, const LastStageTw<P>& twc) {
+  stage_compute<P, STAGE, INV>(v, tw, t, twc);
   if constexpr (STAGE + 1 < P::S) {
     line_sync<P::T>(key);  // earlier readers of `line` are done
     stage_store<P, STAGE>(v, line, t);
     line_sync<P::T>(key);
     load_owned<P>(v, line, t);
-    fft_from<P, STAGE + 1, INV>(v, line, tw, t, key);
+    fft_from<P, STAGE + 1, INV>(v, line, tw, t, key, twc);
   }
 }
 
@@ -277,8 +308,8 @@ __device__ __forceinline__ void fft_from(float2 (&v)[P::E], float2* line, const 
 // it again.
 template <class P, bool INV>
 __device__ __forceinline__ void fft_line(float2 (&v)[P::E], float2* line, const float2* tw, int t,
-                                         unsigned key) {
-  fft_from<P, 0, INV>(v, line, tw, t, key);
+                                         unsigned key, const LastStageTw<P>& twc) {
+  fft_from<P, 0, INV>(v, line, tw, t, key, twc);
 }
 
 }  // namespace ffx

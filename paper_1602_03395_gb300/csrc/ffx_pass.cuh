@@ -27,6 +27,10 @@
 #include "ffx_fft.cuh"
 #include "ffx_internal.h"
 
+#ifndef FFX_PASS_MIN_BLOCKS
+#define FFX_PASS_MIN_BLOCKS 3  // resident 256-thread blocks per SM the register budget aims for
+#endif
+
 namespace ffx {
 
 template <class P, int G>
@@ -74,10 +78,13 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
   const int LINES = G / QG;
   const int NT = LINES * QG * T;  // == blockDim.x
   const int tid = threadIdx.x;
-  const int lg = tid / T;  // line-group in block: line-major, group-minor
+  // Line-groups are laid out group-major: the groups in one warp work on the
+  // same q (different lines) and read the same phase-row segments.  Group r of
+  // line l has index r * LINES + l; group 0 of line l is index l.
+  const int lg = tid / T;
   const int t = tid - lg * T;
-  const int line = lg / QG;
-  const int grp = lg - line * QG;
+  const int grp = lg / LINES;
+  const int line = lg - grp * LINES;
   const unsigned key = line_sync_key<T>(lg, tid);
 
   __syncthreads();  // an earlier call on this block may still read shared memory
@@ -85,6 +92,10 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
     tw_s[i] = a.tab.tw[i];
     if constexpr (KIND == KIND_FWD_FOLD) fold_s[i] = a.tab.fold[i];
   }
+
+  __syncthreads();  // twiddles are in shared memory
+  LastStageTw<P> twc;
+  twc.load(tw_s, t);
 
   const int lam = a.lam;
   const int64_t inner = a.inner;
@@ -169,10 +180,10 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
           float2 v[E];
 #pragma unroll
           for (int e = 0; e < E; ++e) v[e] = cmul(psi_line[pad(t + e * T)], __ldg(Pq + t + e * T));
-          fft_line<P, false>(v, wl, tw_s, t, key);
+          fft_line<P, false>(v, wl, tw_s, t, key, twc);
 #pragma unroll
           for (int e = 0; e < E; ++e) v[e] = cmul(v[e], __ldg(Kq + t + e * T));
-          fft_line<P, true>(v, wl, tw_s, t, key);
+          fft_line<P, true>(v, wl, tw_s, t, key, twc);
           line_sync<T>(key);
           store_owned<P>(v, wl, t);
           line_sync<T>(key);
@@ -189,7 +200,7 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
           float2 v[E];
 #pragma unroll
           for (int e = 0; e < E; ++e) v[e] = cmul(psi_line[pad(t + e * T)], __ldg(Pq + t + e * T));
-          fft_line<P, false>(v, wl, tw_s, t, key);
+          fft_line<P, false>(v, wl, tw_s, t, key, twc);
 #pragma unroll
           for (int e = 0; e < E; ++e) v[e] = cmul(v[e], __ldg(Kq + t + e * T));
           line_sync<T>(key);
@@ -222,7 +233,7 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
           float2 v[E];
 #pragma unroll
           for (int e = 0; e < E; ++e) v[e] = psi_line[pad(t + e * T)];
-          fft_line<P, false>(v, wl, tw_s, t, key);
+          fft_line<P, false>(v, wl, tw_s, t, key, twc);
           line_sync<T>(key);
           store_owned<P>(v, psi_line, t);
         }
@@ -239,7 +250,7 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
             if (idx >= N) idx -= N;
             v[e] = cmulc(psi_line[pad(idx)], __ldg(Kq + t + e * T));
           }
-          fft_line<P, true>(v, wl, tw_s, t, key);
+          fft_line<P, true>(v, wl, tw_s, t, key, twc);
 #pragma unroll
           for (int e = 0; e < E; ++e) res[e] = cadd(res[e], cmulc(v[e], __ldg(Pq + t + e * T)));
           qN += qstep;
@@ -254,7 +265,7 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
         __syncthreads();
         if (grp == 0) {
           for (int r = 1; r < QG; ++r) {
-            const float2* other = work_s + (lg + r) * NP;
+            const float2* other = work_s + (r * LINES + line) * NP;
 #pragma unroll
             for (int e = 0; e < E; ++e) res[e] = cadd(res[e], other[pad(t + e * T)]);
           }
@@ -262,7 +273,7 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
       }
       if constexpr (KIND == KIND_FWD_FOLD) {
         if (QG > 1) __syncthreads();  // the other groups' buffers are read; wl is free again
-        if (grp == 0) fft_line<P, true>(res, wl, tw_s, t, key);
+        if (grp == 0) fft_line<P, true>(res, wl, tw_s, t, key, twc);
       }
 
       if (a.acc) {
@@ -281,7 +292,7 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
           const long long base = base_s[l];
           if (base < 0) continue;
           const int64_t addr = base + (int64_t)n * inner;
-          const float2 v = work_s[(l * QG) * NP + pad(n)];
+          const float2 v = work_s[l * NP + pad(n)];
           if (a.out_c) {
             a.out_c[addr] = v;
           } else {
@@ -307,14 +318,14 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
         if (base < 0) continue;
         // base_s holds the last realization's line; remove its batch offset
         const int64_t addr = base - (int64_t)(nb_loop - 1) * a.M + (int64_t)n * inner;
-        a.out_d[addr] += work_s[(l * QG) * NP + pad(n)].x;
+        a.out_d[addr] += work_s[l * NP + pad(n)].x;
       }
     }
   }
 }
 
 template <class P, int KIND, int G>
-__global__ void __launch_bounds__(P::T * G) pass_kernel(const PassArgs a) {
+__global__ void __launch_bounds__(P::T * G, FFX_PASS_MIN_BLOCKS) pass_kernel(const PassArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   pass_tiles<P, KIND, G>(a, blockIdx.x, INT64_MAX, gridDim.x, smem);
 }
