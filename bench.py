@@ -50,13 +50,13 @@ SMS, FP32_LANES = 152, 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ffx", choices=["ffx", "reference"])
     ap.add_argument("--workload", default="two_cloud",
                     choices=["two_cloud", "1d", "quasicondensate", "large_two_cloud",
                              "large_quasicondensate", "mixed"])
-    ap.add_argument("--form", default="auto", choices=["auto", "paper", "fold"])
+    ap.add_argument("--form", default="auto", choices=["auto", "paper", "fold", "dense"])
     ap.add_argument("--batch", type=int, default=None, help="realizations per step (default: workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -83,11 +83,14 @@ def pass_flops(N: int, lam: int, lines: int, form: str) -> float:
     length N; 6 per complex multiply, 2 per complex add).
     paper form, per term: FFT + IFFT + pre-chirp, k-phase, post-chirp
     multiplies + accumulate = 10 N log2 N + 20 N.
+    dense form: the per-axis map as an N x N complex matrix, 8 N per point.
     fold form, per term: FFT + pre-chirp and k-phase multiplies + fold add
     = 5 N log2 N + 14 N; plus one inverse FFT per line."""
     lg = math.log2(N)
     if form == "paper":
         return lines * lam * (10 * N * lg + 20 * N)
+    if form == "dense":
+        return lines * 8.0 * N * N  # N x N complex matrix times each line
     return lines * (lam * (5 * N * lg + 14 * N) + 5 * N * lg)
 
 
@@ -359,26 +362,52 @@ def run_ffx(args):
         ffx.ffx_expand(plan, pool_in[i % pool_n], pool_out[i % len(pool_out)])
     torch.cuda.synchronize()
 
-    # per-launch events inside the timed region (recorded by the library between launches)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * launches * args.steps)]
-    plan.trace(ev)
+    # The K steps are captured into CUDA graphs of up to GRAPH_STEPS steps and
+    # replayed back to back: the device runs the same kernels on the same
+    # buffers as K separate calls, without host launch gaps between them.
+    # Per-launch events recorded by the library inside the graphs (event-record
+    # nodes) time every pass.
+    GRAPH_STEPS = 200
+    chunk = min(args.steps, GRAPH_STEPS)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * launches * chunk)]
+    graphs = []  # (graph, steps, first step)
+    done = 0
+    while done < args.steps:
+        n = min(chunk, args.steps - done)
+        g = torch.cuda.CUDAGraph()
+        plan.trace(ev if not graphs else None)  # the first graph carries the per-launch events
+        with torch.cuda.graph(g):
+            for i in range(done, done + n):
+                ffx.ffx_expand(plan, pool_in[i % pool_n], pool_out[i % len(pool_out)])
+        plan.trace(None)
+        graphs.append((g, n, done))
+        done += n
+    for g, _, _ in graphs:  # warm the graphs
+        g.replay()
+    torch.cuda.synchronize()
+    # clocks are sampled over a window of sustained load (>= 0.6 s of the same
+    # graphs) that ends with the timed region, so a short timed region still
+    # falls inside the sampled window
     sampler = ClockSampler(local)
     sampler.start()
-    time.sleep(0.3)
+    t_load = time.perf_counter()
+    while time.perf_counter() - t_load < 0.6:
+        for g, _, _ in graphs:
+            g.replay()
+        torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
-    for i in range(args.steps):
-        ffx.ffx_expand(plan, pool_in[i % pool_n], pool_out[i % len(pool_out)])
+    for g, _, _ in graphs:
+        g.replay()
     t_end.record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    plan.trace(None)
     ms = t_start.elapsed_time(t_end)
     if world > 1:
         tt = torch.tensor([ms], device=dev)
@@ -387,7 +416,7 @@ def run_ffx(args):
 
     # per-pass durations from the traced events
     per_pass = [[] for _ in range(launches)]
-    for s in range(args.steps):
+    for s in range(graphs[0][1]):
         for k in range(launches):
             i0 = 2 * (s * launches + k)
             per_pass[k].append(ev[i0].elapsed_time(ev[i0 + 1]))
@@ -396,12 +425,13 @@ def run_ffx(args):
     axis = order[dom]
     N, lam = w.dims[axis], w.lam[axis]
     lines = B_ * M // N
-    flops = pass_flops(N, lam, lines, form)
+    axis_form = plan.axis_forms[axis]
+    flops = pass_flops(N, lam, lines, axis_form)
     pk, pk_src = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     alu_peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
     achieved = flops / (mean_ms[dom] * 1e-3) / 1e12
-    kernel_key = f"pass_{form}_N{N}_lam{lam}_{args.workload}"
+    kernel_key = f"pass_{axis_form}_N{N}_lam{lam}_{args.workload}"
     traffic = load_traffic(kernel_key)
     # HBM view of the same launch: it reads and writes the batch once (complex64,
     # the last pass writes float32 densities)
@@ -452,11 +482,13 @@ def run_ffx(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "dims": list(w.dims), "dx": list(w.dx),
                        "lam": list(w.lam), "t": w.t, "batch_per_gpu": B_, "form": form,
+                       "axis_forms": list(plan.axis_forms),
                        "parallelism": f"replicas x{world} (realizations sharded, no collective)",
                        "l2": f"rotating pool of {pool_n} input buffers "
                              f"({pool_n * step_in_bytes / 2**20:.0f} MiB > 129 MB L2)"},
             "rel_l2_density_err_vs_fp64": err,
             "gpu_launches": launches * args.steps,
+            "graph": f"K steps replayed as {len(graphs)} CUDA graph(s) of <= {GRAPH_STEPS} steps",
             "clocks": clocks,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak,
                          "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": traffic,
@@ -467,7 +499,7 @@ def run_ffx(args):
                              "peak": hbm_peak, "unit": "GB/s",
                              "frac": bytes_launch / (mean_ms[dom] * 1e-3) / 1e9 / hbm_peak,
                              "note": f"of {pk_src} hbm_gbs; one read + one write of the batch"},
-            "pass_ms": {f"axis{order[k]}_N{w.dims[order[k]]}_lam{w.lam[order[k]]}": mean_ms[k]
+            "pass_ms": {f"axis{order[k]}_N{w.dims[order[k]]}_lam{w.lam[order[k]]}_{plan.axis_forms[order[k]]}": mean_ms[k]
                         for k in range(launches)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B_ * M * 8,
                     "d2h_bytes_per_step": B_ * M * 4},

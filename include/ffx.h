@@ -59,11 +59,23 @@ extern "C" {
  *   (lam*m + q) mod M, so every term's k-space line is folded into one
  *   spectrum and a single inverse FFT follows (lam + 1 line FFTs per axis).
  *   Same map, same rounding class.
- * 0 (FFX_FORM_AUTO) lets the plan choose (currently FOLD). */
+ * FFX_FORM_DENSE: the same per-axis map as an N x N complex matrix T_j,
+ *   built at plan time by running the fold form on the N unit vectors, then
+ *   applied as a batched complex matrix product (8*M_j flops per point instead
+ *   of lam_j*(5 log2 M_j + 14)); lines up to 1024 points.
+ * 0 (FFX_FORM_AUTO) chooses per axis: a tuned choice from the cache named by
+ *   the environment variable FFX_TUNE_CACHE if it holds one for this device
+ *   and geometry, else measured at plan time with FFX_TUNE, else a fixed cost
+ *   model (dense when 8 M_j is well below the FFT form's work). */
 #define FFX_FORM_AUTO   0x0u
 #define FFX_FORM_PAPER  0x1u
 #define FFX_FORM_FOLD   0x2u
+#define FFX_FORM_DENSE  0x3u
 #define FFX_FORM_MASK   0xFu
+/* With FFX_FORM_AUTO: time every form of every axis at plan time (a few ms,
+ * on a batch of one, in temporary workspace), use the fastest, and append the
+ * result to the FFX_TUNE_CACHE file when that variable is set. */
+#define FFX_TUNE        0x20u
 /* ffx_expand writes the SUM over the batch of |Psibar|^2, added to what
  * out_density holds ([M_0..M_{d-1}], out += sum_b rho_b), instead of one
  * density per realization.  The sum runs over b in order (deterministic). */
@@ -234,8 +246,12 @@ int ffx_supported_length(int64_t n);
 /* Bytes of plan-owned workspace a call with this batch uses. */
 int64_t ffx_workspace_bytes(ffx_plan_t plan, int64_t batch);
 
-/* The form (FFX_FORM_PAPER or FFX_FORM_FOLD) the plan runs. */
+/* The form every axis runs (FFX_FORM_PAPER, _FOLD or _DENSE), or
+ * FFX_FORM_AUTO if the axes differ. */
 int ffx_plan_form(ffx_plan_t plan);
+
+/* The form lattice axis `axis` runs, or -1. */
+int ffx_plan_axis_form(ffx_plan_t plan, int axis);
 
 /* Number of kernel launches one ffx_expand / ffx_expand_backward call makes
  * with a non-empty batch. */
@@ -250,7 +266,13 @@ int ffx_plan_pass_order(ffx_plan_t plan, int32_t* order);
  * the plan records events[2i] just before and events[2i+1] just after itself
  * on the call's stream, i counting launches, until the array is full.
  * NULL (or n_events = 0) switches tracing off.  The library keeps the
- * pointer, not a copy: the array must outlive the traced calls. */
+ * pointer, not a copy: the array must outlive the traced calls.  Calls made
+ * while the stream is being captured into a CUDA graph record the events as
+ * event-record nodes of the graph (cudaEventRecordExternal), so they time the
+ * launches when the graph runs.  Every entry point except ffx_plan,
+ * ffx_plan_many and ffx_plan_destroy is stream-ordered and can be captured once
+ * the plan's workspace has grown to the batch used (a first, uncaptured call
+ * grows it). */
 int ffx_plan_trace(ffx_plan_t plan, void* const* events, int64_t n_events);
 
 /* Number of events recorded since the last ffx_plan_trace call. */

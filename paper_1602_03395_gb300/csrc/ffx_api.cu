@@ -1,12 +1,16 @@
-// C ABI of the free-flight expansion library: plans, argument checks,
-// workspace, and the sequence of per-axis passes.
+// C ABI of the free-flight expansion library: plans, argument checks, the
+// per-axis choice of form (paper / fold / dense, by cost model or by timing
+// with an on-disk cache), workspace, and the sequence of per-axis passes.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/ffx.h"
 #include "ffx_internal.h"
@@ -106,8 +110,12 @@ struct Axis {
   double dx = 0, a = 0, abar = 0;
   float2 *P = nullptr, *K = nullptr, *Kf = nullptr, *F = nullptr, *tw = nullptr;
   int* fold = nullptr;
-  PassKernelInfo fwd{}, adj{};
-  int grid_fwd = 0, grid_adj = 0;
+  int form = FFX_FORM_FOLD;  // PAPER, FOLD or DENSE
+  PassKernelInfo paper{}, foldk{}, adj{};
+  int grid_paper = 0, grid_fold = 0, grid_adj = 0;
+  float2* T = nullptr;   // dense map [N][N] (N <= kDenseMaxN)
+  float2* TH = nullptr;  // its adjoint
+  int grid_dense = 0, grid_dense_small = 0;
 };
 
 }  // namespace
@@ -124,37 +132,38 @@ struct ffx_plan_s {
   int64_t M = 1;
   double t = 0;
   uint32_t flags = 0;
-  int form = FFX_FORM_FOLD;
   int acc = 0;
   int device = 0;
+  int sms = 1;
   Axis axis[3];
   int order[3] = {0, 1, 2};  // forward pass order
   void* tables = nullptr;
-  void* ws = nullptr;
-  size_t ws_bytes = 0;
-  ManyPlan* many = nullptr;        // set for plans over many instances
-  void* const* trace = nullptr;  // caller's cudaEvent_t array (profiling)
+  void* dense_mem = nullptr;
+  void* ws[2] = {nullptr, nullptr};  // workspace buffers (grown on demand)
+  size_t ws_bytes[2] = {0, 0};
+  ManyPlan* many = nullptr;       // set for plans over many instances
+  void* const* trace = nullptr;   // caller's cudaEvent_t array (profiling)
   int64_t trace_n = 0;
   int64_t trace_i = 0;
 };
 
 namespace {
 
-int axis_outer_inner(const ffx_plan_s* p, int j, int64_t* outer, int64_t* inner) {
+void axis_outer_inner(const ffx_plan_s* p, int j, int64_t* outer, int64_t* inner) {
   int64_t o = 1, in = 1;
   for (int i = 0; i < j; ++i) o *= p->dims[i];
   for (int i = j + 1; i < p->ndim; ++i) in *= p->dims[i];
   *outer = o;
   *inner = in;
-  return 0;
 }
 
-int grid_for(const PassKernelInfo& info, int sms) {
+int grid_for(const void* func, int threads, size_t smem, int sms) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, info.func, info.threads, info.smem) !=
-          cudaSuccess ||
-      per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, threads, smem) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
     per_sm = 1;
+  }
   return per_sm * sms;
 }
 
@@ -192,44 +201,268 @@ int check_ptr(const void* p, const char* name) {
   return FFX_OK;
 }
 
-int ensure_ws(ffx_plan_s* p, int64_t batch) {
+int ensure_ws(ffx_plan_s* p, int which, int64_t batch) {
   const size_t need = (size_t)batch * (size_t)p->M * sizeof(float2);
-  if (need <= p->ws_bytes) return FFX_OK;
-  if (p->ws) {
-    cudaFree(p->ws);  // synchronizes the device: queued users of the old buffer finish first
-    p->ws = nullptr;
-    p->ws_bytes = 0;
+  if (need <= p->ws_bytes[which]) return FFX_OK;
+  if (p->ws[which]) {
+    cudaFree(p->ws[which]);  // synchronizes the device: queued users of the old buffer finish first
+    p->ws[which] = nullptr;
+    p->ws_bytes[which] = 0;
   }
-  cudaError_t e = cudaMalloc(&p->ws, need);
+  cudaError_t e = cudaMalloc(&p->ws[which], need);
   if (e != cudaSuccess) {
-    p->ws = nullptr;
+    p->ws[which] = nullptr;
     cudaGetLastError();
     return fail(FFX_ENOMEM, "workspace of %zu bytes: %s", need, cudaGetErrorString(e));
   }
-  p->ws_bytes = need;
+  p->ws_bytes[which] = need;
   return FFX_OK;
 }
 
-// Launch one pass of axis j.
-int run_pass(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* grad,
-             int grad_shared, float2* out_c, float* out_d, int acc, int64_t batch,
-             cudaStream_t stream) {
+bool inplace_ok(const Axis& ax) { return !(ax.form == FFX_FORM_DENSE && ax.N > kDenseInPlaceMaxN); }
+
+// Launch one pass of axis j (forward or adjoint) with the axis's form.
+int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* grad, int grad_shared,
+             float2* out_c, float* out_d, int acc, int64_t batch, cudaStream_t stream) {
   const Axis& ax = p->axis[j];
-  PassArgs a;
-  std::memset(&a, 0, sizeof(a));
   int64_t outer, inner;
   axis_outer_inner(p, j, &outer, &inner);
-  a.in = in;
-  a.grad = grad;
-  a.grad_shared = grad_shared;
-  a.out_c = out_c;
-  a.out_d = out_d;
-  a.outer = outer;
-  a.inner = inner;
-  a.M = p->M;
-  a.batch = batch;
-  a.acc = acc;
-  a.nlines = acc ? outer * inner : batch * outer * inner;
+  const bool traced = p->trace && p->trace_i + 2 <= p->trace_n;
+  // under stream capture the trace events become event-record nodes of the graph
+  unsigned rec_flags = cudaEventRecordDefault;
+  if (traced) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+      rec_flags = cudaEventRecordExternal;
+    cudaEventRecordWithFlags((cudaEvent_t)p->trace[p->trace_i], stream, rec_flags);
+  }
+  cudaError_t e;
+  if (ax.form == FFX_FORM_DENSE) {
+    DenseArgs d;
+    std::memset(&d, 0, sizeof(d));
+    d.A = adjoint ? ax.TH : ax.T;
+    d.in = in;
+    d.grad = grad;
+    d.grad_shared = grad_shared;
+    d.out_c = out_c;
+    d.out_d = out_d;
+    d.outer = outer;
+    d.inner = inner;
+    d.M = p->M;
+    d.batch = batch;
+    d.acc = acc;
+    d.ncols = acc ? outer * inner : batch * outer * inner;
+    d.N = ax.N;
+    if (ax.N <= kDenseInPlaceMaxN) {
+      int64_t grid = dense_small_tiles(d.ncols);
+      if (grid > ax.grid_dense_small) grid = ax.grid_dense_small;
+      if (grid < 1) grid = 1;
+      e = launch_dense_small(d, (int)grid, stream);
+    } else {
+      int64_t grid = dense_tiles(ax.N, d.ncols);
+      if (grid > ax.grid_dense) grid = ax.grid_dense;
+      if (grid < 1) grid = 1;
+      e = launch_dense(d, (int)grid, stream);
+    }
+  } else {
+    PassArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.in = in;
+    a.grad = grad;
+    a.grad_shared = grad_shared;
+    a.out_c = out_c;
+    a.out_d = out_d;
+    a.outer = outer;
+    a.inner = inner;
+    a.M = p->M;
+    a.batch = batch;
+    a.acc = acc;
+    a.nlines = acc ? outer * inner : batch * outer * inner;
+    a.lam = ax.lam;
+    a.g = ax.g;
+    a.Np = ax.Np;
+    a.tab.P = ax.P;
+    a.tab.K = ax.K;
+    a.tab.Kf = ax.Kf;
+    a.tab.F = ax.F;
+    a.tab.tw = ax.tw;
+    a.tab.fold = ax.fold;
+    const PassKernelInfo& info = adjoint ? ax.adj : (ax.form == FFX_FORM_PAPER ? ax.paper : ax.foldk);
+    const int capacity = adjoint ? ax.grid_adj : (ax.form == FFX_FORM_PAPER ? ax.grid_paper : ax.grid_fold);
+    // The split depends on one realization's lines only, so a realization's
+    // result does not depend on the batch it came in (bitwise).
+    a.qg = choose_qg(info, outer * inner, ax.lam, capacity);
+    const int lines = pass_lines_per_tile(info, a.qg);
+    const int64_t ntiles = (a.nlines + lines - 1) / lines;
+    int64_t grid = capacity;
+    if (grid > ntiles) grid = ntiles;
+    if (grid < 1) grid = 1;
+    e = info.launch(a, (int)grid, stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "pass launch");
+  if (traced) {
+    cudaEventRecordWithFlags((cudaEvent_t)p->trace[p->trace_i + 1], stream, rec_flags);
+    p->trace_i += 2;
+  }
+  return FFX_OK;
+}
+
+// Output buffers of a chain of passes (axes[0..n-1]) whose last pass must
+// write `final`: a pass that cannot run in place writes the other buffer of
+// the pair (final, alt).  outs[0] is where the first pass writes.  Returns
+// whether `alt` is used.
+bool plan_chain(const ffx_plan_s* p, const int* axes, int n, float2* final, float2* alt, float2** outs) {
+  bool uses_alt = false;
+  float2* cur = final;
+  for (int k = n - 1; k >= 0; --k) {
+    outs[k] = cur;
+    if (cur == alt) uses_alt = true;
+    if (k > 0 && !inplace_ok(p->axis[axes[k]])) cur = (cur == final) ? alt : final;
+  }
+  return uses_alt;
+}
+
+// Run a chain of passes (forward or adjoint) from `in` (read only) into
+// `out`; ws[alt_ws] serves as the alternate buffer and ws[1 - alt_ws] as the
+// spare copy of the input when an in-place call meets a pass that cannot run
+// in place.  The first pass may form 2 * grad * in on load.
+int chain_into(ffx_plan_s* p, const int* axes, bool adjoint, const float2* in, const float* grad,
+               int grad_shared, int64_t batch, float2* out, int alt_ws, cudaStream_t s) {
+  const int d = p->ndim;
+  float2* outs[3];
+  float2* probe[3];
+  const bool need_alt = plan_chain(p, axes, d, out, (float2*)(uintptr_t)8, probe);
+  float2* alt = nullptr;
+  int rc;
+  if (need_alt) {
+    if ((rc = ensure_ws(p, alt_ws, batch))) return rc;
+    alt = (float2*)p->ws[alt_ws];
+  }
+  plan_chain(p, axes, d, out, alt, outs);
+  const float2* cur = in;
+  if (in == outs[0] && !inplace_ok(p->axis[axes[0]])) {
+    const int spare = 1 - alt_ws;
+    if ((rc = ensure_ws(p, spare, batch))) return rc;
+    cudaError_t e =
+        cudaMemcpyAsync(p->ws[spare], in, (size_t)batch * p->M * sizeof(float2), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "input copy");
+    cur = (const float2*)p->ws[spare];
+  }
+  for (int r = 0; r < d; ++r) {
+    rc = run_axis(p, axes[r], adjoint, cur, r == 0 ? grad : nullptr, r == 0 ? grad_shared : 0, outs[r], nullptr,
+                  0, batch, s);
+    if (rc) return rc;
+    cur = outs[r];
+  }
+  return FFX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// per-axis form: cost model, timing, cache
+// ---------------------------------------------------------------------------
+
+// Relative cost per point of one axis pass (FP32 flops over the fraction of
+// the FP32 peak each form was measured to reach on GB300).
+double model_cost(const Axis& ax, int form) {
+  const double N = ax.N, lg = std::log2(N), lam = ax.lam;
+  switch (form) {
+    case FFX_FORM_PAPER: return lam * (10 * lg + 20) / 0.18;
+    case FFX_FORM_FOLD: return (lam * (5 * lg + 14) + 5 * lg) / 0.11;
+    default: return 8 * N / 0.45;
+  }
+}
+
+std::mutex g_cache_mutex;
+
+std::string cache_key(const char* dev, const Axis& ax, int64_t outer, int64_t inner) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s|N=%d|lam=%d|outer=%lld|inner=%lld", dev, ax.N, ax.lam, (long long)outer,
+           (long long)inner);
+  return buf;
+}
+
+// Cache lines (JSON, one object per line):
+//   {"key": "...", "form": "dense", "ms": [paper, fold, dense]}
+// The last line for a key wins.
+int cache_lookup(const std::string& key) {
+  const char* path = std::getenv("FFX_TUNE_CACHE");
+  if (!path || !*path) return -1;
+  std::lock_guard<std::mutex> lock(g_cache_mutex);
+  FILE* f = std::fopen(path, "r");
+  if (!f) return -1;
+  char line[2048];
+  int form = -1;
+  const std::string want = "\"key\": \"" + key + "\"";
+  while (std::fgets(line, sizeof(line), f)) {
+    if (!std::strstr(line, want.c_str())) continue;
+    if (std::strstr(line, "\"form\": \"paper\"")) form = FFX_FORM_PAPER;
+    if (std::strstr(line, "\"form\": \"fold\"")) form = FFX_FORM_FOLD;
+    if (std::strstr(line, "\"form\": \"dense\"")) form = FFX_FORM_DENSE;
+  }
+  std::fclose(f);
+  return form;
+}
+
+void cache_store(const std::string& key, int form, const double* ms) {
+  const char* path = std::getenv("FFX_TUNE_CACHE");
+  if (!path || !*path) return;
+  std::lock_guard<std::mutex> lock(g_cache_mutex);
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  const char* names[] = {"", "paper", "fold", "dense"};
+  std::fprintf(f, "{\"key\": \"%s\", \"form\": \"%s\", \"ms\": [%.6g, %.6g, %.6g]}\n", key.c_str(), names[form],
+               ms[0], ms[1], ms[2]);
+  std::fclose(f);
+}
+
+// Time the candidate forms of axis j on a batch of one (ws[0] -> ws[1]).
+int time_forms(ffx_plan_s* p, int j, cudaStream_t s, double* ms) {
+  Axis& ax = p->axis[j];
+  const int saved = ax.form;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int rc = FFX_OK;
+  for (int f = FFX_FORM_PAPER; f <= FFX_FORM_DENSE && rc == FFX_OK; ++f) {
+    ms[f - 1] = 1e30;
+    if (f == FFX_FORM_DENSE && !ax.T) continue;
+    ax.form = f;
+    float best = 1e30f;
+    for (int rep = 0; rep < 6 && rc == FFX_OK; ++rep) {
+      cudaEventRecord(e0, s);
+      rc = run_axis(p, j, false, (const float2*)p->ws[0], nullptr, 0, (float2*)p->ws[1], nullptr, 0, 1, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float t = 0;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (rep > 0 && t < best) best = t;  // the first run warms up
+    }
+    ms[f - 1] = best;
+  }
+  ax.form = saved;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+// Build the dense maps T_j and T_j^H: the fold-form pass applied to the N
+// unit vectors (rows of the identity), then transposed / conjugated.
+int build_dense(ffx_plan_s* p, int j, float2* T, float2* TH, float2* scratch, cudaStream_t s) {
+  Axis& ax = p->axis[j];
+  const int N = ax.N;
+  float2* I = scratch;
+  float2* O = scratch + (size_t)N * N;
+  cudaError_t e = launch_identity(I, N, s);
+  if (e != cudaSuccess) return cuda_fail(e, "identity");
+  PassArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.in = I;
+  a.out_c = O;
+  a.outer = 1;
+  a.inner = 1;
+  a.M = N;
+  a.batch = N;
+  a.nlines = N;
   a.lam = ax.lam;
   a.g = ax.g;
   a.Np = ax.Np;
@@ -239,36 +472,15 @@ int run_pass(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* 
   a.tab.F = ax.F;
   a.tab.tw = ax.tw;
   a.tab.fold = ax.fold;
-  const PassKernelInfo& info = adjoint ? ax.adj : ax.fwd;
-  const int capacity = adjoint ? ax.grid_adj : ax.grid_fwd;
-  // The split depends on one realization's lines only, so a realization's
-  // result does not depend on the batch it came in (bitwise).
-  a.qg = choose_qg(info, outer * inner, ax.lam, capacity);
-  const int lines = pass_lines_per_tile(info, a.qg);
-  const int64_t ntiles = (a.nlines + lines - 1) / lines;
-  int64_t grid = capacity;
-  if (grid > ntiles) grid = ntiles;
-  if (grid < 1) grid = 1;
-  const bool traced = p->trace && p->trace_i + 2 <= p->trace_n;
-  if (traced) cudaEventRecord((cudaEvent_t)p->trace[p->trace_i], stream);
-  cudaError_t e = info.launch(a, (int)grid, stream);
-  if (e != cudaSuccess) return cuda_fail(e, "pass launch");
-  if (traced) {
-    cudaEventRecord((cudaEvent_t)p->trace[p->trace_i + 1], stream);
-    p->trace_i += 2;
-  }
-  return FFX_OK;
-}
-
-// Forward map into a complex field (out may equal in).
-int forward_field(ffx_plan_s* p, const float2* psi0, int64_t batch, float2* out,
-                  cudaStream_t s) {
-  const float2* cur = psi0;
-  for (int k = 0; k < p->ndim; ++k) {
-    int rc = run_pass(p, p->order[k], false, cur, nullptr, 0, out, nullptr, 0, batch, s);
-    if (rc) return rc;
-    cur = out;
-  }
+  a.qg = choose_qg(ax.foldk, N, ax.lam, ax.grid_fold);
+  const int lines = pass_lines_per_tile(ax.foldk, a.qg);
+  int64_t grid = (N + lines - 1) / lines;
+  if (grid > ax.grid_fold) grid = ax.grid_fold;
+  e = ax.foldk.launch(a, (int)grid, s);
+  if (e == cudaSuccess) e = launch_dense_build(O, T, TH, N, s);
+  if (e != cudaSuccess) return cuda_fail(e, "dense map");
+  ax.T = T;
+  ax.TH = TH;
   return FFX_OK;
 }
 
@@ -299,11 +511,10 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
   if (ndim < 1 || ndim > 3) return fail(FFX_EINVAL, "ndim must be 1..3, got %d", ndim);
   if (!dims || !spacing || !magnification) return fail(FFX_EINVAL, "dims/spacing/magnification is NULL");
   if (!std::isfinite(t)) return fail(FFX_EINVAL, "t must be finite");
-  const uint32_t known = FFX_FORM_MASK | FFX_ACCUMULATE;
+  const uint32_t known = FFX_FORM_MASK | FFX_ACCUMULATE | FFX_TUNE;
   if (flags & ~known) return fail(FFX_EINVAL, "unknown flag bits 0x%x", flags & ~known);
   const uint32_t form = flags & FFX_FORM_MASK;
-  if (form != FFX_FORM_AUTO && form != FFX_FORM_PAPER && form != FFX_FORM_FOLD)
-    return fail(FFX_EINVAL, "unknown form %u", form);
+  if (form > FFX_FORM_DENSE) return fail(FFX_EINVAL, "unknown form %u", form);
   int64_t M = 1;
   for (int j = 0; j < ndim; ++j) {
     if (dims[j] < 1) return fail(FFX_EINVAL, "dims[%d] = %lld < 1", j, (long long)dims[j]);
@@ -318,6 +529,9 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
       return fail(FFX_EINVAL, "offsets must be finite");
     if (!supported_length(dims[j]))
       return fail(FFX_EUNSUPPORTED, "no line kernel for length %lld (axis %d)", (long long)dims[j], j);
+    if (form == FFX_FORM_DENSE && dims[j] > kDenseMaxN)
+      return fail(FFX_EUNSUPPORTED, "the dense form takes lines up to %d points (axis %d has %lld)",
+                  kDenseMaxN, j, (long long)dims[j]);
     M *= dims[j];
   }
 
@@ -326,13 +540,20 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
   p->ndim = ndim;
   p->t = t;
   p->flags = flags;
-  p->form = (form == FFX_FORM_PAPER) ? FFX_FORM_PAPER : FFX_FORM_FOLD;
   p->acc = (flags & FFX_ACCUMULATE) ? 1 : 0;
   p->M = M;
   cudaGetDevice(&p->device);
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-  if (sms < 1) sms = 1;
+  p->sms = sms > 0 ? sms : 1;
+  for (int j = 0; j < ndim; ++j) p->dims[j] = dims[j];
+  // Forward order: longest lines first, so the last pass (which may sum the
+  // ensemble and then has only one realization's lines to spread over the
+  // GPU) runs on the axis with the most lines.
+  for (int j = 0; j < ndim; ++j) p->order[j] = j;
+  for (int i = 0; i < ndim; ++i)
+    for (int k = i + 1; k < ndim; ++k)
+      if (p->dims[p->order[k]] > p->dims[p->order[i]]) std::swap(p->order[i], p->order[k]);
 
   // table memory: per axis 4 lam*N complex tables + N twiddles + N fold ints
   size_t bytes = 0;
@@ -355,11 +576,11 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
   }
   char* cur = (char*)p->tables;
   int rc = FFX_OK;
+  std::vector<int> fold_h;
   for (int j = 0; j < ndim && rc == FFX_OK; ++j) {
     Axis& ax = p->axis[j];
     const int N = (int)dims[j];
     const int lam = magnification[j];
-    p->dims[j] = dims[j];
     ax.N = N;
     ax.lam = lam;
     ax.dx = spacing[j];
@@ -390,63 +611,138 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
     // phase constants in turns (hbar = m = 1): s = (abar - a)/dx, tau = pi t / L^2
     const double sv = (ax.abar - ax.a) / ax.dx;
     const double tau = M_PI * t / (L * L);
-    const uint64_t c_sN = frac_fx(sv / N);
-    const uint64_t c_tau = frac_fx(tau);
-    const uint64_t c_2tl = frac_fx(2.0 * tau / lam);
-    const uint64_t c_slN = frac_fx(sv / ((double)lam * N));
-    const uint64_t c_tl2 = frac_fx(tau / ((double)lam * lam));
-    e = launch_fill_tables(N, lam, c_sN, c_tau, c_2tl, c_slN, c_tl2, ax.P, ax.K, ax.Kf, ax.F, ax.tw, s);
+    e = launch_fill_tables(N, lam, frac_fx(sv / N), frac_fx(tau), frac_fx(2.0 * tau / lam),
+                           frac_fx(sv / ((double)lam * N)), frac_fx(tau / ((double)lam * lam)), ax.P, ax.K,
+                           ax.Kf, ax.F, ax.tw, s);
     if (e != cudaSuccess) {
       rc = cuda_fail(e, "table fill");
       break;
     }
     // fold table: m0 with (lam/g) m0 = r/g (mod N/g) for g | r, else -1
-    int* fold_h = (int*)std::malloc(sizeof(int) * N);
-    if (!fold_h) {
-      rc = fail(FFX_ENOMEM, "host allocation failed");
-      break;
-    }
     const int64_t inv = inv_mod((lam / ax.g) % ax.Np, ax.Np);
+    fold_h.assign(N, -1);
     for (int r = 0; r < N; ++r)
-      fold_h[r] = (r % ax.g == 0) ? (int)(((int64_t)(r / ax.g) * inv) % ax.Np) : -1;
-    e = cudaMemcpyAsync(ax.fold, fold_h, sizeof(int) * N, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    std::free(fold_h);
+      if (r % ax.g == 0) fold_h[r] = (int)(((int64_t)(r / ax.g) * inv) % ax.Np);
+    e = cudaMemcpyAsync(ax.fold, fold_h.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // fold_h is reused
     if (e != cudaSuccess) {
       rc = cuda_fail(e, "fold table upload");
       break;
     }
-    const int kind = (p->form == FFX_FORM_PAPER) ? KIND_FWD_PAPER : KIND_FWD_FOLD;
-    if (!find_pass_kernel(N, kind, &ax.fwd) || !find_pass_kernel(N, KIND_ADJ_FOLD, &ax.adj)) {
+    if (!find_pass_kernel(N, KIND_FWD_PAPER, &ax.paper) || !find_pass_kernel(N, KIND_FWD_FOLD, &ax.foldk) ||
+        !find_pass_kernel(N, KIND_ADJ_FOLD, &ax.adj)) {
       rc = fail(FFX_EUNSUPPORTED, "no kernel for length %d", N);
       break;
     }
-    if ((rc = prepare_kernel(ax.fwd)) != FFX_OK) break;
-    if ((rc = prepare_kernel(ax.adj)) != FFX_OK) break;
-    ax.grid_fwd = grid_for(ax.fwd, sms);
-    ax.grid_adj = grid_for(ax.adj, sms);
+    if ((rc = prepare_kernel(ax.paper)) || (rc = prepare_kernel(ax.foldk)) || (rc = prepare_kernel(ax.adj))) break;
+    ax.grid_paper = grid_for(ax.paper.func, ax.paper.threads, ax.paper.smem, p->sms);
+    ax.grid_fold = grid_for(ax.foldk.func, ax.foldk.threads, ax.foldk.smem, p->sms);
+    ax.grid_adj = grid_for(ax.adj.func, ax.adj.threads, ax.adj.smem, p->sms);
+    ax.grid_dense = grid_for(dense_kernel_func(), 256, 0, p->sms);
+    e = cudaFuncSetAttribute(dense_small_func(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)dense_small_smem());
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "cudaFuncSetAttribute");
+      break;
+    }
+    ax.grid_dense_small = grid_for(dense_small_func(), 128, dense_small_smem(), p->sms);
   }
   if (rc == FFX_OK) {
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) rc = cuda_fail(e, "table fill");
   }
+
+  // dense maps where the dense form may be used
+  if (rc == FFX_OK) {
+    size_t dbytes = 0, scratch = 0;
+    for (int j = 0; j < ndim; ++j) {
+      const size_t N = (size_t)dims[j];
+      if (N <= (size_t)kDenseMaxN && (form == FFX_FORM_AUTO || form == FFX_FORM_DENSE)) {
+        dbytes += 2 * N * N * sizeof(float2);
+        scratch = std::max(scratch, 2 * N * N * sizeof(float2));
+      }
+    }
+    if (dbytes > 0) {
+      void* tmp = nullptr;
+      e = cudaMalloc(&p->dense_mem, dbytes);
+      if (e == cudaSuccess) e = cudaMalloc(&tmp, scratch);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(FFX_ENOMEM, "dense maps: %s", cudaGetErrorString(e));
+      } else {
+        float2* dcur = (float2*)p->dense_mem;
+        for (int j = 0; j < ndim && rc == FFX_OK; ++j) {
+          const size_t N = (size_t)dims[j];
+          if (N > (size_t)kDenseMaxN) continue;
+          rc = build_dense(p, j, dcur, dcur + N * N, (float2*)tmp, s);
+          dcur += 2 * N * N;
+        }
+        if (rc == FFX_OK) {
+          e = cudaStreamSynchronize(s);
+          if (e != cudaSuccess) rc = cuda_fail(e, "dense map");
+        }
+      }
+      if (tmp) cudaFree(tmp);
+    }
+  }
+
+  // per-axis form
+  if (rc == FFX_OK) {
+    char dev[256] = "unknown";
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, p->device) == cudaSuccess) snprintf(dev, sizeof(dev), "%s", prop.name);
+    bool tuned_any = false;
+    for (int j = 0; j < ndim && rc == FFX_OK; ++j) {
+      Axis& ax = p->axis[j];
+      if (form != FFX_FORM_AUTO) {
+        ax.form = (int)form;
+        continue;
+      }
+      int64_t outer, inner;
+      axis_outer_inner(p, j, &outer, &inner);
+      const std::string key = cache_key(dev, ax, outer, inner);
+      int f = cache_lookup(key);
+      if (f == FFX_FORM_DENSE && !ax.T) f = -1;
+      if (f < 0 && (flags & FFX_TUNE)) {
+        if (!tuned_any) {
+          if ((rc = ensure_ws(p, 0, 1)) || (rc = ensure_ws(p, 1, 1))) break;
+          e = cudaMemsetAsync(p->ws[0], 0, (size_t)M * sizeof(float2), s);
+          if (e != cudaSuccess) {
+            rc = cuda_fail(e, "tuning input");
+            break;
+          }
+          tuned_any = true;
+        }
+        double ms[3];
+        if ((rc = time_forms(p, j, s, ms))) break;
+        f = FFX_FORM_PAPER;
+        for (int c = FFX_FORM_FOLD; c <= FFX_FORM_DENSE; ++c)
+          if (ms[c - 1] < ms[f - 1]) f = c;
+        cache_store(key, f, ms);
+      }
+      if (f < 0) {
+        f = FFX_FORM_PAPER;
+        for (int c = FFX_FORM_FOLD; c <= FFX_FORM_DENSE; ++c) {
+          if (c == FFX_FORM_DENSE && !ax.T) continue;
+          if (model_cost(ax, c) < model_cost(ax, f)) f = c;
+        }
+      }
+      ax.form = f;
+    }
+    if (rc == FFX_OK && tuned_any) {
+      e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) rc = cuda_fail(e, "tuning");
+    }
+  }
   cudaStreamDestroy(s);
   if (rc != FFX_OK) {
+    for (int w = 0; w < 2; ++w)
+      if (p->ws[w]) cudaFree(p->ws[w]);
+    if (p->dense_mem) cudaFree(p->dense_mem);
     cudaFree(p->tables);
     delete p;
     return rc;
   }
-  // Forward order: longest lines first, so the last pass (which may sum the
-  // ensemble and then has only one realization's lines to spread over the
-  // GPU) runs on the axis with the most lines.
-  for (int j = 0; j < ndim; ++j) p->order[j] = j;
-  for (int i = 0; i < ndim; ++i)
-    for (int k = i + 1; k < ndim; ++k)
-      if (p->dims[p->order[k]] > p->dims[p->order[i]]) {
-        int tmp = p->order[i];
-        p->order[i] = p->order[k];
-        p->order[k] = tmp;
-      }
   *out = p;
   return FFX_OK;
 }
@@ -466,7 +762,7 @@ int ffx_plan_many(ffx_plan_t* out, int n_instances, const ffx_instance_desc* des
   }
   p->many = mp;
   p->ndim = many_max_dim(mp);
-  p->form = many_form(mp);
+  for (int j = 0; j < 3; ++j) p->axis[j].form = many_form(mp);
   p->M = many_total(mp);
   *out = p;
   return FFX_OK;
@@ -487,13 +783,26 @@ int ffx_plan_destroy(ffx_plan_t p) {
     delete p;
     return FFX_OK;
   }
-  if (p->ws) cudaFree(p->ws);
+  for (int w = 0; w < 2; ++w)
+    if (p->ws[w]) cudaFree(p->ws[w]);
+  if (p->dense_mem) cudaFree(p->dense_mem);
   if (p->tables) cudaFree(p->tables);
   delete p;
   return FFX_OK;
 }
 
-int ffx_plan_form(ffx_plan_t p) { return p ? p->form : -1; }
+int ffx_plan_form(ffx_plan_t p) {
+  if (!p) return -1;
+  const int f = p->axis[0].form;
+  for (int j = 1; j < p->ndim; ++j)
+    if (p->axis[j].form != f) return FFX_FORM_AUTO;
+  return f;
+}
+
+int ffx_plan_axis_form(ffx_plan_t p, int axis) {
+  if (!p || axis < 0 || axis >= p->ndim) return -1;
+  return p->axis[axis].form;
+}
 
 int ffx_plan_pass_order(ffx_plan_t p, int32_t* order) {
   if (!p || !order) return fail(FFX_EINVAL, "plan or order is NULL");
@@ -514,13 +823,15 @@ int64_t ffx_plan_trace_count(ffx_plan_t p) { return p ? p->trace_i : -1; }
 
 int64_t ffx_workspace_bytes(ffx_plan_t p, int64_t batch) {
   if (!p || batch < 0) return -1;
-  return batch * p->M * (int64_t)sizeof(float2);
+  int64_t total = 0;
+  for (int w = 0; w < 2; ++w) total += (int64_t)p->ws_bytes[w];
+  const int64_t need = batch * p->M * (int64_t)sizeof(float2);
+  return total > need ? total : need;
 }
 
 int ffx_launches_per_call(ffx_plan_t p, int backward) {
   if (!p) return -1;
-  if (p->many) return backward ? 2 * p->ndim : p->ndim;  // one persistent kernel per phase
-  return backward ? 2 * p->ndim : p->ndim;
+  return backward ? 2 * p->ndim : p->ndim;  // many-plans: one persistent kernel per phase
 }
 
 int ffx_expand(ffx_plan_t p, const void* psi0, int64_t batch, float* out_density, void* stream) {
@@ -536,18 +847,27 @@ int ffx_expand(ffx_plan_t p, const void* psi0, int64_t batch, float* out_density
     rc = many_expand(p->many, psi0, out_density, nullptr, s, &err);
     return rc ? fail(rc, "%s", err.c_str()) : FFX_OK;
   }
-  const float2* in = (const float2*)psi0;
   const int d = p->ndim;
-  if (d > 1 && (rc = ensure_ws(p, batch))) return rc;
-  float2* ws = (float2*)p->ws;
-  for (int k = 0; k < d; ++k) {
-    const int j = p->order[k];
-    const bool last = (k == d - 1);
-    rc = run_pass(p, j, false, k == 0 ? in : ws, nullptr, 0, last ? nullptr : ws,
-                  last ? out_density : nullptr, last ? p->acc : 0, batch, s);
-    if (rc) return rc;
+  const float2* cur = (const float2*)psi0;
+  if (d > 1) {
+    // every pass but the last writes a complex field: ws[0], switching to ws[1]
+    // and back for passes that cannot run in place
+    if ((rc = ensure_ws(p, 0, batch))) return rc;
+    float2* ws0 = (float2*)p->ws[0];
+    float2* target = ws0;
+    for (int k = 0; k < d - 1; ++k) {
+      const int j = p->order[k];
+      if (k > 0 && !inplace_ok(p->axis[j])) {
+        if ((rc = ensure_ws(p, 1, batch))) return rc;
+        ws0 = (float2*)p->ws[0];  // (unchanged: ensure_ws(1) touches only ws[1])
+        target = (cur == ws0) ? (float2*)p->ws[1] : ws0;
+      }
+      rc = run_axis(p, j, false, cur, nullptr, 0, target, nullptr, 0, batch, s);
+      if (rc) return rc;
+      cur = target;
+    }
   }
-  return FFX_OK;
+  return run_axis(p, p->order[d - 1], false, cur, nullptr, 0, nullptr, out_density, p->acc, batch, s);
 }
 
 int ffx_expand_field(ffx_plan_t p, const void* psi0, int64_t batch, void* out_field, void* stream) {
@@ -562,7 +882,8 @@ int ffx_expand_field(ffx_plan_t p, const void* psi0, int64_t batch, void* out_fi
     rc = many_expand(p->many, psi0, nullptr, out_field, (cudaStream_t)stream, &err);
     return rc ? fail(rc, "%s", err.c_str()) : FFX_OK;
   }
-  return forward_field(p, (const float2*)psi0, batch, (float2*)out_field, (cudaStream_t)stream);
+  return chain_into(p, p->order, false, (const float2*)psi0, nullptr, 0, batch, (float2*)out_field, 0,
+                    (cudaStream_t)stream);
 }
 
 int ffx_expand_adjoint(ffx_plan_t p, const void* g_in, int64_t batch, void* g_out, void* stream) {
@@ -572,14 +893,10 @@ int ffx_expand_adjoint(ffx_plan_t p, const void* g_in, int64_t batch, void* g_ou
   int rc;
   if ((rc = check_ptr(g_in, "g_in")) || (rc = check_ptr(g_out, "g_out"))) return rc;
   if (p->many) return fail(FFX_EUNSUPPORTED, "ffx_expand_adjoint does not take a many-instance plan");
-  const float2* cur = (const float2*)g_in;
-  for (int k = p->ndim - 1; k >= 0; --k) {
-    rc = run_pass(p, p->order[k], true, cur, nullptr, 0, (float2*)g_out, nullptr, 0, batch,
-                  (cudaStream_t)stream);
-    if (rc) return rc;
-    cur = (const float2*)g_out;
-  }
-  return FFX_OK;
+  int axes[3];
+  for (int r = 0; r < p->ndim; ++r) axes[r] = p->order[p->ndim - 1 - r];
+  return chain_into(p, axes, true, (const float2*)g_in, nullptr, 0, batch, (float2*)g_out, 0,
+                    (cudaStream_t)stream);
 }
 
 int ffx_expand_backward(ffx_plan_t p, const void* psi0, const float* grad_density, int64_t batch,
@@ -591,25 +908,21 @@ int ffx_expand_backward(ffx_plan_t p, const void* psi0, const float* grad_densit
   if ((rc = check_ptr(psi0, "psi0")) || (rc = check_ptr(grad_density, "grad_density")) ||
       (rc = check_ptr(grad_psi0, "grad_psi0")))
     return rc;
+  cudaStream_t s = (cudaStream_t)stream;
   if (p->many) {
     if (batch != 1) return fail(FFX_EINVAL, "a many-instance plan takes batch = 1");
     std::string err;
-    rc = many_backward(p->many, psi0, grad_density, grad_psi0, (cudaStream_t)stream, &err);
+    rc = many_backward(p->many, psi0, grad_density, grad_psi0, s, &err);
     return rc ? fail(rc, "%s", err.c_str()) : FFX_OK;
   }
-  if ((rc = ensure_ws(p, batch))) return rc;
-  cudaStream_t s = (cudaStream_t)stream;
-  float2* ws = (float2*)p->ws;
-  if ((rc = forward_field(p, (const float2*)psi0, batch, ws, s))) return rc;
-  const float2* cur = ws;
-  for (int k = p->ndim - 1; k >= 0; --k) {
-    const bool first = (k == p->ndim - 1);
-    rc = run_pass(p, p->order[k], true, cur, first ? grad_density : nullptr, first ? p->acc : 0,
-                  (float2*)grad_psi0, nullptr, 0, batch, s);
-    if (rc) return rc;
-    cur = (const float2*)grad_psi0;
-  }
-  return FFX_OK;
+  // T psi0 into ws[0] (ws[1] as the alternate), then T^H (2 grad * .) into
+  // grad_psi0 (ws[1] as the alternate)
+  if ((rc = ensure_ws(p, 0, batch))) return rc;
+  float2* field = (float2*)p->ws[0];
+  if ((rc = chain_into(p, p->order, false, (const float2*)psi0, nullptr, 0, batch, field, 1, s))) return rc;
+  int axes[3];
+  for (int r = 0; r < p->ndim; ++r) axes[r] = p->order[p->ndim - 1 - r];
+  return chain_into(p, axes, true, field, grad_density, p->acc, batch, (float2*)grad_psi0, 1, s);
 }
 
 }  // extern "C"

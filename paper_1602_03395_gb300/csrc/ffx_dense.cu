@@ -1,0 +1,451 @@
+// Dense form of one axis pass: the per-axis map as an N x N matrix.
+//
+// The d-dimensional map of eq. FF is a tensor product of per-axis maps
+// (every phase of eq. FF is exp(i sum_j ...), and n'' is per axis), and each
+// per-axis map is linear: Psibar_nb = sum_n T[nb, n] psi_n.  The plan builds
+// T once on the GPU by running the FFT-form pass (pre-chirp, FFT, k-space
+// phase, fold, inverse FFT) on the N unit vectors, so T is the same map the
+// line passes apply, at the same FP32 accuracy.  A pass then is one batched
+// complex matrix product per axis: for every (realization, outer) slab,
+// OUT[N x inner] = T[N x N] * IN[N x inner]; for the contiguous axis the slab
+// is [lines x N] and the product runs on its transpose.  It costs 8N flops per
+// point instead of the FFT form's lam (5 log2 N + 14), which is the cheaper
+// form when lam is large against N.
+//
+// Kernel: 256 threads compute a 64 (rows nb) x 32 (columns = lines) tile;
+// thread (tx, ty) owns rows ty + 16 i (i < 4) and columns tx + 16 j (j < 2),
+// so shared-memory reads of both operands are conflict-free.  K runs in chunks
+// of 16 through shared memory.  The epilogue writes complex64, or |.|^2, or
+// |.|^2 summed over the batch (the tile then loops over b, deterministic).
+#include <cstring>
+
+#include "ffx_internal.h"
+
+namespace ffx {
+
+namespace {
+
+constexpr int DBM = 64, DBN = 32, DBK = 16, DTX = 16, DTY = 16, DTM = 4, DTN = 2;
+
+__device__ __forceinline__ void dcfma(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+
+__global__ void __launch_bounds__(256) dense_pass_kernel(const DenseArgs a) {
+  __shared__ float2 As[DBK][DBM + 1];
+  __shared__ float2 Bs[DBK][DBN + 1];
+  __shared__ long long cbase[DBN];
+  __shared__ int cb[DBN];
+
+  const int N = a.N;
+  const int tx = threadIdx.x % DTX, ty = threadIdx.x / DTX;
+  const int64_t inner = a.inner;
+  const bool contiguous = (inner == 1);
+  const int64_t ncols = a.ncols;
+  const int row_blocks = (N + DBM - 1) / DBM;
+  const int64_t col_blocks = (ncols + DBN - 1) / DBN;
+  const int64_t ntiles = (int64_t)row_blocks * col_blocks;
+  const int nb_loop = a.acc ? (int)a.batch : 1;
+  const int64_t per_real = a.outer * inner;
+
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int rb = (int)(tile % row_blocks);
+    const int64_t cbk = tile / row_blocks;
+    const int m0 = rb * DBM;
+    const int64_t c0 = cbk * DBN;
+    float racc[DTM][DTN];
+#pragma unroll
+    for (int i = 0; i < DTM; ++i)
+#pragma unroll
+      for (int j = 0; j < DTN; ++j) racc[i][j] = 0.f;
+
+    for (int bl = 0; bl < nb_loop; ++bl) {
+      __syncthreads();
+      if (threadIdx.x < DBN) {
+        const int64_t c = c0 + threadIdx.x;
+        long long base = -1;
+        int b = 0;
+        if (c < ncols) {
+          int64_t bo = c / inner;
+          const int64_t i = c - bo * inner;
+          if (a.acc) {
+            b = bl;
+            bo += (int64_t)bl * a.outer;
+          } else {
+            b = (int)(c / per_real);
+          }
+          base = bo * (int64_t)N * inner + i;
+        }
+        cbase[threadIdx.x] = base;
+        cb[threadIdx.x] = b;
+      }
+      float2 acc[DTM][DTN];
+#pragma unroll
+      for (int i = 0; i < DTM; ++i)
+#pragma unroll
+        for (int j = 0; j < DTN; ++j) acc[i][j] = make_float2(0.f, 0.f);
+
+      for (int k0 = 0; k0 < N; k0 += DBK) {
+        __syncthreads();  // previous chunk consumed; cbase visible
+        // A chunk: As[kk][mm] = T[m0 + mm][k0 + kk]
+        for (int idx = threadIdx.x; idx < DBK * DBM; idx += 256) {
+          const int mm = idx / DBK, kk = idx - mm * DBK;
+          const int m = m0 + mm, k = k0 + kk;
+          As[kk][mm] = (m < N && k < N) ? __ldg(a.A + (size_t)m * N + k) : make_float2(0.f, 0.f);
+        }
+        // B chunk: Bs[kk][cc] = in[col c0 + cc][row k0 + kk]
+        for (int idx = threadIdx.x; idx < DBK * DBN; idx += 256) {
+          int kk, cc;
+          if (contiguous) {
+            cc = idx / DBK;
+            kk = idx - cc * DBK;
+          } else {
+            kk = idx / DBN;
+            cc = idx - kk * DBN;
+          }
+          const int k = k0 + kk;
+          const long long base = cbase[cc];
+          float2 v = make_float2(0.f, 0.f);
+          if (base >= 0 && k < N) {
+            const int64_t addr = base + (int64_t)k * inner;
+            v = a.in[addr];  // plain load: passes may run in place
+            if (a.grad) {
+              const int64_t gaddr = a.grad_shared ? addr - (int64_t)cb[cc] * a.M : addr;
+              const float gr = 2.f * __ldg(a.grad + gaddr);
+              v.x *= gr;
+              v.y *= gr;
+            }
+          }
+          Bs[kk][cc] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < DBK; ++kk) {
+          float2 av[DTM], bv[DTN];
+#pragma unroll
+          for (int i = 0; i < DTM; ++i) av[i] = As[kk][ty + DTY * i];
+#pragma unroll
+          for (int j = 0; j < DTN; ++j) bv[j] = Bs[kk][tx + DTX * j];
+#pragma unroll
+          for (int i = 0; i < DTM; ++i)
+#pragma unroll
+            for (int j = 0; j < DTN; ++j) dcfma(acc[i][j], av[i], bv[j]);
+        }
+      }
+      // epilogue for this realization
+      __syncthreads();  // all reads of this realization's inputs are done (in-place passes)
+      if (a.acc) {
+#pragma unroll
+        for (int i = 0; i < DTM; ++i)
+#pragma unroll
+          for (int j = 0; j < DTN; ++j) racc[i][j] += acc[i][j].x * acc[i][j].x + acc[i][j].y * acc[i][j].y;
+      } else {
+#pragma unroll
+        for (int i = 0; i < DTM; ++i) {
+          const int m = m0 + ty + DTY * i;
+          if (m >= N) continue;
+#pragma unroll
+          for (int j = 0; j < DTN; ++j) {
+            const int cc = tx + DTX * j;
+            const long long base = cbase[cc];
+            if (base < 0) continue;
+            const int64_t addr = base + (int64_t)m * inner;
+            if (a.out_c)
+              a.out_c[addr] = acc[i][j];
+            else
+              a.out_d[addr] = acc[i][j].x * acc[i][j].x + acc[i][j].y * acc[i][j].y;
+          }
+        }
+      }
+    }
+    if (a.acc) {
+#pragma unroll
+      for (int i = 0; i < DTM; ++i) {
+        const int m = m0 + ty + DTY * i;
+        if (m >= N) continue;
+#pragma unroll
+        for (int j = 0; j < DTN; ++j) {
+          const int cc = tx + DTX * j;
+          const long long base = cbase[cc];
+          if (base < 0) continue;
+          const int64_t addr = base - (int64_t)(nb_loop - 1) * a.M + (int64_t)m * inner;
+          a.out_d[addr] += racc[i][j];
+        }
+      }
+    }
+  }
+}
+
+// Lines of at most 64 points: T stays in shared memory for the whole launch,
+// a 64 x 32 output tile takes all of K at once, each of 128 threads owns a
+// 4 x 4 block (rows ty + 16 i, columns tx + 8 j), and the next tile's input is
+// loaded into registers while the current one is multiplied.  Items are
+// (column tile, realization) pairs; with ensemble summing a block takes every
+// realization of its column tile in order.
+constexpr int SBN = 32, STX = 8, STY = 16, STM = 4, STN = 4, SNMAX = 64;
+constexpr int SLOADS = SNMAX * SBN / 128;  // input elements each thread loads per tile
+
+struct SmallItem {
+  int64_t cbk;
+  int b;
+};
+
+__device__ __forceinline__ void small_bases(const DenseArgs& a, int64_t cbk, int b, long long* cbase,
+                                            int* cbr, int t) {
+  // column t of column tile cbk, realization b (b only used when summing the ensemble)
+  const int64_t inner = a.inner;
+  const int64_t c = cbk * SBN + t;
+  long long base = -1;
+  int br = 0;
+  if (c < a.ncols) {
+    int64_t bo = c / inner;
+    const int64_t i = c - bo * inner;
+    if (a.acc) {
+      br = b;
+      bo += (int64_t)b * a.outer;
+    } else {
+      br = (int)(c / (a.outer * inner));
+    }
+    base = bo * (int64_t)a.N * inner + i;
+  }
+  cbase[t] = base;
+  cbr[t] = br;
+}
+
+__global__ void __launch_bounds__(128) dense_small_kernel(const DenseArgs a) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  float2* As = reinterpret_cast<float2*>(dsm);                   // [SNMAX][SNMAX + 1], As[k][m] = A[m][k]
+  float2* Bs = As + SNMAX * (SNMAX + 1);                         // [SNMAX][SBN + 1]
+  __shared__ long long cbase[2][SBN];
+  __shared__ int cbr[2][SBN];
+
+  const int N = a.N;
+  const int tid = threadIdx.x;
+  const int tx = tid % STX, ty = tid / STX;
+  const int64_t inner = a.inner;
+  const bool contiguous = (inner == 1);
+  const int64_t col_tiles = (a.ncols + SBN - 1) / SBN;
+  const int nb = a.acc ? (int)a.batch : 1;
+  // this block's items: column tiles blockIdx.x, blockIdx.x + gridDim.x, ...; each for nb realizations
+  const int64_t my_tiles = (col_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
+  const int64_t n_items = (blockIdx.x < col_tiles) ? my_tiles * nb : 0;
+  if (n_items == 0) return;
+
+  for (int idx = tid; idx < N * N; idx += 128) {
+    const int m = idx / N, k = idx - m * N;
+    As[k * (SNMAX + 1) + m] = __ldg(a.A + idx);
+  }
+
+  auto item_at = [&](int64_t it) {
+    SmallItem r;
+    r.cbk = blockIdx.x + (it / nb) * gridDim.x;
+    r.b = (int)(it % nb);
+    return r;
+  };
+  auto load_item = [&](int buf, float2 (&pre)[SLOADS]) {
+#pragma unroll
+    for (int l = 0; l < SLOADS; ++l) {
+      const int idx = tid + l * 128;
+      int k, cc;
+      if (contiguous) {
+        cc = idx / SNMAX;
+        k = idx - cc * SNMAX;
+      } else {
+        k = idx / SBN;
+        cc = idx - k * SBN;
+      }
+      float2 v = make_float2(0.f, 0.f);
+      const long long base = cbase[buf][cc];
+      if (k < N && base >= 0) {
+        const int64_t addr = base + (int64_t)k * inner;
+        v = a.in[addr];  // plain load: passes may run in place
+        if (a.grad) {
+          const int64_t gaddr = a.grad_shared ? addr - (int64_t)cbr[buf][cc] * a.M : addr;
+          const float gr = 2.f * __ldg(a.grad + gaddr);
+          v.x *= gr;
+          v.y *= gr;
+        }
+      }
+      pre[l] = v;
+    }
+  };
+
+  float2 pre[SLOADS];
+  if (tid < SBN) {
+    const SmallItem i0 = item_at(0);
+    small_bases(a, i0.cbk, i0.b, cbase[0], cbr[0], tid);
+  }
+  __syncthreads();
+  load_item(0, pre);
+
+  float racc[STM][STN];
+#pragma unroll
+  for (int i = 0; i < STM; ++i)
+#pragma unroll
+    for (int j = 0; j < STN; ++j) racc[i][j] = 0.f;
+
+  for (int64_t it = 0; it < n_items; ++it) {
+    const int buf = (int)(it & 1);
+    const SmallItem cur = item_at(it);
+    __syncthreads();  // Bs free (previous tile multiplied and stored)
+#pragma unroll
+    for (int l = 0; l < SLOADS; ++l) {
+      const int idx = tid + l * 128;
+      int k, cc;
+      if (contiguous) {
+        cc = idx / SNMAX;
+        k = idx - cc * SNMAX;
+      } else {
+        k = idx / SBN;
+        cc = idx - k * SBN;
+      }
+      Bs[k * (SBN + 1) + cc] = pre[l];
+    }
+    if (it + 1 < n_items && tid < SBN) {
+      const SmallItem nx = item_at(it + 1);
+      small_bases(a, nx.cbk, nx.b, cbase[buf ^ 1], cbr[buf ^ 1], tid);
+    }
+    __syncthreads();
+    if (it + 1 < n_items) load_item(buf ^ 1, pre);  // in flight during the product
+
+    float2 acc[STM][STN];
+#pragma unroll
+    for (int i = 0; i < STM; ++i)
+#pragma unroll
+      for (int j = 0; j < STN; ++j) acc[i][j] = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (int k = 0; k < N; ++k) {
+      float2 av[STM], bv[STN];
+#pragma unroll
+      for (int i = 0; i < STM; ++i) av[i] = As[k * (SNMAX + 1) + ty + STY * i];
+#pragma unroll
+      for (int j = 0; j < STN; ++j) bv[j] = Bs[k * (SBN + 1) + tx + STX * j];
+#pragma unroll
+      for (int i = 0; i < STM; ++i)
+#pragma unroll
+        for (int j = 0; j < STN; ++j) dcfma(acc[i][j], av[i], bv[j]);
+    }
+
+    const bool tile_done = !a.acc || cur.b == nb - 1;
+    if (a.acc) {
+#pragma unroll
+      for (int i = 0; i < STM; ++i)
+#pragma unroll
+        for (int j = 0; j < STN; ++j) racc[i][j] += acc[i][j].x * acc[i][j].x + acc[i][j].y * acc[i][j].y;
+    }
+    if (tile_done) {
+      // stage the tile in Bs (rows m, columns cc) and store it coalesced
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < STM; ++i)
+#pragma unroll
+        for (int j = 0; j < STN; ++j) {
+          float2 v = acc[i][j];
+          if (a.acc) v = make_float2(racc[i][j], 0.f);
+          Bs[(ty + STY * i) * (SBN + 1) + tx + STX * j] = v;
+        }
+      __syncthreads();
+      for (int idx = tid; idx < N * SBN; idx += 128) {
+        int m, cc;
+        if (contiguous) {
+          cc = idx / N;
+          m = idx - cc * N;
+        } else {
+          m = idx / SBN;
+          cc = idx - m * SBN;
+        }
+        const long long base = cbase[buf][cc];
+        if (base < 0) continue;
+        const float2 v = Bs[m * (SBN + 1) + cc];
+        if (a.acc) {
+          a.out_d[base - (int64_t)cur.b * a.M + (int64_t)m * inner] += v.x;
+        } else {
+          const int64_t addr = base + (int64_t)m * inner;
+          if (a.out_c)
+            a.out_c[addr] = v;
+          else
+            a.out_d[addr] = v.x * v.x + v.y * v.y;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < STM; ++i)
+#pragma unroll
+        for (int j = 0; j < STN; ++j) racc[i][j] = 0.f;
+    }
+  }
+}
+
+}  // namespace
+
+const void* dense_small_func() { return (const void*)dense_small_kernel; }
+size_t dense_small_smem() { return sizeof(float2) * (SNMAX * (SNMAX + 1) + SNMAX * (SBN + 1)); }
+
+cudaError_t launch_dense_small(const DenseArgs& a, int grid, cudaStream_t stream) {
+  dense_small_kernel<<<grid, 128, dense_small_smem(), stream>>>(a);
+  return cudaGetLastError();
+}
+
+int64_t dense_small_tiles(int64_t ncols) { return (ncols + SBN - 1) / SBN; }
+
+const void* dense_kernel_func() { return (const void*)dense_pass_kernel; }
+
+cudaError_t launch_dense(const DenseArgs& a, int grid, cudaStream_t stream) {
+  dense_pass_kernel<<<grid, 256, 0, stream>>>(a);
+  return cudaGetLastError();
+}
+
+int64_t dense_tiles(int N, int64_t ncols) {
+  return (int64_t)((N + DBM - 1) / DBM) * ((ncols + DBN - 1) / DBN);
+}
+
+}  // namespace ffx
+
+namespace ffx {
+
+namespace {
+
+// O[b][nb] = (T e_b)[nb] (the map applied to the unit vectors) -> T[nb][b] = O[b][nb]
+// and T^H[b][nb] = conj(T[nb][b]) = conj(O[b][nb]).
+__global__ void dense_build_kernel(const float2* __restrict__ O, float2* __restrict__ T,
+                                   float2* __restrict__ TH, int N) {
+  const int64_t total = (int64_t)N * N;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = idx / N, nb = idx - b * N;
+    const float2 o = O[idx];
+    T[nb * N + b] = o;
+    TH[idx] = make_float2(o.x, -o.y);
+  }
+}
+
+__global__ void identity_kernel(float2* __restrict__ I, int N) {
+  const int64_t total = (int64_t)N * N;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = idx / N, n = idx - b * N;
+    I[idx] = make_float2(b == n ? 1.f : 0.f, 0.f);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_identity(float2* I, int N, cudaStream_t s) {
+  const int64_t total = (int64_t)N * N;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  identity_kernel<<<blocks, 256, 0, s>>>(I, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense_build(const float2* O, float2* T, float2* TH, int N, cudaStream_t s) {
+  const int64_t total = (int64_t)N * N;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  dense_build_kernel<<<blocks, 256, 0, s>>>(O, T, TH, N);
+  return cudaGetLastError();
+}
+
+}  // namespace ffx

@@ -78,6 +78,33 @@ bool supported_length(int64_t N);
 // Set the calling thread's message for ffx_last_error().
 void set_last_error_message(const char* msg);
 
+// Dense form of one axis pass (ffx_dense.cu): OUT = A * IN along the axis,
+// A = T (forward) or T^H (adjoint), row-major [N][N] complex64.  Not safe in
+// place when N > 64 (row blocks of one column run in different blocks).
+struct DenseArgs {
+  const float2* A;
+  const float2* in;
+  const float* grad;   // non-null: input element is 2 * grad * in
+  float2* out_c;
+  float* out_d;
+  int64_t outer, inner, M, batch;
+  int64_t ncols;       // columns (lines) covered by the tile grid
+  int N;
+  int acc, grad_shared;
+};
+const void* dense_kernel_func();
+cudaError_t launch_dense(const DenseArgs& a, int grid, cudaStream_t stream);
+int64_t dense_tiles(int N, int64_t ncols);
+constexpr int kDenseInPlaceMaxN = 64;
+// lines of at most 64 points: a kernel with T resident in shared memory
+const void* dense_small_func();
+size_t dense_small_smem();
+cudaError_t launch_dense_small(const DenseArgs& a, int grid, cudaStream_t stream);
+int64_t dense_small_tiles(int64_t ncols);
+constexpr int kDenseMaxN = 1024;
+cudaError_t launch_identity(float2* I, int N, cudaStream_t s);
+cudaError_t launch_dense_build(const float2* O, float2* T, float2* TH, int N, cudaStream_t s);
+
 // Plans over many instances (ffx_many.cu).
 struct ManyPlan;
 int many_create(ManyPlan** out, int n, const ffx_instance_desc* d, uint32_t flags, std::string* err);

@@ -22,10 +22,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libffx.so")
 
 FFX_OK, FFX_EINVAL, FFX_ENOMEM, FFX_ECUDA, FFX_EUNSUPPORTED = 0, 1, 2, 3, 4
-FFX_FORM_AUTO, FFX_FORM_PAPER, FFX_FORM_FOLD = 0x0, 0x1, 0x2
+FFX_FORM_AUTO, FFX_FORM_PAPER, FFX_FORM_FOLD, FFX_FORM_DENSE = 0x0, 0x1, 0x2, 0x3
 FFX_ACCUMULATE = 0x10
+FFX_TUNE = 0x20
 
-_FORMS = {"auto": FFX_FORM_AUTO, "paper": FFX_FORM_PAPER, "fold": FFX_FORM_FOLD}
+_FORMS = {"auto": FFX_FORM_AUTO, "paper": FFX_FORM_PAPER, "fold": FFX_FORM_FOLD, "dense": FFX_FORM_DENSE}
+_FORM_NAMES = {FFX_FORM_AUTO: "mixed", FFX_FORM_PAPER: "paper", FFX_FORM_FOLD: "fold", FFX_FORM_DENSE: "dense"}
 
 _lib = None
 
@@ -72,6 +74,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ffx_workspace_bytes.restype = i64
     lib.ffx_plan_form.argtypes = [vp]
     lib.ffx_plan_form.restype = i32
+    lib.ffx_plan_axis_form.argtypes = [vp, i32]
+    lib.ffx_plan_axis_form.restype = i32
     lib.ffx_launches_per_call.argtypes = [vp, i32]
     lib.ffx_launches_per_call.restype = i32
     lib.ffx_plan_pass_order.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
@@ -131,7 +135,7 @@ class Plan:
     """A plan for one geometry (dims, spacing, t, magnification, offsets)."""
 
     def __init__(self, dims, spacing, t, magnification, a=None, abar=None,
-                 form: str = "auto", accumulate: bool = False):
+                 form: str = "auto", accumulate: bool = False, tune: bool = False):
         lib = load_library()
         d = len(dims)
         self.dims = tuple(int(v) for v in dims)
@@ -139,7 +143,7 @@ class Plan:
         self.t = float(t)
         self.magnification = tuple(int(v) for v in magnification)
         self.accumulate = bool(accumulate)
-        flags = _FORMS[form] | (FFX_ACCUMULATE if accumulate else 0)
+        flags = _FORMS[form] | (FFX_ACCUMULATE if accumulate else 0) | (FFX_TUNE if tune else 0)
         arr = lambda ct, v: (ct * d)(*v) if v is not None else None  # noqa: E731
         h = ctypes.c_void_p()
         _check(lib.ffx_plan(ctypes.byref(h), d, arr(ctypes.c_int64, self.dims),
@@ -147,7 +151,8 @@ class Plan:
                             arr(ctypes.c_int32, self.magnification),
                             arr(ctypes.c_double, a), arr(ctypes.c_double, abar), flags), "ffx_plan")
         self._h = h
-        self.form = {FFX_FORM_PAPER: "paper", FFX_FORM_FOLD: "fold"}[lib.ffx_plan_form(h)]
+        self.form = _FORM_NAMES[lib.ffx_plan_form(h)]
+        self.axis_forms = tuple(_FORM_NAMES[lib.ffx_plan_axis_form(h, j)] for j in range(d))
         self.M = 1
         for v in self.dims:
             self.M *= v
@@ -239,7 +244,7 @@ class PlanMany(Plan):
         _check(lib.ffx_plan_many(ctypes.byref(h), n, descs, _FORMS[form]), "ffx_plan_many")
         self._h = h
         self.accumulate = False
-        self.form = {FFX_FORM_PAPER: "paper", FFX_FORM_FOLD: "fold"}[lib.ffx_plan_form(h)]
+        self.form = _FORM_NAMES[lib.ffx_plan_form(h)]
         self.instances = [tuple(tuple(x) if hasattr(x, "__len__") else x for x in spec[:4]) for spec in instances]
         self.points = int(lib.ffx_plan_points(h))
         self.offsets = [int(lib.ffx_plan_many_offset(h, i)) for i in range(n)]
@@ -263,8 +268,9 @@ class PlanMany(Plan):
         return out
 
 
-def ffx_plan(dims, spacing, t, magnification, a=None, abar=None, form="auto", accumulate=False) -> Plan:
-    return Plan(dims, spacing, t, magnification, a, abar, form, accumulate)
+def ffx_plan(dims, spacing, t, magnification, a=None, abar=None, form="auto", accumulate=False,
+             tune=False) -> Plan:
+    return Plan(dims, spacing, t, magnification, a, abar, form, accumulate, tune)
 
 
 def ffx_plan_destroy(plan: Plan):
