@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--workload", default="two_cloud",
                     choices=["two_cloud", "1d", "quasicondensate", "large_two_cloud",
                              "large_quasicondensate", "mixed"])
-    ap.add_argument("--form", default="auto", choices=["auto", "paper", "fold", "dense"])
+    ap.add_argument("--form", default="auto", choices=["auto", "paper", "fold", "dense", "tc"])
     ap.add_argument("--batch", type=int, default=None, help="realizations per step (default: workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -89,7 +89,7 @@ def pass_flops(N: int, lam: int, lines: int, form: str) -> float:
     lg = math.log2(N)
     if form == "paper":
         return lines * lam * (10 * N * lg + 20 * N)
-    if form == "dense":
+    if form in ("dense", "tc"):
         return lines * 8.0 * N * N  # N x N complex matrix times each line
     return lines * (lam * (5 * N * lg + 14 * N) + 5 * N * lg)
 
@@ -188,6 +188,104 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ---------------------------------------------------------------------------
+# comparison baselines (timed only; never on the product path): the same
+# per-axis recipe of eq. FF with every fine index q batched into one library
+# FFT call per axis -- cuFFT through torch.fft on the GPU, pocketfft through
+# scipy.fft on the host cores (FFTW is not installed here)
+# ---------------------------------------------------------------------------
+
+def recipe_tables(N, lam, dx, t):
+    """Phase factors of eqs. presA, presB, presf (paper form) for one axis,
+    default offsets (a = -L/2, abar centring the magnified box), FP64."""
+    L = N * dx
+    s = -(((lam - 1) * N) // 2)
+    tau = math.pi * t / (L * L)
+    q = np.arange(lam, dtype=np.float64)[:, None]
+    n = np.arange(N, dtype=np.float64)[None, :]
+    m = np.arange(N)
+    l = np.where(2 * m < N, m, m - N).astype(np.float64)[None, :]
+    P = np.exp(-2j * np.pi * np.mod(q * n, lam * N) / (lam * N))
+    K = np.exp(2j * np.pi * (l * s / N - tau * l * l - (2 * tau / lam) * l * q))
+    F = np.exp(2j * np.pi * (q * s / (lam * N) + q * n / N - tau * q * q / lam ** 2)) / lam
+    nii = np.mod(lam * np.arange(N), N)
+    return P, K, F, nii
+
+
+def recipe_axis_torch(torch, x, axis, tabs):
+    """One axis of the paper-form recipe with torch.fft (cuFFT) on a [B, ...] field."""
+    P, K, F, nii = tabs
+    x = x.movedim(axis, -1)
+    y = torch.fft.fft(x.unsqueeze(0) * P.view((P.shape[0],) + (1,) * (x.dim() - 1) + (P.shape[1],)), dim=-1)
+    y = torch.fft.ifft(y * K.view((K.shape[0],) + (1,) * (x.dim() - 1) + (K.shape[1],)), dim=-1)
+    y = (y[..., nii] * F.view((F.shape[0],) + (1,) * (x.dim() - 1) + (F.shape[1],))).sum(0)
+    return y.movedim(-1, axis)
+
+
+def cufft_baseline(torch, w, dev, steps=20):
+    """Realizations/s of the same recipe on cuFFT (torch.fft), complex64."""
+    tabs = []
+    for N, lam, dx in zip(w.dims, w.lam, w.dx):
+        P, K, F, nii = recipe_tables(N, lam, dx, w.t)
+        tabs.append((torch.from_numpy(P.astype(np.complex64)).to(dev),
+                     torch.from_numpy(K.astype(np.complex64)).to(dev),
+                     torch.from_numpy(F.astype(np.complex64)).to(dev), torch.from_numpy(nii).to(dev)))
+    x = torch.from_numpy(w.batch_array(w.batch)).to(dev)
+
+    def run():
+        y = x
+        for j in range(len(w.dims)):
+            y = recipe_axis_torch(torch, y, 1 + j, tabs[j])
+        return (y.abs() ** 2)
+
+    try:
+        out = run()
+        for _ in range(2):
+            run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        return {"value": w.batch / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                "kind": "same per-axis recipe (paper form, all q batched) on cuFFT via torch.fft, complex64",
+                "result": out}
+    except RuntimeError as exc:  # e.g. out of memory for lam * M intermediates
+        return {"value": None, "unit": UNIT, "kind": "cuFFT recipe", "error": str(exc)[:200]}
+
+
+def scipy_baseline(w, budget_s=8.0, dtype=np.complex64):
+    """Realizations/s of the same recipe with scipy.fft (pocketfft) on all host cores."""
+    import scipy.fft as sfft
+    workers = os.cpu_count()
+    tabs = [recipe_tables(N, lam, dx, w.t) for N, lam, dx in zip(w.dims, w.lam, w.dx)]
+    tabs = [(P.astype(dtype), K.astype(dtype), F.astype(dtype), nii) for P, K, F, nii in tabs]
+    x0 = w.realization(0).astype(dtype)[None]
+
+    def run(x):
+        for j, (P, K, F, nii) in enumerate(tabs):
+            y = np.moveaxis(x, 1 + j, -1)
+            sh = (P.shape[0],) + (1,) * (y.ndim - 1) + (P.shape[1],)
+            y = sfft.fft(y[None] * P.reshape(sh), axis=-1, workers=workers)
+            y = sfft.ifft(y * K.reshape(sh), axis=-1, workers=workers)
+            y = (y[..., nii] * F.reshape(sh)).sum(0)
+            x = np.moveaxis(y, -1, 1 + j)
+        return np.abs(x) ** 2
+
+    run(x0)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s or n == 0:
+        run(x0)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": workers,
+            "kind": f"same per-axis recipe on scipy.fft (pocketfft), {np.dtype(dtype).name}",
+            "sample": f"{n} realizations in {dt:.1f} s"}
 
 
 def load_traffic(kernel_key: str):
@@ -468,6 +566,18 @@ def run_ffx(args):
         e2e_ms = float(tt.item())
     e2e_value = e2e_steps * B_ * world / (e2e_ms * 1e-3)
 
+    cufft = scipy64 = scipy32 = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cufft = cufft_baseline(torch, w, dev)
+        res = cufft.pop("result", None)
+        if res is not None:
+            ours = ffx.ffx_expand(plan, pool_in[0].contiguous() if B_ == 1 else
+                                  torch.from_numpy(w.batch_array(B_)).to(dev))
+            cufft["max_rel_diff_vs_ffx"] = float(((res - ours).norm() / ours.norm()).item())
+        if M * B_ <= 1 << 22:
+            scipy32 = scipy_baseline(w, dtype=np.complex64)
+            scipy64 = scipy_baseline(w, dtype=np.complex128)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, n, dt = cpu_oracle_rate(w)
@@ -504,6 +614,8 @@ def run_ffx(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B_ * M * 8,
                     "d2h_bytes_per_step": B_ * M * 4},
             "cpu_baseline": cpu,
+            "comparisons": {"cufft_recipe": cufft, "cpu_fft_recipe_c64": scipy32,
+                            "cpu_fft_recipe_c128": scipy64},
         }
         print(json.dumps(line), flush=True)
     plan.close()

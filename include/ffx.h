@@ -71,6 +71,10 @@ extern "C" {
 #define FFX_FORM_PAPER  0x1u
 #define FFX_FORM_FOLD   0x2u
 #define FFX_FORM_DENSE  0x3u
+/* FFX_FORM_TC: the dense form on the tensor cores (tcgen05, TF32 operands
+ *   split into head and tail, three products accumulated in FP32) for lines of
+ *   64 points; other lengths use FFX_FORM_DENSE. */
+#define FFX_FORM_TC     0x4u
 #define FFX_FORM_MASK   0xFu
 /* With FFX_FORM_AUTO: time every form of every axis at plan time (a few ms,
  * on a batch of one, in temporary workspace), use the fastest, and append the
@@ -246,7 +250,7 @@ int ffx_supported_length(int64_t n);
 /* Bytes of plan-owned workspace a call with this batch uses. */
 int64_t ffx_workspace_bytes(ffx_plan_t plan, int64_t batch);
 
-/* The form every axis runs (FFX_FORM_PAPER, _FOLD or _DENSE), or
+/* The form every axis runs (FFX_FORM_PAPER, _FOLD, _DENSE or _TC), or
  * FFX_FORM_AUTO if the axes differ. */
 int ffx_plan_form(ffx_plan_t plan);
 
@@ -277,6 +281,11 @@ int ffx_plan_trace(ffx_plan_t plan, void* const* events, int64_t n_events);
 
 /* Number of events recorded since the last ffx_plan_trace call. */
 int64_t ffx_plan_trace_count(ffx_plan_t plan);
+
+/* Waits that ran out inside the plan's kernels so far (tensor-core passes
+ * bound every wait on the tensor cores and count a timeout here instead of
+ * hanging); 0 when all is well.  Synchronizes with the device. */
+int ffx_plan_device_errors(ffx_plan_t plan);
 
 /* Static strings for return codes; never NULL. */
 const char* ffx_error_string(int code);

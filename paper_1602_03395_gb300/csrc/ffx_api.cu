@@ -116,6 +116,7 @@ struct Axis {
   float2* T = nullptr;   // dense map [N][N] (N <= kDenseMaxN)
   float2* TH = nullptr;  // its adjoint
   int grid_dense = 0, grid_dense_small = 0;
+  float* tc_a[4] = {nullptr, nullptr, nullptr, nullptr};  // split A: fwd hi, fwd lo, adj hi, adj lo
 };
 
 }  // namespace
@@ -139,6 +140,8 @@ struct ffx_plan_s {
   int order[3] = {0, 1, 2};  // forward pass order
   void* tables = nullptr;
   void* dense_mem = nullptr;
+  void* tc_mem = nullptr;    // split tensor-core operands + device error counter
+  int* dev_err = nullptr;
   void* ws[2] = {nullptr, nullptr};  // workspace buffers (grown on demand)
   size_t ws_bytes[2] = {0, 0};
   ManyPlan* many = nullptr;       // set for plans over many instances
@@ -221,6 +224,8 @@ int ensure_ws(ffx_plan_s* p, int which, int64_t batch) {
 
 bool inplace_ok(const Axis& ax) { return !(ax.form == FFX_FORM_DENSE && ax.N > kDenseInPlaceMaxN); }
 
+bool tc_capable(const Axis& ax) { return ax.N == kTcN && ax.tc_a[0] != nullptr; }
+
 // Launch one pass of axis j (forward or adjoint) with the axis's form.
 int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* grad, int grad_shared,
              float2* out_c, float* out_d, int acc, int64_t batch, cudaStream_t stream) {
@@ -237,7 +242,27 @@ int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* 
     cudaEventRecordWithFlags((cudaEvent_t)p->trace[p->trace_i], stream, rec_flags);
   }
   cudaError_t e;
-  if (ax.form == FFX_FORM_DENSE) {
+  if (ax.form == FFX_FORM_TC) {
+    DenseArgs d;
+    std::memset(&d, 0, sizeof(d));
+    d.in = in;
+    d.grad = grad;
+    d.grad_shared = grad_shared;
+    d.out_c = out_c;
+    d.out_d = out_d;
+    d.outer = outer;
+    d.inner = inner;
+    d.M = p->M;
+    d.batch = batch;
+    d.acc = acc;
+    d.ncols = acc ? outer * inner : batch * outer * inner;
+    d.N = ax.N;
+    int64_t grid = dense_tc_tiles(d.ncols);
+    if (grid > p->sms) grid = p->sms;
+    if (grid < 1) grid = 1;
+    e = launch_dense_tc(d, adjoint ? ax.tc_a[2] : ax.tc_a[0], adjoint ? ax.tc_a[3] : ax.tc_a[1], p->dev_err,
+                        (int)grid, stream);
+  } else if (ax.form == FFX_FORM_DENSE) {
     DenseArgs d;
     std::memset(&d, 0, sizeof(d));
     d.A = adjoint ? ax.TH : ax.T;
@@ -514,7 +539,7 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
   const uint32_t known = FFX_FORM_MASK | FFX_ACCUMULATE | FFX_TUNE;
   if (flags & ~known) return fail(FFX_EINVAL, "unknown flag bits 0x%x", flags & ~known);
   const uint32_t form = flags & FFX_FORM_MASK;
-  if (form > FFX_FORM_DENSE) return fail(FFX_EINVAL, "unknown form %u", form);
+  if (form > FFX_FORM_TC) return fail(FFX_EINVAL, "unknown form %u", form);
   int64_t M = 1;
   for (int j = 0; j < ndim; ++j) {
     if (dims[j] < 1) return fail(FFX_EINVAL, "dims[%d] = %lld < 1", j, (long long)dims[j]);
@@ -529,7 +554,7 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
       return fail(FFX_EINVAL, "offsets must be finite");
     if (!supported_length(dims[j]))
       return fail(FFX_EUNSUPPORTED, "no line kernel for length %lld (axis %d)", (long long)dims[j], j);
-    if (form == FFX_FORM_DENSE && dims[j] > kDenseMaxN)
+    if ((form == FFX_FORM_DENSE || form == FFX_FORM_TC) && dims[j] > kDenseMaxN)
       return fail(FFX_EUNSUPPORTED, "the dense form takes lines up to %d points (axis %d has %lld)",
                   kDenseMaxN, j, (long long)dims[j]);
     M *= dims[j];
@@ -657,7 +682,7 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
     size_t dbytes = 0, scratch = 0;
     for (int j = 0; j < ndim; ++j) {
       const size_t N = (size_t)dims[j];
-      if (N <= (size_t)kDenseMaxN && (form == FFX_FORM_AUTO || form == FFX_FORM_DENSE)) {
+      if (N <= (size_t)kDenseMaxN && (form == FFX_FORM_AUTO || form == FFX_FORM_DENSE || form == FFX_FORM_TC)) {
         dbytes += 2 * N * N * sizeof(float2);
         scratch = std::max(scratch, 2 * N * N * sizeof(float2));
       }
@@ -686,6 +711,43 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
     }
   }
 
+  // split tensor-core operands for 64-point axes, and the device error counter
+  if (rc == FFX_OK) {
+    size_t tbytes = 256;
+    for (int j = 0; j < ndim; ++j)
+      if (p->axis[j].N == kTcN && p->axis[j].T && (form == FFX_FORM_AUTO || form == FFX_FORM_TC))
+        tbytes += 4 * dense_tc_a_floats() * sizeof(float);
+    e = cudaMalloc(&p->tc_mem, tbytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      rc = fail(FFX_ENOMEM, "tensor-core operands: %s", cudaGetErrorString(e));
+    } else {
+      p->dev_err = (int*)p->tc_mem;
+      cudaMemsetAsync(p->dev_err, 0, 256, s);
+      float* tcur = (float*)((char*)p->tc_mem + 256);
+      for (int j = 0; j < ndim && rc == FFX_OK; ++j) {
+        Axis& ax = p->axis[j];
+        if (!(ax.N == kTcN && ax.T && (form == FFX_FORM_AUTO || form == FFX_FORM_TC))) continue;
+        for (int q = 0; q < 4; ++q) {
+          ax.tc_a[q] = tcur;
+          tcur += dense_tc_a_floats();
+        }
+        e = launch_tc_build_a(ax.T, ax.tc_a[0], ax.tc_a[1], s);
+        if (e == cudaSuccess) e = launch_tc_build_a(ax.TH, ax.tc_a[2], ax.tc_a[3], s);
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(dense_tc_func(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)dense_tc_smem());
+        if (e != cudaSuccess) rc = cuda_fail(e, "tensor-core operands");
+      }
+      if (rc == FFX_OK) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "tensor-core operands");
+      }
+    }
+  }
+  for (int j = 0; j < ndim && rc == FFX_OK; ++j)
+    if (form == FFX_FORM_TC && !tc_capable(p->axis[j])) p->axis[j].form = FFX_FORM_DENSE;
+
   // per-axis form
   if (rc == FFX_OK) {
     char dev[256] = "unknown";
@@ -695,7 +757,7 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
     for (int j = 0; j < ndim && rc == FFX_OK; ++j) {
       Axis& ax = p->axis[j];
       if (form != FFX_FORM_AUTO) {
-        ax.form = (int)form;
+        ax.form = (form == FFX_FORM_TC && !tc_capable(ax)) ? FFX_FORM_DENSE : (int)form;
         continue;
       }
       int64_t outer, inner;
@@ -739,6 +801,7 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
     for (int w = 0; w < 2; ++w)
       if (p->ws[w]) cudaFree(p->ws[w]);
     if (p->dense_mem) cudaFree(p->dense_mem);
+    if (p->tc_mem) cudaFree(p->tc_mem);
     cudaFree(p->tables);
     delete p;
     return rc;
@@ -786,6 +849,7 @@ int ffx_plan_destroy(ffx_plan_t p) {
   for (int w = 0; w < 2; ++w)
     if (p->ws[w]) cudaFree(p->ws[w]);
   if (p->dense_mem) cudaFree(p->dense_mem);
+  if (p->tc_mem) cudaFree(p->tc_mem);
   if (p->tables) cudaFree(p->tables);
   delete p;
   return FFX_OK;
@@ -820,6 +884,14 @@ int ffx_plan_trace(ffx_plan_t p, void* const* events, int64_t n_events) {
 }
 
 int64_t ffx_plan_trace_count(ffx_plan_t p) { return p ? p->trace_i : -1; }
+
+int ffx_plan_device_errors(ffx_plan_t p) {
+  if (!p) return -1;
+  if (!p->dev_err) return 0;
+  int h = 0;
+  if (cudaMemcpy(&h, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  return h;
+}
 
 int64_t ffx_workspace_bytes(ffx_plan_t p, int64_t batch) {
   if (!p || batch < 0) return -1;

@@ -102,6 +102,15 @@ size_t dense_small_smem();
 cudaError_t launch_dense_small(const DenseArgs& a, int grid, cudaStream_t stream);
 int64_t dense_small_tiles(int64_t ncols);
 constexpr int kDenseMaxN = 1024;
+// dense form of 64-point lines on the tensor cores (ffx_tc.cu), split TF32
+constexpr int kTcN = 64;
+size_t dense_tc_smem();
+const void* dense_tc_func();
+size_t dense_tc_a_floats();
+cudaError_t launch_dense_tc(const DenseArgs& a, const float* Ahi, const float* Alo, int* err, int grid,
+                            cudaStream_t stream);
+int64_t dense_tc_tiles(int64_t ncols);
+cudaError_t launch_tc_build_a(const float2* T, float* Ahi, float* Alo, cudaStream_t s);
 cudaError_t launch_identity(float2* I, int N, cudaStream_t s);
 cudaError_t launch_dense_build(const float2* O, float2* T, float2* TH, int N, cudaStream_t s);
 

@@ -22,12 +22,14 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libffx.so")
 
 FFX_OK, FFX_EINVAL, FFX_ENOMEM, FFX_ECUDA, FFX_EUNSUPPORTED = 0, 1, 2, 3, 4
-FFX_FORM_AUTO, FFX_FORM_PAPER, FFX_FORM_FOLD, FFX_FORM_DENSE = 0x0, 0x1, 0x2, 0x3
+FFX_FORM_AUTO, FFX_FORM_PAPER, FFX_FORM_FOLD, FFX_FORM_DENSE, FFX_FORM_TC = 0x0, 0x1, 0x2, 0x3, 0x4
 FFX_ACCUMULATE = 0x10
 FFX_TUNE = 0x20
 
-_FORMS = {"auto": FFX_FORM_AUTO, "paper": FFX_FORM_PAPER, "fold": FFX_FORM_FOLD, "dense": FFX_FORM_DENSE}
-_FORM_NAMES = {FFX_FORM_AUTO: "mixed", FFX_FORM_PAPER: "paper", FFX_FORM_FOLD: "fold", FFX_FORM_DENSE: "dense"}
+_FORMS = {"auto": FFX_FORM_AUTO, "paper": FFX_FORM_PAPER, "fold": FFX_FORM_FOLD, "dense": FFX_FORM_DENSE,
+          "tc": FFX_FORM_TC}
+_FORM_NAMES = {FFX_FORM_AUTO: "mixed", FFX_FORM_PAPER: "paper", FFX_FORM_FOLD: "fold", FFX_FORM_DENSE: "dense",
+               FFX_FORM_TC: "tc"}
 
 _lib = None
 
@@ -84,6 +86,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ffx_plan_trace.restype = i32
     lib.ffx_plan_trace_count.argtypes = [vp]
     lib.ffx_plan_trace_count.restype = i64
+    lib.ffx_plan_device_errors.argtypes = [vp]
+    lib.ffx_plan_device_errors.restype = i32
     lib.ffx_expand_noalloc.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(dbl), dbl,
                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(dbl),
                                        ctypes.POINTER(dbl), vp, i64, vp, vp]
@@ -213,6 +217,10 @@ class Plan:
 
     def trace_count(self) -> int:
         return int(load_library().ffx_plan_trace_count(self.handle))
+
+    def device_errors(self) -> int:
+        """Bounded waits that ran out in this plan's kernels (0 when all is well)."""
+        return int(load_library().ffx_plan_device_errors(self.handle))
 
 
 class PlanMany(Plan):
