@@ -117,6 +117,7 @@ struct Axis {
   float2* TH = nullptr;  // its adjoint
   int grid_dense = 0, grid_dense_small = 0;
   float* tc_a[4] = {nullptr, nullptr, nullptr, nullptr};  // split A: fwd hi, fwd lo, adj hi, adj lo
+  float2* img[2] = {nullptr, nullptr};                      // lines <= 64: shared-memory images of T, T^H
 };
 
 }  // namespace
@@ -278,6 +279,8 @@ int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* 
     d.acc = acc;
     d.ncols = acc ? outer * inner : batch * outer * inner;
     d.N = ax.N;
+    d.Aimg = adjoint ? ax.img[1] : ax.img[0];
+    d.err = p->dev_err;
     if (ax.N <= kDenseInPlaceMaxN) {
       int64_t grid = dense_small_tiles(d.ncols);
       if (grid > ax.grid_dense_small) grid = ax.grid_dense_small;
@@ -684,6 +687,7 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
       const size_t N = (size_t)dims[j];
       if (N <= (size_t)kDenseMaxN && (form == FFX_FORM_AUTO || form == FFX_FORM_DENSE || form == FFX_FORM_TC)) {
         dbytes += 2 * N * N * sizeof(float2);
+        if (N <= (size_t)kDenseInPlaceMaxN) dbytes += 2 * dense_small_image_floats2((int)N) * sizeof(float2);
         scratch = std::max(scratch, 2 * N * N * sizeof(float2));
       }
     }
@@ -701,6 +705,16 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
           if (N > (size_t)kDenseMaxN) continue;
           rc = build_dense(p, j, dcur, dcur + N * N, (float2*)tmp, s);
           dcur += 2 * N * N;
+          if (rc == FFX_OK && N <= (size_t)kDenseInPlaceMaxN) {
+            Axis& ax = p->axis[j];
+            const size_t isz = dense_small_image_floats2((int)N);
+            ax.img[0] = dcur;
+            ax.img[1] = dcur + isz;
+            dcur += 2 * isz;
+            e = launch_dense_small_image(ax.T, ax.img[0], (int)N, s);
+            if (e == cudaSuccess) e = launch_dense_small_image(ax.TH, ax.img[1], (int)N, s);
+            if (e != cudaSuccess) rc = cuda_fail(e, "dense image");
+          }
         }
         if (rc == FFX_OK) {
           e = cudaStreamSynchronize(s);

@@ -215,12 +215,17 @@ __device__ __forceinline__ void small_bases(const DenseArgs& a, int64_t cbk, int
   cbr[t] = br;
 }
 
+__device__ __forceinline__ uint32_t dsm_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
 __global__ void __launch_bounds__(128) dense_small_kernel(const DenseArgs a) {
   extern __shared__ __align__(16) unsigned char dsm[];
-  float2* As = reinterpret_cast<float2*>(dsm);                   // [SNMAX][SNMAX + 1], As[k][m] = A[m][k]
-  float2* Bs = As + SNMAX * (SNMAX + 1);                         // [SNMAX][SBN + 1]
+  float2* As = reinterpret_cast<float2*>(dsm);     // [SNMAX][SNMAX + 1], As[k][m] = A[m][k]
+  float2* Bs = As + SNMAX * (SNMAX + 1);           // [2][SNMAX][SBN + 1]
+  constexpr int BSTRIDE = SNMAX * (SBN + 1);
   __shared__ long long cbase[2][SBN];
   __shared__ int cbr[2][SBN];
+  __shared__ __align__(8) uint64_t abar;
+  __shared__ int s_abort;
 
   const int N = a.N;
   const int tid = threadIdx.x;
@@ -234,9 +239,19 @@ __global__ void __launch_bounds__(128) dense_small_kernel(const DenseArgs a) {
   const int64_t n_items = (blockIdx.x < col_tiles) ? my_tiles * nb : 0;
   if (n_items == 0) return;
 
-  for (int idx = tid; idx < N * N; idx += 128) {
-    const int m = idx / N, k = idx - m * N;
-    As[k * (SNMAX + 1) + m] = __ldg(a.A + idx);
+  // T, stored in global memory as the image of As, arrives in one bulk (TMA) copy
+  const uint32_t abytes = (uint32_t)(N * (SNMAX + 1) * sizeof(float2));
+  if (tid == 0) {
+    s_abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(dsm_u32(&abar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(dsm_u32(&abar)), "r"(abytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dsm_u32(As)),
+        "l"(a.Aimg), "r"(abytes), "r"(dsm_u32(&abar))
+        : "memory");
   }
 
   auto item_at = [&](int64_t it) {
@@ -245,10 +260,11 @@ __global__ void __launch_bounds__(128) dense_small_kernel(const DenseArgs a) {
     r.b = (int)(it % nb);
     return r;
   };
-  auto load_item = [&](int buf, float2 (&pre)[SLOADS]) {
-#pragma unroll
-    for (int l = 0; l < SLOADS; ++l) {
-      const int idx = tid + l * 128;
+  // input tile of an item: asynchronous 8-byte copies straight into Bs[buf][k][cc]
+  // (with the ensemble-gradient factor the values go through registers)
+  auto issue_item = [&](int buf) {
+    float2* dst = Bs + buf * BSTRIDE;
+    for (int idx = tid; idx < SNMAX * SBN; idx += 128) {
       int k, cc;
       if (contiguous) {
         cc = idx / SNMAX;
@@ -257,29 +273,48 @@ __global__ void __launch_bounds__(128) dense_small_kernel(const DenseArgs a) {
         k = idx / SBN;
         cc = idx - k * SBN;
       }
-      float2 v = make_float2(0.f, 0.f);
+      if (k >= N) continue;
+      float2* d = dst + k * (SBN + 1) + cc;
       const long long base = cbase[buf][cc];
-      if (k < N && base >= 0) {
-        const int64_t addr = base + (int64_t)k * inner;
-        v = a.in[addr];  // plain load: passes may run in place
-        if (a.grad) {
-          const int64_t gaddr = a.grad_shared ? addr - (int64_t)cbr[buf][cc] * a.M : addr;
-          const float gr = 2.f * __ldg(a.grad + gaddr);
-          v.x *= gr;
-          v.y *= gr;
-        }
+      if (base < 0) {
+        *d = make_float2(0.f, 0.f);
+        continue;
       }
-      pre[l] = v;
+      const int64_t addr = base + (int64_t)k * inner;
+      if (a.grad) {
+        float2 v = a.in[addr];
+        const int64_t gaddr = a.grad_shared ? addr - (int64_t)cbr[buf][cc] * a.M : addr;
+        const float gr = 2.f * __ldg(a.grad + gaddr);
+        v.x *= gr;
+        v.y *= gr;
+        *d = v;
+      } else {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dsm_u32(d)), "l"(a.in + addr) : "memory");
+      }
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
   };
 
-  float2 pre[SLOADS];
   if (tid < SBN) {
     const SmallItem i0 = item_at(0);
     small_bases(a, i0.cbk, i0.b, cbase[0], cbr[0], tid);
   }
   __syncthreads();
-  load_item(0, pre);
+  issue_item(0);
+  // every thread waits for T (bounded; a timeout abandons the launch)
+  {
+    bool done = false;
+    for (long long i = 0; i < (1ll << 22) && !done; ++i) {
+      uint32_t d;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(d)
+          : "r"(dsm_u32(&abar))
+          : "memory");
+      done = d != 0;
+    }
+    if (!done) s_abort = 1;
+  }
 
   float racc[STM][STN];
 #pragma unroll
@@ -290,26 +325,22 @@ __global__ void __launch_bounds__(128) dense_small_kernel(const DenseArgs a) {
   for (int64_t it = 0; it < n_items; ++it) {
     const int buf = (int)(it & 1);
     const SmallItem cur = item_at(it);
-    __syncthreads();  // Bs free (previous tile multiplied and stored)
-#pragma unroll
-    for (int l = 0; l < SLOADS; ++l) {
-      const int idx = tid + l * 128;
-      int k, cc;
-      if (contiguous) {
-        cc = idx / SNMAX;
-        k = idx - cc * SNMAX;
-      } else {
-        k = idx / SBN;
-        cc = idx - k * SBN;
+    __syncthreads();  // previous epilogue done with Bs[buf ^ 1] and cbase[buf ^ 1]
+    if (s_abort) break;
+    const bool more = it + 1 < n_items;
+    if (more) {
+      if (tid < SBN) {
+        const SmallItem nx = item_at(it + 1);
+        small_bases(a, nx.cbk, nx.b, cbase[buf ^ 1], cbr[buf ^ 1], tid);
       }
-      Bs[k * (SBN + 1) + cc] = pre[l];
+      __syncthreads();
+      issue_item(buf ^ 1);  // in flight during this item's product
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
-    if (it + 1 < n_items && tid < SBN) {
-      const SmallItem nx = item_at(it + 1);
-      small_bases(a, nx.cbk, nx.b, cbase[buf ^ 1], cbr[buf ^ 1], tid);
-    }
-    __syncthreads();
-    if (it + 1 < n_items) load_item(buf ^ 1, pre);  // in flight during the product
+    __syncthreads();  // this item's tile is in Bs[buf]
+    const float2* B = Bs + buf * BSTRIDE;
 
     float2 acc[STM][STN];
 #pragma unroll
@@ -322,7 +353,7 @@ __global__ void __launch_bounds__(128) dense_small_kernel(const DenseArgs a) {
 #pragma unroll
       for (int i = 0; i < STM; ++i) av[i] = As[k * (SNMAX + 1) + ty + STY * i];
 #pragma unroll
-      for (int j = 0; j < STN; ++j) bv[j] = Bs[k * (SBN + 1) + tx + STX * j];
+      for (int j = 0; j < STN; ++j) bv[j] = B[k * (SBN + 1) + tx + STX * j];
 #pragma unroll
       for (int i = 0; i < STM; ++i)
 #pragma unroll
@@ -337,7 +368,8 @@ __global__ void __launch_bounds__(128) dense_small_kernel(const DenseArgs a) {
         for (int j = 0; j < STN; ++j) racc[i][j] += acc[i][j].x * acc[i][j].x + acc[i][j].y * acc[i][j].y;
     }
     if (tile_done) {
-      // stage the tile in Bs (rows m, columns cc) and store it coalesced
+      // stage the tile in Bs[buf] (rows m, columns cc) and store it coalesced
+      float2* S = Bs + buf * BSTRIDE;
       __syncthreads();
 #pragma unroll
       for (int i = 0; i < STM; ++i)
@@ -345,7 +377,7 @@ __global__ void __launch_bounds__(128) dense_small_kernel(const DenseArgs a) {
         for (int j = 0; j < STN; ++j) {
           float2 v = acc[i][j];
           if (a.acc) v = make_float2(racc[i][j], 0.f);
-          Bs[(ty + STY * i) * (SBN + 1) + tx + STX * j] = v;
+          S[(ty + STY * i) * (SBN + 1) + tx + STX * j] = v;
         }
       __syncthreads();
       for (int idx = tid; idx < N * SBN; idx += 128) {
@@ -359,7 +391,7 @@ __global__ void __launch_bounds__(128) dense_small_kernel(const DenseArgs a) {
         }
         const long long base = cbase[buf][cc];
         if (base < 0) continue;
-        const float2 v = Bs[m * (SBN + 1) + cc];
+        const float2 v = S[m * (SBN + 1) + cc];
         if (a.acc) {
           a.out_d[base - (int64_t)cur.b * a.M + (int64_t)m * inner] += v.x;
         } else {
@@ -376,12 +408,27 @@ __global__ void __launch_bounds__(128) dense_small_kernel(const DenseArgs a) {
         for (int j = 0; j < STN; ++j) racc[i][j] = 0.f;
     }
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if (tid == 0 && s_abort && a.err) atomicAdd(a.err, 1);
+}
+
+// T's image for the kernel above: img[k][m] = T[m][k], rows of SNMAX + 1.
+__global__ void dense_small_image_kernel(const float2* __restrict__ T, float2* __restrict__ img, int N) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N * (SNMAX + 1); idx += gridDim.x * blockDim.x) {
+    const int k = idx / (SNMAX + 1), m = idx - k * (SNMAX + 1);
+    img[idx] = (m < N) ? T[m * N + k] : make_float2(0.f, 0.f);
+  }
 }
 
 }  // namespace
 
 const void* dense_small_func() { return (const void*)dense_small_kernel; }
-size_t dense_small_smem() { return sizeof(float2) * (SNMAX * (SNMAX + 1) + SNMAX * (SBN + 1)); }
+size_t dense_small_smem() { return sizeof(float2) * (SNMAX * (SNMAX + 1) + 2 * SNMAX * (SBN + 1)); }
+size_t dense_small_image_floats2(int N) { return (size_t)N * (SNMAX + 1); }
+cudaError_t launch_dense_small_image(const float2* T, float2* img, int N, cudaStream_t s) {
+  dense_small_image_kernel<<<16, 256, 0, s>>>(T, img, N);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_dense_small(const DenseArgs& a, int grid, cudaStream_t stream) {
   dense_small_kernel<<<grid, 128, dense_small_smem(), stream>>>(a);

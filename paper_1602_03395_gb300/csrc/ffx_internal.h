@@ -83,6 +83,8 @@ void set_last_error_message(const char* msg);
 // place when N > 64 (row blocks of one column run in different blocks).
 struct DenseArgs {
   const float2* A;
+  const float2* Aimg;  // lines <= 64: A's shared-memory image (see ffx_dense.cu)
+  int* err;            // device error counter (bounded waits)
   const float2* in;
   const float* grad;   // non-null: input element is 2 * grad * in
   float2* out_c;
@@ -101,6 +103,8 @@ const void* dense_small_func();
 size_t dense_small_smem();
 cudaError_t launch_dense_small(const DenseArgs& a, int grid, cudaStream_t stream);
 int64_t dense_small_tiles(int64_t ncols);
+size_t dense_small_image_floats2(int N);
+cudaError_t launch_dense_small_image(const float2* T, float2* img, int N, cudaStream_t s);
 constexpr int kDenseMaxN = 1024;
 // dense form of 64-point lines on the tensor cores (ffx_tc.cu), split TF32
 constexpr int kTcN = 64;
