@@ -530,7 +530,7 @@ def run_ffx(args):
     alu_peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
     achieved = flops / (mean_ms[dom] * 1e-3) / 1e12
     kernel_key = f"pass_{axis_form}_N{N}_lam{lam}_{args.workload}"
-    traffic = load_traffic(kernel_key)
+    traffic = load_traffic(f"{axis_form}_N{N}")
     # HBM view of the same launch: it reads and writes the batch once (complex64,
     # the last pass writes float32 densities)
     last = dom == launches - 1
