@@ -63,17 +63,19 @@ extern "C" {
  *   built at plan time by running the fold form on the N unit vectors, then
  *   applied as a batched complex matrix product (8*M_j flops per point instead
  *   of lam_j*(5 log2 M_j + 14)); lines up to 1024 points.
- * 0 (FFX_FORM_AUTO) chooses per axis: a tuned choice from the cache named by
- *   the environment variable FFX_TUNE_CACHE if it holds one for this device
- *   and geometry, else measured at plan time with FFX_TUNE, else a fixed cost
- *   model (dense when 8 M_j is well below the FFT form's work). */
+ * 0 (FFX_FORM_AUTO) chooses per axis among these four: a tuned choice from
+ *   the cache named by the environment variable FFX_TUNE_CACHE if it holds
+ *   one for this device and geometry, else measured at plan time with
+ *   FFX_TUNE, else a fixed cost model (dense or tensor-core when 8 M_j is well
+ *   below the FFT form's work). */
 #define FFX_FORM_AUTO   0x0u
 #define FFX_FORM_PAPER  0x1u
 #define FFX_FORM_FOLD   0x2u
 #define FFX_FORM_DENSE  0x3u
 /* FFX_FORM_TC: the dense form on the tensor cores (tcgen05, TF32 operands
- *   split into head and tail, three products accumulated in FP32) for lines of
- *   64 points; other lengths use FFX_FORM_DENSE. */
+ *   split into head and tail, three products accumulated in FP32) for axes of
+ *   N points with N a multiple of 64 up to 1024; other lengths, and buffers
+ *   not aligned to 16 bytes, use FFX_FORM_DENSE. */
 #define FFX_FORM_TC     0x4u
 #define FFX_FORM_MASK   0xFu
 /* With FFX_FORM_AUTO: time every form of every axis at plan time (a few ms,

@@ -116,7 +116,7 @@ struct Axis {
   float2* T = nullptr;   // dense map [N][N] (N <= kDenseMaxN)
   float2* TH = nullptr;  // its adjoint
   int grid_dense = 0, grid_dense_small = 0;
-  float* tc_a[4] = {nullptr, nullptr, nullptr, nullptr};  // split A: fwd hi, fwd lo, adj hi, adj lo
+  unsigned char* tc_t[2] = {nullptr, nullptr};  // split tensor-core operands of T, T^H (ffx_tc.cu)
   float2* img[2] = {nullptr, nullptr};                      // lines <= 64: shared-memory images of T, T^H
 };
 
@@ -223,9 +223,16 @@ int ensure_ws(ffx_plan_s* p, int which, int64_t batch) {
   return FFX_OK;
 }
 
-bool inplace_ok(const Axis& ax) { return !(ax.form == FFX_FORM_DENSE && ax.N > kDenseInPlaceMaxN); }
+bool inplace_ok(const Axis& ax) {
+  return !((ax.form == FFX_FORM_DENSE || ax.form == FFX_FORM_TC) && ax.N > kDenseInPlaceMaxN);
+}
 
-bool tc_capable(const Axis& ax) { return ax.N == kTcN && ax.tc_a[0] != nullptr; }
+bool tc_capable(const Axis& ax) { return dense_tc_supported(ax.N) && ax.tc_t[0] != nullptr; }
+
+// The tensor-core kernel moves 16-byte vectors; other pointers take the SIMT dense kernels.
+bool tc_aligned(const void* in, const void* out_c, const void* out_d) {
+  return ((uintptr_t)in & 15) == 0 && ((uintptr_t)out_c & 15) == 0 && ((uintptr_t)out_d & 15) == 0;
+}
 
 // Launch one pass of axis j (forward or adjoint) with the axis's form.
 int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* grad, int grad_shared,
@@ -243,7 +250,7 @@ int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* 
     cudaEventRecordWithFlags((cudaEvent_t)p->trace[p->trace_i], stream, rec_flags);
   }
   cudaError_t e;
-  if (ax.form == FFX_FORM_TC) {
+  if (ax.form == FFX_FORM_TC && tc_aligned(in, out_c, out_d)) {
     DenseArgs d;
     std::memset(&d, 0, sizeof(d));
     d.in = in;
@@ -258,12 +265,11 @@ int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* 
     d.acc = acc;
     d.ncols = acc ? outer * inner : batch * outer * inner;
     d.N = ax.N;
-    int64_t grid = dense_tc_tiles(d.ncols);
+    int64_t grid = dense_tc_tiles(ax.N, d.ncols);
     if (grid > p->sms) grid = p->sms;
     if (grid < 1) grid = 1;
-    e = launch_dense_tc(d, adjoint ? ax.tc_a[2] : ax.tc_a[0], adjoint ? ax.tc_a[3] : ax.tc_a[1], p->dev_err,
-                        (int)grid, stream);
-  } else if (ax.form == FFX_FORM_DENSE) {
+    e = launch_dense_tc(d, ax.tc_t[adjoint ? 1 : 0], p->dev_err, (int)grid, stream);
+  } else if (ax.form == FFX_FORM_DENSE || ax.form == FFX_FORM_TC) {
     DenseArgs d;
     std::memset(&d, 0, sizeof(d));
     d.A = adjoint ? ax.TH : ax.T;
@@ -396,6 +402,9 @@ double model_cost(const Axis& ax, int form) {
   switch (form) {
     case FFX_FORM_PAPER: return lam * (10 * lg + 20) / 0.18;
     case FFX_FORM_FOLD: return (lam * (5 * lg + 14) + 5 * lg) / 0.11;
+    // the tensor-core form runs 3x the real flops at ~8x the rate; its 128-line
+    // tiles leave 64-point axes of small batches latency-bound
+    case FFX_FORM_TC: return N < 128 ? 8 * N / 0.40 : 8 * N / 1.2;
     default: return 8 * N / 0.45;
   }
 }
@@ -410,7 +419,7 @@ std::string cache_key(const char* dev, const Axis& ax, int64_t outer, int64_t in
 }
 
 // Cache lines (JSON, one object per line):
-//   {"key": "...", "form": "dense", "ms": [paper, fold, dense]}
+//   {"key": "...", "form": "dense", "ms": [paper, fold, dense, tc]}
 // The last line for a key wins.
 int cache_lookup(const std::string& key) {
   const char* path = std::getenv("FFX_TUNE_CACHE");
@@ -426,6 +435,7 @@ int cache_lookup(const std::string& key) {
     if (std::strstr(line, "\"form\": \"paper\"")) form = FFX_FORM_PAPER;
     if (std::strstr(line, "\"form\": \"fold\"")) form = FFX_FORM_FOLD;
     if (std::strstr(line, "\"form\": \"dense\"")) form = FFX_FORM_DENSE;
+    if (std::strstr(line, "\"form\": \"tc\"")) form = FFX_FORM_TC;
   }
   std::fclose(f);
   return form;
@@ -437,9 +447,9 @@ void cache_store(const std::string& key, int form, const double* ms) {
   std::lock_guard<std::mutex> lock(g_cache_mutex);
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  const char* names[] = {"", "paper", "fold", "dense"};
-  std::fprintf(f, "{\"key\": \"%s\", \"form\": \"%s\", \"ms\": [%.6g, %.6g, %.6g]}\n", key.c_str(), names[form],
-               ms[0], ms[1], ms[2]);
+  const char* names[] = {"", "paper", "fold", "dense", "tc"};
+  std::fprintf(f, "{\"key\": \"%s\", \"form\": \"%s\", \"ms\": [%.6g, %.6g, %.6g, %.6g]}\n", key.c_str(),
+               names[form], ms[0], ms[1], ms[2], ms[3]);
   std::fclose(f);
 }
 
@@ -451,9 +461,10 @@ int time_forms(ffx_plan_s* p, int j, cudaStream_t s, double* ms) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   int rc = FFX_OK;
-  for (int f = FFX_FORM_PAPER; f <= FFX_FORM_DENSE && rc == FFX_OK; ++f) {
+  for (int f = FFX_FORM_PAPER; f <= FFX_FORM_TC && rc == FFX_OK; ++f) {
     ms[f - 1] = 1e30;
     if (f == FFX_FORM_DENSE && !ax.T) continue;
+    if (f == FFX_FORM_TC && !tc_capable(ax)) continue;
     ax.form = f;
     float best = 1e30f;
     for (int rep = 0; rep < 6 && rc == FFX_OK; ++rep) {
@@ -725,12 +736,12 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
     }
   }
 
-  // split tensor-core operands for 64-point axes, and the device error counter
+  // split tensor-core operands, and the device error counter
   if (rc == FFX_OK) {
     size_t tbytes = 256;
     for (int j = 0; j < ndim; ++j)
-      if (p->axis[j].N == kTcN && p->axis[j].T && (form == FFX_FORM_AUTO || form == FFX_FORM_TC))
-        tbytes += 4 * dense_tc_a_floats() * sizeof(float);
+      if (dense_tc_supported(p->axis[j].N) && p->axis[j].T && (form == FFX_FORM_AUTO || form == FFX_FORM_TC))
+        tbytes += 2 * dense_tc_t_bytes(p->axis[j].N);
     e = cudaMalloc(&p->tc_mem, tbytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -738,16 +749,16 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
     } else {
       p->dev_err = (int*)p->tc_mem;
       cudaMemsetAsync(p->dev_err, 0, 256, s);
-      float* tcur = (float*)((char*)p->tc_mem + 256);
+      unsigned char* tcur = (unsigned char*)p->tc_mem + 256;
       for (int j = 0; j < ndim && rc == FFX_OK; ++j) {
         Axis& ax = p->axis[j];
-        if (!(ax.N == kTcN && ax.T && (form == FFX_FORM_AUTO || form == FFX_FORM_TC))) continue;
-        for (int q = 0; q < 4; ++q) {
-          ax.tc_a[q] = tcur;
-          tcur += dense_tc_a_floats();
+        if (!(dense_tc_supported(ax.N) && ax.T && (form == FFX_FORM_AUTO || form == FFX_FORM_TC))) continue;
+        for (int q = 0; q < 2; ++q) {
+          ax.tc_t[q] = tcur;
+          tcur += dense_tc_t_bytes(ax.N);
         }
-        e = launch_tc_build_a(ax.T, ax.tc_a[0], ax.tc_a[1], s);
-        if (e == cudaSuccess) e = launch_tc_build_a(ax.TH, ax.tc_a[2], ax.tc_a[3], s);
+        e = launch_tc_build_t(ax.T, ax.tc_t[0], ax.N, s);
+        if (e == cudaSuccess) e = launch_tc_build_t(ax.TH, ax.tc_t[1], ax.N, s);
         if (e == cudaSuccess)
           e = cudaFuncSetAttribute(dense_tc_func(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)dense_tc_smem());
@@ -779,6 +790,7 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
       const std::string key = cache_key(dev, ax, outer, inner);
       int f = cache_lookup(key);
       if (f == FFX_FORM_DENSE && !ax.T) f = -1;
+      if (f == FFX_FORM_TC && !tc_capable(ax)) f = -1;
       if (f < 0 && (flags & FFX_TUNE)) {
         if (!tuned_any) {
           if ((rc = ensure_ws(p, 0, 1)) || (rc = ensure_ws(p, 1, 1))) break;
@@ -789,17 +801,18 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
           }
           tuned_any = true;
         }
-        double ms[3];
+        double ms[4];
         if ((rc = time_forms(p, j, s, ms))) break;
         f = FFX_FORM_PAPER;
-        for (int c = FFX_FORM_FOLD; c <= FFX_FORM_DENSE; ++c)
+        for (int c = FFX_FORM_FOLD; c <= FFX_FORM_TC; ++c)
           if (ms[c - 1] < ms[f - 1]) f = c;
         cache_store(key, f, ms);
       }
       if (f < 0) {
         f = FFX_FORM_PAPER;
-        for (int c = FFX_FORM_FOLD; c <= FFX_FORM_DENSE; ++c) {
+        for (int c = FFX_FORM_FOLD; c <= FFX_FORM_TC; ++c) {
           if (c == FFX_FORM_DENSE && !ax.T) continue;
+          if (c == FFX_FORM_TC && !tc_capable(ax)) continue;
           if (model_cost(ax, c) < model_cost(ax, f)) f = c;
         }
       }

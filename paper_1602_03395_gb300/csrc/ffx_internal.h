@@ -106,15 +106,16 @@ int64_t dense_small_tiles(int64_t ncols);
 size_t dense_small_image_floats2(int N);
 cudaError_t launch_dense_small_image(const float2* T, float2* img, int N, cudaStream_t s);
 constexpr int kDenseMaxN = 1024;
-// dense form of 64-point lines on the tensor cores (ffx_tc.cu), split TF32
-constexpr int kTcN = 64;
+// dense form on the tensor cores (ffx_tc.cu), split TF32, for lines of N
+// points with N a multiple of 64 up to kDenseMaxN; in place only for N = 64
+bool dense_tc_supported(int N);
 size_t dense_tc_smem();
 const void* dense_tc_func();
-size_t dense_tc_a_floats();
-cudaError_t launch_dense_tc(const DenseArgs& a, const float* Ahi, const float* Alo, int* err, int grid,
+size_t dense_tc_t_bytes(int N);
+cudaError_t launch_dense_tc(const DenseArgs& a, const unsigned char* Tblk, int* err, int grid,
                             cudaStream_t stream);
-int64_t dense_tc_tiles(int64_t ncols);
-cudaError_t launch_tc_build_a(const float2* T, float* Ahi, float* Alo, cudaStream_t s);
+int64_t dense_tc_tiles(int N, int64_t ncols);
+cudaError_t launch_tc_build_t(const float2* T, unsigned char* Tblk, int N, cudaStream_t s);
 cudaError_t launch_identity(float2* I, int N, cudaStream_t s);
 cudaError_t launch_dense_build(const float2* O, float2* T, float2* TH, int N, cudaStream_t s);
 

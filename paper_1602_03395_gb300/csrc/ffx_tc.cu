@@ -1,30 +1,47 @@
-// Dense form on the tensor cores (tcgen05): the per-axis map of lines of
-// 64 points as a real 128 x 128 matrix product with split-TF32 operands.
+// Dense form on the tensor cores (tcgen05): the per-axis map of lines of N
+// points (N a multiple of 64, up to 1024) as a real matrix product with
+// split-TF32 operands, accumulated in tensor memory.
 //
 // The complex map OUT[n][c] = sum_k T[n][k] IN[k][c] becomes a real product
 // with every complex entry t = x + iy of T replaced by the 2 x 2 block
 // [[x, -y], [y, x]] and every complex input v = a + ib by the pair (a, b):
 // real row 2n is Re OUT[n], row 2n + 1 is Im OUT[n]; real K index 2k + p is
-// part p of IN[k].  Each FP32 operand is split into a TF32 head and a TF32
-// tail (hi = rna_tf32(x), lo = rna_tf32(x - hi)); the product accumulates
-// A_hi B_hi + A_hi B_lo + A_lo B_hi in FP32 in tensor memory, which keeps
-// ~2^-21 of relative precision (the dropped lo*lo term is below that).
+// part p of IN[k].  The MMA runs transposed, D[line][row] = sum_K X[line][K]
+// T[row][K], so that tensor-memory lane = line and each epilogue thread owns
+// one line's outputs (coalesced stores along either memory order).  Each FP32
+// operand is split into a TF32 head and tail (hi = rna_tf32(x), lo =
+// rna_tf32(x - hi)); X_hi T_hi accumulates in one FP32 tensor-memory
+// accumulator and the cross terms X_hi T_lo + X_lo T_hi in a second one, added
+// in the epilogue (the dropped lo*lo term is ~2^-22 relative).  The tensor
+// cores' FP32 accumulation rounds with a bias, so its error grows with the
+// number of MMAs into one accumulator; keeping the small cross terms apart
+// leaves the large one N/4 accumulation steps instead of 3N/4.
 //
-// Kernel: one block of 128 threads per SM (persistent), the whole split A
-// (2 x 64 KB) resident in shared memory in the tensor cores' K-major
-// no-swizzle layout (8-row x 16-byte core matrices; 128 bytes between core
-// matrices along K, 4096 bytes between 8-row groups).  Work items are tiles of
-// 64 lines (the MMA N dimension) -- times the realizations of the batch when
-// summing the ensemble.  The input of a tile arrives in 4 chunks of 32 real K
-// (16 complex rows), double-buffered: the threads load, split and lay out
-// chunk c + 1 while the tensor cores multiply chunk c (12 MMAs of
-// M=128, N=64, K=8, issued by one thread, completion signalled on an
-// mbarrier by tcgen05.commit).  The epilogue reads the accumulator from tensor
-// memory (tcgen05.ld, one 32-lane quarter per warp), pairs real and imaginary
-// rows with a shuffle and stores complex64, |.|^2 or the ensemble sum.
+// Kernel: one persistent block of 288 threads per SM, warp-specialised.
+//  * warps 0-3 (producers), per K chunk of 32 real K: thread 0 starts a bulk
+//    (TMA) copy of the pre-split T chunk (128 rows x 32 K, head and tail,
+//    stored in global memory already in the tensor cores' K-major no-swizzle
+//    core-matrix order); all 128 threads load the item's 128 lines x 16
+//    complex inputs (16-byte loads), split them and store them in the same
+//    order (bank-conflict free); they arrive on the stage's "full" barrier.
+//    Thread 0 arrives only after its own copy has landed, so a stage is full
+//    when both halves are in shared memory, and no copy is ever left in flight.
+//  * warp 4 (MMA): per chunk, 4 K-steps x 3 products of tcgen05.mma
+//    (M = 128 lines, N = 128 rows, K = 8, kind::tf32) into one of two tensor-
+//    memory accumulator pairs; tcgen05.commit releases the stage ("empty") and,
+//    after a sub-tile's last chunk, hands the accumulator on ("acc_full").
+//  * warps 5-8 (epilogue): read their 32-lane quarter of the accumulator
+//    (tcgen05.ld), store complex64 or |.|^2 (or add |.|^2 over the batch in
+//    shared memory), and arrive on "acc_empty".
+// Work items are (128 lines, 128 real rows) of the output, rows fastest
+// varying across the items that run together so the lines' inputs are shared
+// in L2; with N > 64 a line's outputs span several items, so such passes do
+// not run in place.
 //
-// Every wait is bounded: a wait that runs out counts an error in
-// a.err (device memory), stops the block's work and frees its tensor memory.
+// Every wait is bounded; a wait that runs out sets a block-wide abort flag
+// (every other wait then gives up at once), the MMA thread waits (bounded)
+// for its own tensor-core work, the block frees its tensor memory, counts an
+// error in `err` and exits.
 #include <cstring>
 
 #include "ffx_internal.h"
@@ -33,20 +50,22 @@ namespace ffx {
 
 namespace {
 
-constexpr int TN = 64;            // complex line length
-constexpr int TM = 128;           // real rows (2 TN) = MMA M
-constexpr int TK = 128;           // real K (2 TN)
-constexpr int TCN = 64;           // lines per tile = MMA N
-constexpr int TKC = 32;           // real K per chunk
-constexpr int TCHUNKS = TK / TKC;  // 4
-constexpr int TSTAGES = 2;
-constexpr int A_BYTES = TM * TK * 4;                 // 64 KB per split part
-constexpr int A_SBO = (TK / 4) * 128;                // 4096: between 8-row groups
-constexpr int B_CHUNK_BYTES = TCN * TKC * 4;         // 8 KB per split part
-constexpr int B_SBO = (TKC / 4) * 128;               // 1024
-constexpr int CORE_LBO = 128;                        // between core matrices along K
-constexpr int TC_SMEM = 2 * A_BYTES + TSTAGES * 2 * B_CHUNK_BYTES + 256;
-constexpr long long kSpinLimit = 1ll << 22;  // try_wait polls: a few seconds at most
+constexpr int LINES = 128;         // lines per item = MMA M = tensor-memory lanes
+constexpr int ROWS = 128;          // real output rows per item = MMA N
+constexpr int TKC = 32;            // real K per chunk
+constexpr int TSTAGES = 3;
+constexpr int CORE_LBO = 128;      // bytes between core matrices along K
+constexpr int CHUNK_SBO = (TKC / 4) * 128;  // 1024: between 8-row groups of a chunk
+constexpr int T_PART = ROWS * TKC * 4;      // 16 KB per split part
+constexpr int X_PART = LINES * TKC * 4;     // 16 KB per split part
+constexpr int T_CHUNK = 2 * T_PART;         // head + tail, one bulk copy
+constexpr int STAGE_BYTES = T_CHUNK + 2 * X_PART;  // 64 KB
+constexpr int TC_SMEM = TSTAGES * STAGE_BYTES;
+constexpr int ACC_SMEM = (ROWS / 2) * 128 * 4;  // |.|^2 sums over the batch, [row][line]
+constexpr int NPROD = 128, NEPI = 128;
+constexpr int NTHREADS = NPROD + 32 + NEPI;  // 288
+constexpr int ACC_COLS = 4 * ROWS;           // two buffers x (head product, cross terms): all 512
+constexpr long long kSpinLimit = 1ll << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -62,27 +81,53 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint
   return d;
 }
 
-// kind::tf32, D = F32, A = B = TF32, both K-major, N = 64, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TCN >> 3) << 17) |
-                            ((uint32_t)(TM >> 4) << 24);
+// kind::tf32, D = F32, A = B = TF32, both K-major, N = ROWS, M = LINES
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(ROWS >> 3) << 17) |
+                            ((uint32_t)(LINES >> 4) << 24);
 
-__device__ __forceinline__ float tf32_hi(float x) {
+__device__ __forceinline__ float tf32_round(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_test(uint32_t mbar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded wait for the phase of the given parity; gives up (false) when the
+// block aborts or the poll budget runs out (then it sets the abort flag).
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int* abort_flag) {
   for (long long i = 0; i < kSpinLimit; ++i) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    if (done) return true;
+    if (mbar_test(mbar, parity)) return true;
+    if (*abort_flag) return false;
   }
+  *abort_flag = 1;
   return false;
+}
+
+// Bounded wait that ignores the abort flag: for work this thread started
+// itself (a bulk copy, tensor-core operations), which must end before exit.
+__device__ __forceinline__ bool mbar_wait_own(uint32_t mbar, uint32_t parity, volatile int* abort_flag) {
+  for (long long i = 0; i < kSpinLimit; ++i)
+    if (mbar_test(mbar, parity)) return true;
+  *abort_flag = 1;
+  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
@@ -93,14 +138,22 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64
       : "memory");
 }
 
-// Lines (columns) of one work item.
-__device__ __forceinline__ void tc_bases(const DenseArgs& a, int64_t ct, int b, long long* cbase, int* cbr,
-                                         int t) {
-  const int64_t inner = a.inner;
-  const int64_t c = ct * TCN + t;
-  long long base = -1;
-  int br = 0;
+// 32 lanes x 16 consecutive 32-bit columns of tensor memory (this warp's lane quarter)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* x) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]), "=r"(x[4]), "=r"(x[5]), "=r"(x[6]), "=r"(x[7]), "=r"(x[8]),
+        "=r"(x[9]), "=r"(x[10]), "=r"(x[11]), "=r"(x[12]), "=r"(x[13]), "=r"(x[14]), "=r"(x[15])
+      : "r"(taddr));
+}
+
+// Line c of the pass (realization b of the batch when accumulating): offset
+// of its first point, or -1 past the end; br = its realization.
+__device__ __forceinline__ void line_ref(const DenseArgs& a, int64_t c, int b, long long& base, int& br) {
+  base = -1;
+  br = 0;
   if (c < a.ncols) {
+    const int64_t inner = a.inner;
     int64_t bo = c / inner;
     const int64_t i = c - bo * inner;
     if (a.acc) {
@@ -109,245 +162,365 @@ __device__ __forceinline__ void tc_bases(const DenseArgs& a, int64_t ct, int b, 
     } else {
       br = (int)(c / (a.outer * inner));
     }
-    base = bo * (int64_t)TN * inner + i;
+    base = bo * (int64_t)a.N * inner + i;
   }
-  cbase[t] = base;
-  cbr[t] = br;
 }
 
-__global__ void __launch_bounds__(128, 1) dense_tc_kernel(const DenseArgs a, const float* __restrict__ Ahi,
-                                                          const float* __restrict__ Alo, int* err) {
+__device__ __forceinline__ void split_store(unsigned char* xh, unsigned char* xl, int off, float4 v) {
+  const float4 hi = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
+  const float4 lo = make_float4(tf32_round(v.x - hi.x), tf32_round(v.y - hi.y), tf32_round(v.z - hi.z),
+                                tf32_round(v.w - hi.w));
+  *reinterpret_cast<float4*>(xh + off) = hi;
+  *reinterpret_cast<float4*>(xl + off) = lo;
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    dense_tc_kernel(const DenseArgs a, const unsigned char* __restrict__ Tblk, int* err) {
   extern __shared__ __align__(1024) unsigned char tsm[];
-  unsigned char* sA_hi = tsm;
-  unsigned char* sA_lo = tsm + A_BYTES;
-  unsigned char* sB = tsm + 2 * A_BYTES;  // [stage][hi, lo][B_CHUNK_BYTES]
-  __shared__ __align__(8) uint64_t mbar[TSTAGES];
+  __shared__ __align__(8) uint64_t full_bar[TSTAGES], empty_bar[TSTAGES], copy_bar[TSTAGES];
+  __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], done_bar;
   __shared__ uint32_t tmem_slot;
-  __shared__ long long cbase[TCN];
-  __shared__ int cbr[TCN];
-  __shared__ int s_abort;
+  __shared__ volatile int s_abort;
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
+  const int mtiles = (2 * a.N) / ROWS;
+  const int kchunks = (2 * a.N) / TKC;
+  const int nb = a.acc ? (int)a.batch : 1;
+  const int64_t ctiles = (a.ncols + LINES - 1) / LINES;
+  const int64_t items = ctiles * mtiles;
+  if ((int64_t)blockIdx.x >= items) return;
+  const int64_t my_items = (items - blockIdx.x + gridDim.x - 1) / gridDim.x;
   const int64_t inner = a.inner;
   const bool contiguous = (inner == 1);
-  const int64_t col_tiles = (a.ncols + TCN - 1) / TCN;
-  const int nb = a.acc ? (int)a.batch : 1;
-  if ((int64_t)blockIdx.x >= col_tiles) return;
-  const int64_t my_tiles = (col_tiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
-  const int64_t n_items = my_tiles * nb;
 
-  // tensor memory for the 128 x 64 FP32 accumulator
-  if (warp == 0) {
+  if (warp == 4) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(TCN)
+                 "r"(ACC_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int s = 0; s < TSTAGES; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[s])) : "memory");
+    for (int s = 0; s < TSTAGES; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full_bar[s])), "r"(NPROD) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty_bar[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&copy_bar[s])) : "memory");
+    }
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accf_bar[b])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acce_bar[b])), "r"(NEPI) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done_bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
   }
-  // the split A, already in core-matrix order in global memory: a straight copy
-  {
-    const float4* gh = reinterpret_cast<const float4*>(Ahi);
-    const float4* gl = reinterpret_cast<const float4*>(Alo);
-    float4* sh = reinterpret_cast<float4*>(sA_hi);
-    float4* sl = reinterpret_cast<float4*>(sA_lo);
-    for (int i = tid; i < A_BYTES / 16; i += 128) {
-      sh[i] = __ldg(gh + i);
-      sl[i] = __ldg(gl + i);
-    }
-  }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  const uint32_t a_hi_addr = smem_u32(sA_hi), a_lo_addr = smem_u32(sA_lo), b_addr = smem_u32(sB);
+  const uint32_t smem_base = smem_u32(tsm);
 
-  float racc[TCN];
+  if (warp < 4) {
+    // ---------------- producers ----------------
+    const int t = tid;
+    int64_t g = 0;  // chunks produced
+    bool ok = true;
+    for (int64_t it = 0; ok && it < my_items; ++it) {
+      const int64_t w = blockIdx.x + it * gridDim.x;
+      const int mt = (int)(w % mtiles);
+      const int64_t ct = w / mtiles;
+      for (int b = 0; ok && b < nb; ++b) {
+        // contiguous lines: thread t loads k-pairs (t>>3)&3 and +4 of the 4 lines
+        // (t&7) + 8 (t>>5) + 32 j; strided lines: k-pairs 0..7 of line t
+        long long lb[4];
+        int lbr[4];
+        if (contiguous) {
 #pragma unroll
-  for (int j = 0; j < TCN; ++j) racc[j] = 0.f;
-
-  int64_t gchunk = 0;  // chunks issued so far (stage = gchunk % 2)
-  bool ok = true;
-  for (int64_t it = 0; it < n_items && ok; ++it) {
-    const int64_t ct = blockIdx.x + (it / nb) * gridDim.x;
-    const int b = (int)(it % nb);
-    __syncthreads();  // cbase of the previous item no longer read
-    if (tid < TCN) tc_bases(a, ct, b, cbase, cbr, tid);
-    __syncthreads();
-    for (int c = 0; c < TCHUNKS && ok; ++c, ++gchunk) {
-      const int stage = (int)(gchunk & 1);
-      if (gchunk >= TSTAGES) {
-        // the MMAs that last read this stage (chunk gchunk - 2) are done;
-        // thread 0 waits, the block follows it through the barrier
-        if (tid == 0 && !mbar_wait(smem_u32(&mbar[stage]), (uint32_t)(((gchunk - TSTAGES) >> 1) & 1)))
-          s_abort = 1;
-        __syncthreads();
-        if (s_abort) {
-          ok = false;
-          break;
+          for (int j = 0; j < 4; ++j) line_ref(a, ct * LINES + (t & 7) + 8 * (t >> 5) + 32 * j, b, lb[j], lbr[j]);
+        } else {
+          line_ref(a, ct * LINES + t, b, lb[0], lbr[0]);
+        }
+        for (int kc = 0; kc < kchunks; ++kc, ++g) {
+          const int s = (int)(g % TSTAGES);
+          const int64_t u = g / TSTAGES;
+          if (u >= 1 && !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)((u - 1) & 1), &s_abort)) {
+            ok = false;
+            break;
+          }
+          unsigned char* st = tsm + s * STAGE_BYTES;
+          if (t == 0) {
+            const uint32_t cb = smem_u32(&copy_bar[s]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cb), "r"(T_CHUNK)
+                         : "memory");
+            const unsigned char* src = Tblk + ((size_t)mt * kchunks + kc) * T_CHUNK;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_base + s * STAGE_BYTES),
+                "l"(src), "r"(T_CHUNK), "r"(cb)
+                : "memory");
+          }
+          unsigned char* xh = st + T_CHUNK;
+          unsigned char* xl = xh + X_PART;
+          float4 v[8];
+          if (contiguous) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int j = i >> 1;
+              const int kp = ((t >> 3) & 3) + 4 * (i & 1);
+              v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+              if (lb[j] >= 0) v[i] = *reinterpret_cast<const float4*>(a.in + lb[j] + kc * 16 + 2 * kp);
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+              if (lb[0] >= 0) {
+                const int64_t addr = lb[0] + (int64_t)(kc * 16 + 2 * i) * inner;
+                const float2 p0 = a.in[addr];  // plain loads: N = 64 passes may run in place
+                const float2 p1 = a.in[addr + inner];
+                v[i] = make_float4(p0.x, p0.y, p1.x, p1.y);
+              }
+            }
+          }
+          if (a.grad) {
+            // the input element is 2 grad * psi (grad shared by the realizations or not)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              long long lbi;
+              int bri, kp;
+              if (contiguous) {
+                lbi = (i < 2) ? lb[0] : (i < 4) ? lb[1] : (i < 6) ? lb[2] : lb[3];
+                bri = (i < 2) ? lbr[0] : (i < 4) ? lbr[1] : (i < 6) ? lbr[2] : lbr[3];
+                kp = ((t >> 3) & 3) + 4 * (i & 1);
+              } else {
+                lbi = lb[0];
+                bri = lbr[0];
+                kp = i;
+              }
+              if (lbi < 0) continue;
+              int64_t addr = lbi + (int64_t)(kc * 16 + 2 * kp) * inner;
+              if (a.grad_shared) addr -= (int64_t)bri * a.M;
+              const float g0 = 2.f * __ldg(a.grad + addr);
+              const float g1 = 2.f * __ldg(a.grad + addr + inner);
+              v[i].x *= g0;
+              v[i].y *= g0;
+              v[i].z *= g1;
+              v[i].w *= g1;
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            int n, kp;
+            if (contiguous) {
+              n = (t & 7) + 8 * (t >> 5) + 32 * (i >> 1);
+              kp = ((t >> 3) & 3) + 4 * (i & 1);
+            } else {
+              n = t;
+              kp = i;
+            }
+            split_store(xh, xl, (n >> 3) * CHUNK_SBO + kp * CORE_LBO + (n & 7) * 16, v[i]);
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          if (t == 0 && !mbar_wait_own(smem_u32(&copy_bar[s]), (uint32_t)(u & 1), &s_abort)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive(smem_u32(&full_bar[s]));
         }
       }
-      // load 16 complex rows x 64 lines, split, lay out as (line n, real k) K-major
-      unsigned char* bh = sB + stage * 2 * B_CHUNK_BYTES;
-      unsigned char* bl = bh + B_CHUNK_BYTES;
-      for (int idx = tid; idx < 16 * TCN; idx += 128) {
-        int kl, n;
-        if (contiguous) {
-          n = idx >> 4;
-          kl = idx & 15;
-        } else {
-          kl = idx / TCN;
-          n = idx - kl * TCN;
+    }
+  } else if (warp == 4) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int64_t g = 0, sub = 0;
+      bool ok = true;
+      for (int64_t it = 0; ok && it < my_items; ++it) {
+        for (int b = 0; ok && b < nb; ++b, ++sub) {
+          const int buf = (int)(sub & 1);
+          const int64_t v = sub >> 1;
+          if (v >= 1 && !mbar_wait(smem_u32(&acce_bar[buf]), (uint32_t)((v - 1) & 1), &s_abort)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t d1 = tmem + (uint32_t)(buf * 2 * ROWS), d2 = d1 + ROWS;
+          for (int kc = 0; kc < kchunks; ++kc, ++g) {
+            const int s = (int)(g % TSTAGES);
+            const int64_t u = g / TSTAGES;
+            if (!mbar_wait(smem_u32(&full_bar[s]), (uint32_t)(u & 1), &s_abort)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t st = smem_base + s * STAGE_BYTES;
+            const uint32_t th = st, tl = st + T_PART, xh = st + T_CHUNK, xl = xh + X_PART;
+#pragma unroll
+            for (int ks = 0; ks < TKC / 8; ++ks) {
+              const uint32_t o = (uint32_t)(ks * 2 * CORE_LBO);
+              const uint64_t dxh = make_desc(xh + o, CORE_LBO, CHUNK_SBO);
+              const uint64_t dxl = make_desc(xl + o, CORE_LBO, CHUNK_SBO);
+              const uint64_t dth = make_desc(th + o, CORE_LBO, CHUNK_SBO);
+              const uint64_t dtl = make_desc(tl + o, CORE_LBO, CHUNK_SBO);
+              const uint32_t more = (kc == 0 && ks == 0) ? 0u : 1u;
+              mma_tf32(d1, dxh, dth, more);
+              mma_tf32(d2, dxh, dtl, more);
+              mma_tf32(d2, dxl, dth, 1u);
+            }
+            mma_commit(smem_u32(&empty_bar[s]));
+          }
+          if (ok) mma_commit(smem_u32(&accf_bar[buf]));
         }
-        const int k = c * 16 + kl;
-        float2 v = make_float2(0.f, 0.f);
-        const long long base = cbase[n];
-        if (base >= 0) {
-          const int64_t addr = base + (int64_t)k * inner;
-          v = a.in[addr];  // plain load: passes may run in place
-          if (a.grad) {
-            const int64_t gaddr = a.grad_shared ? addr - (int64_t)cbr[n] * a.M : addr;
-            const float gr = 2.f * __ldg(a.grad + gaddr);
-            v.x *= gr;
-            v.y *= gr;
+      }
+      // whatever happened, the tensor cores finish this thread's work before exit
+      mma_commit(smem_u32(&done_bar));
+      mbar_wait_own(smem_u32(&done_bar), 0u, &s_abort);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue ----------------
+    const int q = warp & 3;          // tensor-memory lane quarter this warp may read
+    const int r = q * 32 + lane;     // line within the item
+    const int64_t M = a.M;
+    float* racc = reinterpret_cast<float*>(tsm + TC_SMEM);  // accumulating launches only
+    if (a.acc)
+      for (int m = 0; m < ROWS / 2; ++m) racc[m * LINES + r] = 0.f;
+    int64_t sub = 0;
+    bool ok = true;
+    for (int64_t it = 0; ok && it < my_items; ++it) {
+      const int64_t w = blockIdx.x + it * gridDim.x;
+      const int mt = (int)(w % mtiles);
+      const int64_t ct = w / mtiles;
+      const int nbase = mt * (ROWS / 2);
+      for (int b = 0; b < nb; ++b, ++sub) {
+        const int buf = (int)(sub & 1);
+        const int64_t v = sub >> 1;
+        // warp-uniform outcome: the tensor-memory loads below need the whole warp
+        ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&accf_bar[buf]), (uint32_t)(v & 1), &s_abort));
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        long long base;
+        int br;
+        line_ref(a, ct * LINES + r, b, base, br);
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * ROWS);
+#pragma unroll 1
+        for (int j0 = 0; j0 < ROWS; j0 += 16) {
+          uint32_t x[16], z[16];
+          tmem_ld16(taddr + (uint32_t)j0, x);
+          tmem_ld16(taddr + (uint32_t)(ROWS + j0), z);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          float y[16];
+#pragma unroll
+          for (int m = 0; m < 16; ++m) y[m] = __uint_as_float(x[m]) + __uint_as_float(z[m]);
+          const int n0 = nbase + j0 / 2;  // complex outputs n0 .. n0 + 7 of this line
+          if (a.acc) {
+#pragma unroll
+            for (int m = 0; m < 8; ++m)
+              racc[(j0 / 2 + m) * LINES + r] += y[2 * m] * y[2 * m] + y[2 * m + 1] * y[2 * m + 1];
+          } else if (base >= 0) {
+            if (a.out_c) {
+              if (contiguous) {
+                float4* o = reinterpret_cast<float4*>(a.out_c + base + n0);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) o[m] = make_float4(y[4 * m], y[4 * m + 1], y[4 * m + 2], y[4 * m + 3]);
+              } else {
+#pragma unroll
+                for (int m = 0; m < 8; ++m)
+                  a.out_c[base + (int64_t)(n0 + m) * inner] = make_float2(y[2 * m], y[2 * m + 1]);
+              }
+            } else {
+              float dd[8];
+#pragma unroll
+              for (int m = 0; m < 8; ++m) dd[m] = y[2 * m] * y[2 * m] + y[2 * m + 1] * y[2 * m + 1];
+              if (contiguous) {
+                float4* o = reinterpret_cast<float4*>(a.out_d + base + n0);
+                o[0] = make_float4(dd[0], dd[1], dd[2], dd[3]);
+                o[1] = make_float4(dd[4], dd[5], dd[6], dd[7]);
+              } else {
+#pragma unroll
+                for (int m = 0; m < 8; ++m) a.out_d[base + (int64_t)(n0 + m) * inner] = dd[m];
+              }
+            }
           }
         }
-        const float2 hi = make_float2(tf32_hi(v.x), tf32_hi(v.y));
-        const float2 lo = make_float2(tf32_hi(v.x - hi.x), tf32_hi(v.y - hi.y));
-        const int off = (n >> 3) * B_SBO + (kl >> 1) * CORE_LBO + (n & 7) * 16 + (kl & 1) * 8;
-        *reinterpret_cast<float2*>(bh + off) = hi;
-        *reinterpret_cast<float2*>(bl + off) = lo;
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t bh_addr = b_addr + stage * 2 * B_CHUNK_BYTES;
-        const uint32_t bl_addr = bh_addr + B_CHUNK_BYTES;
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(smem_u32(&acce_bar[buf]));
+        if (a.acc && b == nb - 1) {
+          if (base >= 0) {
+            const int64_t o0 = base - (int64_t)br * M + (int64_t)nbase * inner;
+            if (contiguous) {
+              float4* o = reinterpret_cast<float4*>(a.out_d + o0);
 #pragma unroll
-        for (int ks = 0; ks < TKC / 8; ++ks) {
-          const uint32_t a_off = (uint32_t)((c * (TKC / 8) + ks) * 2 * CORE_LBO);
-          const uint32_t b_off = (uint32_t)(ks * 2 * CORE_LBO);
-          const uint64_t dah = make_desc(a_hi_addr + a_off, CORE_LBO, A_SBO);
-          const uint64_t dal = make_desc(a_lo_addr + a_off, CORE_LBO, A_SBO);
-          const uint64_t dbh = make_desc(bh_addr + b_off, CORE_LBO, B_SBO);
-          const uint64_t dbl = make_desc(bl_addr + b_off, CORE_LBO, B_SBO);
-          const uint32_t first = (c == 0 && ks == 0) ? 0u : 1u;
-          mma_tf32(tmem, dah, dbh, first);
-          mma_tf32(tmem, dah, dbl, 1u);
-          mma_tf32(tmem, dal, dbh, 1u);
+              for (int m = 0; m < ROWS / 8; ++m) {
+                float4 cur = o[m];
+                cur.x += racc[(4 * m) * LINES + r];
+                cur.y += racc[(4 * m + 1) * LINES + r];
+                cur.z += racc[(4 * m + 2) * LINES + r];
+                cur.w += racc[(4 * m + 3) * LINES + r];
+                o[m] = cur;
+              }
+            } else {
+#pragma unroll
+              for (int m = 0; m < ROWS / 2; ++m) a.out_d[o0 + (int64_t)m * inner] += racc[m * LINES + r];
+            }
+          }
+          for (int m = 0; m < ROWS / 2; ++m) racc[m * LINES + r] = 0.f;
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(&mbar[stage]))
-                     : "memory");
-      }
-    }
-    if (!ok) break;
-    // the last commit covers every MMA of this item
-    const int64_t last = gchunk - 1;
-    if (tid == 0 && !mbar_wait(smem_u32(&mbar[last & 1]), (uint32_t)((last >> 1) & 1))) s_abort = 1;
-    __syncthreads();
-    if (s_abort) {
-      ok = false;
-      break;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // accumulator row r = 32 warp + lane: output n = r / 2, part r % 2
-    float d[TCN];
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll
-    for (int j0 = 0; j0 < TCN; j0 += 16) {
-      uint32_t r[16];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(taddr + (uint32_t)j0));
-#pragma unroll
-      for (int j = 0; j < 16; ++j) d[j0 + j] = __uint_as_float(r[j]);
-    }
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    const int n = (warp * 32 + lane) >> 1;
-    const bool re_lane = (lane & 1) == 0;
-    const bool tile_done = !a.acc || b == nb - 1;
-#pragma unroll
-    for (int j = 0; j < TCN; ++j) {
-      const float other = __shfl_xor_sync(0xffffffffu, d[j], 1);
-      if (re_lane) {
-        const float re = d[j], im = other;
-        const long long base = cbase[j];
-        if (a.acc) {
-          racc[j] += re * re + im * im;
-        } else if (base >= 0) {
-          const int64_t addr = base + (int64_t)n * inner;
-          if (a.out_c)
-            a.out_c[addr] = make_float2(re, im);
-          else
-            a.out_d[addr] = re * re + im * im;
-        }
-      }
-    }
-    if (a.acc && tile_done && re_lane) {
-#pragma unroll
-      for (int j = 0; j < TCN; ++j) {
-        const long long base = cbase[j];
-        if (base >= 0) a.out_d[base - (int64_t)b * a.M + (int64_t)n * inner] += racc[j];
-        racc[j] = 0.f;
       }
     }
   }
-  if (!ok && tid == 0) atomicAdd(err, 1);
-  // all tensor-memory reads are done before the accumulator is freed
+
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) {
+  if (tid == 0 && s_abort) atomicAdd(err, 1);
+  if (warp == 4) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ACC_COLS) : "memory");
   }
 }
 
-// Split A in core-matrix order from the complex map T [64][64]:
-// real (r, k') with r = 2n + p_out, k' = 2k + p_in, value = block entry of T[n][k].
-__global__ void tc_build_a_kernel(const float2* __restrict__ T, float* __restrict__ Ahi, float* __restrict__ Alo) {
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < TM * TK; idx += gridDim.x * blockDim.x) {
-    const int r = idx / TK, kp = idx - r * TK;
+// Pre-split T chunks from the complex map T [N][N]: for row block mt and K
+// chunk kc, a 32 KB block [head: 128 rows x 32 K][tail] in core-matrix order;
+// real (r, k') with r = 2n + p_out, k' = 2k + p_in holds the 2 x 2 block
+// entry of T[n][k].
+__global__ void tc_build_t_kernel(const float2* __restrict__ T, unsigned char* __restrict__ Tblk, int N) {
+  const int R = 2 * N;
+  const int kchunks = R / TKC;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)R * R;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / R), kp = (int)(idx - (int64_t)r * R);
     const int n = r >> 1, po = r & 1, k = kp >> 1, pi = kp & 1;
-    const float2 t = T[n * TN + k];
+    const float2 t = T[(int64_t)n * N + k];
     float v;
     if (po == 0)
       v = pi == 0 ? t.x : -t.y;
     else
       v = pi == 0 ? t.y : t.x;
-    const float hi = tf32_hi(v);
-    const int off = ((r >> 3) * A_SBO + (kp >> 2) * CORE_LBO + (r & 7) * 16 + (kp & 3) * 4) / 4;
-    Ahi[off] = hi;
-    Alo[off] = tf32_hi(v - hi);
+    const float hi = tf32_round(v);
+    const int mt = r / ROWS, rr = r % ROWS, kc = kp / TKC, kk = kp % TKC;
+    unsigned char* blk = Tblk + ((size_t)mt * kchunks + kc) * T_CHUNK;
+    const int off = (rr >> 3) * CHUNK_SBO + (kk >> 2) * CORE_LBO + (rr & 7) * 16 + (kk & 3) * 4;
+    *reinterpret_cast<float*>(blk + off) = hi;
+    *reinterpret_cast<float*>(blk + T_PART + off) = tf32_round(v - hi);
   }
 }
 
 }  // namespace
 
-size_t dense_tc_smem() { return (size_t)TC_SMEM; }
+bool dense_tc_supported(int N) { return N >= 64 && N <= kDenseMaxN && N % 64 == 0; }
+size_t dense_tc_smem() { return (size_t)(TC_SMEM + ACC_SMEM); }
 const void* dense_tc_func() { return (const void*)dense_tc_kernel; }
-size_t dense_tc_a_floats() { return (size_t)TM * TK; }
+size_t dense_tc_t_bytes(int N) { return (size_t)(2 * N) * (2 * N) * 8; }
 
-cudaError_t launch_dense_tc(const DenseArgs& a, const float* Ahi, const float* Alo, int* err, int grid,
+cudaError_t launch_dense_tc(const DenseArgs& a, const unsigned char* Tblk, int* err, int grid,
                             cudaStream_t stream) {
-  dense_tc_kernel<<<grid, 128, TC_SMEM, stream>>>(a, Ahi, Alo, err);
+  dense_tc_kernel<<<grid, NTHREADS, TC_SMEM + (a.acc ? ACC_SMEM : 0), stream>>>(a, Tblk, err);
   return cudaGetLastError();
 }
 
-int64_t dense_tc_tiles(int64_t ncols) { return (ncols + TCN - 1) / TCN; }
+int64_t dense_tc_tiles(int N, int64_t ncols) { return ((ncols + LINES - 1) / LINES) * ((2 * N) / ROWS); }
 
-cudaError_t launch_tc_build_a(const float2* T, float* Ahi, float* Alo, cudaStream_t s) {
-  tc_build_a_kernel<<<64, 256, 0, s>>>(T, Ahi, Alo);
+cudaError_t launch_tc_build_t(const float2* T, unsigned char* Tblk, int N, cudaStream_t s) {
+  tc_build_t_kernel<<<256, 256, 0, s>>>(T, Tblk, N);
   return cudaGetLastError();
 }
 

@@ -1,5 +1,5 @@
-"""The dense form on the tensor cores (tcgen05, split TF32) for 64-point lines,
-against the FP64 oracle and against the FP32 dense form."""
+"""The dense form on the tensor cores (tcgen05, split TF32) for axes whose
+length is a multiple of 64, against the FP64 oracle."""
 
 import numpy as np
 import pytest
@@ -17,8 +17,25 @@ def ffx():
     return require_gpu()
 
 
-@pytest.mark.parametrize("dims,lam,batch", [((64,), (5,), 3), ((64, 64), (7, 3), 1), ((48, 64), (4, 9), 2),
-                                            ((64, 16, 64), (3, 5, 30), 1), ((64, 64, 64), (30, 30, 3), 2)])
+TC_CASES = [
+    ((64,), (5,), 3),
+    ((64, 64), (7, 3), 1),
+    ((48, 64), (4, 9), 2),
+    ((64, 16, 64), (3, 5, 30), 1),
+    ((64, 64, 64), (30, 30, 3), 2),
+    # longer axes: several row blocks per line, ragged line tiles, strided axes
+    ((128,), (3,), 300),
+    ((192, 48), (5, 2), 3),
+    ((256, 96), (4, 7), 1),
+    ((48, 384), (3, 6), 2),
+    ((512, 32), (3, 4), 1),
+    ((768,), (5,), 2),
+    ((1024,), (3,), 5),
+    ((128, 16, 192), (9, 4, 3), 1),
+]
+
+
+@pytest.mark.parametrize("dims,lam,batch", TC_CASES)
 def test_tc_field_and_density(ffx, dims, lam, batch):
     rng = np.random.default_rng(sum(dims) + batch)
     dx = (0.25,) * len(dims)
@@ -64,3 +81,42 @@ def test_tc_adjoint_and_backward(ffx):
     e2 = rel_l2(g, O.density_loss_gradient(psi, grad, dx, t, lam))
     print(f"tc adjoint {e1:.2e}, backward {e2:.2e}")
     assert e1 < FIELD_TOL and e2 < FIELD_TOL
+
+
+@pytest.mark.parametrize("dims,lam", [((128, 64), (5, 3)), ((256,), (7,)), ((16, 192), (3, 4))])
+def test_tc_accumulate_and_backward_long_axes(ffx, dims, lam):
+    rng = np.random.default_rng(sum(dims))
+    dx, t, batch = (0.25,) * len(dims), 6.0, 3
+    psi = random_field(rng, (batch,) + dims)
+    grad = rng.normal(size=(batch,) + dims).astype(np.float32)
+    ref = np.abs(O.expand_field(psi, dx, t, lam)) ** 2
+    with ffx.Plan(dims, dx, t, lam, form="tc", accumulate=True) as plan:
+        acc = ffx.ffx_expand(plan, to_dev(psi)).cpu().numpy()
+        # an accumulating plan's gradient is shared by the realizations
+        g1 = ffx.ffx_expand_backward(plan, to_dev(psi), to_dev(np.ascontiguousarray(grad[0]))).cpu().numpy()
+        assert plan.device_errors() == 0
+    with ffx.Plan(dims, dx, t, lam, form="tc") as plan:
+        g = ffx.ffx_expand_backward(plan, to_dev(psi), to_dev(grad)).cpu().numpy()
+        assert plan.device_errors() == 0
+    e1 = rel_l2(acc, ref.sum(0))
+    e2 = rel_l2(g, O.density_loss_gradient(psi, grad, dx, t, lam))
+    e3 = rel_l2(g1, O.density_loss_gradient(psi, np.broadcast_to(grad[0], grad.shape), dx, t, lam))
+    print(f"tc {dims}: ensemble sum {e1:.2e}, backward {e2:.2e}, shared-grad backward {e3:.2e}")
+    assert e1 < DENSITY_TOL and e2 < FIELD_TOL and e3 < FIELD_TOL
+
+
+def test_tc_unaligned_buffers_take_the_simt_kernel(ffx):
+    """A field that starts 8 bytes past a 16-byte boundary is still expanded
+    correctly (those passes run on the FP32 SIMT dense kernels)."""
+    dims, dx, lam, t = (128, 64), (0.25, 0.25), (3, 5), 4.0
+    rng = np.random.default_rng(5)
+    psi = random_field(rng, (1,) + dims)
+    buf = torch.zeros(psi.size + 1, dtype=torch.complex64, device="cuda")
+    view = buf[1:].view((1,) + dims)
+    view.copy_(to_dev(psi))
+    with ffx.Plan(dims, dx, t, lam, form="tc") as plan:
+        rho = ffx.ffx_expand(plan, view).cpu().numpy()
+        assert plan.device_errors() == 0
+    e = rel_l2(rho, np.abs(O.expand_field(psi, dx, t, lam)) ** 2)
+    print(f"tc unaligned input: density {e:.2e}")
+    assert e < DENSITY_TOL
