@@ -436,7 +436,9 @@ def run_ffx(args):
     plan = ffx.Plan(w.dims, w.dx, w.t, w.lam, form=args.form)
     form = plan.form
     order = plan.pass_order()
-    launches = plan.launches_per_call()
+    launches = plan.launches_per_call(batch=B_)
+    fused_call = plan.fused and B_ <= plan.fused_max_batch  # all d passes in one launch
+    call_forms = plan.call_forms(B_)  # the kernel each axis runs at this batch
 
     # input pool larger than L2: distinct buffers, each step reads the next one
     step_in_bytes = B_ * M * 8
@@ -520,22 +522,49 @@ def run_ffx(args):
             per_pass[k].append(ev[i0].elapsed_time(ev[i0 + 1]))
     mean_ms = [statistics.mean(v) for v in per_pass]
     dom = max(range(launches), key=lambda k: mean_ms[k])
-    axis = order[dom]
-    N, lam = w.dims[axis], w.lam[axis]
-    lines = B_ * M // N
-    axis_form = plan.axis_forms[axis]
-    flops = pass_flops(N, lam, lines, axis_form)
     pk, pk_src = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     alu_peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
-    achieved = flops / (mean_ms[dom] * 1e-3) / 1e12
-    kernel_key = f"pass_{axis_form}_N{N}_lam{lam}_{args.workload}"
-    traffic = load_traffic(f"{axis_form}_N{N}")
-    # HBM view of the same launch: it reads and writes the batch once (complex64,
-    # the last pass writes float32 densities)
-    last = dom == launches - 1
-    bytes_launch = B_ * M * (8 + (4 if last else 8))
     hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+    if fused_call:
+        # one cooperative launch runs every pass (dense, FP32 SIMT); HBM sees
+        # the input read and the density written, the intermediates stay in L2
+        axis_form = "fused"
+        flops = sum(pass_flops(w.dims[j], w.lam[j], B_ * M // w.dims[j], "dense") for j in order)
+        kernel_key = f"fused_dense_{'x'.join(map(str, w.dims))}_{args.workload}"
+        traffic = load_traffic(f"fused_{'x'.join(map(str, w.dims))}")
+        bytes_launch = B_ * M * (8 + 4)
+        pass_names = ["fused_" + "_".join(f"axis{j}" for j in order)]
+    else:
+        axis = order[dom]
+        N, lam = w.dims[axis], w.lam[axis]
+        axis_form = call_forms[axis]
+        flops = pass_flops(N, lam, B_ * M // N, axis_form)
+        kernel_key = f"pass_{axis_form}_N{N}_lam{lam}_{args.workload}"
+        traffic = load_traffic(f"{axis_form}_N{N}")
+        # HBM view of the same launch: it reads and writes the batch once
+        # (complex64; the last pass writes float32 densities)
+        last = dom == launches - 1
+        bytes_launch = B_ * M * (8 + (4 if last else 8))
+        pass_names = [f"axis{order[k]}_N{w.dims[order[k]]}_lam{w.lam[order[k]]}_{call_forms[order[k]]}"
+                      for k in range(launches)]
+    achieved = flops / (mean_ms[dom] * 1e-3) / 1e12
+    if axis_form == "tc":
+        # split-TF32 contraction on the tensor cores: the sustained bf16 figure
+        # scaled by the nominal TF32 : BF16 dense ratio (1.1 : 2.25 PFLOP/s);
+        # `achieved` counts the algorithmic 8 N^2 flops per line, the tensor
+        # cores execute 3x that (three split products)
+        tc_peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1900.0))) * 1.1 / 2.25
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
+                    "frac": achieved / tc_peak, "traffic": traffic, "kernel": kernel_key,
+                    "launch_ms": mean_ms[dom], "executed_tflops": 3 * achieved,
+                    "peak_source": f"bf16_tflops_sustained x 1.1/2.25 (TF32 dense : BF16 dense, nominal), {pk_src}"}
+    else:
+        roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak,
+                    "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": traffic,
+                    "kernel": kernel_key, "launch_ms": mean_ms[dom],
+                    "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
+                                   f"(sm_max_mhz from MEASURED_PEAKS.json, {pk_src})"}
 
     value = args.steps * B_ * world / (ms * 1e-3)
 
@@ -592,7 +621,8 @@ def run_ffx(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "dims": list(w.dims), "dx": list(w.dx),
                        "lam": list(w.lam), "t": w.t, "batch_per_gpu": B_, "form": form,
-                       "axis_forms": list(plan.axis_forms),
+                       "axis_forms": list(plan.axis_forms), "call_forms": list(call_forms),
+                       "fused_one_launch": bool(fused_call),
                        "parallelism": f"replicas x{world} (realizations sharded, no collective)",
                        "l2": f"rotating pool of {pool_n} input buffers "
                              f"({pool_n * step_in_bytes / 2**20:.0f} MiB > 129 MB L2)"},
@@ -600,17 +630,12 @@ def run_ffx(args):
             "gpu_launches": launches * args.steps,
             "graph": f"K steps replayed as {len(graphs)} CUDA graph(s) of <= {GRAPH_STEPS} steps",
             "clocks": clocks,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak,
-                         "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": traffic,
-                         "kernel": kernel_key, "launch_ms": mean_ms[dom],
-                         "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
-                                        f"(sm_max_mhz from MEASURED_PEAKS.json, {pk_src})"},
+            "roofline": roofline,
             "roofline_hbm": {"bound": "hbm", "achieved": bytes_launch / (mean_ms[dom] * 1e-3) / 1e9,
                              "peak": hbm_peak, "unit": "GB/s",
                              "frac": bytes_launch / (mean_ms[dom] * 1e-3) / 1e9 / hbm_peak,
                              "note": f"of {pk_src} hbm_gbs; one read + one write of the batch"},
-            "pass_ms": {f"axis{order[k]}_N{w.dims[order[k]]}_lam{w.lam[order[k]]}_{plan.axis_forms[order[k]]}": mean_ms[k]
-                        for k in range(launches)},
+            "pass_ms": {pass_names[k]: mean_ms[k] for k in range(launches)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B_ * M * 8,
                     "d2h_bytes_per_step": B_ * M * 4},
             "cpu_baseline": cpu,

@@ -86,6 +86,12 @@ extern "C" {
  * out_density holds ([M_0..M_{d-1}], out += sum_b rho_b), instead of one
  * density per realization.  The sum runs over b in order (deterministic). */
 #define FFX_ACCUMULATE  0x10u
+/* Keep one launch per axis pass.  Without it, a plan with two or three axes
+ * that all take a dense form with at most 64 points runs ffx_expand and
+ * ffx_expand_field on small batches (ffx_plan_fused) as ONE cooperative
+ * launch (one block per SM, the d passes separated by grid-wide barriers,
+ * every T_j resident in shared memory); same arithmetic, same results. */
+#define FFX_UNFUSED     0x40u
 
 typedef struct ffx_plan_s* ffx_plan_t;
 
@@ -260,8 +266,22 @@ int ffx_plan_form(ffx_plan_t plan);
 int ffx_plan_axis_form(ffx_plan_t plan, int axis);
 
 /* Number of kernel launches one ffx_expand / ffx_expand_backward call makes
- * with a non-empty batch. */
+ * with a batch of one. */
 int ffx_launches_per_call(ffx_plan_t plan, int backward);
+
+/* The largest batch for which ffx_expand and ffx_expand_field run as one
+ * fused launch (see FFX_UNFUSED): a batch whose first pass has at most two
+ * 32-line tiles per SM.  0 if the plan never fuses, -1 for a NULL plan. */
+int64_t ffx_plan_fused(ffx_plan_t plan);
+
+/* The form whose kernel a forward call with this batch runs on lattice axis
+ * `axis`: the axis's form, except that under FFX_FORM_AUTO a dense axis whose
+ * pass covers at least 128 lines per SM runs on the tensor cores
+ * (FFX_FORM_TC; a 16-byte-misaligned buffer still takes the FP32 kernel).
+ * Results of the two kernels agree to rounding (within the FP32 tolerance),
+ * not bit for bit; explicit forms never switch.  -1 on a bad argument or a
+ * many-instance plan. */
+int ffx_plan_call_form(ffx_plan_t plan, int axis, int64_t batch);
 
 /* Forward pass order: writes the lattice axis of pass k to order[k],
  * k = 0..ndim-1.  The adjoint runs the same axes in reverse. */

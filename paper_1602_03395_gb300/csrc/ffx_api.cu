@@ -143,6 +143,10 @@ struct ffx_plan_s {
   void* dense_mem = nullptr;
   void* tc_mem = nullptr;    // split tensor-core operands + device error counter
   int* dev_err = nullptr;
+  unsigned* grid_bar = nullptr;  // arrival counter of the fused kernel's grid barriers
+  int64_t fused = 0;             // largest batch whose forward calls run as one launch (ffx_fused.cu)
+  int fused_grid = 0;
+  size_t fused_smem_bytes = 0;
   void* ws[2] = {nullptr, nullptr};  // workspace buffers (grown on demand)
   size_t ws_bytes[2] = {0, 0};
   ManyPlan* many = nullptr;       // set for plans over many instances
@@ -229,6 +233,12 @@ bool inplace_ok(const Axis& ax) {
 
 bool tc_capable(const Axis& ax) { return dense_tc_supported(ax.N) && ax.tc_t[0] != nullptr; }
 
+// The dense map's kernel for a pass over `lines` lines: FFX_FORM_TC or
+// FFX_FORM_DENSE.  An axis the plan's automatic choice gave the FP32 dense form
+// moves to the tensor cores when the pass fills every SM with 128-line tiles
+// (small passes are latency-bound there); explicit forms keep their kernel.
+int dense_kernel_for(const ffx_plan_s* p, const Axis& ax, int64_t lines);
+
 // The tensor-core kernel moves 16-byte vectors; other pointers take the SIMT dense kernels.
 bool tc_aligned(const void* in, const void* out_c, const void* out_d) {
   return ((uintptr_t)in & 15) == 0 && ((uintptr_t)out_c & 15) == 0 && ((uintptr_t)out_d & 15) == 0;
@@ -250,7 +260,9 @@ int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* 
     cudaEventRecordWithFlags((cudaEvent_t)p->trace[p->trace_i], stream, rec_flags);
   }
   cudaError_t e;
-  if (ax.form == FFX_FORM_TC && tc_aligned(in, out_c, out_d)) {
+  const int64_t lines = acc ? outer * inner : batch * outer * inner;
+  if ((ax.form == FFX_FORM_TC || ax.form == FFX_FORM_DENSE) && dense_kernel_for(p, ax, lines) == FFX_FORM_TC &&
+      tc_aligned(in, out_c, out_d)) {
     DenseArgs d;
     std::memset(&d, 0, sizeof(d));
     d.in = in;
@@ -387,6 +399,103 @@ int chain_into(ffx_plan_s* p, const int* axes, bool adjoint, const float2* in, c
                   0, batch, s);
     if (rc) return rc;
     cur = outs[r];
+  }
+  return FFX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// one-launch forward map of small lattices
+// ---------------------------------------------------------------------------
+
+// A plan fuses its forward passes when it has at least two axes, every axis
+// takes a dense form with at most 64 points (its shared-memory image exists),
+// the device runs cooperative launches, and one block of the fused kernel fits
+// on every SM; calls with batches up to p->fused use it.  FFX_UNFUSED keeps
+// the per-axis launches.
+int dense_kernel_for(const ffx_plan_s* p, const Axis& ax, int64_t lines) {
+  if (ax.form == FFX_FORM_TC) return tc_capable(ax) ? FFX_FORM_TC : FFX_FORM_DENSE;
+  if (ax.form == FFX_FORM_DENSE && (p->flags & FFX_FORM_MASK) == FFX_FORM_AUTO && tc_capable(ax) &&
+      lines >= 128 * (int64_t)p->sms)
+    return FFX_FORM_TC;
+  return ax.form;
+}
+
+int plan_fusion(ffx_plan_s* p) {
+  p->fused = 0;
+  if (p->ndim < 2 || (p->flags & FFX_UNFUSED) || !p->grid_bar) return FFX_OK;
+  int Ns[3];
+  for (int k = 0; k < p->ndim; ++k) {
+    const Axis& ax = p->axis[p->order[k]];
+    if (!(ax.form == FFX_FORM_DENSE || ax.form == FFX_FORM_TC) || !ax.img[0] || ax.N > kDenseInPlaceMaxN)
+      return FFX_OK;
+    Ns[k] = ax.N;
+  }
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, p->device);
+  if (!coop) return FFX_OK;
+  const size_t smem = fused_smem(Ns, p->ndim);
+  cudaError_t e = cudaFuncSetAttribute(fused_func(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_func(), fused_threads(), smem);
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return FFX_OK;
+  }
+  // Batches whose first pass has at most two 32-line tiles per block: beyond
+  // that the per-axis kernels (several blocks per SM) keep the ALUs busier.
+  const int64_t tiles = (p->M / Ns[0] + 31) / 32;
+  p->fused = std::max<int64_t>(1, 2 * (int64_t)p->sms / tiles);
+  p->fused_grid = p->sms;  // one block per SM (every block is resident: cooperative launch)
+  p->fused_smem_bytes = smem;
+  return FFX_OK;
+}
+
+// The forward map as one launch: pass k reads `in` (k = 0) or the workspace,
+// writes the workspace, and the last pass writes out_c, or out_d (a density,
+// summed over the batch with FFX_ACCUMULATE).
+int run_fused(ffx_plan_s* p, const float2* in, float2* out_c, float* out_d, int64_t batch, cudaStream_t stream) {
+  int rc;
+  if ((rc = ensure_ws(p, 0, batch))) return rc;
+  float2* ws = (float2*)p->ws[0];
+  FusedArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.npass = p->ndim;
+  a.M = p->M;
+  a.batch = batch;
+  a.bar = p->grid_bar;
+  a.err = p->dev_err;
+  int64_t off = 0;
+  for (int k = 0; k < p->ndim; ++k) {
+    const int j = p->order[k];
+    const Axis& ax = p->axis[j];
+    const bool last = k == p->ndim - 1;
+    FusedPass& P = a.pass[k];
+    axis_outer_inner(p, j, &P.outer, &P.inner);
+    P.in = k == 0 ? in : ws;
+    P.out_c = last ? out_c : ws;
+    P.out_d = last ? out_d : nullptr;
+    P.acc = (last && out_d) ? p->acc : 0;
+    P.ncols = P.acc ? P.outer * P.inner : batch * P.outer * P.inner;
+    P.N = ax.N;
+    P.img = ax.img[0];
+    P.img_off = (int)off;
+    off += (int64_t)ax.N * fused_img_stride();
+  }
+  a.img_floats2 = off;
+  const bool traced = p->trace && p->trace_i + 2 <= p->trace_n;
+  unsigned rec_flags = cudaEventRecordDefault;
+  if (traced) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+      rec_flags = cudaEventRecordExternal;
+    cudaEventRecordWithFlags((cudaEvent_t)p->trace[p->trace_i], stream, rec_flags);
+  }
+  cudaError_t e = launch_fused(a, p->fused_grid, p->fused_smem_bytes, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "fused launch");
+  if (traced) {
+    cudaEventRecordWithFlags((cudaEvent_t)p->trace[p->trace_i + 1], stream, rec_flags);
+    p->trace_i += 2;
   }
   return FFX_OK;
 }
@@ -550,7 +659,7 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
   if (ndim < 1 || ndim > 3) return fail(FFX_EINVAL, "ndim must be 1..3, got %d", ndim);
   if (!dims || !spacing || !magnification) return fail(FFX_EINVAL, "dims/spacing/magnification is NULL");
   if (!std::isfinite(t)) return fail(FFX_EINVAL, "t must be finite");
-  const uint32_t known = FFX_FORM_MASK | FFX_ACCUMULATE | FFX_TUNE;
+  const uint32_t known = FFX_FORM_MASK | FFX_ACCUMULATE | FFX_TUNE | FFX_UNFUSED;
   if (flags & ~known) return fail(FFX_EINVAL, "unknown flag bits 0x%x", flags & ~known);
   const uint32_t form = flags & FFX_FORM_MASK;
   if (form > FFX_FORM_TC) return fail(FFX_EINVAL, "unknown form %u", form);
@@ -748,6 +857,7 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
       rc = fail(FFX_ENOMEM, "tensor-core operands: %s", cudaGetErrorString(e));
     } else {
       p->dev_err = (int*)p->tc_mem;
+      p->grid_bar = (unsigned*)((char*)p->tc_mem + 64);
       cudaMemsetAsync(p->dev_err, 0, 256, s);
       unsigned char* tcur = (unsigned char*)p->tc_mem + 256;
       for (int j = 0; j < ndim && rc == FFX_OK; ++j) {
@@ -823,6 +933,7 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
       if (e != cudaSuccess) rc = cuda_fail(e, "tuning");
     }
   }
+  if (rc == FFX_OK) rc = plan_fusion(p);
   cudaStreamDestroy(s);
   if (rc != FFX_OK) {
     for (int w = 0; w < 2; ++w)
@@ -930,7 +1041,19 @@ int64_t ffx_workspace_bytes(ffx_plan_t p, int64_t batch) {
 
 int ffx_launches_per_call(ffx_plan_t p, int backward) {
   if (!p) return -1;
+  if (p->fused >= 1 && !backward) return 1;
   return backward ? 2 * p->ndim : p->ndim;  // many-plans: one persistent kernel per phase
+}
+
+int64_t ffx_plan_fused(ffx_plan_t p) { return p ? p->fused : -1; }
+
+int ffx_plan_call_form(ffx_plan_t p, int axis, int64_t batch) {
+  if (!p || p->many || axis < 0 || axis >= p->ndim || batch < 1) return -1;
+  if (batch <= p->fused) return FFX_FORM_DENSE;  // the fused kernel: FP32 dense
+  int64_t outer, inner;
+  axis_outer_inner(p, axis, &outer, &inner);
+  const int64_t lines = (p->acc && axis == p->order[p->ndim - 1] ? 1 : batch) * outer * inner;
+  return dense_kernel_for(p, p->axis[axis], lines);
 }
 
 int ffx_expand(ffx_plan_t p, const void* psi0, int64_t batch, float* out_density, void* stream) {
@@ -946,6 +1069,7 @@ int ffx_expand(ffx_plan_t p, const void* psi0, int64_t batch, float* out_density
     rc = many_expand(p->many, psi0, out_density, nullptr, s, &err);
     return rc ? fail(rc, "%s", err.c_str()) : FFX_OK;
   }
+  if (batch <= p->fused) return run_fused(p, (const float2*)psi0, nullptr, out_density, batch, s);
   const int d = p->ndim;
   const float2* cur = (const float2*)psi0;
   if (d > 1) {
@@ -981,6 +1105,8 @@ int ffx_expand_field(ffx_plan_t p, const void* psi0, int64_t batch, void* out_fi
     rc = many_expand(p->many, psi0, nullptr, out_field, (cudaStream_t)stream, &err);
     return rc ? fail(rc, "%s", err.c_str()) : FFX_OK;
   }
+  if (batch <= p->fused)
+    return run_fused(p, (const float2*)psi0, (float2*)out_field, nullptr, batch, (cudaStream_t)stream);
   return chain_into(p, p->order, false, (const float2*)psi0, nullptr, 0, batch, (float2*)out_field, 0,
                     (cudaStream_t)stream);
 }

@@ -117,6 +117,30 @@ cudaError_t launch_dense_tc(const DenseArgs& a, const unsigned char* Tblk, int* 
 int64_t dense_tc_tiles(int N, int64_t ncols);
 cudaError_t launch_tc_build_t(const float2* T, unsigned char* Tblk, int N, cudaStream_t s);
 cudaError_t launch_identity(float2* I, int N, cudaStream_t s);
+
+// The d passes of a small lattice (every axis <= 64 points, dense form) in one
+// cooperative launch with grid-wide barriers between the passes (ffx_fused.cu).
+struct FusedPass {
+  const float2* in;   // the pass's input lines
+  float2* out_c;      // complex output (the workspace, or the caller's field)
+  float* out_d;       // density output of the last pass, or null
+  const float2* img;  // T_j's shared-memory image in global memory ([N][65])
+  int64_t outer, inner, ncols;
+  int N, acc, img_off;  // img_off: position of the image in shared memory (float2 units)
+};
+struct FusedArgs {
+  FusedPass pass[3];
+  int npass;
+  int64_t M, batch;
+  int64_t img_floats2;  // sum of the images (Bs follows them in shared memory)
+  unsigned* bar;        // [2]: grid-barrier arrivals, blocks done (the last block resets both)
+  int* err;
+};
+size_t fused_smem(const int* N, int npass);
+int fused_img_stride();
+const void* fused_func();
+int fused_threads();
+cudaError_t launch_fused(const FusedArgs& a, int grid, size_t smem, cudaStream_t stream);
 cudaError_t launch_dense_build(const float2* O, float2* T, float2* TH, int N, cudaStream_t s);
 
 // Plans over many instances (ffx_many.cu).

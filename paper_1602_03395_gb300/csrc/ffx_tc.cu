@@ -53,16 +53,22 @@ namespace {
 constexpr int LINES = 128;         // lines per item = MMA M = tensor-memory lanes
 constexpr int ROWS = 128;          // real output rows per item = MMA N
 constexpr int TKC = 32;            // real K per chunk
-constexpr int TSTAGES = 3;
+constexpr int TSTAGES = 2;
 constexpr int CORE_LBO = 128;      // bytes between core matrices along K
 constexpr int CHUNK_SBO = (TKC / 4) * 128;  // 1024: between 8-row groups of a chunk
 constexpr int T_PART = ROWS * TKC * 4;      // 16 KB per split part
 constexpr int X_PART = LINES * TKC * 4;     // 16 KB per split part
 constexpr int T_CHUNK = 2 * T_PART;         // head + tail, one bulk copy
 constexpr int STAGE_BYTES = T_CHUNK + 2 * X_PART;  // 64 KB
-constexpr int TC_SMEM = TSTAGES * STAGE_BYTES;
-constexpr int ACC_SMEM = (ROWS / 2) * 128 * 4;  // |.|^2 sums over the batch, [row][line]
 constexpr int NPROD = 128, NEPI = 128;
+constexpr int RAW = 4;                        // input chunks in flight per producer thread
+constexpr int RAW_CHUNK = NPROD * 8 * 16;     // 16 KB: 8 x 16 bytes per producer thread
+constexpr int GRAD_CHUNK = NPROD * 8 * 8;     // 8 KB of gradient factors (backward passes)
+constexpr int TC_SMEM = TSTAGES * STAGE_BYTES + RAW * RAW_CHUNK;  // 192 KB
+// accumulating launches: |.|^2 sums over the batch, [row][line]; backward
+// launches: the gradient ring (the two never meet in one launch)
+constexpr int EXTRA_SMEM = (ROWS / 2) * 128 * 4;
+static_assert(RAW * GRAD_CHUNK <= EXTRA_SMEM, "gradient ring");
 constexpr int NTHREADS = NPROD + 32 + NEPI;  // 288
 constexpr int ACC_COLS = 4 * ROWS;           // two buffers x (head product, cross terms): all 512
 constexpr long long kSpinLimit = 1ll << 22;
@@ -166,6 +172,16 @@ __device__ __forceinline__ void line_ref(const DenseArgs& a, int64_t c, int b, l
   }
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void split_store(unsigned char* xh, unsigned char* xl, int off, float4 v) {
   const float4 hi = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
   const float4 lo = make_float4(tf32_round(v.x - hi.x), tf32_round(v.y - hi.y), tf32_round(v.z - hi.z),
@@ -223,112 +239,143 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp < 4) {
     // ---------------- producers ----------------
     const int t = tid;
-    int64_t g = 0;  // chunks produced
-    bool ok = true;
-    for (int64_t it = 0; ok && it < my_items; ++it) {
-      const int64_t w = blockIdx.x + it * gridDim.x;
-      const int mt = (int)(w % mtiles);
-      const int64_t ct = w / mtiles;
-      for (int b = 0; ok && b < nb; ++b) {
-        // contiguous lines: thread t loads k-pairs (t>>3)&3 and +4 of the 4 lines
-        // (t&7) + 8 (t>>5) + 32 j; strided lines: k-pairs 0..7 of line t
-        long long lb[4];
-        int lbr[4];
-        if (contiguous) {
-#pragma unroll
-          for (int j = 0; j < 4; ++j) line_ref(a, ct * LINES + (t & 7) + 8 * (t >> 5) + 32 * j, b, lb[j], lbr[j]);
-        } else {
-          line_ref(a, ct * LINES + t, b, lb[0], lbr[0]);
-        }
-        for (int kc = 0; kc < kchunks; ++kc, ++g) {
-          const int s = (int)(g % TSTAGES);
-          const int64_t u = g / TSTAGES;
-          if (u >= 1 && !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)((u - 1) & 1), &s_abort)) {
-            ok = false;
-            break;
-          }
-          unsigned char* st = tsm + s * STAGE_BYTES;
-          if (t == 0) {
-            const uint32_t cb = smem_u32(&copy_bar[s]);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cb), "r"(T_CHUNK)
-                         : "memory");
-            const unsigned char* src = Tblk + ((size_t)mt * kchunks + kc) * T_CHUNK;
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    smem_base + s * STAGE_BYTES),
-                "l"(src), "r"(T_CHUNK), "r"(cb)
-                : "memory");
-          }
-          unsigned char* xh = st + T_CHUNK;
-          unsigned char* xl = xh + X_PART;
-          float4 v[8];
+    unsigned char* raw = tsm + TSTAGES * STAGE_BYTES;  // RAW chunks of this thread's inputs
+    unsigned char* graw = tsm + TC_SMEM;               // and of its gradient factors (backward)
+    const int64_t total = my_items * nb * kchunks;     // chunks of this block, in order
+    // issue side: chunk ci = (iit, ib, ikc), RAW - 1 ahead of the consumer
+    int64_t ci = 0, iit = 0;
+    int ib = 0, ikc = 0;
+    long long lb[4];
+    int lbr[4];
+    bool lines_ok = false;
+    auto issue = [&]() {
+      if (ci < total) {
+        if (!lines_ok) {
+          const int64_t ct = (blockIdx.x + iit * gridDim.x) / mtiles;
           if (contiguous) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const int j = i >> 1;
-              const int kp = ((t >> 3) & 3) + 4 * (i & 1);
-              v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-              if (lb[j] >= 0) v[i] = *reinterpret_cast<const float4*>(a.in + lb[j] + kc * 16 + 2 * kp);
-            }
+            for (int j = 0; j < 4; ++j)
+              line_ref(a, ct * LINES + (t & 7) + 8 * (t >> 5) + 32 * j, ib, lb[j], lbr[j]);
           } else {
+            line_ref(a, ct * LINES + t, ib, lb[0], lbr[0]);
+          }
+          lines_ok = true;
+        }
+        const int slot = (int)(ci % RAW);
+        const uint32_t dst0 = smem_u32(raw + slot * RAW_CHUNK) + (uint32_t)t * 16;
+        const uint32_t gdst0 = smem_u32(graw + slot * GRAD_CHUNK) + (uint32_t)t * 8;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-              if (lb[0] >= 0) {
-                const int64_t addr = lb[0] + (int64_t)(kc * 16 + 2 * i) * inner;
-                const float2 p0 = a.in[addr];  // plain loads: N = 64 passes may run in place
-                const float2 p1 = a.in[addr + inner];
-                v[i] = make_float4(p0.x, p0.y, p1.x, p1.y);
-              }
-            }
+        for (int i = 0; i < 8; ++i) {
+          const uint32_t dst = dst0 + (uint32_t)(i * NPROD * 16);
+          long long lbi;
+          int bri, kp;
+          if (contiguous) {
+            lbi = (i < 2) ? lb[0] : (i < 4) ? lb[1] : (i < 6) ? lb[2] : lb[3];
+            bri = (i < 2) ? lbr[0] : (i < 4) ? lbr[1] : (i < 6) ? lbr[2] : lbr[3];
+            kp = ((t >> 3) & 3) + 4 * (i & 1);
+          } else {
+            lbi = lb[0];
+            bri = lbr[0];
+            kp = i;
+          }
+          const bool valid = lbi >= 0;
+          const int64_t addr = valid ? lbi + (int64_t)(ikc * 16 + 2 * kp) * inner : 0;
+          // invalid lines read nothing and land as zeros (source size 0)
+          if (contiguous) {
+            cp_async16(dst, a.in + addr, valid ? 16 : 0);
+          } else {
+            cp_async8(dst, a.in + addr, valid ? 8 : 0);
+            cp_async8(dst + 8, a.in + addr + (valid ? inner : 0), valid ? 8 : 0);
           }
           if (a.grad) {
-            // the input element is 2 grad * psi (grad shared by the realizations or not)
+            const int64_t gaddr = valid && a.grad_shared ? addr - (int64_t)bri * a.M : addr;
+            const uint32_t gdst = gdst0 + (uint32_t)(i * NPROD * 8);
+            cp_async4(gdst, a.grad + gaddr, valid ? 4 : 0);
+            cp_async4(gdst + 4, a.grad + gaddr + (valid ? inner : 0), valid ? 4 : 0);
+          }
+        }
+        ++ci;
+        if (++ikc == kchunks) {
+          ikc = 0;
+          lines_ok = false;
+          if (++ib == nb) {
+            ib = 0;
+            ++iit;
+          }
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");  // one group per call, empty past the end
+    };
+#pragma unroll 1
+    for (int r = 0; r < RAW - 1; ++r) issue();
+    // consumer side: chunk c = (it, kc) of the sequence
+    int64_t it = 0;
+    int b = 0, kc = 0;
+    int mt = (int)(blockIdx.x % mtiles);
+    int last_u[TSTAGES];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              long long lbi;
-              int bri, kp;
-              if (contiguous) {
-                lbi = (i < 2) ? lb[0] : (i < 4) ? lb[1] : (i < 6) ? lb[2] : lb[3];
-                bri = (i < 2) ? lbr[0] : (i < 4) ? lbr[1] : (i < 6) ? lbr[2] : lbr[3];
-                kp = ((t >> 3) & 3) + 4 * (i & 1);
-              } else {
-                lbi = lb[0];
-                bri = lbr[0];
-                kp = i;
-              }
-              if (lbi < 0) continue;
-              int64_t addr = lbi + (int64_t)(kc * 16 + 2 * kp) * inner;
-              if (a.grad_shared) addr -= (int64_t)bri * a.M;
-              const float g0 = 2.f * __ldg(a.grad + addr);
-              const float g1 = 2.f * __ldg(a.grad + addr + inner);
-              v[i].x *= g0;
-              v[i].y *= g0;
-              v[i].z *= g1;
-              v[i].w *= g1;
-            }
-          }
+    for (int q = 0; q < TSTAGES; ++q) last_u[q] = -1;
+#pragma unroll 1
+    for (int64_t c = 0; c < total; ++c) {
+      issue();
+      asm volatile("cp.async.wait_group %0;" ::"n"(RAW - 1) : "memory");  // chunk c has landed
+      const int s = (int)(c % TSTAGES);
+      const int64_t u = c / TSTAGES;
+      if (u >= 1 && !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)((u - 1) & 1), &s_abort)) break;
+      unsigned char* st = tsm + s * STAGE_BYTES;
+      if (t == 0) {
+        const uint32_t cb = smem_u32(&copy_bar[s]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cb), "r"(T_CHUNK) : "memory");
+        const unsigned char* src = Tblk + ((size_t)mt * kchunks + kc) * T_CHUNK;
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_base + s * STAGE_BYTES),
+            "l"(src), "r"(T_CHUNK), "r"(cb)
+            : "memory");
+        last_u[s] = (int)(u & 1);
+      }
+      const int slot = (int)(c % RAW);
+      const unsigned char* rs = raw + slot * RAW_CHUNK + t * 16;
+      const unsigned char* gs = graw + slot * GRAD_CHUNK + t * 8;
+      unsigned char* xh = st + T_CHUNK;
+      unsigned char* xl = xh + X_PART;
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            int n, kp;
-            if (contiguous) {
-              n = (t & 7) + 8 * (t >> 5) + 32 * (i >> 1);
-              kp = ((t >> 3) & 3) + 4 * (i & 1);
-            } else {
-              n = t;
-              kp = i;
-            }
-            split_store(xh, xl, (n >> 3) * CHUNK_SBO + kp * CORE_LBO + (n & 7) * 16, v[i]);
-          }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          if (t == 0 && !mbar_wait_own(smem_u32(&copy_bar[s]), (uint32_t)(u & 1), &s_abort)) {
-            ok = false;
-            break;
-          }
-          mbar_arrive(smem_u32(&full_bar[s]));
+      for (int i = 0; i < 8; ++i) {
+        float4 v = *reinterpret_cast<const float4*>(rs + i * NPROD * 16);
+        if (a.grad) {
+          // the input element is 2 grad * psi
+          const float2 gg = *reinterpret_cast<const float2*>(gs + i * NPROD * 8);
+          v.x *= 2.f * gg.x;
+          v.y *= 2.f * gg.x;
+          v.z *= 2.f * gg.y;
+          v.w *= 2.f * gg.y;
+        }
+        int n, kp;
+        if (contiguous) {
+          n = (t & 7) + 8 * (t >> 5) + 32 * (i >> 1);
+          kp = ((t >> 3) & 3) + 4 * (i & 1);
+        } else {
+          n = t;
+          kp = i;
+        }
+        split_store(xh, xl, (n >> 3) * CHUNK_SBO + kp * CORE_LBO + (n & 7) * 16, v);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(smem_u32(&full_bar[s]));
+      if (++kc == kchunks) {
+        kc = 0;
+        if (++b == nb) {
+          b = 0;
+          ++it;
+          mt = (int)((blockIdx.x + it * gridDim.x) % mtiles);
         }
       }
     }
+    // nothing of this thread's may still be in flight at exit
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (t == 0)
+      for (int q = 0; q < TSTAGES; ++q)
+        if (last_u[q] >= 0) mbar_wait_own(smem_u32(&copy_bar[q]), (uint32_t)last_u[q], &s_abort);
   } else if (warp == 4) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
@@ -347,7 +394,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           for (int kc = 0; kc < kchunks; ++kc, ++g) {
             const int s = (int)(g % TSTAGES);
             const int64_t u = g / TSTAGES;
-            if (!mbar_wait(smem_u32(&full_bar[s]), (uint32_t)(u & 1), &s_abort)) {
+            if (!mbar_wait(smem_u32(&copy_bar[s]), (uint32_t)(u & 1), &s_abort) ||
+                !mbar_wait(smem_u32(&full_bar[s]), (uint32_t)(u & 1), &s_abort)) {
               ok = false;
               break;
             }
@@ -507,13 +555,14 @@ __global__ void tc_build_t_kernel(const float2* __restrict__ T, unsigned char* _
 }  // namespace
 
 bool dense_tc_supported(int N) { return N >= 64 && N <= kDenseMaxN && N % 64 == 0; }
-size_t dense_tc_smem() { return (size_t)(TC_SMEM + ACC_SMEM); }
+size_t dense_tc_smem() { return (size_t)(TC_SMEM + EXTRA_SMEM); }
 const void* dense_tc_func() { return (const void*)dense_tc_kernel; }
 size_t dense_tc_t_bytes(int N) { return (size_t)(2 * N) * (2 * N) * 8; }
 
 cudaError_t launch_dense_tc(const DenseArgs& a, const unsigned char* Tblk, int* err, int grid,
                             cudaStream_t stream) {
-  dense_tc_kernel<<<grid, NTHREADS, TC_SMEM + (a.acc ? ACC_SMEM : 0), stream>>>(a, Tblk, err);
+  const int smem = TC_SMEM + ((a.acc || a.grad) ? EXTRA_SMEM : 0);
+  dense_tc_kernel<<<grid, NTHREADS, smem, stream>>>(a, Tblk, err);
   return cudaGetLastError();
 }
 

@@ -25,6 +25,7 @@ FFX_OK, FFX_EINVAL, FFX_ENOMEM, FFX_ECUDA, FFX_EUNSUPPORTED = 0, 1, 2, 3, 4
 FFX_FORM_AUTO, FFX_FORM_PAPER, FFX_FORM_FOLD, FFX_FORM_DENSE, FFX_FORM_TC = 0x0, 0x1, 0x2, 0x3, 0x4
 FFX_ACCUMULATE = 0x10
 FFX_TUNE = 0x20
+FFX_UNFUSED = 0x40
 
 _FORMS = {"auto": FFX_FORM_AUTO, "paper": FFX_FORM_PAPER, "fold": FFX_FORM_FOLD, "dense": FFX_FORM_DENSE,
           "tc": FFX_FORM_TC}
@@ -80,6 +81,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ffx_plan_axis_form.restype = i32
     lib.ffx_launches_per_call.argtypes = [vp, i32]
     lib.ffx_launches_per_call.restype = i32
+    lib.ffx_plan_fused.argtypes = [vp]
+    lib.ffx_plan_fused.restype = i64
+    lib.ffx_plan_call_form.argtypes = [vp, i32, i64]
+    lib.ffx_plan_call_form.restype = i32
     lib.ffx_plan_pass_order.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
     lib.ffx_plan_pass_order.restype = i32
     lib.ffx_plan_trace.argtypes = [vp, ctypes.POINTER(vp), i64]
@@ -139,7 +144,7 @@ class Plan:
     """A plan for one geometry (dims, spacing, t, magnification, offsets)."""
 
     def __init__(self, dims, spacing, t, magnification, a=None, abar=None,
-                 form: str = "auto", accumulate: bool = False, tune: bool = False):
+                 form: str = "auto", accumulate: bool = False, tune: bool = False, fused: bool = True):
         lib = load_library()
         d = len(dims)
         self.dims = tuple(int(v) for v in dims)
@@ -147,7 +152,8 @@ class Plan:
         self.t = float(t)
         self.magnification = tuple(int(v) for v in magnification)
         self.accumulate = bool(accumulate)
-        flags = _FORMS[form] | (FFX_ACCUMULATE if accumulate else 0) | (FFX_TUNE if tune else 0)
+        flags = (_FORMS[form] | (FFX_ACCUMULATE if accumulate else 0) | (FFX_TUNE if tune else 0)
+                 | (0 if fused else FFX_UNFUSED))
         arr = lambda ct, v: (ct * d)(*v) if v is not None else None  # noqa: E731
         h = ctypes.c_void_p()
         _check(lib.ffx_plan(ctypes.byref(h), d, arr(ctypes.c_int64, self.dims),
@@ -157,6 +163,9 @@ class Plan:
         self._h = h
         self.form = _FORM_NAMES[lib.ffx_plan_form(h)]
         self.axis_forms = tuple(_FORM_NAMES[lib.ffx_plan_axis_form(h, j)] for j in range(d))
+        # largest batch whose forward calls run as one launch (0: never)
+        self.fused_max_batch = int(lib.ffx_plan_fused(h))
+        self.fused = self.fused_max_batch >= 1
         self.M = 1
         for v in self.dims:
             self.M *= v
@@ -192,8 +201,15 @@ class Plan:
     def workspace_bytes(self, batch: int) -> int:
         return int(load_library().ffx_workspace_bytes(self.handle, batch))
 
-    def launches_per_call(self, backward: bool = False) -> int:
+    def launches_per_call(self, backward: bool = False, batch: int = 1) -> int:
+        if not backward and self.fused and batch > self.fused_max_batch:
+            return len(self.dims)
         return int(load_library().ffx_launches_per_call(self.handle, int(backward)))
+
+    def call_forms(self, batch: int = 1):
+        """Per lattice axis, the form whose kernel a forward call with this batch runs."""
+        return tuple(_FORM_NAMES[load_library().ffx_plan_call_form(self.handle, j, batch)]
+                     for j in range(len(self.dims)))
 
     def pass_order(self):
         order = (ctypes.c_int32 * len(self.dims))()
@@ -256,6 +272,7 @@ class PlanMany(Plan):
         self.instances = [tuple(tuple(x) if hasattr(x, "__len__") else x for x in spec[:4]) for spec in instances]
         self.points = int(lib.ffx_plan_points(h))
         self.offsets = [int(lib.ffx_plan_many_offset(h, i)) for i in range(n)]
+        self.fused, self.fused_max_batch = False, 0
         self.dims = (self.points,)
         self.M = self.points
 
