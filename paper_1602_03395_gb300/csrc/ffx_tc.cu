@@ -9,28 +9,30 @@
 // part p of IN[k].  The MMA runs transposed, D[line][row] = sum_K X[line][K]
 // T[row][K], so that tensor-memory lane = line and each epilogue thread owns
 // one line's outputs (coalesced stores along either memory order).  Each FP32
-// operand is split into a TF32 head and tail (hi = rna_tf32(x), lo =
-// rna_tf32(x - hi)); X_hi T_hi accumulates in one FP32 tensor-memory
-// accumulator and the cross terms X_hi T_lo + X_lo T_hi in a second one, added
-// in the epilogue (the dropped lo*lo term is ~2^-22 relative).  The tensor
-// cores' FP32 accumulation rounds with a bias, so its error grows with the
-// number of MMAs into one accumulator; keeping the small cross terms apart
-// leaves the large one N/4 accumulation steps instead of 3N/4.
+// operand is split into a TF32 head and tail: T at plan time (hi =
+// rna_tf32(t), lo = rna_tf32(t - hi)), the input on the fly (head = the TF32
+// bits of x, tail = x - head, exact).  X_hi T_hi accumulates in one FP32
+// tensor-memory accumulator and the cross terms X_hi T_lo + X_lo T_hi in a
+// second one, added in the epilogue (the dropped lo*lo term is ~2^-22
+// relative).  The tensor cores' FP32 accumulation rounds with a bias, so its
+// error grows with the number of MMAs into one accumulator; keeping the small
+// cross terms apart leaves the large one N/4 accumulation steps instead of
+// 3N/4.
 //
-// Kernel: one persistent block of 288 threads per SM, warp-specialised.
-//  * warps 0-3 (producers), per K chunk of 32 real K: thread 0 starts a bulk
+// Kernel: one persistent block of 416 threads per SM, warp-specialised.
+//  * warps 0-7 (producers), per K chunk of 32 real K: thread 0 starts a bulk
 //    (TMA) copy of the pre-split T chunk (128 rows x 32 K, head and tail,
 //    stored in global memory already in the tensor cores' K-major no-swizzle
-//    core-matrix order); all 128 threads load the item's 128 lines x 16
-//    complex inputs (16-byte loads), split them and store them in the same
-//    order (bank-conflict free); they arrive on the stage's "full" barrier.
-//    Thread 0 arrives only after its own copy has landed, so a stage is full
-//    when both halves are in shared memory, and no copy is ever left in flight.
-//  * warp 4 (MMA): per chunk, 4 K-steps x 3 products of tcgen05.mma
-//    (M = 128 lines, N = 128 rows, K = 8, kind::tf32) into one of two tensor-
-//    memory accumulator pairs; tcgen05.commit releases the stage ("empty") and,
-//    after a sub-tile's last chunk, hands the accumulator on ("acc_full").
-//  * warps 5-8 (epilogue): read their 32-lane quarter of the accumulator
+//    core-matrix order) on the stage's "copy" barrier; every producer thread
+//    keeps RAW - 1 chunks of its share of the input (16-byte cp.async) in
+//    flight in a ring, splits the chunk that has landed into the stage (same
+//    core-matrix order, bank-conflict free) and arrives on "full".
+//  * warp 8 (MMA): waits "copy" and "full", issues 4 K-steps x 3 products of
+//    tcgen05.mma (M = 128 lines, N = 128 rows, K = 8, kind::tf32) into one of
+//    two tensor-memory accumulator pairs; tcgen05.commit releases the stage
+//    ("empty") and, after a sub-tile's last chunk, hands the accumulator on
+//    ("acc_full").
+//  * warps 9-12 (epilogue): read their 32-lane quarter of the accumulator
 //    (tcgen05.ld), store complex64 or |.|^2 (or add |.|^2 over the batch in
 //    shared memory), and arrive on "acc_empty".
 // Work items are (128 lines, 128 real rows) of the output, rows fastest
@@ -39,9 +41,9 @@
 // not run in place.
 //
 // Every wait is bounded; a wait that runs out sets a block-wide abort flag
-// (every other wait then gives up at once), the MMA thread waits (bounded)
-// for its own tensor-core work, the block frees its tensor memory, counts an
-// error in `err` and exits.
+// (every other wait then gives up at once); producers drain their own copies,
+// the MMA thread waits (bounded) for its own tensor-core work, the block frees
+// its tensor memory, counts an error in `err` and exits.
 #include <cstring>
 
 #include "ffx_internal.h"
@@ -60,16 +62,18 @@ constexpr int T_PART = ROWS * TKC * 4;      // 16 KB per split part
 constexpr int X_PART = LINES * TKC * 4;     // 16 KB per split part
 constexpr int T_CHUNK = 2 * T_PART;         // head + tail, one bulk copy
 constexpr int STAGE_BYTES = T_CHUNK + 2 * X_PART;  // 64 KB
-constexpr int NPROD = 128, NEPI = 128;
+constexpr int NPROD = 256, NEPI = 128;
+constexpr int PITEMS = LINES * (TKC / 4) / NPROD;  // 16-byte input items per producer thread per chunk
 constexpr int RAW = 4;                        // input chunks in flight per producer thread
-constexpr int RAW_CHUNK = NPROD * 8 * 16;     // 16 KB: 8 x 16 bytes per producer thread
-constexpr int GRAD_CHUNK = NPROD * 8 * 8;     // 8 KB of gradient factors (backward passes)
+constexpr int RAW_CHUNK = NPROD * PITEMS * 16;  // 16 KB
+constexpr int GRAD_CHUNK = NPROD * PITEMS * 8;  // 8 KB of gradient factors (backward passes)
 constexpr int TC_SMEM = TSTAGES * STAGE_BYTES + RAW * RAW_CHUNK;  // 192 KB
 // accumulating launches: |.|^2 sums over the batch, [row][line]; backward
 // launches: the gradient ring (the two never meet in one launch)
 constexpr int EXTRA_SMEM = (ROWS / 2) * 128 * 4;
 static_assert(RAW * GRAD_CHUNK <= EXTRA_SMEM, "gradient ring");
-constexpr int NTHREADS = NPROD + 32 + NEPI;  // 288
+constexpr int NTHREADS = NPROD + 32 + NEPI;  // 416
+constexpr int MMA_WARP = NPROD / 32;         // warp 8; warps 9-12 are the epilogue
 constexpr int ACC_COLS = 4 * ROWS;           // two buffers x (head product, cross terms): all 512
 constexpr long long kSpinLimit = 1ll << 22;
 
@@ -182,10 +186,14 @@ __device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, int byt
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
 }
 
+// Input split: the head keeps the TF32 bits of x (the 13 low mantissa bits
+// cleared), the tail x - head is exact in FP32 and carries <= 13 significant
+// bits, of which the TF32 operand keeps 11: |error| <= 2^-22 |x|.
+__device__ __forceinline__ float tf32_head(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
+
 __device__ __forceinline__ void split_store(unsigned char* xh, unsigned char* xl, int off, float4 v) {
-  const float4 hi = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
-  const float4 lo = make_float4(tf32_round(v.x - hi.x), tf32_round(v.y - hi.y), tf32_round(v.z - hi.z),
-                                tf32_round(v.w - hi.w));
+  const float4 hi = make_float4(tf32_head(v.x), tf32_head(v.y), tf32_head(v.z), tf32_head(v.w));
+  const float4 lo = make_float4(v.x - hi.x, v.y - hi.y, v.z - hi.z, v.w - hi.w);
   *reinterpret_cast<float4*>(xh + off) = hi;
   *reinterpret_cast<float4*>(xl + off) = lo;
 }
@@ -210,7 +218,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int64_t inner = a.inner;
   const bool contiguous = (inner == 1);
 
-  if (warp == 4) {
+  if (warp == MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"(ACC_COLS)
                  : "memory");
@@ -236,7 +244,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t tmem = tmem_slot;
   const uint32_t smem_base = smem_u32(tsm);
 
-  if (warp < 4) {
+  if (warp < MMA_WARP) {
     // ---------------- producers ----------------
     const int t = tid;
     unsigned char* raw = tsm + TSTAGES * STAGE_BYTES;  // RAW chunks of this thread's inputs
@@ -245,8 +253,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // issue side: chunk ci = (iit, ib, ikc), RAW - 1 ahead of the consumer
     int64_t ci = 0, iit = 0;
     int ib = 0, ikc = 0;
-    long long lb[4];
-    int lbr[4];
+    long long lb[2];
+    int lbr[2];
     bool lines_ok = false;
     auto issue = [&]() {
       if (ci < total) {
@@ -254,10 +262,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int64_t ct = (blockIdx.x + iit * gridDim.x) / mtiles;
           if (contiguous) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-              line_ref(a, ct * LINES + (t & 7) + 8 * (t >> 5) + 32 * j, ib, lb[j], lbr[j]);
+            for (int j = 0; j < 2; ++j)
+              line_ref(a, ct * LINES + (t & 7) + 8 * (t >> 5) + 64 * j, ib, lb[j], lbr[j]);
           } else {
-            line_ref(a, ct * LINES + t, ib, lb[0], lbr[0]);
+            line_ref(a, ct * LINES + (t & (LINES - 1)), ib, lb[0], lbr[0]);
           }
           lines_ok = true;
         }
@@ -265,18 +273,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const uint32_t dst0 = smem_u32(raw + slot * RAW_CHUNK) + (uint32_t)t * 16;
         const uint32_t gdst0 = smem_u32(graw + slot * GRAD_CHUNK) + (uint32_t)t * 8;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < PITEMS; ++i) {
           const uint32_t dst = dst0 + (uint32_t)(i * NPROD * 16);
           long long lbi;
           int bri, kp;
           if (contiguous) {
-            lbi = (i < 2) ? lb[0] : (i < 4) ? lb[1] : (i < 6) ? lb[2] : lb[3];
-            bri = (i < 2) ? lbr[0] : (i < 4) ? lbr[1] : (i < 6) ? lbr[2] : lbr[3];
+            lbi = (i < 2) ? lb[0] : lb[1];
+            bri = (i < 2) ? lbr[0] : lbr[1];
             kp = ((t >> 3) & 3) + 4 * (i & 1);
           } else {
             lbi = lb[0];
             bri = lbr[0];
-            kp = i;
+            kp = (t >> 7) * PITEMS + i;
           }
           const bool valid = lbi >= 0;
           const int64_t addr = valid ? lbi + (int64_t)(ikc * 16 + 2 * kp) * inner : 0;
@@ -340,7 +348,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       unsigned char* xh = st + T_CHUNK;
       unsigned char* xl = xh + X_PART;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
+      for (int i = 0; i < PITEMS; ++i) {
         float4 v = *reinterpret_cast<const float4*>(rs + i * NPROD * 16);
         if (a.grad) {
           // the input element is 2 grad * psi
@@ -352,11 +360,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         int n, kp;
         if (contiguous) {
-          n = (t & 7) + 8 * (t >> 5) + 32 * (i >> 1);
+          n = (t & 7) + 8 * (t >> 5) + 64 * (i >> 1);
           kp = ((t >> 3) & 3) + 4 * (i & 1);
         } else {
-          n = t;
-          kp = i;
+          n = t & (LINES - 1);
+          kp = (t >> 7) * PITEMS + i;
         }
         split_store(xh, xl, (n >> 3) * CHUNK_SBO + kp * CORE_LBO + (n & 7) * 16, v);
       }
@@ -376,7 +384,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (t == 0)
       for (int q = 0; q < TSTAGES; ++q)
         if (last_u[q] >= 0) mbar_wait_own(smem_u32(&copy_bar[q]), (uint32_t)last_u[q], &s_abort);
-  } else if (warp == 4) {
+  } else if (warp == MMA_WARP) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       int64_t g = 0, sub = 0;
@@ -520,7 +528,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (tid == 0 && s_abort) atomicAdd(err, 1);
-  if (warp == 4) {
+  if (warp == MMA_WARP) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ACC_COLS) : "memory");
   }
