@@ -290,7 +290,8 @@ def scipy_baseline(w, budget_s=8.0, dtype=np.complex64):
 
 def load_traffic(kernel_key: str):
     """Per-launch DRAM bytes of the dominant kernel from the committed ncu
-    summary, if it was taken on the current sources; else None."""
+    summary, if it was taken on the kernel's current sources (the files the
+    record names); else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
@@ -299,7 +300,12 @@ def load_traffic(kernel_key: str):
         return None
     from paper_1602_03395_gb300 import build as B
     entry = rec.get(kernel_key)
-    if not entry or entry.get("sources_digest") != B._deps_digest():
+    if not entry or not entry.get("sources"):
+        return None
+    try:
+        if entry.get("sources_digest") != B.sources_digest(entry["sources"]):
+            return None
+    except OSError:
         return None
     return entry.get("bytes_per_launch")
 
@@ -532,7 +538,7 @@ def run_ffx(args):
         axis_form = "fused"
         flops = sum(pass_flops(w.dims[j], w.lam[j], B_ * M // w.dims[j], "dense") for j in order)
         kernel_key = f"fused_dense_{'x'.join(map(str, w.dims))}_{args.workload}"
-        traffic = load_traffic(f"fused_{'x'.join(map(str, w.dims))}")
+        traffic = load_traffic(f"{kernel_key}_b{B_}")
         bytes_launch = B_ * M * (8 + 4)
         pass_names = ["fused_" + "_".join(f"axis{j}" for j in order)]
     else:
@@ -541,7 +547,7 @@ def run_ffx(args):
         axis_form = call_forms[axis]
         flops = pass_flops(N, lam, B_ * M // N, axis_form)
         kernel_key = f"pass_{axis_form}_N{N}_lam{lam}_{args.workload}"
-        traffic = load_traffic(f"{axis_form}_N{N}")
+        traffic = load_traffic(f"{kernel_key}_b{B_}")
         # HBM view of the same launch: it reads and writes the batch once
         # (complex64; the last pass writes float32 densities)
         last = dom == launches - 1

@@ -49,6 +49,18 @@ def _deps_digest():
     return h.hexdigest()
 
 
+def sources_digest(names) -> str:
+    """Digest of the named files under csrc/ (with the compile flags): a
+    kernel's own sources, for records of measurements taken on them."""
+    h = hashlib.sha256()
+    for f in sorted(names):
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    h.update(" ".join(NVCC_FLAGS).encode())
+    return h.hexdigest()
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False) -> str:
     """Compile and link libffx.so if its sources changed; return its path."""
     os.makedirs(BUILD, exist_ok=True)
