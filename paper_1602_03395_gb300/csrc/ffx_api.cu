@@ -870,8 +870,7 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
         e = launch_tc_build_t(ax.T, ax.tc_t[0], ax.N, s);
         if (e == cudaSuccess) e = launch_tc_build_t(ax.TH, ax.tc_t[1], ax.N, s);
         if (e == cudaSuccess)
-          e = cudaFuncSetAttribute(dense_tc_func(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)dense_tc_smem());
+          e = dense_tc_prepare();
         if (e != cudaSuccess) rc = cuda_fail(e, "tensor-core operands");
       }
       if (rc == FFX_OK) {

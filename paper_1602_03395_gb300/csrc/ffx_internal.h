@@ -109,8 +109,7 @@ constexpr int kDenseMaxN = 1024;
 // dense form on the tensor cores (ffx_tc.cu), split TF32, for lines of N
 // points with N a multiple of 64 up to kDenseMaxN; in place only for N = 64
 bool dense_tc_supported(int N);
-size_t dense_tc_smem();
-const void* dense_tc_func();
+cudaError_t dense_tc_prepare();  // shared-memory attributes of the kernel's variants
 size_t dense_tc_t_bytes(int N);
 cudaError_t launch_dense_tc(const DenseArgs& a, const unsigned char* Tblk, int* err, int grid,
                             cudaStream_t stream);

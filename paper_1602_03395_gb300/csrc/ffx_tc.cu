@@ -61,17 +61,30 @@ constexpr int CHUNK_SBO = (TKC / 4) * 128;  // 1024: between 8-row groups of a c
 constexpr int T_PART = ROWS * TKC * 4;      // 16 KB per split part
 constexpr int X_PART = LINES * TKC * 4;     // 16 KB per split part
 constexpr int T_CHUNK = 2 * T_PART;         // head + tail, one bulk copy
-constexpr int STAGE_BYTES = T_CHUNK + 2 * X_PART;  // 64 KB
 constexpr int NPROD = 256, NEPI = 128;
 constexpr int PITEMS = LINES * (TKC / 4) / NPROD;  // 16-byte input items per producer thread per chunk
-constexpr int RAW = 4;                        // input chunks in flight per producer thread
 constexpr int RAW_CHUNK = NPROD * PITEMS * 16;  // 16 KB
 constexpr int GRAD_CHUNK = NPROD * PITEMS * 8;  // 8 KB of gradient factors (backward passes)
-constexpr int TC_SMEM = TSTAGES * STAGE_BYTES + RAW * RAW_CHUNK;  // 192 KB
 // accumulating launches: |.|^2 sums over the batch, [row][line]; backward
 // launches: the gradient ring (the two never meet in one launch)
 constexpr int EXTRA_SMEM = (ROWS / 2) * 128 * 4;
-static_assert(RAW * GRAD_CHUNK <= EXTRA_SMEM, "gradient ring");
+constexpr int RES_CHUNKS = (2 * 64) / TKC;  // N = 64: all of T is 4 chunks (128 KB)
+
+// Shared-memory layout.  Streaming (any N): stages of [T chunk | X head | X
+// tail], a 4-deep input ring, and the optional extra region.  Resident (N = 64,
+// plain forward and adjoint passes): all of T stays in shared memory for the
+// launch, stages hold only the split input, and the input ring is 2 deep.
+template <bool RES>
+struct TcLayout {
+  static constexpr int T_RES = RES ? RES_CHUNKS * T_CHUNK : 0;
+  static constexpr int STAGE = (RES ? 0 : T_CHUNK) + 2 * X_PART;
+  static constexpr int X_OFF = RES ? 0 : T_CHUNK;  // split input within a stage
+  static constexpr int RAW = RES ? 2 : 4;           // input chunks in flight per producer thread
+  static constexpr int RAW_OFF = T_RES + TSTAGES * STAGE;
+  static constexpr int SMEM = RAW_OFF + RAW * RAW_CHUNK;  // 224 KB resident, 192 KB streaming
+};
+static_assert(TcLayout<false>::RAW * GRAD_CHUNK <= EXTRA_SMEM, "gradient ring");
+static_assert(TcLayout<false>::SMEM + EXTRA_SMEM <= 227 * 1024 && TcLayout<true>::SMEM <= 227 * 1024, "smem");
 constexpr int NTHREADS = NPROD + 32 + NEPI;  // 416
 constexpr int MMA_WARP = NPROD / 32;         // warp 8; warps 9-12 are the epilogue
 constexpr int ACC_COLS = 4 * ROWS;           // two buffers x (head product, cross terms): all 512
@@ -198,11 +211,13 @@ __device__ __forceinline__ void split_store(unsigned char* xh, unsigned char* xl
   *reinterpret_cast<float4*>(xl + off) = lo;
 }
 
+template <bool RES>
 __global__ void __launch_bounds__(NTHREADS, 1)
     dense_tc_kernel(const DenseArgs a, const unsigned char* __restrict__ Tblk, int* err) {
+  using L = TcLayout<RES>;
   extern __shared__ __align__(1024) unsigned char tsm[];
   __shared__ __align__(8) uint64_t full_bar[TSTAGES], empty_bar[TSTAGES], copy_bar[TSTAGES];
-  __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], done_bar;
+  __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], done_bar, tres_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int s_abort;
 
@@ -235,8 +250,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acce_bar[b])), "r"(NEPI) : "memory");
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done_bar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tres_bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
+    if (RES) {
+      // all of T (N = 64: one row block, 4 chunks), once for the launch
+      const uint32_t tb = smem_u32(&tres_bar);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tb), "r"(L::T_RES) : "memory");
+      for (int c = 0; c < RES_CHUNKS; ++c)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(tsm + c * T_CHUNK)),
+            "l"(Tblk + (size_t)c * T_CHUNK), "r"(T_CHUNK), "r"(tb)
+            : "memory");
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -247,9 +274,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp < MMA_WARP) {
     // ---------------- producers ----------------
     const int t = tid;
-    unsigned char* raw = tsm + TSTAGES * STAGE_BYTES;  // RAW chunks of this thread's inputs
-    unsigned char* graw = tsm + TC_SMEM;               // and of its gradient factors (backward)
+    unsigned char* raw = tsm + L::RAW_OFF;  // RAW chunks of this thread's inputs
+    unsigned char* graw = tsm + L::SMEM;    // and of its gradient factors (backward)
     const int64_t total = my_items * nb * kchunks;     // chunks of this block, in order
+    constexpr int RAW = L::RAW;
     // issue side: chunk ci = (iit, ib, ikc), RAW - 1 ahead of the consumer
     int64_t ci = 0, iit = 0;
     int ib = 0, ikc = 0;
@@ -330,14 +358,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int s = (int)(c % TSTAGES);
       const int64_t u = c / TSTAGES;
       if (u >= 1 && !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)((u - 1) & 1), &s_abort)) break;
-      unsigned char* st = tsm + s * STAGE_BYTES;
-      if (t == 0) {
+      unsigned char* st = tsm + L::T_RES + s * L::STAGE;
+      if (!RES && t == 0) {
         const uint32_t cb = smem_u32(&copy_bar[s]);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cb), "r"(T_CHUNK) : "memory");
         const unsigned char* src = Tblk + ((size_t)mt * kchunks + kc) * T_CHUNK;
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                smem_base + s * STAGE_BYTES),
+                smem_u32(st)),
             "l"(src), "r"(T_CHUNK), "r"(cb)
             : "memory");
         last_u[s] = (int)(u & 1);
@@ -345,7 +373,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int slot = (int)(c % RAW);
       const unsigned char* rs = raw + slot * RAW_CHUNK + t * 16;
       const unsigned char* gs = graw + slot * GRAD_CHUNK + t * 8;
-      unsigned char* xh = st + T_CHUNK;
+      unsigned char* xh = st + L::X_OFF;
       unsigned char* xl = xh + X_PART;
 #pragma unroll
       for (int i = 0; i < PITEMS; ++i) {
@@ -388,7 +416,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       int64_t g = 0, sub = 0;
-      bool ok = true;
+      bool ok = !RES || mbar_wait(smem_u32(&tres_bar), 0u, &s_abort);  // resident T has landed
       for (int64_t it = 0; ok && it < my_items; ++it) {
         for (int b = 0; ok && b < nb; ++b, ++sub) {
           const int buf = (int)(sub & 1);
@@ -402,14 +430,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           for (int kc = 0; kc < kchunks; ++kc, ++g) {
             const int s = (int)(g % TSTAGES);
             const int64_t u = g / TSTAGES;
-            if (!mbar_wait(smem_u32(&copy_bar[s]), (uint32_t)(u & 1), &s_abort) ||
+            if ((!RES && !mbar_wait(smem_u32(&copy_bar[s]), (uint32_t)(u & 1), &s_abort)) ||
                 !mbar_wait(smem_u32(&full_bar[s]), (uint32_t)(u & 1), &s_abort)) {
               ok = false;
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t st = smem_base + s * STAGE_BYTES;
-            const uint32_t th = st, tl = st + T_PART, xh = st + T_CHUNK, xl = xh + X_PART;
+            const uint32_t st = smem_base + (uint32_t)(L::T_RES + s * L::STAGE);
+            const uint32_t th = RES ? smem_base + (uint32_t)(kc * T_CHUNK) : st, tl = th + T_PART;
+            const uint32_t xh = st + L::X_OFF, xl = xh + X_PART;
 #pragma unroll
             for (int ks = 0; ks < TKC / 8; ++ks) {
               const uint32_t o = (uint32_t)(ks * 2 * CORE_LBO);
@@ -437,7 +466,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int q = warp & 3;          // tensor-memory lane quarter this warp may read
     const int r = q * 32 + lane;     // line within the item
     const int64_t M = a.M;
-    float* racc = reinterpret_cast<float*>(tsm + TC_SMEM);  // accumulating launches only
+    float* racc = reinterpret_cast<float*>(tsm + L::SMEM);  // accumulating launches only
     if (a.acc)
       for (int m = 0; m < ROWS / 2; ++m) racc[m * LINES + r] = 0.f;
     int64_t sub = 0;
@@ -525,6 +554,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   }
 
+  // the resident T copies have landed before the block can exit
+  if (RES && tid == 0) mbar_wait_own(smem_u32(&tres_bar), 0u, &s_abort);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (tid == 0 && s_abort) atomicAdd(err, 1);
@@ -563,14 +594,25 @@ __global__ void tc_build_t_kernel(const float2* __restrict__ T, unsigned char* _
 }  // namespace
 
 bool dense_tc_supported(int N) { return N >= 64 && N <= kDenseMaxN && N % 64 == 0; }
-size_t dense_tc_smem() { return (size_t)(TC_SMEM + EXTRA_SMEM); }
-const void* dense_tc_func() { return (const void*)dense_tc_kernel; }
+cudaError_t dense_tc_prepare() {
+  cudaError_t e = cudaFuncSetAttribute(dense_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       TcLayout<false>::SMEM + EXTRA_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(dense_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TcLayout<true>::SMEM);
+  return e;
+}
 size_t dense_tc_t_bytes(int N) { return (size_t)(2 * N) * (2 * N) * 8; }
 
 cudaError_t launch_dense_tc(const DenseArgs& a, const unsigned char* Tblk, int* err, int grid,
                             cudaStream_t stream) {
-  const int smem = TC_SMEM + ((a.acc || a.grad) ? EXTRA_SMEM : 0);
-  dense_tc_kernel<<<grid, NTHREADS, smem, stream>>>(a, Tblk, err);
+  if (a.N == 64 && !a.acc && !a.grad) {
+    // T (128 KB) stays in shared memory for the whole launch
+    dense_tc_kernel<true><<<grid, NTHREADS, TcLayout<true>::SMEM, stream>>>(a, Tblk, err);
+  } else {
+    const int smem = TcLayout<false>::SMEM + ((a.acc || a.grad) ? EXTRA_SMEM : 0);
+    dense_tc_kernel<false><<<grid, NTHREADS, smem, stream>>>(a, Tblk, err);
+  }
   return cudaGetLastError();
 }
 
