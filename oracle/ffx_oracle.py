@@ -58,6 +58,8 @@ __all__ = [
     "naive_field",
     "far_field_density",
     "sample_lines",
+    "column_density",
+    "fringe_phase",
 ]
 
 
@@ -246,6 +248,71 @@ def sample_lines(psi0, dx, t, lam, axis: int, index: tuple, a=None, abar=None) -
     for j, nb in sorted(zip(other, index), reverse=True):
         v = np.tensordot(v, Ts[j][nb], axes=([j], [0]))
     return Ts[axis] @ v
+
+
+# ---------------------------------------------------------------------------
+# detector readout (Sec. 6)
+# ---------------------------------------------------------------------------
+
+def column_density(psi0, dx, t, lam, axis: int, a=None, abar=None) -> np.ndarray:
+    """The detector image: the density integrated along lattice axis ``axis``.
+
+    Sec. 6 takes the image at the detector as the density integrated over the
+    imaging direction, rho(x, y) = integral dz |Psi|^2 (Fig. 4).  On the
+    magnified lattice the points along that axis are lam_axis dx_axis apart
+    (eq. wbx), so the integral is the sum of |Psibar|^2 over the axis times
+    lam_axis dx_axis.  ``axis`` counts lattice axes (0 .. d-1); the result keeps
+    the batch axes and drops that one.
+    """
+    rho = expand_density(psi0, dx, t, lam, a, abar)
+    d = len(dx) if not np.isscalar(dx) else 1
+    dxs = _as_tuple(dx, d, "dx")
+    lams = _as_tuple(lam, d, "lam")
+    if not 0 <= axis < d:
+        raise ValueError("axis out of range")
+    return rho.sum(axis=rho.ndim - d + axis) * (lams[axis] * dxs[axis])
+
+
+def fringe_phase(image, ybar, D: float, t: float, y_axis: int = -1) -> np.ndarray:
+    """Relative phase of two clouds split by D along y, read from the fringes
+    (eq. dphase2, hbar = m = 1): Delta theta_0 = y_peak D / t, where y_peak is
+    the position of the density peak nearest y = 0.
+
+    ``image`` is a density (or detector image) sampled at positions ``ybar``
+    (equally spaced) along ``y_axis``; every position along its other axes
+    gives one estimate.  The peak is the interior local maximum
+    (rho[j] > rho[j-1] and rho[j] >= rho[j+1], compared in the image's own
+    precision) with the smallest |ybar[j]|, the lower j on a tie; its position
+    is refined to the vertex of the parabola through log rho at j-1, j, j+1
+    (in FP64; no refinement when a value is not positive or the parabola is
+    flat).  A row without an interior maximum gives NaN.  Phases are not
+    wrapped.
+    """
+    img = np.moveaxis(np.asarray(image), y_axis, -1)
+    y = np.asarray(ybar, dtype=np.float64)
+    ny = img.shape[-1]
+    if y.shape != (ny,):
+        raise ValueError("ybar must give one position per image point along y")
+    dy = (y[-1] - y[0]) / (ny - 1) if ny > 1 else 0.0
+    flat = img.reshape(-1, ny)
+    out = np.full(flat.shape[0], np.nan)
+    for r, row in enumerate(flat):
+        best = -1
+        for j in range(1, ny - 1):
+            if row[j] > row[j - 1] and row[j] >= row[j + 1]:
+                if best < 0 or abs(y[j]) < abs(y[best]):
+                    best = j
+        if best < 0:
+            continue
+        rm, r0, rp = (float(v) for v in row[best - 1:best + 2])
+        shift = 0.0
+        if rm > 0 and r0 > 0 and rp > 0:
+            lm, l0, lp = math.log(rm), math.log(r0), math.log(rp)
+            curv = lm - 2.0 * l0 + lp
+            if curv != 0.0:
+                shift = 0.5 * (lm - lp) / curv
+        out[r] = (y[best] + shift * dy) * D / t
+    return out.reshape(img.shape[:-1])
 
 
 # ---------------------------------------------------------------------------

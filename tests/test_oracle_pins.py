@@ -121,13 +121,16 @@ def test_two_cloud_interferometer_formula_and_fringe_readout():
     psi2 = Ap * np.exp(-w2 * (2 * y2 - D2) ** 2 / 8) + Am * np.exp(-w2 * (2 * y2 + D2) ** 2 / 8)
     rho = np.abs(O.expand_field(psi2, (dx2,), t2, (lam2,))) ** 2
     yb2 = out_grid(N2, dx2, lam2)
-    spacing = 2 * np.pi * t2 / D2
-    near = np.flatnonzero(np.abs(yb2) < 0.5 * spacing)
-    i0 = near[np.argmax(rho[near])]
-    lm, l0, lp = np.log(rho[i0 - 1:i0 + 2])
-    ypk = yb2[i0] + 0.5 * (lm - lp) / (lm - 2 * l0 + lp) * (yb2[1] - yb2[0])
-    est = ypk * D2 / t2
+    est = float(O.fringe_phase(rho, yb2, D2, t2))
     assert abs(np.angle(np.exp(1j * (est - dtheta)))) < 0.1
+    # the readout of the closed-form density (with its periodic images on the
+    # lam N lattice) at the same points agrees
+    z2 = 1 + 1j * w2 * t2
+    period = lam2 * N2 * dx2
+    ex2 = np.abs(sum(z2 ** -0.5 * (Ap * np.exp(-w2 * (2 * (yb2 + m * period) - D2) ** 2 / (8 * z2))
+                                   + Am * np.exp(-w2 * (2 * (yb2 + m * period) + D2) ** 2 / (8 * z2)))
+                     for m in range(-3, 4))) ** 2
+    assert abs(float(O.fringe_phase(ex2, yb2, D2, t2)) - est) < 1e-8
 
 
 # ---------------------------------------------------------------------------
@@ -356,3 +359,46 @@ def test_sample_lines_matches_full():
     assert np.abs(O.sample_lines(psi, dx, t, lam, 2, (4, 5)) - full[4, 5, :]).max() < 1e-13
     assert np.abs(O.sample_lines(psi, dx, t, lam, 0, (1, 8)) - full[:, 1, 8]).max() < 1e-13
     assert np.abs(O.sample_lines(psi, dx, t, lam, 1, (5, 0)) - full[5, :, 0]).max() < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# detector readout (Sec. 6): column density and the fringe phase
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_column_density_of_separable_gaussian(axis):
+    """A product of free Gaussians stays a product; integrating the density
+    along one axis leaves the other two factors times that axis's sum of
+    |G|^2 over the magnified points times their spacing lam dx (eq. wbx)."""
+    dims, dx, lam, t = (64, 60, 72), (0.12, 0.13, 0.11), (3, 5, 2), 1.5
+    sig, c, k0 = (0.5, 0.5, 0.45), (0.3, -0.2, 0.1), (0.5, -0.4, 0.7)
+    axes_in = [grid(dims[j], dx[j]) for j in range(3)]
+    psi = np.einsum("i,j,k->ijk", *[gauss_t(axes_in[j], 0, sig[j], c[j], k0[j]) for j in range(3)])
+    col = O.column_density(psi[None], dx, t, lam, axis)[0]
+    g = [np.abs(gauss_periodic(out_grid(dims[j], dx[j], lam[j]), t, sig[j], c[j], k0[j],
+                               lam[j] * dims[j] * dx[j])) ** 2 for j in range(3)]
+    other = [j for j in range(3) if j != axis]
+    ex = np.outer(g[other[0]], g[other[1]]) * g[axis].sum() * lam[axis] * dx[axis]
+    assert col.shape == (dims[other[0]], dims[other[1]])
+    assert rel(col, ex) < 1e-9
+
+
+def test_fringe_phase_vertex_and_nearest_peak():
+    """The readout's own steps: on rho = exp(-(y - y*)^2 / w) the parabola
+    through log rho is exact, so the vertex is y* to rounding; among several
+    maxima the one nearest y = 0 is taken; a monotone row has none."""
+    y = -3.0 + 0.1 * np.arange(61)
+    D, t = 2.0, 5.0
+    for ystar in (0.0, 0.037, -0.081, 0.2449):
+        rho = np.exp(-(y - ystar) ** 2 / 0.3)
+        assert abs(float(O.fringe_phase(rho, y, D, t)) - ystar * D / t) < 1e-12
+    # fringes cos^2(pi (y - y0) / s) under a broad envelope: peaks at y0 + k s
+    s_, y0 = 1.3, 0.41
+    rho = np.exp(-y ** 2 / 50) * np.cos(np.pi * (y - y0) / s_) ** 2 + 1e-3
+    est = float(O.fringe_phase(rho, y, D, t))
+    assert abs(est * t / D - y0) < 0.02          # the k = 0 fringe, not k = -1 at y0 - s
+    img = np.stack([rho, np.linspace(1, 2, 61)])  # second row: no interior maximum
+    both = O.fringe_phase(img, y, D, t)
+    assert both[0] == est and np.isnan(both[1])
+    # the y axis may be any axis of the image
+    assert O.fringe_phase(img.T, y, D, t, y_axis=0)[0] == est
