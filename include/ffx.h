@@ -255,6 +255,51 @@ int ffx_expand_noalloc(int ndim, const int64_t* dims, const double* spacing, dou
 /* 1 if this build has a line kernel for length n, else 0. */
 int ffx_supported_length(int64_t n);
 
+/*
+ * ffx_expand_column -- the detector image (Sec. 6): the density integrated
+ * along one lattice axis, as the paper's detector integrates over the imaging
+ * direction (rho(x, y) = integral dz |Psi|^2, Fig. 4).
+ *
+ *  axis          the lattice axis integrated over (0 .. ndim-1).
+ *  out_column    device float32, the lattice without that axis:
+ *                [batch][dims without axis], or [dims without axis] added to
+ *                (+=) with FFX_ACCUMULATE (summed over the batch).  Entry =
+ *                lam_axis * spacing_axis * sum over the axis of |Psibar|^2
+ *                (the magnified lattice's spacing along the axis, eq. wbx).
+ *  The map runs with the integrated axis as the last pass.  Small lattices
+ *  that fuse (ffx_plan_fused) sum inside the fused launch; otherwise the
+ *  densities go to plan workspace and one more launch sums them.  Sums run in
+ *  a fixed order (deterministic).  Not for many-instance plans
+ *  (FFX_EUNSUPPORTED).
+ */
+int ffx_expand_column(ffx_plan_t plan, const void* psi0, int64_t batch, int axis, float* out_column,
+                      void* stream);
+
+/* Positions of the magnified output lattice along `axis` (eq. wbx):
+ * xbar_n = *x0 + n * *step, with *x0 = abar_axis, *step = lam_axis * spacing_axis. */
+int ffx_plan_output_axis(ffx_plan_t plan, int axis, double* x0, double* step);
+
+/*
+ * ffx_fringe_phase -- the relative phase of two clouds split by D along y,
+ * read from their interference fringes (eq. dphase2, hbar = m = 1):
+ * Delta theta_0 = y_peak * D / t, y_peak the density peak nearest y = 0.
+ *
+ *  image       device float32 density or detector image; element (r, j) at
+ *              image[r * row_stride + j * y_stride], r < rows, j < ny (ny >= 3),
+ *              sampled at y_j = y0 + j * dy (dy > 0).
+ *  out_phase   device float64 [rows]: per row, the interior local maximum
+ *              (v[j] > v[j-1] and v[j] >= v[j+1]) with the smallest |y_j| (the
+ *              lower j on a tie), refined to the vertex of the parabola through
+ *              log v at j-1, j, j+1 (FP64; no refinement if a value is not
+ *              positive), times D / t.  NaN for a row with no interior maximum.
+ *              Phases are not wrapped.
+ *  Works on any image; the paper has no counterpart for the GPU kernel, it
+ *  states the estimate.  FFX_EINVAL for bad sizes, t = 0, dy <= 0, a NULL or
+ *  misaligned pointer.
+ */
+int ffx_fringe_phase(const float* image, int64_t rows, int64_t ny, int64_t row_stride, int64_t y_stride,
+                     double y0, double dy, double D, double t, double* out_phase, void* stream);
+
 /* Bytes of plan-owned workspace a call with this batch uses. */
 int64_t ffx_workspace_bytes(ffx_plan_t plan, int64_t batch);
 

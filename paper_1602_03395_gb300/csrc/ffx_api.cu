@@ -147,8 +147,8 @@ struct ffx_plan_s {
   int64_t fused = 0;             // largest batch whose forward calls run as one launch (ffx_fused.cu)
   int fused_grid = 0;
   size_t fused_smem_bytes = 0;
-  void* ws[2] = {nullptr, nullptr};  // workspace buffers (grown on demand)
-  size_t ws_bytes[2] = {0, 0};
+  void* ws[3] = {nullptr, nullptr, nullptr};  // workspace buffers (grown on demand; [2]: detector densities)
+  size_t ws_bytes[3] = {0, 0, 0};
   ManyPlan* many = nullptr;       // set for plans over many instances
   void* const* trace = nullptr;   // caller's cudaEvent_t array (profiling)
   int64_t trace_n = 0;
@@ -451,10 +451,12 @@ int plan_fusion(ffx_plan_s* p) {
   return FFX_OK;
 }
 
-// The forward map as one launch: pass k reads `in` (k = 0) or the workspace,
-// writes the workspace, and the last pass writes out_c, or out_d (a density,
-// summed over the batch with FFX_ACCUMULATE).
-int run_fused(ffx_plan_s* p, const float2* in, float2* out_c, float* out_d, int64_t batch, cudaStream_t stream) {
+// The forward map as one launch, passes in the order `axes`: pass k reads
+// `in` (k = 0) or the workspace, writes the workspace, and the last pass
+// writes out_c, or out_d (a density), or out_col (the density summed along the
+// last pass's axis); the last two summed over the batch with FFX_ACCUMULATE.
+int run_fused(ffx_plan_s* p, const int* axes, const float2* in, float2* out_c, float* out_d, float* out_col,
+              int64_t batch, cudaStream_t stream) {
   int rc;
   if ((rc = ensure_ws(p, 0, batch))) return rc;
   float2* ws = (float2*)p->ws[0];
@@ -467,7 +469,7 @@ int run_fused(ffx_plan_s* p, const float2* in, float2* out_c, float* out_d, int6
   a.err = p->dev_err;
   int64_t off = 0;
   for (int k = 0; k < p->ndim; ++k) {
-    const int j = p->order[k];
+    const int j = axes[k];
     const Axis& ax = p->axis[j];
     const bool last = k == p->ndim - 1;
     FusedPass& P = a.pass[k];
@@ -475,7 +477,9 @@ int run_fused(ffx_plan_s* p, const float2* in, float2* out_c, float* out_d, int6
     P.in = k == 0 ? in : ws;
     P.out_c = last ? out_c : ws;
     P.out_d = last ? out_d : nullptr;
-    P.acc = (last && out_d) ? p->acc : 0;
+    P.out_col = last ? out_col : nullptr;
+    P.col_scale = (float)(ax.lam * ax.dx);
+    P.acc = (last && (out_d || out_col)) ? p->acc : 0;
     P.ncols = P.acc ? P.outer * P.inner : batch * P.outer * P.inner;
     P.N = ax.N;
     P.img = ax.img[0];
@@ -935,7 +939,7 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
   if (rc == FFX_OK) rc = plan_fusion(p);
   cudaStreamDestroy(s);
   if (rc != FFX_OK) {
-    for (int w = 0; w < 2; ++w)
+    for (int w = 0; w < 3; ++w)
       if (p->ws[w]) cudaFree(p->ws[w]);
     if (p->dense_mem) cudaFree(p->dense_mem);
     if (p->tc_mem) cudaFree(p->tc_mem);
@@ -983,7 +987,7 @@ int ffx_plan_destroy(ffx_plan_t p) {
     delete p;
     return FFX_OK;
   }
-  for (int w = 0; w < 2; ++w)
+  for (int w = 0; w < 3; ++w)
     if (p->ws[w]) cudaFree(p->ws[w]);
   if (p->dense_mem) cudaFree(p->dense_mem);
   if (p->tc_mem) cudaFree(p->tc_mem);
@@ -1033,7 +1037,7 @@ int ffx_plan_device_errors(ffx_plan_t p) {
 int64_t ffx_workspace_bytes(ffx_plan_t p, int64_t batch) {
   if (!p || batch < 0) return -1;
   int64_t total = 0;
-  for (int w = 0; w < 2; ++w) total += (int64_t)p->ws_bytes[w];
+  for (int w = 0; w < 3; ++w) total += (int64_t)p->ws_bytes[w];
   const int64_t need = batch * p->M * (int64_t)sizeof(float2);
   return total > need ? total : need;
 }
@@ -1055,6 +1059,33 @@ int ffx_plan_call_form(ffx_plan_t p, int axis, int64_t batch) {
   return dense_kernel_for(p, p->axis[axis], lines);
 }
 
+// The forward passes in the order `axes`, the last one writing densities
+// (summed over the batch with FFX_ACCUMULATE).  Every pass but the last
+// writes a complex field: ws[0], switching to ws[1] and back for passes that
+// cannot run in place.
+int forward_density(ffx_plan_s* p, const int* axes, const float2* in, int64_t batch, float* out_d,
+                    cudaStream_t s) {
+  const int d = p->ndim;
+  const float2* cur = in;
+  int rc;
+  if (d > 1) {
+    if ((rc = ensure_ws(p, 0, batch))) return rc;
+    float2* ws0 = (float2*)p->ws[0];
+    float2* target = ws0;
+    for (int k = 0; k < d - 1; ++k) {
+      const int j = axes[k];
+      if (k > 0 && !inplace_ok(p->axis[j])) {
+        if ((rc = ensure_ws(p, 1, batch))) return rc;
+        target = (cur == ws0) ? (float2*)p->ws[1] : ws0;
+      }
+      rc = run_axis(p, j, false, cur, nullptr, 0, target, nullptr, 0, batch, s);
+      if (rc) return rc;
+      cur = target;
+    }
+  }
+  return run_axis(p, axes[d - 1], false, cur, nullptr, 0, nullptr, out_d, p->acc, batch, s);
+}
+
 int ffx_expand(ffx_plan_t p, const void* psi0, int64_t batch, float* out_density, void* stream) {
   if (!p) return fail(FFX_EINVAL, "plan is NULL");
   if (batch < 0) return fail(FFX_EINVAL, "batch < 0");
@@ -1068,29 +1099,69 @@ int ffx_expand(ffx_plan_t p, const void* psi0, int64_t batch, float* out_density
     rc = many_expand(p->many, psi0, out_density, nullptr, s, &err);
     return rc ? fail(rc, "%s", err.c_str()) : FFX_OK;
   }
-  if (batch <= p->fused) return run_fused(p, (const float2*)psi0, nullptr, out_density, batch, s);
-  const int d = p->ndim;
-  const float2* cur = (const float2*)psi0;
-  if (d > 1) {
-    // every pass but the last writes a complex field: ws[0], switching to ws[1]
-    // and back for passes that cannot run in place
-    if ((rc = ensure_ws(p, 0, batch))) return rc;
-    float2* ws0 = (float2*)p->ws[0];
-    float2* target = ws0;
-    for (int k = 0; k < d - 1; ++k) {
-      const int j = p->order[k];
-      if (k > 0 && !inplace_ok(p->axis[j])) {
-        if ((rc = ensure_ws(p, 1, batch))) return rc;
-        ws0 = (float2*)p->ws[0];  // (unchanged: ensure_ws(1) touches only ws[1])
-        target = (cur == ws0) ? (float2*)p->ws[1] : ws0;
-      }
-      rc = run_axis(p, j, false, cur, nullptr, 0, target, nullptr, 0, batch, s);
-      if (rc) return rc;
-      cur = target;
-    }
-  }
-  return run_axis(p, p->order[d - 1], false, cur, nullptr, 0, nullptr, out_density, p->acc, batch, s);
+  if (batch <= p->fused) return run_fused(p, p->order, (const float2*)psi0, nullptr, out_density, nullptr, batch, s);
+  return forward_density(p, p->order, (const float2*)psi0, batch, out_density, s);
 }
+
+int ffx_expand_column(ffx_plan_t p, const void* psi0, int64_t batch, int axis, float* out_column, void* stream) {
+  if (!p) return fail(FFX_EINVAL, "plan is NULL");
+  if (batch < 0) return fail(FFX_EINVAL, "batch < 0");
+  if (p->many) return fail(FFX_EUNSUPPORTED, "ffx_expand_column does not take a many-instance plan");
+  if (axis < 0 || axis >= p->ndim) return fail(FFX_EINVAL, "axis %d out of range", axis);
+  if (batch == 0) return FFX_OK;
+  int rc;
+  if ((rc = check_ptr(psi0, "psi0")) || (rc = check_ptr(out_column, "out_column"))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the integrated axis runs last: its pass sees whole lines along it
+  int axes[3], n = 0;
+  for (int k = 0; k < p->ndim; ++k)
+    if (p->order[k] != axis) axes[n++] = p->order[k];
+  axes[n] = axis;
+  if (batch <= p->fused) return run_fused(p, axes, (const float2*)psi0, nullptr, nullptr, out_column, batch, s);
+  // densities into ws[2], then the sum along the axis
+  if ((rc = ensure_ws(p, 2, batch))) return rc;
+  float* rho = (float*)p->ws[2];
+  if (p->acc) {
+    cudaError_t e = cudaMemsetAsync(rho, 0, (size_t)p->M * sizeof(float), s);
+    if (e != cudaSuccess) return cuda_fail(e, "density scratch");
+  }
+  if ((rc = forward_density(p, axes, (const float2*)psi0, batch, rho, s))) return rc;
+  int64_t outer, inner;
+  axis_outer_inner(p, axis, &outer, &inner);
+  const Axis& ax = p->axis[axis];
+  cudaError_t e = launch_axis_sum(rho, p->acc ? outer : batch * outer, ax.N, inner, (float)(ax.lam * ax.dx), p->acc,
+                                  out_column, p->sms, s);
+  return e == cudaSuccess ? FFX_OK : cuda_fail(e, "column sum");
+}
+
+int ffx_plan_output_axis(ffx_plan_t p, int axis, double* x0, double* step) {
+  if (!p || !x0 || !step) return fail(FFX_EINVAL, "plan, x0 or step is NULL");
+  if (p->many) return fail(FFX_EUNSUPPORTED, "a many-instance plan has no single output lattice");
+  if (axis < 0 || axis >= p->ndim) return fail(FFX_EINVAL, "axis %d out of range", axis);
+  *x0 = p->axis[axis].abar;
+  *step = p->axis[axis].lam * p->axis[axis].dx;
+  return FFX_OK;
+}
+
+int ffx_fringe_phase(const float* image, int64_t rows, int64_t ny, int64_t row_stride, int64_t y_stride, double y0,
+                     double dy, double D, double t, double* out_phase, void* stream) {
+  g_last_error.clear();
+  if (rows < 0 || ny < 0) return fail(FFX_EINVAL, "rows or ny < 0");
+  if (rows == 0) return FFX_OK;
+  if (ny < 3) return fail(FFX_EINVAL, "ny = %lld: a peak needs three points", (long long)ny);
+  if (!(t != 0.0) || !(dy > 0.0) || !std::isfinite(D) || !std::isfinite(y0))
+    return fail(FFX_EINVAL, "need t != 0, dy > 0, finite D and y0");
+  if (!image || ((uintptr_t)image & 3)) return fail(FFX_EINVAL, "image is NULL or not 4-byte aligned");
+  int rc;
+  if ((rc = check_ptr(out_phase, "out_phase"))) return rc;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = launch_fringe(image, rows, ny, row_stride, y_stride, y0, dy, D, t, out_phase, sms > 0 ? sms : 1,
+                                (cudaStream_t)stream);
+  return e == cudaSuccess ? FFX_OK : cuda_fail(e, "fringe readout");
+}
+
 
 int ffx_expand_field(ffx_plan_t p, const void* psi0, int64_t batch, void* out_field, void* stream) {
   if (!p) return fail(FFX_EINVAL, "plan is NULL");
@@ -1105,7 +1176,8 @@ int ffx_expand_field(ffx_plan_t p, const void* psi0, int64_t batch, void* out_fi
     return rc ? fail(rc, "%s", err.c_str()) : FFX_OK;
   }
   if (batch <= p->fused)
-    return run_fused(p, (const float2*)psi0, (float2*)out_field, nullptr, batch, (cudaStream_t)stream);
+    return run_fused(p, p->order, (const float2*)psi0, (float2*)out_field, nullptr, nullptr, batch,
+                     (cudaStream_t)stream);
   return chain_into(p, p->order, false, (const float2*)psi0, nullptr, 0, batch, (float2*)out_field, 0,
                     (cudaStream_t)stream);
 }

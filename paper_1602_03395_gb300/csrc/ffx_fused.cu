@@ -17,7 +17,8 @@
 //     wait; the last block to leave resets it for the next launch) separates
 //     the passes;
 //   * the last pass writes complex64, |.|^2, or |.|^2 summed over the batch
-//     (a tile then loops over the realizations in order).
+//     (a tile then loops over the realizations in order), or the detector
+//     image: |.|^2 summed along the pass's axis, one value per line (Sec. 6).
 // The arithmetic of a tile is that of the per-axis dense kernels (FP32 FMA,
 // k ascending), so results match the unfused path bit for bit.
 #include <cstring>
@@ -239,26 +240,41 @@ __global__ void __launch_bounds__(THREADS, 1) fused_small_kernel(const FusedArgs
             S[(ty + TY * i) * BS_STRIDE + tx + TX * j] = v;
           }
         __syncthreads();
-        for (int idx = tid; idx < N * FBN; idx += THREADS) {
-          int m, cc;
-          if (contiguous) {
-            cc = idx / N;
-            m = idx - cc * N;
-          } else {
-            m = idx / FBN;
-            cc = idx - m * FBN;
+        if (P.out_col) {
+          // detector image: one sum over the tile's rows per line, in row order
+          if (tid < FBN) {
+            const int64_t c = (blockIdx.x + (it / nb) * gridDim.x) * FBN + tid;
+            if (c < P.ncols) {
+              float sum = 0.f;
+              for (int m = 0; m < N; ++m) {
+                const float2 v = S[m * BS_STRIDE + tid];
+                sum += P.acc ? v.x : v.x * v.x + v.y * v.y;
+              }
+              P.out_col[c] = P.acc ? P.out_col[c] + P.col_scale * sum : P.col_scale * sum;
+            }
           }
-          const long long base = cbase[buf][cc];
-          if (base < 0) continue;
-          const float2 v = S[m * BS_STRIDE + cc];
-          if (P.acc) {
-            P.out_d[base - (int64_t)b * a.M + (int64_t)m * inner] += v.x;
-          } else {
-            const int64_t addr = base + (int64_t)m * inner;
-            if (P.out_c)
-              P.out_c[addr] = v;
-            else
-              P.out_d[addr] = v.x * v.x + v.y * v.y;
+        } else {
+          for (int idx = tid; idx < N * FBN; idx += THREADS) {
+            int m, cc;
+            if (contiguous) {
+              cc = idx / N;
+              m = idx - cc * N;
+            } else {
+              m = idx / FBN;
+              cc = idx - m * FBN;
+            }
+            const long long base = cbase[buf][cc];
+            if (base < 0) continue;
+            const float2 v = S[m * BS_STRIDE + cc];
+            if (P.acc) {
+              P.out_d[base - (int64_t)b * a.M + (int64_t)m * inner] += v.x;
+            } else {
+              const int64_t addr = base + (int64_t)m * inner;
+              if (P.out_c)
+                P.out_c[addr] = v;
+              else
+                P.out_d[addr] = v.x * v.x + v.y * v.y;
+            }
           }
         }
 #pragma unroll

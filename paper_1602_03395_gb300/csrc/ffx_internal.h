@@ -123,6 +123,8 @@ struct FusedPass {
   const float2* in;   // the pass's input lines
   float2* out_c;      // complex output (the workspace, or the caller's field)
   float* out_d;       // density output of the last pass, or null
+  float* out_col;     // detector image of the last pass (sum over its axis), or null
+  float col_scale;    // lam_j dx_j: the magnified spacing along that axis
   const float2* img;  // T_j's shared-memory image in global memory ([N][65])
   int64_t outer, inner, ncols;
   int N, acc, img_off;  // img_off: position of the image in shared memory (float2 units)
@@ -140,6 +142,13 @@ int fused_img_stride();
 const void* fused_func();
 int fused_threads();
 cudaError_t launch_fused(const FusedArgs& a, int grid, size_t smem, cudaStream_t stream);
+
+// Detector readout (ffx_column.cu): sums of a density [outer][N][inner] along
+// N, and the fringe phase of eq. dphase2 per image row.
+cudaError_t launch_axis_sum(const float* rho, int64_t outer, int N, int64_t inner, float scale, int acc, float* out,
+                            int sms, cudaStream_t s);
+cudaError_t launch_fringe(const float* img, int64_t rows, int64_t ny, int64_t rs, int64_t ys, double y0, double dy,
+                          double D, double t, double* out, int sms, cudaStream_t s);
 cudaError_t launch_dense_build(const float2* O, float2* T, float2* TH, int N, cudaStream_t s);
 
 // Plans over many instances (ffx_many.cu).

@@ -85,6 +85,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ffx_plan_fused.restype = i64
     lib.ffx_plan_call_form.argtypes = [vp, i32, i64]
     lib.ffx_plan_call_form.restype = i32
+    lib.ffx_expand_column.argtypes = [vp, vp, i64, i32, vp, vp]
+    lib.ffx_expand_column.restype = i32
+    lib.ffx_plan_output_axis.argtypes = [vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+    lib.ffx_plan_output_axis.restype = i32
+    lib.ffx_fringe_phase.argtypes = [vp, i64, i64, i64, i64, dbl, dbl, dbl, dbl, vp, vp]
+    lib.ffx_fringe_phase.restype = i32
     lib.ffx_plan_pass_order.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
     lib.ffx_plan_pass_order.restype = i32
     lib.ffx_plan_trace.argtypes = [vp, ctypes.POINTER(vp), i64]
@@ -352,6 +358,47 @@ def ffx_expand_backward(plan: Plan, psi0: torch.Tensor, grad_density: torch.Tens
     _check(load_library().ffx_expand_backward(plan.handle, _ptr(psi0), _ptr(grad_density), B,
                                               _ptr(grad_psi0), _stream(stream)), "ffx_expand_backward")
     return grad_psi0
+
+
+def ffx_expand_column(plan: Plan, psi0: torch.Tensor, axis: int, out_column: torch.Tensor | None = None,
+                      stream=None) -> torch.Tensor:
+    """Detector image: |Psibar|^2 integrated along lattice axis ``axis`` (Sec. 6)."""
+    _need(psi0, torch.complex64, "psi0")
+    B = plan._batch(psi0)
+    d = len(plan.dims)
+    if not 0 <= axis < d:
+        raise ValueError(f"axis {axis} out of range for {d} lattice axes")
+    rest = tuple(n for j, n in enumerate(plan.dims) if j != axis)
+    if out_column is None:
+        shape = rest if plan.accumulate else tuple(psi0.shape[:psi0.dim() - d]) + rest
+        out_column = torch.zeros(shape, dtype=torch.float32, device=psi0.device)
+    _need(out_column, torch.float32, "out_column")
+    _check(load_library().ffx_expand_column(plan.handle, _ptr(psi0), B, axis, _ptr(out_column), _stream(stream)),
+           "ffx_expand_column")
+    return out_column
+
+
+def output_axis(plan: Plan, axis: int):
+    """(x0, step) of the magnified output lattice along ``axis`` (eq. wbx)."""
+    x0, step = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().ffx_plan_output_axis(plan.handle, axis, ctypes.byref(x0), ctypes.byref(step)),
+           "ffx_plan_output_axis")
+    return x0.value, step.value
+
+
+def ffx_fringe_phase(image: torch.Tensor, y0: float, dy: float, D: float, t: float, y_dim: int = -1,
+                     stream=None) -> torch.Tensor:
+    """Eq. dphase2 per row of a 2-D float32 image whose dimension ``y_dim`` is y."""
+    if not isinstance(image, torch.Tensor) or not image.is_cuda or image.dtype != torch.float32:
+        raise TypeError("image must be a float32 CUDA tensor")
+    if image.dim() != 2:
+        raise ValueError("image must be 2-D (rows, y) or (y, rows)")
+    yd = y_dim % 2
+    rows, ny = image.shape[1 - yd], image.shape[yd]
+    out = torch.empty(rows, dtype=torch.float64, device=image.device)
+    _check(load_library().ffx_fringe_phase(_ptr(image), rows, ny, image.stride(1 - yd), image.stride(yd),
+                                           y0, dy, D, t, _ptr(out), _stream(stream)), "ffx_fringe_phase")
+    return out
 
 
 class _ExpandDensity(torch.autograd.Function):
