@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--form", default="auto", choices=["auto", "paper", "fold", "dense", "tc"])
     ap.add_argument("--batch", type=int, default=None, help="realizations per step (default: workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--column", type=int, default=None, metavar="AXIS",
+                    help="output the detector image: the density integrated along AXIS (Sec. 6)")
     return ap.parse_args()
 
 
@@ -445,6 +447,22 @@ def run_ffx(args):
     launches = plan.launches_per_call(batch=B_)
     fused_call = plan.fused and B_ <= plan.fused_max_batch  # all d passes in one launch
     call_forms = plan.call_forms(B_)  # the kernel each axis runs at this batch
+    extra_launches = 0
+    if args.column is None:
+        out_shape = (B_,) + tuple(w.dims)
+
+        def call(x, out=None):
+            return ffx.ffx_expand(plan, x, out)
+    else:
+        # detector image: the integrated axis runs last; unfused calls add one
+        # (untraced) launch that sums the densities along it
+        col = args.column
+        out_shape = (B_,) + tuple(n for j, n in enumerate(w.dims) if j != col)
+        order = [j for j in order if j != col] + [col]
+        extra_launches = 0 if fused_call else 1
+
+        def call(x, out=None):
+            return ffx.ffx_expand_column(plan, x, col, out)
 
     # input pool larger than L2: distinct buffers, each step reads the next one
     step_in_bytes = B_ * M * 8
@@ -452,20 +470,22 @@ def run_ffx(args):
     pool_n = min(pool_n, 256)
     distinct = [torch.from_numpy(w.batch_array(B_, start=(rank * 1000 + i) * B_)) for i in range(4)]
     pool_in = [distinct[i % 4].to(dev) for i in range(pool_n)]
-    pool_out = [torch.empty((B_,) + tuple(w.dims), dtype=torch.float32, device=dev)
-                for _ in range(min(pool_n, 64))]
+    pool_out = [torch.empty(out_shape, dtype=torch.float32, device=dev) for _ in range(min(pool_n, 64))]
     stream = torch.cuda.current_stream(dev)
 
     # parity of this very configuration against the FP64 oracle (rank 0, first realization)
     err = None
     if rank == 0 and M <= 1 << 20:
         import oracle as O
-        ref = O.expand_density(distinct[0].numpy()[:1], w.dx, w.t, w.lam)
-        got = ffx.ffx_expand(plan, pool_in[0][:1].contiguous()).cpu().numpy()
+        if args.column is None:
+            ref = O.expand_density(distinct[0].numpy()[:1], w.dx, w.t, w.lam)
+        else:
+            ref = O.column_density(distinct[0].numpy()[:1], w.dx, w.t, w.lam, args.column)
+        got = call(pool_in[0][:1].contiguous()).cpu().numpy()
         err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
 
     for i in range(args.warmup):
-        ffx.ffx_expand(plan, pool_in[i % pool_n], pool_out[i % len(pool_out)])
+        call(pool_in[i % pool_n], pool_out[i % len(pool_out)])
     torch.cuda.synchronize()
 
     # The K steps are captured into CUDA graphs of up to GRAPH_STEPS steps and
@@ -484,7 +504,7 @@ def run_ffx(args):
         plan.trace(ev if not graphs else None)  # the first graph carries the per-launch events
         with torch.cuda.graph(g):
             for i in range(done, done + n):
-                ffx.ffx_expand(plan, pool_in[i % pool_n], pool_out[i % len(pool_out)])
+                call(pool_in[i % pool_n], pool_out[i % len(pool_out)])
         plan.trace(None)
         graphs.append((g, n, done))
         done += n
@@ -532,14 +552,17 @@ def run_ffx(args):
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     alu_peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
     hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+    out_bytes = 4 * int(np.prod(out_shape))
     if fused_call:
         # one cooperative launch runs every pass (dense, FP32 SIMT); HBM sees
         # the input read and the density written, the intermediates stay in L2
         axis_form = "fused"
         flops = sum(pass_flops(w.dims[j], w.lam[j], B_ * M // w.dims[j], "dense") for j in order)
         kernel_key = f"fused_dense_{'x'.join(map(str, w.dims))}_{args.workload}"
+        if args.column is not None:
+            kernel_key += f"_column{args.column}"
         traffic = load_traffic(f"{kernel_key}_b{B_}")
-        bytes_launch = B_ * M * (8 + 4)
+        bytes_launch = B_ * M * 8 + out_bytes
         pass_names = ["fused_" + "_".join(f"axis{j}" for j in order)]
     else:
         axis = order[dom]
@@ -547,6 +570,8 @@ def run_ffx(args):
         axis_form = call_forms[axis]
         flops = pass_flops(N, lam, B_ * M // N, axis_form)
         kernel_key = f"pass_{axis_form}_N{N}_lam{lam}_{args.workload}"
+        if args.column is not None:
+            kernel_key += f"_column{args.column}"
         traffic = load_traffic(f"{kernel_key}_b{B_}")
         # HBM view of the same launch: it reads and writes the batch once
         # (complex64; the last pass writes float32 densities)
@@ -576,12 +601,12 @@ def run_ffx(args):
 
     # end to end through the C ABI with host buffers: pinned H2D, expand, D2H
     h_in = [distinct[i % 4].pin_memory() for i in range(4)]
-    h_out = torch.empty((B_,) + tuple(w.dims), dtype=torch.float32).pin_memory()
+    h_out = torch.empty(out_shape, dtype=torch.float32).pin_memory()
     d_in = torch.empty_like(pool_in[0])
-    d_out = torch.empty((B_,) + tuple(w.dims), dtype=torch.float32, device=dev)
+    d_out = torch.empty(out_shape, dtype=torch.float32, device=dev)
     for i in range(3):
         d_in.copy_(h_in[i % 4], non_blocking=True)
-        ffx.ffx_expand(plan, d_in, d_out)
+        call(d_in, d_out)
         h_out.copy_(d_out, non_blocking=True)
     torch.cuda.synchronize()
     e2e_steps = args.steps
@@ -590,7 +615,7 @@ def run_ffx(args):
     e0.record(stream)
     for i in range(e2e_steps):
         d_in.copy_(h_in[i % 4], non_blocking=True)
-        ffx.ffx_expand(plan, d_in, d_out)
+        call(d_in, d_out)
         h_out.copy_(d_out, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -601,8 +626,29 @@ def run_ffx(args):
         e2e_ms = float(tt.item())
     e2e_value = e2e_steps * B_ * world / (e2e_ms * 1e-3)
 
+    # the fringe readout of eq. dphase2 on the step's detector image (two-cloud
+    # workloads imaged across their separation axis): one launch, timed alone
+    fringe = None
+    if args.column is not None and w.fringe is not None and w.fringe[0] != args.column:
+        sep_axis, D = w.fringe
+        img = pool_out[0][0]
+        y_dim = [j for j in range(len(w.dims)) if j != args.column].index(sep_axis)
+        y0, dy = ffx.output_axis(plan, sep_axis)
+        for _ in range(3):
+            ph = ffx.ffx_fringe_phase(img, y0, dy, D, w.t, y_dim=y_dim)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(100):
+            ffx.ffx_fringe_phase(img, y0, dy, D, w.t, y_dim=y_dim)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fringe = {"us_per_image": f0.elapsed_time(f1) * 10.0, "rows": int(ph.numel()),
+                  "separation_axis": sep_axis, "D": D,
+                  "median_phase_rad": float(torch.nanmedian(ph).item())}
+
     cufft = scipy64 = scipy32 = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.column is None:
         cufft = cufft_baseline(torch, w, dev)
         res = cufft.pop("result", None)
         if res is not None:
@@ -629,11 +675,13 @@ def run_ffx(args):
                        "lam": list(w.lam), "t": w.t, "batch_per_gpu": B_, "form": form,
                        "axis_forms": list(plan.axis_forms), "call_forms": list(call_forms),
                        "fused_one_launch": bool(fused_call),
+                       "output": ("density" if args.column is None else
+                                  f"detector image: density integrated along axis {args.column}"),
                        "parallelism": f"replicas x{world} (realizations sharded, no collective)",
                        "l2": f"rotating pool of {pool_n} input buffers "
                              f"({pool_n * step_in_bytes / 2**20:.0f} MiB > 129 MB L2)"},
             "rel_l2_density_err_vs_fp64": err,
-            "gpu_launches": launches * args.steps,
+            "gpu_launches": (launches + extra_launches) * args.steps,
             "graph": f"K steps replayed as {len(graphs)} CUDA graph(s) of <= {GRAPH_STEPS} steps",
             "clocks": clocks,
             "roofline": roofline,
@@ -643,8 +691,9 @@ def run_ffx(args):
                              "note": f"of {pk_src} hbm_gbs; one read + one write of the batch"},
             "pass_ms": {pass_names[k]: mean_ms[k] for k in range(launches)},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B_ * M * 8,
-                    "d2h_bytes_per_step": B_ * M * 4},
+                    "d2h_bytes_per_step": out_bytes},
             "cpu_baseline": cpu,
+            "fringe_readout": fringe,
             "comparisons": {"cufft_recipe": cufft, "cpu_fft_recipe_c64": scipy32,
                             "cpu_fft_recipe_c128": scipy64},
         }

@@ -54,6 +54,7 @@ class Workload:
     batch: int             # realizations
     seed: int
     make: object = field(repr=False, default=None)   # make(rng) -> complex128 array[dims]
+    fringe: tuple | None = None  # interferometers: (separation axis, cloud separation D)
 
     def realization(self, r: int) -> np.ndarray:
         """Realization r as complex64 (drawn in float64, then rounded)."""
@@ -140,7 +141,7 @@ def config_two_cloud(seed: int = 2, batch: int = 1) -> Workload:
     """3-D interferometer: 64^3, dx=0.25, sigma=(2,2,8), centres +-6 along x,
     lam=(30,30,3), t=40."""
     return Workload("3d_two_cloud_64^3_lam30x30x3", (64, 64, 64), (0.25, 0.25, 0.25),
-                    (30, 30, 3), 40.0, batch, seed, lambda rng: two_cloud_3d(rng))
+                    (30, 30, 3), 40.0, batch, seed, lambda rng: two_cloud_3d(rng), fringe=(0, 12.0))
 
 
 def config_quasicondensate(seed: int = 3, batch: int = 256) -> Workload:
@@ -183,7 +184,7 @@ def config_large(which: str = "two_cloud", seed: int = 5) -> Workload:
     if which == "two_cloud":
         return Workload("3d_two_cloud_256^3_lam100", (256, 256, 256), (0.25,) * 3,
                         (100, 100, 100), 400.0, 1, seed,
-                        lambda rng: two_cloud_3d(rng, (256, 256, 256)))
+                        lambda rng: two_cloud_3d(rng, (256, 256, 256)), fringe=(0, 12.0))
     if which == "quasicondensate":
         return Workload("3d_quasicondensate_128x128x1024_lam100", (128, 128, 1024),
                         (0.25, 0.25, 0.5), (100, 100, 100), 400.0, 1, seed,
