@@ -60,6 +60,8 @@ __all__ = [
     "sample_lines",
     "column_density",
     "fringe_phase",
+    "fine_wavevectors",
+    "positive_p_density",
 ]
 
 
@@ -104,11 +106,21 @@ def _fine_wavevectors(N: int, dx: float, lam: int) -> np.ndarray:
     return 2.0 * np.pi * symmetric_index(lam * N).astype(np.float64) / (lam * L)
 
 
+def fine_wavevectors(N: int, dx: float, lam: int) -> np.ndarray:
+    """The lam N huge-lattice wavevectors k_u in index order u (eq. ulk): the
+    points at which a dispersion omega is sampled for ``omega=`` below."""
+    return _fine_wavevectors(N, dx, lam)
+
+
 def axis_matrix(N: int, dx: float, t: float, lam: int,
-                a: float | None = None, abar: float | None = None) -> np.ndarray:
+                a: float | None = None, abar: float | None = None, omega=None) -> np.ndarray:
     """Dense 1-D free-flight map T[nbar, n] (complex128, N x N).
 
     T[nbar, n] = (1/(lam N)) sum_u exp(i k_u (xbar_nbar - x_n) - i t k_u^2/2).
+
+    Other spectra (Sec. 7, Generalizations): with ``omega`` (lam N values,
+    omega[u] at k_u) the free-particle phase t k_u^2 / 2 becomes t omega[u]
+    (the momentum-space evolution exp(-i t omega_k) replaces eq. free0).
 
     Writing s = (abar - a)/dx = s0 + sf (s0 integer, 0 <= sf < 1) gives
     xbar_nbar - x_n = (s0 + lam nbar - n + sf) dx, and since
@@ -131,7 +143,14 @@ def axis_matrix(N: int, dx: float, t: float, lam: int,
     s = (abar - a) / dx
     s0 = math.floor(s)
     sf = s - s0
-    spec = np.exp(-0.5j * t * k * k + 1j * k * (sf * dx))
+    if omega is None:
+        phase = 0.5 * t * k * k
+    else:
+        omega = np.asarray(omega, dtype=np.float64)
+        if omega.shape != (NN,):
+            raise ValueError("omega must hold lam*N values")
+        phase = t * omega
+    spec = np.exp(-1j * phase + 1j * k * (sf * dx))
     K = np.fft.ifft(spec)  # includes the 1/(lam N)
     nbar = np.arange(N, dtype=np.int64)
     n = np.arange(N, dtype=np.int64)
@@ -164,13 +183,16 @@ def _as_tuple(v, d, name):
     return v
 
 
-def _axis_matrices(dims, dx, t, lam, a, abar):
+def _axis_matrices(dims, dx, t, lam, a, abar, omega=None):
     d = len(dims)
     dx = _as_tuple(dx, d, "dx")
     lam = _as_tuple(lam, d, "lam")
     a = _as_tuple(a, d, "a") if a is not None else (None,) * d
     abar = _as_tuple(abar, d, "abar") if abar is not None else (None,) * d
-    return [axis_matrix(int(dims[j]), float(dx[j]), float(t), int(lam[j]), a[j], abar[j])
+    omega = tuple(omega) if omega is not None else (None,) * d
+    if len(omega) != d:
+        raise ValueError(f"omega must have {d} entries")
+    return [axis_matrix(int(dims[j]), float(dx[j]), float(t), int(lam[j]), a[j], abar[j], omega[j])
             for j in range(d)]
 
 
@@ -179,26 +201,27 @@ def _apply_along(T: np.ndarray, psi: np.ndarray, axis: int) -> np.ndarray:
     return np.moveaxis(out, 0, axis)
 
 
-def expand_field(psi0, dx, t, lam, a=None, abar=None) -> np.ndarray:
+def expand_field(psi0, dx, t, lam, a=None, abar=None, omega=None) -> np.ndarray:
     """Psibar on the magnified lattice for a batch psi0[..., M_1, ..., M_d].
 
     ``dx``, ``lam``, ``a``, ``abar`` are scalars or per-axis sequences; the last
     len(dx) axes (or 1 if scalar) are the lattice axes.  psi0 is promoted to
     complex128 first, so an input already rounded to complex64 is taken as
-    exact.
+    exact.  ``omega``: per axis None (free particle) or the lam_j N_j values of
+    a separable dispersion omega_j at ``fine_wavevectors`` (Sec. 7).
     """
     psi = np.asarray(psi0).astype(np.complex128)
     d = len(dx) if not np.isscalar(dx) else 1
     dims = psi.shape[psi.ndim - d:]
-    Ts = _axis_matrices(dims, dx, t, lam, a, abar)
+    Ts = _axis_matrices(dims, dx, t, lam, a, abar, omega)
     for j in range(d):
         psi = _apply_along(Ts[j], psi, psi.ndim - d + j)
     return psi
 
 
-def expand_density(psi0, dx, t, lam, a=None, abar=None) -> np.ndarray:
+def expand_density(psi0, dx, t, lam, a=None, abar=None, omega=None) -> np.ndarray:
     """rho = |Psibar|^2 per realization (Sec. 2, the measured density)."""
-    f = expand_field(psi0, dx, t, lam, a, abar)
+    f = expand_field(psi0, dx, t, lam, a, abar, omega)
     return f.real ** 2 + f.imag ** 2
 
 
@@ -248,6 +271,29 @@ def sample_lines(psi0, dx, t, lam, axis: int, index: tuple, a=None, abar=None) -
     for j, nb in sorted(zip(other, index), reverse=True):
         v = np.tensordot(v, Ts[j][nb], axes=([j], [0]))
     return Ts[axis] @ v
+
+
+def positive_p_density(psi0, psi0_plus, dx, t, lam, a=None, abar=None, omega=None) -> np.ndarray:
+    """Density of a positive-P pair after free flight (Sec. 7, Generalizations).
+
+    The two independent fields psi (for the annihilation field) and psi+ (for
+    the creation field) evolve by the map and by its complex conjugate:
+    Psibar = T psi0, Psibar+ = conj(T) psi0+ (the conjugate equation of
+    motion; T the per-axis maps as in ``expand_field``).  The normally
+    ordered density is Re(Psibar+ Psibar).  With psi0+ = conj(psi0) it is
+    |Psibar|^2.
+    """
+    psi = np.asarray(psi0).astype(np.complex128)
+    psp = np.asarray(psi0_plus).astype(np.complex128)
+    if psi.shape != psp.shape:
+        raise ValueError("psi0 and psi0_plus must have the same shape")
+    d = len(dx) if not np.isscalar(dx) else 1
+    dims = psi.shape[psi.ndim - d:]
+    Ts = _axis_matrices(dims, dx, t, lam, a, abar, omega)
+    for j in range(d):
+        psi = _apply_along(Ts[j], psi, psi.ndim - d + j)
+        psp = _apply_along(Ts[j].conj(), psp, psp.ndim - d + j)
+    return (psp * psi).real
 
 
 # ---------------------------------------------------------------------------

@@ -402,3 +402,65 @@ def test_fringe_phase_vertex_and_nearest_peak():
     assert both[0] == est and np.isnan(both[1])
     # the y axis may be any axis of the image
     assert O.fringe_phase(img.T, y, D, t, y_axis=0)[0] == est
+
+
+# ---------------------------------------------------------------------------
+# generalizations (Sec. 7): other spectra, positive-P pairs
+# ---------------------------------------------------------------------------
+
+def test_dispersion_free_particle_and_offsets():
+    """omega = k^2/2 given as a table is the free map exactly; a constant
+    offset omega + V only multiplies the field by exp(-i V t)."""
+    dims, dx, lam, t = (24, 20), (0.3, 0.25), (3, 5), 2.5
+    rng = np.random.default_rng(71)
+    psi = rng.normal(size=dims) + 1j * rng.normal(size=dims)
+    ks = [O.fine_wavevectors(dims[j], dx[j], lam[j]) for j in range(2)]
+    free = O.expand_field(psi, dx, t, lam)
+    tab = O.expand_field(psi, dx, t, lam, omega=[0.5 * k * k for k in ks])
+    assert np.abs(tab - free).max() < 1e-13 * np.abs(free).max()
+    V = 0.37
+    off = O.expand_field(psi, dx, t, lam, omega=[0.5 * ks[0] ** 2 + V, None])
+    assert np.abs(off - np.exp(-1j * V * t) * free).max() < 1e-12 * np.abs(free).max()
+
+
+@pytest.mark.parametrize("N,lam,m", [(16, 3, 5), (15, 4, -7), (12, 1, 3)])
+def test_linear_dispersion_is_a_translation(N, lam, m):
+    """omega = v k with v t = m dx moves the field by m huge-lattice points:
+    Psibar_nbar = psi_n where s + lam nbar - n = m (mod lam N), vacuum
+    elsewhere (eq. free0 with a linear spectrum)."""
+    dx, t = 0.2, 1.7
+    v = m * dx / t
+    rng = np.random.default_rng(N + m)
+    psi = rng.normal(size=N) + 1j * rng.normal(size=N)
+    k = O.fine_wavevectors(N, dx, lam)
+    out = O.expand_field(psi, (dx,), t, (lam,), omega=[v * k])
+    a = O.default_a(N, dx)
+    s0 = round((O.default_abar(N, dx, lam, a) - a) / dx)
+    ex = np.zeros(N, complex)
+    for nb in range(N):
+        for n in range(N):
+            if (s0 + lam * nb - n - m) % (lam * N) == 0:
+                ex[nb] += psi[n]
+    assert np.abs(out - ex).max() < 1e-12
+
+
+def test_positive_p_pair():
+    """psi+ = conj(psi) gives |Psibar|^2; the density is bilinear: it is
+    linear in psi+ for fixed psi; and psi+ evolves by conj(T), so swapping
+    the roles of the pair conjugates the product Psibar+ Psibar."""
+    dims, dx, lam, t = (20, 18), (0.3, 0.25), (4, 3), 1.5
+    rng = np.random.default_rng(5)
+    psi = rng.normal(size=dims) + 1j * rng.normal(size=dims)
+    pp1 = rng.normal(size=dims) + 1j * rng.normal(size=dims)
+    pp2 = rng.normal(size=dims) + 1j * rng.normal(size=dims)
+    rho = O.positive_p_density(psi, np.conj(psi), dx, t, lam)
+    assert np.abs(rho - O.expand_density(psi, dx, t, lam)).max() < 1e-12 * rho.max()
+    lin = O.positive_p_density(psi, pp1 + 2.5 * pp2, dx, t, lam)
+    assert np.abs(lin - O.positive_p_density(psi, pp1, dx, t, lam)
+                  - 2.5 * O.positive_p_density(psi, pp2, dx, t, lam)).max() < 1e-11 * np.abs(lin).max()
+    # Re(conj(T) a * T b) = Re(T conj(a) * conj(T) conj(b)): the pair (conj a, conj b) swapped
+    r1 = O.positive_p_density(psi, pp1, dx, t, lam)
+    r2 = O.positive_p_density(np.conj(pp1), np.conj(psi), dx, t, lam)
+    assert np.abs(r1 - r2).max() < 1e-12 * np.abs(r1).max()
+    # and it is not |.|^2 of either field alone
+    assert np.abs(r1 - O.expand_density(psi, dx, t, lam)).max() > 1e-3
