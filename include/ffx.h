@@ -127,6 +127,27 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
 int ffx_plan_destroy(ffx_plan_t plan);
 
 /*
+ * ffx_plan_dispersion -- as ffx_plan, for a spectrum other than the free
+ * particle's (Sec. 7, Generalizations): the momentum-space evolution
+ * exp(-i t omega(k)) replaces exp(-i t k^2 / 2) of eq. free0.  The dispersion
+ * is separable, omega(k) = sum_j omega_j(k_j), so the map keeps its per-axis
+ * form.
+ *
+ *  omega       NULL (every axis free), or ndim host pointers: NULL for a free
+ *              axis, else lam_j * dims[j] finite doubles, omega_j sampled at
+ *              the huge-lattice wavevectors k_u = 2 pi u~ / (lam_j L_j),
+ *              u = 0 .. lam_j dims[j] - 1, u~ the symmetric index of u on
+ *              lam_j dims[j] points (u~ = u below half, u - lam_j dims[j] from
+ *              half on).  Read once at plan creation.
+ *  The phases t omega are reduced to turns in FP64 on the host; free axes
+ *  keep the exact fixed-point reduction.  Every form and call of the plan
+ *  applies the generalized map.
+ */
+int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spacing, double t,
+                        const int32_t* magnification, const double* a, const double* abar,
+                        const double* const* omega, uint32_t flags);
+
+/*
  * ffx_plan_many -- one plan over many instances of possibly different
  * lattices, magnifications and flight times (an ensemble of realizations,
  * Sec. 1), run as one persistent kernel per axis pass over a work list of all
@@ -274,6 +295,22 @@ int ffx_supported_length(int64_t n);
  */
 int ffx_expand_column(ffx_plan_t plan, const void* psi0, int64_t batch, int axis, float* out_column,
                       void* stream);
+
+/*
+ * ffx_expand_positive_p -- the density of positive-P pairs after free flight
+ * (Sec. 7, Generalizations).  The field psi0 (for the annihilation operator)
+ * evolves by the map T, the independent field psi0_plus (for the creation
+ * operator) by its complex conjugate conj(T); the normally ordered density is
+ *   out_density = Re(Psibar+ * Psibar),  Psibar = T psi0, Psibar+ = conj(T) psi0_plus,
+ * per realization [batch][M...], or with FFX_ACCUMULATE summed over the batch
+ * (in order) and added to out_density [M...].  With psi0_plus = conj(psi0) it
+ * is |Psibar|^2.  conj(T) psi0_plus is computed as conj(T conj(psi0_plus)):
+ * both fields run through the same passes.  Uses plan workspace (two
+ * batch * M complex64 fields besides the passes' own).  Not for
+ * many-instance plans (FFX_EUNSUPPORTED).
+ */
+int ffx_expand_positive_p(ffx_plan_t plan, const void* psi0, const void* psi0_plus, int64_t batch,
+                          float* out_density, void* stream);
 
 /* Positions of the magnified output lattice along `axis` (eq. wbx):
  * xbar_n = *x0 + n * *step, with *x0 = abar_axis, *step = lam_axis * spacing_axis. */

@@ -147,8 +147,10 @@ struct ffx_plan_s {
   int64_t fused = 0;             // largest batch whose forward calls run as one launch (ffx_fused.cu)
   int fused_grid = 0;
   size_t fused_smem_bytes = 0;
-  void* ws[3] = {nullptr, nullptr, nullptr};  // workspace buffers (grown on demand; [2]: detector densities)
-  size_t ws_bytes[3] = {0, 0, 0};
+  // workspace buffers, grown on demand: [0], [1] the passes' fields; [2] the
+  // detector densities, or a positive-P pair's first field; [3] its second
+  void* ws[4] = {nullptr, nullptr, nullptr, nullptr};
+  size_t ws_bytes[4] = {0, 0, 0, 0};
   ManyPlan* many = nullptr;       // set for plans over many instances
   void* const* trace = nullptr;   // caller's cudaEvent_t array (profiling)
   int64_t trace_n = 0;
@@ -657,6 +659,12 @@ int ffx_supported_length(int64_t n) { return supported_length(n) ? 1 : 0; }
 
 int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spacing, double t,
              const int32_t* magnification, const double* a, const double* abar, uint32_t flags) {
+  return ffx_plan_dispersion(out, ndim, dims, spacing, t, magnification, a, abar, nullptr, flags);
+}
+
+int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spacing, double t,
+                        const int32_t* magnification, const double* a, const double* abar,
+                        const double* const* omega, uint32_t flags) {
   g_last_error.clear();
   if (!out) return fail(FFX_EINVAL, "out is NULL");
   *out = nullptr;
@@ -681,6 +689,11 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
       return fail(FFX_EINVAL, "offsets must be finite");
     if (!supported_length(dims[j]))
       return fail(FFX_EUNSUPPORTED, "no line kernel for length %lld (axis %d)", (long long)dims[j], j);
+    if (omega && omega[j]) {
+      const int64_t lN = (int64_t)magnification[j] * dims[j];
+      for (int64_t u = 0; u < lN; ++u)
+        if (!std::isfinite(omega[j][u])) return fail(FFX_EINVAL, "omega[%d][%lld] is not finite", j, (long long)u);
+    }
     if ((form == FFX_FORM_DENSE || form == FFX_FORM_TC) && dims[j] > kDenseMaxN)
       return fail(FFX_EUNSUPPORTED, "the dense form takes lines up to %d points (axis %d has %lld)",
                   kDenseMaxN, j, (long long)dims[j]);
@@ -760,12 +773,34 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
     ax.fold = (int*)cur;
     cur += ((size_t)N * sizeof(int) + 255) & ~size_t(255);
 
-    // phase constants in turns (hbar = m = 1): s = (abar - a)/dx, tau = pi t / L^2
+    // phase constants in turns (hbar = m = 1): s = (abar - a)/dx, tau = pi t / L^2;
+    // another spectrum (Sec. 7) replaces the tau terms by a per-wavevector table
     const double sv = (ax.abar - ax.a) / ax.dx;
-    const double tau = M_PI * t / (L * L);
+    const bool disp = omega && omega[j];
+    const double tau = disp ? 0.0 : M_PI * t / (L * L);
+    uint64_t* disp_d = nullptr;
+    if (disp) {
+      std::vector<uint64_t> disp_h((size_t)lam * N);
+      for (size_t u = 0; u < disp_h.size(); ++u) disp_h[u] = frac_fx(-t * omega[j][u] / (2.0 * M_PI));
+      e = cudaMalloc(&disp_d, disp_h.size() * sizeof(uint64_t));
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(disp_d, disp_h.data(), disp_h.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // disp_h goes out of scope
+      if (e != cudaSuccess) {
+        if (disp_d) cudaFree(disp_d);
+        cudaGetLastError();
+        rc = fail(FFX_ENOMEM, "dispersion table: %s", cudaGetErrorString(e));
+        break;
+      }
+    }
     e = launch_fill_tables(N, lam, frac_fx(sv / N), frac_fx(tau), frac_fx(2.0 * tau / lam),
-                           frac_fx(sv / ((double)lam * N)), frac_fx(tau / ((double)lam * lam)), ax.P, ax.K,
-                           ax.Kf, ax.F, ax.tw, s);
+                           frac_fx(sv / ((double)lam * N)), frac_fx(tau / ((double)lam * lam)), disp_d, ax.P,
+                           ax.K, ax.Kf, ax.F, ax.tw, s);
+    if (disp_d) {
+      const cudaError_t e2 = cudaStreamSynchronize(s);
+      cudaFree(disp_d);
+      if (e == cudaSuccess) e = e2;
+    }
     if (e != cudaSuccess) {
       rc = cuda_fail(e, "table fill");
       break;
@@ -939,7 +974,7 @@ int ffx_plan(ffx_plan_t* out, int ndim, const int64_t* dims, const double* spaci
   if (rc == FFX_OK) rc = plan_fusion(p);
   cudaStreamDestroy(s);
   if (rc != FFX_OK) {
-    for (int w = 0; w < 3; ++w)
+    for (int w = 0; w < 4; ++w)
       if (p->ws[w]) cudaFree(p->ws[w]);
     if (p->dense_mem) cudaFree(p->dense_mem);
     if (p->tc_mem) cudaFree(p->tc_mem);
@@ -987,7 +1022,7 @@ int ffx_plan_destroy(ffx_plan_t p) {
     delete p;
     return FFX_OK;
   }
-  for (int w = 0; w < 3; ++w)
+  for (int w = 0; w < 4; ++w)
     if (p->ws[w]) cudaFree(p->ws[w]);
   if (p->dense_mem) cudaFree(p->dense_mem);
   if (p->tc_mem) cudaFree(p->tc_mem);
@@ -1037,7 +1072,7 @@ int ffx_plan_device_errors(ffx_plan_t p) {
 int64_t ffx_workspace_bytes(ffx_plan_t p, int64_t batch) {
   if (!p || batch < 0) return -1;
   int64_t total = 0;
-  for (int w = 0; w < 3; ++w) total += (int64_t)p->ws_bytes[w];
+  for (int w = 0; w < 4; ++w) total += (int64_t)p->ws_bytes[w];
   const int64_t need = batch * p->M * (int64_t)sizeof(float2);
   return total > need ? total : need;
 }
@@ -1132,6 +1167,35 @@ int ffx_expand_column(ffx_plan_t p, const void* psi0, int64_t batch, int axis, f
   cudaError_t e = launch_axis_sum(rho, p->acc ? outer : batch * outer, ax.N, inner, (float)(ax.lam * ax.dx), p->acc,
                                   out_column, p->sms, s);
   return e == cudaSuccess ? FFX_OK : cuda_fail(e, "column sum");
+}
+
+// The forward field map of a batch into `out` (may equal `in`): the fused
+// launch for small batches, else the pass chain (ws[0], ws[1] as spares).
+int field_into(ffx_plan_s* p, const float2* in, int64_t batch, float2* out, cudaStream_t s) {
+  if (batch <= p->fused) return run_fused(p, p->order, in, out, nullptr, nullptr, batch, s);
+  return chain_into(p, p->order, false, in, nullptr, 0, batch, out, 0, s);
+}
+
+int ffx_expand_positive_p(ffx_plan_t p, const void* psi0, const void* psi0_plus, int64_t batch, float* out_density,
+                          void* stream) {
+  if (!p) return fail(FFX_EINVAL, "plan is NULL");
+  if (batch < 0) return fail(FFX_EINVAL, "batch < 0");
+  if (p->many) return fail(FFX_EUNSUPPORTED, "ffx_expand_positive_p does not take a many-instance plan");
+  if (batch == 0) return FFX_OK;
+  int rc;
+  if ((rc = check_ptr(psi0, "psi0")) || (rc = check_ptr(psi0_plus, "psi0_plus")) ||
+      (rc = check_ptr(out_density, "out_density")))
+    return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rc = ensure_ws(p, 2, batch)) || (rc = ensure_ws(p, 3, batch))) return rc;
+  float2* w1 = (float2*)p->ws[2];
+  float2* w2 = (float2*)p->ws[3];
+  if ((rc = field_into(p, (const float2*)psi0, batch, w1, s))) return rc;
+  cudaError_t e = launch_conj_copy((const float2*)psi0_plus, w2, batch * p->M, p->sms, s);
+  if (e != cudaSuccess) return cuda_fail(e, "conjugate copy");
+  if ((rc = field_into(p, w2, batch, w2, s))) return rc;
+  e = launch_pair_density(w1, w2, p->M, batch, p->acc, out_density, p->sms, s);
+  return e == cudaSuccess ? FFX_OK : cuda_fail(e, "pair density");
 }
 
 int ffx_plan_output_axis(ffx_plan_t p, int axis, double* x0, double* step) {

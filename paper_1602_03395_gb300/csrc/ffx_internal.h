@@ -149,6 +149,11 @@ cudaError_t launch_axis_sum(const float* rho, int64_t outer, int N, int64_t inne
                             int sms, cudaStream_t s);
 cudaError_t launch_fringe(const float* img, int64_t rows, int64_t ny, int64_t rs, int64_t ys, double y0, double dy,
                           double D, double t, double* out, int sms, cudaStream_t s);
+
+// Positive-P pairs (ffx_pairs.cu).
+cudaError_t launch_conj_copy(const float2* in, float2* out, int64_t n, int sms, cudaStream_t s);
+cudaError_t launch_pair_density(const float2* w1, const float2* w2, int64_t M, int64_t batch, int acc, float* out,
+                                int sms, cudaStream_t s);
 cudaError_t launch_dense_build(const float2* O, float2* T, float2* TH, int N, cudaStream_t s);
 
 // Plans over many instances (ffx_many.cu).
@@ -165,7 +170,7 @@ int many_backward(ManyPlan* mp, const void* psi0, const float* grad, void* grad_
 
 // Plan-time table fill (one launch per axis).
 cudaError_t launch_fill_tables(int N, int lam, uint64_t c_sN, uint64_t c_tau, uint64_t c_2tl,
-                               uint64_t c_slN, uint64_t c_tl2, float2* P, float2* K, float2* Kf,
-                               float2* F, float2* tw, cudaStream_t stream);
+                               uint64_t c_slN, uint64_t c_tl2, const uint64_t* disp, float2* P, float2* K,
+                               float2* Kf, float2* F, float2* tw, cudaStream_t stream);
 
 }  // namespace ffx

@@ -354,7 +354,7 @@ int many_create(ManyPlan** out, int n, const ffx_instance_desc* d, uint32_t flag
     const double L = at.N * dx, sv = (ab - a) / dx, tau = M_PI * t / (L * L);
     e = launch_fill_tables(at.N, at.lam, frac_fx64(sv / at.N), frac_fx64(tau), frac_fx64(2.0 * tau / at.lam),
                            frac_fx64(sv / ((double)at.lam * at.N)), frac_fx64(tau / ((double)at.lam * at.lam)),
-                           P, K, Kf, F, tw, s);
+                           nullptr, P, K, Kf, F, tw, s);
     if (e != cudaSuccess) {
       rc = FFX_ECUDA;
       *err = std::string("table fill: ") + cudaGetErrorString(e);

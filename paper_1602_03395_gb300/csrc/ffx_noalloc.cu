@@ -192,7 +192,7 @@ extern "C" int ffx_expand_noalloc(int ndim, const int64_t* dims, const double* s
     const double sv = (abj - aj) / dx, tau = M_PI * t / (L * L);
     e = launch_fill_tables(A.N, A.lam, frac_turns(sv / A.N), frac_turns(tau), frac_turns(2.0 * tau / A.lam),
                            frac_turns(sv / ((double)A.lam * A.N)), frac_turns(tau / ((double)A.lam * A.lam)),
-                           P, K, Kf, F, tw, s);
+                           nullptr, P, K, Kf, F, tw, s);
     if (e != cudaSuccess) return nfail(FFX_ECUDA, "table fill: %s", cudaGetErrorString(e));
     const int64_t inv = inverse_mod((A.lam / A.g) % A.Np, A.Np);
     noalloc_fold_kernel<<<(A.N + 255) / 256, 256, 0, s>>>(fcur, A.N, A.g, A.Np, (long long)inv);

@@ -8,6 +8,13 @@
 // turn in [-1/2, 1/2) then goes through double-precision sincospi and is
 // rounded once to float.  Arguments of 10^4..10^6 rad therefore cost no
 // precision.
+//
+// Other spectra (Sec. 7): with a dispersion table (disp != null) the phase
+// -t omega(k) of the huge-lattice wavevector k = 2 pi (lam l + q) / (lam L)
+// replaces the free-particle terms -tau (l + q/lam)^2.  It depends on q and m
+// together, so all of it goes into K (and Kf); F keeps only the shift terms.
+// The host passes the table as fixed-point turns frac(-t omega / 2 pi) per
+// huge-lattice index u, and zero for the tau constants.
 #include "ffx_internal.h"
 
 namespace ffx {
@@ -22,6 +29,7 @@ __device__ __forceinline__ float2 turn_to_unit(uint64_t fx, double scale) {
 struct TableArgs {
   int N, lam;
   uint64_t c_sN, c_tau, c_2tl, c_slN, c_tl2, c_N, c_lamN;
+  const uint64_t* disp;  // [lam N] fixed-point turns of -t omega(k_u), or null (free particle)
   float2 *P, *K, *Kf, *F, *tw;
 };
 
@@ -39,7 +47,13 @@ __global__ void fill_tables_kernel(const TableArgs a) {
     // k-space phase with the symmetric index and the odd-N umklapp
     int64_t l = (2 * n < N) ? n : n - N;
     if ((N & 1) && n == (N - 1) / 2 && 2 * q >= a.lam) l = -(int64_t)(N + 1) / 2;
-    const uint64_t fk = (uint64_t)l * a.c_sN - (uint64_t)(l * l) * a.c_tau - (uint64_t)(l * q) * a.c_2tl;
+    uint64_t fk = (uint64_t)l * a.c_sN - (uint64_t)(l * l) * a.c_tau - (uint64_t)(l * q) * a.c_2tl;
+    if (a.disp) {
+      // huge-lattice index of k = 2 pi (lam l + q) / (lam L)
+      const int64_t lamN = (int64_t)a.lam * N;
+      const int64_t u = (((int64_t)a.lam * l + q) % lamN + lamN) % lamN;
+      fk += a.disp[u];
+    }
     a.K[idx] = turn_to_unit(fk, 1.0);
     const uint64_t fq = (uint64_t)q * a.c_slN - (uint64_t)(q * q) * a.c_tl2;
     a.Kf[idx] = turn_to_unit(fk + fq, inv_lamN);
@@ -51,9 +65,10 @@ __global__ void fill_tables_kernel(const TableArgs a) {
 }
 
 cudaError_t launch_fill_tables(int N, int lam, uint64_t c_sN, uint64_t c_tau, uint64_t c_2tl,
-                               uint64_t c_slN, uint64_t c_tl2, float2* P, float2* K, float2* Kf,
-                               float2* F, float2* tw, cudaStream_t stream) {
+                               uint64_t c_slN, uint64_t c_tl2, const uint64_t* disp, float2* P, float2* K,
+                               float2* Kf, float2* F, float2* tw, cudaStream_t stream) {
   TableArgs a;
+  a.disp = disp;
   a.N = N;
   a.lam = lam;
   a.c_sN = c_sN;

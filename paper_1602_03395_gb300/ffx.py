@@ -16,6 +16,8 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
+
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -61,6 +63,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ffx_plan.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(i64), ctypes.POINTER(dbl), dbl,
                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(dbl), ctypes.POINTER(dbl), u32]
     lib.ffx_plan.restype = i32
+    lib.ffx_plan_dispersion.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(i64), ctypes.POINTER(dbl), dbl,
+                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(dbl), ctypes.POINTER(dbl),
+                                        ctypes.POINTER(ctypes.POINTER(dbl)), u32]
+    lib.ffx_plan_dispersion.restype = i32
     lib.ffx_plan_destroy.argtypes = [vp]
     lib.ffx_plan_destroy.restype = i32
     lib.ffx_expand.argtypes = [vp, vp, i64, vp, vp]
@@ -85,6 +91,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ffx_plan_fused.restype = i64
     lib.ffx_plan_call_form.argtypes = [vp, i32, i64]
     lib.ffx_plan_call_form.restype = i32
+    lib.ffx_expand_positive_p.argtypes = [vp, vp, vp, i64, vp, vp]
+    lib.ffx_expand_positive_p.restype = i32
     lib.ffx_expand_column.argtypes = [vp, vp, i64, i32, vp, vp]
     lib.ffx_expand_column.restype = i32
     lib.ffx_plan_output_axis.argtypes = [vp, i32, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
@@ -146,11 +154,20 @@ def ffx_supported_length(n: int) -> bool:
     return bool(load_library().ffx_supported_length(int(n)))
 
 
+def fine_wavevectors(N: int, dx: float, lam: int) -> np.ndarray:
+    """The lam N huge-lattice wavevectors k_u = 2 pi u~ / (lam N dx), u~ the
+    symmetric index of u (the sample points of a dispersion for ``omega=``)."""
+    M = lam * N
+    u = np.arange(M)
+    return 2.0 * np.pi * np.where(2 * u < M, u, u - M) / (lam * N * dx)
+
+
 class Plan:
     """A plan for one geometry (dims, spacing, t, magnification, offsets)."""
 
     def __init__(self, dims, spacing, t, magnification, a=None, abar=None,
-                 form: str = "auto", accumulate: bool = False, tune: bool = False, fused: bool = True):
+                 form: str = "auto", accumulate: bool = False, tune: bool = False, fused: bool = True,
+                 omega=None):
         lib = load_library()
         d = len(dims)
         self.dims = tuple(int(v) for v in dims)
@@ -162,10 +179,27 @@ class Plan:
                  | (0 if fused else FFX_UNFUSED))
         arr = lambda ct, v: (ct * d)(*v) if v is not None else None  # noqa: E731
         h = ctypes.c_void_p()
-        _check(lib.ffx_plan(ctypes.byref(h), d, arr(ctypes.c_int64, self.dims),
-                            arr(ctypes.c_double, self.spacing), self.t,
-                            arr(ctypes.c_int32, self.magnification),
-                            arr(ctypes.c_double, a), arr(ctypes.c_double, abar), flags), "ffx_plan")
+        if omega is None:
+            _check(lib.ffx_plan(ctypes.byref(h), d, arr(ctypes.c_int64, self.dims),
+                                arr(ctypes.c_double, self.spacing), self.t,
+                                arr(ctypes.c_int32, self.magnification),
+                                arr(ctypes.c_double, a), arr(ctypes.c_double, abar), flags), "ffx_plan")
+        else:
+            # per axis None (free) or lam_j N_j values of omega_j at fine_wavevectors(...)
+            if len(omega) != d:
+                raise ValueError(f"omega needs {d} entries")
+            keep = [None if w is None else np.ascontiguousarray(w, dtype=np.float64) for w in omega]
+            ptrs = (ctypes.POINTER(ctypes.c_double) * d)()
+            for j, w in enumerate(keep):
+                if w is not None:
+                    if w.shape != (self.magnification[j] * self.dims[j],):
+                        raise ValueError(f"omega[{j}] must hold lam*N = {self.magnification[j] * self.dims[j]} values")
+                    ptrs[j] = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            _check(lib.ffx_plan_dispersion(ctypes.byref(h), d, arr(ctypes.c_int64, self.dims),
+                                           arr(ctypes.c_double, self.spacing), self.t,
+                                           arr(ctypes.c_int32, self.magnification),
+                                           arr(ctypes.c_double, a), arr(ctypes.c_double, abar), ptrs, flags),
+                   "ffx_plan_dispersion")
         self._h = h
         self.form = _FORM_NAMES[lib.ffx_plan_form(h)]
         self.axis_forms = tuple(_FORM_NAMES[lib.ffx_plan_axis_form(h, j)] for j in range(d))
@@ -376,6 +410,23 @@ def ffx_expand_column(plan: Plan, psi0: torch.Tensor, axis: int, out_column: tor
     _check(load_library().ffx_expand_column(plan.handle, _ptr(psi0), B, axis, _ptr(out_column), _stream(stream)),
            "ffx_expand_column")
     return out_column
+
+
+def ffx_expand_positive_p(plan: Plan, psi0: torch.Tensor, psi0_plus: torch.Tensor,
+                          out_density: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Re(Psibar+ Psibar) of positive-P pairs: psi0 by the map, psi0_plus by its conjugate."""
+    _need(psi0, torch.complex64, "psi0")
+    _need(psi0_plus, torch.complex64, "psi0_plus")
+    if psi0_plus.shape != psi0.shape:
+        raise ValueError("psi0 and psi0_plus must have the same shape")
+    B = plan._batch(psi0)
+    if out_density is None:
+        shape = plan.dims if plan.accumulate else psi0.shape
+        out_density = torch.zeros(shape, dtype=torch.float32, device=psi0.device)
+    _need(out_density, torch.float32, "out_density")
+    _check(load_library().ffx_expand_positive_p(plan.handle, _ptr(psi0), _ptr(psi0_plus), B, _ptr(out_density),
+                                                _stream(stream)), "ffx_expand_positive_p")
+    return out_density
 
 
 def output_axis(plan: Plan, axis: int):
