@@ -554,11 +554,13 @@ def run_ffx(args):
     hbm_peak = float(pk.get("hbm_gbs", 6800.0))
     out_bytes = 4 * int(np.prod(out_shape))
     if fused_call:
-        # one cooperative launch runs every pass (dense, FP32 SIMT); HBM sees
-        # the input read and the density written, the intermediates stay in L2
-        axis_form = "fused"
+        # one cooperative launch runs every pass (dense map: FP32 SIMT, or the
+        # tensor cores when every axis has 64 points); HBM sees the input read
+        # and the output written, the intermediates stay in L2
+        fused_tc = call_forms[0] == "tc"
+        axis_form = "tc" if fused_tc else "fused"
         flops = sum(pass_flops(w.dims[j], w.lam[j], B_ * M // w.dims[j], "dense") for j in order)
-        kernel_key = f"fused_dense_{'x'.join(map(str, w.dims))}_{args.workload}"
+        kernel_key = f"fused_{'tc' if fused_tc else 'dense'}_{'x'.join(map(str, w.dims))}_{args.workload}"
         if args.column is not None:
             kernel_key += f"_column{args.column}"
         traffic = load_traffic(f"{kernel_key}_b{B_}")

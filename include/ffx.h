@@ -353,12 +353,18 @@ int ffx_launches_per_call(ffx_plan_t plan, int backward);
 
 /* The largest batch for which ffx_expand and ffx_expand_field run as one
  * fused launch (see FFX_UNFUSED): a batch whose first pass has at most two
- * 32-line tiles per SM.  0 if the plan never fuses, -1 for a NULL plan. */
+ * 32-line tiles per SM.  0 if the plan never fuses, -1 for a NULL plan.
+ * When every axis has 64 points and the plan's form is FFX_FORM_AUTO or
+ * FFX_FORM_TC, the fused launch forms its products on the tensor cores
+ * (split TF32, as FFX_FORM_TC) for a 16-byte-aligned psi0; otherwise with the
+ * FP32 dense arithmetic, bitwise equal to the per-axis FFX_FORM_DENSE passes. */
 int64_t ffx_plan_fused(ffx_plan_t plan);
 
 /* The form whose kernel a forward call with this batch runs on lattice axis
- * `axis`: the axis's form, except that under FFX_FORM_AUTO a dense axis whose
- * pass covers at least 128 lines per SM runs on the tensor cores
+ * `axis`: for a fused call the fused launch's arithmetic (FFX_FORM_TC or
+ * FFX_FORM_DENSE, see ffx_plan_fused); else the axis's form, except that
+ * under FFX_FORM_AUTO a dense axis whose pass covers at least 128 lines per
+ * SM runs on the tensor cores
  * (FFX_FORM_TC; a 16-byte-misaligned buffer still takes the FP32 kernel).
  * Results of the two kernels agree to rounding (within the FP32 tolerance),
  * not bit for bit; explicit forms never switch.  -1 on a bad argument or a

@@ -117,6 +117,7 @@ struct Axis {
   float2* TH = nullptr;  // its adjoint
   int grid_dense = 0, grid_dense_small = 0;
   unsigned char* tc_t[2] = {nullptr, nullptr};  // split tensor-core operands of T, T^H (ffx_tc.cu)
+  unsigned char* ft_ts = nullptr;                 // N = 64: T's row-block slices for the fused tensor-core launch
   float2* img[2] = {nullptr, nullptr};                      // lines <= 64: shared-memory images of T, T^H
 };
 
@@ -146,6 +147,8 @@ struct ffx_plan_s {
   unsigned* grid_bar = nullptr;  // arrival counter of the fused kernel's grid barriers
   int64_t fused = 0;             // largest batch whose forward calls run as one launch (ffx_fused.cu)
   int fused_grid = 0;
+  int fused_tc = 0;              // ... on the tensor cores (every axis 64 points, automatic or tc form)
+  int fused_tc_grid = 0;
   size_t fused_smem_bytes = 0;
   // workspace buffers, grown on demand: [0], [1] the passes' fields; [2] the
   // detector densities, or a positive-P pair's first field; [3] its second
@@ -450,6 +453,20 @@ int plan_fusion(ffx_plan_s* p) {
   p->fused = std::max<int64_t>(1, 2 * (int64_t)p->sms / tiles);
   p->fused_grid = p->sms;  // one block per SM (every block is resident: cooperative launch)
   p->fused_smem_bytes = smem;
+  // Every axis 64 points with its tensor-core slices, and a form that allows
+  // the tensor cores: the fused launch runs the products on them.
+  const uint32_t form = p->flags & FFX_FORM_MASK;
+  bool tc_ok = (form == FFX_FORM_AUTO || form == FFX_FORM_TC) && p->sms >= 4;
+  for (int k = 0; k < p->ndim; ++k) tc_ok = tc_ok && p->axis[k].N == 64 && p->axis[k].ft_ts;
+  if (tc_ok) {
+    int tc_per_sm = 0;
+    if (fused_tc_prepare(&tc_per_sm) == cudaSuccess && tc_per_sm >= 1) {
+      p->fused_tc = 1;
+      p->fused_tc_grid = (p->sms / 4) * 4;  // row blocks are fixed per block: a multiple of 4
+    } else {
+      cudaGetLastError();
+    }
+  }
   return FFX_OK;
 }
 
@@ -497,7 +514,13 @@ int run_fused(ffx_plan_s* p, const int* axes, const float2* in, float2* out_c, f
       rec_flags = cudaEventRecordExternal;
     cudaEventRecordWithFlags((cudaEvent_t)p->trace[p->trace_i], stream, rec_flags);
   }
-  cudaError_t e = launch_fused(a, p->fused_grid, p->fused_smem_bytes, stream);
+  cudaError_t e;
+  if (p->fused_tc && !out_col && ((uintptr_t)in & 15) == 0) {
+    for (int k = 0; k < p->ndim; ++k) a.ts[k] = p->axis[axes[k]].ft_ts;
+    e = launch_fused_tc(a, p->fused_tc_grid, stream);
+  } else {
+    e = launch_fused(a, p->fused_grid, p->fused_smem_bytes, stream);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "fused launch");
   if (traced) {
     cudaEventRecordWithFlags((cudaEvent_t)p->trace[p->trace_i + 1], stream, rec_flags);
@@ -889,7 +912,7 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
     size_t tbytes = 256;
     for (int j = 0; j < ndim; ++j)
       if (dense_tc_supported(p->axis[j].N) && p->axis[j].T && (form == FFX_FORM_AUTO || form == FFX_FORM_TC))
-        tbytes += 2 * dense_tc_t_bytes(p->axis[j].N);
+        tbytes += 2 * dense_tc_t_bytes(p->axis[j].N) + (p->axis[j].N == 64 ? fused_tc_slice_bytes() : 0);
     e = cudaMalloc(&p->tc_mem, tbytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -908,6 +931,11 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
         }
         e = launch_tc_build_t(ax.T, ax.tc_t[0], ax.N, s);
         if (e == cudaSuccess) e = launch_tc_build_t(ax.TH, ax.tc_t[1], ax.N, s);
+        if (e == cudaSuccess && ax.N == 64) {
+          ax.ft_ts = tcur;
+          tcur += fused_tc_slice_bytes();
+          e = launch_fused_tc_slices(ax.T, ax.ft_ts, s);
+        }
         if (e == cudaSuccess)
           e = dense_tc_prepare();
         if (e != cudaSuccess) rc = cuda_fail(e, "tensor-core operands");
@@ -1087,7 +1115,7 @@ int64_t ffx_plan_fused(ffx_plan_t p) { return p ? p->fused : -1; }
 
 int ffx_plan_call_form(ffx_plan_t p, int axis, int64_t batch) {
   if (!p || p->many || axis < 0 || axis >= p->ndim || batch < 1) return -1;
-  if (batch <= p->fused) return FFX_FORM_DENSE;  // the fused kernel: FP32 dense
+  if (batch <= p->fused) return p->fused_tc ? FFX_FORM_TC : FFX_FORM_DENSE;  // the fused launch
   int64_t outer, inner;
   axis_outer_inner(p, axis, &outer, &inner);
   const int64_t lines = (p->acc && axis == p->order[p->ndim - 1] ? 1 : batch) * outer * inner;

@@ -24,6 +24,7 @@
 #include <cstring>
 
 #include "ffx_internal.h"
+#include "ffx_tcgen05.cuh"
 
 namespace ffx {
 
@@ -304,7 +305,278 @@ __global__ void __launch_bounds__(THREADS, 1) fused_small_kernel(const FusedArgs
 
 constexpr int kFusedThreads = 512;
 
+// ---------------------------------------------------------------------------
+// The same launch on the tensor cores, for lattices whose axes all have 64
+// points.  A pass is D[line][row] = sum_K X[line][K] T[row][K] over real
+// K = 128 (complex entries as 2 x 2 real blocks, rows and K interleaved as
+// (re, im)), with split-TF32 operands as in the per-axis tensor-core kernel:
+// head products in one TMEM accumulator, the cross terms in a second.  Work
+// item = 128 lines (MMA M) x 32 real rows (MMA N = 16 complex outputs); block
+// b owns row block b % 4 for the whole launch, so it keeps only that 32-row
+// slice of each T_j (32 KB per axis) in shared memory.  Per item: 256 threads
+// load the 128 lines from L2 (16-byte loads, coalesced along either memory
+// order), split them into the core-matrix layout (bank-conflict free), one
+// thread issues 16 K-steps x 3 tcgen05.mma and commits to an mbarrier, and
+// eight warps read the accumulators back (warp w: lane quarter w % 4, column
+// half w / 4) and store.  Summing |.|^2 over the batch stays in registers.
+// ---------------------------------------------------------------------------
+
+constexpr int FT_N = 64;                       // points per line, every axis
+constexpr int FT_K = 2 * FT_N;                 // real K
+constexpr int FT_LINES = 128;                  // lines per item = MMA M
+constexpr int FT_ROWS = 32;                    // real rows per item = MMA N
+constexpr int FT_RB = FT_K / FT_ROWS;          // row blocks
+constexpr int FT_THREADS = 256;
+constexpr int FT_SBO = (FT_K / 4) * 128;       // 4096: between 8-row groups
+constexpr int FT_X_PART = FT_LINES * FT_K * 4;  // 64 KB per split part
+constexpr int FT_TS_PART = FT_ROWS * FT_K * 4;  // 16 KB
+constexpr int FT_TS_BYTES = 2 * FT_TS_PART;     // one row block's slice, head and tail
+constexpr int FT_SMEM = 2 * FT_X_PART + 3 * FT_TS_BYTES;  // 224 KB
+constexpr int FT_COLS = 2 * FT_ROWS;            // head accumulator, cross-term accumulator
+constexpr uint32_t kIdescFT = tc::idesc_tf32(FT_LINES, FT_ROWS);
+
+__global__ void __launch_bounds__(FT_THREADS, 1) fused_tc_kernel(const FusedArgs a) {
+  using namespace tc;
+  extern __shared__ __align__(1024) unsigned char fts[];
+  unsigned char* xh = fts;
+  unsigned char* xl = fts + FT_X_PART;
+  unsigned char* tsl = fts + 2 * FT_X_PART;
+  __shared__ __align__(8) uint64_t tbar, mbar, dbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int s_abort;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rb = (int)(blockIdx.x % FT_RB);  // gridDim.x is a multiple of FT_RB
+  const int64_t cstep = gridDim.x / FT_RB, c0 = blockIdx.x / FT_RB;
+
+  if (warp == 0) tmem_alloc(&tmem_slot, FT_COLS);
+  if (tid == 0) {
+    s_abort = 0;
+    mbar_init(smem_u32(&tbar), 1);
+    mbar_init(smem_u32(&mbar), 1);
+    mbar_init(smem_u32(&dbar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(smem_u32(&tbar), (uint32_t)(a.npass * FT_TS_BYTES));
+    for (int p = 0; p < a.npass; ++p)
+      bulk_g2s(smem_u32(tsl + p * FT_TS_BYTES), a.ts[p] + (size_t)rb * FT_TS_BYTES, FT_TS_BYTES, smem_u32(&tbar));
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  uint32_t phase = 0;
+  bool slices = false;  // (thread 0) the T slices have landed
+  bool issued = false;
+  for (int p = 0; p < a.npass && !s_abort; ++p) {
+    const FusedPass& P = a.pass[p];
+    const int64_t inner = P.inner;
+    const bool contiguous = (inner == 1);
+    const int nb = P.acc ? (int)a.batch : 1;
+    const int64_t ctiles = (P.ncols + FT_LINES - 1) / FT_LINES;
+    const uint32_t th = smem_u32(tsl + p * FT_TS_BYTES), tl = th + FT_TS_PART;
+    for (int64_t ct = c0; ct < ctiles && !s_abort; ct += cstep) {
+      float racc[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) racc[m] = 0.f;
+      for (int b = 0; b < nb && !s_abort; ++b) {
+        // ---- 128 lines of the item into shared memory, split
+        if (contiguous) {
+          // 8 lines x 4 k-pairs per warp and step: 64 contiguous bytes per line
+          const int l0 = (lane & 7) + 8 * warp;
+          const long long b0 = fused_line(P, ct * FT_LINES + l0, b);
+          const long long b1 = fused_line(P, ct * FT_LINES + l0 + 64, b);
+          float4 v[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const long long base = (i & 1) ? b1 : b0;
+            const int kp = (lane >> 3) + 4 * (i >> 1);
+            v[i] = base >= 0 ? __ldcg(reinterpret_cast<const float4*>(P.in + base + 2 * kp))
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int line = l0 + 64 * (i & 1), kp = (lane >> 3) + 4 * (i >> 1);
+            const int off = (line >> 3) * FT_SBO + kp * 128 + (line & 7) * 16;
+            const float4 hi = make_float4(tf32_head(v[i].x), tf32_head(v[i].y), tf32_head(v[i].z), tf32_head(v[i].w));
+            *reinterpret_cast<float4*>(xh + off) = hi;
+            *reinterpret_cast<float4*>(xl + off) =
+                make_float4(v[i].x - hi.x, v[i].y - hi.y, v[i].z - hi.z, v[i].w - hi.w);
+          }
+        } else {
+          // 32 consecutive lines per warp and k-pair: coalesced along the lines
+          const int line = lane + 32 * (warp & 3);
+          const long long base = fused_line(P, ct * FT_LINES + line, b);
+          float4 v[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int kp = (warp >> 2) + 2 * i;
+            v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (base >= 0) {
+              const float2 p0 = __ldcg(P.in + base + (int64_t)(2 * kp) * inner);
+              const float2 p1 = __ldcg(P.in + base + (int64_t)(2 * kp + 1) * inner);
+              v[i] = make_float4(p0.x, p0.y, p1.x, p1.y);
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int kp = (warp >> 2) + 2 * i;
+            const int off = (line >> 3) * FT_SBO + kp * 128 + (line & 7) * 16;
+            const float4 hi = make_float4(tf32_head(v[i].x), tf32_head(v[i].y), tf32_head(v[i].z), tf32_head(v[i].w));
+            *reinterpret_cast<float4*>(xh + off) = hi;
+            *reinterpret_cast<float4*>(xl + off) =
+                make_float4(v[i].x - hi.x, v[i].y - hi.y, v[i].z - hi.z, v[i].w - hi.w);
+          }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        // ---- the product: 16 K-steps x 3 split products
+        if (tid == 0 && !slices) slices = mbar_wait(smem_u32(&tbar), 0u, &s_abort);  // under the first load
+        if (tid == 0 && slices) {
+          tc_fence_after();
+          const uint32_t ah = smem_u32(xh), al = smem_u32(xl);
+#pragma unroll 4
+          for (int ks = 0; ks < FT_K / 8; ++ks) {
+            const uint32_t o = (uint32_t)(ks * 256);
+            const uint64_t dxh = make_desc(ah + o, 128, FT_SBO), dxl = make_desc(al + o, 128, FT_SBO);
+            const uint64_t dth = make_desc(th + o, 128, FT_SBO), dtl = make_desc(tl + o, 128, FT_SBO);
+            const uint32_t more = ks > 0 ? 1u : 0u;
+            mma_tf32(tmem, dxh, dth, kIdescFT, more);
+            mma_tf32(tmem + FT_ROWS, dxh, dtl, kIdescFT, more);
+            mma_tf32(tmem + FT_ROWS, dxl, dth, kIdescFT, 1u);
+          }
+          mma_commit(smem_u32(&mbar));
+          issued = true;
+        }
+        // warp-uniform outcome: the tensor-memory loads below need whole warps
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&mbar), phase, &s_abort));
+        phase ^= 1u;
+        if (!ok) break;
+        tc_fence_after();
+        // ---- epilogue: lanes = lines, columns = real rows
+        const int q = warp & 3, h = warp >> 2;
+        const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * h);
+        float y[16];
+        {
+          uint32_t x1[16], x2[16];
+          tmem_ld16(taddr, x1);
+          tmem_ld16(taddr + FT_ROWS, x2);
+          tmem_wait_ld();
+#pragma unroll
+          for (int m = 0; m < 16; ++m) y[m] = __uint_as_float(x1[m]) + __uint_as_float(x2[m]);
+        }
+        const long long base = fused_line(P, ct * FT_LINES + 32 * q + lane, b);
+        const int n0 = rb * (FT_ROWS / 2) + 8 * h;  // complex outputs n0 .. n0 + 7
+        if (P.acc) {
+#pragma unroll
+          for (int m = 0; m < 8; ++m) racc[m] += y[2 * m] * y[2 * m] + y[2 * m + 1] * y[2 * m + 1];
+          if (b == nb - 1 && base >= 0) {
+            const int64_t o0 = base - (int64_t)b * a.M + (int64_t)n0 * inner;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) P.out_d[o0 + (int64_t)m * inner] += racc[m];
+          }
+        } else if (base >= 0) {
+          if (contiguous && P.out_c && ((uintptr_t)P.out_c & 15) == 0) {
+            float4* o = reinterpret_cast<float4*>(P.out_c + base + n0);  // base, n0 even: 16-byte aligned
+#pragma unroll
+            for (int m = 0; m < 4; ++m) o[m] = make_float4(y[4 * m], y[4 * m + 1], y[4 * m + 2], y[4 * m + 3]);
+          } else if (contiguous && P.out_d && ((uintptr_t)P.out_d & 15) == 0) {
+            float d[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) d[m] = y[2 * m] * y[2 * m] + y[2 * m + 1] * y[2 * m + 1];
+            float4* o = reinterpret_cast<float4*>(P.out_d + base + n0);  // base, n0 multiples of 8
+            o[0] = make_float4(d[0], d[1], d[2], d[3]);
+            o[1] = make_float4(d[4], d[5], d[6], d[7]);
+          } else {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+              const int64_t addr = base + (int64_t)(n0 + m) * inner;
+              if (P.out_c)
+                P.out_c[addr] = make_float2(y[2 * m], y[2 * m + 1]);
+              else
+                P.out_d[addr] = y[2 * m] * y[2 * m] + y[2 * m + 1] * y[2 * m + 1];
+            }
+          }
+        }
+        tc_fence_before();
+        __syncthreads();  // accumulators read and shared tiles free before the next item
+      }
+    }
+    if (p + 1 < a.npass && !grid_barrier(a.bar, (unsigned)(p + 1) * gridDim.x, &s_abort)) break;
+  }
+  // the tensor cores finish this block's work, and the slice copies have
+  // landed, before the block exits
+  if (tid == 0) {
+    if (issued) {
+      mma_commit(smem_u32(&dbar));
+      mbar_wait_own(smem_u32(&dbar), 0u, &s_abort);
+    }
+    mbar_wait_own(smem_u32(&tbar), 0u, &s_abort);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0) {
+    if (s_abort && a.err) atomicAdd(a.err, 1);
+    __threadfence();
+    if (atomicAdd(a.bar + 1, 1u) == gridDim.x - 1) {
+      atomicExch(a.bar, 0u);
+      atomicExch(a.bar + 1, 0u);
+    }
+  }
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_free(tmem, FT_COLS);
+  }
+}
+
+// Row-block slices of T (complex [64][64]) for the kernel above: block rb,
+// [head | tail], real (r, k') with r = 32 rb + r_local, k' < 128 in the
+// core-matrix order of a 32-row K-major operand.
+__global__ void fused_tc_slices_kernel(const float2* __restrict__ T, unsigned char* __restrict__ out) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < FT_K * FT_K; idx += gridDim.x * blockDim.x) {
+    const int r = idx / FT_K, kp = idx % FT_K;
+    const float2 t = T[(r >> 1) * FT_N + (kp >> 1)];
+    const int po = r & 1, pi = kp & 1;
+    const float v = po == 0 ? (pi == 0 ? t.x : -t.y) : (pi == 0 ? t.y : t.x);
+    const float hi = tc::tf32_round(v);
+    const int blk = r / FT_ROWS, rl = r % FT_ROWS;
+    unsigned char* base = out + (size_t)blk * FT_TS_BYTES;
+    const int off = (rl >> 3) * FT_SBO + (kp >> 2) * 128 + (rl & 7) * 16 + (kp & 3) * 4;
+    *reinterpret_cast<float*>(base + off) = hi;
+    *reinterpret_cast<float*>(base + FT_TS_PART + off) = tc::tf32_round(v - hi);
+  }
+}
+
 }  // namespace
+
+size_t fused_tc_slice_bytes() { return (size_t)FT_RB * FT_TS_BYTES; }
+
+cudaError_t launch_fused_tc_slices(const float2* T, unsigned char* out, cudaStream_t s) {
+  fused_tc_slices_kernel<<<64, 256, 0, s>>>(T, out);
+  return cudaGetLastError();
+}
+
+cudaError_t fused_tc_prepare(int* per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(fused_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, FT_SMEM);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, fused_tc_kernel, FT_THREADS, FT_SMEM);
+  return e;
+}
+
+cudaError_t launch_fused_tc(const FusedArgs& a, int grid, cudaStream_t stream) {
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)FT_THREADS);
+  cfg.dynamicSmemBytes = FT_SMEM;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fused_tc_kernel, a);
+}
 
 size_t fused_smem(const int* N, int npass) {
   size_t img = 0;

@@ -136,8 +136,16 @@ struct FusedArgs {
   int64_t img_floats2;  // sum of the images (Bs follows them in shared memory)
   unsigned* bar;        // [2]: grid-barrier arrivals, blocks done (the last block resets both)
   int* err;
+  const unsigned char* ts[3];  // tensor-core variant: per pass, T_j's split 32-row slices
 };
 size_t fused_smem(const int* N, int npass);
+// Tensor-core variant for lattices whose axes all have 64 points: 4 row
+// blocks of 32 real rows; each block's T slice is head and tail of 32 rows x
+// 128 K in core-matrix order (fused_tc_slice_bytes per axis, all 4 blocks).
+size_t fused_tc_slice_bytes();
+cudaError_t launch_fused_tc_slices(const float2* T, unsigned char* out, cudaStream_t s);
+cudaError_t fused_tc_prepare(int* per_sm);
+cudaError_t launch_fused_tc(const FusedArgs& a, int grid, cudaStream_t stream);
 int fused_img_stride();
 const void* fused_func();
 int fused_threads();

@@ -47,6 +47,7 @@
 #include <cstring>
 
 #include "ffx_internal.h"
+#include "ffx_tcgen05.cuh"
 
 namespace ffx {
 
@@ -88,87 +89,11 @@ static_assert(TcLayout<false>::SMEM + EXTRA_SMEM <= 227 * 1024 && TcLayout<true>
 constexpr int NTHREADS = NPROD + 32 + NEPI;  // 416
 constexpr int MMA_WARP = NPROD / 32;         // warp 8; warps 9-12 are the epilogue
 constexpr int ACC_COLS = 4 * ROWS;           // two buffers x (head product, cross terms): all 512
-constexpr long long kSpinLimit = 1ll << 22;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// K-major, no swizzle: start >> 4 | LBO >> 4 << 16 | SBO >> 4 << 32 | version 1 << 46
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
-}
+using namespace tc;
 
 // kind::tf32, D = F32, A = B = TF32, both K-major, N = ROWS, M = LINES
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(ROWS >> 3) << 17) |
-                            ((uint32_t)(LINES >> 4) << 24);
-
-__device__ __forceinline__ float tf32_round(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-__device__ __forceinline__ bool mbar_test(uint32_t mbar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(done)
-      : "r"(mbar), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-
-// Bounded wait for the phase of the given parity; gives up (false) when the
-// block aborts or the poll budget runs out (then it sets the abort flag).
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int* abort_flag) {
-  for (long long i = 0; i < kSpinLimit; ++i) {
-    if (mbar_test(mbar, parity)) return true;
-    if (*abort_flag) return false;
-  }
-  *abort_flag = 1;
-  return false;
-}
-
-// Bounded wait that ignores the abort flag: for work this thread started
-// itself (a bulk copy, tensor-core operations), which must end before exit.
-__device__ __forceinline__ bool mbar_wait_own(uint32_t mbar, uint32_t parity, volatile int* abort_flag) {
-  for (long long i = 0; i < kSpinLimit; ++i)
-    if (mbar_test(mbar, parity)) return true;
-  *abort_flag = 1;
-  return false;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-               : "memory");
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc)
-      : "memory");
-}
-
-// 32 lanes x 16 consecutive 32-bit columns of tensor memory (this warp's lane quarter)
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* x) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]), "=r"(x[4]), "=r"(x[5]), "=r"(x[6]), "=r"(x[7]), "=r"(x[8]),
-        "=r"(x[9]), "=r"(x[10]), "=r"(x[11]), "=r"(x[12]), "=r"(x[13]), "=r"(x[14]), "=r"(x[15])
-      : "r"(taddr));
-}
+constexpr uint32_t kIdesc = idesc_tf32(LINES, ROWS);
 
 // Line c of the pass (realization b of the batch when accumulating): offset
 // of its first point, or -1 past the end; br = its realization.
@@ -198,11 +123,6 @@ __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, int byt
 __device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, int bytes) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
 }
-
-// Input split: the head keeps the TF32 bits of x (the 13 low mantissa bits
-// cleared), the tail x - head is exact in FP32 and carries <= 13 significant
-// bits, of which the TF32 operand keeps 11: |error| <= 2^-22 |x|.
-__device__ __forceinline__ float tf32_head(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
 
 __device__ __forceinline__ void split_store(unsigned char* xh, unsigned char* xl, int off, float4 v) {
   const float4 hi = make_float4(tf32_head(v.x), tf32_head(v.y), tf32_head(v.z), tf32_head(v.w));
@@ -447,9 +367,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               const uint64_t dth = make_desc(th + o, CORE_LBO, CHUNK_SBO);
               const uint64_t dtl = make_desc(tl + o, CORE_LBO, CHUNK_SBO);
               const uint32_t more = (kc == 0 && ks == 0) ? 0u : 1u;
-              mma_tf32(d1, dxh, dth, more);
-              mma_tf32(d2, dxh, dtl, more);
-              mma_tf32(d2, dxl, dth, 1u);
+              mma_tf32(d1, dxh, dth, kIdesc, more);
+              mma_tf32(d2, dxh, dtl, kIdesc, more);
+              mma_tf32(d2, dxl, dth, kIdesc, 1u);
             }
             mma_commit(smem_u32(&empty_bar[s]));
           }

@@ -81,3 +81,31 @@ def test_fusion_applies_only_to_short_dense_axes(ffx):
         assert not p3.fused
     with ffx.Plan((64, 64), (0.25, 0.25), 5.0, (9, 3), form="dense", fused=False) as p4:
         assert not p4.fused
+
+
+@pytest.mark.parametrize("dims,lam,batch", [((64, 64, 64), (30, 30, 3), 1), ((64, 64, 64), (30, 30, 3), 2),
+                                            ((64, 64), (7, 5), 3)])
+def test_fused_tensor_core_launch(ffx, dims, lam, batch):
+    """Axes of 64 points under the automatic form: the fused launch on the
+    tensor cores (split TF32), against the oracle; fields, densities, the
+    ensemble sum and an in-place field."""
+    rng = np.random.default_rng(sum(dims) + 3 * batch)
+    dx, t = (0.25,) * len(dims), 9.0
+    psi = random_field(rng, (batch,) + dims)
+    ref = O.expand_field(psi, dx, t, lam)
+    with ffx.Plan(dims, dx, t, lam) as plan:
+        assert plan.fused and batch <= plan.fused_max_batch
+        assert plan.call_forms(batch) == ("tc",) * len(dims)
+        x = to_dev(psi)
+        rho = ffx.ffx_expand(plan, x).cpu().numpy()
+        fld = ffx.ffx_expand_field(plan, x).cpu().numpy()
+        y = x.clone()
+        ffx.ffx_expand_field(plan, y, y)
+        inplace = y.cpu().numpy()
+        assert plan.device_errors() == 0
+    with ffx.Plan(dims, dx, t, lam, accumulate=True) as plan:
+        acc = ffx.ffx_expand(plan, to_dev(psi)).cpu().numpy()
+    ef, ed = rel_l2(fld, ref), rel_l2(rho, np.abs(ref) ** 2)
+    ea, ei = rel_l2(acc, (np.abs(ref) ** 2).sum(0)), rel_l2(inplace, ref)
+    print(f"fused tc {dims} x{batch}: field {ef:.2e} density {ed:.2e} ensemble {ea:.2e} in place {ei:.2e}")
+    assert max(ef, ei) < FIELD_TOL and max(ed, ea) < DENSITY_TOL

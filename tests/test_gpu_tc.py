@@ -128,7 +128,7 @@ def test_auto_moves_large_dense_passes_to_tensor_cores(ffx):
     ref = np.abs(O.expand_field(psi, w.dx, w.t, w.lam)) ** 2
     with ffx.Plan(w.dims, w.dx, w.t, w.lam) as plan:
         assert plan.axis_forms == ("dense",) * 3
-        assert plan.call_forms(1) == ("dense",) * 3  # small calls: FP32 kernels (fused)
+        assert plan.call_forms(1) == ("tc",) * 3     # small calls: the fused launch, on the tensor cores
         assert plan.call_forms(6) == ("tc",) * 3     # 6 x 4096 lines per pass: tensor cores
         rho = ffx.ffx_expand(plan, to_dev(psi)).cpu().numpy()
         one = ffx.ffx_expand(plan, to_dev(psi[:1])).cpu().numpy()
@@ -136,5 +136,5 @@ def test_auto_moves_large_dense_passes_to_tensor_cores(ffx):
     with ffx.Plan(w.dims, w.dx, w.t, w.lam, form="dense") as plan:
         assert plan.call_forms(6) == ("dense",) * 3  # explicit forms never switch
     e6, e1 = rel_l2(rho, ref), rel_l2(one, ref[:1])
-    print(f"auto {w.name}: batch 6 on tensor cores {e6:.2e}, batch 1 fused FP32 {e1:.2e}")
+    print(f"auto {w.name}: batch 6 on tensor cores {e6:.2e}, batch 1 fused on tensor cores {e1:.2e}")
     assert e6 < DENSITY_TOL and e1 < DENSITY_TOL
