@@ -305,7 +305,7 @@ int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* 
     d.Aimg = adjoint ? ax.img[1] : ax.img[0];
     d.err = p->dev_err;
     if (ax.N <= kDenseInPlaceMaxN) {
-      int64_t grid = dense_small_tiles(d.ncols);
+      int64_t grid = dense_small_tiles(ax.N, d.ncols);
       if (grid > ax.grid_dense_small) grid = ax.grid_dense_small;
       if (grid < 1) grid = 1;
       e = launch_dense_small(d, (int)grid, stream);
@@ -535,15 +535,24 @@ int run_fused(ffx_plan_s* p, const int* axes, const float2* in, float2* out_c, f
 
 // Relative cost per point of one axis pass (FP32 flops over the fraction of
 // the FP32 peak each form was measured to reach on GB300).
-double model_cost(const Axis& ax, int form) {
+// `lines` = lines of one realization along the axis: the dense and
+// tensor-core kernels tile lines by 32 and 128, so a handful of lines (a 1-D
+// field) leaves them latency-bound and the FFT forms take it.
+double model_cost(const Axis& ax, int form, int64_t lines) {
   const double N = ax.N, lg = std::log2(N), lam = ax.lam;
   switch (form) {
     case FFX_FORM_PAPER: return lam * (10 * lg + 20) / 0.18;
-    case FFX_FORM_FOLD: return (lam * (5 * lg + 14) + 5 * lg) / 0.11;
-    // the tensor-core form runs 3x the real flops at ~8x the rate; its 128-line
-    // tiles leave 64-point axes of small batches latency-bound
-    case FFX_FORM_TC: return N < 128 ? 8 * N / 0.40 : 8 * N / 1.2;
-    default: return 8 * N / 0.45;
+    case FFX_FORM_FOLD: return (lam * (5 * lg + 14) + 5 * lg) / (N >= 256 ? 0.16 : 0.11);
+    // the tensor-core form runs 3x the real flops at ~6x the FP32 rate
+    // (measured 1.9-2.3 in these units for N = 64 .. 1024 on full passes);
+    // 64-point axes stay dense at plan time and move to the tensor cores per
+    // call when the call is large (see dense_kernel_for)
+    case FFX_FORM_TC:
+      if (lines < 128) return 1e30;
+      return N < 128 ? 8 * N / 0.40 : 8 * N / 2.0;
+    default:
+      if (lines < 32) return 1e30;
+      return 8 * N / 0.45;
   }
 }
 
@@ -849,13 +858,13 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
     ax.grid_fold = grid_for(ax.foldk.func, ax.foldk.threads, ax.foldk.smem, p->sms);
     ax.grid_adj = grid_for(ax.adj.func, ax.adj.threads, ax.adj.smem, p->sms);
     ax.grid_dense = grid_for(dense_kernel_func(), 256, 0, p->sms);
-    e = cudaFuncSetAttribute(dense_small_func(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)dense_small_smem());
+    e = cudaFuncSetAttribute(dense_small_func(N), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)dense_small_smem(N));
     if (e != cudaSuccess) {
       rc = cuda_fail(e, "cudaFuncSetAttribute");
       break;
     }
-    ax.grid_dense_small = grid_for(dense_small_func(), 128, dense_small_smem(), p->sms);
+    ax.grid_dense_small = grid_for(dense_small_func(N), 128, dense_small_smem(N), p->sms);
   }
   if (rc == FFX_OK) {
     e = cudaStreamSynchronize(s);
@@ -989,7 +998,7 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
         for (int c = FFX_FORM_FOLD; c <= FFX_FORM_TC; ++c) {
           if (c == FFX_FORM_DENSE && !ax.T) continue;
           if (c == FFX_FORM_TC && !tc_capable(ax)) continue;
-          if (model_cost(ax, c) < model_cost(ax, f)) f = c;
+          if (model_cost(ax, c, outer * inner) < model_cost(ax, f, outer * inner)) f = c;
         }
       }
       ax.form = f;

@@ -180,19 +180,23 @@ __global__ void __launch_bounds__(256) dense_pass_kernel(const DenseArgs a) {
 }
 
 // Lines of at most 64 points: T stays in shared memory for the whole launch,
-// a 64 x 32 output tile takes all of K at once, each of 128 threads owns a
-// 4 x 4 block (rows ty + 16 i, columns tx + 8 j), and the next tile's input is
-// loaded into registers while the current one is multiplied.  Items are
-// (column tile, realization) pairs; with ensemble summing a block takes every
-// realization of its column tile in order.
-constexpr int SBN = 32, STX = 8, STY = 16, STM = 4, STN = 4, SNMAX = 64;
-constexpr int SLOADS = SNMAX * SBN / 128;  // input elements each thread loads per tile
+// an NM x BN output tile (rows x lines) takes all of K at once, each of 128
+// threads owns an (NM/16) x (BN/8) block (rows ty + 16 i, columns tx + 8 j),
+// and the next tile's input is loaded into registers while the current one is
+// multiplied.  Two shapes: 64 x 32 for lines of 33..64 points, 32 x 64 for
+// lines of at most 32 (no rows wasted past N).  Items are (column tile,
+// realization) pairs; with ensemble summing a block takes every realization of
+// its column tile in order.  Every output is the same FMA sequence (k
+// ascending) in either shape.
+constexpr int STX = 8, STY = 16, SNMAX = 64;
+constexpr int SIMG = SNMAX + 1;  // image row stride (img[k][m] = T[m][k])
 
 struct SmallItem {
   int64_t cbk;
   int b;
 };
 
+template <int SBN>
 __device__ __forceinline__ void small_bases(const DenseArgs& a, int64_t cbk, int b, long long* cbase,
                                             int* cbr, int t) {
   // column t of column tile cbk, realization b (b only used when summing the ensemble)
@@ -217,11 +221,13 @@ __device__ __forceinline__ void small_bases(const DenseArgs& a, int64_t cbk, int
 
 __device__ __forceinline__ uint32_t dsm_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+template <int NM, int SBN>
 __global__ void __launch_bounds__(128) dense_small_kernel(const DenseArgs a) {
+  constexpr int STM = NM / STY, STN = SBN / STX;
   extern __shared__ __align__(16) unsigned char dsm[];
-  float2* As = reinterpret_cast<float2*>(dsm);     // [SNMAX][SNMAX + 1], As[k][m] = A[m][k]
-  float2* Bs = As + SNMAX * (SNMAX + 1);           // [2][SNMAX][SBN + 1]
-  constexpr int BSTRIDE = SNMAX * (SBN + 1);
+  float2* As = reinterpret_cast<float2*>(dsm);     // [NM][SIMG], As[k][m] = A[m][k]
+  float2* Bs = As + NM * SIMG;                     // [2][NM][SBN + 1]
+  constexpr int BSTRIDE = NM * (SBN + 1);
   __shared__ long long cbase[2][SBN];
   __shared__ int cbr[2][SBN];
   __shared__ __align__(8) uint64_t abar;
@@ -240,7 +246,7 @@ __global__ void __launch_bounds__(128) dense_small_kernel(const DenseArgs a) {
   if (n_items == 0) return;
 
   // T, stored in global memory as the image of As, arrives in one bulk (TMA) copy
-  const uint32_t abytes = (uint32_t)(N * (SNMAX + 1) * sizeof(float2));
+  const uint32_t abytes = (uint32_t)(N * SIMG * sizeof(float2));
   if (tid == 0) {
     s_abort = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(dsm_u32(&abar)) : "memory");
@@ -264,11 +270,11 @@ __global__ void __launch_bounds__(128) dense_small_kernel(const DenseArgs a) {
   // (with the ensemble-gradient factor the values go through registers)
   auto issue_item = [&](int buf) {
     float2* dst = Bs + buf * BSTRIDE;
-    for (int idx = tid; idx < SNMAX * SBN; idx += 128) {
+    for (int idx = tid; idx < NM * SBN; idx += 128) {
       int k, cc;
       if (contiguous) {
-        cc = idx / SNMAX;
-        k = idx - cc * SNMAX;
+        cc = idx / NM;
+        k = idx - cc * NM;
       } else {
         k = idx / SBN;
         cc = idx - k * SBN;
@@ -297,7 +303,7 @@ __global__ void __launch_bounds__(128) dense_small_kernel(const DenseArgs a) {
 
   if (tid < SBN) {
     const SmallItem i0 = item_at(0);
-    small_bases(a, i0.cbk, i0.b, cbase[0], cbr[0], tid);
+    small_bases<SBN>(a, i0.cbk, i0.b, cbase[0], cbr[0], tid);
   }
   __syncthreads();
   issue_item(0);
@@ -331,7 +337,7 @@ __global__ void __launch_bounds__(128) dense_small_kernel(const DenseArgs a) {
     if (more) {
       if (tid < SBN) {
         const SmallItem nx = item_at(it + 1);
-        small_bases(a, nx.cbk, nx.b, cbase[buf ^ 1], cbr[buf ^ 1], tid);
+        small_bases<SBN>(a, nx.cbk, nx.b, cbase[buf ^ 1], cbr[buf ^ 1], tid);
       }
       __syncthreads();
       issue_item(buf ^ 1);  // in flight during this item's product
@@ -351,7 +357,7 @@ __global__ void __launch_bounds__(128) dense_small_kernel(const DenseArgs a) {
     for (int k = 0; k < N; ++k) {
       float2 av[STM], bv[STN];
 #pragma unroll
-      for (int i = 0; i < STM; ++i) av[i] = As[k * (SNMAX + 1) + ty + STY * i];
+      for (int i = 0; i < STM; ++i) av[i] = As[k * SIMG + ty + STY * i];
 #pragma unroll
       for (int j = 0; j < STN; ++j) bv[j] = B[k * (SBN + 1) + tx + STX * j];
 #pragma unroll
@@ -414,28 +420,39 @@ __global__ void __launch_bounds__(128) dense_small_kernel(const DenseArgs a) {
 
 // T's image for the kernel above: img[k][m] = T[m][k], rows of SNMAX + 1.
 __global__ void dense_small_image_kernel(const float2* __restrict__ T, float2* __restrict__ img, int N) {
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N * (SNMAX + 1); idx += gridDim.x * blockDim.x) {
-    const int k = idx / (SNMAX + 1), m = idx - k * (SNMAX + 1);
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N * SIMG; idx += gridDim.x * blockDim.x) {
+    const int k = idx / SIMG, m = idx - k * SIMG;
     img[idx] = (m < N) ? T[m * N + k] : make_float2(0.f, 0.f);
   }
 }
 
 }  // namespace
 
-const void* dense_small_func() { return (const void*)dense_small_kernel; }
-size_t dense_small_smem() { return sizeof(float2) * (SNMAX * (SNMAX + 1) + 2 * SNMAX * (SBN + 1)); }
-size_t dense_small_image_floats2(int N) { return (size_t)N * (SNMAX + 1); }
+// lines of at most 32 points take the 32 x 64 tile, longer ones 64 x 32
+const void* dense_small_func(int N) {
+  return N <= 32 ? (const void*)dense_small_kernel<32, 64> : (const void*)dense_small_kernel<64, 32>;
+}
+size_t dense_small_smem(int N) {
+  return N <= 32 ? sizeof(float2) * (32 * SIMG + 2 * 32 * 65) : sizeof(float2) * (64 * SIMG + 2 * 64 * 33);
+}
+size_t dense_small_image_floats2(int N) { return (size_t)N * SIMG; }
 cudaError_t launch_dense_small_image(const float2* T, float2* img, int N, cudaStream_t s) {
   dense_small_image_kernel<<<16, 256, 0, s>>>(T, img, N);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dense_small(const DenseArgs& a, int grid, cudaStream_t stream) {
-  dense_small_kernel<<<grid, 128, dense_small_smem(), stream>>>(a);
+  if (a.N <= 32)
+    dense_small_kernel<32, 64><<<grid, 128, dense_small_smem(a.N), stream>>>(a);
+  else
+    dense_small_kernel<64, 32><<<grid, 128, dense_small_smem(a.N), stream>>>(a);
   return cudaGetLastError();
 }
 
-int64_t dense_small_tiles(int64_t ncols) { return (ncols + SBN - 1) / SBN; }
+int64_t dense_small_tiles(int N, int64_t ncols) {
+  const int bn = N <= 32 ? 64 : 32;
+  return (ncols + bn - 1) / bn;
+}
 
 const void* dense_kernel_func() { return (const void*)dense_pass_kernel; }
 

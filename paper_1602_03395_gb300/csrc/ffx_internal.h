@@ -99,10 +99,10 @@ cudaError_t launch_dense(const DenseArgs& a, int grid, cudaStream_t stream);
 int64_t dense_tiles(int N, int64_t ncols);
 constexpr int kDenseInPlaceMaxN = 64;
 // lines of at most 64 points: a kernel with T resident in shared memory
-const void* dense_small_func();
-size_t dense_small_smem();
+const void* dense_small_func(int N);
+size_t dense_small_smem(int N);
 cudaError_t launch_dense_small(const DenseArgs& a, int grid, cudaStream_t stream);
-int64_t dense_small_tiles(int64_t ncols);
+int64_t dense_small_tiles(int N, int64_t ncols);
 size_t dense_small_image_floats2(int N);
 cudaError_t launch_dense_small_image(const float2* T, float2* img, int N, cudaStream_t s);
 constexpr int kDenseMaxN = 1024;
