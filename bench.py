@@ -402,7 +402,7 @@ def run_mixed(args, torch, dist, world, rank, dev):
             "clocks": clocks,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved / alu_peak, "traffic": None,
-                         "kernel": "many_kernel (all phases of one call)",
+                         "kernel": ("many_dense_kernel" if plan.form == "dense" else "many_kernel") + " (all phases of one call)",
                          "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({pk_src})"},
             "roofline_hbm": {"bound": "hbm", "achieved": byts / (ms / args.steps * 1e-3) / 1e9,
                              "peak": hbm_peak, "unit": "GB/s",

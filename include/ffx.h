@@ -159,8 +159,18 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
  *                      the defaults of ffx_plan).  Line lengths must be one of
  *                      16, 32, 48, 64, 96, 128, 192, 256 (FFX_EUNSUPPORTED
  *                      otherwise).
- *  flags               FFX_FORM_*; FFX_ACCUMULATE is rejected (instances on
+ *  flags               FFX_FORM_PAPER, FFX_FORM_FOLD, FFX_FORM_DENSE or
+ *                      FFX_FORM_AUTO (dense when the dense per-axis map costs
+ *                      less than the fold form on every instance axis, else
+ *                      fold); FFX_ACCUMULATE is rejected (instances on
  *                      different lattices have no common density grid).
+ *
+ * The dense form builds T_j and T_j^H of every distinct axis geometry at plan
+ * creation (the fold pass on the unit vectors) and runs each phase as one
+ * persistent kernel over 64 x 32 tiles of all instances; it adds a second
+ * packed workspace.  Its passes are not in place for lines over 64 points, so
+ * an in-place ffx_expand_field with a 1-D instance longer than 64 points
+ * returns FFX_EUNSUPPORTED.
  *
  * Data are packed: instance i occupies points [off_i, off_i + M_i) of the
  * input, of the density or field output, and of the gradient buffers, with

@@ -19,164 +19,17 @@
 // |.|^2 summed over the batch (the tile then loops over b, deterministic).
 #include <cstring>
 
+#include "ffx_dense_tile.cuh"
 #include "ffx_internal.h"
 
 namespace ffx {
 
 namespace {
 
-constexpr int DBM = 64, DBN = 32, DBK = 16, DTX = 16, DTY = 16, DTM = 4, DTN = 2;
-
-__device__ __forceinline__ void dcfma(float2& acc, float2 a, float2 b) {
-  acc.x = fmaf(a.x, b.x, acc.x);
-  acc.x = fmaf(-a.y, b.y, acc.x);
-  acc.y = fmaf(a.x, b.y, acc.y);
-  acc.y = fmaf(a.y, b.x, acc.y);
-}
-
 __global__ void __launch_bounds__(256) dense_pass_kernel(const DenseArgs a) {
-  __shared__ float2 As[DBK][DBM + 1];
-  __shared__ float2 Bs[DBK][DBN + 1];
-  __shared__ long long cbase[DBN];
-  __shared__ int cb[DBN];
-
-  const int N = a.N;
-  const int tx = threadIdx.x % DTX, ty = threadIdx.x / DTX;
-  const int64_t inner = a.inner;
-  const bool contiguous = (inner == 1);
-  const int64_t ncols = a.ncols;
-  const int row_blocks = (N + DBM - 1) / DBM;
-  const int64_t col_blocks = (ncols + DBN - 1) / DBN;
-  const int64_t ntiles = (int64_t)row_blocks * col_blocks;
-  const int nb_loop = a.acc ? (int)a.batch : 1;
-  const int64_t per_real = a.outer * inner;
-
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int rb = (int)(tile % row_blocks);
-    const int64_t cbk = tile / row_blocks;
-    const int m0 = rb * DBM;
-    const int64_t c0 = cbk * DBN;
-    float racc[DTM][DTN];
-#pragma unroll
-    for (int i = 0; i < DTM; ++i)
-#pragma unroll
-      for (int j = 0; j < DTN; ++j) racc[i][j] = 0.f;
-
-    for (int bl = 0; bl < nb_loop; ++bl) {
-      __syncthreads();
-      if (threadIdx.x < DBN) {
-        const int64_t c = c0 + threadIdx.x;
-        long long base = -1;
-        int b = 0;
-        if (c < ncols) {
-          int64_t bo = c / inner;
-          const int64_t i = c - bo * inner;
-          if (a.acc) {
-            b = bl;
-            bo += (int64_t)bl * a.outer;
-          } else {
-            b = (int)(c / per_real);
-          }
-          base = bo * (int64_t)N * inner + i;
-        }
-        cbase[threadIdx.x] = base;
-        cb[threadIdx.x] = b;
-      }
-      float2 acc[DTM][DTN];
-#pragma unroll
-      for (int i = 0; i < DTM; ++i)
-#pragma unroll
-        for (int j = 0; j < DTN; ++j) acc[i][j] = make_float2(0.f, 0.f);
-
-      for (int k0 = 0; k0 < N; k0 += DBK) {
-        __syncthreads();  // previous chunk consumed; cbase visible
-        // A chunk: As[kk][mm] = T[m0 + mm][k0 + kk]
-        for (int idx = threadIdx.x; idx < DBK * DBM; idx += 256) {
-          const int mm = idx / DBK, kk = idx - mm * DBK;
-          const int m = m0 + mm, k = k0 + kk;
-          As[kk][mm] = (m < N && k < N) ? __ldg(a.A + (size_t)m * N + k) : make_float2(0.f, 0.f);
-        }
-        // B chunk: Bs[kk][cc] = in[col c0 + cc][row k0 + kk]
-        for (int idx = threadIdx.x; idx < DBK * DBN; idx += 256) {
-          int kk, cc;
-          if (contiguous) {
-            cc = idx / DBK;
-            kk = idx - cc * DBK;
-          } else {
-            kk = idx / DBN;
-            cc = idx - kk * DBN;
-          }
-          const int k = k0 + kk;
-          const long long base = cbase[cc];
-          float2 v = make_float2(0.f, 0.f);
-          if (base >= 0 && k < N) {
-            const int64_t addr = base + (int64_t)k * inner;
-            v = a.in[addr];  // plain load: passes may run in place
-            if (a.grad) {
-              const int64_t gaddr = a.grad_shared ? addr - (int64_t)cb[cc] * a.M : addr;
-              const float gr = 2.f * __ldg(a.grad + gaddr);
-              v.x *= gr;
-              v.y *= gr;
-            }
-          }
-          Bs[kk][cc] = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < DBK; ++kk) {
-          float2 av[DTM], bv[DTN];
-#pragma unroll
-          for (int i = 0; i < DTM; ++i) av[i] = As[kk][ty + DTY * i];
-#pragma unroll
-          for (int j = 0; j < DTN; ++j) bv[j] = Bs[kk][tx + DTX * j];
-#pragma unroll
-          for (int i = 0; i < DTM; ++i)
-#pragma unroll
-            for (int j = 0; j < DTN; ++j) dcfma(acc[i][j], av[i], bv[j]);
-        }
-      }
-      // epilogue for this realization
-      __syncthreads();  // all reads of this realization's inputs are done (in-place passes)
-      if (a.acc) {
-#pragma unroll
-        for (int i = 0; i < DTM; ++i)
-#pragma unroll
-          for (int j = 0; j < DTN; ++j) racc[i][j] += acc[i][j].x * acc[i][j].x + acc[i][j].y * acc[i][j].y;
-      } else {
-#pragma unroll
-        for (int i = 0; i < DTM; ++i) {
-          const int m = m0 + ty + DTY * i;
-          if (m >= N) continue;
-#pragma unroll
-          for (int j = 0; j < DTN; ++j) {
-            const int cc = tx + DTX * j;
-            const long long base = cbase[cc];
-            if (base < 0) continue;
-            const int64_t addr = base + (int64_t)m * inner;
-            if (a.out_c)
-              a.out_c[addr] = acc[i][j];
-            else
-              a.out_d[addr] = acc[i][j].x * acc[i][j].x + acc[i][j].y * acc[i][j].y;
-          }
-        }
-      }
-    }
-    if (a.acc) {
-#pragma unroll
-      for (int i = 0; i < DTM; ++i) {
-        const int m = m0 + ty + DTY * i;
-        if (m >= N) continue;
-#pragma unroll
-        for (int j = 0; j < DTN; ++j) {
-          const int cc = tx + DTX * j;
-          const long long base = cbase[cc];
-          if (base < 0) continue;
-          const int64_t addr = base - (int64_t)(nb_loop - 1) * a.M + (int64_t)m * inner;
-          a.out_d[addr] += racc[i][j];
-        }
-      }
-    }
-  }
+  __shared__ DenseTileSmem sm;
+  const int64_t ntiles = dense_tile_count(a.N, a.ncols);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) dense_tile(a, tile, sm);
 }
 
 // Lines of at most 64 points: T stays in shared memory for the whole launch,
@@ -461,9 +314,7 @@ cudaError_t launch_dense(const DenseArgs& a, int grid, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
-int64_t dense_tiles(int N, int64_t ncols) {
-  return (int64_t)((N + DBM - 1) / DBM) * ((ncols + DBN - 1) / DBN);
-}
+int64_t dense_tiles(int N, int64_t ncols) { return dense_tile_count(N, ncols); }
 
 }  // namespace ffx
 

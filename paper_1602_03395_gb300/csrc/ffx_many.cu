@@ -11,6 +11,13 @@
 // is one CUDA graph, built once per plan and mode and replayed on the caller's
 // stream.  Buffers are packed: instance i occupies points [off_i, off_i + M_i)
 // of the input, the workspace and the output.
+//
+// Dense mode (FFX_FORM_DENSE, or the automatic form when the dense per-axis
+// maps cost less than the fold form for every instance axis): the plan builds
+// T and T^H of every distinct (N, lam, dx, t, a, abar) once, with the fold
+// pass on the unit vectors, and each phase is one persistent kernel over
+// (instance, 64 x 32 tiles) items of the dense product.  Those passes are not
+// in place for N > 64, so pass k of an instance writes workspace k % 2.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -19,6 +26,7 @@
 #include <vector>
 
 #include "../../include/ffx.h"
+#include "ffx_dense_tile.cuh"
 #include "ffx_internal.h"
 #include "ffx_pass.cuh"
 #include "ffx_plans.h"
@@ -27,7 +35,8 @@ namespace ffx {
 
 // Pointers of one call; pass arguments hold byte offsets into these.
 enum ManyBase : int { BASE_NONE = -1, BASE_PSI0 = 0, BASE_WS = 1, BASE_OUTC = 2, BASE_OUTD = 3,
-                      BASE_GRAD = 4, NBASE = 5 };
+                      BASE_GRAD = 4, BASE_WS2 = 5, NBASE = 6 };
+constexpr int KIND_DENSE = 100;  // a dense phase (forward or adjoint: the item's matrix decides)
 struct ManyCall {
   const void* base[NBASE];
 };
@@ -74,6 +83,28 @@ constexpr size_t many_smem_bytes() {
   m = std::max(m, PassSmem<Plan192, kGroups192>::bytes);
   m = std::max(m, PassSmem<Plan256, kGroups256>::bytes);
   return m;
+}
+
+// Dense phases: persistent blocks take (instance, tile range) items.
+__global__ void __launch_bounds__(256) many_dense_kernel(const DenseArgs* __restrict__ args,
+                                                         const ManyItem* __restrict__ items, int n_items,
+                                                         int* counter, const ManyCall call) {
+  __shared__ DenseTileSmem sm;
+  __shared__ int s_item;
+  for (;;) {
+    __syncthreads();  // everyone has read s_item (and is done with the last tile)
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= n_items) break;
+    const ManyItem w = items[it];
+    DenseArgs a = args[w.arg];
+    a.in = (const float2*)rebase(call, w.in_base, a.in);
+    a.out_c = (float2*)rebase(call, w.outc_base, a.out_c);
+    a.out_d = (float*)rebase(call, w.outd_base, a.out_d);
+    a.grad = (const float*)rebase(call, w.grad_base, a.grad);
+    for (long long t = w.t0; t < w.t1; ++t) dense_tile(a, t, sm);
+  }
 }
 
 template <int KIND>
@@ -136,6 +167,8 @@ int64_t invmod_64(int64_t a, int64_t m) {
 struct AxisTab {
   int N, lam, g, Np;
   AxisTables tab;
+  const float2* T = nullptr;   // dense mode: the per-axis map and its adjoint
+  const float2* TH = nullptr;
 };
 
 struct Instance {
@@ -149,6 +182,7 @@ struct Instance {
 struct Phase {
   int kind;
   PassArgs* d_args = nullptr;
+  DenseArgs* d_dargs = nullptr;  // dense phases
   ManyItem* d_items = nullptr;
   int n_items = 0;
 };
@@ -164,6 +198,10 @@ struct ManyPlan {
   std::vector<AxisTab> tabs;
   void* mem = nullptr;      // tables, fold indices, args, items, counters (one allocation)
   float2* ws = nullptr;     // packed workspace (total points)
+  float2* ws2 = nullptr;    // dense mode: the second workspace
+  bool dense = false;
+  void* dense_mem = nullptr;  // dense mode: T, T^H of every table key
+  int grid_dense = 0;
   int* counters = nullptr;  // one per phase
   int grid_fwd = 0, grid_adj = 0;
   size_t smem = 0;
@@ -232,6 +270,75 @@ PassArgs pass_args_for(const Instance& in, int axis, const AxisTab& at, size_t i
 
 }  // namespace
 
+namespace {
+
+// T_j and T_j^H of every table key: the fold pass (the uniform line kernel of
+// that length) on the N unit vectors, then the transpose / conjugate.
+int build_dense_maps(ManyPlan* mp, cudaStream_t s, std::string* err) {
+  size_t bytes = (size_t)mp->total * sizeof(float2);  // the second workspace
+  int nmax = 0;
+  for (const AxisTab& at : mp->tabs) {
+    bytes += 2 * (size_t)at.N * at.N * sizeof(float2);
+    nmax = std::max(nmax, at.N);
+  }
+  const size_t scratch = 2 * (size_t)nmax * nmax * sizeof(float2);
+  cudaError_t e = cudaMalloc(&mp->dense_mem, bytes + scratch);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    mp->dense_mem = nullptr;
+    *err = std::string("dense maps: ") + cudaGetErrorString(e);
+    return FFX_ENOMEM;
+  }
+  char* cur = (char*)mp->dense_mem;
+  mp->ws2 = (float2*)cur;
+  cur += (size_t)mp->total * sizeof(float2);
+  float2* I = (float2*)(cur + (bytes - (size_t)mp->total * sizeof(float2)));
+  float2* O = I + (size_t)nmax * nmax;
+  for (AxisTab& at : mp->tabs) {
+    const int N = at.N;
+    float2* T = (float2*)cur;
+    float2* TH = T + (size_t)N * N;
+    cur += 2 * (size_t)N * N * sizeof(float2);
+    PassKernelInfo info;
+    if (!find_pass_kernel(N, KIND_FWD_FOLD, &info)) {
+      *err = "no fold kernel for length " + std::to_string(N);
+      return FFX_EUNSUPPORTED;
+    }
+    e = cudaFuncSetAttribute(info.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)info.smem);
+    if (e == cudaSuccess) e = launch_identity(I, N, s);
+    PassArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.in = I;
+    a.out_c = O;
+    a.outer = 1;
+    a.inner = 1;
+    a.M = N;
+    a.batch = N;
+    a.nlines = N;
+    a.lam = at.lam;
+    a.g = at.g;
+    a.Np = at.Np;
+    a.qg = 1;
+    a.tab = at.tab;
+    const int lines = pass_lines_per_tile(info, 1);
+    if (e == cudaSuccess) e = info.launch(a, (N + lines - 1) / lines, s);
+    if (e == cudaSuccess) e = launch_dense_build(O, T, TH, N, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // I and O are reused by the next key
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *err = std::string("dense map: ") + cudaGetErrorString(e);
+      return FFX_ECUDA;
+    }
+    at.T = T;
+    at.TH = TH;
+  }
+  mp->dense = true;
+  mp->form = FFX_FORM_DENSE;
+  return FFX_OK;
+}
+
+}  // namespace
+
 int many_create(ManyPlan** out, int n, const ffx_instance_desc* d, uint32_t flags, std::string* err) {
   *out = nullptr;
   if (n < 1 || !d) {
@@ -247,8 +354,8 @@ int many_create(ManyPlan** out, int n, const ffx_instance_desc* d, uint32_t flag
     *err = "unknown flag bits";
     return FFX_EINVAL;
   }
-  if (form != FFX_FORM_AUTO && form != FFX_FORM_PAPER && form != FFX_FORM_FOLD) {
-    *err = "unknown form";
+  if (form != FFX_FORM_AUTO && form != FFX_FORM_PAPER && form != FFX_FORM_FOLD && form != FFX_FORM_DENSE) {
+    *err = "unknown form (paper, fold, dense or automatic)";
     return FFX_EINVAL;
   }
   ManyPlan* mp = new ManyPlan();
@@ -386,8 +493,24 @@ int many_create(ManyPlan** out, int n, const ffx_instance_desc* d, uint32_t flag
       *err = std::string("table fill: ") + cudaGetErrorString(e);
     }
   }
+  // Dense mode: every key's T and T^H (fold pass on the unit vectors).  The
+  // automatic form takes it when the dense map costs less than the fold form
+  // on every key (8 N flops per point at ~0.45 of the FP32 peak against
+  // lam (5 log2 N + 14) + 5 log2 N at ~0.11).
+  if (rc == FFX_OK) {
+    bool dense = (form == FFX_FORM_DENSE);
+    if (form == FFX_FORM_AUTO) {
+      dense = true;
+      for (const AxisTab& at : mp->tabs) {
+        const double lg = std::log2((double)at.N);
+        if (8.0 * at.N / 0.45 >= (at.lam * (5 * lg + 14) + 5 * lg) / 0.11) dense = false;
+      }
+    }
+    if (dense) rc = build_dense_maps(mp, s, err);
+  }
   cudaStreamDestroy(s);
   if (rc != FFX_OK) {
+    if (mp->dense_mem) cudaFree(mp->dense_mem);
     cudaFree(mp->mem);
     delete mp;
     return rc;
@@ -406,6 +529,9 @@ int many_create(ManyPlan** out, int n, const ffx_instance_desc* d, uint32_t flag
   mp->grid_fwd = per * sms;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ka, 256, mp->smem) != cudaSuccess || per < 1) per = 1;
   mp->grid_adj = per * sms;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, many_dense_kernel, 256, 0) != cudaSuccess || per < 1)
+    per = 1;
+  mp->grid_dense = per * sms;
   cudaGetLastError();
   *out = mp;
   return FFX_OK;
@@ -413,8 +539,111 @@ int many_create(ManyPlan** out, int n, const ffx_instance_desc* d, uint32_t flag
 
 namespace {
 
+// Dense phases of one mode.  Instance i runs its own chain of steps: forward
+// passes k = 0 .. n_i - 1 (phase k), then for the backward adjoint passes
+// r = 0 .. n_i - 1 (phase D + r, step n_i + r).  Step s writes workspace s % 2,
+// except the final step, which writes the caller's output; step s reads the
+// input (s = 0) or the workspace of step s - 1.
+int build_dense_phases(ManyPlan* mp, int mode, std::string* err) {
+  std::vector<Phase>& phases = mp->phases[mode];
+  const int D = mp->max_dim;
+  const int nphases = (mode == 2) ? 2 * D : D;
+  for (int ph_i = 0; ph_i < nphases; ++ph_i) {
+    const bool adj = (mode == 2 && ph_i >= D);
+    const int r = adj ? ph_i - D : ph_i;
+    Phase ph;
+    ph.kind = KIND_DENSE;
+    std::vector<DenseArgs> args;
+    std::vector<std::pair<double, ManyItem>> items;
+    for (const Instance& in : mp->inst) {
+      if (r >= in.ndim) continue;
+      const int n_i = in.ndim;
+      const int k = adj ? n_i - 1 - r : r;  // pass index in the forward order
+      const int step = adj ? n_i + r : r;
+      const int last_step = (mode == 2) ? 2 * n_i - 1 : n_i - 1;
+      const int axis = in.order[k];
+      const AxisTab& at = mp->tabs[in.axis_tab[axis]];
+      const size_t off_c = (size_t)in.off * sizeof(float2), off_d = (size_t)in.off * sizeof(float);
+      auto wsb = [](int st) { return (st % 2 == 0) ? BASE_WS : BASE_WS2; };
+      const int in_base = (step == 0) ? BASE_PSI0 : wsb(step - 1);
+      int outc_base = BASE_NONE, outd_base = BASE_NONE;
+      if (step == last_step) {
+        if (mode == 0)
+          outd_base = BASE_OUTD;
+        else
+          outc_base = BASE_OUTC;
+      } else {
+        outc_base = wsb(step);
+      }
+      const int grad_base = (adj && r == 0) ? BASE_GRAD : BASE_NONE;
+      DenseArgs a;
+      std::memset(&a, 0, sizeof(a));
+      int64_t outer = 1, inner = 1;
+      for (int i = 0; i < axis; ++i) outer *= in.dims[i];
+      for (int i = axis + 1; i < in.ndim; ++i) inner *= in.dims[i];
+      a.A = adj ? at.TH : at.T;
+      a.in = (const float2*)(uintptr_t)off_c;
+      a.out_c = outc_base >= 0 ? (float2*)(uintptr_t)off_c : nullptr;
+      a.out_d = outd_base >= 0 ? (float*)(uintptr_t)off_d : nullptr;
+      a.grad = grad_base >= 0 ? (const float*)(uintptr_t)off_d : nullptr;
+      a.outer = outer;
+      a.inner = inner;
+      a.M = in.M;
+      a.batch = 1;
+      a.ncols = outer * inner;
+      a.N = at.N;
+      const int arg = (int)args.size();
+      args.push_back(a);
+      const int64_t ntiles = dense_tile_count(at.N, a.ncols);
+      const int64_t chunk = 4;
+      const double per_tile = (double)at.N * DBM * DBN;
+      for (int64_t t0 = 0; t0 < ntiles; t0 += chunk) {
+        ManyItem w;
+        w.arg = arg;
+        w.N = at.N;
+        w.in_base = in_base;
+        w.outc_base = outc_base;
+        w.outd_base = outd_base;
+        w.grad_base = grad_base;
+        w.t0 = t0;
+        w.t1 = std::min(ntiles, t0 + chunk);
+        items.push_back({per_tile * (double)(w.t1 - w.t0), w});
+      }
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::pair<double, ManyItem>& x, const std::pair<double, ManyItem>& y) {
+                       return x.first > y.first;
+                     });
+    std::vector<ManyItem> flat;
+    flat.reserve(items.size());
+    for (auto& pi : items) flat.push_back(pi.second);
+    const size_t bytes = args.size() * sizeof(DenseArgs) + flat.size() * sizeof(ManyItem);
+    void* m = nullptr;
+    cudaError_t e = cudaMalloc(&m, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *err = std::string("work list: ") + cudaGetErrorString(e);
+      return FFX_ENOMEM;
+    }
+    ph.d_dargs = (DenseArgs*)m;
+    ph.d_items = (ManyItem*)((char*)m + args.size() * sizeof(DenseArgs));
+    ph.n_items = (int)flat.size();
+    e = cudaMemcpy(ph.d_dargs, args.data(), args.size() * sizeof(DenseArgs), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(ph.d_items, flat.data(), flat.size() * sizeof(ManyItem), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(m);
+      *err = std::string("work list upload: ") + cudaGetErrorString(e);
+      return FFX_ECUDA;
+    }
+    phases.push_back(ph);
+  }
+  return FFX_OK;
+}
+
 // Phases of one mode.  mode 0: density, 1: field, 2: backward.
 int build_phases(ManyPlan* mp, int mode, std::string* err) {
+  if (mp->dense) return build_dense_phases(mp, mode, err);
   std::vector<Phase>& phases = mp->phases[mode];
   const int D = mp->max_dim;
   const int fwd_kind = (mp->form == FFX_FORM_PAPER) ? KIND_FWD_PAPER : KIND_FWD_FOLD;
@@ -494,8 +723,24 @@ const void* phase_func(int kind) {
   switch (kind) {
     case KIND_FWD_PAPER: return (const void*)many_kernel<KIND_FWD_PAPER>;
     case KIND_FWD_FOLD: return (const void*)many_kernel<KIND_FWD_FOLD>;
+    case KIND_DENSE: return (const void*)many_dense_kernel;
     default: return (const void*)many_kernel<KIND_ADJ_FOLD>;
   }
+}
+
+// Kernel-node parameters of a phase (params: the kernel's argument pointers).
+void phase_node_params(const ManyPlan* mp, const Phase& ph, void** params, cudaKernelNodeParams* kp) {
+  std::memset(kp, 0, sizeof(*kp));
+  kp->func = (void*)phase_func(ph.kind);
+  if (ph.kind == KIND_DENSE) {
+    kp->gridDim = dim3(mp->grid_dense);
+    kp->sharedMemBytes = 0;  // static
+  } else {
+    kp->gridDim = dim3(ph.kind == KIND_ADJ_FOLD ? mp->grid_adj : mp->grid_fwd);
+    kp->sharedMemBytes = (unsigned)mp->smem;
+  }
+  kp->blockDim = dim3(256);
+  kp->kernelParams = params;
 }
 
 // The graph of one mode: memset(counter_k) -> phase kernel k -> memset(counter_k+1) -> ...
@@ -527,15 +772,10 @@ int build_graph(ManyPlan* mp, int mode, const ManyCall& call, std::string* err) 
     e = cudaGraphAddMemsetNode(&mnode, g, prev ? &prev : nullptr, prev ? 1 : 0, &ms);
     if (e != cudaSuccess) break;
     int* counter = mp->counters + k;
-    void* params[] = {(void*)&ph.d_args, (void*)&ph.d_items, (void*)&ph.n_items, (void*)&counter,
-                      (void*)&call};
+    void* params[] = {ph.kind == KIND_DENSE ? (void*)&ph.d_dargs : (void*)&ph.d_args, (void*)&ph.d_items,
+                      (void*)&ph.n_items, (void*)&counter, (void*)&call};
     cudaKernelNodeParams kp;
-    std::memset(&kp, 0, sizeof(kp));
-    kp.func = (void*)phase_func(ph.kind);
-    kp.gridDim = dim3(ph.kind == KIND_ADJ_FOLD ? mp->grid_adj : mp->grid_fwd);
-    kp.blockDim = dim3(256);
-    kp.sharedMemBytes = (unsigned)mp->smem;
-    kp.kernelParams = params;
+    phase_node_params(mp, ph, params, &kp);
     e = cudaGraphAddKernelNode(&knode, g, &mnode, 1, &kp);
     if (e != cudaSuccess) break;
     kn.push_back(knode);
@@ -563,15 +803,10 @@ int launch_mode(ManyPlan* mp, int mode, const ManyCall& call, cudaStream_t s, st
     for (size_t k = 0; k < phases.size(); ++k) {
       Phase& ph = phases[k];
       int* counter = mp->counters + k;
-      void* params[] = {(void*)&ph.d_args, (void*)&ph.d_items, (void*)&ph.n_items, (void*)&counter,
-                        (void*)&call};
+      void* params[] = {ph.kind == KIND_DENSE ? (void*)&ph.d_dargs : (void*)&ph.d_args, (void*)&ph.d_items,
+                        (void*)&ph.n_items, (void*)&counter, (void*)&call};
       cudaKernelNodeParams kp;
-      std::memset(&kp, 0, sizeof(kp));
-      kp.func = (void*)phase_func(ph.kind);
-      kp.gridDim = dim3(ph.kind == KIND_ADJ_FOLD ? mp->grid_adj : mp->grid_fwd);
-      kp.blockDim = dim3(256);
-      kp.sharedMemBytes = (unsigned)mp->smem;
-      kp.kernelParams = params;
+      phase_node_params(mp, ph, params, &kp);
       cudaError_t e = cudaGraphExecKernelNodeSetParams(mp->exec[mode], mp->knodes[mode][k], &kp);
       if (e != cudaSuccess) {
         *err = std::string("graph update: ") + cudaGetErrorString(e);
@@ -595,8 +830,9 @@ void many_destroy(ManyPlan* mp) {
   for (int m = 0; m < 3; ++m) {
     if (mp->exec[m]) cudaGraphExecDestroy(mp->exec[m]);
     if (mp->graph[m]) cudaGraphDestroy(mp->graph[m]);
-    for (Phase& ph : mp->phases[m]) cudaFree(ph.d_args);
+    for (Phase& ph : mp->phases[m]) cudaFree(ph.kind == KIND_DENSE ? (void*)ph.d_dargs : (void*)ph.d_args);
   }
+  if (mp->dense_mem) cudaFree(mp->dense_mem);
   cudaFree(mp->mem);
   delete mp;
 }
@@ -607,10 +843,20 @@ int many_form(const ManyPlan* mp) { return mp->form; }
 int many_max_dim(const ManyPlan* mp) { return mp->max_dim; }
 
 int many_expand(ManyPlan* mp, const void* psi0, float* out_d, void* out_c, cudaStream_t s, std::string* err) {
+  if (mp->dense && out_c && out_c == psi0) {
+    // a one-pass instance reads and writes the caller's buffer in the same
+    // (not in-place) dense pass
+    for (const Instance& in : mp->inst)
+      if (in.ndim == 1 && in.dims[0] > DBM) {
+        *err = "in-place field of a dense many-instance plan with a 1-D instance longer than 64 points";
+        return FFX_EUNSUPPORTED;
+      }
+  }
   ManyCall c;
   std::memset(&c, 0, sizeof(c));
   c.base[BASE_PSI0] = psi0;
   c.base[BASE_WS] = mp->ws;
+  c.base[BASE_WS2] = mp->ws2;
   c.base[BASE_OUTC] = out_c;
   c.base[BASE_OUTD] = out_d;
   return launch_mode(mp, out_d ? 0 : 1, c, s, err);
@@ -622,6 +868,7 @@ int many_backward(ManyPlan* mp, const void* psi0, const float* grad, void* grad_
   std::memset(&c, 0, sizeof(c));
   c.base[BASE_PSI0] = psi0;
   c.base[BASE_WS] = mp->ws;
+  c.base[BASE_WS2] = mp->ws2;
   c.base[BASE_OUTC] = grad_psi0;
   c.base[BASE_GRAD] = grad;
   return launch_mode(mp, 2, c, s, err);

@@ -32,7 +32,7 @@ def pack(plan, psis):
     return x
 
 
-@pytest.mark.parametrize("form", ["fold", "paper"])
+@pytest.mark.parametrize("form", ["fold", "paper", "dense"])
 def test_many_mixed_shapes_against_oracle(form):
     ffx = require_gpu()
     dims_set = [(48, 16, 32), (32, 32), (96,), (16, 128, 16), (64, 48, 16), (192, 16)]
@@ -75,11 +75,12 @@ def test_many_workload_shapes_match_single_plans_and_replay():
     assert worst < 1e-5
 
 
-def test_many_backward_against_oracle():
+@pytest.mark.parametrize("form", ["auto", "dense"])
+def test_many_backward_against_oracle(form):
     ffx = require_gpu()
-    dims_set = [(32, 48), (16, 32, 16), (64,)]
-    specs, psis = mixed_specs(3, dims_override=dims_set)
-    plan = ffx.PlanMany(specs)
+    dims_set = [(32, 48), (16, 32, 16), (64,), (96, 16)]
+    specs, psis = mixed_specs(4, dims_override=dims_set)
+    plan = ffx.PlanMany(specs, form=form)
     rng = np.random.default_rng(3)
     grads = [rng.normal(size=p.shape).astype(np.float32) for p in psis]
     g = np.zeros(plan.points, np.float32)
@@ -91,7 +92,7 @@ def test_many_backward_against_oracle():
         ref = O.density_loss_gradient(p, gr, dx, t, lam)
         worst = max(worst, rel_l2(got[off:off + p.size].reshape(dims), ref))
     plan.close()
-    print(f"many backward: worst {worst:.2e}")
+    print(f"many backward ({form}): worst {worst:.2e}")
     assert worst < FIELD_TOL
 
 
@@ -100,3 +101,42 @@ def test_many_rejects_unsupported():
     with pytest.raises(ffx.FfxError) as ei:
         ffx.PlanMany([((512,), (0.1,), 1.0, (3,))])
     assert ei.value.code == ffx.FFX_EUNSUPPORTED
+
+
+def test_many_dense_auto_on_the_mixed_workload():
+    """The mixed-batch workload's magnifications (10..100) make the dense maps
+    cheaper than the fold form on every axis: the automatic form takes them;
+    instances against the oracle, field in place, and a replay with new
+    buffers."""
+    ffx = require_gpu()
+    ws = inputs.config_mixed_batch(count=6)
+    specs = [(w.dims, w.dx, w.t, w.lam) for w in ws]
+    psis = [w.realization(0) for w in ws]
+    plan = ffx.PlanMany(specs)
+    assert plan.form == "dense"
+    x = to_dev(pack(plan, psis))
+    rho = ffx.ffx_expand(plan, x).cpu().numpy()
+    y = x.clone()
+    ffx.ffx_expand_field(plan, y, y)
+    field = y.cpu().numpy()
+    worst_d = worst_f = 0.0
+    for (dims, dx, t, lam), p, off in zip(specs, psis, plan.offsets):
+        ref = O.expand_field(p, dx, t, lam)
+        m = p.size
+        worst_d = max(worst_d, rel_l2(rho[off:off + m].reshape(dims), np.abs(ref) ** 2))
+        worst_f = max(worst_f, rel_l2(field[off:off + m].reshape(dims), ref))
+    r2 = ffx.ffx_expand(plan, x.clone()).cpu().numpy()
+    plan.close()
+    print(f"many dense (auto) on the workload: worst density {worst_d:.2e}, field {worst_f:.2e}")
+    assert worst_d < DENSITY_TOL and worst_f < FIELD_TOL
+    assert np.array_equal(r2, rho)
+
+
+def test_many_dense_in_place_guard():
+    ffx = require_gpu()
+    plan = ffx.PlanMany([((96,), (0.1,), 1.0, (40,)), ((32, 32), (0.2, 0.2), 2.0, (30, 30))], form="dense")
+    x = to_dev(np.ones(plan.points, np.complex64))
+    with pytest.raises(ffx.FfxError) as ei:
+        ffx.ffx_expand_field(plan, x, x)
+    assert ei.value.code == ffx.FFX_EUNSUPPORTED
+    plan.close()
