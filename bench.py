@@ -557,7 +557,7 @@ def run_ffx(args):
         # one cooperative launch runs every pass (dense map: FP32 SIMT, or the
         # tensor cores when every axis has 64 points); HBM sees the input read
         # and the output written, the intermediates stay in L2
-        fused_tc = call_forms[0] == "tc"
+        fused_tc = call_forms[0] == "tc" and args.column is None  # detector images: the FP32 fused kernel
         axis_form = "tc" if fused_tc else "fused"
         flops = sum(pass_flops(w.dims[j], w.lam[j], B_ * M // w.dims[j], "dense") for j in order)
         kernel_key = f"fused_{'tc' if fused_tc else 'dense'}_{'x'.join(map(str, w.dims))}_{args.workload}"
