@@ -401,7 +401,8 @@ def run_mixed(args, torch, dist, world, rank, dev):
             "gpu_launches": plan.launches_per_call() * args.steps,
             "clocks": clocks,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                         "frac": achieved / alu_peak, "traffic": None,
+                         "frac": achieved / alu_peak,
+                         "traffic": load_traffic(f"many_dense_mixed_{count}_call") if plan.form == "dense" else None,
                          "kernel": ("many_dense_kernel" if plan.form == "dense" else "many_kernel") + " (all phases of one call)",
                          "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({pk_src})"},
             "roofline_hbm": {"bound": "hbm", "achieved": byts / (ms / args.steps * 1e-3) / 1e9,

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/ffx.h"
+#include "ffx_dense_lines.h"
 #include "ffx_internal.h"
 
 namespace ffx {
@@ -304,7 +305,10 @@ int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* 
     d.N = ax.N;
     d.Aimg = adjoint ? ax.img[1] : ax.img[0];
     d.err = p->dev_err;
-    if (ax.N <= kDenseInPlaceMaxN) {
+    const bool in_place = (const void*)in == (const void*)out_c;
+    if (batch * outer * inner < kDenseFewLines && !in_place) {
+      e = launch_dense_lines(d, stream);
+    } else if (ax.N <= kDenseInPlaceMaxN) {
       int64_t grid = dense_small_tiles(ax.N, d.ncols);
       if (grid > ax.grid_dense_small) grid = ax.grid_dense_small;
       if (grid < 1) grid = 1;
@@ -535,9 +539,11 @@ int run_fused(ffx_plan_s* p, const int* axes, const float2* in, float2* out_c, f
 
 // Relative cost per point of one axis pass (FP32 flops over the fraction of
 // the FP32 peak each form was measured to reach on GB300).
-// `lines` = lines of one realization along the axis: the dense and
-// tensor-core kernels tile lines by 32 and 128, so a handful of lines (a 1-D
-// field) leaves them latency-bound and the FFT forms take it.
+// `lines` = lines of one realization along the axis.  The tensor-core kernel
+// tiles lines by 128, so fewer lines leave it latency-bound.  Fewer than
+// kDenseFewLines lines (a 1-D field) take the dense form: its few-lines kernel
+// spreads the rows of T over N / 8 blocks, while the FFT forms run each line's
+// transforms in sequence inside one block.
 double model_cost(const Axis& ax, int form, int64_t lines) {
   const double N = ax.N, lg = std::log2(N), lam = ax.lam;
   switch (form) {
@@ -551,7 +557,7 @@ double model_cost(const Axis& ax, int form, int64_t lines) {
       if (lines < 128) return 1e30;
       return N < 128 ? 8 * N / 0.40 : 8 * N / 2.0;
     default:
-      if (lines < 32) return 1e30;
+      if (lines < kDenseFewLines) return 0;
       return 8 * N / 0.45;
   }
 }
