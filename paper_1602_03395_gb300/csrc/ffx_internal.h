@@ -107,7 +107,8 @@ size_t dense_small_image_floats2(int N);
 cudaError_t launch_dense_small_image(const float2* T, float2* img, int N, cudaStream_t s);
 constexpr int kDenseMaxN = 1024;
 // dense form on the tensor cores (ffx_tc.cu), split TF32, for lines of N
-// points with N a multiple of 64 up to kDenseMaxN; in place only for N = 64
+// points with N a multiple of 16 from 32 up to kDenseMaxN; in place only for
+// N <= 64
 bool dense_tc_supported(int N);
 cudaError_t dense_tc_prepare();  // shared-memory attributes of the kernel's variants
 size_t dense_tc_t_bytes(int N);

@@ -1,6 +1,6 @@
 // Dense form on the tensor cores (tcgen05): the per-axis map of lines of N
-// points (N a multiple of 64, up to 1024) as a real matrix product with
-// split-TF32 operands, accumulated in tensor memory.
+// points (N a multiple of 16, from 32 up to 1024) as a real matrix product
+// with split-TF32 operands, accumulated in tensor memory.
 //
 // The complex map OUT[n][c] = sum_k T[n][k] IN[k][c] becomes a real product
 // with every complex entry t = x + iy of T replaced by the 2 x 2 block
@@ -38,7 +38,9 @@
 // Work items are (128 lines, 128 real rows) of the output, rows fastest
 // varying across the items that run together so the lines' inputs are shared
 // in L2; with N > 64 a line's outputs span several items, so such passes do
-// not run in place.
+// not run in place.  When 2N is not a multiple of 128 the last row block is
+// narrower: its MMAs run with N = the rows that exist (a multiple of 32), its
+// T chunks are copied only that far, and the epilogue stops there.
 //
 // Every wait is bounded; a wait that runs out sets a block-wide abort flag
 // (every other wait then gives up at once); producers drain their own copies,
@@ -92,8 +94,12 @@ constexpr int ACC_COLS = 4 * ROWS;           // two buffers x (head product, cro
 
 using namespace tc;
 
-// kind::tf32, D = F32, A = B = TF32, both K-major, N = ROWS, M = LINES
-constexpr uint32_t kIdesc = idesc_tf32(LINES, ROWS);
+// Real output rows of row block mt: ROWS, or what is left of 2N in the last
+// block (a multiple of 32, since N is a multiple of 16).
+__host__ __device__ __forceinline__ int row_count(int N, int mt) {
+  const int left = 2 * N - mt * ROWS;
+  return left < ROWS ? left : ROWS;
+}
 
 // Line c of the pass (realization b of the batch when accumulating): offset
 // of its first point, or -1 past the end; br = its realization.
@@ -143,7 +149,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const int mtiles = (2 * a.N) / ROWS;
+  const int mtiles = (2 * a.N + ROWS - 1) / ROWS;
   const int kchunks = (2 * a.N) / TKC;
   const int nb = a.acc ? (int)a.batch : 1;
   const int64_t ctiles = (a.ncols + LINES - 1) / LINES;
@@ -280,14 +286,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (u >= 1 && !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)((u - 1) & 1), &s_abort)) break;
       unsigned char* st = tsm + L::T_RES + s * L::STAGE;
       if (!RES && t == 0) {
+        // the row block's rows that exist, head and tail parts
+        const uint32_t part = (uint32_t)row_count(a.N, mt) * (TKC * 4);
         const uint32_t cb = smem_u32(&copy_bar[s]);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cb), "r"(T_CHUNK) : "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cb), "r"(2 * part) : "memory");
         const unsigned char* src = Tblk + ((size_t)mt * kchunks + kc) * T_CHUNK;
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                smem_u32(st)),
-            "l"(src), "r"(T_CHUNK), "r"(cb)
-            : "memory");
+        bulk_g2s(smem_u32(st), src, part, cb);
+        bulk_g2s(smem_u32(st + T_PART), src + T_PART, part, cb);
         last_u[s] = (int)(u & 1);
       }
       const int slot = (int)(c % RAW);
@@ -338,6 +343,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       int64_t g = 0, sub = 0;
       bool ok = !RES || mbar_wait(smem_u32(&tres_bar), 0u, &s_abort);  // resident T has landed
       for (int64_t it = 0; ok && it < my_items; ++it) {
+        const uint32_t idesc = idesc_tf32(LINES, row_count(a.N, (int)((blockIdx.x + it * gridDim.x) % mtiles)));
         for (int b = 0; ok && b < nb; ++b, ++sub) {
           const int buf = (int)(sub & 1);
           const int64_t v = sub >> 1;
@@ -367,9 +373,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               const uint64_t dth = make_desc(th + o, CORE_LBO, CHUNK_SBO);
               const uint64_t dtl = make_desc(tl + o, CORE_LBO, CHUNK_SBO);
               const uint32_t more = (kc == 0 && ks == 0) ? 0u : 1u;
-              mma_tf32(d1, dxh, dth, kIdesc, more);
-              mma_tf32(d2, dxh, dtl, kIdesc, more);
-              mma_tf32(d2, dxl, dth, kIdesc, 1u);
+              mma_tf32(d1, dxh, dth, idesc, more);
+              mma_tf32(d2, dxh, dtl, idesc, more);
+              mma_tf32(d2, dxl, dth, idesc, 1u);
             }
             mma_commit(smem_u32(&empty_bar[s]));
           }
@@ -396,6 +402,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int mt = (int)(w % mtiles);
       const int64_t ct = w / mtiles;
       const int nbase = mt * (ROWS / 2);
+      const int rows = row_count(a.N, mt);  // real rows of this item
       for (int b = 0; b < nb; ++b, ++sub) {
         const int buf = (int)(sub & 1);
         const int64_t v = sub >> 1;
@@ -408,7 +415,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         line_ref(a, ct * LINES + r, b, base, br);
         const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * ROWS);
 #pragma unroll 1
-        for (int j0 = 0; j0 < ROWS; j0 += 16) {
+        for (int j0 = 0; j0 < rows; j0 += 16) {
           uint32_t x[16], z[16];
           tmem_ld16(taddr + (uint32_t)j0, x);
           tmem_ld16(taddr + (uint32_t)(ROWS + j0), z);
@@ -455,7 +462,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (contiguous) {
               float4* o = reinterpret_cast<float4*>(a.out_d + o0);
 #pragma unroll
-              for (int m = 0; m < ROWS / 8; ++m) {
+              for (int m = 0; m < rows / 8; ++m) {
                 float4 cur = o[m];
                 cur.x += racc[(4 * m) * LINES + r];
                 cur.y += racc[(4 * m + 1) * LINES + r];
@@ -465,7 +472,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               }
             } else {
 #pragma unroll
-              for (int m = 0; m < ROWS / 2; ++m) a.out_d[o0 + (int64_t)m * inner] += racc[m * LINES + r];
+              for (int m = 0; m < rows / 2; ++m) a.out_d[o0 + (int64_t)m * inner] += racc[m * LINES + r];
             }
           }
           for (int m = 0; m < ROWS / 2; ++m) racc[m * LINES + r] = 0.f;
@@ -491,17 +498,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // entry of T[n][k].
 __global__ void tc_build_t_kernel(const float2* __restrict__ T, unsigned char* __restrict__ Tblk, int N) {
   const int R = 2 * N;
+  const int RP = (R + ROWS - 1) / ROWS * ROWS;  // rows padded to whole row blocks (zeros past R)
   const int kchunks = R / TKC;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)R * R;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)RP * R;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(idx / R), kp = (int)(idx - (int64_t)r * R);
     const int n = r >> 1, po = r & 1, k = kp >> 1, pi = kp & 1;
-    const float2 t = T[(int64_t)n * N + k];
-    float v;
-    if (po == 0)
-      v = pi == 0 ? t.x : -t.y;
-    else
-      v = pi == 0 ? t.y : t.x;
+    float v = 0.f;
+    if (r < R) {
+      const float2 t = T[(int64_t)n * N + k];
+      if (po == 0)
+        v = pi == 0 ? t.x : -t.y;
+      else
+        v = pi == 0 ? t.y : t.x;
+    }
     const float hi = tf32_round(v);
     const int mt = r / ROWS, rr = r % ROWS, kc = kp / TKC, kk = kp % TKC;
     unsigned char* blk = Tblk + ((size_t)mt * kchunks + kc) * T_CHUNK;
@@ -513,7 +523,7 @@ __global__ void tc_build_t_kernel(const float2* __restrict__ T, unsigned char* _
 
 }  // namespace
 
-bool dense_tc_supported(int N) { return N >= 64 && N <= kDenseMaxN && N % 64 == 0; }
+bool dense_tc_supported(int N) { return N >= 32 && N <= kDenseMaxN && N % 16 == 0; }
 cudaError_t dense_tc_prepare() {
   cudaError_t e = cudaFuncSetAttribute(dense_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        TcLayout<false>::SMEM + EXTRA_SMEM);
@@ -522,7 +532,9 @@ cudaError_t dense_tc_prepare() {
                              TcLayout<true>::SMEM);
   return e;
 }
-size_t dense_tc_t_bytes(int N) { return (size_t)(2 * N) * (2 * N) * 8; }
+size_t dense_tc_t_bytes(int N) {
+  return (size_t)((2 * N + ROWS - 1) / ROWS) * ((2 * N) / TKC) * T_CHUNK;  // row blocks x K chunks
+}
 
 cudaError_t launch_dense_tc(const DenseArgs& a, const unsigned char* Tblk, int* err, int grid,
                             cudaStream_t stream) {
@@ -536,7 +548,9 @@ cudaError_t launch_dense_tc(const DenseArgs& a, const unsigned char* Tblk, int* 
   return cudaGetLastError();
 }
 
-int64_t dense_tc_tiles(int N, int64_t ncols) { return ((ncols + LINES - 1) / LINES) * ((2 * N) / ROWS); }
+int64_t dense_tc_tiles(int N, int64_t ncols) {
+  return ((ncols + LINES - 1) / LINES) * ((2 * N + ROWS - 1) / ROWS);
+}
 
 cudaError_t launch_tc_build_t(const float2* T, unsigned char* Tblk, int N, cudaStream_t s) {
   tc_build_t_kernel<<<256, 256, 0, s>>>(T, Tblk, N);

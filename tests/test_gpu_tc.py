@@ -1,5 +1,6 @@
 """The dense form on the tensor cores (tcgen05, split TF32) for axes whose
-length is a multiple of 64, against the FP64 oracle."""
+length is a multiple of 16 from 32 up (a last row block narrower than 128 real
+rows when 2N is not a multiple of 128), against the FP64 oracle."""
 
 import numpy as np
 import pytest
@@ -32,6 +33,12 @@ TC_CASES = [
     ((768,), (5,), 2),
     ((1024,), (3,), 5),
     ((128, 16, 192), (9, 4, 3), 1),
+    # lengths whose last row block is partial (2N mod 128 = 32, 64, 96)
+    ((96, 96, 96), (10, 10, 10), 1),
+    ((48, 48, 48), (20, 20, 20), 2),
+    ((32,), (50,), 200),
+    ((128, 32, 32), (15, 15, 15), 1),
+    ((384, 96), (3, 7), 2),
 ]
 
 
@@ -68,8 +75,9 @@ def test_tc_workload_and_accumulate(ffx):
     assert e1 < DENSITY_TOL and e2 < DENSITY_TOL
 
 
-def test_tc_adjoint_and_backward(ffx):
-    dims, dx, lam, t = (64, 32, 64), (0.25, 0.2, 0.3), (6, 3, 4), 3.0
+@pytest.mark.parametrize("dims", [(64, 32, 64), (96, 48, 32)])
+def test_tc_adjoint_and_backward(ffx, dims):
+    dx, lam, t = (0.25, 0.2, 0.3), (6, 3, 4), 3.0
     rng = np.random.default_rng(77)
     psi = random_field(rng, (2,) + dims)
     grad = rng.normal(size=(2,) + dims).astype(np.float32)
