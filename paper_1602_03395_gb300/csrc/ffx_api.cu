@@ -1044,6 +1044,7 @@ int ffx_plan_many(ffx_plan_t* out, int n_instances, const ffx_instance_desc* des
   }
   p->many = mp;
   p->ndim = many_max_dim(mp);
+  p->dev_err = many_device_errors(mp);
   for (int j = 0; j < 3; ++j) p->axis[j].form = many_form(mp);
   p->M = many_total(mp);
   *out = p;

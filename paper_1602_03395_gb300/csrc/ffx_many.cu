@@ -30,6 +30,7 @@
 #include "ffx_internal.h"
 #include "ffx_pass.cuh"
 #include "ffx_plans.h"
+#include "ffx_tc_many.h"
 
 namespace ffx {
 
@@ -37,6 +38,7 @@ namespace ffx {
 enum ManyBase : int { BASE_NONE = -1, BASE_PSI0 = 0, BASE_WS = 1, BASE_OUTC = 2, BASE_OUTD = 3,
                       BASE_GRAD = 4, BASE_WS2 = 5, NBASE = 6 };
 constexpr int KIND_DENSE = 100;  // a dense phase (forward or adjoint: the item's matrix decides)
+constexpr int KIND_TC = 101;     // the same on the tensor cores (split TF32)
 struct ManyCall {
   const void* base[NBASE];
 };
@@ -169,6 +171,7 @@ struct AxisTab {
   AxisTables tab;
   const float2* T = nullptr;   // dense mode: the per-axis map and its adjoint
   const float2* TH = nullptr;
+  const unsigned char* tc[2] = {nullptr, nullptr};  // tensor-core mode: split operand blocks of T, T^H
 };
 
 struct Instance {
@@ -185,6 +188,9 @@ struct Phase {
   DenseArgs* d_dargs = nullptr;  // dense phases
   ManyItem* d_items = nullptr;
   int n_items = 0;
+  TcPassArg* d_targs = nullptr;  // tensor-core phases
+  TcItem* d_titems = nullptr;
+  long long n_titems = 0;
 };
 
 }  // namespace
@@ -200,7 +206,11 @@ struct ManyPlan {
   float2* ws = nullptr;     // packed workspace (total points)
   float2* ws2 = nullptr;    // dense mode: the second workspace
   bool dense = false;
+  bool tc = false;            // dense mode on the tensor cores
   void* dense_mem = nullptr;  // dense mode: T, T^H of every table key
+  void* tc_mem = nullptr;     // tensor-core mode: operand blocks of every key
+  int* dev_err = nullptr;     // launches that gave up on a bounded wait
+  int grid_tc = 0;
   int grid_dense = 0;
   int* counters = nullptr;  // one per phase
   int grid_fwd = 0, grid_adj = 0;
@@ -274,7 +284,7 @@ namespace {
 
 // T_j and T_j^H of every table key: the fold pass (the uniform line kernel of
 // that length) on the N unit vectors, then the transpose / conjugate.
-int build_dense_maps(ManyPlan* mp, cudaStream_t s, std::string* err) {
+int build_dense_maps(ManyPlan* mp, bool tc, cudaStream_t s, std::string* err) {
   size_t bytes = (size_t)mp->total * sizeof(float2);  // the second workspace
   int nmax = 0;
   for (const AxisTab& at : mp->tabs) {
@@ -334,6 +344,53 @@ int build_dense_maps(ManyPlan* mp, cudaStream_t s, std::string* err) {
   }
   mp->dense = true;
   mp->form = FFX_FORM_DENSE;
+  if (!tc) return FFX_OK;
+  // tensor-core mode: the split operand blocks of every key's T and T^H, and
+  // the kernel's shared-memory allowance (one block per SM)
+  size_t tbytes = 0;
+  for (const AxisTab& at : mp->tabs) tbytes += 2 * dense_tc_t_bytes(at.N);
+  e = many_tc_prepare();
+  int per = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, many_tc_func(), many_tc_threads(), many_tc_smem());
+  if (e != cudaSuccess || per < 1) {
+    cudaGetLastError();
+    return FFX_OK;  // the FP32 dense phases
+  }
+  e = cudaMalloc(&mp->tc_mem, tbytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    mp->tc_mem = nullptr;
+    *err = std::string("tensor-core operands: ") + cudaGetErrorString(e);
+    return FFX_ENOMEM;
+  }
+  unsigned char* tcur = (unsigned char*)mp->tc_mem;
+  for (AxisTab& at : mp->tabs) {
+    unsigned char* t0 = tcur;
+    unsigned char* t1 = tcur + dense_tc_t_bytes(at.N);
+    tcur = t1 + dense_tc_t_bytes(at.N);
+    e = launch_tc_build_t(at.T, t0, at.N, s);
+    if (e == cudaSuccess) e = launch_tc_build_t(at.TH, t1, at.N, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *err = std::string("tensor-core operands: ") + cudaGetErrorString(e);
+      return FFX_ECUDA;
+    }
+    at.tc[0] = t0;
+    at.tc[1] = t1;
+  }
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *err = std::string("tensor-core operands: ") + cudaGetErrorString(e);
+    return FFX_ECUDA;
+  }
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  mp->grid_tc = sms;
+  mp->tc = true;
+  mp->form = FFX_FORM_TC;
   return FFX_OK;
 }
 
@@ -354,8 +411,9 @@ int many_create(ManyPlan** out, int n, const ffx_instance_desc* d, uint32_t flag
     *err = "unknown flag bits";
     return FFX_EINVAL;
   }
-  if (form != FFX_FORM_AUTO && form != FFX_FORM_PAPER && form != FFX_FORM_FOLD && form != FFX_FORM_DENSE) {
-    *err = "unknown form (paper, fold, dense or automatic)";
+  if (form != FFX_FORM_AUTO && form != FFX_FORM_PAPER && form != FFX_FORM_FOLD && form != FFX_FORM_DENSE &&
+      form != FFX_FORM_TC) {
+    *err = "unknown form (paper, fold, dense, tc or automatic)";
     return FFX_EINVAL;
   }
   ManyPlan* mp = new ManyPlan();
@@ -437,12 +495,19 @@ int many_create(ManyPlan** out, int n, const ffx_instance_desc* d, uint32_t flag
   mp->ws = (float2*)cur;
   cur += ws_bytes;
   mp->counters = (int*)cur;
+  mp->dev_err = mp->counters + 32;  // the counters' region holds it too (zeroed below)
   cur += cnt_bytes;
   cudaStream_t s;
   cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
   std::vector<int> fold_h;
   int rc = FFX_OK;
-  for (const Key& k : keys) {
+  e = cudaMemsetAsync(mp->counters, 0, cnt_bytes, s);  // phase counters and the error count
+  if (e != cudaSuccess) {
+    rc = FFX_ECUDA;
+    *err = std::string("counters: ") + cudaGetErrorString(e);
+  }
+  for (size_t ki = 0; rc == FFX_OK && ki < keys.size(); ++ki) {
+    const Key& k = keys[ki];
     AxisTab at;
     at.N = (int)std::get<0>(k);
     at.lam = std::get<1>(k);
@@ -497,8 +562,11 @@ int many_create(ManyPlan** out, int n, const ffx_instance_desc* d, uint32_t flag
   // automatic form takes it when the dense map costs less than the fold form
   // on every key (8 N flops per point at ~0.45 of the FP32 peak against
   // lam (5 log2 N + 14) + 5 log2 N at ~0.11).
+  // Tensor-core mode (FFX_FORM_TC, or the automatic form once dense): every
+  // key's lines a multiple of 16 points from 32 up; otherwise, or if the
+  // kernel cannot be resident, the FP32 dense phases.
   if (rc == FFX_OK) {
-    bool dense = (form == FFX_FORM_DENSE);
+    bool dense = (form == FFX_FORM_DENSE || form == FFX_FORM_TC);
     if (form == FFX_FORM_AUTO) {
       dense = true;
       for (const AxisTab& at : mp->tabs) {
@@ -506,10 +574,13 @@ int many_create(ManyPlan** out, int n, const ffx_instance_desc* d, uint32_t flag
         if (8.0 * at.N / 0.45 >= (at.lam * (5 * lg + 14) + 5 * lg) / 0.11) dense = false;
       }
     }
-    if (dense) rc = build_dense_maps(mp, s, err);
+    bool tc = (form == FFX_FORM_TC || form == FFX_FORM_AUTO);
+    for (const AxisTab& at : mp->tabs) tc = tc && dense_tc_supported(at.N);
+    if (dense) rc = build_dense_maps(mp, tc, s, err);
   }
   cudaStreamDestroy(s);
   if (rc != FFX_OK) {
+    if (mp->tc_mem) cudaFree(mp->tc_mem);
     if (mp->dense_mem) cudaFree(mp->dense_mem);
     cudaFree(mp->mem);
     delete mp;
@@ -641,8 +712,114 @@ int build_dense_phases(ManyPlan* mp, int mode, std::string* err) {
   return FFX_OK;
 }
 
+// Tensor-core phases of one mode: the same chains of steps as the dense
+// phases, cut into items of 128 lines x 128 real rows.  Items of one (pass,
+// line tile) stay adjacent (their row blocks share the lines' inputs in L2);
+// those groups run in order of cost, biggest first, and each block takes
+// every gridDim-th item.
+int build_tc_phases(ManyPlan* mp, int mode, std::string* err) {
+  std::vector<Phase>& phases = mp->phases[mode];
+  const int D = mp->max_dim;
+  const int nphases = (mode == 2) ? 2 * D : D;
+  const int64_t LN = many_tc_lines();
+  for (int ph_i = 0; ph_i < nphases; ++ph_i) {
+    const bool adj = (mode == 2 && ph_i >= D);
+    const int r = adj ? ph_i - D : ph_i;
+    Phase ph;
+    ph.kind = KIND_TC;
+    std::vector<TcPassArg> args;
+    std::vector<std::pair<double, int>> groups;  // (cost, pass)
+    for (const Instance& in : mp->inst) {
+      if (r >= in.ndim) continue;
+      const int n_i = in.ndim;
+      const int k = adj ? n_i - 1 - r : r;
+      const int step = adj ? n_i + r : r;
+      const int last_step = (mode == 2) ? 2 * n_i - 1 : n_i - 1;
+      const int axis = in.order[k];
+      const AxisTab& at = mp->tabs[in.axis_tab[axis]];
+      const size_t off_c = (size_t)in.off * sizeof(float2), off_d = (size_t)in.off * sizeof(float);
+      auto wsb = [](int st) { return (st % 2 == 0) ? BASE_WS : BASE_WS2; };
+      TcPassArg pa;
+      std::memset(&pa, 0, sizeof(pa));
+      pa.in_base = (step == 0) ? BASE_PSI0 : wsb(step - 1);
+      pa.outc_base = BASE_NONE;
+      pa.outd_base = BASE_NONE;
+      if (step == last_step) {
+        if (mode == 0)
+          pa.outd_base = BASE_OUTD;
+        else
+          pa.outc_base = BASE_OUTC;
+      } else {
+        pa.outc_base = wsb(step);
+      }
+      pa.grad_base = (adj && r == 0) ? BASE_GRAD : BASE_NONE;
+      int64_t outer = 1, inner = 1;
+      for (int i = 0; i < axis; ++i) outer *= in.dims[i];
+      for (int i = axis + 1; i < in.ndim; ++i) inner *= in.dims[i];
+      DenseArgs& a = pa.d;
+      a.in = (const float2*)(uintptr_t)off_c;
+      a.out_c = pa.outc_base >= 0 ? (float2*)(uintptr_t)off_c : nullptr;
+      a.out_d = pa.outd_base >= 0 ? (float*)(uintptr_t)off_d : nullptr;
+      a.grad = pa.grad_base >= 0 ? (const float*)(uintptr_t)off_d : nullptr;
+      a.outer = outer;
+      a.inner = inner;
+      a.M = in.M;
+      a.batch = 1;
+      a.ncols = outer * inner;
+      a.N = at.N;
+      pa.tblk = at.tc[adj ? 1 : 0];
+      groups.push_back({(double)at.N * at.N, (int)args.size()});
+      args.push_back(pa);
+    }
+    std::vector<std::pair<double, TcItem>> cut;
+    for (const auto& gr : groups) {
+      const TcPassArg& pa = args[gr.second];
+      const int64_t ctiles = (pa.d.ncols + LN - 1) / LN;
+      const int mts = many_tc_row_blocks(pa.d.N);
+      for (int64_t ct = 0; ct < ctiles; ++ct)
+        for (int mt = 0; mt < mts; ++mt) {
+          TcItem w;
+          w.ct = ct;
+          w.arg = gr.second;
+          w.mt = mt;
+          cut.push_back({gr.first, w});
+        }
+    }
+    std::stable_sort(cut.begin(), cut.end(),
+                     [](const std::pair<double, TcItem>& x, const std::pair<double, TcItem>& y) {
+                       return x.first > y.first;
+                     });
+    std::vector<TcItem> flat;
+    flat.reserve(cut.size());
+    for (auto& c : cut) flat.push_back(c.second);
+    const size_t abytes = (args.size() * sizeof(TcPassArg) + 255) & ~size_t(255);
+    const size_t bytes = abytes + flat.size() * sizeof(TcItem);
+    void* m = nullptr;
+    cudaError_t e = cudaMalloc(&m, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *err = std::string("work list: ") + cudaGetErrorString(e);
+      return FFX_ENOMEM;
+    }
+    ph.d_targs = (TcPassArg*)m;
+    ph.d_titems = (TcItem*)((char*)m + abytes);
+    ph.n_titems = (long long)flat.size();
+    e = cudaMemcpy(ph.d_targs, args.data(), args.size() * sizeof(TcPassArg), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(ph.d_titems, flat.data(), flat.size() * sizeof(TcItem), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(m);
+      *err = std::string("work list upload: ") + cudaGetErrorString(e);
+      return FFX_ECUDA;
+    }
+    phases.push_back(ph);
+  }
+  return FFX_OK;
+}
+
 // Phases of one mode.  mode 0: density, 1: field, 2: backward.
 int build_phases(ManyPlan* mp, int mode, std::string* err) {
+  if (mp->tc) return build_tc_phases(mp, mode, err);
   if (mp->dense) return build_dense_phases(mp, mode, err);
   std::vector<Phase>& phases = mp->phases[mode];
   const int D = mp->max_dim;
@@ -721,6 +898,7 @@ int build_phases(ManyPlan* mp, int mode, std::string* err) {
 
 const void* phase_func(int kind) {
   switch (kind) {
+    case KIND_TC: return many_tc_func();
     case KIND_FWD_PAPER: return (const void*)many_kernel<KIND_FWD_PAPER>;
     case KIND_FWD_FOLD: return (const void*)many_kernel<KIND_FWD_FOLD>;
     case KIND_DENSE: return (const void*)many_dense_kernel;
@@ -728,10 +906,30 @@ const void* phase_func(int kind) {
   }
 }
 
+// The tensor-core kernel's parameters for a phase and a call's buffers.
+static_assert(NBASE <= kTcBases, "call bases");
+TcParams tc_params(const ManyPlan* mp, const Phase& ph, const ManyCall& call) {
+  TcParams tp;
+  std::memset(&tp, 0, sizeof(tp));
+  tp.args = ph.d_targs;
+  tp.items = ph.d_titems;
+  tp.n_items = ph.n_titems;
+  tp.err = mp->dev_err;
+  for (int b = 0; b < NBASE; ++b) tp.call.base[b] = call.base[b];
+  return tp;
+}
+
 // Kernel-node parameters of a phase (params: the kernel's argument pointers).
 void phase_node_params(const ManyPlan* mp, const Phase& ph, void** params, cudaKernelNodeParams* kp) {
   std::memset(kp, 0, sizeof(*kp));
   kp->func = (void*)phase_func(ph.kind);
+  if (ph.kind == KIND_TC) {
+    kp->gridDim = dim3(mp->grid_tc);
+    kp->blockDim = dim3(many_tc_threads());
+    kp->sharedMemBytes = (unsigned)many_tc_smem();
+    kp->kernelParams = params;
+    return;
+  }
   if (ph.kind == KIND_DENSE) {
     kp->gridDim = dim3(mp->grid_dense);
     kp->sharedMemBytes = 0;  // static
@@ -774,8 +972,10 @@ int build_graph(ManyPlan* mp, int mode, const ManyCall& call, std::string* err) 
     int* counter = mp->counters + k;
     void* params[] = {ph.kind == KIND_DENSE ? (void*)&ph.d_dargs : (void*)&ph.d_args, (void*)&ph.d_items,
                       (void*)&ph.n_items, (void*)&counter, (void*)&call};
+    TcParams tp = tc_params(mp, ph, call);
+    void* tparams[] = {(void*)&tp};
     cudaKernelNodeParams kp;
-    phase_node_params(mp, ph, params, &kp);
+    phase_node_params(mp, ph, ph.kind == KIND_TC ? tparams : params, &kp);
     e = cudaGraphAddKernelNode(&knode, g, &mnode, 1, &kp);
     if (e != cudaSuccess) break;
     kn.push_back(knode);
@@ -805,8 +1005,10 @@ int launch_mode(ManyPlan* mp, int mode, const ManyCall& call, cudaStream_t s, st
       int* counter = mp->counters + k;
       void* params[] = {ph.kind == KIND_DENSE ? (void*)&ph.d_dargs : (void*)&ph.d_args, (void*)&ph.d_items,
                         (void*)&ph.n_items, (void*)&counter, (void*)&call};
+      TcParams tp = tc_params(mp, ph, call);
+      void* tparams[] = {(void*)&tp};
       cudaKernelNodeParams kp;
-      phase_node_params(mp, ph, params, &kp);
+      phase_node_params(mp, ph, ph.kind == KIND_TC ? tparams : params, &kp);
       cudaError_t e = cudaGraphExecKernelNodeSetParams(mp->exec[mode], mp->knodes[mode][k], &kp);
       if (e != cudaSuccess) {
         *err = std::string("graph update: ") + cudaGetErrorString(e);
@@ -830,8 +1032,10 @@ void many_destroy(ManyPlan* mp) {
   for (int m = 0; m < 3; ++m) {
     if (mp->exec[m]) cudaGraphExecDestroy(mp->exec[m]);
     if (mp->graph[m]) cudaGraphDestroy(mp->graph[m]);
-    for (Phase& ph : mp->phases[m]) cudaFree(ph.kind == KIND_DENSE ? (void*)ph.d_dargs : (void*)ph.d_args);
+    for (Phase& ph : mp->phases[m])
+      cudaFree(ph.kind == KIND_TC ? (void*)ph.d_targs : ph.kind == KIND_DENSE ? (void*)ph.d_dargs : (void*)ph.d_args);
   }
+  if (mp->tc_mem) cudaFree(mp->tc_mem);
   if (mp->dense_mem) cudaFree(mp->dense_mem);
   cudaFree(mp->mem);
   delete mp;
@@ -841,6 +1045,7 @@ int64_t many_total(const ManyPlan* mp) { return mp->total; }
 int64_t many_offset(const ManyPlan* mp, int i) { return (i < 0 || i >= mp->n) ? -1 : mp->inst[i].off; }
 int many_form(const ManyPlan* mp) { return mp->form; }
 int many_max_dim(const ManyPlan* mp) { return mp->max_dim; }
+int* many_device_errors(const ManyPlan* mp) { return mp->dev_err; }
 
 int many_expand(ManyPlan* mp, const void* psi0, float* out_d, void* out_c, cudaStream_t s, std::string* err) {
   if (mp->dense && out_c && out_c == psi0) {

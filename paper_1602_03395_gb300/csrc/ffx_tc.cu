@@ -49,6 +49,7 @@
 #include <cstring>
 
 #include "ffx_internal.h"
+#include "ffx_tc_many.h"
 #include "ffx_tcgen05.cuh"
 
 namespace ffx {
@@ -101,9 +102,70 @@ __host__ __device__ __forceinline__ int row_count(int N, int mt) {
   return left < ROWS ? left : ROWS;
 }
 
+// What a role of the kernel needs of one work item: its pass (pointers,
+// geometry, split operand blocks of T), its line tile ct and row block mt, and
+// the realizations it sums over (nb > 1 only when accumulating).
+struct TcView {
+  const float2* in;
+  const float* grad;
+  float2* out_c;
+  float* out_d;
+  const unsigned char* tblk;
+  int64_t outer, inner, M, ncols, ct;
+  int N, acc, grad_shared, mt, nb;
+};
+
+__device__ __forceinline__ const void* tc_rebase(const TcBases& c, int base, const void* off) {
+  return base < 0 ? nullptr : (const void*)((const char*)c.base[base] + (uintptr_t)off);
+}
+
+template <bool MANY>
+__device__ __forceinline__ TcView tc_view(const TcParams& P, int64_t w) {
+  TcView v;
+  if (MANY) {
+    const TcItem item = P.items[w];
+    const TcPassArg& pa = P.args[item.arg];
+    const DenseArgs& d = pa.d;
+    v.in = (const float2*)tc_rebase(P.call, pa.in_base, d.in);
+    v.grad = (const float*)tc_rebase(P.call, pa.grad_base, d.grad);
+    v.out_c = (float2*)tc_rebase(P.call, pa.outc_base, d.out_c);
+    v.out_d = (float*)tc_rebase(P.call, pa.outd_base, d.out_d);
+    v.tblk = pa.tblk;
+    v.outer = d.outer;
+    v.inner = d.inner;
+    v.M = d.M;
+    v.ncols = d.ncols;
+    v.N = d.N;
+    v.acc = 0;
+    v.grad_shared = d.grad_shared;
+    v.nb = 1;
+    v.ct = item.ct;
+    v.mt = item.mt;
+  } else {
+    const DenseArgs& d = P.a;
+    const int mtiles = (2 * d.N + ROWS - 1) / ROWS;
+    v.in = d.in;
+    v.grad = d.grad;
+    v.out_c = d.out_c;
+    v.out_d = d.out_d;
+    v.tblk = P.tblk;
+    v.outer = d.outer;
+    v.inner = d.inner;
+    v.M = d.M;
+    v.ncols = d.ncols;
+    v.N = d.N;
+    v.acc = d.acc;
+    v.grad_shared = d.grad_shared;
+    v.nb = d.acc ? (int)d.batch : 1;
+    v.ct = w / mtiles;
+    v.mt = (int)(w % mtiles);
+  }
+  return v;
+}
+
 // Line c of the pass (realization b of the batch when accumulating): offset
 // of its first point, or -1 past the end; br = its realization.
-__device__ __forceinline__ void line_ref(const DenseArgs& a, int64_t c, int b, long long& base, int& br) {
+__device__ __forceinline__ void line_ref(const TcView& a, int64_t c, int b, long long& base, int& br) {
   base = -1;
   br = 0;
   if (c < a.ncols) {
@@ -137,9 +199,11 @@ __device__ __forceinline__ void split_store(unsigned char* xh, unsigned char* xl
   *reinterpret_cast<float4*>(xl + off) = lo;
 }
 
-template <bool RES>
-__global__ void __launch_bounds__(NTHREADS, 1)
-    dense_tc_kernel(const DenseArgs a, const unsigned char* __restrict__ Tblk, int* err) {
+// RES: T of a 64-point axis resident (uniform plain passes); MANY: the work
+// list of a many-instance phase (every item streams its own T chunks).
+template <bool RES, bool MANY>
+__global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P) {
+  static_assert(!(RES && MANY), "many-instance launches stream T");
   using L = TcLayout<RES>;
   extern __shared__ __align__(1024) unsigned char tsm[];
   __shared__ __align__(8) uint64_t full_bar[TSTAGES], empty_bar[TSTAGES], copy_bar[TSTAGES];
@@ -149,15 +213,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const int mtiles = (2 * a.N + ROWS - 1) / ROWS;
-  const int kchunks = (2 * a.N) / TKC;
-  const int nb = a.acc ? (int)a.batch : 1;
-  const int64_t ctiles = (a.ncols + LINES - 1) / LINES;
-  const int64_t items = ctiles * mtiles;
+  int64_t items;
+  if (MANY) {
+    items = P.n_items;
+  } else {
+    const int mtiles = (2 * P.a.N + ROWS - 1) / ROWS;
+    items = ((P.a.ncols + LINES - 1) / LINES) * mtiles;
+  }
   if ((int64_t)blockIdx.x >= items) return;
   const int64_t my_items = (items - blockIdx.x + gridDim.x - 1) / gridDim.x;
-  const int64_t inner = a.inner;
-  const bool contiguous = (inner == 1);
 
   if (warp == MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -187,7 +251,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                 smem_u32(tsm + c * T_CHUNK)),
-            "l"(Tblk + (size_t)c * T_CHUNK), "r"(T_CHUNK), "r"(tb)
+            "l"(P.tblk + (size_t)c * T_CHUNK), "r"(T_CHUNK), "r"(tb)
             : "memory");
     }
   }
@@ -202,28 +266,30 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int t = tid;
     unsigned char* raw = tsm + L::RAW_OFF;  // RAW chunks of this thread's inputs
     unsigned char* graw = tsm + L::SMEM;    // and of its gradient factors (backward)
-    const int64_t total = my_items * nb * kchunks;     // chunks of this block, in order
     constexpr int RAW = L::RAW;
-    // issue side: chunk ci = (iit, ib, ikc), RAW - 1 ahead of the consumer
-    int64_t ci = 0, iit = 0;
+    // issue side: chunk (iit, ib, ikc), RAW - 1 ahead of the consumer
+    int64_t iit = 0, ci_issue = 0;
     int ib = 0, ikc = 0;
+    TcView iv = tc_view<MANY>(P, blockIdx.x);
+    int ikchunks = (2 * iv.N) / TKC;
     long long lb[2];
     int lbr[2];
     bool lines_ok = false;
     auto issue = [&]() {
-      if (ci < total) {
+      if (iit < my_items) {
+        const bool contiguous = (iv.inner == 1);
         if (!lines_ok) {
-          const int64_t ct = (blockIdx.x + iit * gridDim.x) / mtiles;
           if (contiguous) {
 #pragma unroll
             for (int j = 0; j < 2; ++j)
-              line_ref(a, ct * LINES + (t & 7) + 8 * (t >> 5) + 64 * j, ib, lb[j], lbr[j]);
+              line_ref(iv, iv.ct * LINES + (t & 7) + 8 * (t >> 5) + 64 * j, ib, lb[j], lbr[j]);
           } else {
-            line_ref(a, ct * LINES + (t & (LINES - 1)), ib, lb[0], lbr[0]);
+            line_ref(iv, iv.ct * LINES + (t & (LINES - 1)), ib, lb[0], lbr[0]);
           }
           lines_ok = true;
         }
-        const int slot = (int)(ci % RAW);
+        const int64_t inner = iv.inner;
+        const int slot = (int)(ci_issue % RAW);
         const uint32_t dst0 = smem_u32(raw + slot * RAW_CHUNK) + (uint32_t)t * 16;
         const uint32_t gdst0 = smem_u32(graw + slot * GRAD_CHUNK) + (uint32_t)t * 8;
 #pragma unroll
@@ -244,25 +310,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int64_t addr = valid ? lbi + (int64_t)(ikc * 16 + 2 * kp) * inner : 0;
           // invalid lines read nothing and land as zeros (source size 0)
           if (contiguous) {
-            cp_async16(dst, a.in + addr, valid ? 16 : 0);
+            cp_async16(dst, iv.in + addr, valid ? 16 : 0);
           } else {
-            cp_async8(dst, a.in + addr, valid ? 8 : 0);
-            cp_async8(dst + 8, a.in + addr + (valid ? inner : 0), valid ? 8 : 0);
+            cp_async8(dst, iv.in + addr, valid ? 8 : 0);
+            cp_async8(dst + 8, iv.in + addr + (valid ? inner : 0), valid ? 8 : 0);
           }
-          if (a.grad) {
-            const int64_t gaddr = valid && a.grad_shared ? addr - (int64_t)bri * a.M : addr;
+          if (iv.grad) {
+            const int64_t gaddr = valid && iv.grad_shared ? addr - (int64_t)bri * iv.M : addr;
             const uint32_t gdst = gdst0 + (uint32_t)(i * NPROD * 8);
-            cp_async4(gdst, a.grad + gaddr, valid ? 4 : 0);
-            cp_async4(gdst + 4, a.grad + gaddr + (valid ? inner : 0), valid ? 4 : 0);
+            cp_async4(gdst, iv.grad + gaddr, valid ? 4 : 0);
+            cp_async4(gdst + 4, iv.grad + gaddr + (valid ? inner : 0), valid ? 4 : 0);
           }
         }
-        ++ci;
-        if (++ikc == kchunks) {
+        ++ci_issue;
+        if (++ikc == ikchunks) {
           ikc = 0;
           lines_ok = false;
-          if (++ib == nb) {
+          if (++ib == iv.nb) {
             ib = 0;
-            ++iit;
+            if (++iit < my_items) {
+              iv = tc_view<MANY>(P, blockIdx.x + iit * gridDim.x);
+              ikchunks = (2 * iv.N) / TKC;
+            }
           }
         }
       }
@@ -270,15 +339,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     };
 #pragma unroll 1
     for (int r = 0; r < RAW - 1; ++r) issue();
-    // consumer side: chunk c = (it, kc) of the sequence
-    int64_t it = 0;
+    // consumer side: chunk c = (it, b, kc) of the sequence
     int b = 0, kc = 0;
-    int mt = (int)(blockIdx.x % mtiles);
+    TcView cv = tc_view<MANY>(P, blockIdx.x);
+    int kchunks = (2 * cv.N) / TKC;
     int last_u[TSTAGES];
 #pragma unroll
     for (int q = 0; q < TSTAGES; ++q) last_u[q] = -1;
+    int64_t c = 0;
 #pragma unroll 1
-    for (int64_t c = 0; c < total; ++c) {
+    for (int64_t it = 0; it < my_items;) {
       issue();
       asm volatile("cp.async.wait_group %0;" ::"n"(RAW - 1) : "memory");  // chunk c has landed
       const int s = (int)(c % TSTAGES);
@@ -287,10 +357,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       unsigned char* st = tsm + L::T_RES + s * L::STAGE;
       if (!RES && t == 0) {
         // the row block's rows that exist, head and tail parts
-        const uint32_t part = (uint32_t)row_count(a.N, mt) * (TKC * 4);
+        const uint32_t part = (uint32_t)row_count(cv.N, cv.mt) * (TKC * 4);
         const uint32_t cb = smem_u32(&copy_bar[s]);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cb), "r"(2 * part) : "memory");
-        const unsigned char* src = Tblk + ((size_t)mt * kchunks + kc) * T_CHUNK;
+        const unsigned char* src = cv.tblk + ((size_t)cv.mt * kchunks + kc) * T_CHUNK;
         bulk_g2s(smem_u32(st), src, part, cb);
         bulk_g2s(smem_u32(st + T_PART), src + T_PART, part, cb);
         last_u[s] = (int)(u & 1);
@@ -300,10 +370,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const unsigned char* gs = graw + slot * GRAD_CHUNK + t * 8;
       unsigned char* xh = st + L::X_OFF;
       unsigned char* xl = xh + X_PART;
+      const bool contiguous = (cv.inner == 1);
 #pragma unroll
       for (int i = 0; i < PITEMS; ++i) {
         float4 v = *reinterpret_cast<const float4*>(rs + i * NPROD * 16);
-        if (a.grad) {
+        if (cv.grad) {
           // the input element is 2 grad * psi
           const float2 gg = *reinterpret_cast<const float2*>(gs + i * NPROD * 8);
           v.x *= 2.f * gg.x;
@@ -323,12 +394,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(smem_u32(&full_bar[s]));
+      ++c;
       if (++kc == kchunks) {
         kc = 0;
-        if (++b == nb) {
+        if (++b == cv.nb) {
           b = 0;
-          ++it;
-          mt = (int)((blockIdx.x + it * gridDim.x) % mtiles);
+          if (++it < my_items) {
+            cv = tc_view<MANY>(P, blockIdx.x + it * gridDim.x);
+            kchunks = (2 * cv.N) / TKC;
+          }
         }
       }
     }
@@ -343,8 +417,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       int64_t g = 0, sub = 0;
       bool ok = !RES || mbar_wait(smem_u32(&tres_bar), 0u, &s_abort);  // resident T has landed
       for (int64_t it = 0; ok && it < my_items; ++it) {
-        const uint32_t idesc = idesc_tf32(LINES, row_count(a.N, (int)((blockIdx.x + it * gridDim.x) % mtiles)));
-        for (int b = 0; ok && b < nb; ++b, ++sub) {
+        const TcView mv = tc_view<MANY>(P, blockIdx.x + it * gridDim.x);
+        const int kchunks = (2 * mv.N) / TKC;
+        const uint32_t idesc = idesc_tf32(LINES, row_count(mv.N, mv.mt));
+        for (int b = 0; ok && b < mv.nb; ++b, ++sub) {
           const int buf = (int)(sub & 1);
           const int64_t v = sub >> 1;
           if (v >= 1 && !mbar_wait(smem_u32(&acce_bar[buf]), (uint32_t)((v - 1) & 1), &s_abort)) {
@@ -391,19 +467,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ---------------- epilogue ----------------
     const int q = warp & 3;          // tensor-memory lane quarter this warp may read
     const int r = q * 32 + lane;     // line within the item
-    const int64_t M = a.M;
     float* racc = reinterpret_cast<float*>(tsm + L::SMEM);  // accumulating launches only
-    if (a.acc)
+    if (!MANY && P.a.acc)
       for (int m = 0; m < ROWS / 2; ++m) racc[m * LINES + r] = 0.f;
     int64_t sub = 0;
     bool ok = true;
     for (int64_t it = 0; ok && it < my_items; ++it) {
-      const int64_t w = blockIdx.x + it * gridDim.x;
-      const int mt = (int)(w % mtiles);
-      const int64_t ct = w / mtiles;
-      const int nbase = mt * (ROWS / 2);
-      const int rows = row_count(a.N, mt);  // real rows of this item
-      for (int b = 0; b < nb; ++b, ++sub) {
+      const TcView ev = tc_view<MANY>(P, blockIdx.x + it * gridDim.x);
+      const int64_t inner = ev.inner;
+      const bool contiguous = (inner == 1);
+      const int nbase = ev.mt * (ROWS / 2);
+      const int rows = row_count(ev.N, ev.mt);  // real rows of this item
+      for (int b = 0; b < ev.nb; ++b, ++sub) {
         const int buf = (int)(sub & 1);
         const int64_t v = sub >> 1;
         // warp-uniform outcome: the tensor-memory loads below need the whole warp
@@ -412,7 +487,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         long long base;
         int br;
-        line_ref(a, ct * LINES + r, b, base, br);
+        line_ref(ev, ev.ct * LINES + r, b, base, br);
         const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * ROWS);
 #pragma unroll 1
         for (int j0 = 0; j0 < rows; j0 += 16) {
@@ -424,44 +499,44 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
           for (int m = 0; m < 16; ++m) y[m] = __uint_as_float(x[m]) + __uint_as_float(z[m]);
           const int n0 = nbase + j0 / 2;  // complex outputs n0 .. n0 + 7 of this line
-          if (a.acc) {
+          if (ev.acc) {
 #pragma unroll
             for (int m = 0; m < 8; ++m)
               racc[(j0 / 2 + m) * LINES + r] += y[2 * m] * y[2 * m] + y[2 * m + 1] * y[2 * m + 1];
           } else if (base >= 0) {
-            if (a.out_c) {
+            if (ev.out_c) {
               if (contiguous) {
-                float4* o = reinterpret_cast<float4*>(a.out_c + base + n0);
+                float4* o = reinterpret_cast<float4*>(ev.out_c + base + n0);
 #pragma unroll
                 for (int m = 0; m < 4; ++m) o[m] = make_float4(y[4 * m], y[4 * m + 1], y[4 * m + 2], y[4 * m + 3]);
               } else {
 #pragma unroll
                 for (int m = 0; m < 8; ++m)
-                  a.out_c[base + (int64_t)(n0 + m) * inner] = make_float2(y[2 * m], y[2 * m + 1]);
+                  ev.out_c[base + (int64_t)(n0 + m) * inner] = make_float2(y[2 * m], y[2 * m + 1]);
               }
             } else {
               float dd[8];
 #pragma unroll
               for (int m = 0; m < 8; ++m) dd[m] = y[2 * m] * y[2 * m] + y[2 * m + 1] * y[2 * m + 1];
               if (contiguous) {
-                float4* o = reinterpret_cast<float4*>(a.out_d + base + n0);
+                float4* o = reinterpret_cast<float4*>(ev.out_d + base + n0);
                 o[0] = make_float4(dd[0], dd[1], dd[2], dd[3]);
                 o[1] = make_float4(dd[4], dd[5], dd[6], dd[7]);
               } else {
 #pragma unroll
-                for (int m = 0; m < 8; ++m) a.out_d[base + (int64_t)(n0 + m) * inner] = dd[m];
+                for (int m = 0; m < 8; ++m) ev.out_d[base + (int64_t)(n0 + m) * inner] = dd[m];
               }
             }
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         mbar_arrive(smem_u32(&acce_bar[buf]));
-        if (a.acc && b == nb - 1) {
+        if (ev.acc && b == ev.nb - 1) {
           if (base >= 0) {
-            const int64_t o0 = base - (int64_t)br * M + (int64_t)nbase * inner;
+            const int64_t o0 = base - (int64_t)br * ev.M + (int64_t)nbase * inner;
             if (contiguous) {
-              float4* o = reinterpret_cast<float4*>(a.out_d + o0);
-#pragma unroll
+              float4* o = reinterpret_cast<float4*>(ev.out_d + o0);
+#pragma unroll 1
               for (int m = 0; m < rows / 8; ++m) {
                 float4 cur = o[m];
                 cur.x += racc[(4 * m) * LINES + r];
@@ -471,8 +546,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 o[m] = cur;
               }
             } else {
-#pragma unroll
-              for (int m = 0; m < rows / 2; ++m) a.out_d[o0 + (int64_t)m * inner] += racc[m * LINES + r];
+#pragma unroll 1
+              for (int m = 0; m < rows / 2; ++m) ev.out_d[o0 + (int64_t)m * inner] += racc[m * LINES + r];
             }
           }
           for (int m = 0; m < ROWS / 2; ++m) racc[m * LINES + r] = 0.f;
@@ -485,7 +560,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (RES && tid == 0) mbar_wait_own(smem_u32(&tres_bar), 0u, &s_abort);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (tid == 0 && s_abort) atomicAdd(err, 1);
+  if (tid == 0 && s_abort) atomicAdd(P.err, 1);
   if (warp == MMA_WARP) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ACC_COLS) : "memory");
@@ -525,10 +600,10 @@ __global__ void tc_build_t_kernel(const float2* __restrict__ T, unsigned char* _
 
 bool dense_tc_supported(int N) { return N >= 32 && N <= kDenseMaxN && N % 16 == 0; }
 cudaError_t dense_tc_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(dense_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(dense_tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        TcLayout<false>::SMEM + EXTRA_SMEM);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(dense_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(dense_tc_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              TcLayout<true>::SMEM);
   return e;
 }
@@ -538,12 +613,17 @@ size_t dense_tc_t_bytes(int N) {
 
 cudaError_t launch_dense_tc(const DenseArgs& a, const unsigned char* Tblk, int* err, int grid,
                             cudaStream_t stream) {
+  TcParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.a = a;
+  P.tblk = Tblk;
+  P.err = err;
   if (a.N == 64 && !a.acc && !a.grad) {
     // T (128 KB) stays in shared memory for the whole launch
-    dense_tc_kernel<true><<<grid, NTHREADS, TcLayout<true>::SMEM, stream>>>(a, Tblk, err);
+    dense_tc_kernel<true, false><<<grid, NTHREADS, TcLayout<true>::SMEM, stream>>>(P);
   } else {
     const int smem = TcLayout<false>::SMEM + ((a.acc || a.grad) ? EXTRA_SMEM : 0);
-    dense_tc_kernel<false><<<grid, NTHREADS, smem, stream>>>(a, Tblk, err);
+    dense_tc_kernel<false, false><<<grid, NTHREADS, smem, stream>>>(P);
   }
   return cudaGetLastError();
 }
@@ -556,5 +636,17 @@ cudaError_t launch_tc_build_t(const float2* T, unsigned char* Tblk, int N, cudaS
   tc_build_t_kernel<<<256, 256, 0, s>>>(T, Tblk, N);
   return cudaGetLastError();
 }
+
+// ---- many-instance phases ----
+
+const void* many_tc_func() { return (const void*)dense_tc_kernel<false, true>; }
+int many_tc_threads() { return NTHREADS; }
+size_t many_tc_smem() { return (size_t)TcLayout<false>::SMEM + EXTRA_SMEM; }
+cudaError_t many_tc_prepare() {
+  return cudaFuncSetAttribute(dense_tc_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)many_tc_smem());
+}
+int many_tc_lines() { return LINES; }
+int many_tc_row_blocks(int N) { return (2 * N + ROWS - 1) / ROWS; }
 
 }  // namespace ffx

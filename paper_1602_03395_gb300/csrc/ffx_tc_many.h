@@ -1,0 +1,51 @@
+// Many-instance phases on the tensor cores: the work list of one phase for
+// the split-TF32 dense kernel of ffx_tc.cu (the pass of every instance's k-th
+// axis, cut into items of 128 lines x 128 real output rows).
+#pragma once
+
+#include "ffx_internal.h"
+
+namespace ffx {
+
+// One instance pass: the dense pass arguments with byte offsets in place of
+// pointers (rebased per call on the bases below; -1 = unused) and the pass's
+// split operand blocks (launch_tc_build_t layout).
+struct TcPassArg {
+  DenseArgs d;
+  const unsigned char* tblk;
+  int in_base, outc_base, outd_base, grad_base;
+};
+
+// One work item: line tile ct (128 lines) and row block mt of pass `arg`.
+struct TcItem {
+  long long ct;
+  int arg, mt;
+};
+
+constexpr int kTcBases = 8;
+struct TcBases {
+  const void* base[kTcBases];
+};
+
+// Kernel parameters.  Uniform launches: the pass `a` with operand blocks
+// `tblk`, items (line tile, row block) numbered row block fastest.
+// Many-instance launches: `items` over the passes `args`.  `err` counts
+// launches that gave up on a bounded wait.
+struct TcParams {
+  DenseArgs a;
+  const unsigned char* tblk;
+  const TcPassArg* args;
+  const TcItem* items;
+  long long n_items;
+  TcBases call;
+  int* err;
+};
+
+const void* many_tc_func();   // kernel(const TcParams), many-instance variant
+int many_tc_threads();
+size_t many_tc_smem();        // dynamic shared memory (with the gradient ring)
+cudaError_t many_tc_prepare();
+int many_tc_lines();          // lines per item
+int many_tc_row_blocks(int N);
+
+}  // namespace ffx

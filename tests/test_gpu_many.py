@@ -52,6 +52,61 @@ def test_many_mixed_shapes_against_oracle(form):
     assert worst_d < DENSITY_TOL and worst_f < FIELD_TOL
 
 
+TC_DIMS = [(48, 32, 32), (32, 32), (96,), (64, 128, 32), (64, 48, 32), (192, 32)]
+
+
+def test_many_tc_against_oracle():
+    """Tensor-core phases (split TF32): every line length a multiple of 16
+    from 32, narrower last row blocks (48, 96, 192), strided and contiguous
+    axes, 1-D to 3-D instances."""
+    ffx = require_gpu()
+    specs, psis = mixed_specs(9, dims_override=TC_DIMS)
+    plan = ffx.PlanMany(specs, form="tc")
+    assert plan.form == "tc"
+    x = to_dev(pack(plan, psis))
+    rho = ffx.ffx_expand(plan, x).cpu().numpy()
+    field = ffx.ffx_expand_field(plan, x).cpu().numpy()
+    assert plan.device_errors() == 0
+    worst_d = worst_f = 0.0
+    for (dims, dx, t, lam), p, off in zip(specs, psis, plan.offsets):
+        ref = O.expand_field(p, dx, t, lam)
+        m = p.size
+        worst_d = max(worst_d, rel_l2(rho[off:off + m].reshape(dims), np.abs(ref) ** 2))
+        worst_f = max(worst_f, rel_l2(field[off:off + m].reshape(dims), ref))
+    plan.close()
+    print(f"many (tc): worst density {worst_d:.2e}, worst field {worst_f:.2e}")
+    assert worst_d < DENSITY_TOL and worst_f < FIELD_TOL
+
+
+def test_many_tc_backward_against_oracle():
+    ffx = require_gpu()
+    specs, psis = mixed_specs(5, dims_override=[(32, 48), (48, 32, 32), (64,), (96, 32), (128, 32)])
+    plan = ffx.PlanMany(specs, form="tc")
+    assert plan.form == "tc"
+    rng = np.random.default_rng(8)
+    grads = [rng.normal(size=p.shape).astype(np.float32) for p in psis]
+    g = np.zeros(plan.points, np.float32)
+    for off, gr in zip(plan.offsets, grads):
+        g[off:off + gr.size] = gr.ravel()
+    got = ffx.ffx_expand_backward(plan, to_dev(pack(plan, psis)), to_dev(g)).cpu().numpy()
+    assert plan.device_errors() == 0
+    worst = 0.0
+    for (dims, dx, t, lam), p, gr, off in zip(specs, psis, grads, plan.offsets):
+        ref = O.density_loss_gradient(p, gr, dx, t, lam)
+        worst = max(worst, rel_l2(got[off:off + p.size].reshape(dims), ref))
+    plan.close()
+    print(f"many backward (tc): worst {worst:.2e}")
+    assert worst < FIELD_TOL
+
+
+def test_many_tc_falls_back_for_16_point_lines():
+    """A 16-point axis has no tensor-core tile: the tc form keeps the FP32
+    dense phases for the whole plan."""
+    ffx = require_gpu()
+    with ffx.PlanMany([((16, 32), (0.2, 0.2), 3.0, (5, 5)), ((64,), (0.1,), 2.0, (9,))], form="tc") as plan:
+        assert plan.form == "dense"
+
+
 def test_many_workload_shapes_match_single_plans_and_replay():
     """Instances of the mixed-batch workload (48^3, 64^3, 96^3, 128x32x32) with
     moderate lam: each equals its own single-lattice plan; a second call with
@@ -103,17 +158,19 @@ def test_many_rejects_unsupported():
     assert ei.value.code == ffx.FFX_EUNSUPPORTED
 
 
-def test_many_dense_auto_on_the_mixed_workload():
+@pytest.mark.parametrize("form", ["auto", "dense"])
+def test_many_dense_auto_on_the_mixed_workload(form):
     """The mixed-batch workload's magnifications (10..100) make the dense maps
-    cheaper than the fold form on every axis: the automatic form takes them;
+    cheaper than the fold form on every axis: the automatic form takes them,
+    on the tensor cores (every line length is a multiple of 16 from 32);
     instances against the oracle, field in place, and a replay with new
     buffers."""
     ffx = require_gpu()
     ws = inputs.config_mixed_batch(count=6)
     specs = [(w.dims, w.dx, w.t, w.lam) for w in ws]
     psis = [w.realization(0) for w in ws]
-    plan = ffx.PlanMany(specs)
-    assert plan.form == "dense"
+    plan = ffx.PlanMany(specs, form=form)
+    assert plan.form == ("tc" if form == "auto" else "dense")
     x = to_dev(pack(plan, psis))
     rho = ffx.ffx_expand(plan, x).cpu().numpy()
     y = x.clone()
@@ -126,8 +183,9 @@ def test_many_dense_auto_on_the_mixed_workload():
         worst_d = max(worst_d, rel_l2(rho[off:off + m].reshape(dims), np.abs(ref) ** 2))
         worst_f = max(worst_f, rel_l2(field[off:off + m].reshape(dims), ref))
     r2 = ffx.ffx_expand(plan, x.clone()).cpu().numpy()
+    assert plan.device_errors() == 0
     plan.close()
-    print(f"many dense (auto) on the workload: worst density {worst_d:.2e}, field {worst_f:.2e}")
+    print(f"many {plan.form} ({form}) on the workload: worst density {worst_d:.2e}, field {worst_f:.2e}")
     assert worst_d < DENSITY_TOL and worst_f < FIELD_TOL
     assert np.array_equal(r2, rho)
 
