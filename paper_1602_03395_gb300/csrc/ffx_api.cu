@@ -241,8 +241,10 @@ bool tc_capable(const Axis& ax) { return dense_tc_supported(ax.N) && ax.tc_t[0] 
 
 // The dense map's kernel for a pass over `lines` lines: FFX_FORM_TC or
 // FFX_FORM_DENSE.  An axis the plan's automatic choice gave the FP32 dense form
-// moves to the tensor cores when the pass fills every SM with 128-line tiles
-// (small passes are latency-bound there); explicit forms keep their kernel.
+// moves to the tensor cores when the pass leaves the few-lines kernel and
+// either its lines have at least 96 points (the FP32 tile kernel's K loop is
+// the slower one there, measured down to a single 128-line tile) or it has at
+// least 64 tensor-core items; explicit forms keep their kernel.
 int dense_kernel_for(const ffx_plan_s* p, const Axis& ax, int64_t lines);
 
 // The tensor-core kernel moves 16-byte vectors; other pointers take the SIMT dense kernels.
@@ -424,7 +426,7 @@ int chain_into(ffx_plan_s* p, const int* axes, bool adjoint, const float2* in, c
 int dense_kernel_for(const ffx_plan_s* p, const Axis& ax, int64_t lines) {
   if (ax.form == FFX_FORM_TC) return tc_capable(ax) ? FFX_FORM_TC : FFX_FORM_DENSE;
   if (ax.form == FFX_FORM_DENSE && (p->flags & FFX_FORM_MASK) == FFX_FORM_AUTO && tc_capable(ax) &&
-      lines >= 128 * (int64_t)p->sms)
+      lines >= kDenseFewLines && (ax.N >= 96 || dense_tc_tiles(ax.N, lines) >= 64))
     return FFX_FORM_TC;
   return ax.form;
 }
@@ -455,6 +457,16 @@ int plan_fusion(ffx_plan_s* p) {
   // that the per-axis kernels (several blocks per SM) keep the ALUs busier.
   const int64_t tiles = (p->M / Ns[0] + 31) / 32;
   p->fused = std::max<int64_t>(1, 2 * (int64_t)p->sms / tiles);
+  // nor past the batch whose per-axis passes all move to the tensor cores
+  for (int64_t b = 2; b <= p->fused; ++b) {
+    bool all_tc = true;
+    for (int k = 0; k < p->ndim; ++k)
+      all_tc = all_tc && dense_kernel_for(p, p->axis[p->order[k]], b * (p->M / Ns[k])) == FFX_FORM_TC;
+    if (all_tc) {
+      p->fused = b - 1;
+      break;
+    }
+  }
   p->fused_grid = p->sms;  // one block per SM (every block is resident: cooperative launch)
   p->fused_smem_bytes = smem;
   // Every axis 64 points with its tensor-core slices, and a form that allows

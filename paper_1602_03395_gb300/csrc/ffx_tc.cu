@@ -163,6 +163,19 @@ __device__ __forceinline__ TcView tc_view(const TcParams& P, int64_t w) {
   return v;
 }
 
+// Item w of a launch: a new view for many-instance launches; uniform launches
+// keep the pass (so its fields stay loop-invariant) and move the item only.
+template <bool MANY>
+__device__ __forceinline__ void tc_next(const TcParams& P, int64_t w, TcView& v) {
+  if (MANY) {
+    v = tc_view<true>(P, w);
+  } else {
+    const int mtiles = (2 * P.a.N + ROWS - 1) / ROWS;
+    v.ct = w / mtiles;
+    v.mt = (int)(w % mtiles);
+  }
+}
+
 // Line c of the pass (realization b of the batch when accumulating): offset
 // of its first point, or -1 past the end; br = its realization.
 __device__ __forceinline__ void line_ref(const TcView& a, int64_t c, int b, long long& base, int& br) {
@@ -201,9 +214,11 @@ __device__ __forceinline__ void split_store(unsigned char* xh, unsigned char* xl
 
 // RES: T of a 64-point axis resident (uniform plain passes); MANY: the work
 // list of a many-instance phase (every item streams its own T chunks).
-template <bool RES, bool MANY>
+// FULL: every row block has ROWS rows (uniform launches with 2N a multiple of
+// 128), so the row count, MMA shape and T copy are constants.
+template <bool RES, bool MANY, bool FULL>
 __global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P) {
-  static_assert(!(RES && MANY), "many-instance launches stream T");
+  static_assert(!(RES && MANY) && !(MANY && FULL), "many-instance launches stream T, rows vary");
   using L = TcLayout<RES>;
   extern __shared__ __align__(1024) unsigned char tsm[];
   __shared__ __align__(8) uint64_t full_bar[TSTAGES], empty_bar[TSTAGES], copy_bar[TSTAGES];
@@ -329,7 +344,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P)
           if (++ib == iv.nb) {
             ib = 0;
             if (++iit < my_items) {
-              iv = tc_view<MANY>(P, blockIdx.x + iit * gridDim.x);
+              tc_next<MANY>(P, blockIdx.x + iit * gridDim.x, iv);
               ikchunks = (2 * iv.N) / TKC;
             }
           }
@@ -357,12 +372,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P)
       unsigned char* st = tsm + L::T_RES + s * L::STAGE;
       if (!RES && t == 0) {
         // the row block's rows that exist, head and tail parts
-        const uint32_t part = (uint32_t)row_count(cv.N, cv.mt) * (TKC * 4);
+        const uint32_t part = (uint32_t)(FULL ? ROWS : row_count(cv.N, cv.mt)) * (TKC * 4);
         const uint32_t cb = smem_u32(&copy_bar[s]);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cb), "r"(2 * part) : "memory");
         const unsigned char* src = cv.tblk + ((size_t)cv.mt * kchunks + kc) * T_CHUNK;
-        bulk_g2s(smem_u32(st), src, part, cb);
-        bulk_g2s(smem_u32(st + T_PART), src + T_PART, part, cb);
+        if (part == (uint32_t)T_PART) {
+          bulk_g2s(smem_u32(st), src, T_CHUNK, cb);  // a whole row block: head and tail in one copy
+        } else {
+          bulk_g2s(smem_u32(st), src, part, cb);
+          bulk_g2s(smem_u32(st + T_PART), src + T_PART, part, cb);
+        }
         last_u[s] = (int)(u & 1);
       }
       const int slot = (int)(c % RAW);
@@ -400,7 +419,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P)
         if (++b == cv.nb) {
           b = 0;
           if (++it < my_items) {
-            cv = tc_view<MANY>(P, blockIdx.x + it * gridDim.x);
+            tc_next<MANY>(P, blockIdx.x + it * gridDim.x, cv);
             kchunks = (2 * cv.N) / TKC;
           }
         }
@@ -416,10 +435,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P)
     if (lane == 0) {
       int64_t g = 0, sub = 0;
       bool ok = !RES || mbar_wait(smem_u32(&tres_bar), 0u, &s_abort);  // resident T has landed
+      TcView mv = tc_view<MANY>(P, blockIdx.x);
       for (int64_t it = 0; ok && it < my_items; ++it) {
-        const TcView mv = tc_view<MANY>(P, blockIdx.x + it * gridDim.x);
+        if (it > 0) tc_next<MANY>(P, blockIdx.x + it * gridDim.x, mv);
         const int kchunks = (2 * mv.N) / TKC;
-        const uint32_t idesc = idesc_tf32(LINES, row_count(mv.N, mv.mt));
+        const uint32_t idesc = idesc_tf32(LINES, FULL ? ROWS : row_count(mv.N, mv.mt));
         for (int b = 0; ok && b < mv.nb; ++b, ++sub) {
           const int buf = (int)(sub & 1);
           const int64_t v = sub >> 1;
@@ -472,12 +492,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P)
       for (int m = 0; m < ROWS / 2; ++m) racc[m * LINES + r] = 0.f;
     int64_t sub = 0;
     bool ok = true;
+    TcView ev = tc_view<MANY>(P, blockIdx.x);
     for (int64_t it = 0; ok && it < my_items; ++it) {
-      const TcView ev = tc_view<MANY>(P, blockIdx.x + it * gridDim.x);
+      if (it > 0) tc_next<MANY>(P, blockIdx.x + it * gridDim.x, ev);
       const int64_t inner = ev.inner;
       const bool contiguous = (inner == 1);
       const int nbase = ev.mt * (ROWS / 2);
-      const int rows = row_count(ev.N, ev.mt);  // real rows of this item
+      const int rows = FULL ? ROWS : row_count(ev.N, ev.mt);  // real rows of this item
       for (int b = 0; b < ev.nb; ++b, ++sub) {
         const int buf = (int)(sub & 1);
         const int64_t v = sub >> 1;
@@ -600,10 +621,13 @@ __global__ void tc_build_t_kernel(const float2* __restrict__ T, unsigned char* _
 
 bool dense_tc_supported(int N) { return N >= 32 && N <= kDenseMaxN && N % 16 == 0; }
 cudaError_t dense_tc_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(dense_tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       TcLayout<false>::SMEM + EXTRA_SMEM);
+  cudaError_t e = cudaFuncSetAttribute(dense_tc_kernel<false, false, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, TcLayout<false>::SMEM + EXTRA_SMEM);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(dense_tc_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(dense_tc_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TcLayout<false>::SMEM + EXTRA_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(dense_tc_kernel<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              TcLayout<true>::SMEM);
   return e;
 }
@@ -620,10 +644,13 @@ cudaError_t launch_dense_tc(const DenseArgs& a, const unsigned char* Tblk, int* 
   P.err = err;
   if (a.N == 64 && !a.acc && !a.grad) {
     // T (128 KB) stays in shared memory for the whole launch
-    dense_tc_kernel<true, false><<<grid, NTHREADS, TcLayout<true>::SMEM, stream>>>(P);
+    dense_tc_kernel<true, false, true><<<grid, NTHREADS, TcLayout<true>::SMEM, stream>>>(P);
   } else {
     const int smem = TcLayout<false>::SMEM + ((a.acc || a.grad) ? EXTRA_SMEM : 0);
-    dense_tc_kernel<false, false><<<grid, NTHREADS, smem, stream>>>(P);
+    if ((2 * a.N) % ROWS == 0)
+      dense_tc_kernel<false, false, true><<<grid, NTHREADS, smem, stream>>>(P);
+    else
+      dense_tc_kernel<false, false, false><<<grid, NTHREADS, smem, stream>>>(P);
   }
   return cudaGetLastError();
 }
@@ -639,11 +666,11 @@ cudaError_t launch_tc_build_t(const float2* T, unsigned char* Tblk, int N, cudaS
 
 // ---- many-instance phases ----
 
-const void* many_tc_func() { return (const void*)dense_tc_kernel<false, true>; }
+const void* many_tc_func() { return (const void*)dense_tc_kernel<false, true, false>; }
 int many_tc_threads() { return NTHREADS; }
 size_t many_tc_smem() { return (size_t)TcLayout<false>::SMEM + EXTRA_SMEM; }
 cudaError_t many_tc_prepare() {
-  return cudaFuncSetAttribute(dense_tc_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(dense_tc_kernel<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)many_tc_smem());
 }
 int many_tc_lines() { return LINES; }

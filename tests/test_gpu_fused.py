@@ -83,8 +83,8 @@ def test_fusion_applies_only_to_short_dense_axes(ffx):
         assert not p4.fused
 
 
-@pytest.mark.parametrize("dims,lam,batch", [((64, 64, 64), (30, 30, 3), 1), ((64, 64, 64), (30, 30, 3), 2),
-                                            ((64, 64), (7, 5), 3)])
+@pytest.mark.parametrize("dims,lam,batch", [((64, 64, 64), (30, 30, 3), 1), ((64, 64), (7, 5), 3),
+                                            ((64, 64), (7, 5), 8)])
 def test_fused_tensor_core_launch(ffx, dims, lam, batch):
     """Axes of 64 points under the automatic form: the fused launch on the
     tensor cores (split TF32), against the oracle; fields, densities, the

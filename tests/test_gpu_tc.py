@@ -113,6 +113,26 @@ def test_tc_accumulate_and_backward_long_axes(ffx, dims, lam):
     assert e1 < DENSITY_TOL and e2 < FIELD_TOL and e3 < FIELD_TOL
 
 
+@pytest.mark.parametrize("dims,lam,batch,forms", [
+    ((96, 96, 96), (10, 10, 10), 1, ("tc",) * 3),       # lines of 96 points: tensor cores from one tile
+    ((48, 48, 48), (20, 20, 20), 2, ("dense",) * 3),    # 36 items per pass: FP32
+    ((48, 48, 48), (20, 20, 20), 4, ("tc",) * 3),       # 72 items: tensor cores
+    ((1024,), (9,), 40, ("tc",)),                       # 40 lines of 1024 points
+    ((1024,), (9,), 31, ("dense",)),                    # 31 lines: the few-lines kernel
+])
+def test_auto_per_call_kernel_choice(ffx, dims, lam, batch, forms):
+    rng = np.random.default_rng(sum(dims) + batch)
+    dx, t = (0.25,) * len(dims), 10.0
+    psi = random_field(rng, (batch,) + dims)
+    with ffx.Plan(dims, dx, t, lam, fused=False) as plan:
+        assert plan.call_forms(batch) == forms
+        rho = ffx.ffx_expand(plan, to_dev(psi)).cpu().numpy()
+        assert plan.device_errors() == 0
+    e = rel_l2(rho, np.abs(O.expand_field(psi, dx, t, lam)) ** 2)
+    print(f"auto {dims} x{batch} {forms}: density {e:.2e}")
+    assert e < DENSITY_TOL
+
+
 def test_tc_unaligned_buffers_take_the_simt_kernel(ffx):
     """A field that starts 8 bytes past a 16-byte boundary is still expanded
     correctly (those passes run on the FP32 SIMT dense kernels)."""
@@ -136,7 +156,9 @@ def test_auto_moves_large_dense_passes_to_tensor_cores(ffx):
     ref = np.abs(O.expand_field(psi, w.dx, w.t, w.lam)) ** 2
     with ffx.Plan(w.dims, w.dx, w.t, w.lam) as plan:
         assert plan.axis_forms == ("dense",) * 3
-        assert plan.call_forms(1) == ("tc",) * 3     # small calls: the fused launch, on the tensor cores
+        assert plan.call_forms(1) == ("tc",) * 3     # batch 1: the fused launch, on the tensor cores
+        assert plan.fused_max_batch == 1             # from batch 2 every pass has 64 tensor-core items
+        assert plan.launches_per_call(batch=2) == 3
         assert plan.call_forms(6) == ("tc",) * 3     # 6 x 4096 lines per pass: tensor cores
         rho = ffx.ffx_expand(plan, to_dev(psi)).cpu().numpy()
         one = ffx.ffx_expand(plan, to_dev(psi[:1])).cpu().numpy()
