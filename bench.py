@@ -290,6 +290,46 @@ def scipy_baseline(w, budget_s=8.0, dtype=np.complex64):
             "sample": f"{n} realizations in {dt:.1f} s"}
 
 
+def pipelined_e2e(torch, dev, plans, call, h_in, d_in, d_out, h_out, steps):
+    """End-to-end milliseconds for `steps` steps, each copying its input from
+    pinned host memory (h_in[i % len(h_in)]), expanding it through the C ABI
+    and copying the densities back to pinned host memory.  Steps alternate
+    between len(plans) lanes (stream, plan, device and host buffers), so with
+    two lanes one step's copies overlap the other lane's expansion, as a
+    streaming caller runs it; every step still moves its own bytes both ways."""
+    main = torch.cuda.current_stream(dev)
+    lanes = [torch.cuda.Stream(dev) for _ in plans]
+    for k, st in enumerate(lanes):  # warm each lane
+        with torch.cuda.stream(st):
+            d_in[k].copy_(h_in[k % len(h_in)], non_blocking=True)
+            call(plans[k], d_in[k], d_out[k])
+            h_out[k].copy_(d_out[k], non_blocking=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(main)
+    for st in lanes:
+        st.wait_event(e0)
+    if len(lanes) == 1:
+        with torch.cuda.stream(lanes[0]):
+            for i in range(steps):
+                d_in[0].copy_(h_in[i % len(h_in)], non_blocking=True)
+                call(plans[0], d_in[0], d_out[0])
+                h_out[0].copy_(d_out[0], non_blocking=True)
+    else:
+        for i in range(steps):
+            k = i % len(lanes)
+            with torch.cuda.stream(lanes[k]):
+                d_in[k].copy_(h_in[i % len(h_in)], non_blocking=True)
+                call(plans[k], d_in[k], d_out[k])
+                h_out[k].copy_(d_out[k], non_blocking=True)
+    for st in lanes:
+        main.wait_stream(st)
+    e1.record(main)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
 def load_traffic(kernel_key: str):
     """Per-launch DRAM bytes of the dominant kernel from the committed ncu
     summary, if it was taken on the kernel's current sources (the files the
@@ -405,23 +445,16 @@ def run_mixed(args, torch, dist, world, rank, dev):
                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({pk_src})"}
     byts = sum(int(np.prod(d)) * (8 + 16 * (len(d) - 1) + 4) for d, _, _, _ in specs)
     hbm_peak = float(pk.get("hbm_gbs", 6800.0))
-    # end to end: pinned host input -> expand -> pinned host densities
+    # end to end: pinned host input -> expand -> pinned host densities, two lanes
     hx = x.cpu().pin_memory()
-    ho = torch.empty(plan.points, dtype=torch.float32).pin_memory()
-    dx_ = torch.empty_like(x)
-    steps_e2e = max(1, min(args.steps, 20))
-    dx_.copy_(hx, non_blocking=True)
-    ffx.ffx_expand(plan, dx_, out)
-    ho.copy_(out, non_blocking=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(steps_e2e):
-        dx_.copy_(hx, non_blocking=True)
-        ffx.ffx_expand(plan, dx_, out)
-        ho.copy_(out, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
+    plan2 = ffx.PlanMany(specs, form=args.form)
+    steps_e2e = max(2, min(args.steps, 20))
+    e2e_ms = pipelined_e2e(torch, dev, [plan, plan2], lambda pl, a, o: ffx.ffx_expand(pl, a, o), [hx],
+                           [torch.empty_like(x) for _ in range(2)], [out, torch.empty_like(out)],
+                           [torch.empty(plan.points, dtype=torch.float32).pin_memory() for _ in range(2)],
+                           steps_e2e)
+    lanes_used = 2
+    plan2.close()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -438,7 +471,7 @@ def run_mixed(args, torch, dist, world, rank, dev):
             "roofline_hbm": {"bound": "hbm", "achieved": byts / (ms / args.steps * 1e-3) / 1e9,
                              "peak": hbm_peak, "unit": "GB/s",
                              "frac": byts / (ms / args.steps * 1e-3) / 1e9 / hbm_peak},
-            "e2e": {"value": steps_e2e * count * world / (e2e_ms * 1e-3), "unit": UNIT,
+            "e2e": {"value": steps_e2e * count * world / (e2e_ms * 1e-3), "unit": UNIT, "lanes": lanes_used,
                     "h2d_bytes_per_step": plan.points * 8, "d2h_bytes_per_step": plan.points * 4},
             "cpu_baseline": None,
         }
@@ -633,26 +666,25 @@ def run_ffx(args):
     value = args.steps * B_ * world / (ms * 1e-3)
 
     # end to end through the C ABI with host buffers: pinned H2D, expand, D2H
-    h_in = [distinct[i % 4].pin_memory() for i in range(4)]
-    h_out = torch.empty(out_shape, dtype=torch.float32).pin_memory()
-    d_in = torch.empty_like(pool_in[0])
-    d_out = torch.empty(out_shape, dtype=torch.float32, device=dev)
-    for i in range(3):
-        d_in.copy_(h_in[i % 4], non_blocking=True)
-        call(d_in, d_out)
-        h_out.copy_(d_out, non_blocking=True)
-    torch.cuda.synchronize()
-    e2e_steps = args.steps
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for i in range(e2e_steps):
-        d_in.copy_(h_in[i % 4], non_blocking=True)
-        call(d_in, d_out)
-        h_out.copy_(d_out, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
+    # per step, two lanes (see pipelined_e2e)
+    plan2 = ffx.Plan(w.dims, w.dx, w.t, w.lam, form=args.form)
+    if args.column is None:
+        def call_pl(pl, x, out):
+            return ffx.ffx_expand(pl, x, out)
+    else:
+        def call_pl(pl, x, out):
+            return ffx.ffx_expand_column(pl, x, args.column, out)
+    e2e_steps = max(2, args.steps)
+    h_in = [distinct[i].pin_memory() for i in range(4)]
+    d_in = [torch.empty_like(pool_in[0]) for _ in range(2)]
+    d_out = [torch.empty(out_shape, dtype=torch.float32, device=dev) for _ in range(2)]
+    h_out = [torch.empty(out_shape, dtype=torch.float32).pin_memory() for _ in range(2)]
+    # one lane (host-bound small steps) and two lanes (copy-bound large steps): the faster
+    e2e_lanes = {n: pipelined_e2e(torch, dev, [plan, plan2][:n], call_pl, h_in, d_in, d_out, h_out, e2e_steps)
+                 for n in (1, 2)}
+    lanes_used = min(e2e_lanes, key=e2e_lanes.get)
+    e2e_ms = e2e_lanes[lanes_used]
+    plan2.close()
     if world > 1:
         tt = torch.tensor([e2e_ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -723,7 +755,7 @@ def run_ffx(args):
                              "frac": bytes_launch / (mean_ms[dom] * 1e-3) / 1e9 / hbm_peak,
                              "note": f"of {pk_src} hbm_gbs; one read + one write of the batch"},
             "pass_ms": {pass_names[k]: mean_ms[k] for k in range(launches)},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B_ * M * 8,
+            "e2e": {"value": e2e_value, "unit": UNIT, "lanes": lanes_used, "h2d_bytes_per_step": B_ * M * 8,
                     "d2h_bytes_per_step": out_bytes},
             "cpu_baseline": cpu,
             "fringe_readout": fringe,
