@@ -74,8 +74,8 @@ extern "C" {
 #define FFX_FORM_DENSE  0x3u
 /* FFX_FORM_TC: the dense form on the tensor cores (tcgen05, TF32 operands
  *   split into head and tail, three products accumulated in FP32) for axes of
- *   N points with N a multiple of 64 up to 1024; other lengths, and buffers
- *   not aligned to 16 bytes, use FFX_FORM_DENSE. */
+ *   N points with N a multiple of 16 from 32 up to 1024; other lengths, and
+ *   buffers not aligned to 16 bytes, use FFX_FORM_DENSE. */
 #define FFX_FORM_TC     0x4u
 #define FFX_FORM_MASK   0xFu
 /* With FFX_FORM_AUTO: time every form of every axis at plan time (a few ms,
@@ -159,18 +159,25 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
  *                      the defaults of ffx_plan).  Line lengths must be one of
  *                      16, 32, 48, 64, 96, 128, 192, 256 (FFX_EUNSUPPORTED
  *                      otherwise).
- *  flags               FFX_FORM_PAPER, FFX_FORM_FOLD, FFX_FORM_DENSE or
- *                      FFX_FORM_AUTO (dense when the dense per-axis map costs
- *                      less than the fold form on every instance axis, else
- *                      fold); FFX_ACCUMULATE is rejected (instances on
- *                      different lattices have no common density grid).
+ *  flags               FFX_FORM_PAPER, FFX_FORM_FOLD, FFX_FORM_DENSE,
+ *                      FFX_FORM_TC or FFX_FORM_AUTO (the dense maps when they
+ *                      cost less than the fold form on every instance axis,
+ *                      else fold; dense maps on the tensor cores when every
+ *                      line length is a multiple of 16 from 32);
+ *                      FFX_ACCUMULATE is rejected (instances on different
+ *                      lattices have no common density grid).
  *
  * The dense form builds T_j and T_j^H of every distinct axis geometry at plan
  * creation (the fold pass on the unit vectors) and runs each phase as one
- * persistent kernel over 64 x 32 tiles of all instances; it adds a second
- * packed workspace.  Its passes are not in place for lines over 64 points, so
- * an in-place ffx_expand_field with a 1-D instance longer than 64 points
- * returns FFX_EUNSUPPORTED.
+ * persistent kernel over 64 x 32 tiles of all instances (FP32); it adds a
+ * second packed workspace.  FFX_FORM_TC (and the automatic form, see above)
+ * also builds their tensor-core operand blocks and runs each phase as one
+ * persistent launch of the split-TF32 kernel over items of 128 lines x 128
+ * real rows, one block per SM; a plan with a 16-point axis keeps the FP32
+ * phases (ffx_plan_form reports which).  Dense passes are not in place for
+ * lines over 64 points, so an in-place ffx_expand_field with a 1-D instance
+ * longer than 64 points returns FFX_EUNSUPPORTED.  ffx_plan_device_errors
+ * counts tensor-core phases that gave up on a bounded wait.
  *
  * Data are packed: instance i occupies points [off_i, off_i + M_i) of the
  * input, of the density or field output, and of the gradient buffers, with
@@ -363,7 +370,9 @@ int ffx_launches_per_call(ffx_plan_t plan, int backward);
 
 /* The largest batch for which ffx_expand and ffx_expand_field run as one
  * fused launch (see FFX_UNFUSED): a batch whose first pass has at most two
- * 32-line tiles per SM.  0 if the plan never fuses, -1 for a NULL plan.
+ * 32-line tiles per SM, and, under FFX_FORM_AUTO, below the batch whose
+ * per-axis passes would all run on the tensor cores (see
+ * ffx_plan_call_form).  0 if the plan never fuses, -1 for a NULL plan.
  * When every axis has 64 points and the plan's form is FFX_FORM_AUTO or
  * FFX_FORM_TC, the fused launch forms its products on the tensor cores
  * (split TF32, as FFX_FORM_TC) for a 16-byte-aligned psi0; otherwise with the
@@ -373,9 +382,11 @@ int64_t ffx_plan_fused(ffx_plan_t plan);
 /* The form whose kernel a forward call with this batch runs on lattice axis
  * `axis`: for a fused call the fused launch's arithmetic (FFX_FORM_TC or
  * FFX_FORM_DENSE, see ffx_plan_fused); else the axis's form, except that
- * under FFX_FORM_AUTO a dense axis whose pass covers at least 128 lines per
- * SM runs on the tensor cores
+ * under FFX_FORM_AUTO a dense axis whose pass covers at least 32 lines (in
+ * all, batch x lines) and either has lines of at least 96 points or at least
+ * 64 tensor-core items (128 lines x 128 real rows) runs on the tensor cores
  * (FFX_FORM_TC; a 16-byte-misaligned buffer still takes the FP32 kernel).
+ * Dense passes over fewer than 32 lines run the FP32 few-lines kernel.
  * Results of the two kernels agree to rounding (within the FP32 tolerance),
  * not bit for bit; explicit forms never switch.  -1 on a bad argument or a
  * many-instance plan. */

@@ -490,11 +490,16 @@ int plan_fusion(ffx_plan_s* p) {
 // `in` (k = 0) or the workspace, writes the workspace, and the last pass
 // writes out_c, or out_d (a density), or out_col (the density summed along the
 // last pass's axis); the last two summed over the batch with FFX_ACCUMULATE.
+// The FP32 launch owns whole lines per tile and runs the middle passes in
+// place; the tensor-core launch splits a line's rows over four blocks, so its
+// passes alternate between two workspaces.
 int run_fused(ffx_plan_s* p, const int* axes, const float2* in, float2* out_c, float* out_d, float* out_col,
               int64_t batch, cudaStream_t stream) {
   int rc;
+  const bool tc = p->fused_tc && !out_col && ((uintptr_t)in & 15) == 0;
   if ((rc = ensure_ws(p, 0, batch))) return rc;
-  float2* ws = (float2*)p->ws[0];
+  if (tc && p->ndim > 2 && (rc = ensure_ws(p, 1, batch))) return rc;
+  float2* ws[2] = {(float2*)p->ws[0], tc && p->ndim > 2 ? (float2*)p->ws[1] : (float2*)p->ws[0]};
   FusedArgs a;
   std::memset(&a, 0, sizeof(a));
   a.npass = p->ndim;
@@ -509,8 +514,8 @@ int run_fused(ffx_plan_s* p, const int* axes, const float2* in, float2* out_c, f
     const bool last = k == p->ndim - 1;
     FusedPass& P = a.pass[k];
     axis_outer_inner(p, j, &P.outer, &P.inner);
-    P.in = k == 0 ? in : ws;
-    P.out_c = last ? out_c : ws;
+    P.in = k == 0 ? in : ws[(k - 1) & 1];
+    P.out_c = last ? out_c : ws[k & 1];
     P.out_d = last ? out_d : nullptr;
     P.out_col = last ? out_col : nullptr;
     P.col_scale = (float)(ax.lam * ax.dx);
@@ -531,7 +536,7 @@ int run_fused(ffx_plan_s* p, const int* axes, const float2* in, float2* out_c, f
     cudaEventRecordWithFlags((cudaEvent_t)p->trace[p->trace_i], stream, rec_flags);
   }
   cudaError_t e;
-  if (p->fused_tc && !out_col && ((uintptr_t)in & 15) == 0) {
+  if (tc) {
     for (int k = 0; k < p->ndim; ++k) a.ts[k] = p->axis[axes[k]].ft_ts;
     e = launch_fused_tc(a, p->fused_tc_grid, stream);
   } else {
