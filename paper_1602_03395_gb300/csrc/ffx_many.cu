@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <queue>
 #include <tuple>
 #include <vector>
 
@@ -190,6 +191,7 @@ struct Phase {
   int n_items = 0;
   TcPassArg* d_targs = nullptr;  // tensor-core phases
   TcItem* d_titems = nullptr;
+  long long* d_first = nullptr;   // per block: first item of its run (grid_tc + 1 entries)
   long long n_titems = 0;
 };
 
@@ -713,10 +715,11 @@ int build_dense_phases(ManyPlan* mp, int mode, std::string* err) {
 }
 
 // Tensor-core phases of one mode: the same chains of steps as the dense
-// phases, cut into items of 128 lines x 128 real rows.  Items of one (pass,
-// line tile) stay adjacent (their row blocks share the lines' inputs in L2);
-// those groups run in order of cost, biggest first, and each block takes
-// every gridDim-th item.
+// phases, cut into items of 128 lines x 128 real rows.  The row blocks of one
+// (pass, line tile) form a group that one block runs back to back, so the
+// second row block reads the lines from L2 right after the first.  Groups are
+// dealt to blocks biggest first, each to the least loaded block (cost: K
+// chunks x rows), and every block runs its groups in the order dealt.
 int build_tc_phases(ManyPlan* mp, int mode, std::string* err) {
   std::vector<Phase>& phases = mp->phases[mode];
   const int D = mp->max_dim;
@@ -771,29 +774,44 @@ int build_tc_phases(ManyPlan* mp, int mode, std::string* err) {
       groups.push_back({(double)at.N * at.N, (int)args.size()});
       args.push_back(pa);
     }
-    std::vector<std::pair<double, TcItem>> cut;
+    std::stable_sort(groups.begin(), groups.end(),
+                     [](const std::pair<double, int>& x, const std::pair<double, int>& y) { return x.first > y.first; });
+    const int nb = mp->grid_tc;
+    std::vector<std::vector<TcItem>> per_block(nb);
+    // least loaded block first (ties: lower index)
+    typedef std::pair<double, int> Load;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int b = 0; b < nb; ++b) heap.push({0.0, b});
     for (const auto& gr : groups) {
       const TcPassArg& pa = args[gr.second];
+      const int N = (int)pa.d.N;
       const int64_t ctiles = (pa.d.ncols + LN - 1) / LN;
-      const int mts = many_tc_row_blocks(pa.d.N);
-      for (int64_t ct = 0; ct < ctiles; ++ct)
+      const int mts = many_tc_row_blocks(N);
+      const double per_group = (2.0 * N / 32) * (2.0 * N);  // K chunks x real rows, all row blocks
+      for (int64_t ct = 0; ct < ctiles; ++ct) {
+        Load l = heap.top();
+        heap.pop();
         for (int mt = 0; mt < mts; ++mt) {
           TcItem w;
           w.ct = ct;
           w.arg = gr.second;
           w.mt = mt;
-          cut.push_back({gr.first, w});
+          per_block[l.second].push_back(w);
         }
+        l.first += per_group;
+        heap.push(l);
+      }
     }
-    std::stable_sort(cut.begin(), cut.end(),
-                     [](const std::pair<double, TcItem>& x, const std::pair<double, TcItem>& y) {
-                       return x.first > y.first;
-                     });
     std::vector<TcItem> flat;
-    flat.reserve(cut.size());
-    for (auto& c : cut) flat.push_back(c.second);
+    std::vector<long long> first(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) {
+      first[b] = (long long)flat.size();
+      flat.insert(flat.end(), per_block[b].begin(), per_block[b].end());
+    }
+    first[nb] = (long long)flat.size();
     const size_t abytes = (args.size() * sizeof(TcPassArg) + 255) & ~size_t(255);
-    const size_t bytes = abytes + flat.size() * sizeof(TcItem);
+    const size_t fbytes = ((size_t)(nb + 1) * sizeof(long long) + 255) & ~size_t(255);
+    const size_t bytes = abytes + fbytes + flat.size() * sizeof(TcItem);
     void* m = nullptr;
     cudaError_t e = cudaMalloc(&m, bytes);
     if (e != cudaSuccess) {
@@ -802,9 +820,12 @@ int build_tc_phases(ManyPlan* mp, int mode, std::string* err) {
       return FFX_ENOMEM;
     }
     ph.d_targs = (TcPassArg*)m;
-    ph.d_titems = (TcItem*)((char*)m + abytes);
+    ph.d_first = (long long*)((char*)m + abytes);
+    ph.d_titems = (TcItem*)((char*)m + abytes + fbytes);
     ph.n_titems = (long long)flat.size();
     e = cudaMemcpy(ph.d_targs, args.data(), args.size() * sizeof(TcPassArg), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(ph.d_first, first.data(), first.size() * sizeof(long long), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
       e = cudaMemcpy(ph.d_titems, flat.data(), flat.size() * sizeof(TcItem), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -913,6 +934,7 @@ TcParams tc_params(const ManyPlan* mp, const Phase& ph, const ManyCall& call) {
   std::memset(&tp, 0, sizeof(tp));
   tp.args = ph.d_targs;
   tp.items = ph.d_titems;
+  tp.block_first = ph.d_first;
   tp.n_items = ph.n_titems;
   tp.err = mp->dev_err;
   for (int b = 0; b < NBASE; ++b) tp.call.base[b] = call.base[b];

@@ -228,15 +228,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P)
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  int64_t items;
+  // this block's items: first, first + stride, ... (my_items of them)
+  int64_t first, stride, my_items;
   if (MANY) {
-    items = P.n_items;
+    first = P.block_first[blockIdx.x];  // a contiguous run of the work list
+    stride = 1;
+    my_items = P.block_first[blockIdx.x + 1] - first;
   } else {
     const int mtiles = (2 * P.a.N + ROWS - 1) / ROWS;
-    items = ((P.a.ncols + LINES - 1) / LINES) * mtiles;
+    const int64_t items = ((P.a.ncols + LINES - 1) / LINES) * mtiles;
+    first = blockIdx.x;
+    stride = gridDim.x;
+    my_items = (items - blockIdx.x + gridDim.x - 1) / gridDim.x;
   }
-  if ((int64_t)blockIdx.x >= items) return;
-  const int64_t my_items = (items - blockIdx.x + gridDim.x - 1) / gridDim.x;
+  if (my_items <= 0) return;
 
   if (warp == MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -285,7 +290,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P)
     // issue side: chunk (iit, ib, ikc), RAW - 1 ahead of the consumer
     int64_t iit = 0, ci_issue = 0;
     int ib = 0, ikc = 0;
-    TcView iv = tc_view<MANY>(P, blockIdx.x);
+    TcView iv = tc_view<MANY>(P, first);
     int ikchunks = (2 * iv.N) / TKC;
     long long lb[2];
     int lbr[2];
@@ -344,7 +349,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P)
           if (++ib == iv.nb) {
             ib = 0;
             if (++iit < my_items) {
-              tc_next<MANY>(P, blockIdx.x + iit * gridDim.x, iv);
+              tc_next<MANY>(P, first + iit * stride, iv);
               ikchunks = (2 * iv.N) / TKC;
             }
           }
@@ -356,7 +361,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P)
     for (int r = 0; r < RAW - 1; ++r) issue();
     // consumer side: chunk c = (it, b, kc) of the sequence
     int b = 0, kc = 0;
-    TcView cv = tc_view<MANY>(P, blockIdx.x);
+    TcView cv = tc_view<MANY>(P, first);
     int kchunks = (2 * cv.N) / TKC;
     int last_u[TSTAGES];
 #pragma unroll
@@ -419,7 +424,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P)
         if (++b == cv.nb) {
           b = 0;
           if (++it < my_items) {
-            tc_next<MANY>(P, blockIdx.x + it * gridDim.x, cv);
+            tc_next<MANY>(P, first + it * stride, cv);
             kchunks = (2 * cv.N) / TKC;
           }
         }
@@ -435,9 +440,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P)
     if (lane == 0) {
       int64_t g = 0, sub = 0;
       bool ok = !RES || mbar_wait(smem_u32(&tres_bar), 0u, &s_abort);  // resident T has landed
-      TcView mv = tc_view<MANY>(P, blockIdx.x);
+      TcView mv = tc_view<MANY>(P, first);
       for (int64_t it = 0; ok && it < my_items; ++it) {
-        if (it > 0) tc_next<MANY>(P, blockIdx.x + it * gridDim.x, mv);
+        if (it > 0) tc_next<MANY>(P, first + it * stride, mv);
         const int kchunks = (2 * mv.N) / TKC;
         const uint32_t idesc = idesc_tf32(LINES, FULL ? ROWS : row_count(mv.N, mv.mt));
         for (int b = 0; ok && b < mv.nb; ++b, ++sub) {
@@ -492,9 +497,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P)
       for (int m = 0; m < ROWS / 2; ++m) racc[m * LINES + r] = 0.f;
     int64_t sub = 0;
     bool ok = true;
-    TcView ev = tc_view<MANY>(P, blockIdx.x);
+    TcView ev = tc_view<MANY>(P, first);
     for (int64_t it = 0; ok && it < my_items; ++it) {
-      if (it > 0) tc_next<MANY>(P, blockIdx.x + it * gridDim.x, ev);
+      if (it > 0) tc_next<MANY>(P, first + it * stride, ev);
       const int64_t inner = ev.inner;
       const bool contiguous = (inner == 1);
       const int nbase = ev.mt * (ROWS / 2);

@@ -28,14 +28,16 @@ struct TcBases {
 };
 
 // Kernel parameters.  Uniform launches: the pass `a` with operand blocks
-// `tblk`, items (line tile, row block) numbered row block fastest.
-// Many-instance launches: `items` over the passes `args`.  `err` counts
-// launches that gave up on a bounded wait.
+// `tblk`, items (line tile, row block) numbered row block fastest, block b
+// taking items b, b + gridDim.x, ...  Many-instance launches: `items` over the
+// passes `args`, block b taking items [block_first[b], block_first[b + 1]).
+// `err` counts launches that gave up on a bounded wait.
 struct TcParams {
   DenseArgs a;
   const unsigned char* tblk;
   const TcPassArg* args;
   const TcItem* items;
+  const long long* block_first;  // gridDim.x + 1 entries
   long long n_items;
   TcBases call;
   int* err;
