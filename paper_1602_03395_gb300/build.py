@@ -57,7 +57,8 @@ def sources_digest(names) -> str:
         with open(os.path.join(CSRC, f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
-    h.update(" ".join(NVCC_FLAGS).encode())
+    # the flags without the machine's checkout path (the include directory)
+    h.update(" ".join(f.replace(ROOT, "<repo>") for f in NVCC_FLAGS).encode())
     return h.hexdigest()
 
 
