@@ -47,6 +47,37 @@ L2_BYTES = 129 * 1024 * 1024
 SMS, FP32_LANES = 152, 128
 
 
+# ---------------------------------------------------------------------------
+# multi-rank host logic (one process per GPU): disjoint seeded shards, the
+# slowest rank's time, the whole job's rate
+# ---------------------------------------------------------------------------
+
+def rank_realizations(rank: int, batch: int, n_buffers: int = 4):
+    """First realization index of each of a rank's distinct input buffers of
+    `batch` realizations: rank r draws [(1000 r + i) B, (1000 r + i + 1) B),
+    disjoint across ranks."""
+    return [(rank * 1000 + i) * batch for i in range(n_buffers)]
+
+
+def mixed_seed(rank: int, i: int) -> int:
+    """Seed of instance i of the mixed batch on rank `rank` (disjoint across
+    ranks for batches below 7919 instances)."""
+    return rank * 7919 + i
+
+
+def max_over_ranks(torch, dist, value: float, device) -> float:
+    """The largest of the ranks' values (the slowest rank's time)."""
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(steps: int, per_rank: int, world: int, ms: float) -> float:
+    """Whole-job realizations/s: every rank ran `steps` steps of `per_rank`
+    realizations in (at most) `ms` milliseconds."""
+    return steps * per_rank * world / (ms * 1e-3)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -378,7 +409,7 @@ def run_mixed(args, torch, dist, world, rank, dev):
     for i, w in enumerate(ws):
         key = (tuple(w.dims), i % 3)
         if key not in cache:
-            cache[key] = torch.from_numpy(w.realization(rank * 7919 + i)).to(dev)
+            cache[key] = torch.from_numpy(w.realization(mixed_seed(rank, i))).to(dev)
         views[i].copy_(cache[key])
     out = torch.empty(plan.points, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -419,10 +450,8 @@ def run_mixed(args, torch, dist, world, rank, dev):
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = args.steps * count * world / (ms * 1e-3)
+        ms = max_over_ranks(torch, dist, ms, dev)
+    value = job_rate(args.steps, count, world, ms)
     flops = mixed_flops(specs, plan.form)
     pk, pk_src = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
@@ -455,6 +484,8 @@ def run_mixed(args, torch, dist, world, rank, dev):
                            steps_e2e)
     lanes_used = 2
     plan2.close()
+    if world > 1:
+        e2e_ms = max_over_ranks(torch, dist, e2e_ms, dev)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -471,7 +502,7 @@ def run_mixed(args, torch, dist, world, rank, dev):
             "roofline_hbm": {"bound": "hbm", "achieved": byts / (ms / args.steps * 1e-3) / 1e9,
                              "peak": hbm_peak, "unit": "GB/s",
                              "frac": byts / (ms / args.steps * 1e-3) / 1e9 / hbm_peak},
-            "e2e": {"value": steps_e2e * count * world / (e2e_ms * 1e-3), "unit": UNIT, "lanes": lanes_used,
+            "e2e": {"value": job_rate(steps_e2e, count, world, e2e_ms), "unit": UNIT, "lanes": lanes_used,
                     "h2d_bytes_per_step": plan.points * 8, "d2h_bytes_per_step": plan.points * 4},
             "cpu_baseline": None,
         }
@@ -532,7 +563,7 @@ def run_ffx(args):
     step_in_bytes = B_ * M * 8
     pool_n = max(2, math.ceil(2 * L2_BYTES / step_in_bytes))
     pool_n = min(pool_n, 256)
-    distinct = [torch.from_numpy(w.batch_array(B_, start=(rank * 1000 + i) * B_)) for i in range(4)]
+    distinct = [torch.from_numpy(w.batch_array(B_, start=s)) for s in rank_realizations(rank, B_)]
     pool_in = [distinct[i % 4].to(dev) for i in range(pool_n)]
     pool_out = [torch.empty(out_shape, dtype=torch.float32, device=dev) for _ in range(min(pool_n, 64))]
     stream = torch.cuda.current_stream(dev)
@@ -601,9 +632,7 @@ def run_ffx(args):
     clocks = sampler.stop()
     ms = t_start.elapsed_time(t_end)
     if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+        ms = max_over_ranks(torch, dist, ms, dev)
 
     # per-pass durations from the traced events
     per_pass = [[] for _ in range(launches)]
@@ -670,7 +699,7 @@ def run_ffx(args):
                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
                                    f"(sm_max_mhz from MEASURED_PEAKS.json, {pk_src})"}
 
-    value = args.steps * B_ * world / (ms * 1e-3)
+    value = job_rate(args.steps, B_, world, ms)
 
     # end to end through the C ABI with host buffers: pinned H2D, expand, D2H
     # per step, two lanes (see pipelined_e2e)
@@ -693,10 +722,8 @@ def run_ffx(args):
     e2e_ms = e2e_lanes[lanes_used]
     plan2.close()
     if world > 1:
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
-    e2e_value = e2e_steps * B_ * world / (e2e_ms * 1e-3)
+        e2e_ms = max_over_ranks(torch, dist, e2e_ms, dev)
+    e2e_value = job_rate(e2e_steps, B_, world, e2e_ms)
 
     # the fringe readout of eq. dphase2 on the step's detector image (two-cloud
     # workloads imaged across their separation axis): one launch, timed alone

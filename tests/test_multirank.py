@@ -1,0 +1,78 @@
+"""The multi-GPU path's host logic on CPU: two gloo ranks, as bench.py runs
+one process per GPU under torchrun.  Realizations are independent, so ranks
+draw disjoint seeded shards and share nothing on the data path; the timing is
+reduced to the slowest rank, and the job's rate counts every rank's
+realizations.  The one exchange an ensemble over GPUs needs (the sum of the
+ranks' mean densities) is checked against a single process computing all of
+it."""
+
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import bench
+import oracle as O
+from paper_1602_03395_gb300 import inputs
+
+WORLD = 2
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, port):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=WORLD)
+    try:
+        # disjoint shards of the two-cloud workload, distinct data
+        B = 3
+        starts = bench.rank_realizations(rank, B)
+        every = [None] * WORLD
+        dist.all_gather_object(every, starts)
+        spans = [set(range(s, s + B)) for r in range(WORLD) for s in every[r]]
+        assert sum(len(x) for x in spans) == len(set().union(*spans)), "ranks share realizations"
+        w = inputs.config_two_cloud()
+        arr = w.batch_array(1, start=starts[0])
+        sums = [None] * WORLD
+        dist.all_gather_object(sums, complex(arr.sum()))
+        assert sums[0] != sums[1]
+        seeds = [None] * WORLD
+        dist.all_gather_object(seeds, [bench.mixed_seed(rank, i) for i in range(1000)])
+        assert not set(seeds[0]) & set(seeds[1])
+
+        # the slowest rank's time, on every rank; the job's rate from it
+        ms = bench.max_over_ranks(torch, dist, 10.0 + 5.0 * rank, "cpu")
+        assert ms == 15.0
+        assert bench.job_rate(steps=4, per_rank=B, world=WORLD, ms=ms) == pytest.approx(4 * B * WORLD / 0.015)
+
+        # the ensemble's one exchange: each rank sums the densities of its own
+        # realizations (a small 1-D geometry), then one all_reduce
+        N, dx, lam, t = 64, 0.2, 7, 3.0
+        rng = np.random.default_rng(1000 + rank)
+        psi = (rng.normal(size=(2, N)) + 1j * rng.normal(size=(2, N))).astype(np.complex64)
+        local = O.expand_density(psi, (dx,), t, (lam,)).sum(axis=0)
+        tot = torch.from_numpy(local.astype(np.float64))
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        if rank == 0:
+            ref = np.zeros(N)
+            for r in range(WORLD):
+                g = np.random.default_rng(1000 + r)
+                p = (g.normal(size=(2, N)) + 1j * g.normal(size=(2, N))).astype(np.complex64)
+                ref += O.expand_density(p, (dx,), t, (lam,)).sum(axis=0)
+            assert np.allclose(tot.numpy(), ref, rtol=1e-12, atol=0)
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks():
+    mp.spawn(_rank_main, args=(_free_port(),), nprocs=WORLD, join=True)
