@@ -316,7 +316,8 @@ constexpr int kFusedThreads = 512;
 // slice of each T_j (32 KB per axis) in shared memory.  Per item: 256 threads
 // load the 128 lines from L2 (16-byte loads, coalesced along either memory
 // order), split them into the core-matrix layout (bank-conflict free), one
-// thread issues 16 K-steps x 3 tcgen05.mma and commits to an mbarrier, and
+// thread issues 16 K-steps x 2 tcgen05.mma (N = 64 over the slice's head and
+// tail rows for X_hi, N = 32 for X_lo) and commits to an mbarrier, and
 // eight warps read the accumulators back (warp w: lane quarter w % 4, column
 // half w / 4) and store.  Summing |.|^2 over the batch stays in registers.
 // ---------------------------------------------------------------------------
@@ -334,6 +335,9 @@ constexpr int FT_TS_BYTES = 2 * FT_TS_PART;     // one row block's slice, head a
 constexpr int FT_SMEM = 2 * FT_X_PART + 3 * FT_TS_BYTES;  // 224 KB
 constexpr int FT_COLS = 2 * FT_ROWS;            // head accumulator, cross-term accumulator
 constexpr uint32_t kIdescFT = tc::idesc_tf32(FT_LINES, FT_ROWS);
+// the slice's head and tail rows are contiguous 8-row groups: one N = 64
+// product forms X_hi T_hi and X_hi T_lo side by side in the two accumulators
+constexpr uint32_t kIdescFT2 = tc::idesc_tf32(FT_LINES, 2 * FT_ROWS);
 
 __global__ void __launch_bounds__(FT_THREADS, 1) fused_tc_kernel(const FusedArgs a) {
   using namespace tc;
@@ -374,7 +378,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fused_tc_kernel(const FusedArgs
     const bool contiguous = (inner == 1);
     const int nb = P.acc ? (int)a.batch : 1;
     const int64_t ctiles = (P.ncols + FT_LINES - 1) / FT_LINES;
-    const uint32_t th = smem_u32(tsl + p * FT_TS_BYTES), tl = th + FT_TS_PART;
+    const uint32_t th = smem_u32(tsl + p * FT_TS_BYTES);  // head rows, then the tail rows
     for (int64_t ct = c0; ct < ctiles && !s_abort; ct += cstep) {
       float racc[8];
 #pragma unroll
@@ -431,7 +435,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fused_tc_kernel(const FusedArgs
         fence_async_smem();
         tc_fence_before();
         __syncthreads();
-        // ---- the product: 16 K-steps x 3 split products
+        // ---- the product: 16 K-steps x 3 split products in 2 MMAs
         if (tid == 0 && !slices) slices = mbar_wait(smem_u32(&tbar), 0u, &s_abort);  // under the first load
         if (tid == 0 && slices) {
           tc_fence_after();
@@ -440,11 +444,10 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fused_tc_kernel(const FusedArgs
           for (int ks = 0; ks < FT_K / 8; ++ks) {
             const uint32_t o = (uint32_t)(ks * 256);
             const uint64_t dxh = make_desc(ah + o, 128, FT_SBO), dxl = make_desc(al + o, 128, FT_SBO);
-            const uint64_t dth = make_desc(th + o, 128, FT_SBO), dtl = make_desc(tl + o, 128, FT_SBO);
+            const uint64_t dth = make_desc(th + o, 128, FT_SBO);
             const uint32_t more = ks > 0 ? 1u : 0u;
-            mma_tf32(tmem, dxh, dth, kIdescFT, more);
-            mma_tf32(tmem + FT_ROWS, dxh, dtl, kIdescFT, more);
-            mma_tf32(tmem + FT_ROWS, dxl, dth, kIdescFT, 1u);
+            mma_tf32(tmem, dxh, dth, kIdescFT2, more);         // [X_hi T_hi | X_hi T_lo]
+            mma_tf32(tmem + FT_ROWS, dxl, dth, kIdescFT, 1u);  // + X_lo T_hi
           }
           mma_commit(smem_u32(&mbar));
           issued = true;

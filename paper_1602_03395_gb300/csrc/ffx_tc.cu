@@ -97,6 +97,9 @@ using namespace tc;
 
 // Real output rows of row block mt: ROWS, or what is left of 2N in the last
 // block (a multiple of 32, since N is a multiple of 16).
+// kind::tf32, M = LINES, N = 2 ROWS: a whole row block's head and tail rows at once
+constexpr uint32_t kIdescStack = idesc_tf32(LINES, 2 * ROWS);
+
 __host__ __device__ __forceinline__ int row_count(int N, int mt) {
   const int left = 2 * N - mt * ROWS;
   return left < ROWS ? left : ROWS;
@@ -474,8 +477,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P)
               const uint64_t dth = make_desc(th + o, CORE_LBO, CHUNK_SBO);
               const uint64_t dtl = make_desc(tl + o, CORE_LBO, CHUNK_SBO);
               const uint32_t more = (kc == 0 && ks == 0) ? 0u : 1u;
-              mma_tf32(d1, dxh, dth, idesc, more);
-              mma_tf32(d2, dxh, dtl, idesc, more);
+              if (RES) {
+                // resident T (a whole row block): the chunk's head and tail rows are
+                // contiguous 8-row groups, so one N = 256 product forms [X_hi T_hi |
+                // X_hi T_lo] in d1, d2 (measured faster here, not on streamed chunks)
+                mma_tf32(d1, dxh, dth, kIdescStack, more);
+              } else {
+                mma_tf32(d1, dxh, dth, idesc, more);
+                mma_tf32(d2, dxh, dtl, idesc, more);
+              }
               mma_tf32(d2, dxl, dth, idesc, 1u);
             }
             mma_commit(smem_u32(&empty_bar[s]));
