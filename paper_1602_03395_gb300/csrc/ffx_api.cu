@@ -130,6 +130,10 @@ void set_last_error_message(const char* msg) { g_last_error = msg ? msg : ""; }
 
 using namespace ffx;
 
+// Head of a plan's tensor-core allocation: device error counter (+0), the
+// fused launch's grid-barrier counters (+64), its tile counters (+1024).
+constexpr size_t kTcHeader = 1024 + kFusedTileFlags * sizeof(unsigned);
+
 struct ffx_plan_s {
   int ndim = 0;
   int64_t dims[3] = {1, 1, 1};
@@ -146,6 +150,7 @@ struct ffx_plan_s {
   void* tc_mem = nullptr;    // split tensor-core operands + device error counter
   int* dev_err = nullptr;
   unsigned* grid_bar = nullptr;  // arrival counter of the fused kernel's grid barriers
+  unsigned* tile_done = nullptr;  // per line tile: row blocks of the fused kernel's previous pass written
   int64_t fused = 0;             // largest batch whose forward calls run as one launch (ffx_fused.cu)
   int fused_grid = 0;
   int fused_tc = 0;              // ... on the tensor cores (every axis 64 points, automatic or tc form)
@@ -536,8 +541,22 @@ int run_fused(ffx_plan_s* p, const int* axes, const float2* in, float2* out_c, f
     cudaEventRecordWithFlags((cudaEvent_t)p->trace[p->trace_i], stream, rec_flags);
   }
   cudaError_t e;
+  a.local_pass = -1;
   if (tc) {
     for (int k = 0; k < p->ndim; ++k) a.ts[k] = p->axis[axes[k]].ft_ts;
+    // A pass may follow the previous one tile by tile when the two passes'
+    // line tiles cover the same points: every pass of a 2-D lattice (a tile
+    // is two realizations), and two passes of a 3-D lattice that both run
+    // along axes 1 and 2 (a tile is two values of axis 0 of one realization).
+    // Not into an accumulating pass over several realizations (its tile
+    // gathers every realization).
+    a.tile_done = p->tile_done;
+    for (int k = 1; k < p->ndim; ++k) {
+      const bool same = p->ndim == 2 || (axes[k - 1] != 0 && axes[k] != 0);
+      const FusedPass& P = a.pass[k];
+      const bool gathers = P.acc && batch > 1;
+      if (same && !gathers && (P.ncols + 127) / 128 <= kFusedTileFlags) a.local_pass = k;
+    }
     e = launch_fused_tc(a, p->fused_tc_grid, stream);
   } else {
     e = launch_fused(a, p->fused_grid, p->fused_smem_bytes, stream);
@@ -941,7 +960,7 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
 
   // split tensor-core operands, and the device error counter
   if (rc == FFX_OK) {
-    size_t tbytes = 256;
+    size_t tbytes = kTcHeader;
     for (int j = 0; j < ndim; ++j)
       if (dense_tc_supported(p->axis[j].N) && p->axis[j].T && (form == FFX_FORM_AUTO || form == FFX_FORM_TC))
         tbytes += 2 * dense_tc_t_bytes(p->axis[j].N) + (p->axis[j].N == 64 ? fused_tc_slice_bytes() : 0);
@@ -952,8 +971,9 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
     } else {
       p->dev_err = (int*)p->tc_mem;
       p->grid_bar = (unsigned*)((char*)p->tc_mem + 64);
-      cudaMemsetAsync(p->dev_err, 0, 256, s);
-      unsigned char* tcur = (unsigned char*)p->tc_mem + 256;
+      p->tile_done = (unsigned*)((char*)p->tc_mem + 1024);
+      cudaMemsetAsync(p->dev_err, 0, kTcHeader, s);
+      unsigned char* tcur = (unsigned char*)p->tc_mem + kTcHeader;
       for (int j = 0; j < ndim && rc == FFX_OK; ++j) {
         Axis& ax = p->axis[j];
         if (!(dense_tc_supported(ax.N) && ax.T && (form == FFX_FORM_AUTO || form == FFX_FORM_TC))) continue;

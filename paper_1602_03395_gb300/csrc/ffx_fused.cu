@@ -370,6 +370,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fused_tc_kernel(const FusedArgs
   const uint32_t tmem = tmem_slot;
 
   uint32_t phase = 0;
+  unsigned barriers = 0;  // grid barriers passed
   bool slices = false;  // (thread 0) the T slices have landed
   bool issued = false;
   for (int p = 0; p < a.npass && !s_abort; ++p) {
@@ -380,6 +381,22 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fused_tc_kernel(const FusedArgs
     const int64_t ctiles = (P.ncols + FT_LINES - 1) / FT_LINES;
     const uint32_t th = smem_u32(tsl + p * FT_TS_BYTES);  // head rows, then the tail rows
     for (int64_t ct = c0; ct < ctiles && !s_abort; ct += cstep) {
+      if (p == a.local_pass) {
+        // this tile's input is written once the previous pass's four row blocks of it are
+        if (tid == 0) {
+          bool ok = false;
+          for (long long i = 0; i < kSpinLimit; ++i) {
+            if (*(volatile unsigned*)(a.tile_done + ct) >= (unsigned)FT_RB) {
+              ok = true;
+              break;
+            }
+          }
+          if (!ok) s_abort = 1;
+          __threadfence();
+        }
+        __syncthreads();
+        if (s_abort) break;
+      }
       float racc[8];
 #pragma unroll
       for (int m = 0; m < 8; ++m) racc[m] = 0.f;
@@ -505,8 +522,15 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fused_tc_kernel(const FusedArgs
         tc_fence_before();
         __syncthreads();  // accumulators read and shared tiles free before the next item
       }
+      if (p + 1 == a.local_pass && tid == 0) {
+        __threadfence();  // this row block of the tile is written
+        atomicAdd(a.tile_done + ct, 1u);
+      }
     }
-    if (p + 1 < a.npass && !grid_barrier(a.bar, (unsigned)(p + 1) * gridDim.x, &s_abort)) break;
+    if (p + 1 < a.npass && p + 1 != a.local_pass) {
+      ++barriers;
+      if (!grid_barrier(a.bar, (unsigned)barriers * gridDim.x, &s_abort)) break;
+    }
   }
   // the tensor cores finish this block's work, and the slice copies have
   // landed, before the block exits
@@ -519,10 +543,18 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fused_tc_kernel(const FusedArgs
   }
   tc_fence_before();
   __syncthreads();
+  __shared__ int s_last;
   if (tid == 0) {
     if (s_abort && a.err) atomicAdd(a.err, 1);
     __threadfence();
-    if (atomicAdd(a.bar + 1, 1u) == gridDim.x - 1) {
+    s_last = atomicAdd(a.bar + 1, 1u) == gridDim.x - 1;  // every block has left every barrier
+  }
+  __syncthreads();
+  if (s_last) {
+    // the last block out resets the counters for the next launch (stream order publishes them)
+    if (a.local_pass > 0)
+      for (int i = tid; i < kFusedTileFlags; i += FT_THREADS) a.tile_done[i] = 0u;
+    if (tid == 0) {
       atomicExch(a.bar, 0u);
       atomicExch(a.bar + 1, 0u);
     }

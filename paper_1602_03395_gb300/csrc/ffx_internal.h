@@ -138,7 +138,14 @@ struct FusedArgs {
   unsigned* bar;        // [2]: grid-barrier arrivals, blocks done (the last block resets both)
   int* err;
   const unsigned char* ts[3];  // tensor-core variant: per pass, T_j's split 32-row slices
+  // tensor-core variant: pass local_pass (> 0) starts each line tile once the
+  // previous pass's four row blocks of the same tile are written (tile_done
+  // counters, kFusedTileFlags of them, reset by the last block) instead of
+  // after a grid barrier; -1: grid barriers only
+  unsigned* tile_done;
+  int local_pass;
 };
+constexpr int kFusedTileFlags = 256;
 size_t fused_smem(const int* N, int npass);
 // Tensor-core variant for lattices whose axes all have 64 points: 4 row
 // blocks of 32 real rows; each block's T slice is head and tail of 32 rows x
