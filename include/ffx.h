@@ -224,6 +224,26 @@ int ffx_expand(ffx_plan_t plan, const void* psi0, int64_t batch, float* out_dens
                void* stream);
 
 /*
+ * ffx_expand_host -- ffx_expand on host buffers, one call per step: copies
+ * psi0_host ([batch][M] complex64 in host memory) into a device staging
+ * buffer of the plan, runs ffx_expand on it, and copies the densities back to
+ * out_host ([batch][M] float32, or [M] with FFX_ACCUMULATE: then out_host's
+ * values are copied in first and the batch sum is added to them).  A
+ * many-instance plan takes batch = 1 and its packed layout.
+ *
+ * Asynchronous on `stream` like ffx_expand: the host buffers must stay valid,
+ * and out_host unread, until the stream reaches the copies
+ * (cudaStreamSynchronize); page-locked (pinned) host memory lets the copies
+ * overlap other work.  The staging buffers are allocated on first use and
+ * grown with larger batches (cudaMalloc, which synchronizes the device), and
+ * are shared by calls on the same plan: calls on different streams need
+ * different plans.  Returns FFX_EINVAL (NULL pointers, batch < 0, a
+ * many-instance batch other than 1), FFX_ENOMEM, FFX_ECUDA, or ffx_expand's
+ * codes.
+ */
+int ffx_expand_host(ffx_plan_t plan, const void* psi0_host, int64_t batch, float* out_host, void* stream);
+
+/*
  * ffx_expand_field -- the complex field Psibar itself, [batch][M...] complex64.
  * out_field may equal psi0 (in place); otherwise the two must not overlap.
  * Needs no workspace.  The phase of Psibar is that of the magnified lattice,

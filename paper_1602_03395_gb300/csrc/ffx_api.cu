@@ -160,6 +160,8 @@ struct ffx_plan_s {
   // detector densities, or a positive-P pair's first field; [3] its second
   void* ws[4] = {nullptr, nullptr, nullptr, nullptr};
   size_t ws_bytes[4] = {0, 0, 0, 0};
+  void* stage[2] = {nullptr, nullptr};  // ffx_expand_host: device copies of the input and the densities
+  size_t stage_bytes[2] = {0, 0};
   ManyPlan* many = nullptr;       // set for plans over many instances
   void* const* trace = nullptr;   // caller's cudaEvent_t array (profiling)
   int64_t trace_n = 0;
@@ -217,6 +219,25 @@ int prepare_kernel(PassKernelInfo& info) {
 int check_ptr(const void* p, const char* name) {
   if (!p) return fail(FFX_EINVAL, "%s is NULL", name);
   if (((uintptr_t)p) & 7) return fail(FFX_EINVAL, "%s is not 8-byte aligned", name);
+  return FFX_OK;
+}
+
+// Device staging buffer k of ffx_expand_host, at least `need` bytes (grown
+// like the workspace: cudaMalloc synchronizes the device the first time).
+int ensure_stage(ffx_plan_s* p, int k, size_t need) {
+  if (need <= p->stage_bytes[k]) return FFX_OK;
+  if (p->stage[k]) {
+    cudaFree(p->stage[k]);
+    p->stage[k] = nullptr;
+    p->stage_bytes[k] = 0;
+  }
+  cudaError_t e = cudaMalloc(&p->stage[k], need);
+  if (e != cudaSuccess) {
+    p->stage[k] = nullptr;
+    cudaGetLastError();
+    return fail(FFX_ENOMEM, "staging buffer of %zu bytes: %s", need, cudaGetErrorString(e));
+  }
+  p->stage_bytes[k] = need;
   return FFX_OK;
 }
 
@@ -1098,6 +1119,8 @@ int64_t ffx_plan_points(ffx_plan_t p) { return p ? p->M : -1; }
 int ffx_plan_destroy(ffx_plan_t p) {
   if (!p) return FFX_OK;
   cudaDeviceSynchronize();
+  for (int k = 0; k < 2; ++k)
+    if (p->stage[k]) cudaFree(p->stage[k]);
   if (p->many) {
     many_destroy(p->many);
     delete p;
@@ -1217,6 +1240,28 @@ int ffx_expand(ffx_plan_t p, const void* psi0, int64_t batch, float* out_density
   }
   if (batch <= p->fused) return run_fused(p, p->order, (const float2*)psi0, nullptr, out_density, nullptr, batch, s);
   return forward_density(p, p->order, (const float2*)psi0, batch, out_density, s);
+}
+
+int ffx_expand_host(ffx_plan_t p, const void* psi0_host, int64_t batch, float* out_host, void* stream) {
+  if (!p) return fail(FFX_EINVAL, "plan is NULL");
+  if (batch < 0) return fail(FFX_EINVAL, "batch < 0");
+  if (batch == 0) return FFX_OK;
+  if (!psi0_host) return fail(FFX_EINVAL, "psi0_host is NULL");
+  if (!out_host) return fail(FFX_EINVAL, "out_host is NULL");
+  if (p->many && batch != 1) return fail(FFX_EINVAL, "a many-instance plan takes batch = 1");
+  int rc;
+  const size_t in_bytes = (size_t)batch * (size_t)p->M * sizeof(float2);
+  const size_t out_bytes = (size_t)(p->acc ? 1 : batch) * (size_t)p->M * sizeof(float);
+  if ((rc = ensure_stage(p, 0, in_bytes)) || (rc = ensure_stage(p, 1, out_bytes))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(p->stage[0], psi0_host, in_bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && p->acc)  // the sum adds to what out_host holds
+    e = cudaMemcpyAsync(p->stage[1], out_host, out_bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "input copy to the device");
+  if ((rc = ffx_expand(p, p->stage[0], batch, (float*)p->stage[1], stream))) return rc;
+  e = cudaMemcpyAsync(out_host, p->stage[1], out_bytes, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "density copy to the host");
+  return FFX_OK;
 }
 
 int ffx_expand_column(ffx_plan_t p, const void* psi0, int64_t batch, int axis, float* out_column, void* stream) {

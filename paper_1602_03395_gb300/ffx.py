@@ -71,6 +71,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ffx_plan_destroy.restype = i32
     lib.ffx_expand.argtypes = [vp, vp, i64, vp, vp]
     lib.ffx_expand.restype = i32
+    lib.ffx_expand_host.argtypes = [vp, vp, i64, vp, vp]
+    lib.ffx_expand_host.restype = i32
     lib.ffx_expand_field.argtypes = [vp, vp, i64, vp, vp]
     lib.ffx_expand_field.restype = i32
     lib.ffx_expand_backward.argtypes = [vp, vp, vp, i64, vp, vp]
@@ -354,6 +356,25 @@ def ffx_expand(plan: Plan, psi0: torch.Tensor, out_density: torch.Tensor | None 
     _need(out_density, torch.float32, "out_density")
     _check(load_library().ffx_expand(plan.handle, _ptr(psi0), B, _ptr(out_density), _stream(stream)),
            "ffx_expand")
+    return out_density
+
+
+def ffx_expand_host(plan: Plan, psi0: torch.Tensor, out_density: torch.Tensor, stream=None) -> torch.Tensor:
+    """ffx_expand on host tensors in one C call: psi0 (complex64, CPU,
+    contiguous; pinned for overlap) is copied to the device, expanded, and the
+    densities are copied into out_density (float32, CPU; [B, *dims], or
+    [*dims] accumulated for an accumulating plan).  Asynchronous on `stream`:
+    synchronize it before reading out_density."""
+    for x, dt, name in ((psi0, torch.complex64, "psi0"), (out_density, torch.float32, "out_density")):
+        if x.device.type != "cpu" or x.dtype != dt or not x.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {dt} tensor in host memory")
+    B = plan._batch(psi0)
+    need = (plan.M if plan.accumulate else B * plan.M)
+    if out_density.numel() != need:
+        raise ValueError(f"out_density must have {need} elements")
+    _check(load_library().ffx_expand_host(plan.handle, ctypes.c_void_p(psi0.data_ptr()), B,
+                                          ctypes.c_void_p(out_density.data_ptr()), _stream(stream)),
+           "ffx_expand_host")
     return out_density
 
 
