@@ -148,23 +148,40 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
         b_s[tid] = b;
       }
       __syncthreads();
-      for (int idx = tid; idx < LINES * N; idx += NT) {
-        int l, n;
-        tile_coords(idx, N, LINES, contiguous, l, n);
-        const long long base = base_s[l];
-        float2 v = make_float2(0.f, 0.f);
-        if (base >= 0) {
-          const int64_t addr = base + (int64_t)n * inner;
-          v = a.in[addr];  // plain load: passes may run in place
-          if (a.grad) {
-            const int64_t b = b_s[l];
-            const int64_t gaddr = a.grad_shared ? addr - b * a.M : addr;
-            const float gr = 2.f * __ldg(a.grad + gaddr);
-            v.x *= gr;
-            v.y *= gr;
+      // the tile's loads go out U at a time per thread, then their stores (same values)
+      constexpr int U = 8;
+      for (int idx0 = tid; idx0 < LINES * N; idx0 += U * NT) {
+        float2 v[U];
+        float gr[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int idx = idx0 + u * NT;
+          v[u] = make_float2(0.f, 0.f);
+          gr[u] = 1.f;
+          if (idx < LINES * N) {
+            int l, n;
+            tile_coords(idx, N, LINES, contiguous, l, n);
+            const long long base = base_s[l];
+            if (base >= 0) {
+              const int64_t addr = base + (int64_t)n * inner;
+              v[u] = a.in[addr];  // plain load: passes may run in place
+              if (a.grad) {
+                const int64_t b = b_s[l];
+                const int64_t gaddr = a.grad_shared ? addr - b * a.M : addr;
+                gr[u] = 2.f * __ldg(a.grad + gaddr);
+              }
+            }
           }
         }
-        psi_s[l * NP + pad(n)] = v;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int idx = idx0 + u * NT;
+          if (idx < LINES * N) {
+            int l, n;
+            tile_coords(idx, N, LINES, contiguous, l, n);
+            psi_s[l * NP + pad(n)] = a.grad ? make_float2(v[u].x * gr[u], v[u].y * gr[u]) : v[u];
+          }
+        }
       }
       __syncthreads();
 
