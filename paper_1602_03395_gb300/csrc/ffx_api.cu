@@ -112,6 +112,7 @@ struct Axis {
   float2 *P = nullptr, *K = nullptr, *Kf = nullptr, *F = nullptr, *tw = nullptr;
   int* fold = nullptr;
   int form = FFX_FORM_FOLD;  // PAPER, FOLD or DENSE
+  bool few = false;          // automatic dense form taken for fewer than kDenseFewLines lines per realization
   PassKernelInfo paper{}, foldk{}, adj{};
   int grid_paper = 0, grid_fold = 0, grid_adj = 0;
   float2* T = nullptr;   // dense map [N][N] (N <= kDenseMaxN)
@@ -265,12 +266,15 @@ bool inplace_ok(const Axis& ax) {
 
 bool tc_capable(const Axis& ax) { return dense_tc_supported(ax.N) && ax.tc_t[0] != nullptr; }
 
-// The dense map's kernel for a pass over `lines` lines: FFX_FORM_TC or
-// FFX_FORM_DENSE.  An axis the plan's automatic choice gave the FP32 dense form
+// The form whose kernel a pass over `lines` lines runs (explicit forms keep
+// theirs).  An axis the plan's automatic choice gave the FP32 dense form
 // moves to the tensor cores when the pass leaves the few-lines kernel and
 // either its lines have at least 96 points (the FP32 tile kernel's K loop is
 // the slower one there, measured down to a single 128-line tile) or it has at
-// least 64 tensor-core items; explicit forms keep their kernel.
+// least 64 tensor-core items.  An axis that took the dense form only for its
+// handful of lines per realization (a 1-D field) takes an FFT form instead
+// when a call over many lines makes that cheaper (small lam).
+double model_cost(const Axis& ax, int form, int64_t lines);
 int dense_kernel_for(const ffx_plan_s* p, const Axis& ax, int64_t lines);
 
 // The tensor-core kernel moves 16-byte vectors; other pointers take the SIMT dense kernels.
@@ -295,8 +299,8 @@ int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* 
   }
   cudaError_t e;
   const int64_t lines = acc ? outer * inner : batch * outer * inner;
-  if ((ax.form == FFX_FORM_TC || ax.form == FFX_FORM_DENSE) && dense_kernel_for(p, ax, lines) == FFX_FORM_TC &&
-      tc_aligned(in, out_c, out_d)) {
+  const int cform = dense_kernel_for(p, ax, lines);  // this call's form
+  if (cform == FFX_FORM_TC && tc_aligned(in, out_c, out_d)) {
     DenseArgs d;
     std::memset(&d, 0, sizeof(d));
     d.in = in;
@@ -315,7 +319,7 @@ int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* 
     if (grid > p->sms) grid = p->sms;
     if (grid < 1) grid = 1;
     e = launch_dense_tc(d, ax.tc_t[adjoint ? 1 : 0], p->dev_err, (int)grid, stream);
-  } else if (ax.form == FFX_FORM_DENSE || ax.form == FFX_FORM_TC) {
+  } else if (cform == FFX_FORM_DENSE || cform == FFX_FORM_TC) {
     DenseArgs d;
     std::memset(&d, 0, sizeof(d));
     d.A = adjoint ? ax.TH : ax.T;
@@ -370,8 +374,8 @@ int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* 
     a.tab.F = ax.F;
     a.tab.tw = ax.tw;
     a.tab.fold = ax.fold;
-    const PassKernelInfo& info = adjoint ? ax.adj : (ax.form == FFX_FORM_PAPER ? ax.paper : ax.foldk);
-    const int capacity = adjoint ? ax.grid_adj : (ax.form == FFX_FORM_PAPER ? ax.grid_paper : ax.grid_fold);
+    const PassKernelInfo& info = adjoint ? ax.adj : (cform == FFX_FORM_PAPER ? ax.paper : ax.foldk);
+    const int capacity = adjoint ? ax.grid_adj : (cform == FFX_FORM_PAPER ? ax.grid_paper : ax.grid_fold);
     // The split depends on one realization's lines only, so a realization's
     // result does not depend on the batch it came in (bitwise).
     a.qg = choose_qg(info, outer * inner, ax.lam, capacity);
@@ -451,10 +455,21 @@ int chain_into(ffx_plan_s* p, const int* axes, bool adjoint, const float2* in, c
 // the per-axis launches.
 int dense_kernel_for(const ffx_plan_s* p, const Axis& ax, int64_t lines) {
   if (ax.form == FFX_FORM_TC) return tc_capable(ax) ? FFX_FORM_TC : FFX_FORM_DENSE;
-  if (ax.form == FFX_FORM_DENSE && (p->flags & FFX_FORM_MASK) == FFX_FORM_AUTO && tc_capable(ax) &&
-      lines >= kDenseFewLines && (ax.N >= 96 || dense_tc_tiles(ax.N, lines) >= 64))
-    return FFX_FORM_TC;
-  return ax.form;
+  if (ax.form != FFX_FORM_DENSE || (p->flags & FFX_FORM_MASK) != FFX_FORM_AUTO || lines < kDenseFewLines)
+    return ax.form;
+  int k = FFX_FORM_DENSE;
+  if (tc_capable(ax) && (ax.N >= 96 || dense_tc_tiles(ax.N, lines) >= 64)) k = FFX_FORM_TC;
+  if (ax.few) {
+    double best = model_cost(ax, k, lines);
+    for (int c : {FFX_FORM_FOLD, FFX_FORM_PAPER}) {
+      const double cc = model_cost(ax, c, lines);
+      if (cc < best) {
+        best = cc;
+        k = c;
+      }
+    }
+  }
+  return k;
 }
 
 int plan_fusion(ffx_plan_s* p) {
@@ -1064,6 +1079,7 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
           if (c == FFX_FORM_TC && !tc_capable(ax)) continue;
           if (model_cost(ax, c, outer * inner) < model_cost(ax, f, outer * inner)) f = c;
         }
+        ax.few = (f == FFX_FORM_DENSE && outer * inner < kDenseFewLines);
       }
       ax.form = f;
     }
