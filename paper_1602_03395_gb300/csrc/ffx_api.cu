@@ -455,8 +455,19 @@ int chain_into(ffx_plan_s* p, const int* axes, bool adjoint, const float2* in, c
 // the per-axis launches.
 int dense_kernel_for(const ffx_plan_s* p, const Axis& ax, int64_t lines) {
   if (ax.form == FFX_FORM_TC) return tc_capable(ax) ? FFX_FORM_TC : FFX_FORM_DENSE;
-  if (ax.form != FFX_FORM_DENSE || (p->flags & FFX_FORM_MASK) != FFX_FORM_AUTO || lines < kDenseFewLines)
+  if ((p->flags & FFX_FORM_MASK) != FFX_FORM_AUTO) return ax.form;
+  if (ax.form == FFX_FORM_PAPER || ax.form == FFX_FORM_FOLD) {
+    // An FFT-form axis (small lam) moves to the tensor cores when the call
+    // fills at least 64 of their items and the dense map on them costs less:
+    // on full calls they reach 8N / 3.5 in the cost model's units (measured
+    // 3.4-4.3 for N = 64 ... 1024), where the model's plan-time figure is
+    // made for a realization's lines alone.
+    if (tc_capable(ax) && dense_tc_tiles(ax.N, lines) >= 64 &&
+        8.0 * ax.N / 3.5 < model_cost(ax, ax.form, lines))
+      return FFX_FORM_TC;
     return ax.form;
+  }
+  if (ax.form != FFX_FORM_DENSE || lines < kDenseFewLines) return ax.form;
   int k = FFX_FORM_DENSE;
   if (tc_capable(ax) && (ax.N >= 96 || dense_tc_tiles(ax.N, lines) >= 64)) k = FFX_FORM_TC;
   if (ax.few) {
