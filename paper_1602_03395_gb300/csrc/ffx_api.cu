@@ -275,7 +275,7 @@ bool tc_capable(const Axis& ax) { return dense_tc_supported(ax.N) && ax.tc_t[0] 
 // handful of lines per realization (a 1-D field) takes an FFT form instead
 // when a call over many lines makes that cheaper (small lam).
 double model_cost(const Axis& ax, int form, int64_t lines);
-int dense_kernel_for(const ffx_plan_s* p, const Axis& ax, int64_t lines);
+int call_form(const ffx_plan_s* p, const Axis& ax, int64_t lines);
 
 // The tensor-core kernel moves 16-byte vectors; other pointers take the SIMT dense kernels.
 bool tc_aligned(const void* in, const void* out_c, const void* out_d) {
@@ -299,7 +299,7 @@ int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* 
   }
   cudaError_t e;
   const int64_t lines = acc ? outer * inner : batch * outer * inner;
-  const int cform = dense_kernel_for(p, ax, lines);  // this call's form
+  const int cform = call_form(p, ax, lines);  // this call's form
   if (cform == FFX_FORM_TC && tc_aligned(in, out_c, out_d)) {
     DenseArgs d;
     std::memset(&d, 0, sizeof(d));
@@ -453,7 +453,7 @@ int chain_into(ffx_plan_s* p, const int* axes, bool adjoint, const float2* in, c
 // the device runs cooperative launches, and one block of the fused kernel fits
 // on every SM; calls with batches up to p->fused use it.  FFX_UNFUSED keeps
 // the per-axis launches.
-int dense_kernel_for(const ffx_plan_s* p, const Axis& ax, int64_t lines) {
+int call_form(const ffx_plan_s* p, const Axis& ax, int64_t lines) {
   if (ax.form == FFX_FORM_TC) return tc_capable(ax) ? FFX_FORM_TC : FFX_FORM_DENSE;
   if ((p->flags & FFX_FORM_MASK) != FFX_FORM_AUTO) return ax.form;
   if (ax.form == FFX_FORM_PAPER || ax.form == FFX_FORM_FOLD) {
@@ -513,7 +513,7 @@ int plan_fusion(ffx_plan_s* p) {
   for (int64_t b = 2; b <= p->fused; ++b) {
     bool all_tc = true;
     for (int k = 0; k < p->ndim; ++k)
-      all_tc = all_tc && dense_kernel_for(p, p->axis[p->order[k]], b * (p->M / Ns[k])) == FFX_FORM_TC;
+      all_tc = all_tc && call_form(p, p->axis[p->order[k]], b * (p->M / Ns[k])) == FFX_FORM_TC;
     if (all_tc) {
       p->fused = b - 1;
       break;
@@ -635,7 +635,7 @@ double model_cost(const Axis& ax, int form, int64_t lines) {
     // the tensor-core form runs 3x the real flops at ~6x the FP32 rate
     // (measured 1.9-2.3 in these units for N = 64 .. 1024 on full passes);
     // 64-point axes stay dense at plan time and move to the tensor cores per
-    // call when the call is large (see dense_kernel_for)
+    // call when the call is large (see call_form)
     case FFX_FORM_TC:
       if (lines < 128) return 1e30;
       return N < 128 ? 8 * N / 0.40 : 8 * N / 2.0;
@@ -1222,7 +1222,7 @@ int ffx_plan_call_form(ffx_plan_t p, int axis, int64_t batch) {
   int64_t outer, inner;
   axis_outer_inner(p, axis, &outer, &inner);
   const int64_t lines = (p->acc && axis == p->order[p->ndim - 1] ? 1 : batch) * outer * inner;
-  return dense_kernel_for(p, p->axis[axis], lines);
+  return call_form(p, p->axis[axis], lines);
 }
 
 // The forward passes in the order `axes`, the last one writing densities
