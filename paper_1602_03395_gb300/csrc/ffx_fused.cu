@@ -313,13 +313,15 @@ constexpr int kFusedThreads = 512;
 // head products in one TMEM accumulator, the cross terms in a second.  Work
 // item = 128 lines (MMA M) x 32 real rows (MMA N = 16 complex outputs); block
 // b owns row block b % 4 for the whole launch, so it keeps only that 32-row
-// slice of each T_j (32 KB per axis) in shared memory.  Per item: 256 threads
-// load the 128 lines from L2 (16-byte loads, coalesced along either memory
-// order), split them into the core-matrix layout (bank-conflict free), one
-// thread issues 16 K-steps x 2 tcgen05.mma (N = 64 over the slice's head and
-// tail rows for X_hi, N = 32 for X_lo) and commits to an mbarrier, and
-// eight warps read the accumulators back (warp w: lane quarter w % 4, column
-// half w / 4) and store.  Summing |.|^2 over the batch stays in registers.
+// slice of each T_j (32 KB per axis) in shared memory.  Per item: each thread
+// loads half of one line from L2 into registers and writes its values and
+// tails into tensor memory (lane = line), where the MMAs read their A operand
+// (shared memory then carries only T: reading both operands from it bounded
+// the products); one thread issues 16 K-steps x 2 tcgen05.mma (N = 64 over the
+// slice's head and tail rows for X_hi, N = 32 for X_lo) and commits to an
+// mbarrier, and eight warps read the accumulators back (warp w: lane quarter
+// w % 4, column half w / 4) and store.  Summing |.|^2 over the batch stays in
+// registers.
 // ---------------------------------------------------------------------------
 
 constexpr int FT_N = 64;                       // points per line, every axis
@@ -329,11 +331,20 @@ constexpr int FT_ROWS = 32;                    // real rows per item = MMA N
 constexpr int FT_RB = FT_K / FT_ROWS;          // row blocks
 constexpr int FT_THREADS = 256;
 constexpr int FT_SBO = (FT_K / 4) * 128;       // 4096: between 8-row groups
-constexpr int FT_X_PART = FT_LINES * FT_K * 4;  // 64 KB per split part
 constexpr int FT_TS_PART = FT_ROWS * FT_K * 4;  // 16 KB
 constexpr int FT_TS_BYTES = 2 * FT_TS_PART;     // one row block's slice, head and tail
-constexpr int FT_SMEM = 2 * FT_X_PART + 3 * FT_TS_BYTES;  // 224 KB
-constexpr int FT_COLS = 2 * FT_ROWS;            // head accumulator, cross-term accumulator
+constexpr int FT_SMEM_USED = 3 * FT_TS_BYTES;   // 96 KB: the T slices (the input lives in tensor memory)
+// requested per block: more than half an SM's shared memory, so that no two
+// blocks share an SM (each allocates all 512 tensor-memory columns, and the
+// grid barrier needs every block running)
+constexpr int FT_SMEM = 160 * 1024;
+static_assert(FT_SMEM >= FT_SMEM_USED && 2 * FT_SMEM > 228 * 1024, "one block per SM");
+// Tensor memory: head and cross-term accumulators (FT_ROWS columns each), then
+// the item's input as the MMAs' A operand, one line per lane: its FP32 values
+// (head: an MMA of kind::tf32 reads only their TF32 bits) and its tails.
+constexpr int FT_A_HI = 128, FT_A_LO = FT_A_HI + FT_K;
+constexpr int FT_COLS = 512;                    // allocation (a power of two >= FT_A_LO + FT_K)
+static_assert(FT_A_LO + FT_K <= FT_COLS && 2 * FT_ROWS <= FT_A_HI, "tensor-memory layout");
 constexpr uint32_t kIdescFT = tc::idesc_tf32(FT_LINES, FT_ROWS);
 // the slice's head and tail rows are contiguous 8-row groups: one N = 64
 // product forms X_hi T_hi and X_hi T_lo side by side in the two accumulators
@@ -342,9 +353,7 @@ constexpr uint32_t kIdescFT2 = tc::idesc_tf32(FT_LINES, 2 * FT_ROWS);
 __global__ void __launch_bounds__(FT_THREADS, 1) fused_tc_kernel(const FusedArgs a) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char fts[];
-  unsigned char* xh = fts;
-  unsigned char* xl = fts + FT_X_PART;
-  unsigned char* tsl = fts + 2 * FT_X_PART;
+  unsigned char* tsl = fts;
   __shared__ __align__(8) uint64_t tbar, mbar, dbar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int s_abort;
@@ -401,70 +410,59 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fused_tc_kernel(const FusedArgs
 #pragma unroll
       for (int m = 0; m < 8; ++m) racc[m] = 0.f;
       for (int b = 0; b < nb && !s_abort; ++b) {
-        // ---- 128 lines of the item into shared memory, split
-        if (contiguous) {
-          // 8 lines x 4 k-pairs per warp and step: 64 contiguous bytes per line
-          const int l0 = (lane & 7) + 8 * warp;
-          const long long b0 = fused_line(P, ct * FT_LINES + l0, b);
-          const long long b1 = fused_line(P, ct * FT_LINES + l0 + 64, b);
-          float4 v[16];
+        // ---- the item's 128 lines into tensor memory, split: warp w writes the
+        // lanes (lines) of its quarter w % 4 and the K half w / 4; every load
+        // of the thread is issued before the first store
+        {
+          const int q = warp & 3, h = warp >> 2;
+          const long long base = fused_line(P, ct * FT_LINES + 32 * q + lane, b);
+          float x[64];  // complex points 32 h .. 32 h + 31 of the line, (re, im)
+          if (contiguous) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const long long base = (i & 1) ? b1 : b0;
-            const int kp = (lane >> 3) + 4 * (i >> 1);
-            v[i] = base >= 0 ? __ldcg(reinterpret_cast<const float4*>(P.in + base + 2 * kp))
-                             : make_float4(0.f, 0.f, 0.f, 0.f);
-          }
+            for (int j = 0; j < 16; ++j) {
+              const float4 v = base >= 0 ? __ldcg(reinterpret_cast<const float4*>(P.in + base + 32 * h + 2 * j))
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+              x[4 * j] = v.x;
+              x[4 * j + 1] = v.y;
+              x[4 * j + 2] = v.z;
+              x[4 * j + 3] = v.w;
+            }
+          } else {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int line = l0 + 64 * (i & 1), kp = (lane >> 3) + 4 * (i >> 1);
-            const int off = (line >> 3) * FT_SBO + kp * 128 + (line & 7) * 16;
-            const float4 hi = make_float4(tf32_head(v[i].x), tf32_head(v[i].y), tf32_head(v[i].z), tf32_head(v[i].w));
-            *reinterpret_cast<float4*>(xh + off) = hi;
-            *reinterpret_cast<float4*>(xl + off) =
-                make_float4(v[i].x - hi.x, v[i].y - hi.y, v[i].z - hi.z, v[i].w - hi.w);
-          }
-        } else {
-          // 32 consecutive lines per warp and k-pair: coalesced along the lines
-          const int line = lane + 32 * (warp & 3);
-          const long long base = fused_line(P, ct * FT_LINES + line, b);
-          float4 v[16];
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int kp = (warp >> 2) + 2 * i;
-            v[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (base >= 0) {
-              const float2 p0 = __ldcg(P.in + base + (int64_t)(2 * kp) * inner);
-              const float2 p1 = __ldcg(P.in + base + (int64_t)(2 * kp + 1) * inner);
-              v[i] = make_float4(p0.x, p0.y, p1.x, p1.y);
+            for (int j = 0; j < 32; ++j) {
+              const float2 v = base >= 0 ? __ldcg(P.in + base + (int64_t)(32 * h + j) * inner) : make_float2(0.f, 0.f);
+              x[2 * j] = v.x;
+              x[2 * j + 1] = v.y;
             }
           }
+          const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(64 * h);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int kp = (warp >> 2) + 2 * i;
-            const int off = (line >> 3) * FT_SBO + kp * 128 + (line & 7) * 16;
-            const float4 hi = make_float4(tf32_head(v[i].x), tf32_head(v[i].y), tf32_head(v[i].z), tf32_head(v[i].w));
-            *reinterpret_cast<float4*>(xh + off) = hi;
-            *reinterpret_cast<float4*>(xl + off) =
-                make_float4(v[i].x - hi.x, v[i].y - hi.y, v[i].z - hi.z, v[i].w - hi.w);
+          for (int g = 0; g < 4; ++g) {
+            uint32_t hi[16], lo[16];
+#pragma unroll
+            for (int m = 0; m < 16; ++m) {
+              const float v = x[16 * g + m];
+              hi[m] = __float_as_uint(v);
+              lo[m] = __float_as_uint(v - tf32_head(v));
+            }
+            tmem_st16(trow + FT_A_HI + 16 * g, hi);
+            tmem_st16(trow + FT_A_LO + 16 * g, lo);
           }
+          tmem_wait_st();
         }
-        fence_async_smem();
         tc_fence_before();
         __syncthreads();
         // ---- the product: 16 K-steps x 3 split products in 2 MMAs
         if (tid == 0 && !slices) slices = mbar_wait(smem_u32(&tbar), 0u, &s_abort);  // under the first load
         if (tid == 0 && slices) {
           tc_fence_after();
-          const uint32_t ah = smem_u32(xh), al = smem_u32(xl);
 #pragma unroll 4
           for (int ks = 0; ks < FT_K / 8; ++ks) {
-            const uint32_t o = (uint32_t)(ks * 256);
-            const uint64_t dxh = make_desc(ah + o, 128, FT_SBO), dxl = make_desc(al + o, 128, FT_SBO);
-            const uint64_t dth = make_desc(th + o, 128, FT_SBO);
+            const uint64_t dth = make_desc(th + (uint32_t)(ks * 256), 128, FT_SBO);
             const uint32_t more = ks > 0 ? 1u : 0u;
-            mma_tf32(tmem, dxh, dth, kIdescFT2, more);         // [X_hi T_hi | X_hi T_lo]
-            mma_tf32(tmem + FT_ROWS, dxl, dth, kIdescFT, 1u);  // + X_lo T_hi
+            // A from tensor memory: K columns 8 ks .. 8 ks + 7 of the head and tail
+            mma_tf32_ts(tmem, tmem + FT_A_HI + 8 * ks, dth, kIdescFT2, more);         // [X_hi T_hi | X_hi T_lo]
+            mma_tf32_ts(tmem + FT_ROWS, tmem + FT_A_LO + 8 * ks, dth, kIdescFT, 1u);  // + X_lo T_hi
           }
           mma_commit(smem_u32(&mbar));
           issued = true;
