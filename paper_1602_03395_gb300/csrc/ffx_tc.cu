@@ -603,6 +603,179 @@ __global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Lines of 64 points with T resident (plain forward and adjoint passes): the
+// input operand in tensor memory, one block per SM, no pipeline stages.  An
+// item is 128 lines x all 128 real rows.  Per item every thread has half a
+// line in registers (loaded during the previous item), writes its values and
+// tails into tensor memory (lane = line), and issues the next item's loads;
+// one thread runs 16 K-steps x 2 MMAs (A from tensor memory, T from shared
+// memory: [X_hi T_hi | X_hi T_lo] at N = 256, then X_lo T_hi); all eight warps
+// read the accumulators back and store.
+// ---------------------------------------------------------------------------
+constexpr int R64_THREADS = 256;
+constexpr int R64_A_HI = 2 * ROWS, R64_A_LO = R64_A_HI + 2 * 64;  // after the accumulator pair
+constexpr uint32_t kIdescRows = idesc_tf32(LINES, ROWS);
+
+__global__ void __launch_bounds__(R64_THREADS, 1)
+    dense64_tm_kernel(const DenseArgs a, const unsigned char* __restrict__ Tblk, int* err) {
+  extern __shared__ __align__(1024) unsigned char tsm[];  // T: RES_CHUNKS chunks of [head | tail]
+  __shared__ __align__(8) uint64_t tbar, mbar, dbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t items = (a.ncols + LINES - 1) / LINES;
+  if ((int64_t)blockIdx.x >= items) return;
+  const int64_t my_items = (items - blockIdx.x + gridDim.x - 1) / gridDim.x;
+
+  if (warp == 0) tmem_alloc(&tmem_slot, 512);
+  if (tid == 0) {
+    s_abort = 0;
+    mbar_init(smem_u32(&tbar), 1);
+    mbar_init(smem_u32(&mbar), 1);
+    mbar_init(smem_u32(&dbar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(smem_u32(&tbar), (uint32_t)(RES_CHUNKS * T_CHUNK));
+    for (int c = 0; c < RES_CHUNKS; ++c)
+      bulk_g2s(smem_u32(tsm + c * T_CHUNK), Tblk + (size_t)c * T_CHUNK, T_CHUNK, smem_u32(&tbar));
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t smem_base = smem_u32(tsm);
+
+  const int q = warp & 3, h = warp >> 2;  // lanes 32 q .. + 31 (lines), points 32 h .. + 31
+  const int64_t inner = a.inner;
+  const bool contiguous = (inner == 1);
+  // line c of the pass: offset of its first point, or -1 past the end
+  auto line_base = [&](int64_t c) -> long long {
+    if (c >= a.ncols) return -1;
+    const int64_t bo = c / inner, i = c - bo * inner;
+    return bo * 64 * inner + i;
+  };
+  float x[64];
+  long long base = line_base((int64_t)blockIdx.x * LINES + 32 * q + lane);
+  auto load = [&](long long bs) {
+    if (contiguous) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float4 v = bs >= 0 ? __ldcg(reinterpret_cast<const float4*>(a.in + bs + 32 * h + 2 * j))
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+        x[4 * j] = v.x;
+        x[4 * j + 1] = v.y;
+        x[4 * j + 2] = v.z;
+        x[4 * j + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float2 v = bs >= 0 ? __ldcg(a.in + bs + (int64_t)(32 * h + j) * inner) : make_float2(0.f, 0.f);
+        x[2 * j] = v.x;
+        x[2 * j + 1] = v.y;
+      }
+    }
+  };
+  load(base);
+  uint32_t phase = 0;
+  bool slices = false, issued = false;
+  const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
+  for (int64_t it = 0; it < my_items && !s_abort; ++it) {
+    const int64_t ct = blockIdx.x + it * gridDim.x;
+    const long long cur = base;
+    // this item's values and tails into tensor memory (the previous item's MMAs are done)
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      uint32_t hi[16], lo[16];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const float v = x[16 * g + m];
+        hi[m] = __float_as_uint(v);
+        lo[m] = __float_as_uint(v - tf32_head(v));
+      }
+      tmem_st16(trow + R64_A_HI + 64 * h + 16 * g, hi);
+      tmem_st16(trow + R64_A_LO + 64 * h + 16 * g, lo);
+    }
+    tmem_wait_st();
+    tc_fence_before();
+    __syncthreads();
+    // the next item's lines, in flight during this item's product and stores
+    if (it + 1 < my_items) {
+      base = line_base((ct + gridDim.x) * LINES + 32 * q + lane);
+      load(base);
+    }
+    if (tid == 0 && !slices) slices = mbar_wait(smem_u32(&tbar), 0u, &s_abort);
+    if (tid == 0 && slices) {
+      tc_fence_after();
+#pragma unroll 4
+      for (int ks = 0; ks < (2 * 64) / 8; ++ks) {
+        const uint32_t th = smem_base + (uint32_t)((ks >> 2) * T_CHUNK + (ks & 3) * 2 * CORE_LBO);
+        const uint64_t dth = make_desc(th, CORE_LBO, CHUNK_SBO);
+        const uint32_t more = ks > 0 ? 1u : 0u;
+        mma_tf32_ts(tmem, tmem + R64_A_HI + 8 * ks, dth, kIdescStack, more);     // [X_hi T_hi | X_hi T_lo]
+        mma_tf32_ts(tmem + ROWS, tmem + R64_A_LO + 8 * ks, dth, kIdescRows, 1u);  // + X_lo T_hi
+      }
+      mma_commit(smem_u32(&mbar));
+      issued = true;
+    }
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&mbar), phase, &s_abort));
+    phase ^= 1u;
+    if (!ok) break;
+    tc_fence_after();
+    // accumulators: warp (q, h) reads real rows 64 h .. 64 h + 63 of its 32 lines
+#pragma unroll 1
+    for (int j0 = 0; j0 < 64; j0 += 16) {
+      uint32_t x1[16], x2[16];
+      tmem_ld16(trow + (uint32_t)(64 * h + j0), x1);
+      tmem_ld16(trow + (uint32_t)(ROWS + 64 * h + j0), x2);
+      tmem_wait_ld();
+      if (cur < 0) continue;
+      float y[16];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) y[m] = __uint_as_float(x1[m]) + __uint_as_float(x2[m]);
+      const int n0 = 32 * h + j0 / 2;  // complex outputs n0 .. n0 + 7
+      if (a.out_c) {
+        if (contiguous) {
+          float4* o = reinterpret_cast<float4*>(a.out_c + cur + n0);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) o[m] = make_float4(y[4 * m], y[4 * m + 1], y[4 * m + 2], y[4 * m + 3]);
+        } else {
+#pragma unroll
+          for (int m = 0; m < 8; ++m) a.out_c[cur + (int64_t)(n0 + m) * inner] = make_float2(y[2 * m], y[2 * m + 1]);
+        }
+      } else {
+        float dd[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) dd[m] = y[2 * m] * y[2 * m] + y[2 * m + 1] * y[2 * m + 1];
+        if (contiguous) {
+          float4* o = reinterpret_cast<float4*>(a.out_d + cur + n0);
+          o[0] = make_float4(dd[0], dd[1], dd[2], dd[3]);
+          o[1] = make_float4(dd[4], dd[5], dd[6], dd[7]);
+        } else {
+#pragma unroll
+          for (int m = 0; m < 8; ++m) a.out_d[cur + (int64_t)(n0 + m) * inner] = dd[m];
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();  // accumulators read before the next item's product
+  }
+  if (tid == 0) {
+    if (issued) {
+      mma_commit(smem_u32(&dbar));
+      mbar_wait_own(smem_u32(&dbar), 0u, &s_abort);
+    }
+    mbar_wait_own(smem_u32(&tbar), 0u, &s_abort);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && s_abort && err) atomicAdd(err, 1);
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_free(tmem, 512);
+  }
+}
+
 // Pre-split T chunks from the complex map T [N][N]: for row block mt and K
 // chunk kc, a 32 KB block [head: 128 rows x 32 K][tail] in core-matrix order;
 // real (r, k') with r = 2n + p_out, k' = 2k + p_in holds the 2 x 2 block
@@ -644,6 +817,8 @@ cudaError_t dense_tc_prepare() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(dense_tc_kernel<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              TcLayout<true>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(dense64_tm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, RES_CHUNKS * T_CHUNK);
   return e;
 }
 size_t dense_tc_t_bytes(int N) {
@@ -657,7 +832,12 @@ cudaError_t launch_dense_tc(const DenseArgs& a, const unsigned char* Tblk, int* 
   P.a = a;
   P.tblk = Tblk;
   P.err = err;
-  if (a.N == 64 && !a.acc && !a.grad) {
+  const int64_t items = (a.ncols + LINES - 1) / LINES;
+  if (a.N == 64 && !a.acc && !a.grad && items <= 4 * (int64_t)grid) {
+    // a few items per block: the input operand in tensor memory, no pipeline
+    // to fill (measured 7-14% faster at up to ~2 items per SM, 6% slower at 13)
+    dense64_tm_kernel<<<grid, R64_THREADS, RES_CHUNKS * T_CHUNK, stream>>>(a, Tblk, err);
+  } else if (a.N == 64 && !a.acc && !a.grad) {
     // T (128 KB) stays in shared memory for the whole launch
     dense_tc_kernel<true, false, true><<<grid, NTHREADS, TcLayout<true>::SMEM, stream>>>(P);
   } else {
