@@ -11,7 +11,8 @@ L2.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ffx|reference]
                   [--workload two_cloud|1d|quasicondensate|large_two_cloud|
-                   large_quasicondensate] [--form auto|paper|fold]
+                   large_quasicondensate|mixed] [--form auto|paper|fold|dense|tc]
+                  [--unsplit] [--batch B] [--column AXIS] [--no-cpu-baseline]
 
 Multi-GPU (torchrun, one rank per GPU): realizations are independent, so each
 rank expands its own share with no collective on the data path (weak
@@ -88,11 +89,17 @@ def parse():
                     choices=["two_cloud", "1d", "quasicondensate", "large_two_cloud",
                              "large_quasicondensate", "mixed"])
     ap.add_argument("--form", default="auto", choices=["auto", "paper", "fold", "dense", "tc"])
+    ap.add_argument("--unsplit", action="store_true",
+                    help="with --form tc: one TF32 product on rounded operands (reported variant, "
+                         "density error of order 1e-3)")
     ap.add_argument("--batch", type=int, default=None, help="realizations per step (default: workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--column", type=int, default=None, metavar="AXIS",
                     help="output the detector image: the density integrated along AXIS (Sec. 6)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.unsplit and (args.form != "tc" or args.workload == "mixed"):
+        ap.error("--unsplit needs --form tc and a single-lattice workload")
+    return args
 
 
 def workload(name, batch):
@@ -562,7 +569,7 @@ def run_ffx(args):
     w = workload(args.workload, args.batch)
     B_ = w.batch
     M = int(np.prod(w.dims))
-    plan = ffx.Plan(w.dims, w.dx, w.t, w.lam, form=args.form)
+    plan = ffx.Plan(w.dims, w.dx, w.t, w.lam, form=args.form, unsplit=args.unsplit)
     form = plan.form
     order = plan.pass_order()
     launches = plan.launches_per_call(batch=B_)
@@ -716,7 +723,8 @@ def run_ffx(args):
         tc_peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1900.0))) * 1.1 / 2.25
         roofline = {"bound": "tensor", "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
                     "frac": achieved / tc_peak, "traffic": traffic, "kernel": kernel_key,
-                    "launch_ms": mean_ms[dom], "launch_time": launch_time, "executed_tflops": 3 * achieved,
+                    "launch_ms": mean_ms[dom], "launch_time": launch_time,
+                    "executed_tflops": (1 if args.unsplit else 3) * achieved,
                     "peak_source": f"bf16_tflops_sustained x 1.1/2.25 (TF32 dense : BF16 dense, nominal), {pk_src}"}
     else:
         roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak,
@@ -729,7 +737,7 @@ def run_ffx(args):
 
     # end to end through the C ABI with host buffers: pinned H2D, expand, D2H
     # per step, two lanes (see pipelined_e2e)
-    plan2 = ffx.Plan(w.dims, w.dx, w.t, w.lam, form=args.form)
+    plan2 = ffx.Plan(w.dims, w.dx, w.t, w.lam, form=args.form, unsplit=args.unsplit)
     if args.column is None:
         def call_pl(pl, x, out):
             return ffx.ffx_expand(pl, x, out)
@@ -806,6 +814,9 @@ def run_ffx(args):
                        "lam": list(w.lam), "t": w.t, "batch_per_gpu": B_, "form": form,
                        "axis_forms": list(plan.axis_forms), "call_forms": list(call_forms),
                        "fused_one_launch": bool(fused_call),
+                       "precision": ("TF32 unsplit: one product on rounded operands (reported variant; "
+                                     "density error of order 1e-3)" if args.unsplit else
+                                     "split TF32 on the tensor cores (three products), else FP32"),
                        "output": ("density" if args.column is None else
                                   f"detector image: density integrated along axis {args.column}"),
                        "parallelism": f"replicas x{world} (realizations sharded, no collective)",

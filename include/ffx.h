@@ -92,6 +92,13 @@ extern "C" {
  * launch (one block per SM, the d passes separated by grid-wide barriers,
  * every T_j resident in shared memory); same arithmetic, same results. */
 #define FFX_UNFUSED     0x40u
+/* With FFX_FORM_TC only: one tensor-core product per K-step, with the input
+ * and T_j rounded to TF32 (round to nearest) and no tails.  A faster and less
+ * accurate variant, reported beside the split one: its density error is of
+ * order 1e-3 against the 2e-5 of the split products.  Such plans never fuse
+ * their passes into one launch, and axes the tensor cores do not take keep
+ * the FP32 dense form.  Any other form with this flag: FFX_EINVAL. */
+#define FFX_TC_UNSPLIT  0x80u
 
 typedef struct ffx_plan_s* ffx_plan_t;
 

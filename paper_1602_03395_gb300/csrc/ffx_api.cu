@@ -313,6 +313,7 @@ int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* 
     d.M = p->M;
     d.batch = batch;
     d.acc = acc;
+    d.unsplit = (p->flags & FFX_TC_UNSPLIT) ? 1 : 0;
     d.ncols = acc ? outer * inner : batch * outer * inner;
     d.N = ax.N;
     int64_t grid = dense_tc_tiles(ax.N, d.ncols);
@@ -485,7 +486,7 @@ int call_form(const ffx_plan_s* p, const Axis& ax, int64_t lines) {
 
 int plan_fusion(ffx_plan_s* p) {
   p->fused = 0;
-  if (p->ndim < 2 || (p->flags & FFX_UNFUSED) || !p->grid_bar) return FFX_OK;
+  if (p->ndim < 2 || (p->flags & (FFX_UNFUSED | FFX_TC_UNSPLIT)) || !p->grid_bar) return FFX_OK;
   int Ns[3];
   for (int k = 0; k < p->ndim; ++k) {
     const Axis& ax = p->axis[p->order[k]];
@@ -792,10 +793,12 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
   if (ndim < 1 || ndim > 3) return fail(FFX_EINVAL, "ndim must be 1..3, got %d", ndim);
   if (!dims || !spacing || !magnification) return fail(FFX_EINVAL, "dims/spacing/magnification is NULL");
   if (!std::isfinite(t)) return fail(FFX_EINVAL, "t must be finite");
-  const uint32_t known = FFX_FORM_MASK | FFX_ACCUMULATE | FFX_TUNE | FFX_UNFUSED;
+  const uint32_t known = FFX_FORM_MASK | FFX_ACCUMULATE | FFX_TUNE | FFX_UNFUSED | FFX_TC_UNSPLIT;
   if (flags & ~known) return fail(FFX_EINVAL, "unknown flag bits 0x%x", flags & ~known);
   const uint32_t form = flags & FFX_FORM_MASK;
   if (form > FFX_FORM_TC) return fail(FFX_EINVAL, "unknown form %u", form);
+  if ((flags & FFX_TC_UNSPLIT) && form != FFX_FORM_TC)
+    return fail(FFX_EINVAL, "FFX_TC_UNSPLIT needs FFX_FORM_TC");
   int64_t M = 1;
   for (int j = 0; j < ndim; ++j) {
     if (dims[j] < 1) return fail(FFX_EINVAL, "dims[%d] = %lld < 1", j, (long long)dims[j]);

@@ -93,6 +93,7 @@ struct DenseArgs {
   int64_t ncols;       // columns (lines) covered by the tile grid
   int N;
   int acc, grad_shared;
+  int unsplit;  // tensor-core kernels: one TF32 product (operands rounded, no tails)
 };
 const void* dense_kernel_func();
 cudaError_t launch_dense(const DenseArgs& a, int grid, cudaStream_t stream);

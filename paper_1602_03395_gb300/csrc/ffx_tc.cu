@@ -245,6 +245,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P)
     my_items = (items - blockIdx.x + gridDim.x - 1) / gridDim.x;
   }
   if (my_items <= 0) return;
+  // one product per K-step: X and T rounded to TF32, no tails (a reported,
+  // less accurate variant)
+  const bool unsplit = !MANY && P.a.unsplit;
 
   if (warp == MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -382,9 +385,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P)
         // the row block's rows that exist, head and tail parts
         const uint32_t part = (uint32_t)(FULL ? ROWS : row_count(cv.N, cv.mt)) * (TKC * 4);
         const uint32_t cb = smem_u32(&copy_bar[s]);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cb), "r"(2 * part) : "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(cb),
+                     "r"(unsplit ? part : 2 * part)
+                     : "memory");
         const unsigned char* src = cv.tblk + ((size_t)cv.mt * kchunks + kc) * T_CHUNK;
-        if (part == (uint32_t)T_PART) {
+        if (unsplit) {
+          bulk_g2s(smem_u32(st), src, part, cb);  // the head rows only
+        } else if (part == (uint32_t)T_PART) {
           bulk_g2s(smem_u32(st), src, T_CHUNK, cb);  // a whole row block: head and tail in one copy
         } else {
           bulk_g2s(smem_u32(st), src, part, cb);
@@ -417,7 +424,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P)
           n = t & (LINES - 1);
           kp = (t >> 7) * PITEMS + i;
         }
-        split_store(xh, xl, (n >> 3) * CHUNK_SBO + kp * CORE_LBO + (n & 7) * 16, v);
+        const int off = (n >> 3) * CHUNK_SBO + kp * CORE_LBO + (n & 7) * 16;
+        if (unsplit)
+          *reinterpret_cast<float4*>(xh + off) =
+              make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
+        else
+          split_store(xh, xl, off, v);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(smem_u32(&full_bar[s]));
@@ -477,6 +489,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P)
               const uint64_t dth = make_desc(th + o, CORE_LBO, CHUNK_SBO);
               const uint64_t dtl = make_desc(tl + o, CORE_LBO, CHUNK_SBO);
               const uint32_t more = (kc == 0 && ks == 0) ? 0u : 1u;
+              if (unsplit) {
+                mma_tf32(d1, dxh, dth, idesc, more);
+                continue;
+              }
               if (RES) {
                 // resident T (a whole row block): the chunk's head and tail rows are
                 // contiguous 8-row groups, so one N = 256 product forms [X_hi T_hi |
@@ -529,11 +545,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P)
         for (int j0 = 0; j0 < rows; j0 += 16) {
           uint32_t x[16], z[16];
           tmem_ld16(taddr + (uint32_t)j0, x);
-          tmem_ld16(taddr + (uint32_t)(ROWS + j0), z);
+          if (!unsplit) tmem_ld16(taddr + (uint32_t)(ROWS + j0), z);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
           float y[16];
+          if (unsplit) {
 #pragma unroll
-          for (int m = 0; m < 16; ++m) y[m] = __uint_as_float(x[m]) + __uint_as_float(z[m]);
+            for (int m = 0; m < 16; ++m) y[m] = __uint_as_float(x[m]);
+          } else {
+#pragma unroll
+            for (int m = 0; m < 16; ++m) y[m] = __uint_as_float(x[m]) + __uint_as_float(z[m]);
+          }
           const int n0 = nbase + j0 / 2;  // complex outputs n0 .. n0 + 7 of this line
           if (ev.acc) {
 #pragma unroll
@@ -611,7 +632,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P)
 // tails into tensor memory (lane = line), and issues the next item's loads;
 // one thread runs 16 K-steps x 2 MMAs (A from tensor memory, T from shared
 // memory: [X_hi T_hi | X_hi T_lo] at N = 256, then X_lo T_hi); all eight warps
-// read the accumulators back and store.
+// read the accumulators back and store.  Unsplit launches write the values
+// rounded to TF32 and run one product per K-step.
 // ---------------------------------------------------------------------------
 constexpr int R64_THREADS = 256;
 constexpr int R64_A_HI = 2 * ROWS, R64_A_LO = R64_A_HI + 2 * 64;  // after the accumulator pair
@@ -684,17 +706,27 @@ __global__ void __launch_bounds__(R64_THREADS, 1)
     const int64_t ct = blockIdx.x + it * gridDim.x;
     const long long cur = base;
     // this item's values and tails into tensor memory (the previous item's MMAs are done)
+    if (a.unsplit) {
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      uint32_t hi[16], lo[16];
+      for (int g = 0; g < 4; ++g) {
+        uint32_t hi[16];
 #pragma unroll
-      for (int m = 0; m < 16; ++m) {
-        const float v = x[16 * g + m];
-        hi[m] = __float_as_uint(v);
-        lo[m] = __float_as_uint(v - tf32_head(v));
+        for (int m = 0; m < 16; ++m) hi[m] = __float_as_uint(tf32_round(x[16 * g + m]));
+        tmem_st16(trow + R64_A_HI + 64 * h + 16 * g, hi);
       }
-      tmem_st16(trow + R64_A_HI + 64 * h + 16 * g, hi);
-      tmem_st16(trow + R64_A_LO + 64 * h + 16 * g, lo);
+    } else {
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        uint32_t hi[16], lo[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          const float v = x[16 * g + m];
+          hi[m] = __float_as_uint(v);
+          lo[m] = __float_as_uint(v - tf32_head(v));
+        }
+        tmem_st16(trow + R64_A_HI + 64 * h + 16 * g, hi);
+        tmem_st16(trow + R64_A_LO + 64 * h + 16 * g, lo);
+      }
     }
     tmem_wait_st();
     tc_fence_before();
@@ -712,8 +744,12 @@ __global__ void __launch_bounds__(R64_THREADS, 1)
         const uint32_t th = smem_base + (uint32_t)((ks >> 2) * T_CHUNK + (ks & 3) * 2 * CORE_LBO);
         const uint64_t dth = make_desc(th, CORE_LBO, CHUNK_SBO);
         const uint32_t more = ks > 0 ? 1u : 0u;
-        mma_tf32_ts(tmem, tmem + R64_A_HI + 8 * ks, dth, kIdescStack, more);     // [X_hi T_hi | X_hi T_lo]
-        mma_tf32_ts(tmem + ROWS, tmem + R64_A_LO + 8 * ks, dth, kIdescRows, 1u);  // + X_lo T_hi
+        if (a.unsplit) {
+          mma_tf32_ts(tmem, tmem + R64_A_HI + 8 * ks, dth, kIdescRows, more);  // X T, rounded operands
+        } else {
+          mma_tf32_ts(tmem, tmem + R64_A_HI + 8 * ks, dth, kIdescStack, more);     // [X_hi T_hi | X_hi T_lo]
+          mma_tf32_ts(tmem + ROWS, tmem + R64_A_LO + 8 * ks, dth, kIdescRows, 1u);  // + X_lo T_hi
+        }
       }
       mma_commit(smem_u32(&mbar));
       issued = true;
@@ -727,12 +763,17 @@ __global__ void __launch_bounds__(R64_THREADS, 1)
     for (int j0 = 0; j0 < 64; j0 += 16) {
       uint32_t x1[16], x2[16];
       tmem_ld16(trow + (uint32_t)(64 * h + j0), x1);
-      tmem_ld16(trow + (uint32_t)(ROWS + 64 * h + j0), x2);
+      if (!a.unsplit) tmem_ld16(trow + (uint32_t)(ROWS + 64 * h + j0), x2);
       tmem_wait_ld();
       if (cur < 0) continue;
       float y[16];
+      if (a.unsplit) {
 #pragma unroll
-      for (int m = 0; m < 16; ++m) y[m] = __uint_as_float(x1[m]) + __uint_as_float(x2[m]);
+        for (int m = 0; m < 16; ++m) y[m] = __uint_as_float(x1[m]);
+      } else {
+#pragma unroll
+        for (int m = 0; m < 16; ++m) y[m] = __uint_as_float(x1[m]) + __uint_as_float(x2[m]);
+      }
       const int n0 = 32 * h + j0 / 2;  // complex outputs n0 .. n0 + 7
       if (a.out_c) {
         if (contiguous) {

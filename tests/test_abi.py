@@ -55,6 +55,11 @@ def test_host_argument_checks(lib):
     assert h.value is None
     lib.ffx_last_error.restype = ctypes.c_char_p
     assert b"flag" in lib.ffx_last_error()
+    # the unsplit tensor-core variant exists for the tensor-core form only
+    for form in (0x0, 0x2, 0x3):
+        assert lib.ffx_plan(ctypes.byref(h), 1, dims, dx, ctypes.c_double(1.0), lam, None, None, 0x80 | form) == 1
+        assert b"FFX_FORM_TC" in lib.ffx_last_error()
+    assert h.value is None
     lib.ffx_error_string.restype = ctypes.c_char_p
     assert lib.ffx_error_string(1) == b"invalid argument"
     lib.ffx_supported_length.argtypes = [ctypes.c_int64]

@@ -1,0 +1,67 @@
+"""The unsplit tensor-core variant (FFX_TC_UNSPLIT): one TF32 product per
+K-step on operands rounded to TF32, reported beside the split products.
+
+Bound: rounding both operands to TF32 (unit roundoff u = 2^-11) gives each
+product a relative error of at most 2u.  With independent roundings the
+field's relative L2 error after one pass is about sqrt(2/3) u (4e-4), after d
+passes about sqrt(d) times that, and the density's about twice the field's:
+~1.4e-3 for d = 3.  The tests hold the density to 4e-3 and check that the
+result is not the split one (the variant really ran)."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_common import random_field, rel_l2, require_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+UNSPLIT_TOL = 4e-3
+
+
+@pytest.fixture(scope="module")
+def ffx():
+    return require_gpu()
+
+
+def run(ffx, dims, dx, t, lam, psi, unsplit, **kw):
+    with ffx.Plan(dims, dx, t, lam, form="tc", unsplit=unsplit, **kw) as plan:
+        rho = ffx.ffx_expand(plan, to_dev(psi)).cpu().numpy()
+        assert plan.device_errors() == 0
+        return rho, plan.fused_max_batch
+
+
+@pytest.mark.parametrize("dims,lam,batch", [
+    ((64, 64, 64), (30, 30, 3), 2),     # 64-point passes, input operand in tensor memory
+    ((64, 64, 64), (30, 30, 3), 40),    # 64-point passes, pipelined kernel with T resident
+    ((128, 16, 192), (9, 4, 3), 1),     # streamed T, whole row blocks (the 16-point axis: FP32)
+    ((96, 48, 32), (10, 6, 4), 2),      # streamed T, narrower last row blocks
+])
+def test_unsplit_density(ffx, dims, lam, batch):
+    rng = np.random.default_rng(sum(dims) + batch)
+    dx, t = (0.25,) * len(dims), 10.0
+    psi = random_field(rng, (batch,) + dims)
+    ref = np.abs(O.expand_field(psi, dx, t, lam)) ** 2
+    rho_u, fused = run(ffx, dims, dx, t, lam, psi, True)
+    rho_s, _ = run(ffx, dims, dx, t, lam, psi, False)
+    eu, es, d = rel_l2(rho_u, ref), rel_l2(rho_s, ref), rel_l2(rho_u, rho_s)
+    print(f"unsplit {dims} x{batch}: density {eu:.2e} (split {es:.2e}, unsplit vs split {d:.2e})")
+    assert fused == 0  # unsplit plans keep the per-axis launches
+    assert eu < UNSPLIT_TOL
+    assert d > 10 * es  # not the split result
+
+
+def test_unsplit_accumulate_and_backward(ffx):
+    dims, dx, lam, t = (64, 32, 64), (0.25, 0.2, 0.3), (6, 3, 4), 3.0
+    rng = np.random.default_rng(91)
+    psi = random_field(rng, (3,) + dims)
+    grad = rng.normal(size=(3,) + dims).astype(np.float32)
+    ref = np.abs(O.expand_field(psi, dx, t, lam)) ** 2
+    acc, _ = run(ffx, dims, dx, t, lam, psi, True, accumulate=True)
+    with ffx.Plan(dims, dx, t, lam, form="tc", unsplit=True) as plan:
+        g = ffx.ffx_expand_backward(plan, to_dev(psi), to_dev(grad)).cpu().numpy()
+        assert plan.device_errors() == 0
+    e1 = rel_l2(acc, ref.sum(0))
+    e2 = rel_l2(g, O.density_loss_gradient(psi, grad, dx, t, lam))
+    print(f"unsplit {dims}: ensemble sum {e1:.2e}, backward {e2:.2e}")
+    assert e1 < UNSPLIT_TOL and e2 < UNSPLIT_TOL
