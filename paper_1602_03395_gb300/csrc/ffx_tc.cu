@@ -46,6 +46,7 @@
 // (every other wait then gives up at once); producers drain their own copies,
 // the MMA thread waits (bounded) for its own tensor-core work, the block frees
 // its tensor memory, counts an error in `err` and exits.
+#include <algorithm>
 #include <cstring>
 
 #include "ffx_internal.h"
@@ -625,23 +626,40 @@ __global__ void __launch_bounds__(NTHREADS, 1) dense_tc_kernel(const TcParams P)
 }
 
 // ---------------------------------------------------------------------------
-// Lines of 64 points with T resident (plain forward and adjoint passes): the
-// input operand in tensor memory, one block per SM, no pipeline stages.  An
-// item is 128 lines x all 128 real rows.  Per item every thread has half a
-// line in registers (loaded during the previous item), writes its values and
-// tails into tensor memory (lane = line), and issues the next item's loads;
-// one thread runs 16 K-steps x 2 MMAs (A from tensor memory, T from shared
-// memory: [X_hi T_hi | X_hi T_lo] at N = 256, then X_lo T_hi); all eight warps
-// read the accumulators back and store.  Unsplit launches write the values
-// rounded to TF32 and run one product per K-step.
+// Lines of NP = 32 or 64 points with T resident (plain forward and adjoint
+// passes): the input operand in tensor memory, no pipeline stages.  An item
+// is 128 lines x all 2 NP real rows.  Per item every thread has half a line in
+// registers (loaded during the previous item), writes its values and tails
+// into tensor memory (lane = line), and issues the next item's loads; one
+// thread runs 2 NP / 8 K-steps (A from tensor memory, T from shared memory);
+// all eight warps read the accumulators back and store.  NP = 64: one block
+// per SM (all 512 columns), [X_hi T_hi | X_hi T_lo] in one N = 256 product
+// (the row block's head and tail rows are contiguous), then X_lo T_hi.
+// NP = 32: 256 columns and 64 KB per block, two blocks per SM (one loads while
+// the other multiplies); three N = 64 products per K-step.  Unsplit launches
+// write the values rounded to TF32 and run one product per K-step.
 // ---------------------------------------------------------------------------
-constexpr int R64_THREADS = 256;
-constexpr int R64_A_HI = 2 * ROWS, R64_A_LO = R64_A_HI + 2 * 64;  // after the accumulator pair
+constexpr int TM_THREADS = 256;
 constexpr uint32_t kIdescRows = idesc_tf32(LINES, ROWS);
 
-__global__ void __launch_bounds__(R64_THREADS, 1)
-    dense64_tm_kernel(const DenseArgs a, const unsigned char* __restrict__ Tblk, int* err) {
-  extern __shared__ __align__(1024) unsigned char tsm[];  // T: RES_CHUNKS chunks of [head | tail]
+template <int NP>
+struct TmLayout {
+  static constexpr int R = 2 * NP;                     // real rows = real K
+  static constexpr int CHUNKS = R / TKC;               // resident T chunks
+  static constexpr int SMEM = CHUNKS * T_CHUNK;        // 128 KB (NP = 64), 64 KB (NP = 32)
+  static constexpr int COLS = NP == 64 ? 512 : 256;    // tensor-memory columns per block
+  static constexpr int D2 = NP == 64 ? ROWS : R;       // cross-term accumulator
+  static constexpr int A_HI = 2 * R, A_LO = A_HI + R;  // the input operand after both accumulators
+  static constexpr int BLOCKS = NP == 64 ? 1 : 2;      // per SM
+  static constexpr int PER_THREAD = NP;                // floats: half a line
+};
+
+template <int NP>
+__global__ void __launch_bounds__(TM_THREADS, TmLayout<NP>::BLOCKS)
+    dense_tm_kernel(const DenseArgs a, const unsigned char* __restrict__ Tblk, int* err) {
+  using L = TmLayout<NP>;
+  static_assert(L::A_LO + L::R <= L::COLS, "tensor-memory columns");
+  extern __shared__ __align__(1024) unsigned char tsm[];  // T: L::CHUNKS chunks of [head | tail]
   __shared__ __align__(8) uint64_t tbar, mbar, dbar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int s_abort;
@@ -649,16 +667,17 @@ __global__ void __launch_bounds__(R64_THREADS, 1)
   const int64_t items = (a.ncols + LINES - 1) / LINES;
   if ((int64_t)blockIdx.x >= items) return;
   const int64_t my_items = (items - blockIdx.x + gridDim.x - 1) / gridDim.x;
+  const bool unsplit = a.unsplit != 0;
 
-  if (warp == 0) tmem_alloc(&tmem_slot, 512);
+  if (warp == 0) tmem_alloc(&tmem_slot, L::COLS);
   if (tid == 0) {
     s_abort = 0;
     mbar_init(smem_u32(&tbar), 1);
     mbar_init(smem_u32(&mbar), 1);
     mbar_init(smem_u32(&dbar), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    mbar_expect_tx(smem_u32(&tbar), (uint32_t)(RES_CHUNKS * T_CHUNK));
-    for (int c = 0; c < RES_CHUNKS; ++c)
+    mbar_expect_tx(smem_u32(&tbar), (uint32_t)L::SMEM);
+    for (int c = 0; c < L::CHUNKS; ++c)
       bulk_g2s(smem_u32(tsm + c * T_CHUNK), Tblk + (size_t)c * T_CHUNK, T_CHUNK, smem_u32(&tbar));
   }
   tc_fence_before();
@@ -667,22 +686,22 @@ __global__ void __launch_bounds__(R64_THREADS, 1)
   const uint32_t tmem = tmem_slot;
   const uint32_t smem_base = smem_u32(tsm);
 
-  const int q = warp & 3, h = warp >> 2;  // lanes 32 q .. + 31 (lines), points 32 h .. + 31
+  const int q = warp & 3, h = warp >> 2;  // lanes 32 q .. + 31 (lines), points NP/2 h .. + NP/2 - 1
   const int64_t inner = a.inner;
   const bool contiguous = (inner == 1);
   // line c of the pass: offset of its first point, or -1 past the end
   auto line_base = [&](int64_t c) -> long long {
     if (c >= a.ncols) return -1;
     const int64_t bo = c / inner, i = c - bo * inner;
-    return bo * 64 * inner + i;
+    return bo * NP * inner + i;
   };
-  float x[64];
+  float x[L::PER_THREAD];
   long long base = line_base((int64_t)blockIdx.x * LINES + 32 * q + lane);
   auto load = [&](long long bs) {
     if (contiguous) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const float4 v = bs >= 0 ? __ldcg(reinterpret_cast<const float4*>(a.in + bs + 32 * h + 2 * j))
+      for (int j = 0; j < NP / 4; ++j) {
+        const float4 v = bs >= 0 ? __ldcg(reinterpret_cast<const float4*>(a.in + bs + (NP / 2) * h + 2 * j))
                                  : make_float4(0.f, 0.f, 0.f, 0.f);
         x[4 * j] = v.x;
         x[4 * j + 1] = v.y;
@@ -691,8 +710,8 @@ __global__ void __launch_bounds__(R64_THREADS, 1)
       }
     } else {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const float2 v = bs >= 0 ? __ldcg(a.in + bs + (int64_t)(32 * h + j) * inner) : make_float2(0.f, 0.f);
+      for (int j = 0; j < NP / 2; ++j) {
+        const float2 v = bs >= 0 ? __ldcg(a.in + bs + (int64_t)((NP / 2) * h + j) * inner) : make_float2(0.f, 0.f);
         x[2 * j] = v.x;
         x[2 * j + 1] = v.y;
       }
@@ -702,21 +721,22 @@ __global__ void __launch_bounds__(R64_THREADS, 1)
   uint32_t phase = 0;
   bool slices = false, issued = false;
   const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
+  const uint32_t a_hi = trow + L::A_HI + (uint32_t)(NP * h), a_lo = trow + L::A_LO + (uint32_t)(NP * h);
   for (int64_t it = 0; it < my_items && !s_abort; ++it) {
     const int64_t ct = blockIdx.x + it * gridDim.x;
     const long long cur = base;
     // this item's values and tails into tensor memory (the previous item's MMAs are done)
-    if (a.unsplit) {
+    if (unsplit) {
 #pragma unroll
-      for (int g = 0; g < 4; ++g) {
+      for (int g = 0; g < NP / 16; ++g) {
         uint32_t hi[16];
 #pragma unroll
         for (int m = 0; m < 16; ++m) hi[m] = __float_as_uint(tf32_round(x[16 * g + m]));
-        tmem_st16(trow + R64_A_HI + 64 * h + 16 * g, hi);
+        tmem_st16(a_hi + 16 * g, hi);
       }
     } else {
 #pragma unroll
-      for (int g = 0; g < 4; ++g) {
+      for (int g = 0; g < NP / 16; ++g) {
         uint32_t hi[16], lo[16];
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
@@ -724,8 +744,8 @@ __global__ void __launch_bounds__(R64_THREADS, 1)
           hi[m] = __float_as_uint(v);
           lo[m] = __float_as_uint(v - tf32_head(v));
         }
-        tmem_st16(trow + R64_A_HI + 64 * h + 16 * g, hi);
-        tmem_st16(trow + R64_A_LO + 64 * h + 16 * g, lo);
+        tmem_st16(a_hi + 16 * g, hi);
+        tmem_st16(a_lo + 16 * g, lo);
       }
     }
     tmem_wait_st();
@@ -740,15 +760,26 @@ __global__ void __launch_bounds__(R64_THREADS, 1)
     if (tid == 0 && slices) {
       tc_fence_after();
 #pragma unroll 4
-      for (int ks = 0; ks < (2 * 64) / 8; ++ks) {
+      for (int ks = 0; ks < L::R / 8; ++ks) {
         const uint32_t th = smem_base + (uint32_t)((ks >> 2) * T_CHUNK + (ks & 3) * 2 * CORE_LBO);
         const uint64_t dth = make_desc(th, CORE_LBO, CHUNK_SBO);
         const uint32_t more = ks > 0 ? 1u : 0u;
-        if (a.unsplit) {
-          mma_tf32_ts(tmem, tmem + R64_A_HI + 8 * ks, dth, kIdescRows, more);  // X T, rounded operands
+        const uint32_t xh = tmem + L::A_HI + 8 * ks, xl = tmem + L::A_LO + 8 * ks;
+        if constexpr (NP == 64) {
+          if (unsplit) {
+            mma_tf32_ts(tmem, xh, dth, kIdescRows, more);  // X T, rounded operands
+          } else {
+            mma_tf32_ts(tmem, xh, dth, kIdescStack, more);           // [X_hi T_hi | X_hi T_lo]
+            mma_tf32_ts(tmem + L::D2, xl, dth, kIdescRows, 1u);     // + X_lo T_hi
+          }
         } else {
-          mma_tf32_ts(tmem, tmem + R64_A_HI + 8 * ks, dth, kIdescStack, more);     // [X_hi T_hi | X_hi T_lo]
-          mma_tf32_ts(tmem + ROWS, tmem + R64_A_LO + 8 * ks, dth, kIdescRows, 1u);  // + X_lo T_hi
+          constexpr uint32_t idesc = idesc_tf32(LINES, 2 * NP);
+          const uint64_t dtl = make_desc(th + T_PART, CORE_LBO, CHUNK_SBO);
+          mma_tf32_ts(tmem, xh, dth, idesc, more);  // X_hi T_hi (unsplit: X T)
+          if (!unsplit) {
+            mma_tf32_ts(tmem + L::D2, xh, dtl, idesc, more);  // X_hi T_lo
+            mma_tf32_ts(tmem + L::D2, xl, dth, idesc, 1u);    // + X_lo T_hi
+          }
         }
       }
       mma_commit(smem_u32(&mbar));
@@ -758,23 +789,23 @@ __global__ void __launch_bounds__(R64_THREADS, 1)
     phase ^= 1u;
     if (!ok) break;
     tc_fence_after();
-    // accumulators: warp (q, h) reads real rows 64 h .. 64 h + 63 of its 32 lines
+    // accumulators: warp (q, h) reads real rows NP h .. NP h + NP - 1 of its 32 lines
 #pragma unroll 1
-    for (int j0 = 0; j0 < 64; j0 += 16) {
+    for (int j0 = 0; j0 < NP; j0 += 16) {
       uint32_t x1[16], x2[16];
-      tmem_ld16(trow + (uint32_t)(64 * h + j0), x1);
-      if (!a.unsplit) tmem_ld16(trow + (uint32_t)(ROWS + 64 * h + j0), x2);
+      tmem_ld16(trow + (uint32_t)(NP * h + j0), x1);
+      if (!unsplit) tmem_ld16(trow + (uint32_t)(L::D2 + NP * h + j0), x2);
       tmem_wait_ld();
       if (cur < 0) continue;
       float y[16];
-      if (a.unsplit) {
+      if (unsplit) {
 #pragma unroll
         for (int m = 0; m < 16; ++m) y[m] = __uint_as_float(x1[m]);
       } else {
 #pragma unroll
         for (int m = 0; m < 16; ++m) y[m] = __uint_as_float(x1[m]) + __uint_as_float(x2[m]);
       }
-      const int n0 = 32 * h + j0 / 2;  // complex outputs n0 .. n0 + 7
+      const int n0 = (NP / 2) * h + j0 / 2;  // complex outputs n0 .. n0 + 7
       if (a.out_c) {
         if (contiguous) {
           float4* o = reinterpret_cast<float4*>(a.out_c + cur + n0);
@@ -813,7 +844,7 @@ __global__ void __launch_bounds__(R64_THREADS, 1)
   if (tid == 0 && s_abort && err) atomicAdd(err, 1);
   if (warp == 0) {
     tc_fence_after();
-    tmem_free(tmem, 512);
+    tmem_free(tmem, L::COLS);
   }
 }
 
@@ -859,7 +890,9 @@ cudaError_t dense_tc_prepare() {
     e = cudaFuncSetAttribute(dense_tc_kernel<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              TcLayout<true>::SMEM);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(dense64_tm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, RES_CHUNKS * T_CHUNK);
+    e = cudaFuncSetAttribute(dense_tm_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, TmLayout<64>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(dense_tm_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, TmLayout<32>::SMEM);
   return e;
 }
 size_t dense_tc_t_bytes(int N) {
@@ -874,10 +907,14 @@ cudaError_t launch_dense_tc(const DenseArgs& a, const unsigned char* Tblk, int* 
   P.tblk = Tblk;
   P.err = err;
   const int64_t items = (a.ncols + LINES - 1) / LINES;
-  if (a.N == 64 && !a.acc && !a.grad && items <= 4 * (int64_t)grid) {
+  if (a.N == 32 && !a.acc && !a.grad) {
+    // two blocks per SM (grid = the SMs when the pass has more items than SMs)
+    const int64_t g = items > grid ? std::min<int64_t>(items, 2 * (int64_t)grid) : grid;
+    dense_tm_kernel<32><<<(unsigned)g, TM_THREADS, TmLayout<32>::SMEM, stream>>>(a, Tblk, err);
+  } else if (a.N == 64 && !a.acc && !a.grad && items <= 4 * (int64_t)grid) {
     // a few items per block: the input operand in tensor memory, no pipeline
     // to fill (measured 7-14% faster at up to ~2 items per SM, 6% slower at 13)
-    dense64_tm_kernel<<<grid, R64_THREADS, RES_CHUNKS * T_CHUNK, stream>>>(a, Tblk, err);
+    dense_tm_kernel<64><<<grid, TM_THREADS, TmLayout<64>::SMEM, stream>>>(a, Tblk, err);
   } else if (a.N == 64 && !a.acc && !a.grad) {
     // T (128 KB) stays in shared memory for the whole launch
     dense_tc_kernel<true, false, true><<<grid, NTHREADS, TcLayout<true>::SMEM, stream>>>(P);
