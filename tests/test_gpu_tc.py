@@ -174,3 +174,26 @@ def test_auto_moves_large_dense_passes_to_tensor_cores(ffx):
     e6, e1 = rel_l2(rho, ref), rel_l2(one, ref[:1])
     print(f"auto {w.name}: batch 6 on tensor cores {e6:.2e}, batch 1 fused on tensor cores {e1:.2e}")
     assert e6 < DENSITY_TOL and e1 < DENSITY_TOL
+
+
+@pytest.mark.parametrize("dims,lam,batch", [
+    ((32,), (50,), 200),         # 32-point lines, two blocks per SM, a ragged last item
+    ((64,), (5,), 300),          # 64-point lines, a few items per block
+    ((32, 64), (7, 3), 40),      # a strided 32-point axis, then a contiguous 64-point axis
+])
+def test_tc_resident_passes_in_place(ffx, dims, lam, batch):
+    """The passes that keep T resident and take the input operand in tensor
+    memory run in place: each item reads its lines whole before it writes them."""
+    rng = np.random.default_rng(sum(dims) + 3 * batch)
+    dx, t = (0.25,) * len(dims), 5.0
+    psi = random_field(rng, (batch,) + dims)
+    ref = O.expand_field(psi, dx, t, lam)
+    with ffx.Plan(dims, dx, t, lam, form="tc") as plan:
+        assert plan.call_forms(batch) == ("tc",) * len(dims)
+        x = to_dev(psi)
+        ffx.ffx_expand_field(plan, x, x)
+        got = x.cpu().numpy()
+        assert plan.device_errors() == 0
+    e = rel_l2(got, ref)
+    print(f"tc in place {dims} x{batch}: field {e:.2e}")
+    assert e < FIELD_TOL
