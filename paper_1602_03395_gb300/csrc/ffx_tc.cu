@@ -46,6 +46,13 @@
 // (every other wait then gives up at once); producers drain their own copies,
 // the MMA thread waits (bounded) for its own tensor-core work, the block frees
 // its tensor memory, counts an error in `err` and exits.
+//
+// Lines of 32 or 64 points (plain passes) also have dense_tm_kernel: T stays
+// resident in shared memory and the input operand goes from registers
+// straight into tensor memory, with no stage pipeline; launch_dense_tc picks
+// it for every 32-point pass (two blocks per SM) and for 64-point passes with
+// at most four items per block.  Unsplit launches (FFX_TC_UNSPLIT) run one
+// product per K-step on operands rounded to TF32.
 #include <algorithm>
 #include <cstring>
 
