@@ -333,9 +333,9 @@ def pipelined_e2e(torch, dev, plans, call, h_in, d_in, d_out, h_out, steps):
     """End-to-end milliseconds for `steps` steps, each copying its input from
     pinned host memory (h_in[i % len(h_in)]), expanding it through the C ABI
     and copying the densities back to pinned host memory.  Steps alternate
-    between len(plans) lanes (stream, plan, device and host buffers), so with
-    two lanes one step's copies overlap the other lane's expansion, as a
-    streaming caller runs it; every step still moves its own bytes both ways."""
+    between len(plans) lanes (stream, plan, device and host buffers), so that
+    one lane's copies overlap the others' expansions, as a streaming caller
+    runs it; every step still moves its own bytes both ways."""
     main = torch.cuda.current_stream(dev)
     lanes = [torch.cuda.Stream(dev) for _ in plans]
     for k, st in enumerate(lanes):  # warm each lane
@@ -373,8 +373,8 @@ def host_api_e2e(torch, dev, ffx, plans, h_in, h_out, steps):
     """End-to-end milliseconds for `steps` steps of ffx_expand_host (one C
     call per step: pinned host input -> device -> expansion -> pinned host
     densities), alternating between len(plans) lanes (stream, plan and host
-    output buffer each), so with two lanes one step's copies overlap the
-    other lane's expansion."""
+    output buffer each), so that one lane's copies overlap the others'
+    expansions."""
     main = torch.cuda.current_stream(dev)
     lanes = [torch.cuda.Stream(dev) for _ in plans]
     for k, st in enumerate(lanes):  # warm each lane (the plan's staging buffers)
@@ -737,8 +737,8 @@ def run_ffx(args):
     value = job_rate(args.steps, B_, world, ms)
 
     # end to end through the C ABI with host buffers: pinned H2D, expand, D2H
-    # per step, two lanes (see pipelined_e2e)
-    # lanes beyond the first: their own plan (staging buffers, workspace) and stream
+    # per step, over 1 .. E2E_MAX_LANES lanes (see host_api_e2e); lanes beyond
+    # the first have their own plan (staging buffers, workspace) and stream
     lane_plans = [plan] + [ffx.Plan(w.dims, w.dx, w.t, w.lam, form=args.form, unsplit=args.unsplit)
                            for _ in range(E2E_MAX_LANES - 1)]
     if args.column is None:
