@@ -76,3 +76,17 @@ def _rank_main(rank, port):
 
 def test_two_gloo_ranks():
     mp.spawn(_rank_main, args=(_free_port(),), nprocs=WORLD, join=True)
+
+
+def test_bench_cli_checks(monkeypatch):
+    """The unsplit variant exists for the tensor-core form of single-lattice
+    workloads only; the end-to-end leg tries up to four lanes."""
+    for argv in (["bench.py", "--unsplit"], ["bench.py", "--unsplit", "--form", "dense"],
+                 ["bench.py", "--unsplit", "--form", "tc", "--workload", "mixed"]):
+        monkeypatch.setattr("sys.argv", argv)
+        with pytest.raises(SystemExit):
+            bench.parse()
+    monkeypatch.setattr("sys.argv", ["bench.py", "--unsplit", "--form", "tc", "--batch", "8"])
+    a = bench.parse()
+    assert a.unsplit and a.form == "tc" and a.batch == 8 and a.gpus == 1
+    assert bench.E2E_MAX_LANES == 4
