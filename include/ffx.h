@@ -48,6 +48,7 @@ extern "C" {
 #define FFX_ENOMEM       2  /* device allocation failed */
 #define FFX_ECUDA        3  /* a CUDA call failed; see ffx_last_error() */
 #define FFX_EUNSUPPORTED 4  /* valid request this build has no kernel for */
+#define FFX_ETIMEOUT     5  /* a kernel of the plan gave up on a bounded wait */
 
 /* ---- plan flags -------------------------------------------------------- */
 /* Form of the per-axis sum over the fine momentum index q (eq. FFpsi).
@@ -287,8 +288,9 @@ int ffx_expand_adjoint(ffx_plan_t plan, const void* g_in, int64_t batch, void* g
 #define FFX_NOALLOC_MAX_FOLD  8192      /* ints: sum over axes of M_j */
 
 /*
- * ffx_expand_noalloc -- ffx_plan + ffx_expand (default flags: fold form, one
- * density per realization) in one call that allocates no memory.  The paper
+ * ffx_expand_noalloc -- the map of ffx_plan + ffx_expand, always with the fold
+ * form (FFX_FORM_FOLD) and one density per realization, in one call that
+ * allocates no memory.  The paper
  * has no counterpart; this exists for callers that cannot call cudaMalloc
  * while they run: a host framework that has reserved nearly all device memory
  * for its own pool (a raw cudaMalloc would fail or fragment it), or a
@@ -442,8 +444,30 @@ int64_t ffx_plan_trace_count(ffx_plan_t plan);
 
 /* Waits that ran out inside the plan's kernels so far (tensor-core passes
  * bound every wait on the tensor cores and count a timeout here instead of
- * hanging); 0 when all is well.  Synchronizes with the device. */
+ * hanging); 0 when all is well.  Synchronizes with the device.
+ *
+ * Where the device has native atomics to host memory (cudaDevAttr-
+ * HostNativeAtomicSupported, e.g. a GB300 next to its Grace CPU), the count
+ * lives in mapped page-locked host memory, and every stream-ordered entry
+ * point of a single-lattice plan (ffx_expand, _host, _field, _column,
+ * _positive_p, _backward, _adjoint) first checks it without synchronizing:
+ * if it grew since the last such report, the call launches nothing and returns
+ * FFX_ETIMEOUT (once per new timeout), since the earlier call's output is not
+ * valid.  A timeout is seen once its launch has finished, e.g. after a stream
+ * synchronization.  Many-instance plans report through this function only. */
 int ffx_plan_device_errors(ffx_plan_t plan);
+
+/* Poll budget of the waits in which a block of the plan's fused launch
+ * (ffx_plan_fused) waits for OTHER blocks: its grid-wide barriers and the
+ * per-tile counters between passes.  polls >= 1 sets it; 0 restores the
+ * default (2^22 polls, far beyond a healthy wait).  A wait that runs out sets
+ * the block's abort flag: the block stops its passes, waits (with the normal
+ * bound) for its own bulk copies and tensor-core work, frees its tensor
+ * memory, counts the timeout (ffx_plan_device_errors) and exits; the next call
+ * returns FFX_ETIMEOUT.  Waits on a block's own copies and products keep their
+ * fixed bound.  The paper has no counterpart: this exercises the failure
+ * path of the bounded waits.  FFX_EINVAL for polls < 0. */
+int ffx_plan_set_wait_limit(ffx_plan_t plan, int64_t polls);
 
 /* Static strings for return codes; never NULL. */
 const char* ffx_error_string(int code);

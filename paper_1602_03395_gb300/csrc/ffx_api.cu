@@ -148,8 +148,14 @@ struct ffx_plan_s {
   int order[3] = {0, 1, 2};  // forward pass order
   void* tables = nullptr;
   void* dense_mem = nullptr;
-  void* tc_mem = nullptr;    // split tensor-core operands + device error counter
-  int* dev_err = nullptr;
+  void* tc_mem = nullptr;    // split tensor-core operands + the fused launch's counters
+  int* dev_err = nullptr;    // kernels that gave up on a bounded wait (device address)
+  // the same counter in mapped page-locked host memory where the device has
+  // native atomics to host memory (else NULL and dev_err is device memory):
+  // the host reads it without a synchronization to report FFX_ETIMEOUT
+  int* host_err = nullptr;
+  int err_seen = 0;          // timeouts already reported through FFX_ETIMEOUT
+  long long wait_limit = kCrossBlockSpin;  // polls of a wait on other blocks
   unsigned* grid_bar = nullptr;  // arrival counter of the fused kernel's grid barriers
   unsigned* tile_done = nullptr;  // per line tile: row blocks of the fused kernel's previous pass written
   int64_t fused = 0;             // largest batch whose forward calls run as one launch (ffx_fused.cu)
@@ -170,6 +176,18 @@ struct ffx_plan_s {
 };
 
 namespace {
+
+// FFX_ETIMEOUT once per new timeout: the kernels count waits that ran out in
+// the mapped word, which the host reads here without synchronizing (a launch
+// that has not finished yet is seen by a later call).
+int check_timeout(ffx_plan_s* p) {
+  if (!p->host_err) return FFX_OK;
+  const int now = *(volatile int*)p->host_err;
+  if (now <= p->err_seen) return FFX_OK;
+  p->err_seen = now;
+  return fail(FFX_ETIMEOUT, "a kernel of this plan gave up on a bounded wait (%d so far): its output is not valid",
+              now);
+}
 
 void axis_outer_inner(const ffx_plan_s* p, int j, int64_t* outer, int64_t* inner) {
   int64_t o = 1, in = 1;
@@ -560,6 +578,7 @@ int run_fused(ffx_plan_s* p, const int* axes, const float2* in, float2* out_c, f
   a.batch = batch;
   a.bar = p->grid_bar;
   a.err = p->dev_err;
+  a.spin = p->wait_limit;
   int64_t off = 0;
   for (int k = 0; k < p->ndim; ++k) {
     const int j = axes[k];
@@ -771,6 +790,7 @@ const char* ffx_error_string(int code) {
     case FFX_ENOMEM: return "out of device memory";
     case FFX_ECUDA: return "CUDA error";
     case FFX_EUNSUPPORTED: return "unsupported configuration";
+    case FFX_ETIMEOUT: return "a bounded device wait ran out";
     default: return "unknown error";
   }
 }
@@ -1022,7 +1042,20 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
       p->dev_err = (int*)p->tc_mem;
       p->grid_bar = (unsigned*)((char*)p->tc_mem + 64);
       p->tile_done = (unsigned*)((char*)p->tc_mem + 1024);
-      cudaMemsetAsync(p->dev_err, 0, kTcHeader, s);
+      cudaMemsetAsync(p->tc_mem, 0, kTcHeader, s);
+      int native = 0;
+      if (cudaDeviceGetAttribute(&native, cudaDevAttrHostNativeAtomicSupported, p->device) == cudaSuccess &&
+          native && cudaHostAlloc((void**)&p->host_err, sizeof(int), cudaHostAllocMapped) == cudaSuccess) {
+        *(volatile int*)p->host_err = 0;
+        int* d = nullptr;
+        if (cudaHostGetDevicePointer((void**)&d, p->host_err, 0) == cudaSuccess && d) {
+          p->dev_err = d;
+        } else {
+          cudaFreeHost(p->host_err);
+          p->host_err = nullptr;
+        }
+      }
+      cudaGetLastError();
       unsigned char* tcur = (unsigned char*)p->tc_mem + kTcHeader;
       for (int j = 0; j < ndim && rc == FFX_OK; ++j) {
         Axis& ax = p->axis[j];
@@ -1109,6 +1142,7 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
       if (p->ws[w]) cudaFree(p->ws[w]);
     if (p->dense_mem) cudaFree(p->dense_mem);
     if (p->tc_mem) cudaFree(p->tc_mem);
+    if (p->host_err) cudaFreeHost(p->host_err);
     cudaFree(p->tables);
     delete p;
     return rc;
@@ -1160,8 +1194,16 @@ int ffx_plan_destroy(ffx_plan_t p) {
     if (p->ws[w]) cudaFree(p->ws[w]);
   if (p->dense_mem) cudaFree(p->dense_mem);
   if (p->tc_mem) cudaFree(p->tc_mem);
+  if (p->host_err) cudaFreeHost(p->host_err);
   if (p->tables) cudaFree(p->tables);
   delete p;
+  return FFX_OK;
+}
+
+int ffx_plan_set_wait_limit(ffx_plan_t p, int64_t polls) {
+  if (!p) return fail(FFX_EINVAL, "plan is NULL");
+  if (polls < 0) return fail(FFX_EINVAL, "polls < 0");
+  p->wait_limit = polls == 0 ? kCrossBlockSpin : (long long)polls;
   return FFX_OK;
 }
 
@@ -1198,6 +1240,10 @@ int64_t ffx_plan_trace_count(ffx_plan_t p) { return p ? p->trace_i : -1; }
 int ffx_plan_device_errors(ffx_plan_t p) {
   if (!p) return -1;
   if (!p->dev_err) return 0;
+  if (p->host_err) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+    return *(volatile int*)p->host_err;
+  }
   int h = 0;
   if (cudaMemcpy(&h, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
   return h;
@@ -1257,6 +1303,7 @@ int forward_density(ffx_plan_s* p, const int* axes, const float2* in, int64_t ba
 
 int ffx_expand(ffx_plan_t p, const void* psi0, int64_t batch, float* out_density, void* stream) {
   if (!p) return fail(FFX_EINVAL, "plan is NULL");
+  if (int trc = check_timeout(p)) return trc;
   if (batch < 0) return fail(FFX_EINVAL, "batch < 0");
   if (batch == 0) return FFX_OK;
   int rc;
@@ -1274,6 +1321,7 @@ int ffx_expand(ffx_plan_t p, const void* psi0, int64_t batch, float* out_density
 
 int ffx_expand_host(ffx_plan_t p, const void* psi0_host, int64_t batch, float* out_host, void* stream) {
   if (!p) return fail(FFX_EINVAL, "plan is NULL");
+  if (int trc = check_timeout(p)) return trc;
   if (batch < 0) return fail(FFX_EINVAL, "batch < 0");
   if (batch == 0) return FFX_OK;
   if (!psi0_host) return fail(FFX_EINVAL, "psi0_host is NULL");
@@ -1296,6 +1344,7 @@ int ffx_expand_host(ffx_plan_t p, const void* psi0_host, int64_t batch, float* o
 
 int ffx_expand_column(ffx_plan_t p, const void* psi0, int64_t batch, int axis, float* out_column, void* stream) {
   if (!p) return fail(FFX_EINVAL, "plan is NULL");
+  if (int trc = check_timeout(p)) return trc;
   if (batch < 0) return fail(FFX_EINVAL, "batch < 0");
   if (p->many) return fail(FFX_EUNSUPPORTED, "ffx_expand_column does not take a many-instance plan");
   if (axis < 0 || axis >= p->ndim) return fail(FFX_EINVAL, "axis %d out of range", axis);
@@ -1335,6 +1384,7 @@ int field_into(ffx_plan_s* p, const float2* in, int64_t batch, float2* out, cuda
 int ffx_expand_positive_p(ffx_plan_t p, const void* psi0, const void* psi0_plus, int64_t batch, float* out_density,
                           void* stream) {
   if (!p) return fail(FFX_EINVAL, "plan is NULL");
+  if (int trc = check_timeout(p)) return trc;
   if (batch < 0) return fail(FFX_EINVAL, "batch < 0");
   if (p->many) return fail(FFX_EUNSUPPORTED, "ffx_expand_positive_p does not take a many-instance plan");
   if (batch == 0) return FFX_OK;
@@ -1385,6 +1435,7 @@ int ffx_fringe_phase(const float* image, int64_t rows, int64_t ny, int64_t row_s
 
 int ffx_expand_field(ffx_plan_t p, const void* psi0, int64_t batch, void* out_field, void* stream) {
   if (!p) return fail(FFX_EINVAL, "plan is NULL");
+  if (int trc = check_timeout(p)) return trc;
   if (batch < 0) return fail(FFX_EINVAL, "batch < 0");
   if (batch == 0) return FFX_OK;
   int rc;
@@ -1404,6 +1455,7 @@ int ffx_expand_field(ffx_plan_t p, const void* psi0, int64_t batch, void* out_fi
 
 int ffx_expand_adjoint(ffx_plan_t p, const void* g_in, int64_t batch, void* g_out, void* stream) {
   if (!p) return fail(FFX_EINVAL, "plan is NULL");
+  if (int trc = check_timeout(p)) return trc;
   if (batch < 0) return fail(FFX_EINVAL, "batch < 0");
   if (batch == 0) return FFX_OK;
   int rc;
@@ -1418,6 +1470,7 @@ int ffx_expand_adjoint(ffx_plan_t p, const void* g_in, int64_t batch, void* g_ou
 int ffx_expand_backward(ffx_plan_t p, const void* psi0, const float* grad_density, int64_t batch,
                         void* grad_psi0, void* stream) {
   if (!p) return fail(FFX_EINVAL, "plan is NULL");
+  if (int trc = check_timeout(p)) return trc;
   if (batch < 0) return fail(FFX_EINVAL, "batch < 0");
   if (batch == 0) return FFX_OK;
   int rc;

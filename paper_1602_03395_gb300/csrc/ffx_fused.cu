@@ -56,14 +56,15 @@ __device__ __forceinline__ long long fused_line(const FusedPass& P, int64_t c, i
 }
 
 // Bounded grid-wide barrier: block arrivals counted in bar[0]; barrier k of
-// the launch waits for (k + 1) * gridDim.x arrivals.
-__device__ bool grid_barrier(unsigned* bar, unsigned target, volatile int* s_abort) {
+// the launch waits for (k + 1) * gridDim.x arrivals, polling at most `spin`
+// times (the plan's budget for waits on other blocks).
+__device__ bool grid_barrier(unsigned* bar, unsigned target, long long spin, volatile int* s_abort) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();  // this block's writes of the pass, before its arrival
     atomicAdd(bar, 1u);
     bool ok = false;
-    for (long long i = 0; i < kSpinLimit; ++i) {
+    for (long long i = 0; i < spin; ++i) {
       if (*(volatile unsigned*)bar >= target) {
         ok = true;
         break;
@@ -285,7 +286,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_small_kernel(const FusedArgs
       }
       if (more) park(buf ^ 1);
     }
-    if (p + 1 < a.npass && !grid_barrier(a.bar, (unsigned)(p + 1) * gridDim.x, &s_abort)) break;
+    if (p + 1 < a.npass && !grid_barrier(a.bar, (unsigned)(p + 1) * gridDim.x, a.spin, &s_abort)) break;
   }
   // copies of images not waited for must land before the block exits
   for (int p = 0; p < a.npass; ++p)
@@ -394,7 +395,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fused_tc_kernel(const FusedArgs
         // this tile's input is written once the previous pass's four row blocks of it are
         if (tid == 0) {
           bool ok = false;
-          for (long long i = 0; i < kSpinLimit; ++i) {
+          for (long long i = 0; i < a.spin; ++i) {
             if (*(volatile unsigned*)(a.tile_done + ct) >= (unsigned)FT_RB) {
               ok = true;
               break;
@@ -527,7 +528,7 @@ __global__ void __launch_bounds__(FT_THREADS, 1) fused_tc_kernel(const FusedArgs
     }
     if (p + 1 < a.npass && p + 1 != a.local_pass) {
       ++barriers;
-      if (!grid_barrier(a.bar, (unsigned)barriers * gridDim.x, &s_abort)) break;
+      if (!grid_barrier(a.bar, (unsigned)barriers * gridDim.x, a.spin, &s_abort)) break;
     }
   }
   // the tensor cores finish this block's work, and the slice copies have

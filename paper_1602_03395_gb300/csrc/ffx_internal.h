@@ -145,8 +145,12 @@ struct FusedArgs {
   // after a grid barrier; -1: grid barriers only
   unsigned* tile_done;
   int local_pass;
+  // polls before a wait on other blocks (grid barrier, tile counters) gives
+  // up; waits on a block's own copies and tensor-core work keep kSpinLimit
+  long long spin;
 };
 constexpr int kFusedTileFlags = 256;
+constexpr long long kCrossBlockSpin = 1ll << 22;  // default of FusedArgs::spin
 size_t fused_smem(const int* N, int npass);
 // Tensor-core variant for lattices whose axes all have 64 points: 4 row
 // blocks of 32 real rows; each block's T slice is head and tail of 32 rows x

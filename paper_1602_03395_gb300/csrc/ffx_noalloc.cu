@@ -10,8 +10,9 @@
 // and output in file-scope __device__ arrays of fixed size, which every GPU
 // that loads the library holds until the process exits.
 //
-// The map and the kernels are those of ffx_plan + ffx_expand with default
-// flags (fold form): the phase tables are rebuilt into the static arrays on
+// The map is that of ffx_plan + ffx_expand, and the kernels are those of the
+// fold form (FFX_FORM_FOLD) on every axis, whatever form ffx_plan's automatic
+// choice would take: the phase tables are rebuilt into the static arrays on
 // every call, on the caller's stream, and the intermediate field between axis
 // passes lives in the static field array.
 #include <cmath>

@@ -23,7 +23,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libffx.so")
 
-FFX_OK, FFX_EINVAL, FFX_ENOMEM, FFX_ECUDA, FFX_EUNSUPPORTED = 0, 1, 2, 3, 4
+FFX_OK, FFX_EINVAL, FFX_ENOMEM, FFX_ECUDA, FFX_EUNSUPPORTED, FFX_ETIMEOUT = 0, 1, 2, 3, 4, 5
 FFX_FORM_AUTO, FFX_FORM_PAPER, FFX_FORM_FOLD, FFX_FORM_DENSE, FFX_FORM_TC = 0x0, 0x1, 0x2, 0x3, 0x4
 FFX_ACCUMULATE = 0x10
 FFX_TUNE = 0x20
@@ -110,6 +110,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ffx_plan_trace_count.restype = i64
     lib.ffx_plan_device_errors.argtypes = [vp]
     lib.ffx_plan_device_errors.restype = i32
+    lib.ffx_plan_set_wait_limit.argtypes = [vp, i64]
+    lib.ffx_plan_set_wait_limit.restype = i32
     lib.ffx_expand_noalloc.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(dbl), dbl,
                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(dbl),
                                        ctypes.POINTER(dbl), vp, i64, vp, vp]
@@ -285,6 +287,10 @@ class Plan:
     def device_errors(self) -> int:
         """Bounded waits that ran out in this plan's kernels (0 when all is well)."""
         return int(load_library().ffx_plan_device_errors(self.handle))
+
+    def set_wait_limit(self, polls: int):
+        """Poll budget of the fused launch's waits on other blocks (0: default)."""
+        _check(load_library().ffx_plan_set_wait_limit(self.handle, int(polls)), "ffx_plan_set_wait_limit")
 
 
 class PlanMany(Plan):

@@ -198,3 +198,57 @@ def test_many_dense_in_place_guard():
         ffx.ffx_expand_field(plan, x, x)
     assert ei.value.code == ffx.FFX_EUNSUPPORTED
     plan.close()
+
+
+def test_many_full_mixed_workload_sampled_instances():
+    """The whole mixed-batch workload: 1000 instances over 48^3, 64^3, 96^3 and
+    128x32x32 with lam ~ U{10..100} and t = 4 lam, in one many-instance plan
+    (one persistent launch per axis phase over about 450 distinct operand
+    geometries).  Forty instances are compared element by element with the FP64
+    oracle: every lattice shape's smallest and largest magnification, and a
+    seeded sample spread over the instance list (and so over the cost-sorted
+    work list: early, middle and late items).  The other instances carry copies
+    of one realization per shape: their values do not change the work."""
+    ffx = require_gpu()
+    ws = inputs.config_mixed_batch(count=1000)
+    specs = [(w.dims, w.dx, w.t, w.lam) for w in ws]
+    plan = ffx.PlanMany(specs)
+    chosen = set()
+    for shape in inputs.MIXED_SHAPES:
+        idx = [i for i, w in enumerate(ws) if tuple(w.dims) == shape]
+        chosen.add(min(idx, key=lambda i: ws[i].lam[0]))
+        chosen.add(max(idx, key=lambda i: ws[i].lam[0]))
+    rng = np.random.default_rng(40)
+    rest = [i for i in range(len(ws)) if i not in chosen]
+    for part in np.array_split(np.array(rest), 32):
+        chosen.add(int(rng.choice(part)))
+    chosen = sorted(chosen)
+    x = torch.empty(plan.points, dtype=torch.complex64, device="cuda")
+    views = plan.unpack(x)
+    filler, own = {}, {}
+    for i, w in enumerate(ws):
+        if i in chosen:
+            own[i] = w.realization(0)
+            views[i].copy_(torch.from_numpy(own[i]))
+        else:
+            key = tuple(w.dims)
+            if key not in filler:
+                filler[key] = torch.from_numpy(w.realization(1)).cuda()
+            views[i].copy_(filler[key])
+    rho = ffx.ffx_expand(plan, x)
+    torch.cuda.synchronize()
+    assert plan.device_errors() == 0
+    form = plan.form
+    out = plan.unpack(rho)
+    worst, geoms = 0.0, set()
+    for i in chosen:
+        w = ws[i]
+        ref = np.abs(O.expand_field(own[i], w.dx, w.t, w.lam)) ** 2
+        got = out[i].cpu().numpy()
+        worst = max(worst, rel_l2(got, ref))
+        geoms.add((tuple(w.dims), w.lam[0]))
+    plan.close()
+    print(f"many full workload ({form}): {len(chosen)} instances, {len(geoms)} geometries, "
+          f"worst density {worst:.2e}")
+    assert len(chosen) >= 40
+    assert worst < DENSITY_TOL

@@ -90,3 +90,20 @@ def test_bench_cli_checks(monkeypatch):
     a = bench.parse()
     assert a.unsplit and a.form == "tc" and a.batch == 8 and a.gpus == 1
     assert bench.E2E_MAX_LANES == 4
+
+
+def test_bench_defaults_and_peak_choice(monkeypatch):
+    """The default line is the largest single-GPU configuration (256^3 at
+    lam = 100, with the 128x128x1024 companion record); the tensor-core
+    roofline divides by the burst bf16 figure for a timed region under a
+    second and by the sustained one for longer regions (both scaled by the
+    nominal TF32 : BF16 ratio)."""
+    monkeypatch.setattr("sys.argv", ["bench.py"])
+    a = bench.parse()
+    assert a.workload == "large_two_cloud" and not a.no_companion
+    assert bench.COMPANION["large_two_cloud"] == "large_quasicondensate"
+    pk = {"bf16_tflops": 1884.7, "bf16_tflops_sustained": 1699.1}
+    burst, src = bench.tensor_peak(pk, "measured", 400.0)
+    assert burst == pytest.approx(1884.7 * 1.1 / 2.25) and src.startswith("bf16_tflops x")
+    sus, src = bench.tensor_peak(pk, "measured", 4000.0)
+    assert sus == pytest.approx(1699.1 * 1.1 / 2.25) and src.startswith("bf16_tflops_sustained")

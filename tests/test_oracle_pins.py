@@ -15,7 +15,7 @@ least one of them:
 * special cases: t = 0 is exact subsampling; lam = 1 with abar = a is a
   unitary circulant; shifting abar by lam*dx shifts the output by one point;
 * invariants: norm summed over the lam sub-lattice offsets (Parseval on the
-  huge lattice), linearity;
+  huge lattice), linearity; the ensemble mean of closed-form densities;
 * limits: the far-field estimate eq. farfieldk is approached like 1/t;
 * negative: the naive magnified DFT of Sec. 4.3 (eq. Psinaive) is wrong once
   the cloud outgrows the box;
@@ -265,6 +265,30 @@ def test_linearity_and_batch():
     c = 0.3 - 1.2j
     g = O.expand_field(x[0] + c * x[1], dx, t, lam)
     assert np.abs(g - (f[0] + c * f[1])).max() < 1e-12
+
+
+def test_ensemble_density_is_mean_of_closed_form_densities():
+    """Ensembles of realizations (Sec. 1): the mean density over a batch of
+    packets with different centres, widths, momenta and amplitudes equals the
+    mean of their closed-form densities (free Gaussian, 2-D, separable).  A
+    sum instead of a mean, a mean over a lattice axis, or a realization
+    mixed into another fails here."""
+    dims, dx, lam, t = (96, 80), (0.1, 0.12), (8, 5), 2.5
+    params = [((0.6, 0.5), (0.3, -0.2), (1.5, 0.0), 1.0),
+              ((0.45, 0.6), (-0.4, 0.1), (-1.0, 2.0), 0.5),
+              ((0.55, 0.4), (0.0, 0.35), (0.5, -1.5), 2.0)]
+    axes_in = [grid(dims[j], dx[j]) for j in range(2)]
+    axes_out = [out_grid(dims[j], dx[j], lam[j]) for j in range(2)]
+    psi = np.empty((len(params),) + dims, np.complex128)
+    ex = np.zeros(dims)
+    for r, (sig, c, k0, amp) in enumerate(params):
+        psi[r] = amp * np.outer(*[gauss_t(axes_in[j], 0, sig[j], c[j], k0[j]) for j in range(2)])
+        f = amp * np.outer(*[gauss_periodic(axes_out[j], t, sig[j], c[j], k0[j], lam[j] * dims[j] * dx[j])
+                             for j in range(2)])
+        ex += np.abs(f) ** 2 / len(params)
+    got = O.ensemble_density(psi, dx, t, lam)
+    assert got.shape == dims
+    assert rel(got, ex) < 1e-10
 
 
 # ---------------------------------------------------------------------------

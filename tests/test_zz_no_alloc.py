@@ -57,6 +57,26 @@ def test_noalloc_matches_plan_path_twice(name, spec):
         assert e < DENSITY_TOL
 
 
+def test_noalloc_against_the_oracle():
+    """The fold-form kernels the entry point always runs, against the FP64
+    oracle directly (not only against the automatic-form plan path)."""
+    import oracle as O
+    ffx = require_gpu()
+    dims, dx, t, lam = (32, 64), (0.25, 0.2), 2.5, (9, 5)
+    psi = random_field(np.random.default_rng(17), (2,) + dims)
+    x = to_dev(psi)
+    lib = ffx.load_library()
+    out = torch.full(psi.shape, float("nan"), dtype=torch.float32, device="cuda")
+    rc = lib.ffx_expand_noalloc(
+        2, (ctypes.c_int64 * 2)(*dims), (ctypes.c_double * 2)(*dx), ctypes.c_double(t),
+        (ctypes.c_int32 * 2)(*lam), None, None, ctypes.c_void_p(x.data_ptr()), 2,
+        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0, lib.ffx_last_error()
+    e = rel_l2(out.cpu().numpy(), O.expand_density(psi, dx, t, lam))
+    print(f"noalloc vs oracle: {e:.2e}")
+    assert e < DENSITY_TOL
+
+
 def test_noalloc_rejects_sizes_beyond_the_static_limit():
     ffx = require_gpu()
     lib = ffx.load_library()
