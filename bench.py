@@ -99,6 +99,11 @@ def parse():
     ap.add_argument("--unsplit", action="store_true",
                     help="with --form tc: one TF32 product on rounded operands (reported variant, "
                          "density error of order 1e-3)")
+    ap.add_argument("--bf16", action="store_true",
+                    help="BF16 operands on the streaming tensor-core passes (kind::f16; split into heads and "
+                         "tails, or unsplit with --unsplit); the automatic form's default")
+    ap.add_argument("--tf32", action="store_true",
+                    help="split TF32 operands on every tensor-core pass (the automatic form's BF16 default off)")
     ap.add_argument("--batch", type=int, default=None, help="realizations per step (default: workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-companion", action="store_true",
@@ -108,6 +113,10 @@ def parse():
     args = ap.parse_args()
     if args.unsplit and (args.form != "tc" or args.workload == "mixed"):
         ap.error("--unsplit needs --form tc and a single-lattice workload")
+    if args.bf16 and (args.form not in ("auto", "tc") or args.workload == "mixed"):
+        ap.error("--bf16 needs --form auto or tc and a single-lattice workload")
+    if args.tf32 and args.bf16:
+        ap.error("--tf32 and --bf16 exclude each other")
     return args
 
 
@@ -556,14 +565,26 @@ def run_mixed(args, torch, dist, world, rank, dev):
     return 0
 
 
-def tensor_peak(pk, pk_src, timed_ms):
-    """TF32 dense peak for the tensor-core passes: the measured bf16 cuBLAS
+def tensor_peak(pk, pk_src, timed_ms, dtype="tf32"):
+    """Dense tensor peak for the tensor-core passes: the measured bf16 cuBLAS
     figure -- the burst one for a timed region under a second, the sustained
-    one for longer regions -- times the nominal TF32 : BF16 dense ratio
-    (1.1 : 2.25 PFLOP/s)."""
+    one for longer regions -- as it stands for BF16 operands, times the
+    nominal TF32 : BF16 dense ratio (1.1 : 2.25 PFLOP/s) for TF32 operands."""
     key = "bf16_tflops" if (timed_ms < 1000.0 or "bf16_tflops_sustained" not in pk) else "bf16_tflops_sustained"
+    if dtype == "bf16":
+        return float(pk.get(key, 1900.0)), f"{key} (BF16 dense), {pk_src}"
     return (float(pk.get(key, 1900.0)) * 1.1 / 2.25,
             f"{key} x 1.1/2.25 (TF32 dense : BF16 dense, nominal), {pk_src}")
+
+
+def precision_label(args, bf16):
+    op = "BF16" if bf16 else "TF32"
+    if args.unsplit:
+        return f"{op} unsplit: one product on rounded operands (reported variant; density error of order 1e-3)"
+    if bf16:
+        return ("split BF16 on the streaming tensor-core passes (kind::f16, three products), split TF32 on the "
+                "other tensor-core passes, else FP32")
+    return "split TF32 on the tensor cores (three products), else FP32"
 
 
 def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary=True):
@@ -574,7 +595,8 @@ def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary
     Returns the JSON record (rank 0) or None."""
     B_ = w.batch
     M = int(np.prod(w.dims))
-    plan = ffx.Plan(w.dims, w.dx, w.t, w.lam, form=args.form, unsplit=args.unsplit)
+    plan = ffx.Plan(w.dims, w.dx, w.t, w.lam, form=args.form, unsplit=args.unsplit, bf16=args.bf16,
+                    tf32=args.tf32)
     form = plan.form
     order = plan.pass_order()
     launches = plan.launches_per_call(batch=B_)
@@ -732,11 +754,16 @@ def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary
         pass_names = [f"axis{order[k]}_N{w.dims[order[k]]}_lam{w.lam[order[k]]}_{call_forms[order[k]]}"
                       for k in range(launches)]
     achieved = flops / (mean_ms[dom] * 1e-3) / 1e12
+    # operands of the dominant tensor-core launch: BF16 where the plan gives
+    # the streaming kernel's passes BF16 (lines of N = 32k >= 64 outside the
+    # tensor-memory kernels' 64-point case), else TF32
+    bf16_launch = (plan.bf16 and not fused_call and w.dims[order[dom]] >= 64 and w.dims[order[dom]] % 32 == 0
+                   and not (w.dims[order[dom]] == 64 and B_ * M // 64 <= 4 * 128 * SMS))
     if axis_form == "tc":
-        # split-TF32 contraction on the tensor cores; `achieved` counts the
+        # split contraction on the tensor cores; `achieved` counts the
         # algorithmic 8 N^2 flops per line, the tensor cores execute 3x that
         # (three split products)
-        tc_peak, tc_src = tensor_peak(pk, pk_src, ms)
+        tc_peak, tc_src = tensor_peak(pk, pk_src, ms, "bf16" if bf16_launch else "tf32")
         roofline = {"bound": "tensor", "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
                     "frac": achieved / tc_peak, "traffic": traffic, "kernel": kernel_key,
                     "launch_ms": mean_ms[dom], "launch_time": launch_time,
@@ -754,7 +781,8 @@ def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary
     # end to end through the C ABI with host buffers: pinned H2D, expand, D2H
     # per step, over 1 .. E2E_MAX_LANES lanes (see host_api_e2e); lanes beyond
     # the first have their own plan (staging buffers, workspace) and stream
-    lane_plans = [plan] + [ffx.Plan(w.dims, w.dx, w.t, w.lam, form=args.form, unsplit=args.unsplit)
+    lane_plans = [plan] + [ffx.Plan(w.dims, w.dx, w.t, w.lam, form=args.form, unsplit=args.unsplit, bf16=args.bf16,
+                                    tf32=args.tf32)
                            for _ in range(E2E_MAX_LANES - 1)]
     if args.column is None:
         def call_pl(pl, x, out):
@@ -837,9 +865,7 @@ def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary
                    "lam": list(w.lam), "t": w.t, "batch_per_gpu": B_, "form": form,
                    "axis_forms": list(plan.axis_forms), "call_forms": list(call_forms),
                    "fused_one_launch": bool(fused_call),
-                   "precision": ("TF32 unsplit: one product on rounded operands (reported variant; "
-                                 "density error of order 1e-3)" if args.unsplit else
-                                 "split TF32 on the tensor cores (three products), else FP32"),
+                   "precision": precision_label(args, plan.bf16),
                    "output": ("density" if args.column is None else
                               f"detector image: density integrated along axis {args.column}"),
                    "parallelism": f"replicas x{world} (realizations sharded, no collective)",

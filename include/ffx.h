@@ -94,12 +94,29 @@ extern "C" {
  * every T_j resident in shared memory); same arithmetic, same results. */
 #define FFX_UNFUSED     0x40u
 /* With FFX_FORM_TC only: one tensor-core product per K-step, with the input
- * and T_j rounded to TF32 (round to nearest) and no tails.  A faster and less
+ * and T_j rounded to TF32 (round to nearest; to BF16 with FFX_TC_BF16) and no
+ * tails.  A faster and less
  * accurate variant, reported beside the split one: its density error is of
  * order 1e-3 against the 2e-5 of the split products.  Such plans never fuse
  * their passes into one launch, and axes the tensor cores do not take keep
  * the FP32 dense form.  Any other form with this flag: FFX_EINVAL. */
 #define FFX_TC_UNSPLIT  0x80u
+/* With FFX_FORM_TC or FFX_FORM_AUTO (where it is the default, see
+ * FFX_TC_TF32): the tensor-core passes of the streaming
+ * kernel (lines of N points, N a multiple of 32 from 64 to 1024; the 64-point
+ * plain passes with at most four items per block, the 32-point passes and the
+ * fused launch keep split TF32) take BF16 operands on kind::f16 products:
+ * every FP32 value v is split into hi = bf16(v) and lo = bf16(v - hi), and
+ * X_hi T_hi, X_hi T_lo and X_lo T_hi are accumulated in FP32 (density error
+ * of order 1e-6, within the 2e-5 of the FP32 path).  With FFX_TC_UNSPLIT
+ * (FFX_FORM_TC only): one product on operands rounded to BF16, the reported
+ * BF16 variant (density error of order 1e-3). */
+#define FFX_TC_BF16     0x100u
+/* Under FFX_FORM_AUTO the streaming tensor-core passes take split BF16
+ * operands (as FFX_TC_BF16) unless this flag asks for split TF32 operands
+ * throughout, or FFX_TC_UNSPLIT is given.  FFX_TC_TF32 with FFX_TC_BF16:
+ * FFX_EINVAL. */
+#define FFX_TC_TF32     0x200u
 
 typedef struct ffx_plan_s* ffx_plan_t;
 
@@ -385,6 +402,11 @@ int ffx_fringe_phase(const float* image, int64_t rows, int64_t ny, int64_t row_s
 
 /* Bytes of plan-owned workspace a call with this batch uses. */
 int64_t ffx_workspace_bytes(ffx_plan_t plan, int64_t batch);
+
+/* 1 if the plan's streaming tensor-core passes take BF16 operands
+ * (FFX_TC_BF16, or the automatic form's default), 0 if not, -1 for a NULL
+ * plan; many-instance plans: 0. */
+int ffx_plan_tc_bf16(ffx_plan_t plan);
 
 /* The form every axis runs (FFX_FORM_PAPER, _FOLD, _DENSE or _TC), or
  * FFX_FORM_AUTO if the axes differ. */

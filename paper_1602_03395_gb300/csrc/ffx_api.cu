@@ -119,6 +119,7 @@ struct Axis {
   float2* TH = nullptr;  // its adjoint
   int grid_dense = 0, grid_dense_small = 0;
   unsigned char* tc_t[2] = {nullptr, nullptr};  // split tensor-core operands of T, T^H (ffx_tc.cu)
+  unsigned char* bf_t[2] = {nullptr, nullptr};  // FFX_TC_BF16: the BF16 operand blocks (ffx_tc16.cu)
   unsigned char* ft_ts = nullptr;                 // N = 64: T's row-block slices for the fused tensor-core launch
   float2* img[2] = {nullptr, nullptr};                      // lines <= 64: shared-memory images of T, T^H
 };
@@ -334,10 +335,18 @@ int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* 
     d.unsplit = (p->flags & FFX_TC_UNSPLIT) ? 1 : 0;
     d.ncols = acc ? outer * inner : batch * outer * inner;
     d.N = ax.N;
-    int64_t grid = dense_tc_tiles(ax.N, d.ncols);
+    const int64_t items = dense_tc_tiles(ax.N, d.ncols);
+    int64_t grid = items;
     if (grid > p->sms) grid = p->sms;
     if (grid < 1) grid = 1;
-    e = launch_dense_tc(d, ax.tc_t[adjoint ? 1 : 0], p->dev_err, (int)grid, stream);
+    // BF16 operands on the streaming kernel's passes; the tensor-memory
+    // kernels (64-point plain passes with at most four items per block) keep
+    // split TF32
+    const bool tm64 = ax.N == 64 && !acc && !grad && items <= 4 * grid;
+    if (ax.bf_t[0] && !tm64)
+      e = launch_dense_bf16(d, ax.bf_t[adjoint ? 1 : 0], p->dev_err, (int)grid, stream);
+    else
+      e = launch_dense_tc(d, ax.tc_t[adjoint ? 1 : 0], p->dev_err, (int)grid, stream);
   } else if (cform == FFX_FORM_DENSE || cform == FFX_FORM_TC) {
     DenseArgs d;
     std::memset(&d, 0, sizeof(d));
@@ -813,12 +822,21 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
   if (ndim < 1 || ndim > 3) return fail(FFX_EINVAL, "ndim must be 1..3, got %d", ndim);
   if (!dims || !spacing || !magnification) return fail(FFX_EINVAL, "dims/spacing/magnification is NULL");
   if (!std::isfinite(t)) return fail(FFX_EINVAL, "t must be finite");
-  const uint32_t known = FFX_FORM_MASK | FFX_ACCUMULATE | FFX_TUNE | FFX_UNFUSED | FFX_TC_UNSPLIT;
+  const uint32_t known =
+      FFX_FORM_MASK | FFX_ACCUMULATE | FFX_TUNE | FFX_UNFUSED | FFX_TC_UNSPLIT | FFX_TC_BF16 | FFX_TC_TF32;
   if (flags & ~known) return fail(FFX_EINVAL, "unknown flag bits 0x%x", flags & ~known);
   const uint32_t form = flags & FFX_FORM_MASK;
   if (form > FFX_FORM_TC) return fail(FFX_EINVAL, "unknown form %u", form);
   if ((flags & FFX_TC_UNSPLIT) && form != FFX_FORM_TC)
     return fail(FFX_EINVAL, "FFX_TC_UNSPLIT needs FFX_FORM_TC");
+  if ((flags & FFX_TC_BF16) && form != FFX_FORM_TC && form != FFX_FORM_AUTO)
+    return fail(FFX_EINVAL, "FFX_TC_BF16 needs FFX_FORM_TC or FFX_FORM_AUTO");
+  if ((flags & FFX_TC_TF32) && (flags & FFX_TC_BF16)) return fail(FFX_EINVAL, "FFX_TC_TF32 and FFX_TC_BF16 exclude each other");
+  // BF16 operands on the streaming tensor-core passes: asked for, or the
+  // automatic form's choice (split BF16 meets the FP32 bar and runs faster
+  // than split TF32) unless TF32 or the unsplit variant is asked for
+  const bool bf16_ops = (flags & FFX_TC_BF16) ||
+                        (form == FFX_FORM_AUTO && !(flags & (FFX_TC_TF32 | FFX_TC_UNSPLIT)));
   int64_t M = 1;
   for (int j = 0; j < ndim; ++j) {
     if (dims[j] < 1) return fail(FFX_EINVAL, "dims[%d] = %lld < 1", j, (long long)dims[j]);
@@ -1032,8 +1050,10 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
   if (rc == FFX_OK) {
     size_t tbytes = kTcHeader;
     for (int j = 0; j < ndim; ++j)
-      if (dense_tc_supported(p->axis[j].N) && p->axis[j].T && (form == FFX_FORM_AUTO || form == FFX_FORM_TC))
+      if (dense_tc_supported(p->axis[j].N) && p->axis[j].T && (form == FFX_FORM_AUTO || form == FFX_FORM_TC)) {
         tbytes += 2 * dense_tc_t_bytes(p->axis[j].N) + (p->axis[j].N == 64 ? fused_tc_slice_bytes() : 0);
+        if (bf16_ops && dense_bf16_supported(p->axis[j].N)) tbytes += 2 * dense_bf16_t_bytes(p->axis[j].N);
+      }
     e = cudaMalloc(&p->tc_mem, tbytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -1070,6 +1090,15 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
           ax.ft_ts = tcur;
           tcur += fused_tc_slice_bytes();
           e = launch_fused_tc_slices(ax.T, ax.ft_ts, s);
+        }
+        if (e == cudaSuccess && bf16_ops && dense_bf16_supported(ax.N)) {
+          for (int q = 0; q < 2; ++q) {
+            ax.bf_t[q] = tcur;
+            tcur += dense_bf16_t_bytes(ax.N);
+          }
+          e = launch_bf16_build_t(ax.T, ax.bf_t[0], ax.N, s);
+          if (e == cudaSuccess) e = launch_bf16_build_t(ax.TH, ax.bf_t[1], ax.N, s);
+          if (e == cudaSuccess) e = dense_bf16_prepare();
         }
         if (e == cudaSuccess)
           e = dense_tc_prepare();
@@ -1198,6 +1227,13 @@ int ffx_plan_destroy(ffx_plan_t p) {
   if (p->tables) cudaFree(p->tables);
   delete p;
   return FFX_OK;
+}
+
+int ffx_plan_tc_bf16(ffx_plan_t p) {
+  if (!p || p->many) return p ? 0 : -1;
+  for (int j = 0; j < p->ndim; ++j)
+    if (p->axis[j].bf_t[0]) return 1;
+  return 0;
 }
 
 int ffx_plan_set_wait_limit(ffx_plan_t p, int64_t polls) {

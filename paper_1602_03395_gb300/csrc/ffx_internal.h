@@ -117,6 +117,15 @@ cudaError_t launch_dense_tc(const DenseArgs& a, const unsigned char* Tblk, int* 
                             cudaStream_t stream);
 int64_t dense_tc_tiles(int N, int64_t ncols);
 cudaError_t launch_tc_build_t(const float2* T, unsigned char* Tblk, int N, cudaStream_t s);
+// the same passes with BF16 operands (ffx_tc16.cu, kind::f16): split into
+// heads and tails (three products), or unsplit with DenseArgs::unsplit; lines
+// of N points with N a multiple of 32 from 64 up to kDenseMaxN; same items
+// (dense_tc_tiles) and in-place rule as the split-TF32 kernel
+bool dense_bf16_supported(int N);
+size_t dense_bf16_t_bytes(int N);
+cudaError_t dense_bf16_prepare();
+cudaError_t launch_bf16_build_t(const float2* T, unsigned char* Tblk, int N, cudaStream_t s);
+cudaError_t launch_dense_bf16(const DenseArgs& a, const unsigned char* Tblk, int* err, int grid, cudaStream_t s);
 cudaError_t launch_identity(float2* I, int N, cudaStream_t s);
 
 // The d passes of a small lattice (every axis <= 64 points, dense form) in one

@@ -1,0 +1,550 @@
+// Dense form on the tensor cores with BF16 operands (tcgen05 kind::f16): the
+// per-axis map of lines of N points (N a multiple of 32, from 64 up to 1024)
+// as a real matrix product, split into BF16 heads and tails, accumulated in
+// FP32 in tensor memory.
+//
+// The real form of the complex map is that of the split-TF32 kernel
+// (ffx_tc.cu): every complex entry t = x + iy of T becomes the 2 x 2 block
+// [[x, -y], [y, x]], every complex input v = a + ib the pair (a, b), and the
+// product runs transposed, D[line][row] = sum_K X[line][K] T[row][K], so that
+// tensor-memory lane = line.  Each FP32 operand value v is split into
+// hi = bf16_rn(v) and lo = bf16_rn(v - hi): T at plan time, the input on the
+// fly.  X_hi T_hi accumulates in one FP32 accumulator and X_hi T_lo + X_lo T_hi
+// in a second one (the large accumulator then takes only 2N/16 steps, which
+// keeps the tensor cores' biased FP32 accumulation small); the lo*lo term and
+// the tails' own rounding leave ~2^-16 per operand pair, measured ~1e-6 on
+// the density.  Unsplit launches run X_hi T_hi alone (~2^-8 per product; the
+// reported BF16 variant).
+//
+// Against the split-TF32 kernel, a K-step covers 16 real K in the same 32
+// bytes of every operand row, so the shared-memory bytes per K halve for the
+// operands; the products run at the kind::f16 rate.  The FP32 input of a chunk
+// (32 KB) is exactly the size of its BF16 head and tail parts, so it lands in
+// the stage itself, each thread's bytes where its own BF16 rows go, and is
+// converted in place: no separate input ring, three 64 KB stages.
+//
+// Kernel: one persistent block of 416 threads per SM, warp-specialised.
+//  * warps 0-7 (producers), per K chunk of 64 real K, once the products of
+//    the chunk three back have freed its stage: thread 0 starts a bulk copy of
+//    the pre-split T chunk (head and tail, 128 rows x 64 K each, already in
+//    the tensor cores' K-major no-swizzle core-matrix order) on the stage's
+//    "copy" barrier, and every producer thread copies its share of the input
+//    into the stage (cp.async); two chunks later the thread converts its share
+//    into BF16 heads and tails in place (16-byte core-matrix rows, conflict
+//    free) and arrives on "full".
+//  * warp 8 (MMA): waits "copy" and "full", issues 4 K-steps x 3 products of
+//    tcgen05.mma kind::f16 (M = 128 lines, N = 128 rows, K = 16) into one of
+//    two accumulator pairs; tcgen05.commit frees the stage ("empty") and,
+//    after an item's last chunk, hands the accumulator on ("acc_full").
+//  * warps 9-12 (epilogue): read their 32-lane quarter of the accumulators,
+//    store complex64 or |.|^2 (or add |.|^2 over the batch in shared memory),
+//    and arrive on "acc_empty".
+// Items are (128 lines, 128 real rows) of the output, numbered row block
+// fastest so that blocks running together share the lines' inputs in L2.
+// Every wait is bounded; one that runs out sets the block's abort flag, the
+// block drains its own copies and products, frees its tensor memory, counts
+// the error and exits.
+#include <cuda_bf16.h>
+
+#include <cstring>
+
+#include "ffx_internal.h"
+#include "ffx_tcgen05.cuh"
+
+namespace ffx {
+
+namespace {
+
+using namespace tc;
+
+constexpr int BL = 128;                      // lines per item = MMA M = tensor-memory lanes
+constexpr int BR = 128;                      // real output rows per item = MMA N
+constexpr int BKC = 64;                      // real K per chunk: four K-steps of 16
+constexpr int BSMAX = 3;  // stages: 3, or 2 in backward launches (their gradient ring)
+constexpr int BCORE = 128;                   // bytes between core matrices along K
+constexpr int BSBO = (BKC / 8) * BCORE;      // 1024: between 8-row groups
+constexpr int BPART = BR * BKC * 2;          // 16 KB: one split part of a chunk (T or X)
+constexpr int BTCHUNK = 2 * BPART;           // T chunk: head, tail
+constexpr int BSTAGE = BTCHUNK + 2 * BPART;  // T chunk, X hi, X lo: 64 KB
+constexpr int BPROD = 256, BEPI = 128;
+constexpr int BTHREADS = BPROD + 32 + BEPI;  // 416
+constexpr int BMMA_WARP = BPROD / 32;        // warp 8; warps 9-12 are the epilogue
+constexpr int BITEMS = BL * (BKC / 8) / BPROD;  // 4 core-matrix rows (8 real K) per producer thread per chunk
+constexpr int BGRAD_CHUNK = BPROD * BITEMS * 16;  // 16 KB: a chunk's gradient factors (backward passes)
+constexpr int BEXTRA = (BR / 2) * BL * 4;       // accumulating launches: |.|^2 over the batch, [row][line]
+constexpr int BCOLS = 4 * BR;                   // two accumulator pairs: all 512 columns
+__host__ __device__ constexpr int bstages(bool grad) { return grad ? 2 : 3; }
+// stages, then the |.|^2 sums of accumulating launches or the gradient ring
+__host__ __device__ constexpr int bsmem(bool grad, bool acc) {
+  return bstages(grad) * BSTAGE + (acc ? BEXTRA : 0) + (grad ? bstages(grad) * BGRAD_CHUNK : 0);
+}
+static_assert(bsmem(false, true) <= 227 * 1024 && bsmem(true, false) <= 227 * 1024, "shared memory");
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+static_assert(BITEMS == 4, "producer mapping");
+
+__host__ __device__ __forceinline__ int brow_count(int N, int mt) {
+  const int left = 2 * N - mt * BR;
+  return left < BR ? left : BR;
+}
+
+// Line c of the pass (realization b when accumulating): offset of its first
+// point, or -1 past the end; br = its realization.
+__device__ __forceinline__ long long bline(const DenseArgs& a, int64_t c, int b, int& br) {
+  br = 0;
+  if (c >= a.ncols) return -1;
+  int64_t bo = c / a.inner;
+  const int64_t i = c - bo * a.inner;
+  if (a.acc) {
+    br = b;
+    bo += (int64_t)b * a.outer;
+  } else {
+    br = (int)(c / (a.outer * a.inner));
+  }
+  return bo * (int64_t)a.N * a.inner + i;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo_k, float hi_k) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(lo_k, hi_k);  // .x (element k) in the low half
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Split 8 consecutive real K values into their BF16 heads and tails.
+__device__ __forceinline__ void split8(const float* v, uint4& hi, uint4& lo, bool unsplit) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const __nv_bfloat162 hb = __floats2bfloat162_rn(v[2 * m], v[2 * m + 1]);
+    h[m] = *reinterpret_cast<const uint32_t*>(&hb);
+    if (!unsplit) {
+      const float2 hf = __bfloat1622float2(hb);
+      l[m] = pack_bf16(v[2 * m] - hf.x, v[2 * m + 1] - hf.y);
+    } else {
+      l[m] = 0u;
+    }
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// FULL: every row block has BR rows (2N a multiple of 128).  GRAD: backward
+// passes, whose input element is 2 grad * psi (the factors come through their
+// own ring; two stages).  ACC: the batch's |.|^2 summed in shared memory.
+template <bool FULL, bool GRAD, bool ACC>
+__global__ void __launch_bounds__(BTHREADS, 1)
+    dense_bf16_kernel(const DenseArgs a, const unsigned char* __restrict__ Tblk, int* err) {
+  constexpr int BSTAGES = bstages(GRAD);
+  extern __shared__ __align__(1024) unsigned char bsm[];
+  __shared__ __align__(8) uint64_t full_bar[BSMAX], empty_bar[BSMAX], copy_bar[BSMAX];
+  __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int s_abort;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int N = a.N;
+  const int mtiles = (2 * N + BR - 1) / BR;
+  const int kchunks = (2 * N) / BKC;
+  const int64_t items = ((a.ncols + BL - 1) / BL) * mtiles;
+  const int64_t my_items = (items - blockIdx.x + gridDim.x - 1) / gridDim.x;
+  if (my_items <= 0) return;
+  const int nb = ACC ? (int)a.batch : 1;
+  const bool unsplit = a.unsplit != 0;
+
+  if (warp == BMMA_WARP) tmem_alloc(&tmem_slot, BCOLS);
+  if (tid == 0) {
+    for (int s = 0; s < BSTAGES; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), BPROD);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+      mbar_init(smem_u32(&copy_bar[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&accf_bar[b]), 1);
+      mbar_init(smem_u32(&acce_bar[b]), BEPI);
+    }
+    mbar_init(smem_u32(&done_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t smem_base = smem_u32(bsm);
+
+  if (warp < BMMA_WARP) {
+    // ---------------- producers ----------------
+    const int t = tid;
+    const int64_t inner = a.inner;
+    const bool contiguous = (inner == 1);
+    const int64_t total = my_items * nb * kchunks;
+    unsigned char* graw = bsm + BSTAGES * BSTAGE;  // gradient factors, one slot per stage (backward)
+    // this thread's 4 core-matrix rows of a chunk: line n_i, K group kp_i
+    // (contiguous lines: two lines, n_0 = n_1 and n_2 = n_3; strided: one),
+    // at byte off_i of the stage's X head and X tail parts
+    auto item_line = [&](int i) { return contiguous ? (t & 7) + 8 * (t >> 5) + 64 * (i >> 1) : (t & (BL - 1)); };
+    auto item_kp = [&](int i) { return contiguous ? ((t >> 3) & 3) + 4 * (i & 1) : (t >> 7) * BITEMS + i; };
+    auto item_off = [&](int i) {
+      const int n = item_line(i);
+      return (n >> 3) * BSBO + item_kp(i) * BCORE + (n & 7) * 16;
+    };
+    // Issue side: chunk j's copies go into stage j % BSTAGES once the products
+    // of chunk j - BSTAGES have freed it: thread 0's bulk copy of the T chunk,
+    // and every thread's FP32 input, which lands where the thread's own BF16
+    // rows will go -- item i's first two complex points on its head row
+    // (X_hi + off_i), the next two on its tail row (X_lo + off_i) -- so that
+    // each thread converts its own bytes in place.  The chunk's position
+    // (item iw, realization ib, K chunk ikc) advances incrementally; the
+    // lines' offsets are computed once per item and realization.
+    int64_t ci = 0, iw = blockIdx.x;
+    int ib = 0, ikc = 0, is = 0;
+    long long ilb[2] = {-1, -1};
+    int ibr[2] = {0, 0};
+    bool lines_ok = false;
+    int last_u[BSMAX];
+#pragma unroll
+    for (int q = 0; q < BSMAX; ++q) last_u[q] = -1;
+    auto issue = [&]() -> bool {
+      if (ci < total) {
+        const int64_t u = ci / BSTAGES;
+        if (u >= 1 && !mbar_wait(smem_u32(&empty_bar[is]), (uint32_t)((u - 1) & 1), &s_abort)) return false;
+        unsigned char* st = bsm + is * BSTAGE;
+        const int mt = (int)(iw % mtiles);
+        if (t == 0) {
+          const uint32_t part = (uint32_t)(FULL ? BR : brow_count(N, mt)) * (BKC * 2);
+          const uint32_t cb = smem_u32(&copy_bar[is]);
+          mbar_expect_tx(cb, unsplit ? part : 2 * part);
+          const unsigned char* src = Tblk + ((size_t)mt * kchunks + ikc) * BTCHUNK;
+          if (unsplit) {
+            bulk_g2s(smem_u32(st), src, part, cb);  // the head rows only
+          } else if (part == (uint32_t)BPART) {
+            bulk_g2s(smem_u32(st), src, BTCHUNK, cb);  // head and tail in one copy
+          } else {
+            bulk_g2s(smem_u32(st), src, part, cb);
+            bulk_g2s(smem_u32(st + BPART), src + BPART, part, cb);
+          }
+          last_u[is] = (int)(u & 1);
+        }
+        if (!lines_ok) {
+          const int64_t ct = iw / mtiles;
+          ilb[0] = bline(a, ct * BL + item_line(0), ib, ibr[0]);
+          if (contiguous) ilb[1] = bline(a, ct * BL + item_line(2), ib, ibr[1]);
+          lines_ok = true;
+        }
+        const uint32_t xh = smem_u32(st + BTCHUNK), xl = xh + BPART;
+        const uint32_t gdst0 = smem_u32(graw + is * BGRAD_CHUNK) + (uint32_t)t * 16;
+#pragma unroll
+        for (int i = 0; i < BITEMS; ++i) {
+          const int li = contiguous ? (i >> 1) : 0;
+          const long long lb = ilb[li];
+          const bool valid = lb >= 0;
+          const int k0 = ikc * (BKC / 2) + 4 * item_kp(i);  // first complex point
+          const int64_t addr = valid ? lb + (int64_t)k0 * inner : 0;
+          const uint32_t off = (uint32_t)item_off(i);
+          // invalid lines read nothing and land as zeros (source size 0)
+          if (contiguous) {
+            cp_async16(xh + off, a.in + addr, valid ? 16 : 0);
+            cp_async16(xl + off, a.in + addr + (valid ? 2 : 0), valid ? 16 : 0);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              cp_async8((j < 2 ? xh : xl) + off + (uint32_t)((j & 1) * 8), a.in + addr + (valid ? j * inner : 0),
+                        valid ? 8 : 0);
+          }
+          if (GRAD) {
+            const int64_t gaddr = valid && a.grad_shared ? addr - (int64_t)ibr[li] * a.M : addr;
+            const uint32_t gd = gdst0 + (uint32_t)(i * BPROD * 16);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              cp_async4(gd + 4 * j, a.grad + gaddr + (valid ? j * inner : 0), valid ? 4 : 0);
+          }
+        }
+        ++ci;
+        is = is + 1 == BSTAGES ? 0 : is + 1;
+        if (++ikc == kchunks) {
+          ikc = 0;
+          lines_ok = false;
+          if (++ib == nb) {
+            ib = 0;
+            iw += gridDim.x;
+          }
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");  // one group per call, empty past the end
+      return true;
+    };
+    bool ok = true;
+#pragma unroll 1
+    for (int r = 0; r < BSTAGES - 1 && ok; ++r) ok = issue();
+#pragma unroll 1
+    for (int64_t c = 0; ok && c < total; ++c) {
+      // chunk c has landed: of this thread's groups only the BSTAGES - 2 newer ones may be pending
+      asm volatile("cp.async.wait_group %0;" ::"n"(BSTAGES - 2) : "memory");
+      const int s = (int)(c % BSTAGES);
+      unsigned char* xh = bsm + s * BSTAGE + BTCHUNK;
+      unsigned char* xl = xh + BPART;
+      const float4* gs = reinterpret_cast<const float4*>(graw + s * BGRAD_CHUNK) + t;
+#pragma unroll
+      for (int i = 0; i < BITEMS; ++i) {
+        const int off = item_off(i);
+        const float4 r0 = *reinterpret_cast<const float4*>(xh + off);
+        const float4 r1 = *reinterpret_cast<const float4*>(xl + off);
+        float v[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+        if (GRAD) {
+          // the input element is 2 grad * psi
+          const float4 g = gs[i * BPROD];
+          const float g4[4] = {2.f * g.x, 2.f * g.y, 2.f * g.z, 2.f * g.w};
+#pragma unroll
+          for (int m = 0; m < 8; ++m) v[m] *= g4[m >> 1];
+        }
+        uint4 hi, lo;
+        split8(v, hi, lo, unsplit);
+        *reinterpret_cast<uint4*>(xh + off) = hi;
+        if (!unsplit) *reinterpret_cast<uint4*>(xl + off) = lo;
+      }
+      fence_async_smem();
+      mbar_arrive(smem_u32(&full_bar[s]));
+      // the copies of chunk c + BSTAGES - 1, into the stage chunk c - 1 used
+      ok = issue();
+    }
+    // nothing of this thread's may still be in flight at exit
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (t == 0)
+      for (int q = 0; q < BSTAGES; ++q)
+        if (last_u[q] >= 0) mbar_wait_own(smem_u32(&copy_bar[q]), (uint32_t)last_u[q], &s_abort);
+  } else if (warp == BMMA_WARP) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int64_t g = 0, sub = 0;
+      bool ok = true;
+      for (int64_t it = 0; ok && it < my_items; ++it) {
+        const int mt = (int)((blockIdx.x + it * gridDim.x) % mtiles);
+        const uint32_t idesc = idesc_bf16(BL, FULL ? BR : brow_count(N, mt));
+        for (int b = 0; ok && b < nb; ++b, ++sub) {
+          const int buf = (int)(sub & 1);
+          const int64_t v = sub >> 1;
+          if (v >= 1 && !mbar_wait(smem_u32(&acce_bar[buf]), (uint32_t)((v - 1) & 1), &s_abort)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d1 = tmem + (uint32_t)(buf * 2 * BR), d2 = d1 + BR;
+          for (int kc = 0; kc < kchunks; ++kc, ++g) {
+            const int s = (int)(g % BSTAGES);
+            const int64_t u = g / BSTAGES;
+            if (!mbar_wait(smem_u32(&copy_bar[s]), (uint32_t)(u & 1), &s_abort) ||
+                !mbar_wait(smem_u32(&full_bar[s]), (uint32_t)(u & 1), &s_abort)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t th = smem_base + (uint32_t)(s * BSTAGE), tl = th + BPART;
+            const uint32_t xh = th + BTCHUNK, xl = xh + BPART;
+#pragma unroll
+            for (int ks = 0; ks < BKC / 16; ++ks) {
+              const uint32_t o = (uint32_t)(ks * 2 * BCORE);
+              const uint64_t dxh = make_desc(xh + o, BCORE, BSBO);
+              const uint64_t dth = make_desc(th + o, BCORE, BSBO);
+              const uint32_t more = (kc == 0 && ks == 0) ? 0u : 1u;
+              mma_f16(d1, dxh, dth, idesc, more);
+              if (!unsplit) {
+                mma_f16(d2, dxh, make_desc(tl + o, BCORE, BSBO), idesc, more);
+                mma_f16(d2, make_desc(xl + o, BCORE, BSBO), dth, idesc, 1u);
+              }
+            }
+            mma_commit(smem_u32(&empty_bar[s]));
+          }
+          if (ok) mma_commit(smem_u32(&accf_bar[buf]));
+        }
+      }
+      // whatever happened, the tensor cores finish this thread's work before exit
+      mma_commit(smem_u32(&done_bar));
+      mbar_wait_own(smem_u32(&done_bar), 0u, &s_abort);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue ----------------
+    const int q = warp & 3;       // tensor-memory lane quarter this warp may read
+    const int r = q * 32 + lane;  // line within the item
+    const int64_t inner = a.inner;
+    const bool contiguous = (inner == 1);
+    float* racc = reinterpret_cast<float*>(bsm + BSTAGES * BSTAGE);  // accumulating launches only
+    if (ACC)
+      for (int m = 0; m < BR / 2; ++m) racc[m * BL + r] = 0.f;
+    int64_t sub = 0;
+    bool ok = true;
+    for (int64_t it = 0; ok && it < my_items; ++it) {
+      const int64_t w = blockIdx.x + it * gridDim.x;
+      const int64_t ct = w / mtiles;
+      const int mt = (int)(w % mtiles);
+      const int nbase = mt * (BR / 2);
+      const int rows = FULL ? BR : brow_count(N, mt);
+      for (int b = 0; b < nb; ++b, ++sub) {
+        const int buf = (int)(sub & 1);
+        const int64_t v = sub >> 1;
+        // warp-uniform outcome: the tensor-memory loads below need the whole warp
+        ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&accf_bar[buf]), (uint32_t)(v & 1), &s_abort));
+        if (!ok) break;
+        tc_fence_after();
+        int br;
+        const long long base = bline(a, ct * BL + r, b, br);
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * BR);
+#pragma unroll 1
+        for (int j0 = 0; j0 < rows; j0 += 16) {
+          uint32_t x[16], z[16];
+          tmem_ld16(taddr + (uint32_t)j0, x);
+          if (!unsplit) tmem_ld16(taddr + (uint32_t)(BR + j0), z);
+          tmem_wait_ld();
+          float y[16];
+#pragma unroll
+          for (int m = 0; m < 16; ++m) y[m] = __uint_as_float(x[m]) + (unsplit ? 0.f : __uint_as_float(z[m]));
+          const int n0 = nbase + j0 / 2;  // complex outputs n0 .. n0 + 7 of this line
+          if (ACC) {
+#pragma unroll
+            for (int m = 0; m < 8; ++m)
+              racc[(j0 / 2 + m) * BL + r] += y[2 * m] * y[2 * m] + y[2 * m + 1] * y[2 * m + 1];
+          } else if (base >= 0) {
+            if (a.out_c) {
+              if (contiguous) {
+                float4* o = reinterpret_cast<float4*>(a.out_c + base + n0);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) o[m] = make_float4(y[4 * m], y[4 * m + 1], y[4 * m + 2], y[4 * m + 3]);
+              } else {
+#pragma unroll
+                for (int m = 0; m < 8; ++m) a.out_c[base + (int64_t)(n0 + m) * inner] = make_float2(y[2 * m], y[2 * m + 1]);
+              }
+            } else {
+              float dd[8];
+#pragma unroll
+              for (int m = 0; m < 8; ++m) dd[m] = y[2 * m] * y[2 * m] + y[2 * m + 1] * y[2 * m + 1];
+              if (contiguous) {
+                float4* o = reinterpret_cast<float4*>(a.out_d + base + n0);
+                o[0] = make_float4(dd[0], dd[1], dd[2], dd[3]);
+                o[1] = make_float4(dd[4], dd[5], dd[6], dd[7]);
+              } else {
+#pragma unroll
+                for (int m = 0; m < 8; ++m) a.out_d[base + (int64_t)(n0 + m) * inner] = dd[m];
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(smem_u32(&acce_bar[buf]));
+        if (ACC && b == nb - 1) {
+          if (base >= 0) {
+            const int64_t o0 = base - (int64_t)br * a.M + (int64_t)nbase * inner;
+            if (contiguous) {
+              float4* o = reinterpret_cast<float4*>(a.out_d + o0);
+#pragma unroll 1
+              for (int m = 0; m < rows / 8; ++m) {
+                float4 cur = o[m];
+                cur.x += racc[(4 * m) * BL + r];
+                cur.y += racc[(4 * m + 1) * BL + r];
+                cur.z += racc[(4 * m + 2) * BL + r];
+                cur.w += racc[(4 * m + 3) * BL + r];
+                o[m] = cur;
+              }
+            } else {
+#pragma unroll 1
+              for (int m = 0; m < rows / 2; ++m) a.out_d[o0 + (int64_t)m * inner] += racc[m * BL + r];
+            }
+          }
+          for (int m = 0; m < BR / 2; ++m) racc[m * BL + r] = 0.f;
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && s_abort && err) atomicAdd(err, 1);
+  if (warp == BMMA_WARP) {
+    tc_fence_after();
+    tmem_free(tmem, BCOLS);
+  }
+}
+
+// Pre-split BF16 T chunks from the complex map T [N][N]: for row block mt and
+// K chunk kc, a 32 KB block [head: 128 rows x 64 K][tail] in core-matrix
+// order; real (r, k') with r = 2n + p_out, k' = 2k + p_in holds the 2 x 2
+// block entry of T[n][k]; rows past 2N are zero.
+__global__ void bf16_build_t_kernel(const float2* __restrict__ T, unsigned char* __restrict__ Tblk, int N) {
+  const int R = 2 * N;
+  const int RP = (R + BR - 1) / BR * BR;
+  const int kchunks = R / BKC;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)RP * R;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / R), kp = (int)(idx - (int64_t)r * R);
+    const int n = r >> 1, po = r & 1, k = kp >> 1, pi = kp & 1;
+    float v = 0.f;
+    if (r < R) {
+      const float2 t = T[(int64_t)n * N + k];
+      v = po == 0 ? (pi == 0 ? t.x : -t.y) : (pi == 0 ? t.y : t.x);
+    }
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+    const int mt = r / BR, rr = r % BR, kc = kp / BKC, kk = kp % BKC;
+    unsigned char* blk = Tblk + ((size_t)mt * kchunks + kc) * BTCHUNK;
+    const int off = (rr >> 3) * BSBO + (kk >> 3) * BCORE + (rr & 7) * 16 + (kk & 7) * 2;
+    *reinterpret_cast<__nv_bfloat16*>(blk + off) = hi;
+    *reinterpret_cast<__nv_bfloat16*>(blk + BPART + off) = lo;
+  }
+}
+
+}  // namespace
+
+bool dense_bf16_supported(int N) { return N >= 64 && N <= kDenseMaxN && N % 32 == 0; }
+
+size_t dense_bf16_t_bytes(int N) { return (size_t)((2 * N + BR - 1) / BR) * ((2 * N) / BKC) * BTCHUNK; }
+
+cudaError_t dense_bf16_prepare() {
+  const void* f[6] = {(const void*)dense_bf16_kernel<true, false, false>,
+                      (const void*)dense_bf16_kernel<false, false, false>,
+                      (const void*)dense_bf16_kernel<true, false, true>,
+                      (const void*)dense_bf16_kernel<false, false, true>,
+                      (const void*)dense_bf16_kernel<true, true, false>,
+                      (const void*)dense_bf16_kernel<false, true, false>};
+  const int smem[6] = {bsmem(false, false), bsmem(false, false), bsmem(false, true),
+                       bsmem(false, true),  bsmem(true, false),  bsmem(true, false)};
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 6 && e == cudaSuccess; ++i)
+    e = cudaFuncSetAttribute(f[i], cudaFuncAttributeMaxDynamicSharedMemorySize, smem[i]);
+  return e;
+}
+
+cudaError_t launch_bf16_build_t(const float2* T, unsigned char* Tblk, int N, cudaStream_t s) {
+  bf16_build_t_kernel<<<256, 256, 0, s>>>(T, Tblk, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense_bf16(const DenseArgs& a, const unsigned char* Tblk, int* err, int grid, cudaStream_t s) {
+  const bool full = (2 * a.N) % BR == 0;
+  if (a.grad) {
+    // backward passes never accumulate over the batch
+    if (full)
+      dense_bf16_kernel<true, true, false><<<grid, BTHREADS, bsmem(true, false), s>>>(a, Tblk, err);
+    else
+      dense_bf16_kernel<false, true, false><<<grid, BTHREADS, bsmem(true, false), s>>>(a, Tblk, err);
+  } else if (a.acc) {
+    if (full)
+      dense_bf16_kernel<true, false, true><<<grid, BTHREADS, bsmem(false, true), s>>>(a, Tblk, err);
+    else
+      dense_bf16_kernel<false, false, true><<<grid, BTHREADS, bsmem(false, true), s>>>(a, Tblk, err);
+  } else {
+    if (full)
+      dense_bf16_kernel<true, false, false><<<grid, BTHREADS, bsmem(false, false), s>>>(a, Tblk, err);
+    else
+      dense_bf16_kernel<false, false, false><<<grid, BTHREADS, bsmem(false, false), s>>>(a, Tblk, err);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ffx

@@ -29,6 +29,8 @@ FFX_ACCUMULATE = 0x10
 FFX_TUNE = 0x20
 FFX_UNFUSED = 0x40
 FFX_TC_UNSPLIT = 0x80
+FFX_TC_BF16 = 0x100
+FFX_TC_TF32 = 0x200
 
 _FORMS = {"auto": FFX_FORM_AUTO, "paper": FFX_FORM_PAPER, "fold": FFX_FORM_FOLD, "dense": FFX_FORM_DENSE,
           "tc": FFX_FORM_TC}
@@ -112,6 +114,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ffx_plan_device_errors.restype = i32
     lib.ffx_plan_set_wait_limit.argtypes = [vp, i64]
     lib.ffx_plan_set_wait_limit.restype = i32
+    lib.ffx_plan_tc_bf16.argtypes = [vp]
+    lib.ffx_plan_tc_bf16.restype = i32
     lib.ffx_expand_noalloc.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(dbl), dbl,
                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(dbl),
                                        ctypes.POINTER(dbl), vp, i64, vp, vp]
@@ -172,11 +176,15 @@ class Plan:
 
     ``unsplit=True`` (with ``form="tc"``) runs one TF32 product per K-step
     on rounded operands instead of the split products: faster, with a
-    density error of order 1e-3 (FFX_TC_UNSPLIT)."""
+    density error of order 1e-3 (FFX_TC_UNSPLIT).  ``bf16=True`` (automatic
+    or tc form) gives the streaming tensor-core passes BF16 operands
+    (FFX_TC_BF16): split into heads and tails, or unsplit with
+    ``unsplit=True``; the automatic form takes split BF16 by default, and
+    ``tf32=True`` keeps split TF32 operands there (FFX_TC_TF32)."""
 
     def __init__(self, dims, spacing, t, magnification, a=None, abar=None,
                  form: str = "auto", accumulate: bool = False, tune: bool = False, fused: bool = True,
-                 omega=None, unsplit: bool = False):
+                 omega=None, unsplit: bool = False, bf16: bool = False, tf32: bool = False):
         lib = load_library()
         d = len(dims)
         self.dims = tuple(int(v) for v in dims)
@@ -185,7 +193,8 @@ class Plan:
         self.magnification = tuple(int(v) for v in magnification)
         self.accumulate = bool(accumulate)
         flags = (_FORMS[form] | (FFX_ACCUMULATE if accumulate else 0) | (FFX_TUNE if tune else 0)
-                 | (0 if fused else FFX_UNFUSED) | (FFX_TC_UNSPLIT if unsplit else 0))
+                 | (0 if fused else FFX_UNFUSED) | (FFX_TC_UNSPLIT if unsplit else 0)
+                 | (FFX_TC_BF16 if bf16 else 0) | (FFX_TC_TF32 if tf32 else 0))
         self.unsplit = bool(unsplit)
         arr = lambda ct, v: (ct * d)(*v) if v is not None else None  # noqa: E731
         h = ctypes.c_void_p()
@@ -215,6 +224,8 @@ class Plan:
         self.axis_forms = tuple(_FORM_NAMES[lib.ffx_plan_axis_form(h, j)] for j in range(d))
         # largest batch whose forward calls run as one launch (0: never)
         self.fused_max_batch = int(lib.ffx_plan_fused(h))
+        # BF16 operands on the streaming tensor-core passes (asked for, or the automatic default)
+        self.bf16 = lib.ffx_plan_tc_bf16(h) == 1
         self.fused = self.fused_max_batch >= 1
         self.M = 1
         for v in self.dims:

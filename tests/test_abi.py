@@ -51,10 +51,15 @@ def test_host_argument_checks(lib):
     odd = (ctypes.c_int64 * 1)(100)
     assert lib.ffx_plan(ctypes.byref(h), 1, odd, dx, ctypes.c_double(1.0), lam, None, None, 0) == 4
     assert lib.ffx_plan(ctypes.byref(h), 1, dims, dx, ctypes.c_double(float("nan")), lam, None, None, 0) == 1
-    assert lib.ffx_plan(ctypes.byref(h), 1, dims, dx, ctypes.c_double(1.0), lam, None, None, 0x100) == 1
+    assert lib.ffx_plan(ctypes.byref(h), 1, dims, dx, ctypes.c_double(1.0), lam, None, None, 0x400) == 1
     assert h.value is None
     lib.ffx_last_error.restype = ctypes.c_char_p
     assert b"flag" in lib.ffx_last_error()
+    # operand flags: BF16 with a non-tensor-core form, BF16 and TF32 together
+    assert lib.ffx_plan(ctypes.byref(h), 1, dims, dx, ctypes.c_double(1.0), lam, None, None, 0x100 | 0x2) == 1
+    assert b"FFX_TC_BF16" in lib.ffx_last_error()
+    assert lib.ffx_plan(ctypes.byref(h), 1, dims, dx, ctypes.c_double(1.0), lam, None, None, 0x100 | 0x200) == 1
+    assert b"exclude" in lib.ffx_last_error()
     # the unsplit tensor-core variant exists for the tensor-core form only
     for form in (0x0, 0x2, 0x3):
         assert lib.ffx_plan(ctypes.byref(h), 1, dims, dx, ctypes.c_double(1.0), lam, None, None, 0x80 | form) == 1
