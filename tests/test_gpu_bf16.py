@@ -31,6 +31,7 @@ CASES = [
     ((64, 64, 64), (30, 30, 3), 24),  # 64-point passes with more than four items per block
     ((16, 1024), (4, 7), 2),          # 1024-point lines (the 16-point axis: FP32)
     ((256, 32), (100, 6), 3),         # lam = 100 on a strided 256-point axis; 32-point lines keep TF32
+    ((128, 48), (7, 5), 2),           # a stride of 48 lines: per-thread loads instead of bulk copies
 ]
 
 
