@@ -725,6 +725,11 @@ def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary
     alu_peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
     hbm_peak = float(pk.get("hbm_gbs", 6800.0))
     out_bytes = 4 * int(np.prod(out_shape))
+    # operands of the dominant tensor-core launch: BF16 where the plan gives
+    # the streaming kernel's passes BF16 (lines of N = 32k >= 64 outside the
+    # tensor-memory kernels' 64-point case), else TF32
+    bf16_launch = (plan.bf16 and not fused_call and w.dims[order[dom]] >= 64 and w.dims[order[dom]] % 32 == 0
+                   and not (w.dims[order[dom]] == 64 and B_ * M // 64 <= 4 * 128 * SMS))
     if fused_call:
         # one cooperative launch runs every pass (dense map: FP32 SIMT, or the
         # tensor cores when every axis has 64 points); HBM sees the input read
@@ -743,22 +748,17 @@ def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary
         N, lam = w.dims[axis], w.lam[axis]
         axis_form = call_forms[axis]
         flops = pass_flops(N, lam, B_ * M // N, axis_form)
-        kernel_key = f"pass_{axis_form}_N{N}_lam{lam}_{w.key}"
-        if args.column is not None:
-            kernel_key += f"_column{args.column}"
-        traffic = load_traffic(f"{kernel_key}_b{B_}")
         # HBM view of the same launch: it reads and writes the batch once
         # (complex64; the last pass writes float32 densities)
         last = dom == launches - 1
+        kernel_key = f"pass_{axis_form}_N{N}_lam{lam}_{w.key}" + ("_bf16" if bf16_launch else "")
+        if args.column is not None:
+            kernel_key += f"_column{args.column}"
+        traffic = load_traffic(f"{kernel_key}_b{B_}" + ("_density" if last else ""))
         bytes_launch = B_ * M * (8 + (4 if last else 8))
         pass_names = [f"axis{order[k]}_N{w.dims[order[k]]}_lam{w.lam[order[k]]}_{call_forms[order[k]]}"
                       for k in range(launches)]
     achieved = flops / (mean_ms[dom] * 1e-3) / 1e12
-    # operands of the dominant tensor-core launch: BF16 where the plan gives
-    # the streaming kernel's passes BF16 (lines of N = 32k >= 64 outside the
-    # tensor-memory kernels' 64-point case), else TF32
-    bf16_launch = (plan.bf16 and not fused_call and w.dims[order[dom]] >= 64 and w.dims[order[dom]] % 32 == 0
-                   and not (w.dims[order[dom]] == 64 and B_ * M // 64 <= 4 * 128 * SMS))
     if axis_form == "tc":
         # split contraction on the tensor cores; `achieved` counts the
         # algorithmic 8 N^2 flops per line, the tensor cores execute 3x that
