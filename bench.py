@@ -106,6 +106,9 @@ def parse():
                     help="split TF32 operands on every tensor-core pass (the automatic form's BF16 default off)")
     ap.add_argument("--batch", type=int, default=None, help="realizations per step (default: workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fft-passes", action="store_true",
+                    help="time the FFT-form (fold) passes at lam = 1 and 2 on 64^3 x 64, 256^3 and 1-D N=1024 x 65536 "
+                         "lines, per pass against the HBM roofline (one JSON line)")
     ap.add_argument("--no-companion", action="store_true",
                     help="large_two_cloud: skip the 128x128x1024 quasicondensate extra record")
     ap.add_argument("--column", type=int, default=None, metavar="AXIS",
@@ -894,6 +897,60 @@ def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary
     }
 
 
+FFT_PASS_CASES = [
+    ("64^3 x 64", (64, 64, 64), 64),
+    ("256^3", (256, 256, 256), 1),
+    ("1-D N=1024 x 65536", (1024,), 65536),
+]
+
+
+def run_fft_passes(args, torch, dev, ffx):
+    """The FFT (fold) form's passes where they move more bytes than they
+    compute (lam = 1 and 2): per-pass CUDA events around each launch of a
+    traced graph (median of 20 replays), bytes = one read and one write of the
+    batch (complex64; the last pass writes float32 densities), against the
+    measured HBM copy figure."""
+    pk, pk_src = peaks()
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    cases = []
+    for name, dims, batch in FFT_PASS_CASES:
+        for lam in (1, 2):
+            d = len(dims)
+            plan = ffx.Plan(dims, (0.25,) * d, 1.0, (lam,) * d, form="fold")
+            M = int(np.prod(dims))
+            xs = [torch.randn((batch,) + dims, dtype=torch.complex64, device=dev) for _ in range(2)]
+            out = torch.empty((batch,) + dims, dtype=torch.float32, device=dev)
+            n = plan.launches_per_call(batch=batch)
+            for i in range(3):
+                ffx.ffx_expand(plan, xs[i % 2], out)
+            reps = 20
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * n * reps)]
+            g = torch.cuda.CUDAGraph()
+            plan.trace(ev)
+            with torch.cuda.graph(g):
+                for i in range(reps):
+                    ffx.ffx_expand(plan, xs[i % 2], out)
+            plan.trace(None)
+            g.replay()
+            torch.cuda.synchronize()
+            order = plan.pass_order()
+            passes = []
+            for k in range(n):
+                ms = statistics.median(ev[2 * (r * n + k)].elapsed_time(ev[2 * (r * n + k) + 1]) for r in range(reps))
+                byts = batch * M * (8 + (4 if k == n - 1 else 8))
+                passes.append({"axis": order[k], "N": dims[order[k]], "ms": ms, "bytes": byts,
+                               "gbs": byts / (ms * 1e-3) / 1e9, "frac": byts / (ms * 1e-3) / 1e9 / hbm,
+                               "out": "density" if k == n - 1 else "complex"})
+            cases.append({"case": name, "lam": lam, "batch": batch, "passes": passes})
+            plan.close()
+            del xs, out
+            torch.cuda.empty_cache()
+    print(json.dumps({"metric": "HBM GB/s of the FFT-form passes at lam <= 2", "unit": "GB/s", "peak": hbm,
+                      "peak_source": f"hbm_gbs, {pk_src}", "form": "fold", "timing":
+                      "CUDA events around each launch in a traced graph (event nodes add ~2-4 us per launch)",
+                      "cases": cases}), flush=True)
+
+
 # The companion record printed inside the line of a workload (the largest
 # configuration has two lattices: the two-cloud 256^3 is the headline, the
 # 128x128x1024 quasicondensate rides along as an extra record).
@@ -917,6 +974,12 @@ def run_ffx(args):
     from paper_1602_03395_gb300 import build as B
     B.build()
     from paper_1602_03395_gb300 import ffx
+
+    if args.fft_passes:
+        run_fft_passes(args, torch, dev, ffx)
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
 
     if args.workload == "mixed":
         rc = run_mixed(args, torch, dist, world, rank, dev)

@@ -1,15 +1,24 @@
-// Line FFTs held in registers and exchanged through shared memory.
+// Line FFTs held in registers, with the butterflies across threads done by
+// warp shuffles.
 //
-// A line of N complex points is transformed by T = N/E threads, each holding
-// E points.  Thread t "owns" the positions t + e*T, e = 0..E-1.  The transform
-// is a mixed-radix Stockham sequence (radices R_0 ... R_{S-1}, product N):
-// stage s with span Ns (product of the earlier radices) runs N/R_s butterflies
-// j = 0..N/R_s-1; butterfly j reads the points j + r*N/R_s, multiplies point
-// r by W_N^{r (j mod Ns) N/(Ns R_s)}, applies a radix-R_s DFT and writes
-// its outputs to (j div Ns)*Ns*R_s + (j mod Ns) + r*Ns.  The output is in
-// natural order.  Thread t runs the butterflies j = t + b*T, b < E/R_s; their
-// inputs are its owned positions (e = b + r*E/R_s), and so are the last
-// stage's outputs.  Only the stages in between go through shared memory.
+// A line of N = E * T complex points is transformed by T threads, each holding
+// E points: thread t owns the positions t + e T, e = 0..E-1 (natural order,
+// the layout of the forward input and of the inverse output).  With
+// n = t + T e and k = k_e + E k_t the DFT factorises as
+//   X[k_e + E k_t] = sum_t w_T^(t k_t) [ w_N^(t k_e) sum_e w_E^(e k_e) x[t + T e] ],
+// so the forward transform is
+//   1. an E-point DFT over the thread's own registers (radix 4, 8, 12 or 16),
+//   2. the twiddle w_N^(t k_e), read from a [k_e][t] table (conflict free),
+//   3. a T-point DFT across the threads for every k_e: log2 T radix-2
+//      decimation-in-frequency stages, partner t ^ d, by __shfl_xor_sync
+//      within a warp and through shared memory for the stages that cross
+//      warps (lines of more than 32 threads).
+// Its output is in the spectral layout: thread t's register e holds frequency
+// spec(t, e) = e + E * rev_T(t), rev_T the bit reversal of log2 T bits.  The
+// inverse transform takes the spectral layout (decimation in time across the
+// threads, the conjugate twiddles, the inverse E-point DFTs) and returns the
+// natural layout, so no reordering pass is needed; callers index k-space
+// tables and folds by spec(t, e).
 //
 // Every DFT here is unnormalised: forward sum x_n e^{-2 pi i m n / N},
 // inverse sum x_m e^{+2 pi i m n / N}.
@@ -133,6 +142,38 @@ __device__ __forceinline__ void dft16(float2* x) {
   }
 }
 
+// 12 = 4 x 3: with n = n1 + 4 n2 and k = 3 k1 + k2,
+// X[3 k1 + k2] = sum_n1 w_4^(n1 k1) w_12^(n1 k2) sum_n2 w_3^(n2 k2) x[n1 + 4 n2].
+template <bool INV>
+__device__ __forceinline__ void dft12(float2* x) {
+  float2 y[4][3];
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) {
+    float2 z[3] = {x[n1], x[n1 + 4], x[n1 + 8]};
+    dft3<INV>(z);
+    y[n1][0] = z[0];
+    y[n1][1] = z[1];
+    y[n1][2] = z[2];
+  }
+  // w_12^(n1 k2) for n1 = 1..3, k2 = 1..2: angles pi/6 (n1 k2 = 1), pi/3 (2),
+  // pi/2 (3), 2 pi/3 (4), pi (6)
+  const float c30 = 0.86602540378443865f, s30 = 0.5f;
+  const float sg = INV ? 1.f : -1.f;
+  y[1][1] = cmul(y[1][1], make_float2(c30, sg * s30));
+  y[1][2] = cmul(y[1][2], make_float2(s30, sg * c30));
+  y[2][1] = cmul(y[2][1], make_float2(s30, sg * c30));
+  y[2][2] = cmul(y[2][2], make_float2(-s30, sg * c30));
+  y[3][1] = rot90<INV>(y[3][1]);
+  y[3][2] = make_float2(-y[3][2].x, -y[3][2].y);
+#pragma unroll
+  for (int k2 = 0; k2 < 3; ++k2) {
+    float2 z[4] = {y[0][k2], y[1][k2], y[2][k2], y[3][k2]};
+    dft4<INV>(z);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) x[3 * k1 + k2] = z[k1];
+  }
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dft(float2* x) {
   if constexpr (R == 2) {
@@ -143,6 +184,8 @@ __device__ __forceinline__ void dft(float2* x) {
     dft4<INV>(x);
   } else if constexpr (R == 8) {
     dft8<INV>(x);
+  } else if constexpr (R == 12) {
+    dft12<INV>(x);
   } else if constexpr (R == 16) {
     dft16<INV>(x);
   } else {
@@ -152,26 +195,22 @@ __device__ __forceinline__ void dft(float2* x) {
 
 // ---- line plans ---------------------------------------------------------------
 
-template <int N_, int E_, int R0, int R1 = 1, int R2 = 1, int R3 = 1, int R4 = 1>
+__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
+
+// N = E * T points per line, T threads per line (a power of two), E points per
+// thread (4, 8, 12 or 16).
+template <int N_, int E_>
 struct LinePlan {
   static constexpr int N = N_;
   static constexpr int E = E_;
   static constexpr int T = N_ / E_;
-  static constexpr int S = (R1 > 1) + (R2 > 1) + (R3 > 1) + (R4 > 1) + 1;
-  static_assert(R0 * R1 * R2 * R3 * R4 == N_, "radices must multiply to N");
-  static_assert(E_ % R0 == 0 && E_ % R1 == 0 && E_ % R2 == 0 && E_ % R3 == 0 && E_ % R4 == 0,
-                "each radix must divide E");
-  static_assert(N_ % E_ == 0, "E must divide N");
-  static __host__ __device__ constexpr int radix(int s) {
-    return s == 0 ? R0 : s == 1 ? R1 : s == 2 ? R2 : s == 3 ? R3 : R4;
-  }
-  static __host__ __device__ constexpr int span(int s) {  // product of radices before s
-    return s == 0 ? 1 : span(s - 1) * radix(s - 1);
-  }
+  static_assert(N_ % E_ == 0 && (T & (T - 1)) == 0, "T = N / E must be a power of two");
+  static_assert(E_ == 4 || E_ == 8 || E_ == 12 || E_ == 16, "E must be 4, 8, 12 or 16");
+  static constexpr int LOG_T = ilog2(T);
 };
 
-// Padded shared-memory index: one spare slot every 16 points spreads the
-// stride-R stores of the Stockham stages over the banks.
+// Padded shared-memory index: one spare slot every 16 points spreads
+// stride-16 accesses over the banks.
 __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
 template <int N>
 struct Padded {
@@ -202,78 +241,119 @@ __device__ __forceinline__ void line_sync(unsigned key) {
   }
 }
 
-// Twiddles of the last stage, which depend only on the thread: kept in
-// registers when there are few of them (forward and inverse share them).
-template <class P>
-struct LastStageTw {
-  static constexpr int STAGE = P::S - 1;
-  static constexpr int R = P::radix(STAGE);
-  static constexpr int NB = P::E / R;
-  static constexpr int COUNT = NB * (R - 1);
-  static constexpr bool enabled = (P::S > 1) && COUNT <= 8;
-  float2 w[enabled ? COUNT : 1];
-  __device__ __forceinline__ void load(const float2* __restrict__ tw, int t) {
-    if constexpr (enabled) {
-      constexpr int Ns = P::span(STAGE);
-      constexpr int step = P::N / (Ns * R);
-#pragma unroll
-      for (int b = 0; b < NB; ++b) {
-        const int k = (t + b * P::T) % Ns;
-#pragma unroll
-        for (int r = 1; r < R; ++r) w[b * (R - 1) + r - 1] = tw[r * k * step];
-      }
-    }
-  }
-};
-
-// One butterfly stage on the registers (inputs at owned positions).
-template <class P, int STAGE, bool INV>
-__device__ __forceinline__ void stage_compute(float2 (&v)[P::E], const float2* __restrict__ tw, int t,
-                                              const LastStageTw<P>& twc) {
-  constexpr int R = P::radix(STAGE);
-  constexpr int Ns = P::span(STAGE);
-  constexpr int NB = P::E / R;
-  constexpr bool cached = (STAGE == P::S - 1) && LastStageTw<P>::enabled;
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    float2 x[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = v[b + r * NB];
-    if constexpr (Ns > 1) {
-      const int j = t + b * P::T;
-      const int k = j % Ns;
-      constexpr int step = P::N / (Ns * R);
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        float2 w;
-        if constexpr (cached) {
-          w = twc.w[b * (R - 1) + r - 1];
-        } else {
-          w = tw[r * k * step];
-        }
-        if (INV) w.y = -w.y;
-        x[r] = cmul(x[r], w);
-      }
-    }
-    dft<R, INV>(x);
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[b + r * NB] = x[r];
+template <int T>
+__device__ __forceinline__ int bitrev(int t) {
+  if constexpr (T <= 1) {
+    return 0;
+  } else {
+    return (int)(__brev((unsigned)t) >> (32 - ilog2(T)));
   }
 }
 
-// Store the outputs of stage STAGE to their Stockham positions.
-template <class P, int STAGE>
-__device__ __forceinline__ void stage_store(const float2 (&v)[P::E], float2* __restrict__ line, int t) {
-  constexpr int R = P::radix(STAGE);
-  constexpr int Ns = P::span(STAGE);
-  constexpr int NB = P::E / R;
-#pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    const int j = t + b * P::T;
-    const int base = (j / Ns) * Ns * R + (j % Ns);
-#pragma unroll
-    for (int r = 0; r < R; ++r) line[pad(base + r * Ns)] = v[b + r * NB];
+// Frequency held by thread t's register e after a forward transform (and
+// expected there by an inverse one).
+template <class P>
+__device__ __forceinline__ int spec_index(int t, int e) {
+  return e + P::E * bitrev<P::T>(t);
+}
+
+// Per-thread constants of a line transform: the shuffle mask of the thread's
+// line-group, and the cross-thread stage twiddles w_(2d)^j = e^{-i pi j / d},
+// j < d, of every distance d = 1, 2, .., T/2 in a block-shared table at
+// d + j (forward sign; the inverse takes their conjugates).
+template <class P>
+struct LineFftCtx {
+  const float2* stw;
+  unsigned mask;
+  __device__ __forceinline__ void init(const float2* stage_tw, unsigned key) {
+    stw = stage_tw;
+    mask = P::T >= 32 ? 0xffffffffu : key;
   }
+};
+
+// Twiddle tables of a line transform, filled by a whole block (NT threads):
+// tw2[k_e * T + t] = w_N^(t k_e) (the step between the local and the
+// cross-thread DFTs, from the length-N table tw[i] = w_N^i), and the stage
+// table stw[d + j] = w_(2d)^j (T entries; entry 0 unused).
+template <class P>
+__device__ __forceinline__ void fill_line_twiddles(float2* tw2, float2* stw, const float2* __restrict__ tw, int tid,
+                                                   int NT) {
+  for (int i = tid; i < P::N; i += NT) {
+    const int ke = i / P::T, t = i - ke * P::T;
+    tw2[i] = tw[(t * ke) % P::N];
+  }
+  for (int i = tid; i < P::T; i += NT) {
+    const int d = i > 0 ? 1 << (31 - __clz(i)) : 1;  // the power of two below or at i
+    float sn, cs;
+    sincospif((float)(i - d) / (float)d, &sn, &cs);
+    stw[i] = make_float2(cs, -sn);
+  }
+}
+
+// One radix-2 stage across threads at distance d (a power of two below T),
+// partner p = the value of thread t ^ d, w = w_(2d)^(t mod d):
+//  DIF (forward): bit clear: v + p; bit set: (p - v) w, i.e. (s v + p) w'
+//                 with s = -+1, w' = w or 1;
+//  DIT (inverse): bit clear: v + w* p; bit set: p - w* v, i.e. A v + B p
+//                 with (A, B) = (1, w*) or (-w*, 1).
+template <class P, bool INV>
+__device__ __forceinline__ void cross_stage(float2 (&v)[P::E], int t, int s, const LineFftCtx<P>& c, float2* line,
+                                            unsigned key) {
+  const int d = 1 << s;
+  const bool up = (t & d) != 0;
+  float2 w = c.stw[d + (t & (d - 1))];
+  if (INV) w.y = -w.y;
+  const float sg = up ? -1.f : 1.f;
+  const float2 wp = up ? w : make_float2(1.f, 0.f);                         // DIF
+  const float2 A = up ? make_float2(-w.x, -w.y) : make_float2(1.f, 0.f);    // DIT
+  const float2 B = up ? make_float2(1.f, 0.f) : w;
+  auto combine = [&](float2 x, float2 p) -> float2 {
+    if (!INV) return cmul(make_float2(fmaf(sg, x.x, p.x), fmaf(sg, x.y, p.y)), wp);
+    return cfma(B, p, cmul(A, x));
+  };
+  if (d < 32) {
+#pragma unroll
+    for (int e = 0; e < P::E; ++e) {
+      float2 p;
+      p.x = __shfl_xor_sync(c.mask, v[e].x, d);
+      p.y = __shfl_xor_sync(c.mask, v[e].y, d);
+      v[e] = combine(v[e], p);
+    }
+  } else {
+    // partner in another warp: through the line's exchange buffer, thread t's
+    // register e at e * T + t (consecutive threads, consecutive slots)
+    line_sync<P::T>(key);  // earlier readers of `line` are done
+#pragma unroll
+    for (int e = 0; e < P::E; ++e) line[pad(e * P::T + t)] = v[e];
+    line_sync<P::T>(key);
+#pragma unroll
+    for (int e = 0; e < P::E; ++e) v[e] = combine(v[e], line[pad(e * P::T + (t ^ d))]);
+  }
+}
+
+// Forward line transform: natural layout in, spectral layout out.  `line` is
+// the line's exchange buffer (used only by lines of more than 32 threads);
+// tw2 is the step-twiddle table (fill_step_twiddles).  Threads may still read
+// `line` on return: callers line_sync before writing it again.
+template <class P>
+__device__ __forceinline__ void fft_fwd(float2 (&v)[P::E], float2* line, const float2* tw2, int t, unsigned key,
+                                        const LineFftCtx<P>& c) {
+  dft<P::E, false>(v);
+#pragma unroll
+  for (int e = 1; e < P::E; ++e) v[e] = cmul(v[e], tw2[e * P::T + t]);
+#pragma unroll
+  for (int s = P::LOG_T - 1; s >= 0; --s) cross_stage<P, false>(v, t, s, c, line, key);
+}
+
+// Inverse line transform: spectral layout in, natural layout out.
+template <class P>
+__device__ __forceinline__ void fft_inv(float2 (&v)[P::E], float2* line, const float2* tw2, int t, unsigned key,
+                                        const LineFftCtx<P>& c) {
+#pragma unroll
+  for (int s = 0; s < P::LOG_T; ++s) cross_stage<P, true>(v, t, s, c, line, key);
+#pragma unroll
+  for (int e = 1; e < P::E; ++e) v[e] = cmulc(v[e], tw2[e * P::T + t]);
+  dft<P::E, true>(v);
 }
 
 template <class P>
@@ -288,28 +368,12 @@ __device__ __forceinline__ void store_owned(const float2 (&v)[P::E], float2* __r
   for (int e = 0; e < P::E; ++e) line[pad(t + e * P::T)] = v[e];
 }
 
-template <class P, int STAGE, bool INV>
-__device__ __forceinline__ void fft_from(float2 (&v)[P::E], float2* line, const float2* tw, int t,
-                                         unsigned key, const LastStageTw<P>& twc) {
-  stage_compute<P, STAGE, INV>(v, tw, t, twc);
-  if constexpr (STAGE + 1 < P::S) {
-    line_sync<P::T>(key);  // earlier readers of `line` are done
-    stage_store<P, STAGE>(v, line, t);
-    line_sync<P::T>(key);
-    load_owned<P>(v, line, t);
-    fft_from<P, STAGE + 1, INV>(v, line, tw, t, key, twc);
-  }
-}
-
-// Full line transform: v holds the input at owned positions and receives the
-// output at owned positions.  `line` is this line's shared exchange buffer.
-// It is written only after a line_sync, so earlier readers are safe; threads
-// may still be reading it on return, so the caller line_syncs before writing
-// it again.
-template <class P, bool INV>
-__device__ __forceinline__ void fft_line(float2 (&v)[P::E], float2* line, const float2* tw, int t,
-                                         unsigned key, const LastStageTw<P>& twc) {
-  fft_from<P, 0, INV>(v, line, tw, t, key, twc);
+// A spectral-layout line into natural order in shared memory.
+template <class P>
+__device__ __forceinline__ void store_spectral(const float2 (&v)[P::E], float2* __restrict__ line, int t) {
+  const int base = P::E * bitrev<P::T>(t);
+#pragma unroll
+  for (int e = 0; e < P::E; ++e) line[pad(base + e)] = v[e];
 }
 
 }  // namespace ffx

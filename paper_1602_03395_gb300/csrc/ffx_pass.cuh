@@ -4,10 +4,14 @@
 // A block holds G line-groups of T = N/E threads.  qg groups share one line
 // and split its sum over the fine momentum index q (group r takes
 // q = r, r + qg, ...; the paper notes the terms are independent, Sec. 7.1),
-// so a tile is G/qg lines.  The tile is loaded into shared memory with
-// coalesced accesses; each group transforms its line in registers (see
-// ffx_fft.cuh); the groups' partial sums are added in shared memory in group
-// order (deterministic); the result is staged back through shared memory and
+// so a tile is G/qg lines.  Tiles are loaded into shared memory by cp.async,
+// coalesced (along a contiguous line, or across neighbouring strided lines),
+// one tile ahead of the one being transformed; each group transforms its line
+// in registers, exchanging across its threads by warp shuffles (see
+// ffx_fft.cuh), and indexes the k-space phases and the fold by the spectral
+// position spec(t, e) of each register; the groups' partial sums are added in
+// shared memory in group order (deterministic); the result is staged back
+// through shared memory and
 // stored coalesced: complex64, or |.|^2 as float32, or |.|^2 summed over the
 // realizations of the batch (tiles then loop over b in order, so the sum is
 // deterministic and needs no atomics).
@@ -36,27 +40,58 @@ namespace ffx {
 template <class P, int G>
 struct PassSmem {
   static constexpr int NP = Padded<P::N>::value;
-  static constexpr size_t tw_off = 0;
-  static constexpr size_t fold_off = tw_off + sizeof(float2) * P::N;
+  static constexpr size_t tw_off = 0;                                   // w_N^(t k_e) as [k_e][t]
+  static constexpr size_t stw_off = tw_off + sizeof(float2) * P::N;     // stage twiddles (T)
+  static constexpr size_t fold_off = stw_off + sizeof(float2) * P::T;
+  // line offsets of three units (the one being stored, the one being
+  // transformed, the one in flight: a slot is rewritten only two units after
+  // its last reader), and tiles of two (transformed, in flight)
   static constexpr size_t base_off = (fold_off + sizeof(int) * P::N + 15) & ~size_t(15);
-  static constexpr size_t b_off = base_off + sizeof(long long) * G;
-  static constexpr size_t psi_off = (b_off + sizeof(int) * G + 15) & ~size_t(15);
-  static constexpr size_t work_off = psi_off + sizeof(float2) * G * NP;
+  static constexpr size_t b_off = base_off + 3 * sizeof(long long) * G;
+  static constexpr size_t psi_off = (b_off + 3 * sizeof(int) * G + 15) & ~size_t(15);
+  static constexpr size_t work_off = psi_off + 2 * sizeof(float2) * G * NP;
   static constexpr size_t bytes = work_off + sizeof(float2) * G * NP;
 };
 
-// Element idx of a tile copy -> (line l, point n): along n for contiguous
-// lines, along the line index for strided ones (neighbouring lines are
-// neighbours in memory), so either way the copy is coalesced.
-__device__ __forceinline__ void tile_coords(int idx, int N, int lines, bool contiguous, int& l, int& n) {
-  if (contiguous) {
-    l = idx / N;
-    n = idx - l * N;
-  } else {
-    n = idx / lines;
-    l = idx - n * lines;
+// A thread's walk over the elements idx = tid, tid + NT, ... of a tile copy,
+// element idx being (line l, point n) along n for contiguous lines and along
+// the line index for strided ones (neighbouring lines are neighbours in
+// memory), so either way the copy is coalesced; no division per element:
+// contiguous lines advance along n, strided ones along the line index (which
+// stays put when NT is a multiple of the tile's line count).
+template <int N>
+struct TileWalk {
+  int l, n, dl, dn;
+  bool contiguous;
+  int lines;
+  __device__ __forceinline__ TileWalk(int tid, int NT, bool contig, int LINES) : contiguous(contig), lines(LINES) {
+    if (contiguous) {
+      l = tid / N;
+      n = tid - l * N;
+      dl = NT / N;
+      dn = NT - dl * N;
+    } else {
+      l = tid % LINES;
+      n = tid / LINES;
+      dl = NT % LINES;
+      dn = NT / LINES;
+    }
   }
-}
+  __device__ __forceinline__ bool ok() const { return l < lines && n < N; }
+  __device__ __forceinline__ void next() {
+    l += dl;
+    n += dn;
+    if (contiguous) {
+      if (n >= N) {
+        n -= N;
+        ++l;
+      }
+    } else if (l >= lines) {
+      l -= lines;
+      ++n;
+    }
+  }
+};
 
 // Tiles first, first + step, ... (below min(last, number of tiles)) of one
 // pass.  Called by a whole block; uses `smem` (PassSmem<P, G>::bytes).
@@ -67,10 +102,11 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
   using SM = PassSmem<P, G>;
   constexpr int NP = SM::NP;
   float2* tw_s = reinterpret_cast<float2*>(smem + SM::tw_off);
+  float2* stw_s = reinterpret_cast<float2*>(smem + SM::stw_off);
   int* fold_s = reinterpret_cast<int*>(smem + SM::fold_off);
-  long long* base_s = reinterpret_cast<long long*>(smem + SM::base_off);
-  int* b_s = reinterpret_cast<int*>(smem + SM::b_off);
-  float2* psi_s = reinterpret_cast<float2*>(smem + SM::psi_off);
+  long long* const base_all = reinterpret_cast<long long*>(smem + SM::base_off);
+  int* const b_all = reinterpret_cast<int*>(smem + SM::b_off);
+  float2* const psi_all = reinterpret_cast<float2*>(smem + SM::psi_off);
   float2* work_s = reinterpret_cast<float2*>(smem + SM::work_off);
 
   if (a.acc && a.batch <= 0) return;  // nothing to sum (the host never launches this)
@@ -88,14 +124,13 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
   const unsigned key = line_sync_key<T>(lg, tid);
 
   __syncthreads();  // an earlier call on this block may still read shared memory
-  for (int i = tid; i < N; i += NT) {
-    tw_s[i] = a.tab.tw[i];
-    if constexpr (KIND == KIND_FWD_FOLD) fold_s[i] = a.tab.fold[i];
-  }
+  fill_line_twiddles<P>(tw_s, stw_s, a.tab.tw, tid, NT);
+  if constexpr (KIND == KIND_FWD_FOLD)
+    for (int i = tid; i < N; i += NT) fold_s[i] = a.tab.fold[i];
 
   __syncthreads();  // twiddles are in shared memory
-  LastStageTw<P> twc;
-  twc.load(tw_s, t);
+  LineFftCtx<P> fc;
+  fc.init(stw_s, key);
 
   const int lam = a.lam;
   const int64_t inner = a.inner;
@@ -105,85 +140,115 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
   if (last < ntiles) ntiles = last;
   const int nb_loop = a.acc ? (int)a.batch : 1;
 
-  float2* psi_line = psi_s + line * NP;
   float2* wl = work_s + lg * NP;
 
-  // per-thread index helper (q-independent): (lam * (t + e T)) mod N
+  // per-thread index helper (q-independent): (lam * j) mod N for the
+  // register's position j: the natural one t + e T (post-chirp gather of the
+  // paper form) or the spectral one spec(t, e) (the adjoint's fold gather)
   int nii[E];
   {
     const int lmod = lam % N;
-    const int step = (lmod * T) % N;
-    int v = (lmod * t) % N;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      nii[e] = v;
-      v += step;
-      if (v >= N) v -= N;
+      const int j = KIND == KIND_ADJ_FOLD ? spec_index<P>(t, e) : t + e * T;
+      nii[e] = (int)(((long long)lmod * j) % N);
     }
   }
+  // spectral position of register e: sbase + e (k-space tables, the fold)
+  const int sbase = spec_index<P>(t, 0);
 
-  for (int64_t tile = first; tile < ntiles; tile += step) {
-    float racc[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) racc[e] = 0.f;
-
-    for (int bl = 0; bl < nb_loop; ++bl) {
-      __syncthreads();  // previous users of base_s / psi_s / work_s are done
-      if (tid < LINES) {
-        const int64_t gline = tile * LINES + tid;
-        long long base = -1;
-        int b = 0;
-        if (gline < a.nlines) {
-          int64_t bo = gline / inner;
-          const int64_t i = gline - bo * inner;
-          if (a.acc) {
-            b = bl;
-            bo += (int64_t)bl * a.outer;
-          } else {
-            b = (int)(gline / per_real_lines);
-          }
-          base = bo * (int64_t)N * inner + i;
+  // The block's units -- (tile, realization) pairs, realizations innermost --
+  // run as a two-stage pipeline: while unit k is transformed and stored, the
+  // copies of unit k + 1 (cp.async, 8 bytes per point, coalesced along the
+  // line or across neighbouring strided lines) land in the other buffer.
+  const int64_t my_tiles = first < ntiles ? (ntiles - first + step - 1) / step : 0;
+  const int64_t units = my_tiles * nb_loop;
+  // lines' offsets of unit u into slot `slot` (threads below LINES)
+  auto unit_bases = [&](int64_t u, int slot) {
+    if (tid < LINES) {
+      const int64_t tile = first + (u / nb_loop) * step;
+      const int bl = (int)(u % nb_loop);
+      const int64_t gline = tile * LINES + tid;
+      long long base = -1;
+      int b = 0;
+      if (gline < a.nlines) {
+        int64_t bo = gline / inner;
+        const int64_t i = gline - bo * inner;
+        if (a.acc) {
+          b = bl;
+          bo += (int64_t)bl * a.outer;
+        } else {
+          b = (int)(gline / per_real_lines);
         }
-        base_s[tid] = base;
-        b_s[tid] = b;
+        base = bo * (int64_t)N * inner + i;
+      }
+      base_all[slot * G + tid] = base;
+      b_all[slot * G + tid] = b;
+    }
+  };
+  // the copies of a unit whose offsets are in slot `slot` into tile buffer
+  // `buf` (one commit group)
+  auto unit_loads = [&](int slot, int buf) {
+    const long long* bs = base_all + slot * G;
+    const uint32_t dst0 = (uint32_t)__cvta_generic_to_shared(psi_all + buf * G * NP);
+    for (TileWalk<N> w(tid, NT, contiguous, LINES); w.ok(); w.next()) {
+      const int l = w.l, n = w.n;
+      const long long base = bs[l];
+      const bool valid = base >= 0;
+      const float2* src = a.in + (valid ? base + (int64_t)n * inner : 0);
+      // invalid lines read nothing and land as zeros (source size 0)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst0 + (uint32_t)(l * NP + pad(n)) * 8u),
+                   "l"(src), "r"(valid ? 8 : 0)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if (units > 0) {
+    unit_bases(0, 0);
+    __syncthreads();
+    unit_loads(0, 0);
+  }
+  float racc[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) racc[e] = 0.f;
+  for (int64_t k = 0; k < units; ++k) {
+    const int buf = (int)(k & 1);
+    const int slot = (int)(k % 3), next_slot = slot == 2 ? 0 : slot + 1;
+    const int bl = (int)(k % nb_loop);
+    if (bl == 0) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) racc[e] = 0.f;
+    }
+    // unit k + 1's offsets (a slot last read by unit k - 2) and copies;
+    // after the barrier everyone is past unit k - 1, the last reader of the
+    // other tile buffer and of work_s
+    if (k + 1 < units) unit_bases(k + 1, next_slot);
+    __syncthreads();
+    if (k + 1 < units) {
+      unit_loads(next_slot, buf ^ 1);
+    } else {
+      asm volatile("cp.async.commit_group;" ::: "memory");  // an empty group keeps the count
+    }
+    asm volatile("cp.async.wait_group 1;" ::: "memory");  // this thread's copies of unit k
+    __syncthreads();                                       // ... and everyone's
+    const long long* base_s = base_all + slot * G;
+    const int* b_s = b_all + slot * G;
+    float2* const psi_s = psi_all + buf * G * NP;
+    float2* const psi_line = psi_s + line * NP;
+    if (a.grad) {
+      // backward passes: the input element is 2 grad * psi
+      for (TileWalk<N> w(tid, NT, contiguous, LINES); w.ok(); w.next()) {
+        const int l = w.l, n = w.n;
+        const long long base = base_s[l];
+        if (base < 0) continue;
+        const int64_t addr = base + (int64_t)n * inner;
+        const int64_t gaddr = a.grad_shared ? addr - (int64_t)b_s[l] * a.M : addr;
+        const float gr = 2.f * __ldg(a.grad + gaddr);
+        float2& x = psi_s[l * NP + pad(n)];
+        x = make_float2(x.x * gr, x.y * gr);
       }
       __syncthreads();
-      // the tile's loads go out U at a time per thread, then their stores (same values)
-      constexpr int U = 8;
-      for (int idx0 = tid; idx0 < LINES * N; idx0 += U * NT) {
-        float2 v[U];
-        float gr[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int idx = idx0 + u * NT;
-          v[u] = make_float2(0.f, 0.f);
-          gr[u] = 1.f;
-          if (idx < LINES * N) {
-            int l, n;
-            tile_coords(idx, N, LINES, contiguous, l, n);
-            const long long base = base_s[l];
-            if (base >= 0) {
-              const int64_t addr = base + (int64_t)n * inner;
-              v[u] = a.in[addr];  // plain load: passes may run in place
-              if (a.grad) {
-                const int64_t b = b_s[l];
-                const int64_t gaddr = a.grad_shared ? addr - b * a.M : addr;
-                gr[u] = 2.f * __ldg(a.grad + gaddr);
-              }
-            }
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int idx = idx0 + u * NT;
-          if (idx < LINES * N) {
-            int l, n;
-            tile_coords(idx, N, LINES, contiguous, l, n);
-            psi_s[l * NP + pad(n)] = a.grad ? make_float2(v[u].x * gr[u], v[u].y * gr[u]) : v[u];
-          }
-        }
-      }
-      __syncthreads();
+    }
 
       float2 res[E];
 #pragma unroll
@@ -196,11 +261,12 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
           const float2* Fq = a.tab.F + (size_t)q * N;
           float2 v[E];
 #pragma unroll
-          for (int e = 0; e < E; ++e) v[e] = cmul(psi_line[pad(t + e * T)], __ldg(Pq + t + e * T));
-          fft_line<P, false>(v, wl, tw_s, t, key, twc);
+          for (int e = 0; e < E; ++e)  // the q = 0 pre-chirp is 1
+            v[e] = q == 0 ? psi_line[pad(t + e * T)] : cmul(psi_line[pad(t + e * T)], __ldg(Pq + t + e * T));
+          fft_fwd<P>(v, wl, tw_s, t, key, fc);
 #pragma unroll
-          for (int e = 0; e < E; ++e) v[e] = cmul(v[e], __ldg(Kq + t + e * T));
-          fft_line<P, true>(v, wl, tw_s, t, key, twc);
+          for (int e = 0; e < E; ++e) v[e] = cmul(v[e], __ldg(Kq + (sbase + e)));
+          fft_inv<P>(v, wl, tw_s, t, key, fc);
           line_sync<T>(key);
           store_owned<P>(v, wl, t);
           line_sync<T>(key);
@@ -216,24 +282,32 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
           const float2* Kq = a.tab.Kf + (size_t)q * N;
           float2 v[E];
 #pragma unroll
-          for (int e = 0; e < E; ++e) v[e] = cmul(psi_line[pad(t + e * T)], __ldg(Pq + t + e * T));
-          fft_line<P, false>(v, wl, tw_s, t, key, twc);
+          for (int e = 0; e < E; ++e)  // the q = 0 pre-chirp is 1
+            v[e] = q == 0 ? psi_line[pad(t + e * T)] : cmul(psi_line[pad(t + e * T)], __ldg(Pq + t + e * T));
+          fft_fwd<P>(v, wl, tw_s, t, key, fc);
 #pragma unroll
-          for (int e = 0; e < E; ++e) v[e] = cmul(v[e], __ldg(Kq + t + e * T));
+          for (int e = 0; e < E; ++e) v[e] = cmul(v[e], __ldg(Kq + (sbase + e)));
+          if (lam == 1) {
+            // the fold is the identity: D = Kf_0 * FFT(psi), in place
+#pragma unroll
+            for (int e = 0; e < E; ++e) res[e] = cadd(res[e], v[e]);
+            continue;
+          }
           line_sync<T>(key);
-          store_owned<P>(v, wl, t);
+          store_spectral<P>(v, wl, t);
           line_sync<T>(key);
+          // D[j] at the register's spectral position j (the layout the inverse takes)
           if (g == 1) {
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-              int jq = t + e * T - qN;
+              int jq = (sbase + e) - qN;
               if (jq < 0) jq += N;
               res[e] = cadd(res[e], wl[pad(fold_s[jq])]);
             }
           } else {
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-              int jq = t + e * T - qN;
+              int jq = (sbase + e) - qN;
               if (jq < 0) jq += N;
               const int m0 = fold_s[jq];
               if (m0 >= 0) {
@@ -250,9 +324,9 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
           float2 v[E];
 #pragma unroll
           for (int e = 0; e < E; ++e) v[e] = psi_line[pad(t + e * T)];
-          fft_line<P, false>(v, wl, tw_s, t, key, twc);
+          fft_fwd<P>(v, wl, tw_s, t, key, fc);
           line_sync<T>(key);
-          store_owned<P>(v, psi_line, t);
+          store_spectral<P>(v, psi_line, t);  // D in natural order
         }
         __syncthreads();
         int qN = grp % N;
@@ -265,11 +339,12 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
           for (int e = 0; e < E; ++e) {
             int idx = nii[e] + qN;
             if (idx >= N) idx -= N;
-            v[e] = cmulc(psi_line[pad(idx)], __ldg(Kq + t + e * T));
+            v[e] = cmulc(psi_line[pad(idx)], __ldg(Kq + (sbase + e)));
           }
-          fft_line<P, true>(v, wl, tw_s, t, key, twc);
+          fft_inv<P>(v, wl, tw_s, t, key, fc);
 #pragma unroll
-          for (int e = 0; e < E; ++e) res[e] = cadd(res[e], cmulc(v[e], __ldg(Pq + t + e * T)));
+          for (int e = 0; e < E; ++e)  // the q = 0 pre-chirp is 1
+            res[e] = cadd(res[e], q == 0 ? v[e] : cmulc(v[e], __ldg(Pq + t + e * T)));
           qN += qstep;
           if (qN >= N) qN -= N;
         }
@@ -290,7 +365,7 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
       }
       if constexpr (KIND == KIND_FWD_FOLD) {
         if (QG > 1) __syncthreads();  // the other groups' buffers are read; wl is free again
-        if (grp == 0) fft_line<P, true>(res, wl, tw_s, t, key, twc);
+        if (grp == 0) fft_inv<P>(res, wl, tw_s, t, key, fc);
       }
 
       if (a.acc) {
@@ -303,9 +378,8 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
         __syncthreads();
         if (grp == 0) store_owned<P>(res, wl, t);
         __syncthreads();
-        for (int idx = tid; idx < LINES * N; idx += NT) {
-          int l, n;
-          tile_coords(idx, N, LINES, contiguous, l, n);
+        for (TileWalk<N> w(tid, NT, contiguous, LINES); w.ok(); w.next()) {
+          const int l = w.l, n = w.n;
           const long long base = base_s[l];
           if (base < 0) continue;
           const int64_t addr = base + (int64_t)n * inner;
@@ -317,9 +391,8 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
           }
         }
       }
-    }  // batch loop
 
-    if (a.acc) {
+    if (a.acc && bl == nb_loop - 1) {
       __syncthreads();
       if (grp == 0) {
         float2 tmp[E];
@@ -328,9 +401,8 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
         store_owned<P>(tmp, wl, t);
       }
       __syncthreads();
-      for (int idx = tid; idx < LINES * N; idx += NT) {
-        int l, n;
-        tile_coords(idx, N, LINES, contiguous, l, n);
+      for (TileWalk<N> w(tid, NT, contiguous, LINES); w.ok(); w.next()) {
+        const int l = w.l, n = w.n;
         const long long base = base_s[l];
         if (base < 0) continue;
         // base_s holds the last realization's line; remove its batch offset
@@ -339,6 +411,7 @@ __device__ __forceinline__ void pass_tiles(const PassArgs& a, int64_t first, int
       }
     }
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 template <class P, int KIND, int G>
