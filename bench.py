@@ -605,6 +605,8 @@ def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary
     launches = plan.launches_per_call(batch=B_)
     fused_call = plan.fused and B_ <= plan.fused_max_batch  # all d passes in one launch
     call_forms = plan.call_forms(B_)  # the kernel each axis runs at this batch
+    # BF16 chain: one launch splits the input into BF16 planes, then the passes
+    chain = plan.bf16_chain(B_) and args.column is None
     extra_launches = 0
     if args.column is None:
         out_shape = (B_,) + tuple(w.dims)
@@ -618,6 +620,7 @@ def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary
         out_shape = (B_,) + tuple(n for j, n in enumerate(w.dims) if j != col)
         order = [j for j in order if j != col] + [col]
         extra_launches = 0 if fused_call else 1
+        launches = len(order) if not fused_call else launches
 
         def call(x, out=None):
             return ffx.ffx_expand_column(plan, x, col, out)
@@ -722,7 +725,9 @@ def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary
         # the launch time
         mean_ms = [ms / args.steps]
         launch_time = "one launch per step: the timed region's step time (CUDA events at its ends)"
-    dom = max(range(launches), key=lambda k: mean_ms[k])
+    # the lattice axis of each traced launch (None: the BF16 split of a chain)
+    launch_axis = ([None] if chain else []) + list(order)
+    dom = max((k for k in range(launches) if fused_call or launch_axis[k] is not None), key=lambda k: mean_ms[k])
     pk, pk_src = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     alu_peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
@@ -731,8 +736,9 @@ def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary
     # operands of the dominant tensor-core launch: BF16 where the plan gives
     # the streaming kernel's passes BF16 (lines of N = 32k >= 64 outside the
     # tensor-memory kernels' 64-point case), else TF32
-    bf16_launch = (plan.bf16 and not fused_call and w.dims[order[dom]] >= 64 and w.dims[order[dom]] % 32 == 0
-                   and not (w.dims[order[dom]] == 64 and B_ * M // 64 <= 4 * 128 * SMS))
+    dom_axis = order[0] if fused_call else launch_axis[dom]
+    bf16_launch = (plan.bf16 and not fused_call and w.dims[dom_axis] >= 64 and w.dims[dom_axis] % 32 == 0
+                   and not (w.dims[dom_axis] == 64 and B_ * M // 64 <= 4 * 128 * SMS))
     if fused_call:
         # one cooperative launch runs every pass (dense map: FP32 SIMT, or the
         # tensor cores when every axis has 64 points); HBM sees the input read
@@ -747,7 +753,7 @@ def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary
         bytes_launch = B_ * M * 8 + out_bytes
         pass_names = ["fused_" + "_".join(f"axis{j}" for j in order)]
     else:
-        axis = order[dom]
+        axis = dom_axis
         N, lam = w.dims[axis], w.lam[axis]
         axis_form = call_forms[axis]
         flops = pass_flops(N, lam, B_ * M // N, axis_form)
@@ -759,8 +765,8 @@ def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary
             kernel_key += f"_column{args.column}"
         traffic = load_traffic(f"{kernel_key}_b{B_}" + ("_density" if last else ""))
         bytes_launch = B_ * M * (8 + (4 if last else 8))
-        pass_names = [f"axis{order[k]}_N{w.dims[order[k]]}_lam{w.lam[order[k]]}_{call_forms[order[k]]}"
-                      for k in range(launches)]
+        pass_names = ["split_bf16_planes" if j is None else f"axis{j}_N{w.dims[j]}_lam{w.lam[j]}_{call_forms[j]}"
+                      for j in launch_axis]
     achieved = flops / (mean_ms[dom] * 1e-3) / 1e12
     if axis_form == "tc":
         # split contraction on the tensor cores; `achieved` counts the

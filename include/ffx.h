@@ -416,7 +416,9 @@ int ffx_plan_form(ffx_plan_t plan);
 int ffx_plan_axis_form(ffx_plan_t plan, int axis);
 
 /* Number of kernel launches one ffx_expand / ffx_expand_backward call makes
- * with a batch of one. */
+ * with a batch of one.  A call that runs as a BF16 chain
+ * (ffx_plan_bf16_chain) makes one more: the split of its input into BF16
+ * planes (in ffx_expand_backward: the forward half of a 3-D plan). */
 int ffx_launches_per_call(ffx_plan_t plan, int backward);
 
 /* The largest batch for which ffx_expand and ffx_expand_field run as one
@@ -442,6 +444,21 @@ int64_t ffx_plan_fused(ffx_plan_t plan);
  * not bit for bit; explicit forms never switch.  -1 on a bad argument or a
  * many-instance plan. */
 int ffx_plan_call_form(ffx_plan_t plan, int axis, int64_t batch);
+
+/* 1 if ffx_expand over `batch` realizations (16-byte aligned buffers) runs
+ * as a BF16 chain, else 0; -1 on a bad argument (ffx_expand_field and the
+ * forward half of ffx_expand_backward take the same chains).  A
+ * BF16 chain runs when every axis's pass of the call would take the
+ * streaming BF16 tensor-core kernel (FFX_TC_BF16, or the automatic form's
+ * default, and ffx_plan_call_form's choice FFX_FORM_TC): the passes run from
+ * the last axis to the first (ffx_plan_pass_order), each writing its output
+ * transposed -- point n' of a line goes n' (M / N_j) places after the line's
+ * first -- so that the next pass's lines are contiguous, and the fields
+ * between passes are kept as BF16 head and tail planes (bf16(v),
+ * bf16(v - bf16(v)) of each FP32 value v: the operands the next pass would
+ * split it into, so the results are those of the per-axis passes in the same
+ * order).  The planes use the plan's two field workspaces. */
+int ffx_plan_bf16_chain(ffx_plan_t plan, int64_t batch);
 
 /* Forward pass order: writes the lattice axis of pass k to order[k],
  * k = 0..ndim-1.  The adjoint runs the same axes in reverse. */

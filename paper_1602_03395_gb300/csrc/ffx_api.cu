@@ -147,6 +147,10 @@ struct ffx_plan_s {
   int sms = 1;
   Axis axis[3];
   int order[3] = {0, 1, 2};  // forward pass order
+  // every axis has BF16 operand blocks and the driver makes TMA maps: large
+  // forward calls may run as a BF16 chain (ffx_tc16.cu), whose order -- the
+  // last axis first -- is then the plan's forward order
+  int chain_bf16 = 0;
   void* tables = nullptr;
   void* dense_mem = nullptr;
   void* tc_mem = nullptr;    // split tensor-core operands + the fused launch's counters
@@ -301,21 +305,48 @@ bool tc_aligned(const void* in, const void* out_c, const void* out_d) {
   return ((uintptr_t)in & 15) == 0 && ((uintptr_t)out_c & 15) == 0 && ((uintptr_t)out_d & 15) == 0;
 }
 
-// Launch one pass of axis j (forward or adjoint) with the axis's form.
+// Profiling: with a trace set (ffx_plan_trace), each launch sits between a
+// pair of the caller's events; under stream capture they become event-record
+// nodes of the graph.  trace_begin returns the record flags, ~0u when the
+// trace is off or full.
+unsigned trace_begin(ffx_plan_s* p, cudaStream_t stream) {
+  if (!(p->trace && p->trace_i + 2 <= p->trace_n)) return ~0u;
+  unsigned rec_flags = cudaEventRecordDefault;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    rec_flags = cudaEventRecordExternal;
+  cudaEventRecordWithFlags((cudaEvent_t)p->trace[p->trace_i], stream, rec_flags);
+  return rec_flags;
+}
+void trace_end(ffx_plan_s* p, cudaStream_t stream, unsigned rec_flags) {
+  if (rec_flags == ~0u) return;
+  cudaEventRecordWithFlags((cudaEvent_t)p->trace[p->trace_i + 1], stream, rec_flags);
+  p->trace_i += 2;
+}
+
+// A pass of a BF16 chain (forward only): its lines are contiguous (the
+// previous pass wrote them transposed, or the axis is the last one), read
+// from BF16 planes (in_bf) or the FP32 field `in`; its output goes to BF16
+// planes (out_bf) or the caller's buffers, transposed: point n' of line rho
+// at n' (M / N) + rho of its realization.  plane: points per plane.
+struct ChainIo {
+  const uint32_t* in_bf;
+  uint32_t* out_bf;
+  int64_t plane;
+};
+
+// Launch one pass of axis j (forward or adjoint) with the axis's form, or,
+// with `io`, a pass of a BF16 chain.
 int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* grad, int grad_shared,
-             float2* out_c, float* out_d, int acc, int64_t batch, cudaStream_t stream) {
+             float2* out_c, float* out_d, int acc, int64_t batch, cudaStream_t stream, const ChainIo* io = nullptr) {
   const Axis& ax = p->axis[j];
   int64_t outer, inner;
   axis_outer_inner(p, j, &outer, &inner);
-  const bool traced = p->trace && p->trace_i + 2 <= p->trace_n;
-  // under stream capture the trace events become event-record nodes of the graph
-  unsigned rec_flags = cudaEventRecordDefault;
-  if (traced) {
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
-      rec_flags = cudaEventRecordExternal;
-    cudaEventRecordWithFlags((cudaEvent_t)p->trace[p->trace_i], stream, rec_flags);
+  if (io) {
+    outer = p->M / ax.N;
+    inner = 1;
   }
+  const unsigned rec_flags = trace_begin(p, stream);
   cudaError_t e;
   const int64_t lines = acc ? outer * inner : batch * outer * inner;
   const int cform = call_form(p, ax, lines);  // this call's form
@@ -343,10 +374,21 @@ int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* 
     // kernels (64-point plain passes with at most four items per block) keep
     // split TF32
     const bool tm64 = ax.N == 64 && !acc && !grad && items <= 4 * grid;
+    if (io) {
+      if (!ax.bf_t[0] || tm64 || adjoint || grad)
+        return fail(FFX_EUNSUPPORTED, "internal: a BF16 chain pass of axis %d without the BF16 kernel", j);
+      d.in_bf = io->in_bf;
+      d.out_bf = io->out_bf;
+      d.bf_plane = io->plane;
+      d.oouter = 1;
+      d.oinner = outer;
+    }
     if (ax.bf_t[0] && !tm64)
       e = launch_dense_bf16(d, ax.bf_t[adjoint ? 1 : 0], p->dev_err, (int)grid, stream);
     else
       e = launch_dense_tc(d, ax.tc_t[adjoint ? 1 : 0], p->dev_err, (int)grid, stream);
+  } else if (io) {
+    return fail(FFX_EUNSUPPORTED, "internal: a BF16 chain pass of axis %d off the tensor cores", j);
   } else if (cform == FFX_FORM_DENSE || cform == FFX_FORM_TC) {
     DenseArgs d;
     std::memset(&d, 0, sizeof(d));
@@ -415,10 +457,7 @@ int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* 
     e = info.launch(a, (int)grid, stream);
   }
   if (e != cudaSuccess) return cuda_fail(e, "pass launch");
-  if (traced) {
-    cudaEventRecordWithFlags((cudaEvent_t)p->trace[p->trace_i + 1], stream, rec_flags);
-    p->trace_i += 2;
-  }
+  trace_end(p, stream, rec_flags);
   return FFX_OK;
 }
 
@@ -437,6 +476,56 @@ bool plan_chain(const ffx_plan_s* p, const int* axes, int n, float2* final, floa
   return uses_alt;
 }
 
+// Whether a forward call over `batch` realizations runs as a BF16 chain:
+// the plan allows it, and every pass takes the BF16 streaming kernel in this
+// call (the per-axis passes' choice: tensor-core form, not the 64-point
+// tensor-memory kernel) with 16-byte aligned pointers.
+bool bf16_chain_ok(const ffx_plan_s* p, int64_t batch, const void* in, const void* out_c, const void* out_d) {
+  if (!p->chain_bf16 || p->many || !tc_aligned(in, out_c, out_d)) return false;
+  for (int r = 0; r < p->ndim; ++r) {
+    const Axis& ax = p->axis[p->order[r]];
+    const bool acc = r == p->ndim - 1 && out_d && p->acc;
+    const int64_t lines = (acc ? 1 : batch) * (p->M / ax.N);
+    if (call_form(p, ax, lines) != FFX_FORM_TC) return false;
+    const int64_t items = dense_tc_tiles(ax.N, lines);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(items, p->sms));
+    if (ax.N == 64 && !acc && items <= 4 * grid) return false;
+  }
+  return true;
+}
+
+// The forward map of a batch as a BF16 chain: the input split into BF16
+// planes in ws[1] (head plane, then tail plane: 8 bytes a point, the size of
+// a complex64 field), then the passes in the plan's order (the last axis
+// first), each reading planes and writing planes (ws[0], ws[1], ...), the
+// last one the caller's field (out_c) or densities (out_d, summed over the
+// batch with FFX_ACCUMULATE).  `in` is read by the split alone, so out_c may
+// equal it; it must not be ws[1].
+int chain_bf16(ffx_plan_s* p, const float2* in, int64_t batch, float2* out_c, float* out_d, cudaStream_t s) {
+  const int d = p->ndim;
+  int rc;
+  if ((rc = ensure_ws(p, 0, batch)) || (rc = ensure_ws(p, 1, batch))) return rc;
+  const int64_t plane = batch * p->M;
+  const int unsplit = (p->flags & FFX_TC_UNSPLIT) ? 1 : 0;
+  const unsigned rec = trace_begin(p, s);
+  cudaError_t e = launch_bf16_split(in, (uint32_t*)p->ws[1], plane, plane, unsplit, p->sms, s);
+  if (e != cudaSuccess) return cuda_fail(e, "BF16 split of the input");
+  trace_end(p, s, rec);
+  const uint32_t* cur_bf = (const uint32_t*)p->ws[1];
+  for (int r = 0; r < d; ++r) {
+    const bool last = r == d - 1;
+    ChainIo io;
+    io.in_bf = cur_bf;
+    io.out_bf = last ? nullptr : (uint32_t*)p->ws[r & 1];
+    io.plane = plane;
+    rc = run_axis(p, p->order[r], false, nullptr, nullptr, 0, last ? out_c : nullptr, last ? out_d : nullptr,
+                  last && out_d ? p->acc : 0, batch, s, &io);
+    if (rc) return rc;
+    cur_bf = io.out_bf;
+  }
+  return FFX_OK;
+}
+
 // Run a chain of passes (forward or adjoint) from `in` (read only) into
 // `out`; ws[alt_ws] serves as the alternate buffer and ws[1 - alt_ws] as the
 // spare copy of the input when an in-place call meets a pass that cannot run
@@ -444,6 +533,12 @@ bool plan_chain(const ffx_plan_s* p, const int* axes, int n, float2* final, floa
 int chain_into(ffx_plan_s* p, const int* axes, bool adjoint, const float2* in, const float* grad,
                int grad_shared, int64_t batch, float2* out, int alt_ws, cudaStream_t s) {
   const int d = p->ndim;
+  // forward fields take the BF16 chain (its planes live in ws[0] and ws[1])
+  // unless the input is ws[1], which its split writes, or the output is the
+  // buffer its last pass reads
+  if (!adjoint && !grad && axes == p->order && (const void*)in != p->ws[1] && (void*)out != p->ws[(d - 2) & 1] &&
+      bf16_chain_ok(p, batch, in, out, nullptr))
+    return chain_bf16(p, in, batch, out, nullptr, s);
   float2* outs[3];
   float2* probe[3];
   const bool need_alt = plan_chain(p, axes, d, out, (float2*)(uintptr_t)8, probe);
@@ -1164,6 +1259,14 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
       if (e != cudaSuccess) rc = cuda_fail(e, "tuning");
     }
   }
+  if (rc == FFX_OK && ndim >= 2 && dense_bf16_chain_supported()) {
+    bool all = true;
+    for (int j = 0; j < ndim; ++j) all = all && p->axis[j].bf_t[0] != nullptr;
+    if (all) {
+      p->chain_bf16 = 1;
+      for (int r = 0; r < ndim; ++r) p->order[r] = ndim - 1 - r;
+    }
+  }
   if (rc == FFX_OK) rc = plan_fusion(p);
   cudaStreamDestroy(s);
   if (rc != FFX_OK) {
@@ -1301,6 +1404,13 @@ int ffx_launches_per_call(ffx_plan_t p, int backward) {
 
 int64_t ffx_plan_fused(ffx_plan_t p) { return p ? p->fused : -1; }
 
+int ffx_plan_bf16_chain(ffx_plan_t p, int64_t batch) {
+  if (!p || batch < 1) return -1;
+  if (p->many || batch <= p->fused) return 0;
+  const void* aligned = (const void*)(uintptr_t)16;
+  return bf16_chain_ok(p, batch, aligned, aligned, aligned) ? 1 : 0;
+}
+
 int ffx_plan_call_form(ffx_plan_t p, int axis, int64_t batch) {
   if (!p || p->many || axis < 0 || axis >= p->ndim || batch < 1) return -1;
   if (batch <= p->fused) return p->fused_tc ? FFX_FORM_TC : FFX_FORM_DENSE;  // the fused launch
@@ -1317,6 +1427,8 @@ int ffx_plan_call_form(ffx_plan_t p, int axis, int64_t batch) {
 int forward_density(ffx_plan_s* p, const int* axes, const float2* in, int64_t batch, float* out_d,
                     cudaStream_t s) {
   const int d = p->ndim;
+  if (axes == p->order && (const void*)in != p->ws[1] && bf16_chain_ok(p, batch, in, nullptr, out_d))
+    return chain_bf16(p, in, batch, nullptr, out_d, s);
   const float2* cur = in;
   int rc;
   if (d > 1) {

@@ -94,6 +94,14 @@ struct DenseArgs {
   int N;
   int acc, grad_shared;
   int unsplit;  // tensor-core kernels: one TF32 product (operands rounded, no tails)
+  // BF16 pass chains (ffx_tc16.cu): the input (in_bf) and/or the output
+  // (out_bf) as BF16 head and tail planes of (re, im) pairs, bf_plane pairs
+  // apart (the tail plane is absent from unsplit chains); the output's own
+  // line decomposition (oouter, oinner; 0 = the input's)
+  const uint32_t* in_bf;
+  uint32_t* out_bf;
+  int64_t bf_plane;
+  int64_t oouter, oinner;
 };
 const void* dense_kernel_func();
 cudaError_t launch_dense(const DenseArgs& a, int grid, cudaStream_t stream);
@@ -126,6 +134,13 @@ size_t dense_bf16_t_bytes(int N);
 cudaError_t dense_bf16_prepare();
 cudaError_t launch_bf16_build_t(const float2* T, unsigned char* Tblk, int N, cudaStream_t s);
 cudaError_t launch_dense_bf16(const DenseArgs& a, const unsigned char* Tblk, int* err, int grid, cudaStream_t s);
+// whether BF16 planes can be read as TMA tiles here (the driver offers
+// cuTensorMapEncodeTiled): the condition of the BF16 pass chain
+bool dense_bf16_chain_supported();
+// n complex values (n even, `in` 16-byte aligned) into BF16 head and tail
+// planes (the tail `plane` pairs after the head; head only when unsplit)
+cudaError_t launch_bf16_split(const float2* in, uint32_t* planes, int64_t n, int64_t plane, int unsplit, int sms,
+                              cudaStream_t s);
 cudaError_t launch_identity(float2* I, int N, cudaStream_t s);
 
 // The d passes of a small lattice (every axis <= 64 points, dense form) in one

@@ -41,6 +41,18 @@
 //    and arrive on "acc_empty".
 // Items are (128 lines, 128 real rows) of the output, numbered row block
 // fastest so that blocks running together share the lines' inputs in L2.
+//
+// BF16 pass chains: the d passes of a forward map run from the last axis to
+// the first, and every pass but the last writes its output as BF16 head and
+// tail planes, transposed: point n' of line rho (of R lines per realization)
+// goes to n' R + rho, so that the next axis is the contiguous one for the next
+// pass and, after the pass along axis 0, the lattice is back in its own
+// order.  The epilogue makes the split the next pass would have made of the
+// same FP32 value (bitwise the same operands), and writes 32 consecutive
+// lines per warp store.  A pass with BF16 planes as input needs no producers:
+// thread 0 loads each chunk's head and tail rows as one TMA tile (a 3-D map
+// over [plane][line][2N], 128-byte swizzle) straight into the layout the
+// tensor cores read (K-major, 128-byte swizzle), next to the T chunk.
 // Every wait is bounded; one that runs out sets the block's abort flag, the
 // block drains its own copies and products, frees its tensor memory, counts
 // the error and exits.
@@ -82,7 +94,10 @@ __host__ __device__ constexpr int bstages(bool grad, bool acc) { return grad ? 2
 __host__ __device__ constexpr int bsmem(bool grad, bool acc) {
   return bstages(grad, acc) * BSTAGE + (acc ? BEXTRA : 0) + (grad ? bstages(grad, acc) * BGRAD_CHUNK : 0);
 }
-static_assert(bsmem(false, true) <= 227 * 1024 && bsmem(true, false) <= 227 * 1024, "shared memory");
+// a launch's dynamic shared memory: 1 KB more, to start the stages on a
+// 1024-byte boundary (the swizzled tiles' atoms)
+__host__ __device__ constexpr int bsmem_launch(bool grad, bool acc) { return bsmem(grad, acc) + 1024; }
+static_assert(bsmem_launch(false, true) <= 227 * 1024 && bsmem_launch(true, false) <= 227 * 1024, "shared memory");
 
 // The 256 producer threads' named barrier (id 1): every thread passes its
 // flag and gets the AND of all of them, so that a decision to stop is the
@@ -131,6 +146,21 @@ __device__ __forceinline__ long long bline(const DenseArgs& a, int64_t c, int b,
   return bo * (int64_t)a.N * a.inner + i;
 }
 
+// The same for the output, with the output's decomposition (oouter, oinner).
+__device__ __forceinline__ long long bline_o(const DenseArgs& a, int64_t c, int b, int& br) {
+  br = 0;
+  if (c >= a.ncols) return -1;
+  int64_t bo = c / a.oinner;
+  const int64_t i = c - bo * a.oinner;
+  if (a.acc) {
+    br = b;
+    bo += (int64_t)b * a.oouter;
+  } else {
+    br = (int)(c / (a.oouter * a.oinner));
+  }
+  return bo * (int64_t)a.N * a.oinner + i;
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float lo_k, float hi_k) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(lo_k, hi_k);  // .x (element k) in the low half
   return *reinterpret_cast<const uint32_t*>(&h);
@@ -162,17 +192,22 @@ __device__ __forceinline__ void split8(const float* v, uint4& hi, uint4& lo, boo
 // thread converts its own bytes, with no barrier).  Measured on 256^3
 // passes: contiguous lines 0.17 ms by TMA against 0.20 ms per thread; strided
 // lines 0.17 ms per thread against 0.21 ms by a 3-D TMA tile.
-enum BLoad { kTmaContiguous = 0, kInPlace = 1 };
+// BF16 planes (a pass of a chain): the head and tail rows as one TMA tile.
+enum BLoad { kTmaContiguous = 0, kInPlace = 1, kTmaPlanes = 2 };
 
 // FULL: every row block has BR rows (2N a multiple of 128).  GRAD: backward
 // passes, whose input element is 2 grad * psi (the factors come through their
 // own ring; two stages).  ACC: the batch's |.|^2 summed in shared memory.
-template <bool FULL, bool GRAD, bool ACC>
+// INBF: the input is BF16 planes (mode kTmaPlanes; never with GRAD).
+template <bool FULL, bool GRAD, bool ACC, bool INBF>
 __global__ void __launch_bounds__(BTHREADS, 1)
     dense_bf16_kernel(const DenseArgs a, const unsigned char* __restrict__ Tblk, int* err,
                       const __grid_constant__ CUtensorMap xmap, const int mode) {
+  static_assert(!(GRAD && INBF), "backward passes take FP32 input");
   constexpr int BSTAGES = bstages(GRAD, ACC);
-  extern __shared__ __align__(1024) unsigned char bsm[];
+  extern __shared__ __align__(1024) unsigned char bsm_raw[];
+  // the stages on a 1024-byte boundary (the launch adds 1 KB for it)
+  unsigned char* const bsm = bsm_raw + ((1024u - (smem_u32(bsm_raw) & 1023u)) & 1023u);
   __shared__ __align__(8) uint64_t full_bar[BSMAX], empty_bar[BSMAX], copy_bar[BSMAX];
   __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], done_bar;
   __shared__ uint32_t tmem_slot;
@@ -210,7 +245,62 @@ __global__ void __launch_bounds__(BTHREADS, 1)
   const uint32_t tmem = tmem_slot;
   const uint32_t smem_base = smem_u32(bsm);
 
-  if (warp < BMMA_WARP) {
+  if (INBF && warp < BMMA_WARP) {
+    // ---------------- loads of a BF16-plane input: thread 0 alone ----------------
+    if (tid == 0) {
+      const int64_t total = my_items * nb * kchunks;
+      const uint64_t map_addr = reinterpret_cast<uint64_t>(&xmap);
+      const uint32_t xbytes = unsplit ? (uint32_t)BPART : (uint32_t)BXAREA;
+      int64_t iw = blockIdx.x, u = 0;
+      int ib = 0, ikc = 0, is = 0;
+      int last_u[BSMAX];
+#pragma unroll
+      for (int q = 0; q < BSMAX; ++q) last_u[q] = -1;
+#pragma unroll 1
+      for (int64_t ci = 0; ci < total; ++ci) {
+        // chunk ci into stage is once the products of chunk ci - BSTAGES freed it
+        if (u >= 1 && !mbar_wait(smem_u32(&empty_bar[is]), (uint32_t)((u - 1) & 1), &s_abort)) break;
+        const int mt = (int)(iw % mtiles);
+        const int64_t ct = iw / mtiles;
+        const uint32_t st = smem_u32(bsm + is * BSTAGE);
+        const uint32_t part = (uint32_t)(FULL ? BR : brow_count(N, mt)) * (BKC * 2);
+        const uint32_t cb = smem_u32(&copy_bar[is]);
+        mbar_expect_tx(cb, (unsplit ? part : 2 * part) + xbytes);
+        const unsigned char* src = Tblk + ((size_t)mt * kchunks + ikc) * BTCHUNK;
+        if (unsplit) {
+          bulk_g2s(st, src, part, cb);
+        } else if (part == (uint32_t)BPART) {
+          bulk_g2s(st, src, BTCHUNK, cb);
+        } else {
+          bulk_g2s(st, src, part, cb);
+          bulk_g2s(st + BPART, src + BPART, part, cb);
+        }
+        // rows: the tile's lines (realization ib's when accumulating); x: the
+        // chunk's 64 real K; z: the head plane (and the tail plane)
+        const int row = (int)(ct * BL + (ACC ? (int64_t)ib * a.outer : 0));
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+            "[%5];" ::"r"(st + (uint32_t)BTCHUNK),
+            "l"(map_addr), "r"(ikc * BKC), "r"(row), "r"(0), "r"(cb)
+            : "memory");
+        last_u[is] = (int)(u & 1);
+        if (++is == BSTAGES) {
+          is = 0;
+          ++u;
+        }
+        if (++ikc == kchunks) {
+          ikc = 0;
+          if (++ib == nb) {
+            ib = 0;
+            iw += gridDim.x;
+          }
+        }
+      }
+      // nothing of this thread's may still be in flight at exit
+      for (int q = 0; q < BSTAGES; ++q)
+        if (last_u[q] >= 0) mbar_wait_own(smem_u32(&copy_bar[q]), (uint32_t)last_u[q], &s_abort);
+    }
+  } else if (warp < BMMA_WARP) {
     // ---------------- producers ----------------
     const int t = tid;
     const int64_t inner = a.inner;
@@ -423,7 +513,7 @@ __global__ void __launch_bounds__(BTHREADS, 1)
             const int s = (int)(g % BSTAGES);
             const int64_t u = g / BSTAGES;
             if (!mbar_wait(smem_u32(&copy_bar[s]), (uint32_t)(u & 1), &s_abort) ||
-                !mbar_wait(smem_u32(&full_bar[s]), (uint32_t)(u & 1), &s_abort)) {
+                (!INBF && !mbar_wait(smem_u32(&full_bar[s]), (uint32_t)(u & 1), &s_abort))) {
               ok = false;
               break;
             }
@@ -433,13 +523,16 @@ __global__ void __launch_bounds__(BTHREADS, 1)
 #pragma unroll
             for (int ks = 0; ks < BKC / 16; ++ks) {
               const uint32_t o = (uint32_t)(ks * 2 * BCORE);
-              const uint64_t dxh = make_desc(xh + o, BCORE, BSBO);
+              // X: core matrices of the producers, or the swizzled TMA tile (32 bytes per K step)
+              const uint64_t dxh = INBF ? make_desc_sw128(xh + (uint32_t)(ks * 32)) : make_desc(xh + o, BCORE, BSBO);
               const uint64_t dth = make_desc(th + o, BCORE, BSBO);
               const uint32_t more = (kc == 0 && ks == 0) ? 0u : 1u;
               mma_f16(d1, dxh, dth, idesc, more);
               if (!unsplit) {
+                const uint64_t dxl =
+                    INBF ? make_desc_sw128(xl + (uint32_t)(ks * 32)) : make_desc(xl + o, BCORE, BSBO);
                 mma_f16(d2, dxh, make_desc(tl + o, BCORE, BSBO), idesc, more);
-                mma_f16(d2, make_desc(xl + o, BCORE, BSBO), dth, idesc, 1u);
+                mma_f16(d2, dxl, dth, idesc, 1u);
               }
             }
             mma_commit(smem_u32(&empty_bar[s]));
@@ -456,7 +549,7 @@ __global__ void __launch_bounds__(BTHREADS, 1)
     // ---------------- epilogue ----------------
     const int q = warp & 3;       // tensor-memory lane quarter this warp may read
     const int r = q * 32 + lane;  // line within the item
-    const int64_t inner = a.inner;
+    const int64_t inner = a.oinner;  // the output's decomposition
     const bool contiguous = (inner == 1);
     float* racc = reinterpret_cast<float*>(bsm + BSTAGES * BSTAGE);  // accumulating launches only
     if (ACC)
@@ -479,7 +572,7 @@ __global__ void __launch_bounds__(BTHREADS, 1)
         if (!ok) break;
         tc_fence_after();
         int br;
-        const long long base = bline(a, ct * BL + r, b, br);
+        const long long base = bline_o(a, ct * BL + r, b, br);
         const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * BR);
 #pragma unroll 1
         for (int j0 = 0; j0 < rows; j0 += 16) {
@@ -496,7 +589,19 @@ __global__ void __launch_bounds__(BTHREADS, 1)
             for (int m = 0; m < 8; ++m)
               racc[(j0 / 2 + m) * BL + r] += y[2 * m] * y[2 * m] + y[2 * m + 1] * y[2 * m + 1];
           } else if (base >= 0) {
-            if (a.out_c) {
+            if (a.out_bf) {
+              // BF16 head and tail planes for the next pass of a chain
+#pragma unroll
+              for (int m = 0; m < 8; ++m) {
+                const __nv_bfloat162 hb = __floats2bfloat162_rn(y[2 * m], y[2 * m + 1]);
+                const int64_t e = base + (int64_t)(n0 + m) * inner;
+                a.out_bf[e] = *reinterpret_cast<const uint32_t*>(&hb);
+                if (!unsplit) {
+                  const float2 hf = __bfloat1622float2(hb);
+                  a.out_bf[a.bf_plane + e] = pack_bf16(y[2 * m] - hf.x, y[2 * m + 1] - hf.y);
+                }
+              }
+            } else if (a.out_c) {
               if (contiguous) {
                 float4* o = reinterpret_cast<float4*>(a.out_c + base + n0);
 #pragma unroll
@@ -583,24 +688,66 @@ __global__ void bf16_build_t_kernel(const float2* __restrict__ T, unsigned char*
   }
 }
 
+// The first pass of a BF16 chain reads its FP32 input as BF16 planes too:
+// every (re, im) pair v becomes bf16(v) in the head plane and bf16(v - bf16(v))
+// in the tail plane (the split the pass would make on the fly), in the same
+// order; two pairs per thread step, 16-byte loads.
+__global__ void __launch_bounds__(256) bf16_split_kernel(const float4* __restrict__ in, uint2* __restrict__ hi,
+                                                          uint2* __restrict__ lo, int64_t n2, int unsplit) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v = in[i];
+    const __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y), h1 = __floats2bfloat162_rn(v.z, v.w);
+    hi[i] = make_uint2(*reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1));
+    if (!unsplit) {
+      const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+      lo[i] = make_uint2(pack_bf16(v.x - f0.x, v.y - f0.y), pack_bf16(v.z - f1.x, v.w - f1.y));
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_bf16_split(const float2* in, uint32_t* planes, int64_t n, int64_t plane, int unsplit, int sms,
+                              cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t n2 = n / 2;  // n is even: whole realizations of lattices of >= 64 points
+  int64_t grid = (n2 + 255) / 256;
+  if (grid > 8 * (int64_t)sms) grid = 8 * (int64_t)sms;
+  bf16_split_kernel<<<(int)grid, 256, 0, s>>>(reinterpret_cast<const float4*>(in), reinterpret_cast<uint2*>(planes),
+                                              reinterpret_cast<uint2*>(planes + plane), n2, unsplit);
+  return cudaGetLastError();
+}
 
 bool dense_bf16_supported(int N) { return N >= 64 && N <= kDenseMaxN && N % 32 == 0; }
 
 size_t dense_bf16_t_bytes(int N) { return (size_t)((2 * N + BR - 1) / BR) * ((2 * N) / BKC) * BTCHUNK; }
 
+namespace {
+
+// the kernel's variants, indexed [FULL][kind], kind 0 plain, 1 ACC, 2 GRAD,
+// 3 INBF, 4 INBF + ACC
+using BKernel = void (*)(const DenseArgs, const unsigned char*, int*, const CUtensorMap, const int);
+constexpr int kBKinds = 5;
+BKernel bf16_kernel(bool full, int kind) {
+  static const BKernel k[2][kBKinds] = {
+      {dense_bf16_kernel<false, false, false, false>, dense_bf16_kernel<false, false, true, false>,
+       dense_bf16_kernel<false, true, false, false>, dense_bf16_kernel<false, false, false, true>,
+       dense_bf16_kernel<false, false, true, true>},
+      {dense_bf16_kernel<true, false, false, false>, dense_bf16_kernel<true, false, true, false>,
+       dense_bf16_kernel<true, true, false, false>, dense_bf16_kernel<true, false, false, true>,
+       dense_bf16_kernel<true, false, true, true>}};
+  return k[full ? 1 : 0][kind];
+}
+int bf16_kind_smem(int kind) { return bsmem_launch(kind == 2, kind == 1 || kind == 4); }
+
+}  // namespace
+
 cudaError_t dense_bf16_prepare() {
-  const void* f[6] = {(const void*)dense_bf16_kernel<true, false, false>,
-                      (const void*)dense_bf16_kernel<false, false, false>,
-                      (const void*)dense_bf16_kernel<true, false, true>,
-                      (const void*)dense_bf16_kernel<false, false, true>,
-                      (const void*)dense_bf16_kernel<true, true, false>,
-                      (const void*)dense_bf16_kernel<false, true, false>};
-  const int smem[6] = {bsmem(false, false), bsmem(false, false), bsmem(false, true),
-                       bsmem(false, true),  bsmem(true, false),  bsmem(true, false)};
   cudaError_t e = cudaSuccess;
-  for (int i = 0; i < 6 && e == cudaSuccess; ++i)
-    e = cudaFuncSetAttribute(f[i], cudaFuncAttributeMaxDynamicSharedMemorySize, smem[i]);
+  for (int f = 0; f < 2 && e == cudaSuccess; ++f)
+    for (int k = 0; k < kBKinds && e == cudaSuccess; ++k)
+      e = cudaFuncSetAttribute((const void*)bf16_kernel(f == 1, k), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               bf16_kind_smem(k));
   return e;
 }
 
@@ -631,14 +778,31 @@ EncodeTiledFn encode_tiled() {
   return fn;
 }
 
-// The input tile map of a launch and how the kernel loads its chunks: TMA
-// tiles for contiguous lines of forward and adjoint passes, in place
-// otherwise (or when the map cannot be made).
-void input_map(const DenseArgs& a, CUtensorMap* map, int* mode) {
+// The input tile map of a launch and how the kernel loads its chunks: BF16
+// planes as 3-D TMA tiles; FP32 TMA tiles for contiguous lines of forward and
+// adjoint passes; in place otherwise (or when the FP32 map cannot be made).
+// Returns false when BF16 planes come without a map.
+bool input_map(const DenseArgs& a, CUtensorMap* map, int* mode) {
   std::memset(map, 0, sizeof(*map));
   *mode = kInPlace;
   const EncodeTiledFn enc = encode_tiled();
-  if (a.grad || a.inner != 1 || !enc) return;
+  if (a.in_bf) {
+    // [plane][line][2N bf16]: the lines of every realization (contiguous:
+    // inner == 1), the tail plane bf_plane pairs after the head plane; a box
+    // of 64 values x 128 lines x the planes the launch reads
+    if (!enc || a.inner != 1 || a.grad) return false;
+    const cuuint64_t rows = (cuuint64_t)a.batch * (cuuint64_t)a.outer;
+    const cuuint64_t dims[3] = {(cuuint64_t)(2 * a.N), rows, a.unsplit ? 1u : 2u};
+    const cuuint64_t strides[2] = {(cuuint64_t)(2 * a.N) * 2, (cuuint64_t)a.bf_plane * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)BKC, (cuuint32_t)BL, a.unsplit ? 1u : 2u}, estr[3] = {1, 1, 1};
+    if (enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)a.in_bf, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+    *mode = kTmaPlanes;
+    return true;
+  }
+  if (a.grad || a.inner != 1 || !enc) return true;
   const cuuint64_t rows = (cuuint64_t)a.batch * (cuuint64_t)a.outer;  // every realization's lines
   const cuuint64_t dims[2] = {(cuuint64_t)(2 * a.N), rows};
   const cuuint64_t strides[1] = {(cuuint64_t)(2 * a.N) * 4};
@@ -649,32 +813,26 @@ void input_map(const DenseArgs& a, CUtensorMap* map, int* mode) {
     *mode = kTmaContiguous;
   else
     std::memset(map, 0, sizeof(*map));
+  return true;
 }
 
 }  // namespace
 
-cudaError_t launch_dense_bf16(const DenseArgs& a, const unsigned char* Tblk, int* err, int grid, cudaStream_t s) {
+bool dense_bf16_chain_supported() { return encode_tiled() != nullptr; }
+
+cudaError_t launch_dense_bf16(const DenseArgs& args, const unsigned char* Tblk, int* err, int grid, cudaStream_t s) {
+  DenseArgs a = args;
+  if (a.oinner == 0) {
+    a.oouter = a.outer;
+    a.oinner = a.inner;
+  }
   CUtensorMap map;
   int mode;
-  input_map(a, &map, &mode);
+  if (!input_map(a, &map, &mode)) return cudaErrorInvalidValue;
   const bool full = (2 * a.N) % BR == 0;
-  if (a.grad) {
-    // backward passes never accumulate over the batch
-    if (full)
-      dense_bf16_kernel<true, true, false><<<grid, BTHREADS, bsmem(true, false), s>>>(a, Tblk, err, map, mode);
-    else
-      dense_bf16_kernel<false, true, false><<<grid, BTHREADS, bsmem(true, false), s>>>(a, Tblk, err, map, mode);
-  } else if (a.acc) {
-    if (full)
-      dense_bf16_kernel<true, false, true><<<grid, BTHREADS, bsmem(false, true), s>>>(a, Tblk, err, map, mode);
-    else
-      dense_bf16_kernel<false, false, true><<<grid, BTHREADS, bsmem(false, true), s>>>(a, Tblk, err, map, mode);
-  } else {
-    if (full)
-      dense_bf16_kernel<true, false, false><<<grid, BTHREADS, bsmem(false, false), s>>>(a, Tblk, err, map, mode);
-    else
-      dense_bf16_kernel<false, false, false><<<grid, BTHREADS, bsmem(false, false), s>>>(a, Tblk, err, map, mode);
-  }
+  // backward passes never accumulate over the batch, nor read BF16 planes
+  const int kind = a.grad ? 2 : a.in_bf ? (a.acc ? 4 : 3) : (a.acc ? 1 : 0);
+  bf16_kernel(full, kind)<<<grid, BTHREADS, bf16_kind_smem(kind), s>>>(a, Tblk, err, map, mode);
   return cudaGetLastError();
 }
 

@@ -26,6 +26,15 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint
   return d;
 }
 
+// Shared-memory matrix descriptor, K-major, 128-byte swizzle (layout type 2
+// in bits 61-63): rows of 128 bytes in 8-row atoms of 1024 bytes (SBO), the
+// 16-byte chunk c of row r stored at chunk c ^ (r % 8) -- the layout a TMA
+// tile load with 128-byte swizzle writes.  The atoms start on 1024-byte
+// boundaries; a K step inside an atom moves the start address by its bytes.
+__device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr) {
+  return make_desc(saddr, 16, 1024) | ((uint64_t)2 << 61);
+}
+
 // Instruction descriptor of kind::tf32 with an FP32 accumulator, both
 // operands TF32 and K-major, for an M x N tile.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {

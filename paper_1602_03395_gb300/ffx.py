@@ -96,6 +96,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ffx_plan_fused.restype = i64
     lib.ffx_plan_call_form.argtypes = [vp, i32, i64]
     lib.ffx_plan_call_form.restype = i32
+    lib.ffx_plan_bf16_chain.argtypes = [vp, i64]
+    lib.ffx_plan_bf16_chain.restype = i32
     lib.ffx_expand_positive_p.argtypes = [vp, vp, vp, i64, vp, vp]
     lib.ffx_expand_positive_p.restype = i32
     lib.ffx_expand_column.argtypes = [vp, vp, i64, i32, vp, vp]
@@ -263,14 +265,23 @@ class Plan:
         return int(load_library().ffx_workspace_bytes(self.handle, batch))
 
     def launches_per_call(self, backward: bool = False, batch: int = 1) -> int:
+        n = len(self.dims)
+        # a BF16 chain adds the split of its input (the forward half of a
+        # backward call takes a chain on 3-D plans)
+        chain = 1 if self.bf16_chain(batch) and (not backward or n == 3) else 0
         if not backward and self.fused and batch > self.fused_max_batch:
-            return len(self.dims)
-        return int(load_library().ffx_launches_per_call(self.handle, int(backward)))
+            return n + chain
+        return int(load_library().ffx_launches_per_call(self.handle, int(backward))) + chain
 
     def call_forms(self, batch: int = 1):
         """Per lattice axis, the form whose kernel a forward call with this batch runs."""
         return tuple(_FORM_NAMES[load_library().ffx_plan_call_form(self.handle, j, batch)]
                      for j in range(len(self.dims)))
+
+    def bf16_chain(self, batch: int = 1) -> bool:
+        """Whether forward calls with this batch run as a BF16 chain (the
+        passes from the last axis to the first, BF16 planes between them)."""
+        return load_library().ffx_plan_bf16_chain(self.handle, batch) == 1
 
     def pass_order(self):
         order = (ctypes.c_int32 * len(self.dims))()

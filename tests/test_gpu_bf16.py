@@ -116,3 +116,43 @@ def test_bf16_flag_checks(ffx):
     with pytest.raises(ffx.FfxError) as ei:
         ffx.Plan((64, 64), (0.25, 0.25), 1.0, (3, 3), form="fold", bf16=True)
     assert ei.value.code == ffx.FFX_EINVAL
+
+
+# BF16 chains: lattices whose lines per realization are not multiples of the
+# 128-line tile (tiles straddle realizations), 2-D and 3-D, density, field and
+# ensemble sum
+CHAIN_CASES = [
+    ((96, 192), (5, 9), 3),
+    ((128, 96, 192), (30, 4, 7), 2),
+]
+
+
+@pytest.mark.parametrize("dims,lam,batch", CHAIN_CASES)
+def test_bf16_chain_density_field_accumulate(ffx, dims, lam, batch):
+    rng = np.random.default_rng(11 * batch + len(dims))
+    dx, t = (0.25,) * len(dims), 10.0
+    psi = random_field(rng, (batch,) + dims)
+    ref = O.expand_field(psi, dx, t, lam)
+    with ffx.Plan(dims, dx, t, lam, form="tc", bf16=True) as plan:
+        assert plan.bf16_chain(batch)
+        assert plan.pass_order() == tuple(reversed(range(len(dims))))
+        x = to_dev(psi)
+        rho = ffx.ffx_expand(plan, x).cpu().numpy()
+        f = ffx.ffx_expand_field(plan, x).cpu().numpy()
+        assert plan.device_errors() == 0
+    with ffx.Plan(dims, dx, t, lam, form="tc", bf16=True, accumulate=True) as plan:
+        assert plan.bf16_chain(batch)
+        acc = ffx.ffx_expand(plan, to_dev(psi)).cpu().numpy()
+        assert plan.device_errors() == 0
+    with ffx.Plan(dims, dx, t, lam, form="tc", bf16=True, unsplit=True) as plan:
+        assert plan.bf16_chain(batch)
+        rho_u = ffx.ffx_expand(plan, to_dev(psi)).cpu().numpy()
+        assert plan.device_errors() == 0
+    dens = np.abs(ref) ** 2
+    e_d, e_f = rel_l2(rho, dens), rel_l2(f, ref)
+    e_acc, e_u = rel_l2(acc, dens.sum(0)), rel_l2(rho_u, dens)
+    print(f"bf16 chain {dims} x{batch}: density {e_d:.2e}, field {e_f:.2e}, ensemble sum {e_acc:.2e}, "
+          f"unsplit density {e_u:.2e}")
+    assert e_d < DENSITY_TOL and e_f < FIELD_TOL and e_acc < DENSITY_TOL and e_u < BF16_UNSPLIT_TOL
+    # the density is |field|^2 of the same chain (to FP32 rounding)
+    assert rel_l2(rho, np.abs(f) ** 2) < 1e-6
