@@ -500,6 +500,9 @@ __global__ void __launch_bounds__(BTHREADS, 1)
       for (int64_t it = 0; ok && it < my_items; ++it) {
         const int mt = (int)((blockIdx.x + it * gridDim.x) % mtiles);
         const uint32_t idesc = idesc_bf16(BL, FULL ? BR : brow_count(N, mt));
+        // whole row blocks: X_hi against [T_hi; T_lo] (the T chunk's 256 rows,
+        // head rows then tail rows) in one N = 256 product into the adjacent
+        // accumulators [d1 | d2] -- the operand X_hi is read once for both
         for (int b = 0; ok && b < nb; ++b, ++sub) {
           const int buf = (int)(sub & 1);
           const int64_t v = sub >> 1;
@@ -527,11 +530,17 @@ __global__ void __launch_bounds__(BTHREADS, 1)
               const uint64_t dxh = INBF ? make_desc_sw128(xh + (uint32_t)(ks * 32)) : make_desc(xh + o, BCORE, BSBO);
               const uint64_t dth = make_desc(th + o, BCORE, BSBO);
               const uint32_t more = (kc == 0 && ks == 0) ? 0u : 1u;
-              mma_f16(d1, dxh, dth, idesc, more);
-              if (!unsplit) {
+              if (unsplit) {
+                mma_f16(d1, dxh, dth, idesc, more);
+              } else {
                 const uint64_t dxl =
                     INBF ? make_desc_sw128(xl + (uint32_t)(ks * 32)) : make_desc(xl + o, BCORE, BSBO);
-                mma_f16(d2, dxh, make_desc(tl + o, BCORE, BSBO), idesc, more);
+                if (FULL) {
+                  mma_f16(d1, dxh, dth, idesc_bf16(BL, 2 * BR), more);
+                } else {
+                  mma_f16(d1, dxh, dth, idesc, more);
+                  mma_f16(d2, dxh, make_desc(tl + o, BCORE, BSBO), idesc, more);
+                }
                 mma_f16(d2, dxl, dth, idesc, 1u);
               }
             }
