@@ -492,6 +492,9 @@ def run_mixed(args, torch, dist, world, rank, dev):
             err["x".join(map(str, w.dims)) + f"_lam{w.lam[0]}"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
     for _ in range(args.warmup):
         ffx.ffx_expand(plan, x, out)
+    n0 = plan.launch_count()
+    ffx.ffx_expand(plan, x, out)
+    per_call = plan.launch_count() - n0  # the call's graph: one kernel per phase
     torch.cuda.synchronize()
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     sampler.start()
@@ -552,7 +555,7 @@ def run_mixed(args, torch, dist, world, rank, dev):
                        "parallelism": f"replicas x{world}",
                        "l2": f"inputs {plan.points * 8 / 2**30:.2f} GiB > 129 MB L2"},
             "rel_l2_density_err_vs_fp64": err,
-            "gpu_launches": plan.launches_per_call() * args.steps,
+            "gpu_launches": per_call * args.steps,
             "clocks": clocks,
             "roofline": roofline,
             "roofline_hbm": {"bound": "hbm", "achieved": byts / (ms / args.steps * 1e-3) / 1e9,
@@ -602,12 +605,10 @@ def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary
                     tf32=args.tf32)
     form = plan.form
     order = plan.pass_order()
-    launches = plan.launches_per_call(batch=B_)
     fused_call = plan.fused and B_ <= plan.fused_max_batch  # all d passes in one launch
     call_forms = plan.call_forms(B_)  # the kernel each axis runs at this batch
     # BF16 chain: one launch splits the input into BF16 planes, then the passes
     chain = plan.bf16_chain(B_) and args.column is None
-    extra_launches = 0
     if args.column is None:
         out_shape = (B_,) + tuple(w.dims)
 
@@ -619,8 +620,6 @@ def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary
         col = args.column
         out_shape = (B_,) + tuple(n for j, n in enumerate(w.dims) if j != col)
         order = [j for j in order if j != col] + [col]
-        extra_launches = 0 if fused_call else 1
-        launches = len(order) if not fused_call else launches
 
         def call(x, out=None):
             return ffx.ffx_expand_column(plan, x, col, out)
@@ -650,6 +649,18 @@ def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary
 
     for i in range(args.warmup):
         call(pool_in[i % pool_n], pool_out[i % len(pool_out)])
+    torch.cuda.synchronize()
+    # one more call, counted: the kernels it launches (the library's own
+    # count) and the traced intervals it records (one per pass; a BF16 chain
+    # adds its input split, a pass that splits its own input records both
+    # launches in its interval)
+    n0 = plan.launch_count()
+    trial = [torch.cuda.Event(enable_timing=True) for _ in range(64)]
+    plan.trace(trial)
+    call(pool_in[0], pool_out[0])
+    launches = plan.trace_count() // 2
+    plan.trace(None)
+    per_call = plan.launch_count() - n0
     torch.cuda.synchronize()
 
     # The K steps are captured into CUDA graphs of up to GRAPH_STEPS steps and
@@ -883,7 +894,7 @@ def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary
                    "timed_region_ms": ms},
         "rel_l2_density_err_vs_fp64": err,
         "rel_l2_scope": "whole output lattice of the first realization, against the FP64 oracle",
-        "gpu_launches": (launches + extra_launches) * args.steps,
+        "gpu_launches": per_call * args.steps,
         "graph": f"K steps replayed as {len(graphs)} CUDA graph(s) of <= {GRAPH_STEPS} steps, no trace "
                  f"nodes; pass_ms from a separate graph of {n_traced} traced steps run before the timed region",
         "clocks": clocks,

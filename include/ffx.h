@@ -445,6 +445,12 @@ int64_t ffx_plan_fused(ffx_plan_t plan);
  * many-instance plan. */
 int ffx_plan_call_form(ffx_plan_t plan, int axis, int64_t batch);
 
+/* Kernels the plan's calls have launched so far, counted as each call
+ * enqueues them (a call captured into a CUDA graph counts once, at capture;
+ * replays of the graph do not count); -1 for a NULL plan.  The difference
+ * across one call is that call's number of kernel launches. */
+int64_t ffx_plan_launch_count(ffx_plan_t plan);
+
 /* 1 if ffx_expand over `batch` realizations (16-byte aligned buffers) runs
  * as a BF16 chain, else 0; -1 on a bad argument (ffx_expand_field and the
  * forward half of ffx_expand_backward take the same chains).  A

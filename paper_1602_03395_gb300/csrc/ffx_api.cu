@@ -136,6 +136,8 @@ using namespace ffx;
 // fused launch's grid-barrier counters (+64), its tile counters (+1024).
 constexpr size_t kTcHeader = 1024 + kFusedTileFlags * sizeof(unsigned);
 
+constexpr int kWs = 5, kWsSplit = 4;
+
 struct ffx_plan_s {
   int ndim = 0;
   int64_t dims[3] = {1, 1, 1};
@@ -169,9 +171,11 @@ struct ffx_plan_s {
   int fused_tc_grid = 0;
   size_t fused_smem_bytes = 0;
   // workspace buffers, grown on demand: [0], [1] the passes' fields; [2] the
-  // detector densities, or a positive-P pair's first field; [3] its second
-  void* ws[4] = {nullptr, nullptr, nullptr, nullptr};
-  size_t ws_bytes[4] = {0, 0, 0, 0};
+  // detector densities, or a positive-P pair's first field; [3] its second;
+  // [4] the BF16 planes a per-axis BF16 pass splits its FP32 input into
+  void* ws[kWs] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  size_t ws_bytes[kWs] = {0, 0, 0, 0, 0};
+  int64_t launches = 0;  // kernels the plan's calls have launched (ffx_plan_launch_count)
   void* stage[2] = {nullptr, nullptr};  // ffx_expand_host: device copies of the input and the densities
   size_t stage_bytes[2] = {0, 0};
   ManyPlan* many = nullptr;       // set for plans over many instances
@@ -382,6 +386,19 @@ int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* 
       d.bf_plane = io->plane;
       d.oouter = 1;
       d.oinner = outer;
+    } else if (ax.bf_t[0] && !tm64 && !grad && inner == 1) {
+      // contiguous FP32 lines: split into BF16 planes first (an HBM-bound
+      // pass), so that the pass loads its operands straight into the tensor
+      // cores' layout instead of converting them on the way
+      int rc = ensure_ws(p, kWsSplit, batch);
+      if (rc) return rc;
+      const int64_t plane = batch * p->M;
+      e = launch_bf16_split(in, (uint32_t*)p->ws[kWsSplit], plane, plane, d.unsplit, p->sms, stream);
+      if (e != cudaSuccess) return cuda_fail(e, "BF16 split of a pass input");
+      ++p->launches;
+      d.in_bf = (const uint32_t*)p->ws[kWsSplit];
+      d.bf_plane = plane;
+      d.in = nullptr;
     }
     if (ax.bf_t[0] && !tm64)
       e = launch_dense_bf16(d, ax.bf_t[adjoint ? 1 : 0], p->dev_err, (int)grid, stream);
@@ -457,6 +474,7 @@ int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* 
     e = info.launch(a, (int)grid, stream);
   }
   if (e != cudaSuccess) return cuda_fail(e, "pass launch");
+  ++p->launches;
   trace_end(p, stream, rec_flags);
   return FFX_OK;
 }
@@ -510,6 +528,7 @@ int chain_bf16(ffx_plan_s* p, const float2* in, int64_t batch, float2* out_c, fl
   const unsigned rec = trace_begin(p, s);
   cudaError_t e = launch_bf16_split(in, (uint32_t*)p->ws[1], plane, plane, unsplit, p->sms, s);
   if (e != cudaSuccess) return cuda_fail(e, "BF16 split of the input");
+  ++p->launches;
   trace_end(p, s, rec);
   const uint32_t* cur_bf = (const uint32_t*)p->ws[1];
   for (int r = 0; r < d; ++r) {
@@ -733,6 +752,7 @@ int run_fused(ffx_plan_s* p, const int* axes, const float2* in, float2* out_c, f
     e = launch_fused(a, p->fused_grid, p->fused_smem_bytes, stream);
   }
   if (e != cudaSuccess) return cuda_fail(e, "fused launch");
+  ++p->launches;
   if (traced) {
     cudaEventRecordWithFlags((cudaEvent_t)p->trace[p->trace_i + 1], stream, rec_flags);
     p->trace_i += 2;
@@ -1270,7 +1290,7 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
   if (rc == FFX_OK) rc = plan_fusion(p);
   cudaStreamDestroy(s);
   if (rc != FFX_OK) {
-    for (int w = 0; w < 4; ++w)
+    for (int w = 0; w < kWs; ++w)
       if (p->ws[w]) cudaFree(p->ws[w]);
     if (p->dense_mem) cudaFree(p->dense_mem);
     if (p->tc_mem) cudaFree(p->tc_mem);
@@ -1322,7 +1342,7 @@ int ffx_plan_destroy(ffx_plan_t p) {
     delete p;
     return FFX_OK;
   }
-  for (int w = 0; w < 4; ++w)
+  for (int w = 0; w < kWs; ++w)
     if (p->ws[w]) cudaFree(p->ws[w]);
   if (p->dense_mem) cudaFree(p->dense_mem);
   if (p->tc_mem) cudaFree(p->tc_mem);
@@ -1391,7 +1411,7 @@ int ffx_plan_device_errors(ffx_plan_t p) {
 int64_t ffx_workspace_bytes(ffx_plan_t p, int64_t batch) {
   if (!p || batch < 0) return -1;
   int64_t total = 0;
-  for (int w = 0; w < 4; ++w) total += (int64_t)p->ws_bytes[w];
+  for (int w = 0; w < kWs; ++w) total += (int64_t)p->ws_bytes[w];
   const int64_t need = batch * p->M * (int64_t)sizeof(float2);
   return total > need ? total : need;
 }
@@ -1410,6 +1430,8 @@ int ffx_plan_bf16_chain(ffx_plan_t p, int64_t batch) {
   const void* aligned = (const void*)(uintptr_t)16;
   return bf16_chain_ok(p, batch, aligned, aligned, aligned) ? 1 : 0;
 }
+
+int64_t ffx_plan_launch_count(ffx_plan_t p) { return p ? p->launches : -1; }
 
 int ffx_plan_call_form(ffx_plan_t p, int axis, int64_t batch) {
   if (!p || p->many || axis < 0 || axis >= p->ndim || batch < 1) return -1;
@@ -1461,7 +1483,9 @@ int ffx_expand(ffx_plan_t p, const void* psi0, int64_t batch, float* out_density
     if (batch != 1) return fail(FFX_EINVAL, "a many-instance plan takes batch = 1");
     std::string err;
     rc = many_expand(p->many, psi0, out_density, nullptr, s, &err);
-    return rc ? fail(rc, "%s", err.c_str()) : FFX_OK;
+    if (rc) return fail(rc, "%s", err.c_str());
+    p->launches += many_kernels(p->many, 0);
+    return FFX_OK;
   }
   if (batch <= p->fused) return run_fused(p, p->order, (const float2*)psi0, nullptr, out_density, nullptr, batch, s);
   return forward_density(p, p->order, (const float2*)psi0, batch, out_density, s);
@@ -1519,7 +1543,9 @@ int ffx_expand_column(ffx_plan_t p, const void* psi0, int64_t batch, int axis, f
   const Axis& ax = p->axis[axis];
   cudaError_t e = launch_axis_sum(rho, p->acc ? outer : batch * outer, ax.N, inner, (float)(ax.lam * ax.dx), p->acc,
                                   out_column, p->sms, s);
-  return e == cudaSuccess ? FFX_OK : cuda_fail(e, "column sum");
+  if (e != cudaSuccess) return cuda_fail(e, "column sum");
+  ++p->launches;
+  return FFX_OK;
 }
 
 // The forward field map of a batch into `out` (may equal `in`): the fused
@@ -1547,9 +1573,12 @@ int ffx_expand_positive_p(ffx_plan_t p, const void* psi0, const void* psi0_plus,
   if ((rc = field_into(p, (const float2*)psi0, batch, w1, s))) return rc;
   cudaError_t e = launch_conj_copy((const float2*)psi0_plus, w2, batch * p->M, p->sms, s);
   if (e != cudaSuccess) return cuda_fail(e, "conjugate copy");
+  ++p->launches;
   if ((rc = field_into(p, w2, batch, w2, s))) return rc;
   e = launch_pair_density(w1, w2, p->M, batch, p->acc, out_density, p->sms, s);
-  return e == cudaSuccess ? FFX_OK : cuda_fail(e, "pair density");
+  if (e != cudaSuccess) return cuda_fail(e, "pair density");
+  ++p->launches;
+  return FFX_OK;
 }
 
 int ffx_plan_output_axis(ffx_plan_t p, int axis, double* x0, double* step) {
@@ -1592,7 +1621,9 @@ int ffx_expand_field(ffx_plan_t p, const void* psi0, int64_t batch, void* out_fi
     if (batch != 1) return fail(FFX_EINVAL, "a many-instance plan takes batch = 1");
     std::string err;
     rc = many_expand(p->many, psi0, nullptr, out_field, (cudaStream_t)stream, &err);
-    return rc ? fail(rc, "%s", err.c_str()) : FFX_OK;
+    if (rc) return fail(rc, "%s", err.c_str());
+    p->launches += many_kernels(p->many, 1);
+    return FFX_OK;
   }
   if (batch <= p->fused)
     return run_fused(p, p->order, (const float2*)psi0, (float2*)out_field, nullptr, nullptr, batch,
@@ -1630,7 +1661,9 @@ int ffx_expand_backward(ffx_plan_t p, const void* psi0, const float* grad_densit
     if (batch != 1) return fail(FFX_EINVAL, "a many-instance plan takes batch = 1");
     std::string err;
     rc = many_backward(p->many, psi0, grad_density, grad_psi0, s, &err);
-    return rc ? fail(rc, "%s", err.c_str()) : FFX_OK;
+    if (rc) return fail(rc, "%s", err.c_str());
+    p->launches += many_kernels(p->many, 2);
+    return FFX_OK;
   }
   // T psi0 into ws[0] (ws[1] as the alternate), then T^H (2 grad * .) into
   // grad_psi0 (ws[1] as the alternate)

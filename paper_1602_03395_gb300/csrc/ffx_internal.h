@@ -206,6 +206,9 @@ struct ManyPlan;
 int many_create(ManyPlan** out, int n, const ffx_instance_desc* d, uint32_t flags, std::string* err);
 void many_destroy(ManyPlan* mp);
 int64_t many_total(const ManyPlan* mp);
+// kernels one call launches (its graph's phase nodes); mode 0 densities,
+// 1 fields, 2 backward
+int64_t many_kernels(const ManyPlan* mp, int mode);
 int64_t many_offset(const ManyPlan* mp, int i);
 int many_form(const ManyPlan* mp);
 int many_max_dim(const ManyPlan* mp);

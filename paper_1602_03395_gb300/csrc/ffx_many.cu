@@ -1064,6 +1064,7 @@ void many_destroy(ManyPlan* mp) {
 }
 
 int64_t many_total(const ManyPlan* mp) { return mp->total; }
+int64_t many_kernels(const ManyPlan* mp, int mode) { return (int64_t)mp->phases[mode].size(); }
 int64_t many_offset(const ManyPlan* mp, int i) { return (i < 0 || i >= mp->n) ? -1 : mp->inst[i].off; }
 int many_form(const ManyPlan* mp) { return mp->form; }
 int many_max_dim(const ManyPlan* mp) { return mp->max_dim; }

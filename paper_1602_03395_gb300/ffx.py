@@ -98,6 +98,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.ffx_plan_call_form.restype = i32
     lib.ffx_plan_bf16_chain.argtypes = [vp, i64]
     lib.ffx_plan_bf16_chain.restype = i32
+    lib.ffx_plan_launch_count.argtypes = [vp]
+    lib.ffx_plan_launch_count.restype = i64
     lib.ffx_expand_positive_p.argtypes = [vp, vp, vp, i64, vp, vp]
     lib.ffx_expand_positive_p.restype = i32
     lib.ffx_expand_column.argtypes = [vp, vp, i64, i32, vp, vp]
@@ -265,6 +267,9 @@ class Plan:
         return int(load_library().ffx_workspace_bytes(self.handle, batch))
 
     def launches_per_call(self, backward: bool = False, batch: int = 1) -> int:
+        """Passes a call makes (one launch for a fused call), plus the input
+        split of a BF16 chain.  A per-axis BF16 pass over contiguous FP32
+        lines adds its own split launch; launch_count() counts exactly."""
         n = len(self.dims)
         # a BF16 chain adds the split of its input (the forward half of a
         # backward call takes a chain on 3-D plans)
@@ -277,6 +282,11 @@ class Plan:
         """Per lattice axis, the form whose kernel a forward call with this batch runs."""
         return tuple(_FORM_NAMES[load_library().ffx_plan_call_form(self.handle, j, batch)]
                      for j in range(len(self.dims)))
+
+    def launch_count(self) -> int:
+        """Kernels this plan's calls have launched so far (captured calls
+        count once; graph replays do not)."""
+        return int(load_library().ffx_plan_launch_count(self.handle))
 
     def bf16_chain(self, batch: int = 1) -> bool:
         """Whether forward calls with this batch run as a BF16 chain (the

@@ -156,3 +156,34 @@ def test_bf16_chain_density_field_accumulate(ffx, dims, lam, batch):
     assert e_d < DENSITY_TOL and e_f < FIELD_TOL and e_acc < DENSITY_TOL and e_u < BF16_UNSPLIT_TOL
     # the density is |field|^2 of the same chain (to FP32 rounding)
     assert rel_l2(rho, np.abs(f) ** 2) < 1e-6
+
+
+def test_bf16_pass_splits_contiguous_fp32_input(ffx):
+    """Per-axis path (the 32-point axes keep TF32, so no chain): the BF16 pass
+    along the last axis first splits its contiguous FP32 lines into BF16
+    planes (one more launch), for densities, fields, the ensemble sum and the
+    adjoint half of the backward pass."""
+    dims, lam, batch = (32, 32, 256), (5, 6, 20), 3
+    rng = np.random.default_rng(2024)
+    dx, t = (0.25, 0.25, 0.3), 10.0
+    psi = random_field(rng, (batch,) + dims)
+    grad = rng.normal(size=(batch,) + dims).astype(np.float32)
+    ref = O.expand_field(psi, dx, t, lam)
+    dens = np.abs(ref) ** 2
+    with ffx.Plan(dims, dx, t, lam, form="tc", bf16=True) as plan:
+        assert not plan.bf16_chain(batch)
+        x = to_dev(psi)
+        n0 = plan.launch_count()
+        rho = ffx.ffx_expand(plan, x).cpu().numpy()
+        assert plan.launch_count() - n0 == len(dims) + 1  # the passes and the split
+        f = ffx.ffx_expand_field(plan, x).cpu().numpy()
+        g = ffx.ffx_expand_backward(plan, x, to_dev(grad)).cpu().numpy()
+        assert plan.device_errors() == 0
+    with ffx.Plan(dims, dx, t, lam, form="tc", bf16=True, accumulate=True) as plan:
+        acc = ffx.ffx_expand(plan, to_dev(psi)).cpu().numpy()
+        assert plan.device_errors() == 0
+    e_d, e_f, e_acc = rel_l2(rho, dens), rel_l2(f, ref), rel_l2(acc, dens.sum(0))
+    e_g = rel_l2(g, O.density_loss_gradient(psi, grad, dx, t, lam))
+    print(f"bf16 split first pass {dims} x{batch}: density {e_d:.2e}, field {e_f:.2e}, ensemble sum {e_acc:.2e}, "
+          f"backward {e_g:.2e}")
+    assert e_d < DENSITY_TOL and e_f < FIELD_TOL and e_acc < DENSITY_TOL and e_g < FIELD_TOL
