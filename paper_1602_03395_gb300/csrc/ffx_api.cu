@@ -461,17 +461,23 @@ int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* 
     a.tab.F = ax.F;
     a.tab.tw = ax.tw;
     a.tab.fold = ax.fold;
-    const PassKernelInfo& info = adjoint ? ax.adj : (cform == FFX_FORM_PAPER ? ax.paper : ax.foldk);
-    const int capacity = adjoint ? ax.grid_adj : (cform == FFX_FORM_PAPER ? ax.grid_paper : ax.grid_fold);
-    // The split depends on one realization's lines only, so a realization's
-    // result does not depend on the batch it came in (bitwise).
-    a.qg = choose_qg(info, outer * inner, ax.lam, capacity);
-    const int lines = pass_lines_per_tile(info, a.qg);
-    const int64_t ntiles = (a.nlines + lines - 1) / lines;
-    int64_t grid = capacity;
-    if (grid > ntiles) grid = ntiles;
-    if (grid < 1) grid = 1;
-    e = info.launch(a, (int)grid, stream);
+    if (conv_supported(ax.N, ax.lam, acc)) {
+      // lam = 1 on lines of 16, 64 or 256 points: the one-term convolution kernel
+      const int kind = adjoint ? KIND_ADJ_FOLD : (cform == FFX_FORM_PAPER ? KIND_FWD_PAPER : KIND_FWD_FOLD);
+      e = launch_conv(a, kind, ax.N, p->sms, stream);
+    } else {
+      const PassKernelInfo& info = adjoint ? ax.adj : (cform == FFX_FORM_PAPER ? ax.paper : ax.foldk);
+      const int capacity = adjoint ? ax.grid_adj : (cform == FFX_FORM_PAPER ? ax.grid_paper : ax.grid_fold);
+      // The split depends on one realization's lines only, so a realization's
+      // result does not depend on the batch it came in (bitwise).
+      a.qg = choose_qg(info, outer * inner, ax.lam, capacity);
+      const int lines = pass_lines_per_tile(info, a.qg);
+      const int64_t ntiles = (a.nlines + lines - 1) / lines;
+      int64_t grid = capacity;
+      if (grid > ntiles) grid = ntiles;
+      if (grid < 1) grid = 1;
+      e = info.launch(a, (int)grid, stream);
+    }
   }
   if (e != cudaSuccess) return cuda_fail(e, "pass launch");
   ++p->launches;
