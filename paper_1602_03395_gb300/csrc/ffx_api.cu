@@ -461,9 +461,10 @@ int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* 
     a.tab.F = ax.F;
     a.tab.tw = ax.tw;
     a.tab.fold = ax.fold;
-    if (conv_supported(ax.N, ax.lam, acc)) {
-      // lam = 1 on lines of 16, 64 or 256 points: the one-term convolution kernel
-      const int kind = adjoint ? KIND_ADJ_FOLD : (cform == FFX_FORM_PAPER ? KIND_FWD_PAPER : KIND_FWD_FOLD);
+    const int kind = adjoint ? KIND_ADJ_FOLD : (cform == FFX_FORM_PAPER ? KIND_FWD_PAPER : KIND_FWD_FOLD);
+    if (conv_supported(ax.N, ax.lam, acc, kind)) {
+      // one or two terms on lines of 16, 64, 256 or 1024 points: the kernel
+      // with four-step line transforms in registers
       e = launch_conv(a, kind, ax.N, p->sms, stream);
     } else {
       const PassKernelInfo& info = adjoint ? ax.adj : (cform == FFX_FORM_PAPER ? ax.paper : ax.foldk);

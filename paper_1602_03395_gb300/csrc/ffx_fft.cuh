@@ -142,6 +142,35 @@ __device__ __forceinline__ void dft16(float2* x) {
   }
 }
 
+template <bool INV>
+__device__ __forceinline__ void dft32(float2* x) {
+  float2 e[16], o[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    e[k] = x[2 * k];
+    o[k] = x[2 * k + 1];
+  }
+  dft16<INV>(e);
+  dft16<INV>(o);
+  // o[k] *= exp(-+ 2 pi i k / 32) = cos(pi k / 16) -+ i sin(pi k / 16)
+  const float c[8] = {1.f, 0.98078528040323043f, 0.92387953251128674f, 0.83146961230254524f,
+                      0.70710678118654752f, 0.55557023301960218f, 0.38268343236508978f, 0.19509032201612825f};
+  const float sg = INV ? 1.f : -1.f;
+#pragma unroll
+  for (int k = 1; k < 16; ++k) {
+    // c[j] = cos(pi j / 16), j = 0..7: cos(pi k / 16) is c[k], 0 (k = 8) or
+    // -c[16 - k]; sin(pi k / 16) is c[8 - k] (k <= 8) or c[k - 8]
+    const float cs = k < 8 ? c[k] : (k == 8 ? 0.f : -c[16 - k]);
+    const float sn = k <= 8 ? c[8 - k] : c[k - 8];
+    o[k] = cmul(o[k], make_float2(cs, sg * sn));
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    x[k] = cadd(e[k], o[k]);
+    x[k + 16] = csub(e[k], o[k]);
+  }
+}
+
 // 12 = 4 x 3: with n = n1 + 4 n2 and k = 3 k1 + k2,
 // X[3 k1 + k2] = sum_n1 w_4^(n1 k1) w_12^(n1 k2) sum_n2 w_3^(n2 k2) x[n1 + 4 n2].
 template <bool INV>
@@ -188,6 +217,8 @@ __device__ __forceinline__ void dft(float2* x) {
     dft12<INV>(x);
   } else if constexpr (R == 16) {
     dft16<INV>(x);
+  } else if constexpr (R == 32) {
+    dft32<INV>(x);
   } else {
     static_assert(R == 2, "unsupported radix");
   }

@@ -75,10 +75,10 @@ inline int pass_lines_per_tile(const PassKernelInfo& k, int qg) { return k.lines
 bool find_pass_kernel(int N, int kind, PassKernelInfo* out);
 bool supported_length(int64_t N);
 
-// FFT-form passes at lam = 1 on lines of 16, 64 or 256 points without the
-// ensemble sum (ffx_conv.cu): one convolution per line, kind KIND_FWD_PAPER,
-// KIND_FWD_FOLD or KIND_ADJ_FOLD
-bool conv_supported(int N, int lam, int acc);
+// FFT-form passes with one or two terms (ffx_conv.cu), on lines of 16, 64,
+// 256 or 1024 points without the ensemble sum: lam = 1 (kind KIND_FWD_PAPER,
+// KIND_FWD_FOLD or KIND_ADJ_FOLD), lam = 2 (KIND_FWD_FOLD)
+bool conv_supported(int N, int lam, int acc, int kind);
 cudaError_t launch_conv(const PassArgs& a, int kind, int N, int sms, cudaStream_t s);
 
 // Set the calling thread's message for ffx_last_error().

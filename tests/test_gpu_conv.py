@@ -1,8 +1,8 @@
-"""FFT-form passes at magnification 1 on lines of 16, 64 and 256 points (the
-one-term convolution kernel: two four-step line FFTs in registers around the
-k-space phase), against the FP64 oracle: both explicit forms, densities,
-fields (also in place), the adjoint and the backward pass, contiguous and
-strided axes, tiles that end inside a realization, and results that do not
+"""FFT-form passes with one or two terms on lines of 16, 64, 256 and 1024
+points (four-step line FFTs in registers): magnification 1 in both explicit
+forms (densities, fields also in place, the adjoint and the backward pass)
+and magnification 2 in the fold form, against the FP64 oracle, on contiguous
+and strided axes with tiles that end inside a realization; results do not
 depend on the batch a realization comes in."""
 
 import numpy as np
@@ -21,6 +21,8 @@ CASES = [
     ((256, 16), 3),
     ((64, 16, 256), 1),
     ((256,), 7),
+    ((1024, 16), 2),
+    ((16, 1024), 3),
 ]
 
 
@@ -65,3 +67,33 @@ def test_conv_batch_independent_bitwise(ffx):
         all6 = ffx.ffx_expand(plan, to_dev(psi)).cpu().numpy()
         one = ffx.ffx_expand(plan, to_dev(psi[4:5])).cpu().numpy()
     assert np.array_equal(all6[4:5], one)
+
+
+# magnification 2 (two terms folded into one spectrum), fold form
+CASES_LAM2 = [
+    ((64, 64, 64), 2),
+    ((256, 16), 3),
+    ((16, 1024), 2),
+    ((1024,), 5),
+]
+
+
+@pytest.mark.parametrize("dims,batch", CASES_LAM2)
+def test_conv_two_terms_fold(ffx, dims, batch):
+    d = len(dims)
+    rng = np.random.default_rng(sum(dims) + 7 * batch)
+    dx = tuple(0.25 - 0.02 * j for j in range(d))
+    lam, t = (2,) * d, 5.0
+    psi = random_field(rng, (batch,) + dims)
+    ref = O.expand_field(psi, dx, t, lam)
+    with ffx.Plan(dims, dx, t, lam, form="fold") as plan:
+        x = to_dev(psi)
+        rho = ffx.ffx_expand(plan, x).cpu().numpy()
+        f = ffx.ffx_expand_field(plan, x).cpu().numpy()
+        y = x.clone()
+        ffx.ffx_expand_field(plan, y, y)
+        assert plan.device_errors() == 0
+    e_d, e_f = rel_l2(rho, np.abs(ref) ** 2), rel_l2(f, ref)
+    print(f"conv lam 2 fold {dims} x{batch}: density {e_d:.2e}, field {e_f:.2e}")
+    assert e_d < DENSITY_TOL and e_f < FIELD_TOL
+    assert np.array_equal(y.cpu().numpy(), f)
