@@ -27,9 +27,9 @@
 // R threads of a line read consecutive points (line-major lanes, warp
 // barriers); across strided lines neighbouring threads take neighbouring
 // lines of the tile (the block's barriers around the exchanges), so a warp
-// reads 8 or more lines' neighbouring points at a time.  With lam = 1 and
-// R <= 16 the loads of the next tile are issued before the current tile is
-// transformed.
+// reads 8 or more lines' neighbouring points at a time.  Where the registers
+// allow it (lam = 1 and R <= 16, lam = 2 and R <= 8) the loads of the next
+// tile are issued before the current tile is transformed.
 #include "ffx_fft.cuh"
 #include "ffx_internal.h"
 
@@ -53,7 +53,7 @@ struct ConvCfg {
   static constexpr int LS = CONTIG ? LS0 : (LS0 | 1);
   static constexpr bool TWREG = R <= 16;               // twiddles in registers
   static constexpr bool TABREG = LAM == 1 && R <= 8;   // K (or Kf) in registers
-  static constexpr bool PREFETCH = LAM == 1 && R <= 16;
+  static constexpr bool PREFETCH = (LAM == 1 && R <= 16) || (LAM == 2 && R <= 8);
   // shared tables, each [e][t] (entry t + R e of the natural-order row):
   // twiddles w_N^(t e), K_0 or Kf_0, F_0 (paper form) or Kf_1 (lam = 2), P_1
   static constexpr int NTAB = 4;
@@ -155,8 +155,10 @@ __global__ void __launch_bounds__(kConvThreads, (R == 32 && LAM == 2) ? 1 : 2)
     }
   }
 
-  const int64_t inner = a.inner;
+  const int64_t inner = CONTIG ? 1 : a.inner;  // contiguous lines: the stride is 1
   const int64_t per_real = a.outer * inner;
+  // offset of the thread's register e from its line's first point
+  auto off = [&](int e) -> int64_t { return CONTIG ? (int64_t)(t + R * e) : (int64_t)(t + R * e) * inner; };
   const int64_t ntiles = (a.nlines + LB - 1) / LB;
   // line c's first point, or -1 past the end
   auto line_base = [&](int64_t c) -> long long {
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__(kConvThreads, (R == 32 && LAM == 2) ? 1 : 2)
   auto load = [&](long long base, float2 (&v)[R]) {
 #pragma unroll
     for (int e = 0; e < R; ++e)
-      v[e] = base >= 0 ? __ldcs(a.in + base + (int64_t)(t + R * e) * inner) : make_float2(0.f, 0.f);
+      v[e] = base >= 0 ? __ldcs(a.in + base + off(e)) : make_float2(0.f, 0.f);
   };
 
   int64_t tile = blockIdx.x;
@@ -191,7 +193,7 @@ __global__ void __launch_bounds__(kConvThreads, (R == 32 && LAM == 2) ? 1 : 2)
       const int64_t goff = a.grad_shared ? base - (c / per_real) * a.M : base;
 #pragma unroll
       for (int e = 0; e < R; ++e) {
-        const float gr = 2.f * __ldg(a.grad + goff + (int64_t)(t + R * e) * inner);
+        const float gr = 2.f * __ldg(a.grad + goff + off(e));
         v[e] = make_float2(v[e].x * gr, v[e].y * gr);
       }
     }
@@ -225,11 +227,11 @@ __global__ void __launch_bounds__(kConvThreads, (R == 32 && LAM == 2) ? 1 : 2)
     if (base >= 0) {
       if (a.out_c) {
 #pragma unroll
-        for (int e = 0; e < R; ++e) __stcs(a.out_c + base + (int64_t)(t + R * e) * inner, v[e]);
+        for (int e = 0; e < R; ++e) __stcs(a.out_c + base + off(e), v[e]);
       } else {
 #pragma unroll
         for (int e = 0; e < R; ++e)
-          __stcs(a.out_d + base + (int64_t)(t + R * e) * inner, v[e].x * v[e].x + v[e].y * v[e].y);
+          __stcs(a.out_d + base + off(e), v[e].x * v[e].x + v[e].y * v[e].y);
       }
     }
     if constexpr (C::PREFETCH) {
