@@ -780,6 +780,12 @@ int run_fused(ffx_plan_s* p, const int* axes, const float2* in, float2* out_c, f
 // transforms in sequence inside one block.
 double model_cost(const Axis& ax, int form, int64_t lines) {
   const double N = ax.N, lg = std::log2(N), lam = ax.lam;
+  // the one- and two-term kernel (ffx_conv.cu), measured on full passes at
+  // 136-150 (lam = 1) and 180-253 (lam = 2) in these units, near the HBM
+  // bound of ~100; the paper form takes it at lam = 1 only, one unit dearer
+  // so that ties go to the fold form
+  if (form == FFX_FORM_FOLD && conv_supported(ax.N, ax.lam, 0, KIND_FWD_FOLD)) return ax.lam == 1 ? 140 : 230;
+  if (form == FFX_FORM_PAPER && conv_supported(ax.N, ax.lam, 0, KIND_FWD_PAPER)) return 141;
   switch (form) {
     case FFX_FORM_PAPER: return lam * (10 * lg + 20) / 0.18;
     case FFX_FORM_FOLD: return (lam * (5 * lg + 14) + 5 * lg) / (N >= 256 ? 0.16 : 0.11);

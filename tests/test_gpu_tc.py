@@ -121,7 +121,10 @@ def test_tc_accumulate_and_backward_long_axes(ffx, dims, lam):
     ((1024,), (1,), 256, ("fft",)),                     # lam = 1: an FFT form beats the dense map
     ((512,), (20,), 256, ("tc",)),                      # lam = 20: tensor cores
     ((1024,), (9,), 31, ("dense",)),                    # 31 lines: the few-lines kernel
-    ((64, 64, 64), (1, 2, 1), 4, ("tc",) * 3),          # FFT-form axes (small lam), a large call: tensor cores
+    # small lam, a large call: the lam = 1 axes take the one-term FFT kernel,
+    # the lam = 2 axis the tensor cores (cheaper there than the two-term kernel)
+    ((64, 64, 64), (1, 2, 1), 4, ("fft", "tc", "fft")),
+    ((256, 256), (1, 2), 2, ("fft", "fft")),            # 256 points: the FFT kernels beat the dense map
     ((512,), (2,), 256, ("fft",)),                      # lam = 2 on 512 points: the FFT form stays
 ])
 def test_auto_per_call_kernel_choice(ffx, dims, lam, batch, forms):
