@@ -583,13 +583,15 @@ def tensor_peak(pk, pk_src, timed_ms, dtype="tf32"):
             f"{key} x 1.1/2.25 (TF32 dense : BF16 dense, nominal), {pk_src}")
 
 
-def precision_label(args, bf16):
+def precision_label(args, bf16, chain=False):
     op = "BF16" if bf16 else "TF32"
     if args.unsplit:
         return f"{op} unsplit: one product on rounded operands (reported variant; density error of order 1e-3)"
     if bf16:
-        return ("split BF16 on the streaming tensor-core passes (kind::f16, three products), split TF32 on the "
-                "other tensor-core passes, else FP32")
+        return (("BF16 chain: the input split into BF16 head and tail planes, every pass on them "
+                 "(kind::f16, three products), planes between the passes; " if chain else
+                 "split BF16 on the streaming tensor-core passes (kind::f16, three products); ")
+                + "split TF32 on the other tensor-core passes, else FP32")
     return "split TF32 on the tensor cores (three products), else FP32"
 
 
@@ -748,7 +750,8 @@ def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary
     # the streaming kernel's passes BF16 (lines of N = 32k >= 64 outside the
     # tensor-memory kernels' 64-point case), else TF32
     dom_axis = order[0] if fused_call else launch_axis[dom]
-    bf16_launch = (plan.bf16 and not fused_call and w.dims[dom_axis] >= 64 and w.dims[dom_axis] % 32 == 0
+    bf16_launch = (plan.bf16 and not fused_call and call_forms[dom_axis] == "tc"
+                   and w.dims[dom_axis] >= 64 and w.dims[dom_axis] % 32 == 0
                    and not (w.dims[dom_axis] == 64 and B_ * M // 64 <= 4 * 128 * SMS))
     if fused_call:
         # one cooperative launch runs every pass (dense map: FP32 SIMT, or the
@@ -885,7 +888,7 @@ def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary
                    "lam": list(w.lam), "t": w.t, "batch_per_gpu": B_, "form": form,
                    "axis_forms": list(plan.axis_forms), "call_forms": list(call_forms),
                    "fused_one_launch": bool(fused_call),
-                   "precision": precision_label(args, plan.bf16),
+                   "precision": precision_label(args, plan.bf16, chain),
                    "output": ("density" if args.column is None else
                               f"detector image: density integrated along axis {args.column}"),
                    "parallelism": f"replicas x{world} (realizations sharded, no collective)",
