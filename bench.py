@@ -583,6 +583,25 @@ def tensor_peak(pk, pk_src, timed_ms, dtype="tf32"):
             f"{key} x 1.1/2.25 (TF32 dense : BF16 dense, nominal), {pk_src}")
 
 
+def hbm_step_record(w, batch, chain, fused_call, out_bytes, step_ms, hbm_peak, pk_src):
+    """Whole-step HBM view: the algorithmic bytes of a step (read psi0, 8 B
+    per point, write the output) and the bytes the implementation's launches
+    move (the BF16 chain's input split, 16 B per point; every pass one read
+    and one write of the batch, 8 + 8 B per point, 4 B for densities; the fused
+    launch keeps its intermediates in L2), over the step's time."""
+    pts = batch * int(np.prod(w.dims))
+    algo = pts * 8 + out_bytes
+    if fused_call:
+        impl = algo
+    else:
+        impl = (16 * pts if chain else 0) + (len(w.dims) - 1) * 16 * pts + pts * 8 + out_bytes
+    sec = step_ms * 1e-3
+    return {"algorithmic_bytes": algo, "implementation_bytes": impl, "unit": "GB/s", "peak": hbm_peak,
+            "algorithmic_gbs": algo / sec / 1e9, "algorithmic_frac": algo / sec / 1e9 / hbm_peak,
+            "implementation_gbs": impl / sec / 1e9, "implementation_frac": impl / sec / 1e9 / hbm_peak,
+            "note": f"per step over ms_per_step; of {pk_src} hbm_gbs"}
+
+
 def precision_label(args, bf16, chain=False):
     op = "BF16" if bf16 else "TF32"
     if args.unsplit:
@@ -906,6 +925,7 @@ def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary
                          "peak": hbm_peak, "unit": "GB/s",
                          "frac": bytes_launch / (mean_ms[dom] * 1e-3) / 1e9 / hbm_peak,
                          "note": f"of {pk_src} hbm_gbs; one read + one write of the batch"},
+        "hbm_step": hbm_step_record(w, B_, chain, fused_call, out_bytes, ms / args.steps, hbm_peak, pk_src),
         "pass_ms": {pass_names[k]: mean_ms[k] for k in range(launches)},
         "e2e": {"value": e2e_value, "unit": UNIT, "api": e2e_api, "lanes": lanes_used,
                 "h2d_bytes_per_step": B_ * M * 8,
@@ -976,7 +996,7 @@ def run_fft_passes(args, torch, dev, ffx):
 # 128x128x1024 quasicondensate rides along as an extra record).
 COMPANION = {"large_two_cloud": "large_quasicondensate"}
 EXTRA_KEYS = ("value", "unit", "ms_per_step", "config", "rel_l2_density_err_vs_fp64", "gpu_launches",
-              "clocks", "roofline", "roofline_hbm", "pass_ms", "e2e")
+              "clocks", "roofline", "roofline_hbm", "hbm_step", "pass_ms", "e2e")
 
 
 def run_ffx(args):

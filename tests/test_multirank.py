@@ -107,3 +107,25 @@ def test_bench_defaults_and_peak_choice(monkeypatch):
     assert burst == pytest.approx(1884.7 * 1.1 / 2.25) and src.startswith("bf16_tflops x")
     sus, src = bench.tensor_peak(pk, "measured", 4000.0)
     assert sus == pytest.approx(1699.1 * 1.1 / 2.25) and src.startswith("bf16_tflops_sustained")
+
+
+def test_bench_hbm_step_record():
+    """Whole-step HBM bytes: 12 B per point algorithmic (psi0 in, densities
+    out); the BF16 chain's launches move 16 (split) + 2 x 16 + 12 B per point
+    on a 3-D lattice, the per-axis passes 16 + 16 + 12, a fused launch the
+    algorithmic bytes."""
+    import bench
+
+    class W:
+        dims = (64, 32, 16)
+
+    pts = 64 * 32 * 16
+    r = bench.hbm_step_record(W(), 2, True, False, 2 * pts * 4, 1.0, 1000.0, "measured")
+    assert r["algorithmic_bytes"] == 2 * pts * 12
+    assert r["implementation_bytes"] == 2 * pts * (16 + 32 + 12)
+    assert abs(r["algorithmic_gbs"] - 2 * pts * 12 / 1e-3 / 1e9) < 1e-9
+    assert abs(r["implementation_frac"] - r["implementation_gbs"] / 1000.0) < 1e-12
+    r = bench.hbm_step_record(W(), 2, False, False, 2 * pts * 4, 1.0, 1000.0, "measured")
+    assert r["implementation_bytes"] == 2 * pts * (32 + 12)
+    r = bench.hbm_step_record(W(), 2, False, True, 2 * pts * 4, 1.0, 1000.0, "measured")
+    assert r["implementation_bytes"] == r["algorithmic_bytes"]
