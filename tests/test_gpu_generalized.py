@@ -81,3 +81,28 @@ def test_positive_p_pairs(ffx, fused, accumulate):
                 else np.abs(O.expand_field(psi, dx, t, lam)) ** 2)
     print(f"positive-P fused={fused} acc={accumulate}: {e:.2e}, classical limit {ec:.2e}")
     assert e < DENSITY_TOL and ec < DENSITY_TOL
+
+
+@pytest.mark.parametrize("kind", ["quartic", "masses"])
+def test_dispersion_and_positive_p_on_the_bf16_chain(ffx, kind):
+    """Every axis on the BF16 tensor-core kernel (96 and 128 points): the
+    forward calls run as a BF16 chain (input split, passes from the last axis
+    to the first, planes between them) with the dispersion tables and for
+    both fields of a positive-P pair."""
+    dims, dx, lam, t = (128, 96, 128), (0.25, 0.3, 0.2), (5, 7, 3), 2.0
+    batch = 2
+    rng = np.random.default_rng(len(kind) + 400)
+    psi = random_field(rng, (batch,) + dims)
+    psp = random_field(rng, (batch,) + dims)
+    omega = spectra(dims, dx, lam, kind)
+    ref = O.expand_field(psi, dx, t, lam, omega=omega)
+    with ffx.Plan(dims, dx, t, lam, form="tc", bf16=True, omega=omega) as plan:
+        assert plan.bf16_chain(batch)
+        field = ffx.ffx_expand_field(plan, to_dev(psi)).cpu().numpy()
+        rho = ffx.ffx_expand(plan, to_dev(psi)).cpu().numpy()
+        pp = ffx.ffx_expand_positive_p(plan, to_dev(psi), to_dev(psp)).cpu().numpy()
+        assert plan.device_errors() == 0
+    refp = O.positive_p_density(psi, psp, dx, t, lam, omega=omega)
+    ef, ed, ep = rel_l2(field, ref), rel_l2(rho, np.abs(ref) ** 2), rel_l2(pp, refp)
+    print(f"bf16 chain, dispersion {kind}: field {ef:.2e} density {ed:.2e} positive-P {ep:.2e}")
+    assert ef < FIELD_TOL and ed < DENSITY_TOL and ep < DENSITY_TOL

@@ -18,7 +18,8 @@ def ffx():
 
 
 @pytest.mark.parametrize("dims,lam,batch", [((16, 32, 48), (3, 4, 2), 3), ((64, 64, 64), (30, 30, 3), 1),
-                                            ((512,), (20,), 2)])
+                                            ((512,), (20,), 2),
+                                            ((128, 96, 128), (20, 9, 3), 2)])  # a BF16 chain
 def test_host_call_equals_device_call(ffx, dims, lam, batch):
     rng = np.random.default_rng(sum(dims) + batch)
     dx, t = (0.25,) * len(dims), 6.0
