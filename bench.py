@@ -442,13 +442,19 @@ def load_traffic(kernel_key: str):
     return entry.get("bytes_per_launch")
 
 
-def mixed_flops(specs, form):
-    tot = 0.0
+def mixed_flops(specs, form, bf16=False):
+    """Algorithmic flops of one call: (all, the share on BF16 operands).  With
+    BF16 phases the passes over lines of 64 to 256 points, a multiple of 32,
+    run on the BF16 kernel, the others on split TF32."""
+    tot = bf = 0.0
     for dims, dx, t, lam in specs:
         M = int(np.prod(dims))
         for j, N in enumerate(dims):
-            tot += pass_flops(N, lam[j], M // N, form)
-    return tot
+            f = pass_flops(N, lam[j], M // N, form)
+            tot += f
+            if bf16 and 64 <= N <= 256 and N % 32 == 0:
+                bf += f
+    return tot, bf
 
 
 def run_mixed(args, torch, dist, world, rank, dev):
@@ -459,7 +465,7 @@ def run_mixed(args, torch, dist, world, rank, dev):
     count = args.batch or 1000
     ws = inputs.config_mixed_batch(count=count)
     specs = [(w.dims, w.dx, w.t, w.lam) for w in ws]
-    plan = ffx.PlanMany(specs, form=args.form)
+    plan = ffx.PlanMany(specs, form=args.form, tf32=args.tf32)
     # a few distinct realizations per lattice shape, repeated to fill the batch
     # (the values do not change the work; all instances stay distinct buffers)
     cache = {}
@@ -514,19 +520,27 @@ def run_mixed(args, torch, dist, world, rank, dev):
     if world > 1:
         ms = max_over_ranks(torch, dist, ms, dev)
     value = job_rate(args.steps, count, world, ms)
-    flops = mixed_flops(specs, plan.form)
+    flops, flops_bf = mixed_flops(specs, plan.form, plan.bf16)
     pk, pk_src = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     alu_peak = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
     achieved = flops / (ms / args.steps * 1e-3) / 1e12
     if plan.form == "tc":
-        # split-TF32 phases on the tensor cores: TF32 peak as for the uniform
-        # tensor-core passes; `achieved` counts the algorithmic 8 N flops per point
-        tc_peak, tc_src = tensor_peak(pk, pk_src, ms)
+        # tensor-core phases: `achieved` counts the algorithmic 8 N flops per
+        # point; the peak is that of the call's mix, the flops on BF16 operands
+        # at the BF16 peak and the rest at the TF32 peak (time-weighted:
+        # all flops / (bf16 flops / P_bf16 + tf32 flops / P_tf32))
+        tf_peak, tf_src = tensor_peak(pk, pk_src, ms)
+        bf_peak, bf_src = tensor_peak(pk, pk_src, ms, "bf16")
+        tc_peak = flops / (flops_bf / bf_peak + (flops - flops_bf) / tf_peak)
+        kern = ("dense_bf16_many_kernel + dense_tc_kernel<false, true, false>" if plan.bf16
+                else "dense_tc_kernel<false, true, false>")
         roofline = {"bound": "tensor", "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
-                    "frac": achieved / tc_peak, "traffic": load_traffic(f"many_tc_mixed_{count}_call"),
-                    "kernel": "dense_tc_kernel<false, true> (all phases of one call)",
-                    "executed_tflops": 3 * achieved, "peak_source": tc_src}
+                    "frac": achieved / tc_peak,
+                    "traffic": load_traffic(f"many_tc_mixed_{count}_call" + ("_bf16" if plan.bf16 else "")),
+                    "kernel": kern + " (all phases of one call)",
+                    "executed_tflops": 3 * achieved, "bf16_flop_share": flops_bf / flops,
+                    "peak_source": (f"BF16 share at {bf_src}; the rest at {tf_src}" if plan.bf16 else tf_src)}
     else:
         roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                     "frac": achieved / alu_peak,
@@ -537,7 +551,7 @@ def run_mixed(args, torch, dist, world, rank, dev):
     hbm_peak = float(pk.get("hbm_gbs", 6800.0))
     # end to end: pinned host input -> expand -> pinned host densities, two lanes
     hx = x.cpu().pin_memory()
-    plan2 = ffx.PlanMany(specs, form=args.form)
+    plan2 = ffx.PlanMany(specs, form=args.form, tf32=args.tf32)
     steps_e2e = max(2, min(args.steps, 20))
     e2e_ms = host_api_e2e(torch, dev, ffx, [plan, plan2], [hx],
                           [torch.empty(plan.points, dtype=torch.float32).pin_memory() for _ in range(2)], steps_e2e)
@@ -552,6 +566,10 @@ def run_mixed(args, torch, dist, world, rank, dev):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"mixed_{count}_instances_48^3_64^3_96^3_128x32x32_lam10-100",
                        "batch_per_gpu": count, "form": plan.form, "points_per_step": plan.points,
+                       "precision": ("split BF16 on the 64..256-point passes (kind::f16, three products), "
+                                     "split TF32 on the 32- and 48-point passes" if plan.bf16 else
+                                     "split TF32 on the tensor cores (three products)" if plan.form == "tc"
+                                     else "FP32"),
                        "parallelism": f"replicas x{world}",
                        "l2": f"inputs {plan.points * 8 / 2**30:.2f} GiB > 129 MB L2"},
             "rel_l2_density_err_vs_fp64": err,

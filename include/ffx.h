@@ -188,18 +188,24 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
  *                      FFX_FORM_TC or FFX_FORM_AUTO (the dense maps when they
  *                      cost less than the fold form on every instance axis,
  *                      else fold; dense maps on the tensor cores when every
- *                      line length is a multiple of 16 from 32);
- *                      FFX_ACCUMULATE is rejected (instances on different
- *                      lattices have no common density grid).
+ *                      line length is a multiple of 16 from 32); with
+ *                      FFX_FORM_TC or FFX_FORM_AUTO, FFX_TC_TF32 (split TF32
+ *                      operands throughout) or FFX_TC_BF16 (the default, see
+ *                      below); FFX_ACCUMULATE, FFX_TUNE, FFX_UNFUSED and
+ *                      FFX_TC_UNSPLIT are rejected (FFX_EINVAL; instances on
+ *                      different lattices have no common density grid).
  *
  * The dense form builds T_j and T_j^H of every distinct axis geometry at plan
  * creation (the fold pass on the unit vectors) and runs each phase as one
  * persistent kernel over 64 x 32 tiles of all instances (FP32); it adds a
  * second packed workspace.  FFX_FORM_TC (and the automatic form, see above)
- * also builds their tensor-core operand blocks and runs each phase as one
- * persistent launch of the split-TF32 kernel over items of 128 lines x 128
- * real rows, one block per SM; a plan with a 16-point axis keeps the FP32
- * phases (ffx_plan_form reports which).  Dense passes are not in place for
+ * also builds their tensor-core operand blocks and runs each phase as
+ * persistent launches over items of 128 lines x 128 real rows, one block per
+ * SM: the passes over lines of 64 to 256 points, a multiple of 32, on split
+ * BF16 operands (kind::f16 products, density error of order 1e-6; not the
+ * first adjoint pass of ffx_expand_backward, nor with FFX_TC_TF32), the others
+ * on split TF32 operands, one launch each per phase.  A plan with a 16-point
+ * axis keeps the FP32 phases (ffx_plan_form reports which).  Dense passes are not in place for
  * lines over 64 points, so an in-place ffx_expand_field with a 1-D instance
  * longer than 64 points returns FFX_EUNSUPPORTED.  ffx_plan_device_errors
  * counts tensor-core phases that gave up on a bounded wait.
@@ -405,7 +411,7 @@ int64_t ffx_workspace_bytes(ffx_plan_t plan, int64_t batch);
 
 /* 1 if the plan's streaming tensor-core passes take BF16 operands
  * (FFX_TC_BF16, or the automatic form's default), 0 if not, -1 for a NULL
- * plan; many-instance plans: 0. */
+ * plan; many-instance plans: 1 if some of their tensor-core phases do. */
 int ffx_plan_tc_bf16(ffx_plan_t plan);
 
 /* The form every axis runs (FFX_FORM_PAPER, _FOLD, _DENSE or _TC), or

@@ -1366,7 +1366,8 @@ int ffx_plan_destroy(ffx_plan_t p) {
 }
 
 int ffx_plan_tc_bf16(ffx_plan_t p) {
-  if (!p || p->many) return p ? 0 : -1;
+  if (!p) return -1;
+  if (p->many) return many_bf16(p->many) ? 1 : 0;
   for (int j = 0; j < p->ndim; ++j)
     if (p->axis[j].bf_t[0]) return 1;
   return 0;

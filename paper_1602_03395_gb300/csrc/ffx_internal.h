@@ -217,6 +217,7 @@ int64_t many_total(const ManyPlan* mp);
 int64_t many_kernels(const ManyPlan* mp, int mode);
 int64_t many_offset(const ManyPlan* mp, int i);
 int many_form(const ManyPlan* mp);
+bool many_bf16(const ManyPlan* mp);  // some tensor-core passes take split BF16 operands
 int many_max_dim(const ManyPlan* mp);
 int* many_device_errors(const ManyPlan* mp);  // device count of launches that gave up on a wait
 int many_expand(ManyPlan* mp, const void* psi0, float* out_d, void* out_c, cudaStream_t s, std::string* err);

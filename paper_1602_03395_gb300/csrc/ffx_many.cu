@@ -40,6 +40,7 @@ enum ManyBase : int { BASE_NONE = -1, BASE_PSI0 = 0, BASE_WS = 1, BASE_OUTC = 2,
                       BASE_GRAD = 4, BASE_WS2 = 5, NBASE = 6 };
 constexpr int KIND_DENSE = 100;  // a dense phase (forward or adjoint: the item's matrix decides)
 constexpr int KIND_TC = 101;     // the same on the tensor cores (split TF32)
+constexpr int KIND_TC16 = 102;   // the same with split BF16 operands (lines of 64..256 points, multiples of 32)
 struct ManyCall {
   const void* base[NBASE];
 };
@@ -173,6 +174,7 @@ struct AxisTab {
   const float2* T = nullptr;   // dense mode: the per-axis map and its adjoint
   const float2* TH = nullptr;
   const unsigned char* tc[2] = {nullptr, nullptr};  // tensor-core mode: split operand blocks of T, T^H
+  const unsigned char* bf[2] = {nullptr, nullptr};  // the same as split BF16 blocks (BF16 phases)
 };
 
 struct Instance {
@@ -209,6 +211,7 @@ struct ManyPlan {
   float2* ws2 = nullptr;    // dense mode: the second workspace
   bool dense = false;
   bool tc = false;            // dense mode on the tensor cores
+  bool bf16 = false;          // tensor-core passes with split BF16 operands where the length allows
   void* dense_mem = nullptr;  // dense mode: T, T^H of every table key
   void* tc_mem = nullptr;     // tensor-core mode: operand blocks of every key
   int* dev_err = nullptr;     // launches that gave up on a bounded wait
@@ -286,7 +289,7 @@ namespace {
 
 // T_j and T_j^H of every table key: the fold pass (the uniform line kernel of
 // that length) on the N unit vectors, then the transpose / conjugate.
-int build_dense_maps(ManyPlan* mp, bool tc, cudaStream_t s, std::string* err) {
+int build_dense_maps(ManyPlan* mp, bool tc, bool bf16, cudaStream_t s, std::string* err) {
   size_t bytes = (size_t)mp->total * sizeof(float2);  // the second workspace
   int nmax = 0;
   for (const AxisTab& at : mp->tabs) {
@@ -347,10 +350,9 @@ int build_dense_maps(ManyPlan* mp, bool tc, cudaStream_t s, std::string* err) {
   mp->dense = true;
   mp->form = FFX_FORM_DENSE;
   if (!tc) return FFX_OK;
-  // tensor-core mode: the split operand blocks of every key's T and T^H, and
-  // the kernel's shared-memory allowance (one block per SM)
-  size_t tbytes = 0;
-  for (const AxisTab& at : mp->tabs) tbytes += 2 * dense_tc_t_bytes(at.N);
+  // tensor-core mode: the split operand blocks of every key's T and T^H (TF32,
+  // and BF16 for the lengths the BF16 kernel takes), and the kernels'
+  // shared-memory allowance (one block per SM)
   e = many_tc_prepare();
   int per = 0;
   if (e == cudaSuccess)
@@ -358,6 +360,22 @@ int build_dense_maps(ManyPlan* mp, bool tc, cudaStream_t s, std::string* err) {
   if (e != cudaSuccess || per < 1) {
     cudaGetLastError();
     return FFX_OK;  // the FP32 dense phases
+  }
+  if (bf16) {
+    per = 0;
+    e = many_bf16_prepare();
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, many_bf16_func(), many_bf16_threads(),
+                                                        many_bf16_smem());
+    if (e != cudaSuccess || per < 1) {
+      cudaGetLastError();
+      bf16 = false;  // split TF32 throughout
+    }
+  }
+  size_t tbytes = 0;
+  for (const AxisTab& at : mp->tabs) {
+    tbytes += 2 * dense_tc_t_bytes(at.N);
+    if (bf16 && many_bf16_supported(at.N)) tbytes += 2 * dense_bf16_t_bytes(at.N);
   }
   e = cudaMalloc(&mp->tc_mem, tbytes);
   if (e != cudaSuccess) {
@@ -373,6 +391,13 @@ int build_dense_maps(ManyPlan* mp, bool tc, cudaStream_t s, std::string* err) {
     tcur = t1 + dense_tc_t_bytes(at.N);
     e = launch_tc_build_t(at.T, t0, at.N, s);
     if (e == cudaSuccess) e = launch_tc_build_t(at.TH, t1, at.N, s);
+    if (e == cudaSuccess && bf16 && many_bf16_supported(at.N)) {
+      at.bf[0] = tcur;
+      at.bf[1] = tcur + dense_bf16_t_bytes(at.N);
+      tcur += 2 * dense_bf16_t_bytes(at.N);
+      e = launch_bf16_build_t(at.T, (unsigned char*)at.bf[0], at.N, s);
+      if (e == cudaSuccess) e = launch_bf16_build_t(at.TH, (unsigned char*)at.bf[1], at.N, s);
+    }
     if (e != cudaSuccess) {
       cudaGetLastError();
       *err = std::string("tensor-core operands: ") + cudaGetErrorString(e);
@@ -392,6 +417,7 @@ int build_dense_maps(ManyPlan* mp, bool tc, cudaStream_t s, std::string* err) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   mp->grid_tc = sms;
   mp->tc = true;
+  mp->bf16 = bf16;
   mp->form = FFX_FORM_TC;
   return FFX_OK;
 }
@@ -409,8 +435,16 @@ int many_create(ManyPlan** out, int n, const ffx_instance_desc* d, uint32_t flag
     return FFX_EINVAL;
   }
   const uint32_t form = flags & FFX_FORM_MASK;
-  if (flags & ~(FFX_FORM_MASK)) {
-    *err = "unknown flag bits";
+  if (flags & ~(FFX_FORM_MASK | FFX_TC_BF16 | FFX_TC_TF32)) {
+    *err = "unknown flag bits (FFX_TUNE, FFX_UNFUSED and FFX_TC_UNSPLIT do not apply to many-instance plans)";
+    return FFX_EINVAL;
+  }
+  if ((flags & FFX_TC_BF16) && (flags & FFX_TC_TF32)) {
+    *err = "FFX_TC_BF16 and FFX_TC_TF32 exclude each other";
+    return FFX_EINVAL;
+  }
+  if ((flags & (FFX_TC_BF16 | FFX_TC_TF32)) && form != FFX_FORM_TC && form != FFX_FORM_AUTO) {
+    *err = "FFX_TC_BF16 and FFX_TC_TF32 need FFX_FORM_TC or FFX_FORM_AUTO";
     return FFX_EINVAL;
   }
   if (form != FFX_FORM_AUTO && form != FFX_FORM_PAPER && form != FFX_FORM_FOLD && form != FFX_FORM_DENSE &&
@@ -566,7 +600,10 @@ int many_create(ManyPlan** out, int n, const ffx_instance_desc* d, uint32_t flag
   // lam (5 log2 N + 14) + 5 log2 N at ~0.11).
   // Tensor-core mode (FFX_FORM_TC, or the automatic form once dense): every
   // key's lines a multiple of 16 points from 32 up; otherwise, or if the
-  // kernel cannot be resident, the FP32 dense phases.
+  // kernel cannot be resident, the FP32 dense phases.  Its passes over lines
+  // of 64 to 256 points, a multiple of 32, take split BF16 operands (but the
+  // first adjoint pass of a backward call, with its gradient factors), the
+  // others split TF32.
   if (rc == FFX_OK) {
     bool dense = (form == FFX_FORM_DENSE || form == FFX_FORM_TC);
     if (form == FFX_FORM_AUTO) {
@@ -578,7 +615,10 @@ int many_create(ManyPlan** out, int n, const ffx_instance_desc* d, uint32_t flag
     }
     bool tc = (form == FFX_FORM_TC || form == FFX_FORM_AUTO);
     for (const AxisTab& at : mp->tabs) tc = tc && dense_tc_supported(at.N);
-    if (dense) rc = build_dense_maps(mp, tc, s, err);
+    // split BF16 operands on the lengths the BF16 kernel takes, unless split
+    // TF32 is asked for
+    const bool bf16 = !(flags & FFX_TC_TF32);
+    if (dense) rc = build_dense_maps(mp, tc, bf16, s, err);
   }
   cudaStreamDestroy(s);
   if (rc != FFX_OK) {
@@ -714,24 +754,96 @@ int build_dense_phases(ManyPlan* mp, int mode, std::string* err) {
   return FFX_OK;
 }
 
+// One tensor-core phase launch over the passes `args` (split TF32 or BF16
+// kernel): the row blocks of one (pass, line tile) form a group that one block
+// runs back to back, so the second row block reads the lines from L2 right
+// after the first.  Groups are dealt to blocks biggest first, each to the least
+// loaded block (cost: K chunks x rows), and every block runs its groups in the
+// order dealt.
+int deal_tc_phase(ManyPlan* mp, int kind, const std::vector<TcPassArg>& args, std::vector<Phase>& phases,
+                  std::string* err) {
+  if (args.empty()) return FFX_OK;
+  const bool bf = (kind == KIND_TC16);
+  const int64_t LN = bf ? many_bf16_lines() : many_tc_lines();
+  Phase ph;
+  ph.kind = kind;
+  std::vector<std::pair<double, int>> groups;  // (cost, pass)
+  for (size_t i = 0; i < args.size(); ++i) groups.push_back({(double)args[i].d.N * args[i].d.N, (int)i});
+  std::stable_sort(groups.begin(), groups.end(),
+                   [](const std::pair<double, int>& x, const std::pair<double, int>& y) { return x.first > y.first; });
+  const int nb = mp->grid_tc;
+  std::vector<std::vector<TcItem>> per_block(nb);
+  // least loaded block first (ties: lower index)
+  typedef std::pair<double, int> Load;
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+  for (int b = 0; b < nb; ++b) heap.push({0.0, b});
+  for (const auto& gr : groups) {
+    const TcPassArg& pa = args[gr.second];
+    const int N = (int)pa.d.N;
+    const int64_t ctiles = (pa.d.ncols + LN - 1) / LN;
+    const int mts = bf ? many_bf16_row_blocks(N) : many_tc_row_blocks(N);
+    const double per_group = (2.0 * N / 32) * (2.0 * N);  // K chunks x real rows, all row blocks
+    for (int64_t ct = 0; ct < ctiles; ++ct) {
+      Load l = heap.top();
+      heap.pop();
+      for (int mt = 0; mt < mts; ++mt) {
+        TcItem w;
+        w.ct = ct;
+        w.arg = gr.second;
+        w.mt = mt;
+        per_block[l.second].push_back(w);
+      }
+      l.first += per_group;
+      heap.push(l);
+    }
+  }
+  std::vector<TcItem> flat;
+  std::vector<long long> first(nb + 1, 0);
+  for (int b = 0; b < nb; ++b) {
+    first[b] = (long long)flat.size();
+    flat.insert(flat.end(), per_block[b].begin(), per_block[b].end());
+  }
+  first[nb] = (long long)flat.size();
+  const size_t abytes = (args.size() * sizeof(TcPassArg) + 255) & ~size_t(255);
+  const size_t fbytes = ((size_t)(nb + 1) * sizeof(long long) + 255) & ~size_t(255);
+  const size_t bytes = abytes + fbytes + flat.size() * sizeof(TcItem);
+  void* m = nullptr;
+  cudaError_t e = cudaMalloc(&m, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *err = std::string("work list: ") + cudaGetErrorString(e);
+    return FFX_ENOMEM;
+  }
+  ph.d_targs = (TcPassArg*)m;
+  ph.d_first = (long long*)((char*)m + abytes);
+  ph.d_titems = (TcItem*)((char*)m + abytes + fbytes);
+  ph.n_titems = (long long)flat.size();
+  e = cudaMemcpy(ph.d_targs, args.data(), args.size() * sizeof(TcPassArg), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(ph.d_first, first.data(), first.size() * sizeof(long long), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ph.d_titems, flat.data(), flat.size() * sizeof(TcItem), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(m);
+    *err = std::string("work list upload: ") + cudaGetErrorString(e);
+    return FFX_ECUDA;
+  }
+  phases.push_back(ph);
+  return FFX_OK;
+}
+
 // Tensor-core phases of one mode: the same chains of steps as the dense
-// phases, cut into items of 128 lines x 128 real rows.  The row blocks of one
-// (pass, line tile) form a group that one block runs back to back, so the
-// second row block reads the lines from L2 right after the first.  Groups are
-// dealt to blocks biggest first, each to the least loaded block (cost: K
-// chunks x rows), and every block runs its groups in the order dealt.
+// phases, cut into items of 128 lines x 128 real rows.  Each step is one
+// launch of the BF16 kernel over the passes it takes (BF16 plans, lines of 64
+// to 256 points, a multiple of 32, no gradient factors) and one launch of the
+// split-TF32 kernel over the others; the two touch different instances.
 int build_tc_phases(ManyPlan* mp, int mode, std::string* err) {
   std::vector<Phase>& phases = mp->phases[mode];
   const int D = mp->max_dim;
   const int nphases = (mode == 2) ? 2 * D : D;
-  const int64_t LN = many_tc_lines();
   for (int ph_i = 0; ph_i < nphases; ++ph_i) {
     const bool adj = (mode == 2 && ph_i >= D);
     const int r = adj ? ph_i - D : ph_i;
-    Phase ph;
-    ph.kind = KIND_TC;
-    std::vector<TcPassArg> args;
-    std::vector<std::pair<double, int>> groups;  // (cost, pass)
+    std::vector<TcPassArg> args_tf, args_bf;
     for (const Instance& in : mp->inst) {
       if (r >= in.ndim) continue;
       const int n_i = in.ndim;
@@ -770,70 +882,13 @@ int build_tc_phases(ManyPlan* mp, int mode, std::string* err) {
       a.batch = 1;
       a.ncols = outer * inner;
       a.N = at.N;
-      pa.tblk = at.tc[adj ? 1 : 0];
-      groups.push_back({(double)at.N * at.N, (int)args.size()});
-      args.push_back(pa);
+      const bool bf = at.bf[adj ? 1 : 0] != nullptr && pa.grad_base < 0;
+      pa.tblk = bf ? at.bf[adj ? 1 : 0] : at.tc[adj ? 1 : 0];
+      (bf ? args_bf : args_tf).push_back(pa);
     }
-    std::stable_sort(groups.begin(), groups.end(),
-                     [](const std::pair<double, int>& x, const std::pair<double, int>& y) { return x.first > y.first; });
-    const int nb = mp->grid_tc;
-    std::vector<std::vector<TcItem>> per_block(nb);
-    // least loaded block first (ties: lower index)
-    typedef std::pair<double, int> Load;
-    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-    for (int b = 0; b < nb; ++b) heap.push({0.0, b});
-    for (const auto& gr : groups) {
-      const TcPassArg& pa = args[gr.second];
-      const int N = (int)pa.d.N;
-      const int64_t ctiles = (pa.d.ncols + LN - 1) / LN;
-      const int mts = many_tc_row_blocks(N);
-      const double per_group = (2.0 * N / 32) * (2.0 * N);  // K chunks x real rows, all row blocks
-      for (int64_t ct = 0; ct < ctiles; ++ct) {
-        Load l = heap.top();
-        heap.pop();
-        for (int mt = 0; mt < mts; ++mt) {
-          TcItem w;
-          w.ct = ct;
-          w.arg = gr.second;
-          w.mt = mt;
-          per_block[l.second].push_back(w);
-        }
-        l.first += per_group;
-        heap.push(l);
-      }
-    }
-    std::vector<TcItem> flat;
-    std::vector<long long> first(nb + 1, 0);
-    for (int b = 0; b < nb; ++b) {
-      first[b] = (long long)flat.size();
-      flat.insert(flat.end(), per_block[b].begin(), per_block[b].end());
-    }
-    first[nb] = (long long)flat.size();
-    const size_t abytes = (args.size() * sizeof(TcPassArg) + 255) & ~size_t(255);
-    const size_t fbytes = ((size_t)(nb + 1) * sizeof(long long) + 255) & ~size_t(255);
-    const size_t bytes = abytes + fbytes + flat.size() * sizeof(TcItem);
-    void* m = nullptr;
-    cudaError_t e = cudaMalloc(&m, bytes);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      *err = std::string("work list: ") + cudaGetErrorString(e);
-      return FFX_ENOMEM;
-    }
-    ph.d_targs = (TcPassArg*)m;
-    ph.d_first = (long long*)((char*)m + abytes);
-    ph.d_titems = (TcItem*)((char*)m + abytes + fbytes);
-    ph.n_titems = (long long)flat.size();
-    e = cudaMemcpy(ph.d_targs, args.data(), args.size() * sizeof(TcPassArg), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-      e = cudaMemcpy(ph.d_first, first.data(), first.size() * sizeof(long long), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-      e = cudaMemcpy(ph.d_titems, flat.data(), flat.size() * sizeof(TcItem), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-      cudaFree(m);
-      *err = std::string("work list upload: ") + cudaGetErrorString(e);
-      return FFX_ECUDA;
-    }
-    phases.push_back(ph);
+    int rc = deal_tc_phase(mp, KIND_TC16, args_bf, phases, err);
+    if (rc == FFX_OK) rc = deal_tc_phase(mp, KIND_TC, args_tf, phases, err);
+    if (rc) return rc;
   }
   return FFX_OK;
 }
@@ -920,6 +975,7 @@ int build_phases(ManyPlan* mp, int mode, std::string* err) {
 const void* phase_func(int kind) {
   switch (kind) {
     case KIND_TC: return many_tc_func();
+    case KIND_TC16: return many_bf16_func();
     case KIND_FWD_PAPER: return (const void*)many_kernel<KIND_FWD_PAPER>;
     case KIND_FWD_FOLD: return (const void*)many_kernel<KIND_FWD_FOLD>;
     case KIND_DENSE: return (const void*)many_dense_kernel;
@@ -945,10 +1001,11 @@ TcParams tc_params(const ManyPlan* mp, const Phase& ph, const ManyCall& call) {
 void phase_node_params(const ManyPlan* mp, const Phase& ph, void** params, cudaKernelNodeParams* kp) {
   std::memset(kp, 0, sizeof(*kp));
   kp->func = (void*)phase_func(ph.kind);
-  if (ph.kind == KIND_TC) {
+  if (ph.kind == KIND_TC || ph.kind == KIND_TC16) {
+    const bool bf = ph.kind == KIND_TC16;
     kp->gridDim = dim3(mp->grid_tc);
-    kp->blockDim = dim3(many_tc_threads());
-    kp->sharedMemBytes = (unsigned)many_tc_smem();
+    kp->blockDim = dim3(bf ? many_bf16_threads() : many_tc_threads());
+    kp->sharedMemBytes = (unsigned)(bf ? many_bf16_smem() : many_tc_smem());
     kp->kernelParams = params;
     return;
   }
@@ -997,7 +1054,7 @@ int build_graph(ManyPlan* mp, int mode, const ManyCall& call, std::string* err) 
     TcParams tp = tc_params(mp, ph, call);
     void* tparams[] = {(void*)&tp};
     cudaKernelNodeParams kp;
-    phase_node_params(mp, ph, ph.kind == KIND_TC ? tparams : params, &kp);
+    phase_node_params(mp, ph, (ph.kind == KIND_TC || ph.kind == KIND_TC16) ? tparams : params, &kp);
     e = cudaGraphAddKernelNode(&knode, g, &mnode, 1, &kp);
     if (e != cudaSuccess) break;
     kn.push_back(knode);
@@ -1030,7 +1087,7 @@ int launch_mode(ManyPlan* mp, int mode, const ManyCall& call, cudaStream_t s, st
       TcParams tp = tc_params(mp, ph, call);
       void* tparams[] = {(void*)&tp};
       cudaKernelNodeParams kp;
-      phase_node_params(mp, ph, ph.kind == KIND_TC ? tparams : params, &kp);
+      phase_node_params(mp, ph, (ph.kind == KIND_TC || ph.kind == KIND_TC16) ? tparams : params, &kp);
       cudaError_t e = cudaGraphExecKernelNodeSetParams(mp->exec[mode], mp->knodes[mode][k], &kp);
       if (e != cudaSuccess) {
         *err = std::string("graph update: ") + cudaGetErrorString(e);
@@ -1055,7 +1112,9 @@ void many_destroy(ManyPlan* mp) {
     if (mp->exec[m]) cudaGraphExecDestroy(mp->exec[m]);
     if (mp->graph[m]) cudaGraphDestroy(mp->graph[m]);
     for (Phase& ph : mp->phases[m])
-      cudaFree(ph.kind == KIND_TC ? (void*)ph.d_targs : ph.kind == KIND_DENSE ? (void*)ph.d_dargs : (void*)ph.d_args);
+      cudaFree((ph.kind == KIND_TC || ph.kind == KIND_TC16) ? (void*)ph.d_targs
+               : ph.kind == KIND_DENSE                      ? (void*)ph.d_dargs
+                                                            : (void*)ph.d_args);
   }
   if (mp->tc_mem) cudaFree(mp->tc_mem);
   if (mp->dense_mem) cudaFree(mp->dense_mem);
@@ -1067,6 +1126,12 @@ int64_t many_total(const ManyPlan* mp) { return mp->total; }
 int64_t many_kernels(const ManyPlan* mp, int mode) { return (int64_t)mp->phases[mode].size(); }
 int64_t many_offset(const ManyPlan* mp, int i) { return (i < 0 || i >= mp->n) ? -1 : mp->inst[i].off; }
 int many_form(const ManyPlan* mp) { return mp->form; }
+bool many_bf16(const ManyPlan* mp) {
+  if (!mp->tc || !mp->bf16) return false;
+  for (const AxisTab& at : mp->tabs)
+    if (at.bf[0]) return true;
+  return false;
+}
 int many_max_dim(const ManyPlan* mp) { return mp->max_dim; }
 int* many_device_errors(const ManyPlan* mp) { return mp->dev_err; }
 

@@ -62,6 +62,7 @@
 #include <cstring>
 
 #include "ffx_internal.h"
+#include "ffx_tc_many.h"
 #include "ffx_tcgen05.cuh"
 
 namespace ffx {
@@ -714,6 +715,353 @@ __global__ void __launch_bounds__(256) bf16_split_kernel(const float4* __restric
   }
 }
 
+// ---------------------------------------------------------------------------
+// Many-instance phases (ffx_plan_many): one launch runs the work list of a
+// phase, items of 128 lines x 128 real rows of the passes of many instances,
+// each pass with its own N, line geometry, buffers and T blocks; block b takes
+// items [block_first[b], block_first[b + 1]).  The roles, stages, barriers and
+// bounded waits are those of dense_bf16_kernel with the FP32 input copied in
+// place by the producers (a tensor map per launch would not cover the
+// instances' buffers); three stages, split operands, no batch sum and no
+// gradient factors.  Row blocks of 128 rows take X_hi [T_hi; T_lo] as one
+// N = 256 product, the last (shorter) row block of an axis two products.
+
+// What a role needs of one work item.
+struct BView {
+  const float2* in;
+  float2* out_c;
+  float* out_d;
+  const unsigned char* tblk;
+  int64_t inner, ncols, ct;
+  int N, mt;
+};
+
+__device__ __forceinline__ const void* many_rebase(const TcBases& c, int base, const void* off) {
+  return base < 0 ? nullptr : (const void*)((const char*)c.base[base] + (uintptr_t)off);
+}
+
+__device__ __forceinline__ BView many_view(const TcParams& P, int64_t w) {
+  const TcItem item = P.items[w];
+  const TcPassArg& pa = P.args[item.arg];
+  BView v;
+  v.in = (const float2*)many_rebase(P.call, pa.in_base, pa.d.in);
+  v.out_c = (float2*)many_rebase(P.call, pa.outc_base, pa.d.out_c);
+  v.out_d = (float*)many_rebase(P.call, pa.outd_base, pa.d.out_d);
+  v.tblk = pa.tblk;
+  v.inner = pa.d.inner;
+  v.ncols = pa.d.ncols;
+  v.N = pa.d.N;
+  v.ct = item.ct;
+  v.mt = item.mt;
+  return v;
+}
+
+// First point of line c of an item's pass (a batch of one), or -1 past the end.
+__device__ __forceinline__ long long many_line(const BView& v, int64_t c) {
+  if (c >= v.ncols) return -1;
+  const int64_t bo = c / v.inner;
+  return bo * (int64_t)v.N * v.inner + (c - bo * v.inner);
+}
+
+// Producer thread t's 4 core-matrix rows of a chunk, as in dense_bf16_kernel:
+// row i is line prod_line of the item and K group prod_kp, at byte prod_off of
+// the stage's X head and X tail parts.
+__device__ __forceinline__ int prod_line(bool contiguous, int t, int i) {
+  return contiguous ? (t & 7) + 8 * (t >> 5) + 64 * (i >> 1) : (t & (BL - 1));
+}
+__device__ __forceinline__ int prod_kp(bool contiguous, int t, int i) {
+  return contiguous ? ((t >> 3) & 3) + 4 * (i & 1) : (t >> 7) * BITEMS + i;
+}
+__device__ __forceinline__ int prod_off(bool contiguous, int t, int i) {
+  const int n = prod_line(contiguous, t, i);
+  return (n >> 3) * BSBO + prod_kp(contiguous, t, i) * BCORE + (n & 7) * 16;
+}
+
+constexpr int BMANY_STAGES = 3;
+constexpr int BMANY_SMEM = BMANY_STAGES * BSTAGE;
+
+__global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcParams P) {
+  constexpr int BSTAGES = BMANY_STAGES;
+  extern __shared__ __align__(1024) unsigned char bsm[];
+  __shared__ __align__(8) uint64_t full_bar[BSTAGES], empty_bar[BSTAGES], copy_bar[BSTAGES];
+  __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int s_abort;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int64_t first = P.block_first[blockIdx.x], last = P.block_first[blockIdx.x + 1];
+  if (first >= last) return;
+
+  if (warp == BMMA_WARP) tmem_alloc(&tmem_slot, BCOLS);
+  if (tid == 0) {
+    for (int s = 0; s < BSTAGES; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), BPROD);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+      mbar_init(smem_u32(&copy_bar[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&accf_bar[b]), 1);
+      mbar_init(smem_u32(&acce_bar[b]), BEPI);
+    }
+    mbar_init(smem_u32(&done_bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t smem_base = smem_u32(bsm);
+
+  if (warp < BMMA_WARP) {
+    // ---------------- producers ----------------
+    const int t = tid;
+    // Issue side: chunk j of the block's run into stage j % BSTAGES once the
+    // products of chunk j - BSTAGES have freed it; thread 0 copies the T chunk
+    // on the stage's "copy" barrier, every thread its points of the input.
+    // The chunk's position (item iw, K chunk ikc) advances incrementally.
+    int64_t iw = first, ci = 0;
+    int ikc = 0, is = 0;
+    BView iv = many_view(P, first);
+    int ikch = (2 * iv.N) / BKC;
+    long long ilb[2] = {-1, -1};
+    bool lines_ok = false;
+    int last_u[BSTAGES];
+#pragma unroll
+    for (int q = 0; q < BSTAGES; ++q) last_u[q] = -1;
+    auto issue = [&]() -> bool {
+      if (iw < last) {
+        const int64_t u = ci / BSTAGES;
+        if (u >= 1 && !mbar_wait(smem_u32(&empty_bar[is]), (uint32_t)((u - 1) & 1), &s_abort)) return false;
+        unsigned char* st = bsm + is * BSTAGE;
+        const uint32_t xh = smem_u32(st + BTCHUNK), xl = xh + BPART;
+        if (t == 0) {
+          const uint32_t part = (uint32_t)brow_count(iv.N, iv.mt) * (BKC * 2);
+          const uint32_t cb = smem_u32(&copy_bar[is]);
+          mbar_expect_tx(cb, 2 * part);
+          const unsigned char* src = iv.tblk + ((size_t)iv.mt * ikch + ikc) * BTCHUNK;
+          const uint32_t dst = smem_u32(st);
+          if (part == (uint32_t)BPART) {
+            bulk_g2s(dst, src, BTCHUNK, cb);  // head and tail in one copy
+          } else {
+            bulk_g2s(dst, src, part, cb);
+            bulk_g2s(dst + BPART, src + BPART, part, cb);
+          }
+          last_u[is] = (int)(u & 1);
+        }
+        const int64_t inner = iv.inner;
+        const bool contiguous = (inner == 1);
+        if (!lines_ok) {
+          ilb[0] = many_line(iv, iv.ct * BL + prod_line(contiguous, t, 0));
+          if (contiguous) ilb[1] = many_line(iv, iv.ct * BL + prod_line(contiguous, t, 2));
+          lines_ok = true;
+        }
+#pragma unroll
+        for (int i = 0; i < BITEMS; ++i) {
+          const long long lb = ilb[contiguous ? (i >> 1) : 0];
+          const bool valid = lb >= 0;
+          const int k0 = ikc * (BKC / 2) + 4 * prod_kp(contiguous, t, i);  // first complex point
+          const int64_t addr = valid ? lb + (int64_t)k0 * inner : 0;
+          const uint32_t off = (uint32_t)prod_off(contiguous, t, i);
+          // lines past the pass's end read nothing and land as zeros (source size 0)
+          if (contiguous) {
+            cp_async16(xh + off, iv.in + addr, valid ? 16 : 0);
+            cp_async16(xl + off, iv.in + addr + (valid ? 2 : 0), valid ? 16 : 0);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              cp_async8((j < 2 ? xh : xl) + off + (uint32_t)((j & 1) * 8), iv.in + addr + (valid ? j * inner : 0),
+                        valid ? 8 : 0);
+          }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        ++ci;
+        is = is + 1 == BSTAGES ? 0 : is + 1;
+        if (++ikc == ikch) {
+          ikc = 0;
+          lines_ok = false;
+          if (++iw < last) {
+            iv = many_view(P, iw);
+            ikch = (2 * iv.N) / BKC;
+          }
+        }
+      } else {
+        asm volatile("cp.async.commit_group;" ::: "memory");  // an empty group past the end keeps the count
+      }
+      return true;
+    };
+    bool ok = true;
+#pragma unroll 1
+    for (int r = 0; r < BSTAGES - 1; ++r) ok = issue() && ok;
+    // Conversion side: its own position (item cw, K chunk ckc), BSTAGES - 1
+    // chunks behind the issue side.
+    int64_t cw = first;
+    int ckc = 0;
+    int cN = P.args[P.items[first].arg].d.N;
+    bool ccontig = P.args[P.items[first].arg].d.inner == 1;
+#pragma unroll 1
+    for (int64_t c = 0; cw < last; ++c) {
+      const int s = (int)(c % BSTAGES);
+      unsigned char* xa = bsm + s * BSTAGE + BTCHUNK;
+      // this thread's points of the chunk have landed (of its groups only the
+      // BSTAGES - 2 newer ones may be pending); it alone touches their bytes
+      asm volatile("cp.async.wait_group %0;" ::"n"(BSTAGES - 2) : "memory");
+      if (!ok) break;
+#pragma unroll
+      for (int i = 0; i < BITEMS; ++i) {
+        const int off = prod_off(ccontig, t, i);
+        const float4 r0 = *reinterpret_cast<const float4*>(xa + off);
+        const float4 r1 = *reinterpret_cast<const float4*>(xa + BPART + off);
+        const float v[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+        uint4 hi, lo;
+        split8(v, hi, lo, false);
+        *reinterpret_cast<uint4*>(xa + off) = hi;
+        *reinterpret_cast<uint4*>(xa + BPART + off) = lo;
+      }
+      fence_async_smem();
+      mbar_arrive(smem_u32(&full_bar[s]));
+      // the copies of chunk c + BSTAGES - 1, into the stage chunk c - 1 used
+      ok = issue() && ok;
+      if (++ckc == (2 * cN) / BKC) {
+        ckc = 0;
+        if (++cw < last) {
+          const DenseArgs& d = P.args[P.items[cw].arg].d;
+          cN = d.N;
+          ccontig = d.inner == 1;
+        }
+      }
+    }
+    // nothing of this thread's may still be in flight at exit
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (t == 0)
+      for (int q = 0; q < BSTAGES; ++q)
+        if (last_u[q] >= 0) mbar_wait_own(smem_u32(&copy_bar[q]), (uint32_t)last_u[q], &s_abort);
+  } else if (warp == BMMA_WARP) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int64_t g = 0, sub = 0;
+      bool ok = true;
+      for (int64_t w = first; ok && w < last; ++w, ++sub) {
+        const TcItem item = P.items[w];
+        const int N = P.args[item.arg].d.N;
+        const int rows = brow_count(N, item.mt);
+        const int kchunks = (2 * N) / BKC;
+        const uint32_t idesc = idesc_bf16(BL, rows);
+        const bool whole = rows == BR;
+        const int buf = (int)(sub & 1);
+        const int64_t v = sub >> 1;
+        if (v >= 1 && !mbar_wait(smem_u32(&acce_bar[buf]), (uint32_t)((v - 1) & 1), &s_abort)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d1 = tmem + (uint32_t)(buf * 2 * BR), d2 = d1 + BR;
+        for (int kc = 0; kc < kchunks; ++kc, ++g) {
+          const int s = (int)(g % BSTAGES);
+          const int64_t u = g / BSTAGES;
+          if (!mbar_wait(smem_u32(&copy_bar[s]), (uint32_t)(u & 1), &s_abort) ||
+              !mbar_wait(smem_u32(&full_bar[s]), (uint32_t)(u & 1), &s_abort)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t th = smem_base + (uint32_t)(s * BSTAGE), tl = th + BPART;
+          const uint32_t xh = th + BTCHUNK, xl = xh + BPART;
+#pragma unroll
+          for (int ks = 0; ks < BKC / 16; ++ks) {
+            const uint32_t o = (uint32_t)(ks * 2 * BCORE);
+            const uint64_t dxh = make_desc(xh + o, BCORE, BSBO), dxl = make_desc(xl + o, BCORE, BSBO);
+            const uint64_t dth = make_desc(th + o, BCORE, BSBO);
+            const uint32_t more = (kc == 0 && ks == 0) ? 0u : 1u;
+            if (whole) {
+              // the T chunk's 256 rows (head rows, then tail rows) into [d1 | d2]
+              mma_f16(d1, dxh, dth, idesc_bf16(BL, 2 * BR), more);
+            } else {
+              mma_f16(d1, dxh, dth, idesc, more);
+              mma_f16(d2, dxh, make_desc(tl + o, BCORE, BSBO), idesc, more);
+            }
+            mma_f16(d2, dxl, dth, idesc, 1u);
+          }
+          mma_commit(smem_u32(&empty_bar[s]));
+        }
+        if (ok) mma_commit(smem_u32(&accf_bar[buf]));
+      }
+      // whatever happened, the tensor cores finish this thread's work before exit
+      mma_commit(smem_u32(&done_bar));
+      mbar_wait_own(smem_u32(&done_bar), 0u, &s_abort);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue ----------------
+    const int q = warp & 3;       // tensor-memory lane quarter this warp may read
+    const int r = q * 32 + lane;  // line within the item
+    int64_t sub = 0;
+    bool ok = true;
+    for (int64_t w = first; ok && w < last; ++w, ++sub) {
+      const BView ev = many_view(P, w);
+      const int64_t inner = ev.inner;
+      const bool contiguous = (inner == 1);
+      const int nbase = ev.mt * (BR / 2);
+      const int rows = brow_count(ev.N, ev.mt);
+      const int buf = (int)(sub & 1);
+      const int64_t v = sub >> 1;
+      // lane 0 polls; the outcome is the warp's (its tensor-memory loads need the whole warp)
+      bool got = true;
+      if (lane == 0) got = mbar_wait(smem_u32(&accf_bar[buf]), (uint32_t)(v & 1), &s_abort);
+      ok = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+      if (!ok) break;
+      tc_fence_after();
+      const long long base = many_line(ev, ev.ct * BL + r);
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * BR);
+#pragma unroll 1
+      for (int j0 = 0; j0 < rows; j0 += 16) {
+        uint32_t x[16], z[16];
+        tmem_ld16(taddr + (uint32_t)j0, x);
+        tmem_ld16(taddr + (uint32_t)(BR + j0), z);
+        tmem_wait_ld();
+        float y[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) y[m] = __uint_as_float(x[m]) + __uint_as_float(z[m]);
+        const int n0 = nbase + j0 / 2;  // complex outputs n0 .. n0 + 7 of this line
+        if (base < 0) continue;
+        if (ev.out_c) {
+          if (contiguous) {
+            float4* o = reinterpret_cast<float4*>(ev.out_c + base + n0);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) o[m] = make_float4(y[4 * m], y[4 * m + 1], y[4 * m + 2], y[4 * m + 3]);
+          } else {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) ev.out_c[base + (int64_t)(n0 + m) * inner] = make_float2(y[2 * m], y[2 * m + 1]);
+          }
+        } else {
+          float dd[8];
+#pragma unroll
+          for (int m = 0; m < 8; ++m) dd[m] = y[2 * m] * y[2 * m] + y[2 * m + 1] * y[2 * m + 1];
+          if (contiguous) {
+            float4* o = reinterpret_cast<float4*>(ev.out_d + base + n0);
+            o[0] = make_float4(dd[0], dd[1], dd[2], dd[3]);
+            o[1] = make_float4(dd[4], dd[5], dd[6], dd[7]);
+          } else {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) ev.out_d[base + (int64_t)(n0 + m) * inner] = dd[m];
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(smem_u32(&acce_bar[buf]));
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && s_abort && P.err) atomicAdd(P.err, 1);
+  if (warp == BMMA_WARP) {
+    tc_fence_after();
+    tmem_free(tmem, BCOLS);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_bf16_split(const float2* in, uint32_t* planes, int64_t n, int64_t plane, int unsplit, int sms,
@@ -759,6 +1107,17 @@ cudaError_t dense_bf16_prepare() {
                                bf16_kind_smem(k));
   return e;
 }
+
+const void* many_bf16_func() { return (const void*)dense_bf16_many_kernel; }
+int many_bf16_threads() { return BTHREADS; }
+size_t many_bf16_smem() { return (size_t)BMANY_SMEM; }
+cudaError_t many_bf16_prepare() {
+  return cudaFuncSetAttribute((const void*)dense_bf16_many_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              BMANY_SMEM);
+}
+int many_bf16_lines() { return BL; }
+int many_bf16_row_blocks(int N) { return (2 * N + BR - 1) / BR; }
+bool many_bf16_supported(int N) { return N >= 64 && N <= 256 && N % 32 == 0; }
 
 cudaError_t launch_bf16_build_t(const float2* T, unsigned char* Tblk, int N, cudaStream_t s) {
   bf16_build_t_kernel<<<256, 256, 0, s>>>(T, Tblk, N);

@@ -50,4 +50,15 @@ cudaError_t many_tc_prepare();
 int many_tc_lines();          // lines per item
 int many_tc_row_blocks(int N);
 
+// The BF16 variant (ffx_tc16.cu) for lines of 64 to 256 points, a multiple
+// of 32: the same work lists and parameters, with split BF16 operand blocks
+// of T (launch_bf16_build_t layout) in TcPassArg::tblk.  No gradient passes.
+const void* many_bf16_func();
+int many_bf16_threads();
+size_t many_bf16_smem();
+cudaError_t many_bf16_prepare();
+int many_bf16_lines();
+int many_bf16_row_blocks(int N);
+bool many_bf16_supported(int N);
+
 }  // namespace ffx

@@ -330,9 +330,12 @@ class PlanMany(Plan):
 
     ``instances``: sequence of (dims, spacing, t, magnification) or
     (dims, spacing, t, magnification, a, abar).  Inputs and outputs are packed
-    1-D tensors of ``points`` elements; instance i starts at ``offsets[i]``."""
+    1-D tensors of ``points`` elements; instance i starts at ``offsets[i]``.
+    ``tf32=True`` keeps split TF32 operands on every tensor-core phase
+    (FFX_TC_TF32); by default the passes over lines of 64 to 256 points, a
+    multiple of 32, take split BF16 operands."""
 
-    def __init__(self, instances, form: str = "auto"):
+    def __init__(self, instances, form: str = "auto", tf32: bool = False):
         lib = load_library()
         n = len(instances)
         descs = (InstanceDesc * n)()
@@ -351,13 +354,15 @@ class PlanMany(Plan):
                     d.a[j] = float(spec[4][j])
                     d.abar[j] = float(spec[5][j])
         h = ctypes.c_void_p()
-        _check(lib.ffx_plan_many(ctypes.byref(h), n, descs, _FORMS[form]), "ffx_plan_many")
+        flags = _FORMS[form] | (FFX_TC_TF32 if tf32 else 0)
+        _check(lib.ffx_plan_many(ctypes.byref(h), n, descs, flags), "ffx_plan_many")
         self._h = h
         self.accumulate = False
         self.form = _FORM_NAMES[lib.ffx_plan_form(h)]
         self.instances = [tuple(tuple(x) if hasattr(x, "__len__") else x for x in spec[:4]) for spec in instances]
         self.points = int(lib.ffx_plan_points(h))
         self.offsets = [int(lib.ffx_plan_many_offset(h, i)) for i in range(n)]
+        self.bf16 = lib.ffx_plan_tc_bf16(h) == 1
         self.fused, self.fused_max_batch = False, 0
         self.dims = (self.points,)
         self.M = self.points

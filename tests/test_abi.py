@@ -74,3 +74,22 @@ def test_host_argument_checks(lib):
                                ctypes.c_void_p]
     assert lib.ffx_expand(None, None, 1, None, None) == 1
     assert lib.ffx_plan_destroy(None) == 0
+
+
+def test_many_plan_flag_checks(lib):
+    """Many-instance plans reject the flags that do not apply to them, and the
+    operand flags outside the tensor-core forms, before any CUDA call."""
+    from paper_1602_03395_gb300.ffx import InstanceDesc
+    descs = (InstanceDesc * 1)()
+    descs[0].ndim = 1
+    descs[0].dims[0] = 64
+    descs[0].spacing[0] = 0.2
+    descs[0].magnification[0] = 3
+    descs[0].t = 1.0
+    lib.ffx_last_error.restype = ctypes.c_char_p
+    h = ctypes.c_void_p()
+    for flags, text in [(0x10, b"ACCUMULATE"), (0x20, b"flag"), (0x40, b"flag"), (0x80 | 0x4, b"flag"),
+                        (0x100 | 0x200, b"exclude"), (0x200 | 0x2, b"FFX_FORM_TC"), (0x100 | 0x3, b"FFX_FORM_TC")]:
+        assert lib.ffx_plan_many(ctypes.byref(h), 1, descs, ctypes.c_uint32(flags)) == 1, hex(flags)
+        assert text in lib.ffx_last_error(), (hex(flags), lib.ffx_last_error())
+        assert h.value is None

@@ -55,14 +55,18 @@ def test_many_mixed_shapes_against_oracle(form):
 TC_DIMS = [(48, 32, 32), (32, 32), (96,), (64, 128, 32), (64, 48, 32), (192, 32)]
 
 
-def test_many_tc_against_oracle():
-    """Tensor-core phases (split TF32): every line length a multiple of 16
-    from 32, narrower last row blocks (48, 96, 192), strided and contiguous
-    axes, 1-D to 3-D instances."""
+@pytest.mark.parametrize("tf32", [False, True])
+def test_many_tc_against_oracle(tf32):
+    """Tensor-core phases: every line length a multiple of 16 from 32,
+    narrower last row blocks (48, 96, 192), strided and contiguous axes, 1-D
+    to 3-D instances.  By default the 64-, 96-, 128- and 192-point passes run
+    on the BF16 kernel and the 32- and 48-point passes on the split-TF32
+    kernel in the same phases; tf32 keeps split TF32 throughout."""
     ffx = require_gpu()
     specs, psis = mixed_specs(9, dims_override=TC_DIMS)
-    plan = ffx.PlanMany(specs, form="tc")
+    plan = ffx.PlanMany(specs, form="tc", tf32=tf32)
     assert plan.form == "tc"
+    assert plan.bf16 == (not tf32)
     x = to_dev(pack(plan, psis))
     rho = ffx.ffx_expand(plan, x).cpu().numpy()
     field = ffx.ffx_expand_field(plan, x).cpu().numpy()
@@ -74,14 +78,17 @@ def test_many_tc_against_oracle():
         worst_d = max(worst_d, rel_l2(rho[off:off + m].reshape(dims), np.abs(ref) ** 2))
         worst_f = max(worst_f, rel_l2(field[off:off + m].reshape(dims), ref))
     plan.close()
-    print(f"many (tc): worst density {worst_d:.2e}, worst field {worst_f:.2e}")
+    print(f"many (tc, tf32={tf32}): worst density {worst_d:.2e}, worst field {worst_f:.2e}")
     assert worst_d < DENSITY_TOL and worst_f < FIELD_TOL
 
 
-def test_many_tc_backward_against_oracle():
+@pytest.mark.parametrize("tf32", [False, True])
+def test_many_tc_backward_against_oracle(tf32):
+    """Backward calls: the first adjoint pass (with the gradient factors) on
+    split TF32, the other passes of 64..256-point lines on BF16 by default."""
     ffx = require_gpu()
     specs, psis = mixed_specs(5, dims_override=[(32, 48), (48, 32, 32), (64,), (96, 32), (128, 32)])
-    plan = ffx.PlanMany(specs, form="tc")
+    plan = ffx.PlanMany(specs, form="tc", tf32=tf32)
     assert plan.form == "tc"
     rng = np.random.default_rng(8)
     grads = [rng.normal(size=p.shape).astype(np.float32) for p in psis]
@@ -95,7 +102,7 @@ def test_many_tc_backward_against_oracle():
         ref = O.density_loss_gradient(p, gr, dx, t, lam)
         worst = max(worst, rel_l2(got[off:off + p.size].reshape(dims), ref))
     plan.close()
-    print(f"many backward (tc): worst {worst:.2e}")
+    print(f"many backward (tc, tf32={tf32}): worst {worst:.2e}")
     assert worst < FIELD_TOL
 
 
@@ -251,4 +258,28 @@ def test_many_full_mixed_workload_sampled_instances():
     print(f"many full workload ({form}): {len(chosen)} instances, {len(geoms)} geometries, "
           f"worst density {worst:.2e}")
     assert len(chosen) >= 40
+    assert worst < DENSITY_TOL
+
+
+def test_many_bf16_phases_match_tf32_phases_and_are_batch_independent():
+    """The BF16 phases on the mixed-batch shapes (64^3, 96^3, 128x32x32 with
+    its 32-point axes on split TF32 in the same phases, 48^3 on split TF32):
+    every instance within the density tolerance of the split-TF32 plan's, and
+    an instance's densities do not depend on the other instances in the plan
+    (bitwise: its items run the same arithmetic wherever they are dealt)."""
+    ffx = require_gpu()
+    ws = inputs.config_mixed_batch(count=12)
+    specs = [(w.dims, w.dx, w.t, w.lam) for w in ws]
+    psis = [w.realization(0) for w in ws]
+    with ffx.PlanMany(specs) as pb, ffx.PlanMany(specs, tf32=True) as pt:
+        assert pb.bf16 and not pt.bf16
+        rb = pb.unpack(ffx.ffx_expand(pb, to_dev(pack(pb, psis))))
+        rt = pt.unpack(ffx.ffx_expand(pt, to_dev(pack(pt, psis))))
+        assert pb.device_errors() == 0 and pt.device_errors() == 0
+        worst = max(rel_l2(a.cpu().numpy(), b.cpu().numpy()) for a, b in zip(rb, rt))
+        k = next(i for i, w in enumerate(ws) if w.dims[0] % 32 == 0)
+        with ffx.PlanMany(specs[k:k + 1]) as one:
+            r1 = ffx.ffx_expand(one, to_dev(psis[k].ravel())).cpu().numpy()
+        assert np.array_equal(r1, rb[k].cpu().numpy().ravel())
+    print(f"many bf16 vs tf32 phases: worst {worst:.2e}")
     assert worst < DENSITY_TOL
