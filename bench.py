@@ -444,15 +444,15 @@ def load_traffic(kernel_key: str):
 
 def mixed_flops(specs, form, bf16=False):
     """Algorithmic flops of one call: (all, the share on BF16 operands).  With
-    BF16 phases the passes over lines of 64 to 256 points, a multiple of 32,
-    run on the BF16 kernel, the others on split TF32."""
+    BF16 phases every pass of a tensor-core plan (lines of 32 to 256 points,
+    a multiple of 16) runs on the BF16 kernel."""
     tot = bf = 0.0
     for dims, dx, t, lam in specs:
         M = int(np.prod(dims))
         for j, N in enumerate(dims):
             f = pass_flops(N, lam[j], M // N, form)
             tot += f
-            if bf16 and 64 <= N <= 256 and N % 32 == 0:
+            if bf16 and 32 <= N <= 256 and N % 16 == 0:
                 bf += f
     return tot, bf
 
@@ -566,8 +566,7 @@ def run_mixed(args, torch, dist, world, rank, dev):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"mixed_{count}_instances_48^3_64^3_96^3_128x32x32_lam10-100",
                        "batch_per_gpu": count, "form": plan.form, "points_per_step": plan.points,
-                       "precision": ("split BF16 on the 64..256-point passes (kind::f16, three products), "
-                                     "split TF32 on the 32- and 48-point passes" if plan.bf16 else
+                       "precision": ("split BF16 on the tensor cores (kind::f16, three products)" if plan.bf16 else
                                      "split TF32 on the tensor cores (three products)" if plan.form == "tc"
                                      else "FP32"),
                        "parallelism": f"replicas x{world}",

@@ -201,11 +201,11 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
  * second packed workspace.  FFX_FORM_TC (and the automatic form, see above)
  * also builds their tensor-core operand blocks and runs each phase as
  * persistent launches over items of 128 lines x 128 real rows, one block per
- * SM: the passes over lines of 64 to 256 points, a multiple of 32, on split
- * BF16 operands (kind::f16 products, density error of order 1e-6; not the
- * first adjoint pass of ffx_expand_backward, nor with FFX_TC_TF32), the others
- * on split TF32 operands, one launch each per phase.  A plan with a 16-point
- * axis keeps the FP32 phases (ffx_plan_form reports which).  Dense passes are not in place for
+ * SM: on split BF16 operands (kind::f16 products, density error of order
+ * 1e-6), except with FFX_TC_TF32 and in the first adjoint pass of
+ * ffx_expand_backward (its gradient factors), which take split TF32 operands
+ * (one more launch in that phase).  A plan with a 16-point axis keeps the
+ * FP32 phases (ffx_plan_form reports which).  Dense passes are not in place for
  * lines over 64 points, so an in-place ffx_expand_field with a 1-D instance
  * longer than 64 points returns FFX_EUNSUPPORTED.  ffx_plan_device_errors
  * counts tensor-core phases that gave up on a bounded wait.

@@ -40,7 +40,7 @@ enum ManyBase : int { BASE_NONE = -1, BASE_PSI0 = 0, BASE_WS = 1, BASE_OUTC = 2,
                       BASE_GRAD = 4, BASE_WS2 = 5, NBASE = 6 };
 constexpr int KIND_DENSE = 100;  // a dense phase (forward or adjoint: the item's matrix decides)
 constexpr int KIND_TC = 101;     // the same on the tensor cores (split TF32)
-constexpr int KIND_TC16 = 102;   // the same with split BF16 operands (lines of 64..256 points, multiples of 32)
+constexpr int KIND_TC16 = 102;   // the same with split BF16 operands
 struct ManyCall {
   const void* base[NBASE];
 };
@@ -600,10 +600,9 @@ int many_create(ManyPlan** out, int n, const ffx_instance_desc* d, uint32_t flag
   // lam (5 log2 N + 14) + 5 log2 N at ~0.11).
   // Tensor-core mode (FFX_FORM_TC, or the automatic form once dense): every
   // key's lines a multiple of 16 points from 32 up; otherwise, or if the
-  // kernel cannot be resident, the FP32 dense phases.  Its passes over lines
-  // of 64 to 256 points, a multiple of 32, take split BF16 operands (but the
-  // first adjoint pass of a backward call, with its gradient factors), the
-  // others split TF32.
+  // kernel cannot be resident, the FP32 dense phases.  Its passes take split
+  // BF16 operands, but the first adjoint pass of a backward call (with its
+  // gradient factors) and the passes of FFX_TC_TF32 plans split TF32.
   if (rc == FFX_OK) {
     bool dense = (form == FFX_FORM_DENSE || form == FFX_FORM_TC);
     if (form == FFX_FORM_AUTO) {
@@ -833,9 +832,9 @@ int deal_tc_phase(ManyPlan* mp, int kind, const std::vector<TcPassArg>& args, st
 
 // Tensor-core phases of one mode: the same chains of steps as the dense
 // phases, cut into items of 128 lines x 128 real rows.  Each step is one
-// launch of the BF16 kernel over the passes it takes (BF16 plans, lines of 64
-// to 256 points, a multiple of 32, no gradient factors) and one launch of the
-// split-TF32 kernel over the others; the two touch different instances.
+// launch of the BF16 kernel over the passes it takes (BF16 plans, no gradient
+// factors) and one launch of the split-TF32 kernel over the others, where a
+// step has both kinds.
 int build_tc_phases(ManyPlan* mp, int mode, std::string* err) {
   std::vector<Phase>& phases = mp->phases[mode];
   const int D = mp->max_dim;

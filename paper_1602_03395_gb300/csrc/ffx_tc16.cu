@@ -674,17 +674,19 @@ __global__ void __launch_bounds__(BTHREADS, 1)
 // Pre-split BF16 T chunks from the complex map T [N][N]: for row block mt and
 // K chunk kc, a 32 KB block [head: 128 rows x 64 K][tail] in core-matrix
 // order; real (r, k') with r = 2n + p_out, k' = 2k + p_in holds the 2 x 2
-// block entry of T[n][k]; rows past 2N are zero.
+// block entry of T[n][k]; rows and K columns past 2N are zero (a last K
+// chunk of 2N = 32 mod 64 is half zeros).
 __global__ void bf16_build_t_kernel(const float2* __restrict__ T, unsigned char* __restrict__ Tblk, int N) {
   const int R = 2 * N;
   const int RP = (R + BR - 1) / BR * BR;
-  const int kchunks = R / BKC;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)RP * R;
+  const int kchunks = (R + BKC - 1) / BKC;
+  const int KP = kchunks * BKC;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)RP * KP;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(idx / R), kp = (int)(idx - (int64_t)r * R);
+    const int r = (int)(idx / KP), kp = (int)(idx - (int64_t)r * KP);
     const int n = r >> 1, po = r & 1, k = kp >> 1, pi = kp & 1;
     float v = 0.f;
-    if (r < R) {
+    if (r < R && kp < R) {
       const float2 t = T[(int64_t)n * N + k];
       v = po == 0 ? (pi == 0 ? t.x : -t.y) : (pi == 0 ? t.y : t.x);
     }
@@ -779,7 +781,6 @@ __device__ __forceinline__ int prod_off(bool contiguous, int t, int i) {
 
 constexpr int BMANY_STAGES = 3;
 constexpr int BMANY_SMEM = BMANY_STAGES * BSTAGE;
-
 __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcParams P) {
   constexpr int BSTAGES = BMANY_STAGES;
   extern __shared__ __align__(1024) unsigned char bsm[];
@@ -824,7 +825,7 @@ __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcPa
     int64_t iw = first, ci = 0;
     int ikc = 0, is = 0;
     BView iv = many_view(P, first);
-    int ikch = (2 * iv.N) / BKC;
+    int ikch = (2 * iv.N + BKC - 1) / BKC;
     long long ilb[2] = {-1, -1};
     bool lines_ok = false;
     int last_u[BSTAGES];
@@ -857,18 +858,36 @@ __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcPa
           if (contiguous) ilb[1] = many_line(iv, iv.ct * BL + prod_line(contiguous, t, 2));
           lines_ok = true;
         }
+        // lines past the pass's end, and K past 2N in the last chunk of a
+        // 2N = 32 mod 64 axis, read nothing and land as zeros (source size 0)
+        if (contiguous) {
+          // lanes t and t ^ 8 hold the rows (line, kp) and (line, kp + 1) of
+          // a row pair, 8 complex points: the even lane copies points 0-1 and
+          // 4-5 (the head rows), the odd lane 2-3 and 6-7 (the tail rows), so
+          // that each copy instruction requests whole 32-byte sectors; a row's
+          // two halves then come from both lanes (a warp barrier before the
+          // conversion)
+          const int e = (t >> 3) & 1;
+          const uint32_t dst = e ? xl : xh;
 #pragma unroll
-        for (int i = 0; i < BITEMS; ++i) {
-          const long long lb = ilb[contiguous ? (i >> 1) : 0];
-          const bool valid = lb >= 0;
-          const int k0 = ikc * (BKC / 2) + 4 * prod_kp(contiguous, t, i);  // first complex point
-          const int64_t addr = valid ? lb + (int64_t)k0 * inner : 0;
-          const uint32_t off = (uint32_t)prod_off(contiguous, t, i);
-          // lines past the pass's end read nothing and land as zeros (source size 0)
-          if (contiguous) {
-            cp_async16(xh + off, iv.in + addr, valid ? 16 : 0);
-            cp_async16(xl + off, iv.in + addr + (valid ? 2 : 0), valid ? 16 : 0);
-          } else {
+          for (int i = 0; i < BITEMS; ++i) {
+            const long long lb = ilb[i >> 1];
+            const int kpe = prod_kp(true, t, i) & ~1;
+            const int k0 = ikc * (BKC / 2) + 4 * kpe;  // first complex point of the row pair
+            const bool valid = lb >= 0 && k0 < iv.N;
+            const int64_t addr = valid ? lb + k0 + 2 * e : 0;
+            const uint32_t off = (uint32_t)(prod_off(true, t, i) - ((t >> 3) & 1) * BCORE);  // the even row
+            cp_async16(dst + off, iv.in + addr, valid ? 16 : 0);
+            cp_async16(dst + off + BCORE, iv.in + addr + (valid ? 4 : 0), valid ? 16 : 0);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < BITEMS; ++i) {
+            const long long lb = ilb[0];
+            const int k0 = ikc * (BKC / 2) + 4 * prod_kp(false, t, i);  // first complex point
+            const bool valid = lb >= 0 && k0 < iv.N;
+            const int64_t addr = valid ? lb + (int64_t)k0 * inner : 0;
+            const uint32_t off = (uint32_t)prod_off(false, t, i);
 #pragma unroll
             for (int j = 0; j < 4; ++j)
               cp_async8((j < 2 ? xh : xl) + off + (uint32_t)((j & 1) * 8), iv.in + addr + (valid ? j * inner : 0),
@@ -883,7 +902,7 @@ __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcPa
           lines_ok = false;
           if (++iw < last) {
             iv = many_view(P, iw);
-            ikch = (2 * iv.N) / BKC;
+            ikch = (2 * iv.N + BKC - 1) / BKC;
           }
         }
       } else {
@@ -907,7 +926,9 @@ __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcPa
       // this thread's points of the chunk have landed (of its groups only the
       // BSTAGES - 2 newer ones may be pending); it alone touches their bytes
       asm volatile("cp.async.wait_group %0;" ::"n"(BSTAGES - 2) : "memory");
-      if (!ok) break;
+      // the warp stops as one (the barrier below needs every lane)
+      if (!__all_sync(0xffffffffu, ok)) break;
+      if (ccontig) __syncwarp();  // the partner lane's halves of this thread's rows
 #pragma unroll
       for (int i = 0; i < BITEMS; ++i) {
         const int off = prod_off(ccontig, t, i);
@@ -923,7 +944,7 @@ __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcPa
       mbar_arrive(smem_u32(&full_bar[s]));
       // the copies of chunk c + BSTAGES - 1, into the stage chunk c - 1 used
       ok = issue() && ok;
-      if (++ckc == (2 * cN) / BKC) {
+      if (++ckc == (2 * cN + BKC - 1) / BKC) {
         ckc = 0;
         if (++cw < last) {
           const DenseArgs& d = P.args[P.items[cw].arg].d;
@@ -946,7 +967,7 @@ __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcPa
         const TcItem item = P.items[w];
         const int N = P.args[item.arg].d.N;
         const int rows = brow_count(N, item.mt);
-        const int kchunks = (2 * N) / BKC;
+        const int kchunks = (2 * N + BKC - 1) / BKC;
         const uint32_t idesc = idesc_bf16(BL, rows);
         const bool whole = rows == BR;
         const int buf = (int)(sub & 1);
@@ -1077,7 +1098,7 @@ cudaError_t launch_bf16_split(const float2* in, uint32_t* planes, int64_t n, int
 
 bool dense_bf16_supported(int N) { return N >= 64 && N <= kDenseMaxN && N % 32 == 0; }
 
-size_t dense_bf16_t_bytes(int N) { return (size_t)((2 * N + BR - 1) / BR) * ((2 * N) / BKC) * BTCHUNK; }
+size_t dense_bf16_t_bytes(int N) { return (size_t)((2 * N + BR - 1) / BR) * ((2 * N + BKC - 1) / BKC) * BTCHUNK; }
 
 namespace {
 
@@ -1117,7 +1138,7 @@ cudaError_t many_bf16_prepare() {
 }
 int many_bf16_lines() { return BL; }
 int many_bf16_row_blocks(int N) { return (2 * N + BR - 1) / BR; }
-bool many_bf16_supported(int N) { return N >= 64 && N <= 256 && N % 32 == 0; }
+bool many_bf16_supported(int N) { return N >= 32 && N <= 256 && N % 16 == 0; }
 
 cudaError_t launch_bf16_build_t(const float2* T, unsigned char* Tblk, int N, cudaStream_t s) {
   bf16_build_t_kernel<<<256, 256, 0, s>>>(T, Tblk, N);

@@ -50,8 +50,8 @@ cudaError_t many_tc_prepare();
 int many_tc_lines();          // lines per item
 int many_tc_row_blocks(int N);
 
-// The BF16 variant (ffx_tc16.cu) for lines of 64 to 256 points, a multiple
-// of 32: the same work lists and parameters, with split BF16 operand blocks
+// The BF16 variant (ffx_tc16.cu) for lines of 32 to 256 points, a multiple
+// of 16: the same work lists and parameters, with split BF16 operand blocks
 // of T (launch_bf16_build_t layout) in TcPassArg::tblk.  No gradient passes.
 const void* many_bf16_func();
 int many_bf16_threads();

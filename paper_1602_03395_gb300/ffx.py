@@ -332,8 +332,8 @@ class PlanMany(Plan):
     (dims, spacing, t, magnification, a, abar).  Inputs and outputs are packed
     1-D tensors of ``points`` elements; instance i starts at ``offsets[i]``.
     ``tf32=True`` keeps split TF32 operands on every tensor-core phase
-    (FFX_TC_TF32); by default the passes over lines of 64 to 256 points, a
-    multiple of 32, take split BF16 operands."""
+    (FFX_TC_TF32); by default they take split BF16 operands (but the first
+    adjoint pass of a backward call)."""
 
     def __init__(self, instances, form: str = "auto", tf32: bool = False):
         lib = load_library()
