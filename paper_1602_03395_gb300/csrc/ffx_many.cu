@@ -41,6 +41,8 @@ enum ManyBase : int { BASE_NONE = -1, BASE_PSI0 = 0, BASE_WS = 1, BASE_OUTC = 2,
 constexpr int KIND_DENSE = 100;  // a dense phase (forward or adjoint: the item's matrix decides)
 constexpr int KIND_TC = 101;     // the same on the tensor cores (split TF32)
 constexpr int KIND_TC16 = 102;   // the same with split BF16 operands
+constexpr int KIND_TC16T = 103;  // the same, every input by TMA tiles (a tile map per pass)
+bool tc_kind(int kind) { return kind == KIND_TC || kind == KIND_TC16 || kind == KIND_TC16T; }
 struct ManyCall {
   const void* base[NBASE];
 };
@@ -195,6 +197,7 @@ struct Phase {
   TcItem* d_titems = nullptr;
   long long* d_first = nullptr;   // per block: first item of its run (grid_tc + 1 entries)
   long long n_titems = 0;
+  const void* d_xmaps = nullptr;  // BF16 phases: tile maps of inputs in the plan's workspaces
 };
 
 }  // namespace
@@ -365,8 +368,13 @@ int build_dense_maps(ManyPlan* mp, bool tc, bool bf16, cudaStream_t s, std::stri
     per = 0;
     e = many_bf16_prepare();
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, many_bf16_func(), many_bf16_threads(),
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, many_bf16_func(false), many_bf16_threads(),
                                                         many_bf16_smem());
+    int per_tma = 0;
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_tma, many_bf16_func(true), many_bf16_threads(),
+                                                        many_bf16_smem());
+    if (per_tma < per) per = per_tma;
     if (e != cudaSuccess || per < 1) {
       cudaGetLastError();
       bf16 = false;  // split TF32 throughout
@@ -759,10 +767,38 @@ int build_dense_phases(ManyPlan* mp, int mode, std::string* err) {
 // after the first.  Groups are dealt to blocks biggest first, each to the least
 // loaded block (cost: K chunks x rows), and every block runs its groups in the
 // order dealt.
-int deal_tc_phase(ManyPlan* mp, int kind, const std::vector<TcPassArg>& args, std::vector<Phase>& phases,
+int deal_tc_phase(ManyPlan* mp, int kind, std::vector<TcPassArg> args, std::vector<Phase>& phases,
                   std::string* err) {
   if (args.empty()) return FFX_OK;
   const bool bf = (kind == KIND_TC16);
+  // BF16 phases: a tile map of every input of contiguous lines in the plan's
+  // workspaces (the kernel loads those as TMA tiles; the others, the caller's
+  // input and strided lines, by per-thread copies)
+  // by TMA when every pass of the launch has one (one input mode per launch)
+  std::vector<unsigned char> maps;
+  bool all_maps = bf;
+  for (TcPassArg& pa : args) {
+    pa.xmap = -1;
+    if (!all_maps || pa.d.inner != 1 || (pa.in_base != BASE_WS && pa.in_base != BASE_WS2)) {
+      all_maps = false;
+      continue;
+    }
+    const float2* ws = pa.in_base == BASE_WS ? mp->ws : mp->ws2;
+    const float2* base = (const float2*)((const char*)ws + (uintptr_t)pa.d.in);
+    unsigned char m[128];
+    if (!many_bf16_line_map(base, (int)pa.d.N, pa.d.ncols, m)) {
+      all_maps = false;
+      continue;
+    }
+    pa.xmap = (int)(maps.size() / 128);
+    maps.insert(maps.end(), m, m + 128);
+  }
+  if (!all_maps) {
+    maps.clear();
+    for (TcPassArg& pa : args) pa.xmap = -1;
+  } else {
+    kind = KIND_TC16T;
+  }
   const int64_t LN = bf ? many_bf16_lines() : many_tc_lines();
   Phase ph;
   ph.kind = kind;
@@ -805,7 +841,8 @@ int deal_tc_phase(ManyPlan* mp, int kind, const std::vector<TcPassArg>& args, st
   first[nb] = (long long)flat.size();
   const size_t abytes = (args.size() * sizeof(TcPassArg) + 255) & ~size_t(255);
   const size_t fbytes = ((size_t)(nb + 1) * sizeof(long long) + 255) & ~size_t(255);
-  const size_t bytes = abytes + fbytes + flat.size() * sizeof(TcItem);
+  const size_t ibytes = (flat.size() * sizeof(TcItem) + 255) & ~size_t(255);
+  const size_t bytes = abytes + fbytes + ibytes + maps.size();
   void* m = nullptr;
   cudaError_t e = cudaMalloc(&m, bytes);
   if (e != cudaSuccess) {
@@ -817,10 +854,13 @@ int deal_tc_phase(ManyPlan* mp, int kind, const std::vector<TcPassArg>& args, st
   ph.d_first = (long long*)((char*)m + abytes);
   ph.d_titems = (TcItem*)((char*)m + abytes + fbytes);
   ph.n_titems = (long long)flat.size();
+  ph.d_xmaps = maps.empty() ? nullptr : (const void*)((char*)m + abytes + fbytes + ibytes);
   e = cudaMemcpy(ph.d_targs, args.data(), args.size() * sizeof(TcPassArg), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(ph.d_first, first.data(), first.size() * sizeof(long long), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ph.d_titems, flat.data(), flat.size() * sizeof(TcItem), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !maps.empty())
+    e = cudaMemcpy((void*)ph.d_xmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     cudaFree(m);
     *err = std::string("work list upload: ") + cudaGetErrorString(e);
@@ -974,7 +1014,8 @@ int build_phases(ManyPlan* mp, int mode, std::string* err) {
 const void* phase_func(int kind) {
   switch (kind) {
     case KIND_TC: return many_tc_func();
-    case KIND_TC16: return many_bf16_func();
+    case KIND_TC16: return many_bf16_func(false);
+    case KIND_TC16T: return many_bf16_func(true);
     case KIND_FWD_PAPER: return (const void*)many_kernel<KIND_FWD_PAPER>;
     case KIND_FWD_FOLD: return (const void*)many_kernel<KIND_FWD_FOLD>;
     case KIND_DENSE: return (const void*)many_dense_kernel;
@@ -992,6 +1033,7 @@ TcParams tc_params(const ManyPlan* mp, const Phase& ph, const ManyCall& call) {
   tp.block_first = ph.d_first;
   tp.n_items = ph.n_titems;
   tp.err = mp->dev_err;
+  tp.xmaps = ph.d_xmaps;
   for (int b = 0; b < NBASE; ++b) tp.call.base[b] = call.base[b];
   return tp;
 }
@@ -1000,8 +1042,8 @@ TcParams tc_params(const ManyPlan* mp, const Phase& ph, const ManyCall& call) {
 void phase_node_params(const ManyPlan* mp, const Phase& ph, void** params, cudaKernelNodeParams* kp) {
   std::memset(kp, 0, sizeof(*kp));
   kp->func = (void*)phase_func(ph.kind);
-  if (ph.kind == KIND_TC || ph.kind == KIND_TC16) {
-    const bool bf = ph.kind == KIND_TC16;
+  if (tc_kind(ph.kind)) {
+    const bool bf = ph.kind != KIND_TC;
     kp->gridDim = dim3(mp->grid_tc);
     kp->blockDim = dim3(bf ? many_bf16_threads() : many_tc_threads());
     kp->sharedMemBytes = (unsigned)(bf ? many_bf16_smem() : many_tc_smem());
@@ -1053,7 +1095,7 @@ int build_graph(ManyPlan* mp, int mode, const ManyCall& call, std::string* err) 
     TcParams tp = tc_params(mp, ph, call);
     void* tparams[] = {(void*)&tp};
     cudaKernelNodeParams kp;
-    phase_node_params(mp, ph, (ph.kind == KIND_TC || ph.kind == KIND_TC16) ? tparams : params, &kp);
+    phase_node_params(mp, ph, tc_kind(ph.kind) ? tparams : params, &kp);
     e = cudaGraphAddKernelNode(&knode, g, &mnode, 1, &kp);
     if (e != cudaSuccess) break;
     kn.push_back(knode);
@@ -1086,7 +1128,7 @@ int launch_mode(ManyPlan* mp, int mode, const ManyCall& call, cudaStream_t s, st
       TcParams tp = tc_params(mp, ph, call);
       void* tparams[] = {(void*)&tp};
       cudaKernelNodeParams kp;
-      phase_node_params(mp, ph, (ph.kind == KIND_TC || ph.kind == KIND_TC16) ? tparams : params, &kp);
+      phase_node_params(mp, ph, tc_kind(ph.kind) ? tparams : params, &kp);
       cudaError_t e = cudaGraphExecKernelNodeSetParams(mp->exec[mode], mp->knodes[mode][k], &kp);
       if (e != cudaSuccess) {
         *err = std::string("graph update: ") + cudaGetErrorString(e);
@@ -1111,7 +1153,7 @@ void many_destroy(ManyPlan* mp) {
     if (mp->exec[m]) cudaGraphExecDestroy(mp->exec[m]);
     if (mp->graph[m]) cudaGraphDestroy(mp->graph[m]);
     for (Phase& ph : mp->phases[m])
-      cudaFree((ph.kind == KIND_TC || ph.kind == KIND_TC16) ? (void*)ph.d_targs
+      cudaFree(tc_kind(ph.kind) ? (void*)ph.d_targs
                : ph.kind == KIND_DENSE                      ? (void*)ph.d_dargs
                                                             : (void*)ph.d_args);
   }

@@ -397,10 +397,16 @@ __global__ void __launch_bounds__(BTHREADS, 1)
               cp_async16(xh + off, a.in + addr, valid ? 16 : 0);
               cp_async16(xl + off, a.in + addr + (valid ? 2 : 0), valid ? 16 : 0);
             } else {
+              // point k0 + j of the line into half j % 2 of the head (j < 2) or
+              // tail row; lanes 8-15 and 24-31 take the points in the order
+              // 1, 0, 3, 2 so that each copy instruction's 8-byte pieces fall
+              // on every bank twice (two wavefronts) instead of four times
 #pragma unroll
-              for (int j = 0; j < 4; ++j)
+              for (int j0 = 0; j0 < 4; ++j0) {
+                const int j = j0 ^ ((t >> 3) & 1);
                 cp_async8((j < 2 ? xh : xl) + off + (uint32_t)((j & 1) * 8), a.in + addr + (valid ? j * inner : 0),
                           valid ? 8 : 0);
+              }
             }
             if (GRAD) {
               const int64_t gaddr = valid && a.grad_shared ? addr - (int64_t)ibr[li] * a.M : addr;
@@ -722,11 +728,13 @@ __global__ void __launch_bounds__(256) bf16_split_kernel(const float4* __restric
 // phase, items of 128 lines x 128 real rows of the passes of many instances,
 // each pass with its own N, line geometry, buffers and T blocks; block b takes
 // items [block_first[b], block_first[b + 1]).  The roles, stages, barriers and
-// bounded waits are those of dense_bf16_kernel with the FP32 input copied in
-// place by the producers (a tensor map per launch would not cover the
-// instances' buffers); three stages, split operands, no batch sum and no
-// gradient factors.  Row blocks of 128 rows take X_hi [T_hi; T_lo] as one
-// N = 256 product, the last (shorter) row block of an axis two products.
+// bounded waits are those of dense_bf16_kernel; three stages, split operands,
+// no batch sum and no gradient factors.  The FP32 input of an item reaches the
+// stage as a TMA tile where its pass has a tile map (contiguous lines in the
+// plan's own workspaces, maps made at plan time), else by per-thread copies in
+// place (the caller's input, strided lines).  Row blocks of 128 rows take
+// X_hi [T_hi; T_lo] as one N = 256 product, the last (shorter) row block of an
+// axis two products.
 
 // What a role needs of one work item.
 struct BView {
@@ -734,6 +742,7 @@ struct BView {
   float2* out_c;
   float* out_d;
   const unsigned char* tblk;
+  const void* xmap;  // the input's tile map, or NULL
   int64_t inner, ncols, ct;
   int N, mt;
 };
@@ -750,6 +759,7 @@ __device__ __forceinline__ BView many_view(const TcParams& P, int64_t w) {
   v.out_c = (float2*)many_rebase(P.call, pa.outc_base, pa.d.out_c);
   v.out_d = (float*)many_rebase(P.call, pa.outd_base, pa.d.out_d);
   v.tblk = pa.tblk;
+  v.xmap = pa.xmap >= 0 ? (const void*)((const unsigned char*)P.xmaps + (size_t)pa.xmap * 128) : nullptr;
   v.inner = pa.d.inner;
   v.ncols = pa.d.ncols;
   v.N = pa.d.N;
@@ -780,10 +790,19 @@ __device__ __forceinline__ int prod_off(bool contiguous, int t, int i) {
 }
 
 constexpr int BMANY_STAGES = 3;
-constexpr int BMANY_SMEM = BMANY_STAGES * BSTAGE;
+// the stages, and 1 KB to start them on a 1024-byte boundary (the swizzled
+// tiles' atoms)
+constexpr int BMANY_SMEM = BMANY_STAGES * BSTAGE + 1024;
+// TMA: every pass of the launch has a tile map (the inputs by TMA tiles,
+// thread 0 polling and a producer barrier passing the outcome on); else every
+// input by per-thread copies, each producer polling for itself and the warps
+// moving on independently.  One mode per launch: a barrier of the producers
+// that some warps skip would never open.
+template <bool TMA>
 __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcParams P) {
   constexpr int BSTAGES = BMANY_STAGES;
-  extern __shared__ __align__(1024) unsigned char bsm[];
+  extern __shared__ __align__(1024) unsigned char bsm_raw[];
+  unsigned char* const bsm = bsm_raw + ((1024u - (smem_u32(bsm_raw) & 1023u)) & 1023u);
   __shared__ __align__(8) uint64_t full_bar[BSTAGES], empty_bar[BSTAGES], copy_bar[BSTAGES];
   __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], done_bar;
   __shared__ uint32_t tmem_slot;
@@ -820,8 +839,10 @@ __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcPa
     const int t = tid;
     // Issue side: chunk j of the block's run into stage j % BSTAGES once the
     // products of chunk j - BSTAGES have freed it; thread 0 copies the T chunk
-    // on the stage's "copy" barrier, every thread its points of the input.
-    // The chunk's position (item iw, K chunk ikc) advances incrementally.
+    // (and, where the pass has a tile map, the input tile: two 128 x 32-float
+    // boxes, 128-byte swizzle) on the stage's "copy" barrier, else every
+    // thread its points of the input.  The chunk's position (item iw, K chunk
+    // ikc) advances incrementally.
     int64_t iw = first, ci = 0;
     int ikc = 0, is = 0;
     BView iv = many_view(P, first);
@@ -837,10 +858,11 @@ __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcPa
         if (u >= 1 && !mbar_wait(smem_u32(&empty_bar[is]), (uint32_t)((u - 1) & 1), &s_abort)) return false;
         unsigned char* st = bsm + is * BSTAGE;
         const uint32_t xh = smem_u32(st + BTCHUNK), xl = xh + BPART;
+        const bool tma = TMA;
         if (t == 0) {
           const uint32_t part = (uint32_t)brow_count(iv.N, iv.mt) * (BKC * 2);
           const uint32_t cb = smem_u32(&copy_bar[is]);
-          mbar_expect_tx(cb, 2 * part);
+          mbar_expect_tx(cb, 2 * part + (tma ? (uint32_t)BXAREA : 0u));
           const unsigned char* src = iv.tblk + ((size_t)iv.mt * ikch + ikc) * BTCHUNK;
           const uint32_t dst = smem_u32(st);
           if (part == (uint32_t)BPART) {
@@ -849,18 +871,34 @@ __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcPa
             bulk_g2s(dst, src, part, cb);
             bulk_g2s(dst + BPART, src + BPART, part, cb);
           }
+          if (tma) {
+            // rows: the tile's lines (past the pass's end: zeros); x: the
+            // chunk's 64 real K (past 2N: zeros) in two 32-float boxes
+            const uint64_t map_addr = reinterpret_cast<uint64_t>(iv.xmap);
+            const int row = (int)(iv.ct * BL);
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+              asm volatile(
+                  "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+                  "%3}], [%4];" ::"r"(xh + (uint32_t)(h * BPART)),
+                  "l"(map_addr), "r"(ikc * BKC + 32 * h), "r"(row), "r"(cb)
+                  : "memory");
+          }
           last_u[is] = (int)(u & 1);
         }
         const int64_t inner = iv.inner;
         const bool contiguous = (inner == 1);
-        if (!lines_ok) {
+        if (tma) {
+          // nothing for the other threads to copy (an empty group keeps the count)
+        } else if (!lines_ok) {
           ilb[0] = many_line(iv, iv.ct * BL + prod_line(contiguous, t, 0));
           if (contiguous) ilb[1] = many_line(iv, iv.ct * BL + prod_line(contiguous, t, 2));
           lines_ok = true;
         }
         // lines past the pass's end, and K past 2N in the last chunk of a
         // 2N = 32 mod 64 axis, read nothing and land as zeros (source size 0)
-        if (contiguous) {
+        if (tma) {
+        } else if (contiguous) {
           // lanes t and t ^ 8 hold the rows (line, kp) and (line, kp + 1) of
           // a row pair, 8 complex points: the even lane copies points 0-1 and
           // 4-5 (the head rows), the odd lane 2-3 and 6-7 (the tail rows), so
@@ -888,10 +926,14 @@ __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcPa
             const bool valid = lb >= 0 && k0 < iv.N;
             const int64_t addr = valid ? lb + (int64_t)k0 * inner : 0;
             const uint32_t off = (uint32_t)prod_off(false, t, i);
+            // the point order of dense_bf16_kernel's strided copies (two
+            // wavefronts per instruction)
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
+            for (int j0 = 0; j0 < 4; ++j0) {
+              const int j = j0 ^ ((t >> 3) & 1);
               cp_async8((j < 2 ? xh : xl) + off + (uint32_t)((j & 1) * 8), iv.in + addr + (valid ? j * inner : 0),
                         valid ? 8 : 0);
+            }
           }
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
@@ -901,8 +943,12 @@ __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcPa
           ikc = 0;
           lines_ok = false;
           if (++iw < last) {
+            const void* prev = iv.xmap;
             iv = many_view(P, iw);
             ikch = (2 * iv.N + BKC - 1) / BKC;
+            // a map written before the launch, read by the tensor copies
+            if (TMA && t == 0 && iv.xmap != prev)
+              asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(iv.xmap) : "memory");
           }
         }
       } else {
@@ -910,6 +956,7 @@ __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcPa
       }
       return true;
     };
+    if (TMA && t == 0) asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(iv.xmap) : "memory");
     bool ok = true;
 #pragma unroll 1
     for (int r = 0; r < BSTAGES - 1; ++r) ok = issue() && ok;
@@ -923,20 +970,46 @@ __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcPa
     for (int64_t c = 0; cw < last; ++c) {
       const int s = (int)(c % BSTAGES);
       unsigned char* xa = bsm + s * BSTAGE + BTCHUNK;
-      // this thread's points of the chunk have landed (of its groups only the
-      // BSTAGES - 2 newer ones may be pending); it alone touches their bytes
-      asm volatile("cp.async.wait_group %0;" ::"n"(BSTAGES - 2) : "memory");
-      // the warp stops as one (the barrier below needs every lane)
-      if (!__all_sync(0xffffffffu, ok)) break;
-      if (ccontig) __syncwarp();  // the partner lane's halves of this thread's rows
+      if (TMA) {
+        // the tile has landed: thread 0 polls the copy barrier, the barrier
+        // passes the outcome and the data on
+        if (t == 0) ok = ok && mbar_wait(smem_u32(&copy_bar[s]), (uint32_t)((c / BSTAGES) & 1), &s_abort);
+        if (!prod_all(ok)) break;
+      } else {
+        // this thread's points of the chunk have landed (of its groups only
+        // the BSTAGES - 2 newer ones may be pending); the warp stops as one
+        // and sees the partner lane's halves of this thread's rows
+        asm volatile("cp.async.wait_group %0;" ::"n"(BSTAGES - 2) : "memory");
+        if (!__all_sync(0xffffffffu, ok)) break;
+        if (ccontig) __syncwarp();
+      }
+      float v[BITEMS][8];
+#pragma unroll
+      for (int i = 0; i < BITEMS; ++i) {
+        if (TMA) {
+          // box kp / 4, row n, 16-byte chunks 2 (kp % 4) and + 1, swizzled by n % 8
+          const int n = prod_line(true, t, i), kp = prod_kp(true, t, i);
+          const unsigned char* row = xa + (kp >> 2) * BPART + n * 128;
+          const int c0 = 2 * (kp & 3);
+          const float4 r0 = *reinterpret_cast<const float4*>(row + ((c0 ^ (n & 7)) << 4));
+          const float4 r1 = *reinterpret_cast<const float4*>(row + (((c0 + 1) ^ (n & 7)) << 4));
+          v[i][0] = r0.x, v[i][1] = r0.y, v[i][2] = r0.z, v[i][3] = r0.w;
+          v[i][4] = r1.x, v[i][5] = r1.y, v[i][6] = r1.z, v[i][7] = r1.w;
+        } else {
+          const int off = prod_off(ccontig, t, i);
+          const float4 r0 = *reinterpret_cast<const float4*>(xa + off);
+          const float4 r1 = *reinterpret_cast<const float4*>(xa + BPART + off);
+          v[i][0] = r0.x, v[i][1] = r0.y, v[i][2] = r0.z, v[i][3] = r0.w;
+          v[i][4] = r1.x, v[i][5] = r1.y, v[i][6] = r1.z, v[i][7] = r1.w;
+        }
+      }
+      // every producer has read its input before any overwrites the tile with BF16 rows
+      if (TMA) prod_sync();
 #pragma unroll
       for (int i = 0; i < BITEMS; ++i) {
         const int off = prod_off(ccontig, t, i);
-        const float4 r0 = *reinterpret_cast<const float4*>(xa + off);
-        const float4 r1 = *reinterpret_cast<const float4*>(xa + BPART + off);
-        const float v[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
         uint4 hi, lo;
-        split8(v, hi, lo, false);
+        split8(v[i], hi, lo, false);
         *reinterpret_cast<uint4*>(xa + off) = hi;
         *reinterpret_cast<uint4*>(xa + BPART + off) = lo;
       }
@@ -947,9 +1020,9 @@ __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcPa
       if (++ckc == (2 * cN + BKC - 1) / BKC) {
         ckc = 0;
         if (++cw < last) {
-          const DenseArgs& d = P.args[P.items[cw].arg].d;
-          cN = d.N;
-          ccontig = d.inner == 1;
+          const TcPassArg& pa = P.args[P.items[cw].arg];
+          cN = pa.d.N;
+          ccontig = pa.d.inner == 1;
         }
       }
     }
@@ -1129,12 +1202,18 @@ cudaError_t dense_bf16_prepare() {
   return e;
 }
 
-const void* many_bf16_func() { return (const void*)dense_bf16_many_kernel; }
+const void* many_bf16_func(bool tma) {
+  return tma ? (const void*)dense_bf16_many_kernel<true> : (const void*)dense_bf16_many_kernel<false>;
+}
 int many_bf16_threads() { return BTHREADS; }
 size_t many_bf16_smem() { return (size_t)BMANY_SMEM; }
 cudaError_t many_bf16_prepare() {
-  return cudaFuncSetAttribute((const void*)dense_bf16_many_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              BMANY_SMEM);
+  cudaError_t e = cudaFuncSetAttribute((const void*)dense_bf16_many_kernel<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, BMANY_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)dense_bf16_many_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             BMANY_SMEM);
+  return e;
 }
 int many_bf16_lines() { return BL; }
 int many_bf16_row_blocks(int N) { return (2 * N + BR - 1) / BR; }
@@ -1208,6 +1287,25 @@ bool input_map(const DenseArgs& a, CUtensorMap* map, int* mode) {
 }  // namespace
 
 bool dense_bf16_chain_supported() { return encode_tiled() != nullptr; }
+
+bool many_bf16_line_map(const float2* base, int N, int64_t lines, void* map) {
+  // [lines][2N floats], boxes of 32 floats x 128 lines, 128-byte swizzle: the
+  // map of the uniform kernel's TMA tiles of contiguous lines
+  std::memset(map, 0, sizeof(CUtensorMap));
+  const EncodeTiledFn enc = encode_tiled();
+  if (!enc || lines < 1 || (reinterpret_cast<uintptr_t>(base) & 15u)) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)(2 * N), (cuuint64_t)lines};
+  const cuuint64_t strides[1] = {(cuuint64_t)(2 * N) * 4};
+  const cuuint32_t box[2] = {32, (cuuint32_t)BL}, estr[2] = {1, 1};
+  if (enc(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+    std::memset(map, 0, sizeof(CUtensorMap));
+    return false;
+  }
+  return true;
+}
+static_assert(sizeof(CUtensorMap) == 128, "tile maps are 128 bytes");
 
 cudaError_t launch_dense_bf16(const DenseArgs& args, const unsigned char* Tblk, int* err, int grid, cudaStream_t s) {
   DenseArgs a = args;

@@ -14,6 +14,7 @@ struct TcPassArg {
   DenseArgs d;
   const unsigned char* tblk;
   int in_base, outc_base, outd_base, grad_base;
+  int xmap;  // BF16 phases: index of the input's tile map in TcParams::xmaps, or -1
 };
 
 // One work item: line tile ct (128 lines) and row block mt of pass `arg`.
@@ -41,6 +42,9 @@ struct TcParams {
   long long n_items;
   TcBases call;
   int* err;
+  // BF16 phases: tile maps (128-byte CUtensorMap objects) of contiguous lines
+  // in the plan's own workspaces, indexed by TcPassArg::xmap
+  const void* xmaps;
 };
 
 const void* many_tc_func();   // kernel(const TcParams), many-instance variant
@@ -53,12 +57,16 @@ int many_tc_row_blocks(int N);
 // The BF16 variant (ffx_tc16.cu) for lines of 32 to 256 points, a multiple
 // of 16: the same work lists and parameters, with split BF16 operand blocks
 // of T (launch_bf16_build_t layout) in TcPassArg::tblk.  No gradient passes.
-const void* many_bf16_func();
+const void* many_bf16_func(bool tma);  // tma: every pass of the launch has a tile map
 int many_bf16_threads();
 size_t many_bf16_smem();
 cudaError_t many_bf16_prepare();
 int many_bf16_lines();
 int many_bf16_row_blocks(int N);
 bool many_bf16_supported(int N);
+// Encode the tile map of `lines` contiguous lines of N complex points at
+// `base` (16-byte aligned) into map[128] (64-byte aligned); false if the
+// driver cannot.
+bool many_bf16_line_map(const float2* base, int N, int64_t lines, void* map);
 
 }  // namespace ffx
