@@ -533,7 +533,7 @@ def run_mixed(args, torch, dist, world, rank, dev):
         tf_peak, tf_src = tensor_peak(pk, pk_src, ms)
         bf_peak, bf_src = tensor_peak(pk, pk_src, ms, "bf16")
         tc_peak = flops / (flops_bf / bf_peak + (flops - flops_bf) / tf_peak)
-        kern = ("dense_bf16_many_kernel + dense_tc_kernel<false, true, false>" if plan.bf16
+        kern = ("dense_bf16_many_kernel<false> (per-thread copies) and <true> (TMA tiles)" if plan.bf16
                 else "dense_tc_kernel<false, true, false>")
         roofline = {"bound": "tensor", "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
                     "frac": achieved / tc_peak,

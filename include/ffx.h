@@ -204,8 +204,13 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
  * SM: on split BF16 operands (kind::f16 products, density error of order
  * 1e-6), except with FFX_TC_TF32 and in the first adjoint pass of
  * ffx_expand_backward (its gradient factors), which take split TF32 operands
- * (one more launch in that phase).  A plan with a 16-point axis keeps the
- * FP32 phases (ffx_plan_form reports which).  Dense passes are not in place for
+ * (one more launch in that phase).  Forward calls on BF16 operands run as a
+ * chain: each instance's passes from its last axis to its first, the
+ * intermediate results kept as BF16 head and tail planes in the workspaces.
+ * Every call of a plan on the tensor cores takes 16-byte aligned buffers
+ * (FFX_EINVAL otherwise).  A plan
+ * with a 16-point axis keeps the FP32 phases (ffx_plan_form reports which).
+ * Dense passes are not in place for
  * lines over 64 points, so an in-place ffx_expand_field with a 1-D instance
  * longer than 64 points returns FFX_EUNSUPPORTED.  ffx_plan_device_errors
  * counts tensor-core phases that gave up on a bounded wait.

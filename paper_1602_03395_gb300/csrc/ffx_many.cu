@@ -42,7 +42,15 @@ constexpr int KIND_DENSE = 100;  // a dense phase (forward or adjoint: the item'
 constexpr int KIND_TC = 101;     // the same on the tensor cores (split TF32)
 constexpr int KIND_TC16 = 102;   // the same with split BF16 operands
 constexpr int KIND_TC16T = 103;  // the same, every input by TMA tiles (a tile map per pass)
-bool tc_kind(int kind) { return kind == KIND_TC || kind == KIND_TC16 || kind == KIND_TC16T; }
+constexpr int KIND_TC16P = 104;  // a BF16 chain pass: planes in, planes (or the output) out, transposed
+constexpr int KIND_SPLIT = 105;  // a BF16 chain's input split into planes
+constexpr int KIND_TC16P0 = 106;  // a BF16 chain's first pass: the caller's FP32 input in, planes out
+bool tc_kind(int kind) {
+  return kind == KIND_TC || kind == KIND_TC16 || kind == KIND_TC16T || kind == KIND_TC16P || kind == KIND_TC16P0;
+}
+#ifndef FFX_MANY_CHAIN_SPLIT
+#define FFX_MANY_CHAIN_SPLIT 0
+#endif
 struct ManyCall {
   const void* base[NBASE];
 };
@@ -368,13 +376,14 @@ int build_dense_maps(ManyPlan* mp, bool tc, bool bf16, cudaStream_t s, std::stri
     per = 0;
     e = many_bf16_prepare();
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, many_bf16_func(false), many_bf16_threads(),
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, many_bf16_func(0), many_bf16_threads(),
                                                         many_bf16_smem());
-    int per_tma = 0;
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_tma, many_bf16_func(true), many_bf16_threads(),
+    for (int m = 1; m < 3 && e == cudaSuccess; ++m) {
+      int per_m = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_m, many_bf16_func(m), many_bf16_threads(),
                                                         many_bf16_smem());
-    if (per_tma < per) per = per_tma;
+      if (per_m < per) per = per_m;
+    }
     if (e != cudaSuccess || per < 1) {
       cudaGetLastError();
       bf16 = false;  // split TF32 throughout
@@ -768,16 +777,18 @@ int build_dense_phases(ManyPlan* mp, int mode, std::string* err) {
 // loaded block (cost: K chunks x rows), and every block runs its groups in the
 // order dealt.
 int deal_tc_phase(ManyPlan* mp, int kind, std::vector<TcPassArg> args, std::vector<Phase>& phases,
-                  std::string* err) {
+                  std::string* err, const std::vector<unsigned char>* plane_maps = nullptr) {
   if (args.empty()) return FFX_OK;
-  const bool bf = (kind == KIND_TC16);
+  const bool bf = (kind != KIND_TC);
   // BF16 phases: a tile map of every input of contiguous lines in the plan's
   // workspaces (the kernel loads those as TMA tiles; the others, the caller's
   // input and strided lines, by per-thread copies)
   // by TMA when every pass of the launch has one (one input mode per launch)
   std::vector<unsigned char> maps;
-  bool all_maps = bf;
+  bool all_maps = kind == KIND_TC16;
+  if (kind == KIND_TC16P) maps = *plane_maps;  // the chain's pass arguments carry their map indices
   for (TcPassArg& pa : args) {
+    if (kind == KIND_TC16P) break;
     pa.xmap = -1;
     if (!all_maps || pa.d.inner != 1 || (pa.in_base != BASE_WS && pa.in_base != BASE_WS2)) {
       all_maps = false;
@@ -793,7 +804,8 @@ int deal_tc_phase(ManyPlan* mp, int kind, std::vector<TcPassArg> args, std::vect
     pa.xmap = (int)(maps.size() / 128);
     maps.insert(maps.end(), m, m + 128);
   }
-  if (!all_maps) {
+  if (kind == KIND_TC16P) {
+  } else if (!all_maps) {
     maps.clear();
     for (TcPassArg& pa : args) pa.xmap = -1;
   } else {
@@ -932,8 +944,89 @@ int build_tc_phases(ManyPlan* mp, int mode, std::string* err) {
   return FFX_OK;
 }
 
+// BF16 chain phases of a forward mode (0: density, 1: field), as the uniform
+// plans' BF16 chains: the caller's input split into BF16 head and tail planes
+// (the second workspace), then phase r runs every instance's pass along its
+// axis n_i - 1 - r on planes of contiguous lines (TMA tiles), writing its
+// output transposed -- point n of line c at c + n R, R the pass's lines -- as
+// the next pass's planes (the workspaces in turn) or, after the pass along
+// axis 0, the caller's output in the lattice's own order.  Returns
+// FFX_EUNSUPPORTED (nothing built) where a plane map cannot be made.
+int build_chain_phases(ManyPlan* mp, int mode, std::string* err) {
+  std::vector<Phase> phases;
+  const bool split_first = FFX_MANY_CHAIN_SPLIT != 0;
+  if (split_first) {
+    Phase split;
+    split.kind = KIND_SPLIT;
+    phases.push_back(split);
+  }
+  const int D = mp->max_dim;
+  for (int r = 0; r < D; ++r) {
+    std::vector<TcPassArg> args;
+    std::vector<unsigned char> maps;
+    const bool fp32_in = (r == 0 && !split_first);  // the caller's input, by per-thread copies
+    const int in_base = fp32_in ? BASE_PSI0 : (r % 2 == 0) ? BASE_WS2 : BASE_WS;
+    const int ws_out = (r % 2 == 0) ? BASE_WS : BASE_WS2;
+    const uint32_t* in_planes = (const uint32_t*)(in_base == BASE_WS2 ? mp->ws2 : mp->ws);
+    for (const Instance& in : mp->inst) {
+      if (r >= in.ndim) continue;
+      const int axis = in.ndim - 1 - r;
+      const AxisTab& at = mp->tabs[in.axis_tab[axis]];
+      const int64_t R = in.M / at.N;
+      TcPassArg pa;
+      std::memset(&pa, 0, sizeof(pa));
+      pa.in_base = in_base;
+      pa.outc_base = BASE_NONE;
+      pa.outd_base = BASE_NONE;
+      pa.grad_base = BASE_NONE;
+      DenseArgs& a = pa.d;
+      a.in = (const float2*)(uintptr_t)((size_t)in.off * (fp32_in ? sizeof(float2) : sizeof(uint32_t)));
+      if (r == in.ndim - 1) {
+        if (mode == 0) {
+          pa.outd_base = BASE_OUTD;
+          a.out_d = (float*)(uintptr_t)((size_t)in.off * sizeof(float));
+        } else {
+          pa.outc_base = BASE_OUTC;
+          a.out_c = (float2*)(uintptr_t)((size_t)in.off * sizeof(float2));
+        }
+      } else {
+        pa.outc_base = ws_out;
+        pa.out_planes = 1;
+        a.out_bf = (uint32_t*)(uintptr_t)((size_t)in.off * sizeof(uint32_t));
+      }
+      a.bf_plane = mp->total;
+      a.outer = R;
+      a.inner = 1;
+      a.M = in.M;
+      a.batch = 1;
+      a.ncols = R;
+      a.N = at.N;
+      pa.tblk = at.bf[0];
+      pa.xmap = -1;
+      unsigned char m[128];
+      if (!pa.tblk || (!fp32_in && !many_bf16_plane_map(in_planes + in.off, at.N, R, mp->total, m))) {
+        for (Phase& ph : phases) cudaFree(ph.d_targs);
+        return FFX_EUNSUPPORTED;
+      }
+      if (!fp32_in) {
+        pa.xmap = (int)(maps.size() / 128);
+        maps.insert(maps.end(), m, m + 128);
+      }
+      args.push_back(pa);
+    }
+    int rc = deal_tc_phase(mp, fp32_in ? KIND_TC16P0 : KIND_TC16P, args, phases, err, &maps);
+    if (rc) {
+      for (Phase& ph : phases) cudaFree(ph.d_targs);
+      return rc;
+    }
+  }
+  mp->phases[mode] = phases;
+  return FFX_OK;
+}
+
 // Phases of one mode.  mode 0: density, 1: field, 2: backward.
 int build_phases(ManyPlan* mp, int mode, std::string* err) {
+  if (mp->tc && mp->bf16 && mode != 2 && build_chain_phases(mp, mode, err) == FFX_OK) return FFX_OK;
   if (mp->tc) return build_tc_phases(mp, mode, err);
   if (mp->dense) return build_dense_phases(mp, mode, err);
   std::vector<Phase>& phases = mp->phases[mode];
@@ -1014,8 +1107,10 @@ int build_phases(ManyPlan* mp, int mode, std::string* err) {
 const void* phase_func(int kind) {
   switch (kind) {
     case KIND_TC: return many_tc_func();
-    case KIND_TC16: return many_bf16_func(false);
-    case KIND_TC16T: return many_bf16_func(true);
+    case KIND_TC16: return many_bf16_func(0);
+    case KIND_TC16T: return many_bf16_func(1);
+    case KIND_TC16P: return many_bf16_func(2);
+    case KIND_TC16P0: return many_bf16_func(3);
     case KIND_FWD_PAPER: return (const void*)many_kernel<KIND_FWD_PAPER>;
     case KIND_FWD_FOLD: return (const void*)many_kernel<KIND_FWD_FOLD>;
     case KIND_DENSE: return (const void*)many_dense_kernel;
@@ -1061,6 +1156,57 @@ void phase_node_params(const ManyPlan* mp, const Phase& ph, void** params, cudaK
   kp->kernelParams = params;
 }
 
+// A phase kernel node's argument values and their pointers, alive while the
+// node is added or updated.
+struct NodeArgs {
+  int* counter;
+  TcParams tp;
+  const void* s_in;
+  void* s_hi;
+  void* s_lo;
+  long long s_n2;
+  int s_unsplit;
+  void* params[5];
+};
+
+// Node parameters of phase k for a call's buffers.
+void node_args(const ManyPlan* mp, Phase& ph, size_t k, const ManyCall& call, NodeArgs& na,
+               cudaKernelNodeParams* kp) {
+  na.counter = mp->counters + k;
+  if (ph.kind == KIND_SPLIT) {
+    // the chain's input split: the caller's input into BF16 planes in the
+    // second workspace (head plane, then the tail plane `total` pairs on)
+    na.s_in = call.base[BASE_PSI0];
+    na.s_hi = mp->ws2;
+    na.s_lo = (uint32_t*)mp->ws2 + mp->total;
+    na.s_n2 = mp->total / 2;
+    na.s_unsplit = 0;
+    na.params[0] = (void*)&na.s_in;
+    na.params[1] = (void*)&na.s_hi;
+    na.params[2] = (void*)&na.s_lo;
+    na.params[3] = (void*)&na.s_n2;
+    na.params[4] = (void*)&na.s_unsplit;
+    std::memset(kp, 0, sizeof(*kp));
+    kp->func = (void*)bf16_split_func();
+    kp->gridDim = dim3(bf16_split_grid(mp->total, mp->grid_tc));
+    kp->blockDim = dim3(256);
+    kp->sharedMemBytes = 0;
+    kp->kernelParams = na.params;
+    return;
+  }
+  if (tc_kind(ph.kind)) {
+    na.tp = tc_params(mp, ph, call);
+    na.params[0] = (void*)&na.tp;
+  } else {
+    na.params[0] = ph.kind == KIND_DENSE ? (void*)&ph.d_dargs : (void*)&ph.d_args;
+    na.params[1] = (void*)&ph.d_items;
+    na.params[2] = (void*)&ph.n_items;
+    na.params[3] = (void*)&na.counter;
+    na.params[4] = (void*)&call;
+  }
+  phase_node_params(mp, ph, na.params, kp);
+}
+
 // The graph of one mode: memset(counter_k) -> phase kernel k -> memset(counter_k+1) -> ...
 int build_graph(ManyPlan* mp, int mode, const ManyCall& call, std::string* err) {
   if (mp->phases[mode].empty()) {
@@ -1089,13 +1235,9 @@ int build_graph(ManyPlan* mp, int mode, const ManyCall& call, std::string* err) 
     cudaGraphNode_t mnode, knode;
     e = cudaGraphAddMemsetNode(&mnode, g, prev ? &prev : nullptr, prev ? 1 : 0, &ms);
     if (e != cudaSuccess) break;
-    int* counter = mp->counters + k;
-    void* params[] = {ph.kind == KIND_DENSE ? (void*)&ph.d_dargs : (void*)&ph.d_args, (void*)&ph.d_items,
-                      (void*)&ph.n_items, (void*)&counter, (void*)&call};
-    TcParams tp = tc_params(mp, ph, call);
-    void* tparams[] = {(void*)&tp};
+    NodeArgs na;
     cudaKernelNodeParams kp;
-    phase_node_params(mp, ph, tc_kind(ph.kind) ? tparams : params, &kp);
+    node_args(mp, ph, k, call, na, &kp);
     e = cudaGraphAddKernelNode(&knode, g, &mnode, 1, &kp);
     if (e != cudaSuccess) break;
     kn.push_back(knode);
@@ -1122,13 +1264,9 @@ int launch_mode(ManyPlan* mp, int mode, const ManyCall& call, cudaStream_t s, st
     std::vector<Phase>& phases = mp->phases[mode];
     for (size_t k = 0; k < phases.size(); ++k) {
       Phase& ph = phases[k];
-      int* counter = mp->counters + k;
-      void* params[] = {ph.kind == KIND_DENSE ? (void*)&ph.d_dargs : (void*)&ph.d_args, (void*)&ph.d_items,
-                        (void*)&ph.n_items, (void*)&counter, (void*)&call};
-      TcParams tp = tc_params(mp, ph, call);
-      void* tparams[] = {(void*)&tp};
+      NodeArgs na;
       cudaKernelNodeParams kp;
-      phase_node_params(mp, ph, tc_kind(ph.kind) ? tparams : params, &kp);
+      node_args(mp, ph, k, call, na, &kp);
       cudaError_t e = cudaGraphExecKernelNodeSetParams(mp->exec[mode], mp->knodes[mode][k], &kp);
       if (e != cudaSuccess) {
         *err = std::string("graph update: ") + cudaGetErrorString(e);
@@ -1176,7 +1314,15 @@ bool many_bf16(const ManyPlan* mp) {
 int many_max_dim(const ManyPlan* mp) { return mp->max_dim; }
 int* many_device_errors(const ManyPlan* mp) { return mp->dev_err; }
 
+// Tensor-core phases copy and store 16 bytes at a time: 16-byte aligned buffers.
+bool tc_buffers_ok(const ManyPlan* mp, const void* a, const void* b, const void* c, std::string* err) {
+  if (!mp->tc || ((((uintptr_t)a) | ((uintptr_t)b) | ((uintptr_t)c)) & 15) == 0) return true;
+  *err = "the tensor-core phases of a many-instance plan take 16-byte aligned buffers";
+  return false;
+}
+
 int many_expand(ManyPlan* mp, const void* psi0, float* out_d, void* out_c, cudaStream_t s, std::string* err) {
+  if (!tc_buffers_ok(mp, psi0, out_d, out_c, err)) return FFX_EINVAL;
   if (mp->dense && out_c && out_c == psi0) {
     // a one-pass instance reads and writes the caller's buffer in the same
     // (not in-place) dense pass
@@ -1198,6 +1344,7 @@ int many_expand(ManyPlan* mp, const void* psi0, float* out_d, void* out_c, cudaS
 
 int many_backward(ManyPlan* mp, const void* psi0, const float* grad, void* grad_psi0, cudaStream_t s,
                   std::string* err) {
+  if (!tc_buffers_ok(mp, psi0, grad, grad_psi0, err)) return FFX_EINVAL;
   ManyCall c;
   std::memset(&c, 0, sizeof(c));
   c.base[BASE_PSI0] = psi0;

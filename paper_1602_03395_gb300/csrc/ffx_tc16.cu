@@ -743,7 +743,8 @@ struct BView {
   float* out_d;
   const unsigned char* tblk;
   const void* xmap;  // the input's tile map, or NULL
-  int64_t inner, ncols, ct;
+  uint32_t* out_bf;  // BF16 planes out (chains), or NULL
+  int64_t inner, ncols, ct, bf_plane;
   int N, mt;
 };
 
@@ -760,6 +761,9 @@ __device__ __forceinline__ BView many_view(const TcParams& P, int64_t w) {
   v.out_d = (float*)many_rebase(P.call, pa.outd_base, pa.d.out_d);
   v.tblk = pa.tblk;
   v.xmap = pa.xmap >= 0 ? (const void*)((const unsigned char*)P.xmaps + (size_t)pa.xmap * 128) : nullptr;
+  v.out_bf = pa.out_planes ? (uint32_t*)many_rebase(P.call, pa.outc_base, pa.d.out_bf) : nullptr;
+  if (pa.out_planes) v.out_c = nullptr;
+  v.bf_plane = pa.d.bf_plane;
   v.inner = pa.d.inner;
   v.ncols = pa.d.ncols;
   v.N = pa.d.N;
@@ -793,14 +797,25 @@ constexpr int BMANY_STAGES = 3;
 // the stages, and 1 KB to start them on a 1024-byte boundary (the swizzled
 // tiles' atoms)
 constexpr int BMANY_SMEM = BMANY_STAGES * BSTAGE + 1024;
-// TMA: every pass of the launch has a tile map (the inputs by TMA tiles,
-// thread 0 polling and a producer barrier passing the outcome on); else every
-// input by per-thread copies, each producer polling for itself and the warps
-// moving on independently.  One mode per launch: a barrier of the producers
-// that some warps skip would never open.
-template <bool TMA>
+// XM, the input mode of every pass of the launch (one mode per launch: a
+// barrier of the producers that some warps skip would never open):
+//  * kInPlace: FP32 input by per-thread copies, each producer polling for
+//    itself and the warps moving on independently;
+//  * kTmaContiguous: FP32 contiguous lines by TMA tiles (a tile map per
+//    pass), thread 0 polling and a producer barrier passing the outcome on;
+//  * kTmaPlanes (BF16 chains): BF16 head and tail planes of contiguous lines
+//    by one 3-D TMA tile per chunk straight into the tensor cores' swizzled
+//    K-major layout (thread 0 alone; no conversion), output transposed
+//    (point n of line c at c + n lines) as the next pass's planes or, after
+//    the last pass, in the lattice's own order.
+// TOUT: the output transposed so, also for FP32 input (a chain's first pass
+// reading the caller's input).
+template <int XM, bool TOUT>
 __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcParams P) {
   constexpr int BSTAGES = BMANY_STAGES;
+  constexpr bool TMA = XM == kTmaContiguous;
+  constexpr bool PLANES = XM == kTmaPlanes;
+  static_assert(TOUT || !PLANES, "plane input comes with transposed output");
   extern __shared__ __align__(1024) unsigned char bsm_raw[];
   unsigned char* const bsm = bsm_raw + ((1024u - (smem_u32(bsm_raw) & 1023u)) & 1023u);
   __shared__ __align__(8) uint64_t full_bar[BSTAGES], empty_bar[BSTAGES], copy_bar[BSTAGES];
@@ -834,7 +849,59 @@ __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcPa
   const uint32_t tmem = tmem_slot;
   const uint32_t smem_base = smem_u32(bsm);
 
-  if (warp < BMMA_WARP) {
+  if (PLANES && warp < BMMA_WARP) {
+    // ---------------- loads of BF16 planes: thread 0 alone ----------------
+    if (tid == 0) {
+      int64_t iw = first, ci = 0;
+      int ikc = 0, is = 0;
+      BView iv = many_view(P, first);
+      int ikch = (2 * iv.N + BKC - 1) / BKC;
+      int last_u[BSTAGES];
+#pragma unroll
+      for (int q = 0; q < BSTAGES; ++q) last_u[q] = -1;
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(iv.xmap) : "memory");
+#pragma unroll 1
+      while (iw < last) {
+        // chunk ci into stage is once the products of chunk ci - BSTAGES freed it
+        const int64_t u = ci / BSTAGES;
+        if (u >= 1 && !mbar_wait(smem_u32(&empty_bar[is]), (uint32_t)((u - 1) & 1), &s_abort)) break;
+        const uint32_t st = smem_u32(bsm + is * BSTAGE);
+        const uint32_t part = (uint32_t)brow_count(iv.N, iv.mt) * (BKC * 2);
+        const uint32_t cb = smem_u32(&copy_bar[is]);
+        mbar_expect_tx(cb, 2 * part + (uint32_t)BXAREA);
+        const unsigned char* src = iv.tblk + ((size_t)iv.mt * ikch + ikc) * BTCHUNK;
+        if (part == (uint32_t)BPART) {
+          bulk_g2s(st, src, BTCHUNK, cb);
+        } else {
+          bulk_g2s(st, src, part, cb);
+          bulk_g2s(st + BPART, src + BPART, part, cb);
+        }
+        // x: the chunk's 64 real K (past 2N: zeros); rows: the tile's lines
+        // (past the pass's end: zeros); z: the head and tail planes
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+            "%4}], [%5];" ::"r"(st + (uint32_t)BTCHUNK),
+            "l"(reinterpret_cast<uint64_t>(iv.xmap)), "r"(ikc * BKC), "r"((int)(iv.ct * BL)), "r"(0), "r"(cb)
+            : "memory");
+        last_u[is] = (int)(u & 1);
+        ++ci;
+        is = is + 1 == BSTAGES ? 0 : is + 1;
+        if (++ikc == ikch) {
+          ikc = 0;
+          if (++iw < last) {
+            const void* prev = iv.xmap;
+            iv = many_view(P, iw);
+            ikch = (2 * iv.N + BKC - 1) / BKC;
+            if (iv.xmap != prev)
+              asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(iv.xmap) : "memory");
+          }
+        }
+      }
+      // nothing of this thread's may still be in flight at exit
+      for (int q = 0; q < BSTAGES; ++q)
+        if (last_u[q] >= 0) mbar_wait_own(smem_u32(&copy_bar[q]), (uint32_t)last_u[q], &s_abort);
+    }
+  } else if (warp < BMMA_WARP) {
     // ---------------- producers ----------------
     const int t = tid;
     // Issue side: chunk j of the block's run into stage j % BSTAGES once the
@@ -1055,7 +1122,7 @@ __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcPa
           const int s = (int)(g % BSTAGES);
           const int64_t u = g / BSTAGES;
           if (!mbar_wait(smem_u32(&copy_bar[s]), (uint32_t)(u & 1), &s_abort) ||
-              !mbar_wait(smem_u32(&full_bar[s]), (uint32_t)(u & 1), &s_abort)) {
+              (!PLANES && !mbar_wait(smem_u32(&full_bar[s]), (uint32_t)(u & 1), &s_abort))) {
             ok = false;
             break;
           }
@@ -1065,7 +1132,9 @@ __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcPa
 #pragma unroll
           for (int ks = 0; ks < BKC / 16; ++ks) {
             const uint32_t o = (uint32_t)(ks * 2 * BCORE);
-            const uint64_t dxh = make_desc(xh + o, BCORE, BSBO), dxl = make_desc(xl + o, BCORE, BSBO);
+            // X: the producers' core matrices, or the swizzled TMA tile (32 bytes per K step)
+            const uint64_t dxh = PLANES ? make_desc_sw128(xh + (uint32_t)(ks * 32)) : make_desc(xh + o, BCORE, BSBO);
+            const uint64_t dxl = PLANES ? make_desc_sw128(xl + (uint32_t)(ks * 32)) : make_desc(xl + o, BCORE, BSBO);
             const uint64_t dth = make_desc(th + o, BCORE, BSBO);
             const uint32_t more = (kc == 0 && ks == 0) ? 0u : 1u;
             if (whole) {
@@ -1094,8 +1163,10 @@ __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcPa
     bool ok = true;
     for (int64_t w = first; ok && w < last; ++w, ++sub) {
       const BView ev = many_view(P, w);
-      const int64_t inner = ev.inner;
-      const bool contiguous = (inner == 1);
+      // the output's stride between a line's points: the input's, or (chains)
+      // the transposed order's, the pass's line count
+      const int64_t inner = TOUT ? ev.ncols : ev.inner;
+      const bool contiguous = !TOUT && inner == 1;
       const int nbase = ev.mt * (BR / 2);
       const int rows = brow_count(ev.N, ev.mt);
       const int buf = (int)(sub & 1);
@@ -1106,7 +1177,8 @@ __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcPa
       ok = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
       if (!ok) break;
       tc_fence_after();
-      const long long base = many_line(ev, ev.ct * BL + r);
+      const int64_t line = ev.ct * BL + r;
+      const long long base = TOUT ? (line < ev.ncols ? line : -1) : many_line(ev, line);
       const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * BR);
 #pragma unroll 1
       for (int j0 = 0; j0 < rows; j0 += 16) {
@@ -1119,7 +1191,18 @@ __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcPa
         for (int m = 0; m < 16; ++m) y[m] = __uint_as_float(x[m]) + __uint_as_float(z[m]);
         const int n0 = nbase + j0 / 2;  // complex outputs n0 .. n0 + 7 of this line
         if (base < 0) continue;
-        if (ev.out_c) {
+        if (TOUT && ev.out_bf) {
+          // BF16 head and tail planes for the next pass (the split that pass
+          // would make of the same FP32 value)
+#pragma unroll
+          for (int m = 0; m < 8; ++m) {
+            const __nv_bfloat162 hb = __floats2bfloat162_rn(y[2 * m], y[2 * m + 1]);
+            const int64_t e = base + (int64_t)(n0 + m) * inner;
+            ev.out_bf[e] = *reinterpret_cast<const uint32_t*>(&hb);
+            const float2 hf = __bfloat1622float2(hb);
+            ev.out_bf[ev.bf_plane + e] = pack_bf16(y[2 * m] - hf.x, y[2 * m + 1] - hf.y);
+          }
+        } else if (ev.out_c) {
           if (contiguous) {
             float4* o = reinterpret_cast<float4*>(ev.out_c + base + n0);
 #pragma unroll
@@ -1158,13 +1241,19 @@ __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcPa
 
 }  // namespace
 
+const void* bf16_split_func() { return (const void*)bf16_split_kernel; }
+int bf16_split_grid(int64_t n, int sms) {
+  int64_t grid = (n / 2 + 255) / 256;
+  if (grid > 8 * (int64_t)sms) grid = 8 * (int64_t)sms;
+  return grid < 1 ? 1 : (int)grid;
+}
+
 cudaError_t launch_bf16_split(const float2* in, uint32_t* planes, int64_t n, int64_t plane, int unsplit, int sms,
                               cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int64_t n2 = n / 2;  // n is even: whole realizations of lattices of >= 64 points
-  int64_t grid = (n2 + 255) / 256;
-  if (grid > 8 * (int64_t)sms) grid = 8 * (int64_t)sms;
-  bf16_split_kernel<<<(int)grid, 256, 0, s>>>(reinterpret_cast<const float4*>(in), reinterpret_cast<uint2*>(planes),
+  const int grid = bf16_split_grid(n, sms);
+  bf16_split_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const float4*>(in), reinterpret_cast<uint2*>(planes),
                                               reinterpret_cast<uint2*>(planes + plane), n2, unsplit);
   return cudaGetLastError();
 }
@@ -1202,17 +1291,20 @@ cudaError_t dense_bf16_prepare() {
   return e;
 }
 
-const void* many_bf16_func(bool tma) {
-  return tma ? (const void*)dense_bf16_many_kernel<true> : (const void*)dense_bf16_many_kernel<false>;
+const void* many_bf16_func(int mode) {
+  switch (mode) {
+    case 1: return (const void*)dense_bf16_many_kernel<kTmaContiguous, false>;
+    case 2: return (const void*)dense_bf16_many_kernel<kTmaPlanes, true>;
+    case 3: return (const void*)dense_bf16_many_kernel<kInPlace, true>;
+    default: return (const void*)dense_bf16_many_kernel<kInPlace, false>;
+  }
 }
 int many_bf16_threads() { return BTHREADS; }
 size_t many_bf16_smem() { return (size_t)BMANY_SMEM; }
 cudaError_t many_bf16_prepare() {
-  cudaError_t e = cudaFuncSetAttribute((const void*)dense_bf16_many_kernel<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, BMANY_SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute((const void*)dense_bf16_many_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             BMANY_SMEM);
+  cudaError_t e = cudaSuccess;
+  for (int m = 0; m < 4 && e == cudaSuccess; ++m)
+    e = cudaFuncSetAttribute(many_bf16_func(m), cudaFuncAttributeMaxDynamicSharedMemorySize, BMANY_SMEM);
   return e;
 }
 int many_bf16_lines() { return BL; }
@@ -1306,6 +1398,24 @@ bool many_bf16_line_map(const float2* base, int N, int64_t lines, void* map) {
   return true;
 }
 static_assert(sizeof(CUtensorMap) == 128, "tile maps are 128 bytes");
+
+bool many_bf16_plane_map(const uint32_t* head, int N, int64_t lines, int64_t plane, void* map) {
+  // [plane][line][2N bf16], boxes of 64 values x 128 lines x both planes, 128-byte
+  // swizzle: the map of the uniform kernel's BF16-plane tiles
+  std::memset(map, 0, sizeof(CUtensorMap));
+  const EncodeTiledFn enc = encode_tiled();
+  if (!enc || lines < 1 || (reinterpret_cast<uintptr_t>(head) & 15u) || ((plane * 4) & 15)) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)(2 * N), (cuuint64_t)lines, 2u};
+  const cuuint64_t strides[2] = {(cuuint64_t)(2 * N) * 2, (cuuint64_t)plane * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)BKC, (cuuint32_t)BL, 2u}, estr[3] = {1, 1, 1};
+  if (enc(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)head, dims, strides, box,
+          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+    std::memset(map, 0, sizeof(CUtensorMap));
+    return false;
+  }
+  return true;
+}
 
 cudaError_t launch_dense_bf16(const DenseArgs& args, const unsigned char* Tblk, int* err, int grid, cudaStream_t s) {
   DenseArgs a = args;

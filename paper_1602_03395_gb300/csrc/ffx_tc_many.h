@@ -15,6 +15,9 @@ struct TcPassArg {
   const unsigned char* tblk;
   int in_base, outc_base, outd_base, grad_base;
   int xmap;  // BF16 phases: index of the input's tile map in TcParams::xmaps, or -1
+  // BF16 chains: the output is BF16 head and tail planes (d.out_bf, an offset
+  // on outc_base's buffer; d.bf_plane pairs apart), transposed
+  int out_planes;
 };
 
 // One work item: line tile ct (128 lines) and row block mt of pass `arg`.
@@ -57,7 +60,10 @@ int many_tc_row_blocks(int N);
 // The BF16 variant (ffx_tc16.cu) for lines of 32 to 256 points, a multiple
 // of 16: the same work lists and parameters, with split BF16 operand blocks
 // of T (launch_bf16_build_t layout) in TcPassArg::tblk.  No gradient passes.
-const void* many_bf16_func(bool tma);  // tma: every pass of the launch has a tile map
+// mode 0: FP32 input by per-thread copies; 1: FP32 contiguous lines by TMA
+// tiles (every pass a tile map); 2: BF16 planes by TMA tiles (chains); 3: as
+// 0 with a chain pass's transposed output (a chain's first pass)
+const void* many_bf16_func(int mode);
 int many_bf16_threads();
 size_t many_bf16_smem();
 cudaError_t many_bf16_prepare();
@@ -68,5 +74,13 @@ bool many_bf16_supported(int N);
 // `base` (16-byte aligned) into map[128] (64-byte aligned); false if the
 // driver cannot.
 bool many_bf16_line_map(const float2* base, int N, int64_t lines, void* map);
+// The same for BF16 head and tail planes of `lines` contiguous lines of N
+// points: the head plane at `head` (16-byte aligned), the tail plane `plane`
+// pairs after it (4 * plane a multiple of 16).
+bool many_bf16_plane_map(const uint32_t* head, int N, int64_t lines, int64_t plane, void* map);
+// The input split of a BF16 chain as a graph node: the kernel of
+// launch_bf16_split and its grid for n points.
+const void* bf16_split_func();
+int bf16_split_grid(int64_t n, int sms);
 
 }  // namespace ffx

@@ -2,6 +2,8 @@
 one persistent launch per axis pass, replayed as a CUDA graph.  Every
 instance against the FP64 oracle and against its own single-lattice plan."""
 
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -283,3 +285,22 @@ def test_many_bf16_phases_match_tf32_phases_and_are_batch_independent():
         assert np.array_equal(r1, rb[k].cpu().numpy().ravel())
     print(f"many bf16 vs tf32 phases: worst {worst:.2e}")
     assert worst < DENSITY_TOL
+
+
+def test_many_tc_rejects_buffers_not_16_byte_aligned():
+    """The tensor-core phases copy and store 16 bytes at a time: a buffer only
+    8-byte aligned is refused on the host (FFX_EINVAL), before any launch."""
+    ffx = require_gpu()
+    specs = [((64, 32), (0.2, 0.2), 2.0, (3, 3)), ((32, 32, 32), (0.2,) * 3, 3.0, (2, 2, 2))]
+    with ffx.PlanMany(specs, form="tc") as plan:
+        assert plan.form == "tc"
+        big = torch.zeros(plan.points + 1, dtype=torch.complex64, device="cuda")
+        out = torch.empty(plan.points + 2, dtype=torch.float32, device="cuda")
+        lib = ffx.load_library()
+        rc = lib.ffx_expand(plan.handle, ctypes.c_void_p(big.data_ptr() + 8), 1,
+                            ctypes.c_void_p(out.data_ptr()), None)
+        assert rc == ffx.FFX_EINVAL
+        rc = lib.ffx_expand(plan.handle, ctypes.c_void_p(big.data_ptr()), 1,
+                            ctypes.c_void_p(out.data_ptr() + 8), None)
+        assert rc == ffx.FFX_EINVAL
+        assert plan.device_errors() == 0
