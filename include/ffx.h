@@ -208,7 +208,9 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
  * chain: each instance's passes from its last axis to its first, the
  * intermediate results kept as BF16 head and tail planes in the workspaces.
  * Every call of a plan on the tensor cores takes 16-byte aligned buffers
- * (FFX_EINVAL otherwise).  A plan
+ * (FFX_EINVAL otherwise); the first forward call with a new input buffer
+ * uploads the chain's tile maps of it from host memory (on the call's
+ * stream), so such a call cannot be captured into a CUDA graph.  A plan
  * with a 16-point axis keeps the FP32 phases (ffx_plan_form reports which).
  * Dense passes are not in place for
  * lines over 64 points, so an in-place ffx_expand_field with a 1-D instance

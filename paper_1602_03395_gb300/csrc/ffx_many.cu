@@ -19,6 +19,7 @@
 // (instance, 64 x 32 tiles) items of the dense product.  Those passes are not
 // in place for N > 64, so pass k of an instance writes workspace k % 2.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -45,11 +46,16 @@ constexpr int KIND_TC16T = 103;  // the same, every input by TMA tiles (a tile m
 constexpr int KIND_TC16P = 104;  // a BF16 chain pass: planes in, planes (or the output) out, transposed
 constexpr int KIND_SPLIT = 105;  // a BF16 chain's input split into planes
 constexpr int KIND_TC16P0 = 106;  // a BF16 chain's first pass: the caller's FP32 input in, planes out
+constexpr int KIND_TC16P1 = 107;  // the same by TMA tiles (tile maps of each call's input)
 bool tc_kind(int kind) {
-  return kind == KIND_TC || kind == KIND_TC16 || kind == KIND_TC16T || kind == KIND_TC16P || kind == KIND_TC16P0;
+  return kind == KIND_TC || kind == KIND_TC16 || kind == KIND_TC16T || kind == KIND_TC16P || kind == KIND_TC16P0 ||
+         kind == KIND_TC16P1;
 }
 #ifndef FFX_MANY_CHAIN_SPLIT
 #define FFX_MANY_CHAIN_SPLIT 0
+#endif
+#ifndef FFX_MANY_CHAIN_TMA0
+#define FFX_MANY_CHAIN_TMA0 1
 #endif
 struct ManyCall {
   const void* base[NBASE];
@@ -206,6 +212,9 @@ struct Phase {
   long long* d_first = nullptr;   // per block: first item of its run (grid_tc + 1 entries)
   long long n_titems = 0;
   const void* d_xmaps = nullptr;  // BF16 phases: tile maps of inputs in the plan's workspaces
+  // a chain's first pass by TMA: per pass argument (instance offset, N, lines)
+  // of the tile map made for each call's input
+  std::vector<std::array<int64_t, 3>> call_maps;
 };
 
 }  // namespace
@@ -786,9 +795,10 @@ int deal_tc_phase(ManyPlan* mp, int kind, std::vector<TcPassArg> args, std::vect
   // by TMA when every pass of the launch has one (one input mode per launch)
   std::vector<unsigned char> maps;
   bool all_maps = kind == KIND_TC16;
-  if (kind == KIND_TC16P) maps = *plane_maps;  // the chain's pass arguments carry their map indices
+  const bool premade = kind == KIND_TC16P || kind == KIND_TC16P1;
+  if (premade) maps = *plane_maps;  // the chain's pass arguments carry their map indices
   for (TcPassArg& pa : args) {
-    if (kind == KIND_TC16P) break;
+    if (premade) break;
     pa.xmap = -1;
     if (!all_maps || pa.d.inner != 1 || (pa.in_base != BASE_WS && pa.in_base != BASE_WS2)) {
       all_maps = false;
@@ -804,7 +814,7 @@ int deal_tc_phase(ManyPlan* mp, int kind, std::vector<TcPassArg> args, std::vect
     pa.xmap = (int)(maps.size() / 128);
     maps.insert(maps.end(), m, m + 128);
   }
-  if (kind == KIND_TC16P) {
+  if (premade) {
   } else if (!all_maps) {
     maps.clear();
     for (TcPassArg& pa : args) pa.xmap = -1;
@@ -964,7 +974,8 @@ int build_chain_phases(ManyPlan* mp, int mode, std::string* err) {
   for (int r = 0; r < D; ++r) {
     std::vector<TcPassArg> args;
     std::vector<unsigned char> maps;
-    const bool fp32_in = (r == 0 && !split_first);  // the caller's input, by per-thread copies
+    const bool fp32_in = (r == 0 && !split_first);  // the caller's input
+    std::vector<std::array<int64_t, 3>> call_maps;
     const int in_base = fp32_in ? BASE_PSI0 : (r % 2 == 0) ? BASE_WS2 : BASE_WS;
     const int ws_out = (r % 2 == 0) ? BASE_WS : BASE_WS2;
     const uint32_t* in_planes = (const uint32_t*)(in_base == BASE_WS2 ? mp->ws2 : mp->ws);
@@ -1008,13 +1019,18 @@ int build_chain_phases(ManyPlan* mp, int mode, std::string* err) {
         for (Phase& ph : phases) cudaFree(ph.d_targs);
         return FFX_EUNSUPPORTED;
       }
-      if (!fp32_in) {
+      if (!fp32_in || FFX_MANY_CHAIN_TMA0) {
+        // the first pass's maps are made for each call's input (zeros until then)
+        if (fp32_in) std::memset(m, 0, sizeof(m));
         pa.xmap = (int)(maps.size() / 128);
         maps.insert(maps.end(), m, m + 128);
+        if (fp32_in) call_maps.push_back({in.off, (int64_t)at.N, R});
       }
       args.push_back(pa);
     }
-    int rc = deal_tc_phase(mp, fp32_in ? KIND_TC16P0 : KIND_TC16P, args, phases, err, &maps);
+    const int kind = !fp32_in ? KIND_TC16P : FFX_MANY_CHAIN_TMA0 ? KIND_TC16P1 : KIND_TC16P0;
+    int rc = deal_tc_phase(mp, kind, args, phases, err, &maps);
+    if (rc == FFX_OK && kind == KIND_TC16P1) phases.back().call_maps = call_maps;
     if (rc) {
       for (Phase& ph : phases) cudaFree(ph.d_targs);
       return rc;
@@ -1111,6 +1127,7 @@ const void* phase_func(int kind) {
     case KIND_TC16T: return many_bf16_func(1);
     case KIND_TC16P: return many_bf16_func(2);
     case KIND_TC16P0: return many_bf16_func(3);
+    case KIND_TC16P1: return many_bf16_func(4);
     case KIND_FWD_PAPER: return (const void*)many_kernel<KIND_FWD_PAPER>;
     case KIND_FWD_FOLD: return (const void*)many_kernel<KIND_FWD_FOLD>;
     case KIND_DENSE: return (const void*)many_dense_kernel;
@@ -1255,11 +1272,38 @@ int build_graph(ManyPlan* mp, int mode, const ManyCall& call, std::string* err) 
   return FFX_OK;
 }
 
+// The tile maps of a chain's first pass over the call's input, uploaded on the
+// call's stream (ordered after the launches that used the previous ones).
+int refresh_call_maps(ManyPlan* mp, int mode, const ManyCall& call, cudaStream_t s, std::string* err) {
+  for (Phase& ph : mp->phases[mode]) {
+    if (ph.call_maps.empty()) continue;
+    std::vector<unsigned char> maps(ph.call_maps.size() * 128);
+    for (size_t i = 0; i < ph.call_maps.size(); ++i) {
+      const std::array<int64_t, 3>& g = ph.call_maps[i];
+      const float2* base = (const float2*)call.base[BASE_PSI0] + g[0];
+      if (!many_bf16_line_map(base, (int)g[1], g[2], maps.data() + 128 * i)) {
+        *err = "tile map of the input";
+        return FFX_ECUDA;
+      }
+    }
+    cudaError_t e = cudaMemcpyAsync((void*)ph.d_xmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+      *err = std::string("tile map upload: ") + cudaGetErrorString(e);
+      return FFX_ECUDA;
+    }
+  }
+  return FFX_OK;
+}
+
 int launch_mode(ManyPlan* mp, int mode, const ManyCall& call, cudaStream_t s, std::string* err) {
   int rc;
   if (!mp->exec[mode]) {
     if ((rc = build_graph(mp, mode, call, err))) return rc;
+    if ((rc = refresh_call_maps(mp, mode, call, s, err))) return rc;
   } else if (std::memcmp(&call, &mp->last_call[mode], sizeof(call)) != 0) {
+    if (call.base[BASE_PSI0] != mp->last_call[mode].base[BASE_PSI0] &&
+        (rc = refresh_call_maps(mp, mode, call, s, err)))
+      return rc;
     // new buffers: rewrite the phase kernels' call pointers in the executable graph
     std::vector<Phase>& phases = mp->phases[mode];
     for (size_t k = 0; k < phases.size(); ++k) {

@@ -1296,6 +1296,7 @@ const void* many_bf16_func(int mode) {
     case 1: return (const void*)dense_bf16_many_kernel<kTmaContiguous, false>;
     case 2: return (const void*)dense_bf16_many_kernel<kTmaPlanes, true>;
     case 3: return (const void*)dense_bf16_many_kernel<kInPlace, true>;
+    case 4: return (const void*)dense_bf16_many_kernel<kTmaContiguous, true>;
     default: return (const void*)dense_bf16_many_kernel<kInPlace, false>;
   }
 }
@@ -1303,7 +1304,7 @@ int many_bf16_threads() { return BTHREADS; }
 size_t many_bf16_smem() { return (size_t)BMANY_SMEM; }
 cudaError_t many_bf16_prepare() {
   cudaError_t e = cudaSuccess;
-  for (int m = 0; m < 4 && e == cudaSuccess; ++m)
+  for (int m = 0; m < 5 && e == cudaSuccess; ++m)
     e = cudaFuncSetAttribute(many_bf16_func(m), cudaFuncAttributeMaxDynamicSharedMemorySize, BMANY_SMEM);
   return e;
 }

@@ -62,7 +62,8 @@ int many_tc_row_blocks(int N);
 // of T (launch_bf16_build_t layout) in TcPassArg::tblk.  No gradient passes.
 // mode 0: FP32 input by per-thread copies; 1: FP32 contiguous lines by TMA
 // tiles (every pass a tile map); 2: BF16 planes by TMA tiles (chains); 3: as
-// 0 with a chain pass's transposed output (a chain's first pass)
+// 0 with a chain pass's transposed output (a chain's first pass); 4: as 1
+// with that output
 const void* many_bf16_func(int mode);
 int many_bf16_threads();
 size_t many_bf16_smem();
