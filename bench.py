@@ -106,6 +106,8 @@ def parse():
                     help="split TF32 operands on every tensor-core pass (the automatic form's BF16 default off)")
     ap.add_argument("--batch", type=int, default=None, help="realizations per step (default: workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-backward", action="store_true",
+                    help="skip the ffx_expand_backward record of the workload")
     ap.add_argument("--fft-passes", action="store_true",
                     help="time the FFT-form (fold) passes at lam = 1 and 2 on 64^3 x 64, 256^3 and 1-D N=1024 x 65536 "
                          "lines, per pass against the HBM roofline (one JSON line)")
@@ -600,6 +602,45 @@ def tensor_peak(pk, pk_src, timed_ms, dtype="tf32"):
             f"{key} x 1.1/2.25 (TF32 dense : BF16 dense, nominal), {pk_src}")
 
 
+def backward_record(args, torch, ffx, plan, w, pool_in, stream, M):
+    """ffx_expand_backward on the bench's plan: the batch's gradient with
+    respect to psi0 of a loss with a seeded dL/drho, K calls after W warm-up
+    calls (inputs from the rotating pool, so larger than L2), CUDA events on
+    the stream; the kernels one call launches; the rel-L2 error of the first
+    realization's gradient against the FP64 oracle's (lattices up to 2^25
+    points)."""
+    B_ = pool_in[0].shape[0]
+    g = torch.from_numpy(np.random.default_rng(11).normal(size=tuple(pool_in[0].shape)).astype(np.float32))
+    g = g.to(pool_in[0].device)
+    out = torch.empty_like(pool_in[0])
+    n = len(pool_in)
+    for i in range(max(3, args.warmup)):
+        ffx.ffx_expand_backward(plan, pool_in[i % n], g, out)
+    torch.cuda.synchronize()
+    n0 = plan.launch_count()
+    ffx.ffx_expand_backward(plan, pool_in[0], g, out)
+    per_call = plan.launch_count() - n0
+    steps = max(3, min(args.steps, 20))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(steps):
+        ffx.ffx_expand_backward(plan, pool_in[(i + 1) % n], g, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    err = None
+    if M <= 1 << 25:
+        import oracle as O
+        got = ffx.ffx_expand_backward(plan, pool_in[0][:1].contiguous(), g[:1].contiguous()).cpu().numpy()
+        ref = O.density_loss_gradient(pool_in[0][:1].cpu().numpy(), g[:1].cpu().numpy(), w.dx, w.t, w.lam)
+        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    return {"value": B_ / (ms * 1e-3), "unit": UNIT, "ms_per_call": ms, "batch": B_, "calls": steps,
+            "gpu_launches_per_call": per_call, "rel_l2_grad_err_vs_fp64": err,
+            "timing": "CUDA events around direct calls on the stream, inputs rotating through the pool"}
+
+
 def hbm_step_record(w, batch, chain, fused_call, out_bytes, step_ms, hbm_peak, pk_src):
     """Whole-step HBM view: the algorithmic bytes of a step (read psi0, 8 B
     per point, write the output) and the bytes the implementation's launches
@@ -907,6 +948,13 @@ def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary
             scipy32 = scipy_baseline(w, dtype=np.complex64)
             scipy64 = scipy_baseline(w, dtype=np.complex128)
 
+    # the gradient of an image-space loss (ffx_expand_backward: T^H (2 g . T psi0))
+    # on the same plan, timed with CUDA events over direct calls; its error
+    # against the FP64 oracle's gradient for the first realization
+    backward = None
+    if primary and rank == 0 and args.column is None and not args.no_backward:
+        backward = backward_record(args, torch, ffx, plan, w, pool_in, stream, M)
+
     cpu = None
     if primary and rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, n, dt = cpu_oracle_rate(w, [d.numpy()[0] for d in distinct])
@@ -948,6 +996,7 @@ def measure_workload(args, torch, dist, world, rank, local, dev, ffx, w, primary
                 "h2d_bytes_per_step": B_ * M * 8,
                 "d2h_bytes_per_step": out_bytes},
         "cpu_baseline": cpu,
+        "backward": backward,
         "fringe_readout": fringe,
         "comparisons": {"cufft_recipe": cufft, "cpu_fft_recipe_c64": scipy32,
                         "cpu_fft_recipe_c128": scipy64},
