@@ -27,7 +27,11 @@
  *    workspace (device memory).
  *  - Calls are asynchronous on the given stream (a cudaStream_t passed as
  *    void*; NULL means the legacy default stream).  No entry point except
- *    ffx_plan / ffx_plan_destroy synchronizes with the host.
+ *    ffx_plan / ffx_plan_destroy synchronizes with the host, but where noted
+ *    (a first call that allocates or uploads).
+ *  - A plan's calls share its workspace: calls on one plan that overlap on the
+ *    GPU race.  Issue them on one stream (or order them), one plan per
+ *    concurrent stream.
  *  - Errors are returned as codes, never as exceptions.  ffx_last_error()
  *    gives a message for the most recent failure in the calling thread.
  *  - A plan may be used from one host thread at a time.
@@ -209,8 +213,9 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
  * intermediate results kept as BF16 head and tail planes in the workspaces.
  * Every call of a plan on the tensor cores takes 16-byte aligned buffers
  * (FFX_EINVAL otherwise); the first forward call with a new input buffer
- * uploads the chain's tile maps of it from host memory (on the call's
- * stream), so such a call cannot be captured into a CUDA graph.  A plan
+ * uploads the chain's tile maps of it from host memory on the call's stream
+ * (a copy that waits for the stream's earlier work), so such a call cannot
+ * be captured into a CUDA graph.  A plan
  * with a 16-point axis keeps the FP32 phases (ffx_plan_form reports which).
  * Dense passes are not in place for
  * lines over 64 points, so an in-place ffx_expand_field with a 1-D instance
