@@ -304,3 +304,36 @@ def test_many_tc_rejects_buffers_not_16_byte_aligned():
                             ctypes.c_void_p(out.data_ptr() + 8), None)
         assert rc == ffx.FFX_EINVAL
         assert plan.device_errors() == 0
+
+
+def test_many_chain_new_buffers_modes_and_in_place_field():
+    """Forward calls of a BF16 tensor-core plan run as chains whose first pass
+    reads the call's input through tile maps made for that input buffer: a
+    density call on a new buffer (maps remade) gives bitwise the same result,
+    density and field calls alternate on different buffers, and a field call
+    in place (1-D instance of 64 points, 2-D and 3-D instances) equals the
+    out-of-place one and the FP64 oracle."""
+    ffx = require_gpu()
+    dims_set = [(64, 32, 48), (96, 32), (64,), (32, 128, 32)]
+    specs, psis = mixed_specs(6, dims_override=dims_set)
+    with ffx.PlanMany(specs, form="tc") as plan:
+        assert plan.form == "tc" and plan.bf16
+        x1 = to_dev(pack(plan, psis))
+        x2 = x1.clone()
+        r1 = ffx.ffx_expand(plan, x1).clone()
+        f2 = ffx.ffx_expand_field(plan, x2).clone()
+        r2 = ffx.ffx_expand(plan, x2)
+        assert torch.equal(r1, r2)
+        y = x1.clone()
+        ffx.ffx_expand_field(plan, y, y)
+        assert torch.equal(y, f2)
+        assert plan.device_errors() == 0
+        rho, field = r1.cpu().numpy(), f2.cpu().numpy()
+        worst_d = worst_f = 0.0
+        for (dims, dx, t, lam), p, off in zip(specs, psis, plan.offsets):
+            ref = O.expand_field(p, dx, t, lam)
+            m = p.size
+            worst_d = max(worst_d, rel_l2(rho[off:off + m].reshape(dims), np.abs(ref) ** 2))
+            worst_f = max(worst_f, rel_l2(field[off:off + m].reshape(dims), ref))
+    print(f"many chain buffers/modes: worst density {worst_d:.2e}, worst field {worst_f:.2e}")
+    assert worst_d < DENSITY_TOL and worst_f < FIELD_TOL
