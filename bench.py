@@ -459,6 +459,43 @@ def mixed_flops(specs, form, bf16=False):
     return tot, bf
 
 
+def mixed_backward_record(args, torch, ffx, plan, ws, x, stream):
+    """ffx_expand_backward on the mixed-batch plan (every instance's gradient
+    with respect to psi0 for a seeded normal dL/drho), CUDA events over direct
+    calls after warm-up; the rel-L2 error of the first instance's gradient
+    against the FP64 oracle's."""
+    g = torch.from_numpy(np.random.default_rng(12).normal(size=plan.points).astype(np.float32)).to(x.device)
+    out = torch.empty_like(x)
+    for _ in range(3):
+        ffx.ffx_expand_backward(plan, x, g, out)
+    torch.cuda.synchronize()
+    n0 = plan.launch_count()
+    ffx.ffx_expand_backward(plan, x, g, out)
+    per_call = plan.launch_count() - n0
+    steps = max(3, min(args.steps, 20))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        ffx.ffx_expand_backward(plan, x, g, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    import oracle as O
+    w = ws[0]
+    m = int(np.prod(w.dims))
+    psi = x[:m].cpu().numpy().reshape((1,) + tuple(w.dims))
+    gi = g[:m].cpu().numpy().reshape((1,) + tuple(w.dims))
+    ref = O.density_loss_gradient(psi, gi, w.dx, w.t, w.lam)
+    got = out[:m].cpu().numpy().reshape(ref.shape)
+    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    return {"value": len(ws) / (ms * 1e-3), "unit": UNIT, "ms_per_call": ms, "calls": steps,
+            "gpu_launches_per_call": per_call, "rel_l2_grad_err_vs_fp64_first_instance": err,
+            "loss": "dL/drho a seeded normal field",
+            "timing": "CUDA events around direct calls on the stream"}
+
+
 def run_mixed(args, torch, dist, world, rank, dev):
     """The mixed-lattice ensemble: every instance of the batch in one
     ffx_expand on a many-instance plan (one persistent kernel per axis pass,
@@ -561,6 +598,9 @@ def run_mixed(args, torch, dist, world, rank, dev):
     plan2.close()
     if world > 1:
         e2e_ms = max_over_ranks(torch, dist, e2e_ms, dev)
+    backward = None
+    if rank == 0 and not args.no_backward:
+        backward = mixed_backward_record(args, torch, ffx, plan, ws, x, stream)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -584,6 +624,7 @@ def run_mixed(args, torch, dist, world, rank, dev):
                     "lanes": lanes_used,
                     "h2d_bytes_per_step": plan.points * 8, "d2h_bytes_per_step": plan.points * 4},
             "cpu_baseline": None,
+            "backward": backward,
         }
         print(json.dumps(line), flush=True)
     plan.close()
