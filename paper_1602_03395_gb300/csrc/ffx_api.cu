@@ -379,7 +379,7 @@ int run_axis(ffx_plan_s* p, int j, bool adjoint, const float2* in, const float* 
     // split TF32
     const bool tm64 = ax.N == 64 && !acc && !grad && items <= 4 * grid;
     if (io) {
-      if (!ax.bf_t[0] || tm64 || adjoint || grad)
+      if (!ax.bf_t[adjoint ? 1 : 0] || tm64 || grad)
         return fail(FFX_EUNSUPPORTED, "internal: a BF16 chain pass of axis %d without the BF16 kernel", j);
       d.in_bf = io->in_bf;
       d.out_bf = io->out_bf;
@@ -519,6 +519,13 @@ bool bf16_chain_ok(const ffx_plan_s* p, int64_t batch, const void* in, const voi
   return true;
 }
 
+// Every axis has the BF16 blocks of T_j^H too (adjoint chains).
+bool bf16_adjoint_ok(const ffx_plan_s* p) {
+  for (int r = 0; r < p->ndim; ++r)
+    if (!p->axis[r].bf_t[1]) return false;
+  return true;
+}
+
 // The forward map of a batch as a BF16 chain: the input split into BF16
 // planes in ws[1] (head plane, then tail plane: 8 bytes a point, the size of
 // a complex64 field), then the passes in the plan's order (the last axis
@@ -546,6 +553,38 @@ int chain_bf16(ffx_plan_s* p, const float2* in, int64_t batch, float2* out_c, fl
     io.plane = plane;
     rc = run_axis(p, p->order[r], false, nullptr, nullptr, 0, last ? out_c : nullptr, last ? out_d : nullptr,
                   last && out_d ? p->acc : 0, batch, s, &io);
+    if (rc) return rc;
+    cur_bf = io.out_bf;
+  }
+  return FFX_OK;
+}
+
+// The adjoint half of a backward call as a BF16 chain: 2 grad * field split
+// into BF16 planes in ws[1], then the adjoint passes in the chain's order
+// (T_j^H along the last axis first; the axes' factors commute), planes
+// between them in ws[0] and ws[1] as in chain_bf16, the last pass writing
+// `out`.  `field` is read by the split alone (it may be ws[0]).
+int chain_bf16_adjoint(ffx_plan_s* p, const float2* field, const float* grad, int grad_shared, int64_t batch,
+                       float2* out, cudaStream_t s) {
+  const int d = p->ndim;
+  int rc;
+  if ((rc = ensure_ws(p, 0, batch)) || (rc = ensure_ws(p, 1, batch))) return rc;
+  const int64_t plane = batch * p->M;
+  const int unsplit = (p->flags & FFX_TC_UNSPLIT) ? 1 : 0;
+  const unsigned rec = trace_begin(p, s);
+  cudaError_t e = launch_bf16_split_grad(field, grad, grad_shared, p->M, (uint32_t*)p->ws[1], plane, plane, unsplit,
+                                         p->sms, s);
+  if (e != cudaSuccess) return cuda_fail(e, "BF16 split of the gradient factors");
+  ++p->launches;
+  trace_end(p, s, rec);
+  const uint32_t* cur_bf = (const uint32_t*)p->ws[1];
+  for (int r = 0; r < d; ++r) {
+    const bool last = r == d - 1;
+    ChainIo io;
+    io.in_bf = cur_bf;
+    io.out_bf = last ? nullptr : (uint32_t*)p->ws[r & 1];
+    io.plane = plane;
+    rc = run_axis(p, p->order[r], true, nullptr, nullptr, 0, last ? out : nullptr, nullptr, 0, batch, s, &io);
     if (rc) return rc;
     cur_bf = io.out_bf;
   }
@@ -1684,6 +1723,9 @@ int ffx_expand_backward(ffx_plan_t p, const void* psi0, const float* grad_densit
   if ((rc = ensure_ws(p, 0, batch))) return rc;
   float2* field = (float2*)p->ws[0];
   if ((rc = chain_into(p, p->order, false, (const float2*)psi0, nullptr, 0, batch, field, 1, s))) return rc;
+  // the adjoint half as a BF16 chain where the forward map takes one
+  if (bf16_chain_ok(p, batch, field, grad_psi0, nullptr) && bf16_adjoint_ok(p))
+    return chain_bf16_adjoint(p, field, grad_density, p->acc, batch, (float2*)grad_psi0, s);
   int axes[3];
   for (int r = 0; r < p->ndim; ++r) axes[r] = p->order[p->ndim - 1 - r];
   return chain_into(p, axes, true, field, grad_density, p->acc, batch, (float2*)grad_psi0, 1, s);

@@ -147,6 +147,10 @@ bool dense_bf16_chain_supported();
 // planes (the tail `plane` pairs after the head; head only when unsplit)
 cudaError_t launch_bf16_split(const float2* in, uint32_t* planes, int64_t n, int64_t plane, int unsplit, int sms,
                               cudaStream_t s);
+// The same for a backward call's adjoint chain: planes of 2 g psi, g per point
+// of each realization or (grad_shared) one [M] array for the batch.
+cudaError_t launch_bf16_split_grad(const float2* field, const float* grad, int grad_shared, int64_t M,
+                                   uint32_t* planes, int64_t n, int64_t plane, int unsplit, int sms, cudaStream_t s);
 cudaError_t launch_identity(float2* I, int N, cudaStream_t s);
 
 // The d passes of a small lattice (every axis <= 64 points, dense form) in one

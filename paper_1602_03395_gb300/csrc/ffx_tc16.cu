@@ -1239,7 +1239,39 @@ __global__ void __launch_bounds__(BTHREADS, 1) dense_bf16_many_kernel(const TcPa
   }
 }
 
+// The split of a backward call's adjoint chain: x = 2 g psi (psi the forward
+// field, g the density gradient: per realization, or one [M] array shared by
+// the batch), into BF16 head and tail planes as bf16_split_kernel does.
+__global__ void __launch_bounds__(256) bf16_split_grad_kernel(const float4* __restrict__ field,
+                                                               const float2* __restrict__ grad, uint2* __restrict__ hi,
+                                                               uint2* __restrict__ lo, int64_t n2, int64_t m2,
+                                                               int shared, int unsplit) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v = field[i];
+    const float2 g = grad[shared ? i % m2 : i];
+    const float a = 2.f * g.x, b = 2.f * g.y;
+    const float x0 = a * v.x, x1 = a * v.y, x2 = b * v.z, x3 = b * v.w;
+    const __nv_bfloat162 h0 = __floats2bfloat162_rn(x0, x1), h1 = __floats2bfloat162_rn(x2, x3);
+    hi[i] = make_uint2(*reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1));
+    if (!unsplit) {
+      const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+      lo[i] = make_uint2(pack_bf16(x0 - f0.x, x1 - f0.y), pack_bf16(x2 - f1.x, x3 - f1.y));
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_bf16_split_grad(const float2* field, const float* grad, int grad_shared, int64_t M,
+                                   uint32_t* planes, int64_t n, int64_t plane, int unsplit, int sms, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = bf16_split_grid(n, sms);
+  bf16_split_grad_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const float4*>(field),
+                                              reinterpret_cast<const float2*>(grad), reinterpret_cast<uint2*>(planes),
+                                              reinterpret_cast<uint2*>(planes + plane), n / 2, M / 2, grad_shared,
+                                              unsplit);
+  return cudaGetLastError();
+}
 
 const void* bf16_split_func() { return (const void*)bf16_split_kernel; }
 int bf16_split_grid(int64_t n, int sms) {

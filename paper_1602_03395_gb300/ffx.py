@@ -272,8 +272,10 @@ class Plan:
         lines adds its own split launch; launch_count() counts exactly."""
         n = len(self.dims)
         # a BF16 chain adds the split of its input (the forward half of a
-        # backward call takes a chain on 3-D plans)
-        chain = 1 if self.bf16_chain(batch) and (not backward or n == 3) else 0
+        # backward call takes a chain except on 2-D plans, its adjoint half
+        # always, with the split of its gradient factors)
+        bf = self.bf16_chain(batch)
+        chain = (1 if bf and (not backward or n != 2) else 0) + (1 if bf and backward else 0)
         if not backward and self.fused and batch > self.fused_max_batch:
             return n + chain
         return int(load_library().ffx_launches_per_call(self.handle, int(backward))) + chain

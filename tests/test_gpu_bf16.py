@@ -187,3 +187,37 @@ def test_bf16_pass_splits_contiguous_fp32_input(ffx):
     print(f"bf16 split first pass {dims} x{batch}: density {e_d:.2e}, field {e_f:.2e}, ensemble sum {e_acc:.2e}, "
           f"backward {e_g:.2e}")
     assert e_d < DENSITY_TOL and e_f < FIELD_TOL and e_acc < DENSITY_TOL and e_g < FIELD_TOL
+
+
+@pytest.mark.parametrize("dims,lam,batch", CHAIN_CASES)
+def test_bf16_chain_backward(ffx, dims, lam, batch):
+    """Backward calls on BF16-chain plans: the forward field (a chain except on
+    2-D plans), then the adjoint half as a chain -- the split of 2 g psi into
+    BF16 planes and the T_j^H passes from the last axis to the first -- per
+    realization and with the batch's shared gradient of an ensemble-sum plan,
+    against the oracle's gradient; the launches the call makes."""
+    rng = np.random.default_rng(5 * batch + len(dims))
+    dx, t = (0.25,) * len(dims), 10.0
+    d = len(dims)
+    psi = random_field(rng, (batch,) + dims)
+    grad = rng.normal(size=(batch,) + dims).astype(np.float32)
+    gsum = rng.normal(size=dims).astype(np.float32)
+    with ffx.Plan(dims, dx, t, lam, form="tc", bf16=True) as plan:
+        assert plan.bf16_chain(batch)
+        x = to_dev(psi)
+        n0 = plan.launch_count()
+        g = ffx.ffx_expand_backward(plan, x, to_dev(grad)).cpu().numpy()
+        # forward: the chain's split and d passes, or on 2-D plans the per-axis
+        # passes with the split of the contiguous axis's FP32 lines; adjoint:
+        # the gradient split and d passes
+        assert plan.launch_count() - n0 == 2 * d + 2
+        assert plan.device_errors() == 0
+    with ffx.Plan(dims, dx, t, lam, form="tc", bf16=True, accumulate=True) as plan:
+        assert plan.bf16_chain(batch)
+        gs = ffx.ffx_expand_backward(plan, to_dev(psi), to_dev(gsum)).cpu().numpy()
+        assert plan.device_errors() == 0
+    e_g = rel_l2(g, O.density_loss_gradient(psi, grad, dx, t, lam))
+    ref_s = np.stack([O.density_loss_gradient(psi[b:b + 1], gsum[None], dx, t, lam)[0] for b in range(batch)])
+    e_s = rel_l2(gs, ref_s)
+    print(f"bf16 chain backward {dims} x{batch}: {e_g:.2e}, shared gradient {e_s:.2e}")
+    assert e_g < FIELD_TOL and e_s < FIELD_TOL
