@@ -206,11 +206,11 @@ int ffx_plan_dispersion(ffx_plan_t* out, int ndim, const int64_t* dims, const do
  * also builds their tensor-core operand blocks and runs each phase as
  * persistent launches over items of 128 lines x 128 real rows, one block per
  * SM: on split BF16 operands (kind::f16 products, density error of order
- * 1e-6), except with FFX_TC_TF32 and in the first adjoint pass of
- * ffx_expand_backward (its gradient factors), which take split TF32 operands
- * (one more launch in that phase).  Forward calls on BF16 operands run as a
- * chain: each instance's passes from its last axis to its first, the
- * intermediate results kept as BF16 head and tail planes in the workspaces.
+ * 1e-6), or with FFX_TC_TF32 on split TF32 operands.  Calls on BF16 operands
+ * run as chains: each instance's passes from its last axis to its first, the
+ * intermediate results kept as BF16 head and tail planes in the workspaces;
+ * a backward call runs the forward chain into its gradient buffer, one launch
+ * that splits 2 grad * field into planes, and the adjoint chain.
  * Every call of a plan on the tensor cores takes 16-byte aligned buffers
  * (FFX_EINVAL otherwise); the first forward call with a new input buffer
  * uploads the chain's tile maps of it from host memory on the call's stream

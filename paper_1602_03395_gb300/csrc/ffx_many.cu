@@ -44,19 +44,11 @@ constexpr int KIND_TC = 101;     // the same on the tensor cores (split TF32)
 constexpr int KIND_TC16 = 102;   // the same with split BF16 operands
 constexpr int KIND_TC16T = 103;  // the same, every input by TMA tiles (a tile map per pass)
 constexpr int KIND_TC16P = 104;  // a BF16 chain pass: planes in, planes (or the output) out, transposed
-constexpr int KIND_SPLIT = 105;  // a BF16 chain's input split into planes
-constexpr int KIND_TC16P0 = 106;  // a BF16 chain's first pass: the caller's FP32 input in, planes out
-constexpr int KIND_TC16P1 = 107;  // the same by TMA tiles (tile maps of each call's input)
+constexpr int KIND_SPLITG = 105;  // a backward chain's split of 2 grad * field into planes
+constexpr int KIND_TC16P1 = 107;  // a BF16 chain's first pass: the caller's FP32 input by TMA tiles, planes out
 bool tc_kind(int kind) {
-  return kind == KIND_TC || kind == KIND_TC16 || kind == KIND_TC16T || kind == KIND_TC16P || kind == KIND_TC16P0 ||
-         kind == KIND_TC16P1;
+  return kind == KIND_TC || kind == KIND_TC16 || kind == KIND_TC16T || kind == KIND_TC16P || kind == KIND_TC16P1;
 }
-#ifndef FFX_MANY_CHAIN_SPLIT
-#define FFX_MANY_CHAIN_SPLIT 0
-#endif
-#ifndef FFX_MANY_CHAIN_TMA0
-#define FFX_MANY_CHAIN_TMA0 1
-#endif
 struct ManyCall {
   const void* base[NBASE];
 };
@@ -387,7 +379,8 @@ int build_dense_maps(ManyPlan* mp, bool tc, bool bf16, cudaStream_t s, std::stri
     if (e == cudaSuccess)
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, many_bf16_func(0), many_bf16_threads(),
                                                         many_bf16_smem());
-    for (int m = 1; m < 3 && e == cudaSuccess; ++m) {
+    for (int m : {1, 2, 4}) {
+      if (e != cudaSuccess) break;
       int per_m = 0;
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_m, many_bf16_func(m), many_bf16_threads(),
                                                         many_bf16_smem());
@@ -954,87 +947,93 @@ int build_tc_phases(ManyPlan* mp, int mode, std::string* err) {
   return FFX_OK;
 }
 
-// BF16 chain phases of a forward mode (0: density, 1: field), as the uniform
-// plans' BF16 chains: the caller's input split into BF16 head and tail planes
-// (the second workspace), then phase r runs every instance's pass along its
-// axis n_i - 1 - r on planes of contiguous lines (TMA tiles), writing its
-// output transposed -- point n of line c at c + n R, R the pass's lines -- as
-// the next pass's planes (the workspaces in turn) or, after the pass along
-// axis 0, the caller's output in the lattice's own order.  Returns
-// FFX_EUNSUPPORTED (nothing built) where a plane map cannot be made.
+// The passes of one chain phase: every instance's pass r (of its n_i) along
+// axis n_i - 1 - r, with T (adjoint: T^H) on planes of contiguous lines, or
+// for the first forward pass the caller's FP32 input (tile maps made per
+// input buffer); the output transposed -- point n of line c at c + n R, R the
+// pass's lines -- as the next planes (the workspaces in turn: in_base WS2 for
+// even r, WS for odd r, out the other) or, after the pass along axis 0, in
+// the lattice's own order to out_last (BASE_OUTD densities, else a field).
+int chain_phase(ManyPlan* mp, int r, bool adjoint, int out_last, std::vector<Phase>& phases, std::string* err) {
+  std::vector<TcPassArg> args;
+  std::vector<unsigned char> maps;
+  std::vector<std::array<int64_t, 3>> call_maps;
+  const bool fp32_in = (r == 0 && !adjoint);
+  const int in_base = fp32_in ? BASE_PSI0 : (r % 2 == 0) ? BASE_WS2 : BASE_WS;
+  const int ws_out = (r % 2 == 0) ? BASE_WS : BASE_WS2;
+  const uint32_t* in_planes = (const uint32_t*)(in_base == BASE_WS2 ? mp->ws2 : mp->ws);
+  for (const Instance& in : mp->inst) {
+    if (r >= in.ndim) continue;
+    const int axis = in.ndim - 1 - r;
+    const AxisTab& at = mp->tabs[in.axis_tab[axis]];
+    const int64_t R = in.M / at.N;
+    TcPassArg pa;
+    std::memset(&pa, 0, sizeof(pa));
+    pa.in_base = in_base;
+    pa.outc_base = BASE_NONE;
+    pa.outd_base = BASE_NONE;
+    pa.grad_base = BASE_NONE;
+    DenseArgs& a = pa.d;
+    a.in = (const float2*)(uintptr_t)((size_t)in.off * (fp32_in ? sizeof(float2) : sizeof(uint32_t)));
+    if (r == in.ndim - 1) {
+      if (out_last == BASE_OUTD) {
+        pa.outd_base = BASE_OUTD;
+        a.out_d = (float*)(uintptr_t)((size_t)in.off * sizeof(float));
+      } else {
+        pa.outc_base = out_last;
+        a.out_c = (float2*)(uintptr_t)((size_t)in.off * sizeof(float2));
+      }
+    } else {
+      pa.outc_base = ws_out;
+      pa.out_planes = 1;
+      a.out_bf = (uint32_t*)(uintptr_t)((size_t)in.off * sizeof(uint32_t));
+    }
+    a.bf_plane = mp->total;
+    a.outer = R;
+    a.inner = 1;
+    a.M = in.M;
+    a.batch = 1;
+    a.ncols = R;
+    a.N = at.N;
+    pa.tblk = at.bf[adjoint ? 1 : 0];
+    unsigned char m[128];
+    std::memset(m, 0, sizeof(m));  // the first pass's maps are made for each call's input
+    if (!pa.tblk || (!fp32_in && !many_bf16_plane_map(in_planes + in.off, at.N, R, mp->total, m)))
+      return FFX_EUNSUPPORTED;
+    pa.xmap = (int)(maps.size() / 128);
+    maps.insert(maps.end(), m, m + 128);
+    if (fp32_in) call_maps.push_back({in.off, (int64_t)at.N, R});
+    args.push_back(pa);
+  }
+  const int kind = fp32_in ? KIND_TC16P1 : KIND_TC16P;
+  int rc = deal_tc_phase(mp, kind, args, phases, err, &maps);
+  if (rc == FFX_OK && fp32_in) phases.back().call_maps = call_maps;
+  return rc;
+}
+
+// BF16 chain phases, as the uniform plans' BF16 chains.  Forward modes (0:
+// density, 1: field): the chain phases r = 0 .. D - 1 into the caller's
+// output.  Backward (2): the forward chain writes each field to the caller's
+// gradient buffer, a split phase forms 2 grad * field as BF16 planes (the
+// second workspace) for every point, and the adjoint chain (T^H along the
+// last axis first; the axes' factors commute) writes the gradient over the
+// fields.  Returns FFX_EUNSUPPORTED (nothing built) where a plane map cannot
+// be made.
 int build_chain_phases(ManyPlan* mp, int mode, std::string* err) {
   std::vector<Phase> phases;
-  const bool split_first = FFX_MANY_CHAIN_SPLIT != 0;
-  if (split_first) {
-    Phase split;
-    split.kind = KIND_SPLIT;
-    phases.push_back(split);
-  }
   const int D = mp->max_dim;
-  for (int r = 0; r < D; ++r) {
-    std::vector<TcPassArg> args;
-    std::vector<unsigned char> maps;
-    const bool fp32_in = (r == 0 && !split_first);  // the caller's input
-    std::vector<std::array<int64_t, 3>> call_maps;
-    const int in_base = fp32_in ? BASE_PSI0 : (r % 2 == 0) ? BASE_WS2 : BASE_WS;
-    const int ws_out = (r % 2 == 0) ? BASE_WS : BASE_WS2;
-    const uint32_t* in_planes = (const uint32_t*)(in_base == BASE_WS2 ? mp->ws2 : mp->ws);
-    for (const Instance& in : mp->inst) {
-      if (r >= in.ndim) continue;
-      const int axis = in.ndim - 1 - r;
-      const AxisTab& at = mp->tabs[in.axis_tab[axis]];
-      const int64_t R = in.M / at.N;
-      TcPassArg pa;
-      std::memset(&pa, 0, sizeof(pa));
-      pa.in_base = in_base;
-      pa.outc_base = BASE_NONE;
-      pa.outd_base = BASE_NONE;
-      pa.grad_base = BASE_NONE;
-      DenseArgs& a = pa.d;
-      a.in = (const float2*)(uintptr_t)((size_t)in.off * (fp32_in ? sizeof(float2) : sizeof(uint32_t)));
-      if (r == in.ndim - 1) {
-        if (mode == 0) {
-          pa.outd_base = BASE_OUTD;
-          a.out_d = (float*)(uintptr_t)((size_t)in.off * sizeof(float));
-        } else {
-          pa.outc_base = BASE_OUTC;
-          a.out_c = (float2*)(uintptr_t)((size_t)in.off * sizeof(float2));
-        }
-      } else {
-        pa.outc_base = ws_out;
-        pa.out_planes = 1;
-        a.out_bf = (uint32_t*)(uintptr_t)((size_t)in.off * sizeof(uint32_t));
-      }
-      a.bf_plane = mp->total;
-      a.outer = R;
-      a.inner = 1;
-      a.M = in.M;
-      a.batch = 1;
-      a.ncols = R;
-      a.N = at.N;
-      pa.tblk = at.bf[0];
-      pa.xmap = -1;
-      unsigned char m[128];
-      if (!pa.tblk || (!fp32_in && !many_bf16_plane_map(in_planes + in.off, at.N, R, mp->total, m))) {
-        for (Phase& ph : phases) cudaFree(ph.d_targs);
-        return FFX_EUNSUPPORTED;
-      }
-      if (!fp32_in || FFX_MANY_CHAIN_TMA0) {
-        // the first pass's maps are made for each call's input (zeros until then)
-        if (fp32_in) std::memset(m, 0, sizeof(m));
-        pa.xmap = (int)(maps.size() / 128);
-        maps.insert(maps.end(), m, m + 128);
-        if (fp32_in) call_maps.push_back({in.off, (int64_t)at.N, R});
-      }
-      args.push_back(pa);
-    }
-    const int kind = !fp32_in ? KIND_TC16P : FFX_MANY_CHAIN_TMA0 ? KIND_TC16P1 : KIND_TC16P0;
-    int rc = deal_tc_phase(mp, kind, args, phases, err, &maps);
-    if (rc == FFX_OK && kind == KIND_TC16P1) phases.back().call_maps = call_maps;
-    if (rc) {
-      for (Phase& ph : phases) cudaFree(ph.d_targs);
-      return rc;
-    }
+  int rc = FFX_OK;
+  const int out_fwd = mode == 0 ? BASE_OUTD : BASE_OUTC;
+  for (int r = 0; rc == FFX_OK && r < D; ++r) rc = chain_phase(mp, r, false, out_fwd, phases, err);
+  if (rc == FFX_OK && mode == 2) {
+    Phase split;
+    split.kind = KIND_SPLITG;
+    phases.push_back(split);
+    for (int r = 0; rc == FFX_OK && r < D; ++r) rc = chain_phase(mp, r, true, BASE_OUTC, phases, err);
+  }
+  if (rc) {
+    for (Phase& ph : phases) cudaFree(ph.d_targs);
+    return rc;
   }
   mp->phases[mode] = phases;
   return FFX_OK;
@@ -1042,7 +1041,7 @@ int build_chain_phases(ManyPlan* mp, int mode, std::string* err) {
 
 // Phases of one mode.  mode 0: density, 1: field, 2: backward.
 int build_phases(ManyPlan* mp, int mode, std::string* err) {
-  if (mp->tc && mp->bf16 && mode != 2 && build_chain_phases(mp, mode, err) == FFX_OK) return FFX_OK;
+  if (mp->tc && mp->bf16 && build_chain_phases(mp, mode, err) == FFX_OK) return FFX_OK;
   if (mp->tc) return build_tc_phases(mp, mode, err);
   if (mp->dense) return build_dense_phases(mp, mode, err);
   std::vector<Phase>& phases = mp->phases[mode];
@@ -1126,7 +1125,6 @@ const void* phase_func(int kind) {
     case KIND_TC16: return many_bf16_func(0);
     case KIND_TC16T: return many_bf16_func(1);
     case KIND_TC16P: return many_bf16_func(2);
-    case KIND_TC16P0: return many_bf16_func(3);
     case KIND_TC16P1: return many_bf16_func(4);
     case KIND_FWD_PAPER: return (const void*)many_kernel<KIND_FWD_PAPER>;
     case KIND_FWD_FOLD: return (const void*)many_kernel<KIND_FWD_FOLD>;
@@ -1178,33 +1176,36 @@ void phase_node_params(const ManyPlan* mp, const Phase& ph, void** params, cudaK
 struct NodeArgs {
   int* counter;
   TcParams tp;
-  const void* s_in;
+  const void* s_field;
+  const void* s_grad;
   void* s_hi;
   void* s_lo;
-  long long s_n2;
-  int s_unsplit;
-  void* params[5];
+  long long s_n2, s_m2;
+  int s_shared, s_unsplit;
+  void* params[8];
 };
 
 // Node parameters of phase k for a call's buffers.
 void node_args(const ManyPlan* mp, Phase& ph, size_t k, const ManyCall& call, NodeArgs& na,
                cudaKernelNodeParams* kp) {
   na.counter = mp->counters + k;
-  if (ph.kind == KIND_SPLIT) {
-    // the chain's input split: the caller's input into BF16 planes in the
-    // second workspace (head plane, then the tail plane `total` pairs on)
-    na.s_in = call.base[BASE_PSI0];
+  if (ph.kind == KIND_SPLITG) {
+    // a backward chain's split: 2 grad * field, the fields in the caller's
+    // gradient buffer, into BF16 planes in the second workspace (head plane,
+    // then the tail plane `total` pairs on)
+    na.s_field = call.base[BASE_OUTC];
+    na.s_grad = call.base[BASE_GRAD];
     na.s_hi = mp->ws2;
     na.s_lo = (uint32_t*)mp->ws2 + mp->total;
     na.s_n2 = mp->total / 2;
+    na.s_m2 = mp->total / 2;
+    na.s_shared = 0;
     na.s_unsplit = 0;
-    na.params[0] = (void*)&na.s_in;
-    na.params[1] = (void*)&na.s_hi;
-    na.params[2] = (void*)&na.s_lo;
-    na.params[3] = (void*)&na.s_n2;
-    na.params[4] = (void*)&na.s_unsplit;
+    void* const args[8] = {(void*)&na.s_field, (void*)&na.s_grad, (void*)&na.s_hi, (void*)&na.s_lo,
+                           (void*)&na.s_n2,    (void*)&na.s_m2,   (void*)&na.s_shared, (void*)&na.s_unsplit};
+    for (int i = 0; i < 8; ++i) na.params[i] = args[i];
     std::memset(kp, 0, sizeof(*kp));
-    kp->func = (void*)bf16_split_func();
+    kp->func = (void*)bf16_split_grad_func();
     kp->gridDim = dim3(bf16_split_grid(mp->total, mp->grid_tc));
     kp->blockDim = dim3(256);
     kp->sharedMemBytes = 0;
@@ -1389,6 +1390,15 @@ int many_expand(ManyPlan* mp, const void* psi0, float* out_d, void* out_c, cudaS
 int many_backward(ManyPlan* mp, const void* psi0, const float* grad, void* grad_psi0, cudaStream_t s,
                   std::string* err) {
   if (!tc_buffers_ok(mp, psi0, grad, grad_psi0, err)) return FFX_EINVAL;
+  if (mp->dense && grad_psi0 == psi0) {
+    // a one-pass instance's first pass reads the caller's input and writes the
+    // gradient buffer (its field) in the same (not in-place) dense pass
+    for (const Instance& in : mp->inst)
+      if (in.ndim == 1 && in.dims[0] > DBM) {
+        *err = "in-place gradient of a dense many-instance plan with a 1-D instance longer than 64 points";
+        return FFX_EUNSUPPORTED;
+      }
+  }
   ManyCall c;
   std::memset(&c, 0, sizeof(c));
   c.base[BASE_PSI0] = psi0;

@@ -1273,7 +1273,7 @@ cudaError_t launch_bf16_split_grad(const float2* field, const float* grad, int g
   return cudaGetLastError();
 }
 
-const void* bf16_split_func() { return (const void*)bf16_split_kernel; }
+const void* bf16_split_grad_func() { return (const void*)bf16_split_grad_kernel; }
 int bf16_split_grid(int64_t n, int sms) {
   int64_t grid = (n / 2 + 255) / 256;
   if (grid > 8 * (int64_t)sms) grid = 8 * (int64_t)sms;
@@ -1327,7 +1327,6 @@ const void* many_bf16_func(int mode) {
   switch (mode) {
     case 1: return (const void*)dense_bf16_many_kernel<kTmaContiguous, false>;
     case 2: return (const void*)dense_bf16_many_kernel<kTmaPlanes, true>;
-    case 3: return (const void*)dense_bf16_many_kernel<kInPlace, true>;
     case 4: return (const void*)dense_bf16_many_kernel<kTmaContiguous, true>;
     default: return (const void*)dense_bf16_many_kernel<kInPlace, false>;
   }
@@ -1336,8 +1335,8 @@ int many_bf16_threads() { return BTHREADS; }
 size_t many_bf16_smem() { return (size_t)BMANY_SMEM; }
 cudaError_t many_bf16_prepare() {
   cudaError_t e = cudaSuccess;
-  for (int m = 0; m < 5 && e == cudaSuccess; ++m)
-    e = cudaFuncSetAttribute(many_bf16_func(m), cudaFuncAttributeMaxDynamicSharedMemorySize, BMANY_SMEM);
+  for (int m : {0, 1, 2, 4})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(many_bf16_func(m), cudaFuncAttributeMaxDynamicSharedMemorySize, BMANY_SMEM);
   return e;
 }
 int many_bf16_lines() { return BL; }

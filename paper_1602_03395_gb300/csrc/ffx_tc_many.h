@@ -61,9 +61,8 @@ int many_tc_row_blocks(int N);
 // of 16: the same work lists and parameters, with split BF16 operand blocks
 // of T (launch_bf16_build_t layout) in TcPassArg::tblk.  No gradient passes.
 // mode 0: FP32 input by per-thread copies; 1: FP32 contiguous lines by TMA
-// tiles (every pass a tile map); 2: BF16 planes by TMA tiles (chains); 3: as
-// 0 with a chain pass's transposed output (a chain's first pass); 4: as 1
-// with that output
+// tiles (every pass a tile map); 2: BF16 planes by TMA tiles (chains); 4: as
+// 1 with a chain pass's transposed output (a chain's first pass)
 const void* many_bf16_func(int mode);
 int many_bf16_threads();
 size_t many_bf16_smem();
@@ -79,9 +78,10 @@ bool many_bf16_line_map(const float2* base, int N, int64_t lines, void* map);
 // points: the head plane at `head` (16-byte aligned), the tail plane `plane`
 // pairs after it (4 * plane a multiple of 16).
 bool many_bf16_plane_map(const uint32_t* head, int N, int64_t lines, int64_t plane, void* map);
-// The input split of a BF16 chain as a graph node: the kernel of
-// launch_bf16_split and its grid for n points.
-const void* bf16_split_func();
+// The grid of launch_bf16_split for n points.
 int bf16_split_grid(int64_t n, int sms);
+// A backward chain's split (launch_bf16_split_grad's kernel) as a graph node:
+// kernel(field float4*, grad float2*, hi uint2*, lo uint2*, n2, m2, shared, unsplit).
+const void* bf16_split_grad_func();
 
 }  // namespace ffx
