@@ -337,3 +337,26 @@ def test_many_chain_new_buffers_modes_and_in_place_field():
             worst_f = max(worst_f, rel_l2(field[off:off + m].reshape(dims), ref))
     print(f"many chain buffers/modes: worst density {worst_d:.2e}, worst field {worst_f:.2e}")
     assert worst_d < DENSITY_TOL and worst_f < FIELD_TOL
+
+
+def test_many_backward_in_place_guard():
+    """A backward call whose gradient buffer is its input: a 1-D instance of
+    more than 64 points would read and write that buffer in one dense pass,
+    so the call is refused (FFX_EUNSUPPORTED) on the host; without such an
+    instance it runs and equals the out-of-place gradient."""
+    ffx = require_gpu()
+    rng = np.random.default_rng(21)
+    with ffx.PlanMany([((96,), (0.1,), 1.0, (40,)), ((32, 32), (0.2, 0.2), 2.0, (30, 30))], form="tc") as plan:
+        x = to_dev(rng.normal(size=plan.points).astype(np.complex64))
+        g = to_dev(rng.normal(size=plan.points).astype(np.float32))
+        with pytest.raises(ffx.FfxError) as ei:
+            ffx.ffx_expand_backward(plan, x, g, x)
+        assert ei.value.code == ffx.FFX_EUNSUPPORTED
+    with ffx.PlanMany([((64,), (0.1,), 1.0, (40,)), ((32, 64), (0.2, 0.2), 2.0, (30, 30))], form="tc") as plan:
+        x = to_dev((rng.normal(size=plan.points) + 1j * rng.normal(size=plan.points)).astype(np.complex64))
+        g = to_dev(rng.normal(size=plan.points).astype(np.float32))
+        ref = ffx.ffx_expand_backward(plan, x, g).clone()
+        y = x.clone()
+        ffx.ffx_expand_backward(plan, y, g, y)
+        assert torch.equal(y, ref)
+        assert plan.device_errors() == 0
